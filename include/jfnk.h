@@ -1,0 +1,202 @@
+/*
+ * jfnk.h -- C ABI of the GB300 (sm_103a) symmetry-preserving JFNK hot path.
+ *
+ * The library evaluates, on one GPU, the matrix-free pieces of the implicit
+ * solver of Hossain & Alam, "Assessment of a symmetry-preserving JFNK method
+ * for atmospheric convection":
+ *
+ *   F(u)   semi-discrete right-hand side of the dry nonhydrostatic equations
+ *          (Section 2.1, Eqs. ch2_28-ch2_30; Eq. ds), discretised with the
+ *          Deslauriers-Dubuc collocation derivative (Section 2.3), the
+ *          skew-symmetric convective form (Section 2.2) and constant or
+ *          Smagorinsky exchange coefficients (Section 2.4, Table 1);
+ *   R(u)   trapezoidal residual 2u/dt - F(u) - [2u^n/dt + F(u^n)] (Eq. ns);
+ *   J v    finite-difference Jacobian-vector product (Eq. fd);
+ *   M^-1 r field-block physics-based preconditioner (Section 2.5.2);
+ *   step   one implicit step by inexact Newton + restarted right-preconditioned
+ *          GMRES(m) (Section 2.5.1, Eq. jv).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - State vectors are float64, field-major, x fastest:
+ *     2D: [field][z][x], fields (u, w, theta, p)
+ *     3D: [field][z][y][x], fields (u, v, w, theta, p)
+ *   theta is the potential-temperature perturbation, p the c_p-scaled Exner
+ *   perturbation.  n = n_fields * nx * ny * nz values (ny = 1 in 2D).
+ * - Grid: x (and y) periodic with nodes x_i = -lx/2 + i lx/nx; z cell-centred,
+ *   z_k = (k + 1/2) lz/nz, mirror walls at z = 0 and z = lz (w odd; theta, p
+ *   even; u, v even for free slip, odd for no slip).
+ * - Unless stated otherwise, vector arguments are DEVICE pointers owned by the
+ *   caller (e.g. torch tensor data pointers), 8-byte aligned, not aliased with
+ *   each other.  The library owns its workspace, allocated once in
+ *   jfnk_create; no entry point allocates afterwards.
+ * - Every call is enqueued on the handle's CUDA stream.  Calls that fill a
+ *   host struct (jfnk_step, jfnk_budgets, jfnk_get_*) synchronise that stream
+ *   before returning; the others return without synchronising.
+ * - Errors are returned as jfnk_status; nothing is thrown across the ABI.
+ *   On JFNK_ERR_INVALID_ARG nothing was enqueued and no state changed.
+ *   On JFNK_ERR_CUDA the handle should be destroyed.
+ * - A handle is not thread-safe: one host thread at a time, one stream.
+ */
+#ifndef JFNK_H
+#define JFNK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    JFNK_OK = 0,
+    JFNK_ERR_INVALID_ARG = 1,   /* bad size, pointer, option; nothing enqueued   */
+    JFNK_ERR_CUDA = 2,          /* a CUDA runtime call failed                     */
+    JFNK_ERR_OOM = 3,           /* workspace allocation failed in jfnk_create     */
+    JFNK_ERR_NOT_CONVERGED = 4, /* Newton hit max_newton above tolerance          */
+    JFNK_ERR_BREAKDOWN = 5,     /* GMRES found no descent (zero Krylov space)     */
+    JFNK_ERR_NAN = 6,           /* a residual norm was not finite                 */
+    JFNK_ERR_TIMEOUT = 7,       /* a bounded device loop hit its iteration cap    */
+    JFNK_ERR_UNSUPPORTED = 8    /* valid request this build does not implement    */
+} jfnk_status;
+
+enum { JFNK_FREESLIP = 0, JFNK_NOSLIP = 1 };
+enum { JFNK_SGS_CONST = 0, JFNK_SGS_SMAGORINSKY = 1 };
+enum { JFNK_FP64 = 0, JFNK_MIXED = 1 };
+enum { JFNK_PC_NONE = 0, JFNK_PC_BLOCK = 1 };
+
+/* Largest Krylov dimension m accepted by jfnk_create. */
+#define JFNK_MAX_KRYLOV 32
+/* Length of the per-step history arrays in jfnk_stats. */
+#define JFNK_MAX_NEWTON 32
+
+/* Grid (Section 3.1 / 3.2 domains).  dim = 2 or 3; ny = 1 when dim = 2.
+ * nx, ny >= 1 and nz >= 2(2p-2) (one mirror reflection must cover the
+ * stencil's two-level halo).  Lengths in metres.  bc_* select the parity of
+ * the horizontal velocity at the bottom / top wall. */
+typedef struct {
+    int dim, nx, ny, nz;
+    double lx, ly, lz;
+    int bc_bottom, bc_top;
+} jfnk_grid;
+
+/* Stratification and thermodynamics (Section 2.1).  theta0 [K] background
+ * potential temperature; beta = d(theta_bar)/dz [K/m]; pbar the constant base
+ * Exner value multiplying div(u) in Eq. ch2_28 (c_p = 1004 by default);
+ * gamma_p the coefficient of that term (R/c_v); g [m/s^2]; rho0 [kg/m^3] and
+ * cp [J/(kg K)] convert the surface heat flux into a theta source. */
+typedef struct {
+    double theta0, beta, pbar, g, gamma_p, rho0, cp;
+} jfnk_strat;
+
+/* Sub-grid closure (Section 2.4).  mode JFNK_SGS_CONST uses K_M, K_H [m^2/s]
+ * (Table 1); JFNK_SGS_SMAGORINSKY uses nu = (Cs Delta)^2 sqrt(2 S:S),
+ * Delta = (dx dz)^(1/2) in 2D, (dx dy dz)^(1/3) in 3D, K_M = nu, K_H = nu/Pr. */
+typedef struct {
+    int mode;
+    double K_M, K_H, Cs, Pr;
+} jfnk_sgs;
+
+/* Solver options.
+ * precision   JFNK_FP64: every kernel in float64.
+ *             JFNK_MIXED: stencils of the Jacobian-vector product, Krylov basis
+ *             and preconditioner in float32; the Newton residual, the FD
+ *             difference quotient, Hessenberg/Givens and the update in float64.
+ * wavelet_p   order p of the Deslauriers-Dubuc derivative (2 supported).
+ * krylov_m    restart length m (1..JFNK_MAX_KRYLOV).
+ * flexible    accepted for compatibility; the library always stores the
+ *             preconditioned directions (FGMRES form), identical in exact
+ *             arithmetic to right-preconditioned GMRES for a linear M.
+ * precond     JFNK_PC_NONE or JFNK_PC_BLOCK (pc_sweeps Chebyshev steps per block).
+ * newton_rtol, newton_atol_factor, eta, max_newton, max_restarts: stopping rules
+ *             ||W R|| <= max(rtol ||W R_0||, atol_factor ||W 2u^n/dt||);
+ *             GMRES stops at ||W(R + J du)|| <= eta ||W R||.
+ * dt          time step [s].
+ * scale_*     field scales U, Theta, P of the diagonal scaling W used for
+ *             norms, the FD step and the Krylov inner product. */
+typedef struct {
+    int precision, wavelet_p, krylov_m, flexible, precond, pc_sweeps;
+    double newton_rtol, newton_atol_factor, eta;
+    int max_newton, max_restarts;
+    double dt, scale_u, scale_theta, scale_p;
+} jfnk_opts;
+
+/* Per-step report filled by jfnk_step / jfnk_step_host. */
+typedef struct {
+    int newton_iters;                        /* Newton corrections taken            */
+    int gmres_iters;                         /* Krylov iterations over all Newtons  */
+    int restarts;                            /* GMRES restarts over all Newtons     */
+    int converged;                           /* 1 if the Newton test was met        */
+    double res0, res_final, tol;             /* ||W R|| at start / end, threshold   */
+    double res_hist[JFNK_MAX_NEWTON + 1];    /* ||W R|| after each correction       */
+    int gmres_per_newton[JFNK_MAX_NEWTON];   /* Krylov iterations per correction    */
+} jfnk_stats;
+
+/* Budgets of Section 3.1.3 (literal E_k, E_p) plus conservation diagnostics. */
+typedef struct {
+    double E_k, E_p, sum_theta, sum_div;
+    double max[5], min[5];
+} jfnk_budget;
+
+typedef struct jfnk_handle jfnk_handle;
+
+/* Create a solver for one grid.  Validates every field of the four structs,
+ * allocates all device workspace on the current device and binds the handle
+ * to `cuda_stream` (a cudaStream_t, NULL for the legacy default stream).
+ * *out receives the handle, or NULL on error. */
+jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* strat,
+                        const jfnk_sgs* sgs, const jfnk_opts* opts,
+                        void* cuda_stream, jfnk_handle** out);
+
+/* Free the workspace and the handle (NULL is accepted). */
+jfnk_status jfnk_destroy(jfnk_handle* h);
+
+/* Surface heat-flux anomaly H [W/m^2] of Section 3.2, device float64 array of
+ * nx (2D) or ny*nx (3D) values; it adds H/(rho0 cp dz) to the theta tendency
+ * of the bottom row.  The array is copied into the workspace; NULL clears it. */
+jfnk_status jfnk_set_surface_flux(jfnk_handle* h, const double* H);
+
+/* F(u) of Eq. ds for all fields: u, F are n-vectors (see conventions).
+ * Evaluated in the handle's stencil precision (float32 when MIXED, with u
+ * rounded to float32; float64 otherwise). */
+jfnk_status jfnk_rhs(jfnk_handle* h, const double* u, double* F);
+
+/* Trapezoidal residual R(u) = 2u/dt - F(u) - 2u_n/dt - F(u_n) (Eq. ns), always float64. */
+jfnk_status jfnk_residual(jfnk_handle* h, const double* u_n, const double* u, double* R);
+
+/* Forward-difference Jacobian-vector product of R (Eq. fd), unscaled units:
+ *   Jv = 2 v/dt - (F(u + eps v) - F(u)) / eps.
+ * F_u may be NULL (then F(u) is evaluated here) or F(u) from jfnk_rhs.
+ * eps > 0 is used as given; eps <= 0 selects the rule
+ *   eps = sqrt(eps_mach (1 + ||W u||)) / ||W v||
+ * with eps_mach = 2^-52 (FP64) or 2^-23 (MIXED).  *eps_out (host pointer,
+ * may be NULL) receives the step used; this synchronises the stream. */
+jfnk_status jfnk_jv(jfnk_handle* h, const double* u, const double* F_u, const double* v,
+                    double eps, double* Jv, double* eps_out);
+
+/* Field-block preconditioner z = M^-1 r (Section 2.5.2) with the exchange
+ * coefficients frozen at state u; r and z in scaled units (W applied).
+ * With JFNK_PC_NONE z = r. */
+jfnk_status jfnk_precond_apply(jfnk_handle* h, const double* u, const double* r, double* z);
+
+/* One implicit step u^n -> u^{n+1} in place on the device vector u.
+ * Returns JFNK_ERR_NOT_CONVERGED (u holds the last iterate) when the Newton
+ * test is not met within max_newton corrections.  `out` may be NULL. */
+jfnk_status jfnk_step(jfnk_handle* h, double* u, jfnk_stats* out);
+
+/* Same as jfnk_step for a HOST state vector: copies u_host to the device,
+ * steps, and copies the result back (pinned memory recommended). */
+jfnk_status jfnk_step_host(jfnk_handle* h, double* u_host, jfnk_stats* out);
+
+/* Energy budgets and extremes of the device state u (Section 3.1.3). */
+jfnk_status jfnk_budgets(jfnk_handle* h, const double* u, jfnk_budget* out);
+
+/* Number of this library's kernel launches enqueued since the handle was created. */
+jfnk_status jfnk_get_launch_count(jfnk_handle* h, long long* out);
+
+/* Static description of a status code. */
+const char* jfnk_status_str(jfnk_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JFNK_H */

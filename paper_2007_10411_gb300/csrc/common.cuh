@@ -1,0 +1,157 @@
+// Device-side definitions shared by the kernels of libjfnk (sm_103a).
+//
+// Vectors are field-major planes [field][z][x] (x fastest), n = nf * npt
+// entries.  Krylov vectors live in scaled units (every field divided by its
+// scale U, U, Theta, P); the state and the Newton residual are float64 and
+// unscaled.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/jfnk.h"
+
+namespace jfnk {
+
+constexpr int KMAX = 32;          // largest restart length the kernels are built for
+constexpr int NTHREADS = 256;     // threads per block of every streaming kernel
+constexpr int MAX_STREAM_BLOCKS = 2 * 152;  // streaming grid: two CTAs per SM
+
+// Geometry and physics constants, passed by value to the stencil kernels.
+struct Geo {
+    int nx, nz, npt, nf;
+    int pb[5], pt[5];                 // mirror parity per field at bottom / top (+1 / -1)
+    double inv_dx, inv_dz;
+    double theta0, beta, pbar, g, gamma_p, heat_coef;   // heat_coef = 1/(rho0 cp dz)
+    int smag;
+    double K_M, K_H, cs2;             // cs2 = (Cs Delta)^2
+    double inv_Pr;
+    double two_over_dt;
+    double scale[5], inv_scale[5];
+    const double* heat;               // surface flux H(x) or nullptr
+};
+
+// Solver control block in device memory.  Written by the "last block" of the
+// reduction kernels, read by later kernels and, after a stream sync, by the host.
+struct Ctl {
+    int done;            // current GMRES cycle finished: later cycle kernels return at once
+    int converged;       // |g_{j+1}| <= target (or lucky breakdown)
+    int breakdown;
+    int nan;
+    int k;               // columns in the finished cycle
+    int iters;           // Krylov iterations in this Newton solve
+    int m;               // restart length
+    int pad_;
+    double beta0;        // ||b|| of the Newton system
+    double target;       // eta * beta0
+    double res2;         // ||W R||^2 of the last residual evaluation
+    double unorm2;       // ||W u||^2 of the same state
+    double eps_mach;     // unit roundoff of the stencil precision
+    double eps_jv;       // finite-difference step of the next Jacobian-vector product
+    double inv_hn;       // 1 / h_{j+1,j} for pass C
+    double kmax;         // max eddy coefficient K_M (preconditioner bounds)
+    double scratch[8];   // misc reductions (||x||^2, ||r||^2, ...)
+    double h1[KMAX + 1];
+    double hsum[KMAX + 1];
+    double Hbar[KMAX + 1][KMAX];     // Hessenberg as built (row, col)
+    double Rt[KMAX][KMAX];           // rotated upper-triangular factor
+    double cs[KMAX], sn[KMAX];
+    double g[KMAX + 1];
+    double y[KMAX];
+    unsigned int counter[8];         // last-block counters, one per kernel family
+};
+
+enum CounterSlot { CNT_STENCIL = 0, CNT_PASSA, CNT_PASSB, CNT_UPDATE, CNT_RESTART, CNT_PC, CNT_EDDY, CNT_MISC };
+
+// ---------------------------------------------------------------- reductions
+// Sum NV thread-local doubles over the block and store them at
+// part[k * stride + blk] (k < nv).  Deterministic (fixed shuffle tree).
+template <int NV>
+__device__ __forceinline__ void block_partials(const double (&v)[NV], int nv, double* part,
+                                               int stride, int blk) {
+    __shared__ double red[NV][NTHREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        if (k < nv) {
+            double s = v[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) red[k][warp] = s;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += red[k][w];
+        part[(size_t)k * stride + blk] = s;
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ void block_partials_max(const double (&v)[NV], int nv, double* part,
+                                                   int stride, int blk) {
+    __shared__ double red[NV][NTHREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        if (k < nv) {
+            double s = v[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+            if (lane == 0) red[k][warp] = s;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        double s = red[k][0];
+        for (int w = 1; w < nw; ++w) s = fmax(s, red[k][w]);
+        part[(size_t)k * stride + blk] = s;
+    }
+}
+
+// True in exactly one block: the last one to arrive.  Counters wrap to zero
+// by themselves (atomicInc limit), so no reset is needed between launches.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int total) {
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicInc(counter, total - 1);
+        am_last = (t == total - 1);
+    }
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
+}
+
+// In the last block: out[k] = sum over blocks of part[k * nblk + b], fixed order.
+__device__ __forceinline__ void final_sums(const double* part, int nblk, int nv, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int k = warp; k < nv; k += nw) {
+        double s = 0.0;
+        for (int b = lane; b < nblk; b += 32) s += __ldcg(part + (size_t)k * nblk + b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) out[k] = s;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void final_maxes(const double* part, int nblk, int nv, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int k = warp; k < nv; k += nw) {
+        double s = -1.0e300;
+        for (int b = lane; b < nblk; b += 32) s = fmax(s, __ldcg(part + (size_t)k * nblk + b));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+        if (lane == 0) out[k] = s;
+    }
+    __syncthreads();
+}
+
+}  // namespace jfnk

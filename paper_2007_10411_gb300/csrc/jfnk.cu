@@ -1,0 +1,580 @@
+// C ABI of libjfnk: handle management, argument validation, the per-call
+// entry points and the implicit-step driver (inexact Newton, Section 2.5.1,
+// around restarted GMRES(m) on the device).
+//
+// The host only sequences kernels and reads the device control block once
+// per GMRES cycle and once per Newton correction; every vector operation of
+// the step runs in this library's kernels.  The end of a cycle is detected
+// with a pipelined poll: after enqueueing Arnoldi step j the host waits for
+// step j - LAG and stops enqueueing once that step reports the cycle done
+// (steps enqueued after the finish return at entry).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace jfnk;
+
+namespace {
+constexpr int LAG = 2;
+}
+
+struct jfnk_handle {
+    jfnk_grid grid;
+    jfnk_strat strat;
+    jfnk_sgs sgs;
+    jfnk_opts opts;
+    cudaStream_t stream;
+    Geo G;
+    size_t npt, n, ld;
+    int mixed, m;
+    // float64 buffers
+    double *un, *f, *R, *Fu64, *x, *tmp64, *udev, *heat, *budg;
+    // stencil-precision buffers (double for FP64, float for MIXED)
+    void *V, *Z, *w, *uT, *xT, *za, *zb, *da, *db, *nu, *tA, *tB;
+    double* part;
+    Ctl* ctl;
+    Ctl* hctl;       // pinned mirror of the control header
+    int* hdone;      // pinned ring of per-step "done" flags
+    cudaEvent_t ev[KMAX];
+    long long launches;
+};
+
+#define CK(call)                                                                  \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            fprintf(stderr, "libjfnk: %s failed: %s (%s:%d)\n", #call,            \
+                    cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+            return JFNK_ERR_CUDA;                                                 \
+        }                                                                         \
+    } while (0)
+
+static const size_t CTL_HEAD = offsetof(Ctl, h1);
+
+// ------------------------------------------------------------------ helpers
+static bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+static jfnk_status validate(const jfnk_grid* g, const jfnk_strat* s, const jfnk_sgs* q,
+                            const jfnk_opts* o) {
+    if (!g || !s || !q || !o) return JFNK_ERR_INVALID_ARG;
+    if (g->dim != 2 && g->dim != 3) return JFNK_ERR_INVALID_ARG;
+    if (g->nx < 1 || g->nz < 1 || (g->dim == 3 && g->ny < 1)) return JFNK_ERR_INVALID_ARG;
+    if (!finite_pos(g->lx) || !finite_pos(g->lz) || (g->dim == 3 && !finite_pos(g->ly)))
+        return JFNK_ERR_INVALID_ARG;
+    if ((g->bc_bottom != JFNK_FREESLIP && g->bc_bottom != JFNK_NOSLIP) ||
+        (g->bc_top != JFNK_FREESLIP && g->bc_top != JFNK_NOSLIP))
+        return JFNK_ERR_INVALID_ARG;
+    if (!finite_pos(s->theta0) || !isfinite(s->beta) || !isfinite(s->pbar) || !isfinite(s->g) ||
+        !isfinite(s->gamma_p) || !finite_pos(s->rho0) || !finite_pos(s->cp))
+        return JFNK_ERR_INVALID_ARG;
+    if (q->mode != JFNK_SGS_CONST && q->mode != JFNK_SGS_SMAGORINSKY) return JFNK_ERR_INVALID_ARG;
+    if (!(q->K_M >= 0.0) || !(q->K_H >= 0.0) || !(q->Cs >= 0.0) || !finite_pos(q->Pr) ||
+        !isfinite(q->K_M) || !isfinite(q->K_H) || !isfinite(q->Cs))
+        return JFNK_ERR_INVALID_ARG;
+    if (o->precision != JFNK_FP64 && o->precision != JFNK_MIXED) return JFNK_ERR_INVALID_ARG;
+    if (o->krylov_m < 1 || o->krylov_m > JFNK_MAX_KRYLOV) return JFNK_ERR_INVALID_ARG;
+    if (o->precond != JFNK_PC_NONE && o->precond != JFNK_PC_BLOCK) return JFNK_ERR_INVALID_ARG;
+    if (o->pc_sweeps < 1 || o->pc_sweeps > 64) return JFNK_ERR_INVALID_ARG;
+    if (!finite_pos(o->newton_rtol) || !(o->newton_atol_factor >= 0.0) ||
+        !(o->eta > 0.0 && o->eta < 1.0))
+        return JFNK_ERR_INVALID_ARG;
+    if (o->max_newton < 0 || o->max_newton > JFNK_MAX_NEWTON || o->max_restarts < 0)
+        return JFNK_ERR_INVALID_ARG;
+    if (!finite_pos(o->dt) || !finite_pos(o->scale_u) || !finite_pos(o->scale_theta) ||
+        !finite_pos(o->scale_p))
+        return JFNK_ERR_INVALID_ARG;
+    if (o->wavelet_p < 1) return JFNK_ERR_INVALID_ARG;
+    // implemented subset
+    if (g->dim != 2 || o->wavelet_p != 2) return JFNK_ERR_UNSUPPORTED;
+    if (g->nz < 4) return JFNK_ERR_INVALID_ARG;      // one mirror reflection covers the halo
+    return JFNK_OK;
+}
+
+static void free_all(jfnk_handle* h) {
+    void* dev[] = {h->un, h->f, h->R, h->Fu64, h->x, h->tmp64, h->udev, h->heat, h->budg,
+                   h->V, h->Z, h->w, h->uT, h->xT, h->za, h->zb, h->da, h->db, h->nu,
+                   h->tA, h->tB, h->part, h->ctl};
+    for (void* p : dev)
+        if (p) cudaFree(p);
+    if (h->hctl) cudaFreeHost(h->hctl);
+    if (h->hdone) cudaFreeHost(h->hdone);
+    for (int i = 0; i < KMAX; ++i)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+}
+
+template <typename T>
+static int stencil_part_blocks(const Geo& G) {
+    return stencil_blocks<T>(G) * 4;
+}
+
+// ------------------------------------------------------------------ create
+extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* strat,
+                                   const jfnk_sgs* sgs, const jfnk_opts* opts, void* cuda_stream,
+                                   jfnk_handle** out) {
+    if (!out) return JFNK_ERR_INVALID_ARG;
+    *out = nullptr;
+    jfnk_status st = validate(grid, strat, sgs, opts);
+    if (st != JFNK_OK) return st;
+    jfnk_handle* h = new (std::nothrow) jfnk_handle;
+    if (!h) return JFNK_ERR_OOM;
+    memset(h, 0, sizeof(*h));
+    h->grid = *grid;
+    h->strat = *strat;
+    h->sgs = *sgs;
+    h->opts = *opts;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->mixed = opts->precision == JFNK_MIXED;
+    h->m = opts->krylov_m;
+    h->npt = (size_t)grid->nx * grid->nz;
+    h->n = 4 * h->npt;
+    h->ld = (h->n + 63) / 64 * 64;
+
+    Geo& G = h->G;
+    memset(&G, 0, sizeof(G));
+    G.nx = grid->nx;
+    G.nz = grid->nz;
+    G.npt = (int)h->npt;
+    G.nf = 4;
+    const int sb = grid->bc_bottom == JFNK_FREESLIP ? 1 : -1;
+    const int stp = grid->bc_top == JFNK_FREESLIP ? 1 : -1;
+    const int pb[4] = {sb, -1, 1, 1}, pt[4] = {stp, -1, 1, 1};
+    for (int f = 0; f < 4; ++f) { G.pb[f] = pb[f]; G.pt[f] = pt[f]; }
+    const double dx = grid->lx / grid->nx, dz = grid->lz / grid->nz;
+    G.inv_dx = 1.0 / dx;
+    G.inv_dz = 1.0 / dz;
+    G.theta0 = strat->theta0;
+    G.beta = strat->beta;
+    G.pbar = strat->pbar;
+    G.g = strat->g;
+    G.gamma_p = strat->gamma_p;
+    G.heat_coef = 1.0 / (strat->rho0 * strat->cp * dz);
+    G.smag = sgs->mode == JFNK_SGS_SMAGORINSKY;
+    G.K_M = G.smag ? 0.0 : sgs->K_M;
+    G.K_H = G.smag ? 0.0 : sgs->K_H;
+    const double delta = sqrt(dx * dz);
+    G.cs2 = (sgs->Cs * delta) * (sgs->Cs * delta);
+    G.inv_Pr = 1.0 / sgs->Pr;
+    G.two_over_dt = 2.0 / opts->dt;
+    const double sc[4] = {opts->scale_u, opts->scale_u, opts->scale_theta, opts->scale_p};
+    for (int f = 0; f < 4; ++f) { G.scale[f] = sc[f]; G.inv_scale[f] = 1.0 / sc[f]; }
+    G.heat = nullptr;
+
+    const size_t eT = h->mixed ? sizeof(float) : sizeof(double);
+    const size_t nb8 = h->ld * sizeof(double);
+    const size_t nbT = h->ld * eT;
+    const int m = h->m;
+    int maxblk = MAX_STREAM_BLOCKS;
+    maxblk = std::max(maxblk, stencil_part_blocks<double>(G));
+    maxblk = std::max(maxblk, stencil_part_blocks<float>(G));
+    const size_t part_len = (size_t)maxblk * (KMAX + 2) + 16 * (size_t)MAX_STREAM_BLOCKS;
+
+#define ALLOC(ptr, bytes)                                                         \
+    do {                                                                          \
+        if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) {                 \
+            cudaGetLastError();                                                   \
+            free_all(h);                                                          \
+            delete h;                                                             \
+            return JFNK_ERR_OOM;                                                  \
+        }                                                                         \
+    } while (0)
+    ALLOC(h->un, nb8);
+    ALLOC(h->f, nb8);
+    ALLOC(h->R, nb8);
+    if (!h->mixed) ALLOC(h->Fu64, nb8);
+    ALLOC(h->x, nb8);
+    ALLOC(h->tmp64, nb8);
+    ALLOC(h->udev, nb8);
+    ALLOC(h->heat, (size_t)grid->nx * sizeof(double));
+    ALLOC(h->budg, 64 * sizeof(double));
+    ALLOC(h->V, (size_t)(m + 1) * nbT);
+    if (opts->precond == JFNK_PC_BLOCK) ALLOC(h->Z, (size_t)m * nbT);
+    ALLOC(h->w, nbT);
+    if (h->mixed) {
+        ALLOC(h->uT, nbT);
+        ALLOC(h->xT, nbT);
+    }
+    ALLOC(h->za, nbT);
+    ALLOC(h->zb, nbT);
+    ALLOC(h->da, nbT);
+    ALLOC(h->db, nbT);
+    ALLOC(h->nu, h->npt * eT);
+    ALLOC(h->tA, nbT);
+    ALLOC(h->tB, nbT);
+    ALLOC(h->part, part_len * sizeof(double));
+    ALLOC(h->ctl, sizeof(Ctl));
+#undef ALLOC
+    if (cudaMallocHost((void**)&h->hctl, sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->hdone, KMAX * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        return JFNK_ERR_OOM;
+    }
+    for (int i = 0; i < KMAX; ++i) {
+        if (cudaEventCreateWithFlags(&h->ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            free_all(h);
+            delete h;
+            return JFNK_ERR_CUDA;
+        }
+    }
+    Ctl init;
+    memset(&init, 0, sizeof(init));
+    init.eps_mach = h->mixed ? ldexp(1.0, -23) : ldexp(1.0, -52);
+    init.m = m;
+    if (cudaMemcpy(h->ctl, &init, sizeof(Ctl), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(h->part, 0, part_len * sizeof(double)) != cudaSuccess ||
+        cudaMemset(h->x, 0, nb8) != cudaSuccess) {
+        free_all(h);
+        delete h;
+        return JFNK_ERR_CUDA;
+    }
+    *out = h;
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_destroy(jfnk_handle* h) {
+    if (!h) return JFNK_OK;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_set_surface_flux(jfnk_handle* h, const double* H) {
+    if (!h) return JFNK_ERR_INVALID_ARG;
+    if (H == nullptr) {
+        h->G.heat = nullptr;
+        return JFNK_OK;
+    }
+    CK(cudaMemcpyAsync(h->heat, H, (size_t)h->grid.nx * sizeof(double), cudaMemcpyDeviceToDevice,
+                       h->stream));
+    h->G.heat = h->heat;
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_get_launch_count(jfnk_handle* h, long long* out) {
+    if (!h || !out) return JFNK_ERR_INVALID_ARG;
+    *out = h->launches;
+    return JFNK_OK;
+}
+
+// ------------------------------------------------------------ per-call ABI
+template <typename T>
+static jfnk_status rhs_impl(jfnk_handle* h, const double* u, double* F) {
+    cudaStream_t s = h->stream;
+    if (sizeof(T) == sizeof(double)) {
+        CK(launch_stencil<double>(MODE_F, h->G, u, nullptr, nullptr, nullptr, F, nullptr, h->part,
+                                  h->ctl, 0, s));
+        h->launches += 1;
+        return JFNK_OK;
+    }
+    T* uT = (T*)h->tA;
+    T* FT = (T*)h->tB;
+    CK((launch_convert<double, T>(u, uT, h->n, s)));
+    CK(launch_stencil<T>(MODE_F, h->G, uT, nullptr, nullptr, nullptr, FT, nullptr, h->part, h->ctl,
+                         0, s));
+    CK((launch_convert<T, double>(FT, F, h->n, s)));
+    h->launches += 3;
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_rhs(jfnk_handle* h, const double* u, double* F) {
+    if (!h || !u || !F) return JFNK_ERR_INVALID_ARG;
+    return h->mixed ? rhs_impl<float>(h, u, F) : rhs_impl<double>(h, u, F);
+}
+
+extern "C" jfnk_status jfnk_residual(jfnk_handle* h, const double* u_n, const double* u, double* R) {
+    if (!h || !u_n || !u || !R) return JFNK_ERR_INVALID_ARG;
+    cudaStream_t s = h->stream;
+    CK(launch_stencil<double>(MODE_RHS, h->G, u_n, nullptr, nullptr, nullptr, h->tmp64, nullptr,
+                              h->part, h->ctl, 0, s));
+    CK(launch_stencil<double>(MODE_RES, h->G, u, nullptr, nullptr, h->tmp64, R, nullptr, h->part,
+                              h->ctl, 0, s));
+    h->launches += 2;
+    return JFNK_OK;
+}
+
+template <typename T>
+static jfnk_status jv_impl(jfnk_handle* h, const double* u, const double* F_u, const double* v,
+                           double eps, double* Jv) {
+    cudaStream_t s = h->stream;
+    const Geo& G = h->G;
+    CK(launch_norm2<double>(G, u, h->n, 1, 2, h->part, h->ctl, s));
+    CK(launch_norm2<double>(G, v, h->n, 1, 3, h->part, h->ctl, s));
+    CK(launch_set_eps(eps, 2, 3, h->ctl, s));
+    T* vh = (T*)h->tA;
+    T* wh = (T*)h->tB;
+    CK((launch_rescale<double, T>(G, v, vh, h->n, 0, s)));
+    h->launches += 4;
+    if (sizeof(T) == sizeof(double)) {
+        const double* Fu = F_u;
+        if (!Fu) {
+            CK(launch_stencil<double>(MODE_F, G, u, nullptr, nullptr, nullptr, h->tmp64, nullptr,
+                                      h->part, h->ctl, 0, s));
+            Fu = h->tmp64;
+            h->launches += 1;
+        }
+        CK(launch_stencil<double>(MODE_JV, G, u, (const double*)vh, Fu, nullptr, (double*)wh,
+                                  nullptr, h->part, h->ctl, 0, s));
+    } else {
+        T* uT = (T*)h->uT;
+        CK((launch_convert<double, T>(u, uT, h->n, s)));
+        CK(launch_jv_diff<T>(G, uT, vh, wh, h->part, h->ctl, 0, s));
+        h->launches += 1;
+    }
+    CK((launch_rescale<T, double>(G, wh, Jv, h->n, 1, s)));
+    h->launches += 2;
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_jv(jfnk_handle* h, const double* u, const double* F_u, const double* v,
+                               double eps, double* Jv, double* eps_out) {
+    if (!h || !u || !v || !Jv || !isfinite(eps)) return JFNK_ERR_INVALID_ARG;
+    jfnk_status st = h->mixed ? jv_impl<float>(h, u, F_u, v, eps, Jv) : jv_impl<double>(h, u, F_u, v, eps, Jv);
+    if (st != JFNK_OK) return st;
+    if (eps_out) {
+        CK(cudaMemcpyAsync(h->hctl, h->ctl, CTL_HEAD, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        *eps_out = h->hctl->eps_jv;
+    }
+    return JFNK_OK;
+}
+
+template <typename T>
+static jfnk_status precond_impl(jfnk_handle* h, const double* u, const double* r, double* z) {
+    cudaStream_t s = h->stream;
+    const Geo& G = h->G;
+    if (h->opts.precond == JFNK_PC_NONE) {
+        CK(cudaMemcpyAsync(z, r, h->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        return JFNK_OK;
+    }
+    const T* uT;
+    const T* rT;
+    T* zT;
+    if (sizeof(T) == sizeof(double)) {
+        uT = (const T*)u;
+        rT = (const T*)r;
+        zT = (T*)z;
+    } else {
+        CK((launch_convert<double, T>(u, (T*)h->uT, h->n, s)));
+        CK((launch_convert<double, T>(r, (T*)h->tA, h->n, s)));
+        h->launches += 2;
+        uT = (const T*)h->uT;
+        rT = (const T*)h->tA;
+        zT = (T*)h->tB;
+    }
+    if (G.smag) {
+        CK(launch_eddy<T>(G, uT, (T*)h->nu, h->part, h->ctl, s));
+        h->launches += 1;
+    }
+    CK(launch_precond<T>(G, h->opts.pc_sweeps, rT, zT, (T*)h->za, (T*)h->zb, (T*)h->da, (T*)h->db,
+                         (const T*)h->nu, h->part, h->ctl, 0, s, &h->launches));
+    if (sizeof(T) != sizeof(double)) {
+        CK((launch_convert<T, double>(zT, z, h->n, s)));
+        h->launches += 1;
+    }
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_precond_apply(jfnk_handle* h, const double* u, const double* r, double* z) {
+    if (!h || !u || !r || !z) return JFNK_ERR_INVALID_ARG;
+    return h->mixed ? precond_impl<float>(h, u, r, z) : precond_impl<double>(h, u, r, z);
+}
+
+// ------------------------------------------------------------------- step
+static jfnk_status read_ctl(jfnk_handle* h) {
+    CK(cudaMemcpyAsync(h->hctl, h->ctl, CTL_HEAD, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return JFNK_OK;
+}
+
+// Jacobian-vector product of the Newton system in scaled units: w = J_hat z.
+template <typename T>
+static jfnk_status apply_jv(jfnk_handle* h, const T* uT, const T* z, T* w, int check_done) {
+    if (sizeof(T) == sizeof(double)) {
+        CK(launch_stencil<double>(MODE_JV, h->G, (const double*)uT, (const double*)z, h->Fu64,
+                                  nullptr, (double*)w, nullptr, h->part, h->ctl, check_done, h->stream));
+    } else {
+        CK(launch_jv_diff<T>(h->G, uT, z, w, h->part, h->ctl, check_done, h->stream));
+    }
+    h->launches += 1;
+    return JFNK_OK;
+}
+
+// Restarted GMRES(m) on J_hat x = -W R from x = 0 (cycle_init already enqueued).
+template <typename T>
+static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* restarts, int* conv) {
+    cudaStream_t s = h->stream;
+    const Geo& G = h->G;
+    const size_t n = h->n, ld = h->ld;
+    const int m = h->m;
+    const bool pc = h->opts.precond == JFNK_PC_BLOCK;
+    T* V = (T*)h->V;
+    T* Z = pc ? (T*)h->Z : V;
+    T* w = (T*)h->w;
+    T* xT = h->mixed ? (T*)h->xT : (T*)h->x;
+    *restarts = 0;
+    *conv = 0;
+    for (int cycle = 0;; ++cycle) {
+        for (int j = 0; j < m; ++j) {
+            T* vj = V + (size_t)j * ld;
+            T* zj = Z + (size_t)j * ld;
+            if (pc) {
+                CK(launch_precond<T>(G, h->opts.pc_sweeps, vj, zj, (T*)h->za, (T*)h->zb, (T*)h->da,
+                                     (T*)h->db, (const T*)h->nu, h->part, h->ctl, 1, s, &h->launches));
+            }
+            jfnk_status st = apply_jv<T>(h, uT, zj, w, 1);
+            if (st != JFNK_OK) return st;
+            CK(launch_arnoldi_a<T>(V, ld, w, n, j + 1, h->part, h->ctl, s));
+            CK(launch_arnoldi_b<T>(V, ld, w, n, j + 1, m, h->part, h->ctl, s));
+            CK(launch_arnoldi_c<T>(V, ld, w, n, j + 1, h->ctl, s));
+            h->launches += 3;
+            CK(cudaMemcpyAsync(&h->hdone[j], &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaEventRecord(h->ev[j], s));
+            if (j >= LAG) {
+                CK(cudaEventSynchronize(h->ev[j - LAG]));
+                if (h->hdone[j - LAG]) break;
+            }
+        }
+        CK(launch_update<T>(Z, ld, h->x, h->mixed ? xT : nullptr, n, h->part, h->ctl, s));
+        h->launches += 1;
+        jfnk_status st = read_ctl(h);
+        if (st != JFNK_OK) return st;
+        const Ctl& c = *h->hctl;
+        *iters = c.iters;
+        if (c.nan) return JFNK_ERR_NAN;
+        if (c.converged) {
+            *conv = 1;
+            return JFNK_OK;
+        }
+        if (cycle >= h->opts.max_restarts) return JFNK_OK;
+        *restarts = cycle + 1;
+        st = apply_jv<T>(h, uT, xT, w, 0);
+        if (st != JFNK_OK) return st;
+        CK(launch_restart<T>(G, h->R, w, V, n, pc ? 0 : 1, h->part, h->ctl, s, &h->launches));
+    }
+}
+
+template <typename T>
+static jfnk_status residual_eval(jfnk_handle* h, const double* u) {
+    CK(launch_stencil<double>(MODE_RES, h->G, u, nullptr, nullptr, h->f, h->R, h->mixed ? nullptr : h->Fu64,
+                              h->part, h->ctl, 0, h->stream));
+    h->launches += 1;
+    return read_ctl(h);
+}
+
+template <typename T>
+static jfnk_status step_impl(jfnk_handle* h, double* u, jfnk_stats* out) {
+    cudaStream_t s = h->stream;
+    const Geo& G = h->G;
+    const size_t n = h->n;
+    jfnk_stats stats;
+    memset(&stats, 0, sizeof(stats));
+    CK(cudaMemcpyAsync(h->un, u, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    T* uT = h->mixed ? (T*)h->uT : (T*)u;
+    if (h->mixed) {
+        CK((launch_convert<double, T>(u, uT, n, s)));
+        h->launches += 1;
+    }
+    CK(launch_stencil<double>(MODE_RHS, G, h->un, nullptr, nullptr, nullptr, h->f, nullptr, h->part,
+                              h->ctl, 0, s));
+    h->launches += 1;
+    jfnk_status st = residual_eval<T>(h, u);
+    if (st != JFNK_OK) return st;
+    if (h->hctl->nan) return JFNK_ERR_NAN;
+    const double r0 = sqrt(h->hctl->res2);
+    const double tol = fmax(h->opts.newton_rtol * r0,
+                            h->opts.newton_atol_factor * G.two_over_dt * sqrt(h->hctl->unorm2));
+    stats.res0 = r0;
+    stats.tol = tol;
+    stats.res_hist[0] = r0;
+    double res = r0;
+    int k = 0;
+    while (res > tol && k < h->opts.max_newton) {
+        if (h->opts.precond == JFNK_PC_BLOCK && G.smag) {
+            CK(launch_eddy<T>(G, uT, (T*)h->nu, h->part, h->ctl, s));
+            h->launches += 1;
+        }
+        CK(launch_cycle_init<T>(G, h->R, (T*)h->V, h->x, n, h->opts.eta, h->m,
+                                h->opts.precond == JFNK_PC_NONE, h->ctl, s));
+        h->launches += 1;
+        int it = 0, rs = 0, cv = 0;
+        st = gmres_solve<T>(h, uT, &it, &rs, &cv);
+        if (st != JFNK_OK) return st;
+        stats.gmres_per_newton[k] = it;
+        stats.gmres_iters += it;
+        stats.restarts += rs;
+        CK(launch_newton_update<T>(G, u, h->x, h->mixed ? uT : nullptr, n, s));
+        h->launches += 1;
+        st = residual_eval<T>(h, u);
+        if (st != JFNK_OK) return st;
+        if (h->hctl->nan) return JFNK_ERR_NAN;
+        res = sqrt(h->hctl->res2);
+        ++k;
+        stats.res_hist[k] = res;
+    }
+    stats.newton_iters = k;
+    stats.res_final = res;
+    stats.converged = res <= tol;
+    if (out) *out = stats;
+    return stats.converged ? JFNK_OK : JFNK_ERR_NOT_CONVERGED;
+}
+
+extern "C" jfnk_status jfnk_step(jfnk_handle* h, double* u, jfnk_stats* out) {
+    if (!h || !u) return JFNK_ERR_INVALID_ARG;
+    return h->mixed ? step_impl<float>(h, u, out) : step_impl<double>(h, u, out);
+}
+
+extern "C" jfnk_status jfnk_step_host(jfnk_handle* h, double* u_host, jfnk_stats* out) {
+    if (!h || !u_host) return JFNK_ERR_INVALID_ARG;
+    const size_t bytes = h->n * sizeof(double);
+    CK(cudaMemcpyAsync(h->udev, u_host, bytes, cudaMemcpyHostToDevice, h->stream));
+    jfnk_status st = jfnk_step(h, h->udev, out);
+    if (st != JFNK_OK && st != JFNK_ERR_NOT_CONVERGED) return st;
+    CK(cudaMemcpyAsync(u_host, h->udev, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return st;
+}
+
+extern "C" jfnk_status jfnk_budgets(jfnk_handle* h, const double* u, jfnk_budget* out) {
+    if (!h || !u || !out) return JFNK_ERR_INVALID_ARG;
+    const double dx = h->grid.lx / h->grid.nx, dz = h->grid.lz / h->grid.nz;
+    CK(launch_budgets(h->G, u, dx, dz, h->grid.lz, h->part, h->ctl, h->budg, h->stream));
+    h->launches += 1;
+    double b[12];
+    CK(cudaMemcpyAsync(b, h->budg, sizeof(b), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    memset(out, 0, sizeof(*out));
+    out->E_k = b[0];
+    out->E_p = b[1];
+    out->sum_theta = b[2];
+    out->sum_div = b[3];
+    for (int f = 0; f < 4; ++f) {
+        out->max[f] = b[4 + f];
+        out->min[f] = b[8 + f];
+    }
+    return JFNK_OK;
+}
+
+extern "C" const char* jfnk_status_str(jfnk_status s) {
+    switch (s) {
+        case JFNK_OK: return "ok";
+        case JFNK_ERR_INVALID_ARG: return "invalid argument";
+        case JFNK_ERR_CUDA: return "CUDA runtime error";
+        case JFNK_ERR_OOM: return "device memory allocation failed";
+        case JFNK_ERR_NOT_CONVERGED: return "Newton iteration did not converge";
+        case JFNK_ERR_BREAKDOWN: return "GMRES breakdown";
+        case JFNK_ERR_NAN: return "non-finite residual";
+        case JFNK_ERR_TIMEOUT: return "device loop iteration cap reached";
+        case JFNK_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}

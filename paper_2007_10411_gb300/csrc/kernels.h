@@ -1,0 +1,74 @@
+// Host-side launchers of the libjfnk kernels (internal to the library).
+#pragma once
+
+#include "common.cuh"
+
+namespace jfnk {
+
+enum StencilMode { MODE_F = 0, MODE_RHS = 1, MODE_RES = 2, MODE_JV = 3 };
+
+// Number of blocks of the 2-D stencil grid for element type T.
+template <typename T> int stencil_blocks(const Geo& G);
+
+// F / 2u/dt + F / residual / plain forward-difference Jv (see stencil.cu).
+template <typename T>
+cudaError_t launch_stencil(int mode, const Geo& G, const T* u, const T* v, const T* Fu,
+                           const double* f, T* out, T* out2, double* part, Ctl* ctl,
+                           int check_done, cudaStream_t s);
+
+// Mixed-path Jv: difference F(u + eps V) - F(u) formed without cancellation.
+template <typename T>
+cudaError_t launch_jv_diff(const Geo& G, const T* u, const T* v, T* out, double* part, Ctl* ctl,
+                           int check_done, cudaStream_t s);
+
+// Smagorinsky nu at every point of u, and its maximum into ctl->kmax.
+template <typename T>
+cudaError_t launch_eddy(const Geo& G, const T* u, T* nu, double* part, Ctl* ctl, cudaStream_t s);
+
+// Field-block Chebyshev preconditioner z = M^{-1} r (sweeps >= 1); sets ctl->eps_jv from ||z||.
+template <typename T>
+cudaError_t launch_precond(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da, T* db,
+                           const T* nu, double* part, Ctl* ctl, int check_done, cudaStream_t s,
+                           long long* launches);
+
+// Budgets (E_k, E_p, sum theta, sum div, max/min per field) into out[0..4+2nf).
+cudaError_t launch_budgets(const Geo& G, const double* u, double dx, double dz, double lz,
+                           double* part, Ctl* ctl, double* out, cudaStream_t s);
+
+// ------------------------------------------------------------ Krylov kernels
+template <typename T>
+cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int nv, double* part,
+                             Ctl* ctl, cudaStream_t s);
+template <typename T>
+cudaError_t launch_arnoldi_b(const T* V, size_t ldv, const T* w, size_t n, int nv, int m,
+                             double* part, Ctl* ctl, cudaStream_t s);
+template <typename T>
+cudaError_t launch_arnoldi_c(T* V, size_t ldv, const T* w, size_t n, int nv, Ctl* ctl,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_update(const T* Z, size_t ldz, double* x, T* xT, size_t n, double* part,
+                          Ctl* ctl, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cycle_init(const Geo& G, const double* R, T* V0, double* x, size_t n, double eta,
+                              int m, int pc_none, Ctl* ctl, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restart(const Geo& G, const double* R, const T* w, T* V0, size_t n, int pc_none,
+                           double* part, Ctl* ctl, cudaStream_t s, long long* launches);
+template <typename T>
+cudaError_t launch_newton_update(const Geo& G, double* u, const double* x, T* uT, size_t n,
+                                 cudaStream_t s);
+
+// ------------------------------------------------------- vector utilities
+template <typename TI, typename TO>
+cudaError_t launch_convert(const TI* in, TO* out, size_t n, cudaStream_t s);
+// out = in * (scale ? scale_f : 1/scale_f) per field
+template <typename TI, typename TO>
+cudaError_t launch_rescale(const Geo& G, const TI* in, TO* out, size_t n, int multiply, cudaStream_t s);
+// ctl->scratch[slot] = ||W a||^2 (weighted = 1) or ||a||^2
+template <typename T>
+cudaError_t launch_norm2(const Geo& G, const T* a, size_t n, int weighted, int slot, double* part,
+                         Ctl* ctl, cudaStream_t s);
+// ctl->eps_jv = eps > 0 ? eps : sqrt(eps_mach (1 + sqrt(scratch[su]))) / sqrt(scratch[sv])
+cudaError_t launch_set_eps(double eps, int su, int sv, Ctl* ctl, cudaStream_t s);
+
+}  // namespace jfnk

@@ -1,0 +1,494 @@
+// Krylov kernels of libjfnk: restarted GMRES(m) with right preconditioning in
+// the flexible (stored z_j) form, classical Gram-Schmidt applied twice.
+//
+// One Arnoldi step j (w = J z_j already formed) is three streaming passes over
+// the basis V = [v_0 .. v_j]:
+//   A:  h1 = V^T w                                  (multi-dot)
+//   B:  w' = w - V h1,  h2 = V^T w',  ||w'||^2        (multi-axpy fused with multi-dot)
+//       last block: h = h1 + h2, h_{j+1,j} = sqrt(||w'||^2 - ||h2||^2), Givens
+//       rotation of the Hessenberg column, residual estimate |g_{j+1}|,
+//       stopping test and (when the cycle ends) the triangular solve for y
+//   C:  v_{j+1} = (w - V h) / h_{j+1,j}               (multi-axpy + scale)
+// Reductions are two-stage and deterministic: every block writes its partial
+// sums, the last block to finish adds them in a fixed order.  Per-thread
+// partials of float32 vectors are accumulated in float32 over at most FLUSH
+// elements and then folded into float64.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace jfnk {
+
+constexpr int FLUSH = 16;
+
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; static constexpr int W = 4; };
+template <> struct V4<double> { using type = double2; static constexpr int W = 2; };
+
+__device__ __forceinline__ float dotv(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+__device__ __forceinline__ double dotv(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
+__device__ __forceinline__ float4 axpyv(float4 y, float a, float4 x) {
+    return make_float4(y.x - a * x.x, y.y - a * x.y, y.z - a * x.z, y.w - a * x.w);
+}
+__device__ __forceinline__ double2 axpyv(double2 y, double a, double2 x) {
+    return make_double2(y.x - a * x.x, y.y - a * x.y);
+}
+__device__ __forceinline__ float4 scalev(float4 x, float a) { return make_float4(a * x.x, a * x.y, a * x.z, a * x.w); }
+__device__ __forceinline__ double2 scalev(double2 x, double a) { return make_double2(a * x.x, a * x.y); }
+
+static int stream_blocks(size_t n) {
+    size_t b = (n + NTHREADS - 1) / NTHREADS;
+    return (int)(b < (size_t)MAX_STREAM_BLOCKS ? (b > 0 ? b : 1) : MAX_STREAM_BLOCKS);
+}
+
+// ---------------------------------------------------------------- pass A
+template <typename T, int NV>
+__global__ void __launch_bounds__(NTHREADS)
+arnoldi_a(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv,
+          double* part, Ctl* ctl) {
+    if (ctl->done) return;
+    using VT = typename V4<T>::type;
+    constexpr int W = V4<T>::W;
+    T acc_t[NV];
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) { acc_t[k] = T(0); acc[k] = 0.0; }
+    const size_t nvec = n / W;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    int cnt = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvec; i += stride) {
+        const VT wv = reinterpret_cast<const VT*>(w)[i];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < nv) acc_t[k] += dotv(reinterpret_cast<const VT*>(V + k * ldv)[i], wv);
+        if (++cnt == FLUSH) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) { acc[k] += (double)acc_t[k]; acc_t[k] = T(0); }
+            cnt = 0;
+        }
+    }
+    for (size_t i = nvec * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < nv) acc_t[k] += V[k * ldv + i] * w[i];
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] += (double)acc_t[k];
+    block_partials<NV>(acc, nv, part, gridDim.x, blockIdx.x);
+    if (arrive_last(&ctl->counter[CNT_PASSA], gridDim.x)) {
+        __shared__ double tot[NV];
+        final_sums(part, gridDim.x, nv, tot);
+        for (int k = threadIdx.x; k < nv; k += blockDim.x) ctl->h1[k] = tot[k];
+    }
+}
+
+// ---------------------------------------------------------------- pass B
+// Serial Hessenberg / Givens update for column j (one thread).
+__device__ void givens_update(Ctl* c, int j, int m, const double* h2, double wn2) {
+    double col[KMAX + 1];
+    double hh2 = 0.0;
+    for (int k = 0; k <= j; ++k) {
+        const double hk = c->h1[k] + h2[k];
+        c->hsum[k] = hk;
+        c->Hbar[k][j] = hk;
+        col[k] = hk;
+        hh2 += h2[k] * h2[k];
+    }
+    const double hn2 = wn2 - hh2;
+    const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
+    c->Hbar[j + 1][j] = hn;
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double t = c->cs[i] * col[i] + c->sn[i] * col[i + 1];
+        col[i + 1] = -c->sn[i] * col[i] + c->cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    double cs = 1.0, sn = 0.0;
+    if (col[j + 1] != 0.0) {
+        const double rho = hypot(col[j], col[j + 1]);
+        cs = col[j] / rho;
+        sn = col[j + 1] / rho;
+    }
+    c->cs[j] = cs;
+    c->sn[j] = sn;
+    for (int k = 0; k < j; ++k) c->Rt[k][j] = col[k];
+    c->Rt[j][j] = cs * col[j] + sn * col[j + 1];
+    const double gj = c->g[j];
+    c->g[j + 1] = -sn * gj;
+    c->g[j] = cs * gj;
+    c->iters += 1;
+    const bool finite = isfinite(hn2) && isfinite(c->g[j + 1]) && isfinite(c->Rt[j][j]);
+    const bool conv = fabs(c->g[j + 1]) <= c->target;
+    const bool brk = hn == 0.0;
+    c->inv_hn = hn > 0.0 ? 1.0 / hn : 0.0;
+    if (!finite) {
+        c->nan = 1;
+        c->done = 1;
+        c->k = 0;
+        return;
+    }
+    if (conv || brk || j == m - 1) {
+        const int k = j + 1;
+        for (int i = k - 1; i >= 0; --i) {     // back substitution R y = g
+            double s = c->g[i];
+            for (int l = i + 1; l < k; ++l) s -= c->Rt[i][l] * c->y[l];
+            c->y[i] = s / c->Rt[i][i];
+        }
+        c->k = k;
+        c->converged = conv || brk;
+        c->breakdown = brk && !conv;
+        c->done = 1;
+    }
+}
+
+template <typename T, int NV>
+__global__ void __launch_bounds__(NTHREADS)
+arnoldi_b(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv, int m,
+          double* part, Ctl* ctl) {
+    if (ctl->done) return;
+    using VT = typename V4<T>::type;
+    constexpr int W = V4<T>::W;
+    __shared__ T h1s[NV];
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) h1s[k] = T(ctl->h1[k]);
+    __syncthreads();
+    // slot 0: ||w'||^2, slot 1 + k: v_k . w'
+    T acc_t[NV + 1];
+    double acc[NV + 1];
+#pragma unroll
+    for (int k = 0; k <= NV; ++k) { acc_t[k] = T(0); acc[k] = 0.0; }
+    const size_t nvec = n / W;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    int cnt = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvec; i += stride) {
+        VT wp = reinterpret_cast<const VT*>(w)[i];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < nv) wp = axpyv(wp, h1s[k], reinterpret_cast<const VT*>(V + k * ldv)[i]);
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < nv) acc_t[1 + k] += dotv(reinterpret_cast<const VT*>(V + k * ldv)[i], wp);
+        acc_t[0] += dotv(wp, wp);
+        if (++cnt == FLUSH) {
+#pragma unroll
+            for (int k = 0; k <= NV; ++k) { acc[k] += (double)acc_t[k]; acc_t[k] = T(0); }
+            cnt = 0;
+        }
+    }
+    for (size_t i = nvec * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        T wp = w[i];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < nv) wp -= h1s[k] * V[k * ldv + i];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < nv) acc_t[1 + k] += V[k * ldv + i] * wp;
+        acc_t[0] += wp * wp;
+    }
+#pragma unroll
+    for (int k = 0; k <= NV; ++k) acc[k] += (double)acc_t[k];
+    block_partials<NV + 1>(acc, nv + 1, part, gridDim.x, blockIdx.x);
+    if (arrive_last(&ctl->counter[CNT_PASSB], gridDim.x)) {
+        __shared__ double tot[NV + 1];
+        final_sums(part, gridDim.x, nv + 1, tot);
+        if (threadIdx.x == 0) givens_update(ctl, nv - 1, m, tot + 1, tot[0]);
+    }
+}
+
+// ---------------------------------------------------------------- pass C
+template <typename T, int NV>
+__global__ void __launch_bounds__(NTHREADS)
+arnoldi_c(T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv, Ctl* ctl) {
+    if (ctl->done) return;
+    using VT = typename V4<T>::type;
+    constexpr int W = V4<T>::W;
+    __shared__ T hs[NV];
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = T(ctl->hsum[k]);
+    __syncthreads();
+    const T inv = T(ctl->inv_hn);
+    const size_t nvec = n / W;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    T* vout = V + (size_t)nv * ldv;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvec; i += stride) {
+        VT wp = reinterpret_cast<const VT*>(w)[i];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < nv) wp = axpyv(wp, hs[k], reinterpret_cast<const VT*>(V + k * ldv)[i]);
+        reinterpret_cast<VT*>(vout)[i] = scalev(wp, inv);
+    }
+    for (size_t i = nvec * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        T wp = w[i];
+        for (int k = 0; k < nv; ++k) wp -= hs[k] * V[k * ldv + i];
+        vout[i] = wp * inv;
+    }
+}
+
+// ---------------------------------------------------------------- update
+// x += sum_{k < K} y_k z_k (float64); xT = x rounded to T; eps_jv for J x.
+template <typename T, int NV>
+__global__ void __launch_bounds__(NTHREADS)
+update_x(const T* __restrict__ Z, size_t ldz, double* __restrict__ x, T* __restrict__ xT, size_t n,
+         double* part, Ctl* ctl) {
+    const int K = ctl->k;
+    __shared__ double ys[NV];
+    for (int k = threadIdx.x; k < NV; k += blockDim.x) ys[k] = k < K ? ctl->y[k] : 0.0;
+    __syncthreads();
+    double acc[1] = {0.0};
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        double s = x[i];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < K) s += ys[k] * (double)Z[k * ldz + i];
+        x[i] = s;
+        if (xT != nullptr) xT[i] = T(s);
+        acc[0] += s * s;
+    }
+    block_partials<1>(acc, 1, part, gridDim.x, blockIdx.x);
+    if (arrive_last(&ctl->counter[CNT_UPDATE], gridDim.x)) {
+        __shared__ double tot[1];
+        final_sums(part, gridDim.x, 1, tot);
+        if (threadIdx.x == 0) {
+            ctl->scratch[0] = tot[0];
+            const double xn = sqrt(tot[0]);
+            ctl->eps_jv = xn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / xn : 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- cycle start
+// First cycle of a Newton solve: b = -W R, v_0 = b / ||b||, x = 0, control reset.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+cycle_init(Geo G, const double* __restrict__ R, T* __restrict__ V0, double* __restrict__ x, size_t n,
+           double eta, int m, int pc_none, Ctl* ctl) {
+    const double beta = sqrt(ctl->res2);
+    const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int f = (int)(i / G.npt);
+        V0[i] = T(-R[i] * G.inv_scale[f] * inv);
+        x[i] = 0.0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->beta0 = beta;
+        ctl->target = eta * beta;
+        ctl->g[0] = beta;
+        ctl->done = 0;
+        ctl->converged = beta == 0.0;
+        ctl->breakdown = 0;
+        ctl->k = 0;
+        ctl->iters = 0;
+        ctl->m = m;
+        if (pc_none) ctl->eps_jv = sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2)));
+    }
+}
+
+// Restart: r = b - w with w = J x, stored unnormalised in v_0 plus ||r||^2.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+restart_residual(Geo G, const double* __restrict__ R, const T* __restrict__ w, T* __restrict__ V0,
+                 size_t n, double* part, Ctl* ctl) {
+    double acc[1] = {0.0};
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int f = (int)(i / G.npt);
+        const double r = -R[i] * G.inv_scale[f] - (double)w[i];
+        V0[i] = T(r);
+        acc[0] += r * r;
+    }
+    block_partials<1>(acc, 1, part, gridDim.x, blockIdx.x);
+    if (arrive_last(&ctl->counter[CNT_RESTART], gridDim.x)) {
+        __shared__ double tot[1];
+        final_sums(part, gridDim.x, 1, tot);
+        if (threadIdx.x == 0) ctl->scratch[1] = tot[0];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+restart_scale(T* __restrict__ V0, size_t n, int pc_none, Ctl* ctl) {
+    const double beta = sqrt(ctl->scratch[1]);
+    const T inv = T(beta > 0.0 ? 1.0 / beta : 0.0);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) V0[i] *= inv;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->g[0] = beta;
+        ctl->done = 0;
+        ctl->converged = 0;
+        ctl->breakdown = 0;
+        ctl->k = 0;
+        if (pc_none) ctl->eps_jv = sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2)));
+    }
+}
+
+// u += W^{-1} x (float64), uT = u rounded to T.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+newton_update(Geo G, double* __restrict__ u, const double* __restrict__ x, T* __restrict__ uT, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int f = (int)(i / G.npt);
+        const double v = u[i] + G.scale[f] * x[i];
+        u[i] = v;
+        if (uT != nullptr) uT[i] = T(v);
+    }
+}
+
+// ---------------------------------------------------------------- utilities
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(NTHREADS) convert_k(const TI* __restrict__ in, TO* __restrict__ out, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) out[i] = TO(in[i]);
+}
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(NTHREADS)
+rescale_k(Geo G, const TI* __restrict__ in, TO* __restrict__ out, size_t n, int multiply) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int f = (int)(i / G.npt);
+        out[i] = TO((double)in[i] * (multiply ? G.scale[f] : G.inv_scale[f]));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+norm2_k(Geo G, const T* __restrict__ a, size_t n, int weighted, int slot, double* part, Ctl* ctl) {
+    double acc[1] = {0.0};
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        double v = (double)a[i];
+        if (weighted) v *= G.inv_scale[i / G.npt];
+        acc[0] += v * v;
+    }
+    block_partials<1>(acc, 1, part, gridDim.x, blockIdx.x);
+    if (arrive_last(&ctl->counter[CNT_MISC], gridDim.x)) {
+        __shared__ double tot[1];
+        final_sums(part, gridDim.x, 1, tot);
+        if (threadIdx.x == 0) ctl->scratch[slot] = tot[0];
+    }
+}
+
+__global__ void set_eps_k(double eps, int su, int sv, Ctl* ctl) {
+    if (eps > 0.0) {
+        ctl->eps_jv = eps;
+    } else {
+        const double vn = sqrt(ctl->scratch[sv]);
+        ctl->eps_jv = vn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->scratch[su]))) / vn : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <typename T>
+cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int nv, double* part,
+                             Ctl* ctl, cudaStream_t s) {
+    const int nb = stream_blocks(n / V4<T>::W);
+    if (nv <= 8) arnoldi_a<T, 8><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, part, ctl);
+    else if (nv <= 16) arnoldi_a<T, 16><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, part, ctl);
+    else arnoldi_a<T, 32><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, part, ctl);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_arnoldi_b(const T* V, size_t ldv, const T* w, size_t n, int nv, int m,
+                             double* part, Ctl* ctl, cudaStream_t s) {
+    const int nb = stream_blocks(n / V4<T>::W);
+    if (nv <= 8) arnoldi_b<T, 8><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);
+    else if (nv <= 16) arnoldi_b<T, 16><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);
+    else arnoldi_b<T, 32><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_arnoldi_c(T* V, size_t ldv, const T* w, size_t n, int nv, Ctl* ctl,
+                             cudaStream_t s) {
+    const int nb = stream_blocks(n / V4<T>::W);
+    if (nv <= 8) arnoldi_c<T, 8><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, ctl);
+    else if (nv <= 16) arnoldi_c<T, 16><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, ctl);
+    else arnoldi_c<T, 32><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, ctl);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_update(const T* Z, size_t ldz, double* x, T* xT, size_t n, double* part,
+                          Ctl* ctl, cudaStream_t s) {
+    update_x<T, KMAX><<<stream_blocks(n), NTHREADS, 0, s>>>(Z, ldz, x, xT, n, part, ctl);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cycle_init(const Geo& G, const double* R, T* V0, double* x, size_t n, double eta,
+                              int m, int pc_none, Ctl* ctl, cudaStream_t s) {
+    cycle_init<T><<<stream_blocks(n), NTHREADS, 0, s>>>(G, R, V0, x, n, eta, m, pc_none, ctl);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restart(const Geo& G, const double* R, const T* w, T* V0, size_t n, int pc_none,
+                           double* part, Ctl* ctl, cudaStream_t s, long long* launches) {
+    restart_residual<T><<<stream_blocks(n), NTHREADS, 0, s>>>(G, R, w, V0, n, part, ctl);
+    restart_scale<T><<<stream_blocks(n), NTHREADS, 0, s>>>(V0, n, pc_none, ctl);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_newton_update(const Geo& G, double* u, const double* x, T* uT, size_t n,
+                                 cudaStream_t s) {
+    newton_update<T><<<stream_blocks(n), NTHREADS, 0, s>>>(G, u, x, uT, n);
+    return cudaGetLastError();
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_convert(const TI* in, TO* out, size_t n, cudaStream_t s) {
+    convert_k<TI, TO><<<stream_blocks(n), NTHREADS, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_rescale(const Geo& G, const TI* in, TO* out, size_t n, int multiply, cudaStream_t s) {
+    rescale_k<TI, TO><<<stream_blocks(n), NTHREADS, 0, s>>>(G, in, out, n, multiply);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_norm2(const Geo& G, const T* a, size_t n, int weighted, int slot, double* part,
+                         Ctl* ctl, cudaStream_t s) {
+    norm2_k<T><<<stream_blocks(n), NTHREADS, 0, s>>>(G, a, n, weighted, slot, part, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_eps(double eps, int su, int sv, Ctl* ctl, cudaStream_t s) {
+    set_eps_k<<<1, 1, 0, s>>>(eps, su, sv, ctl);
+    return cudaGetLastError();
+}
+
+#define JF_INST(T)                                                                                     \
+    template cudaError_t launch_arnoldi_a<T>(const T*, size_t, const T*, size_t, int, double*, Ctl*,  \
+                                             cudaStream_t);                                            \
+    template cudaError_t launch_arnoldi_b<T>(const T*, size_t, const T*, size_t, int, int, double*,   \
+                                             Ctl*, cudaStream_t);                                      \
+    template cudaError_t launch_arnoldi_c<T>(T*, size_t, const T*, size_t, int, Ctl*, cudaStream_t);  \
+    template cudaError_t launch_update<T>(const T*, size_t, double*, T*, size_t, double*, Ctl*,       \
+                                          cudaStream_t);                                               \
+    template cudaError_t launch_cycle_init<T>(const Geo&, const double*, T*, double*, size_t, double, \
+                                              int, int, Ctl*, cudaStream_t);                           \
+    template cudaError_t launch_restart<T>(const Geo&, const double*, const T*, T*, size_t, int,      \
+                                           double*, Ctl*, cudaStream_t, long long*);                  \
+    template cudaError_t launch_newton_update<T>(const Geo&, double*, const double*, T*, size_t,      \
+                                                 cudaStream_t);                                        \
+    template cudaError_t launch_norm2<T>(const Geo&, const T*, size_t, int, int, double*, Ctl*,       \
+                                         cudaStream_t);
+JF_INST(float)
+JF_INST(double)
+
+template cudaError_t launch_convert<double, float>(const double*, float*, size_t, cudaStream_t);
+template cudaError_t launch_convert<float, double>(const float*, double*, size_t, cudaStream_t);
+template cudaError_t launch_convert<double, double>(const double*, double*, size_t, cudaStream_t);
+template cudaError_t launch_rescale<double, float>(const Geo&, const double*, float*, size_t, int, cudaStream_t);
+template cudaError_t launch_rescale<double, double>(const Geo&, const double*, double*, size_t, int, cudaStream_t);
+template cudaError_t launch_rescale<float, double>(const Geo&, const float*, double*, size_t, int, cudaStream_t);
+
+}  // namespace jfnk

@@ -1,0 +1,833 @@
+// 2-D stencil kernels of libjfnk: F(u), R(u), the Jacobian-vector product,
+// the Smagorinsky eddy field, the field-block Chebyshev preconditioner and
+// the budgets.
+//
+// Discretisation (Hossain & Alam):
+//   * Deslauriers-Dubuc collocation derivative of order p = 2 (Section 2.3):
+//     the 4-point interpolating scheme gives phi'(+-1) = -+2/3, phi'(+-2) = +-1/12,
+//     i.e. D f_j = [2/3 (f_{j+1} - f_{j-1}) - 1/12 (f_{j+2} - f_{j-2})] / h.
+//   * skew-symmetric convection C(u)phi = 1/2 D_j(u_j phi) + 1/2 u_j D_j phi (Section 2.2)
+//     for every field;
+//   * Eqs. ch2_28-ch2_30 with Laplacian-form eddy diffusion sum_j D_j(K D_j phi),
+//     constant K_M, K_H (Table 1) or Smagorinsky nu = (Cs Delta)^2 sqrt(2 S:S),
+//     K_M = nu, K_H = nu / Pr (Section 2.4);
+//   * x periodic, z cell-centred with mirror ghosts (w odd, theta and p even,
+//     u even for free slip / odd for no slip); the eddy field is mirrored even.
+//
+// Tiling: one CTA computes a TX x TZ tile of output points.  Stage 1 stages
+// the four fields with a halo of 2r = 4 points in shared memory (periodic /
+// mirror index mapping, coalesced along x); stage 2 forms the first
+// derivatives of u, w, theta (and nu) on the tile plus a halo of r = 2;
+// stage 3 assembles the fluxes, the second application of D and the
+// point-wise terms, and writes coalesced rows.  Nothing but the inputs and
+// the outputs touches HBM: the eddy viscosity and the derivatives live only
+// in shared memory.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace jfnk {
+
+constexpr int R = 2;          // derivative radius for p = 2
+constexpr int HALO = 2 * R;   // input halo (derivative applied twice)
+
+template <typename T> struct Tile;
+template <> struct Tile<double> { static constexpr int TX = 32, TZ = 16; };
+template <> struct Tile<float>  { static constexpr int TX = 64, TZ = 16; };
+// The difference-form Jacobian product stages two states: smaller tiles.
+template <typename T> struct TileD;
+template <> struct TileD<double> { static constexpr int TX = 32, TZ = 8; };
+template <> struct TileD<float>  { static constexpr int TX = 32, TZ = 16; };
+
+template <typename T>
+__device__ __forceinline__ T dd(const T* s, int i, int st, T inv_h) {
+    return (T(2.0 / 3.0) * (s[i + st] - s[i - st]) - T(1.0 / 12.0) * (s[i + 2 * st] - s[i - 2 * st])) * inv_h;
+}
+
+// derivative of the point-wise product a*b
+template <typename T>
+__device__ __forceinline__ T ddp(const T* a, const T* b, int i, int st, T inv_h) {
+    return (T(2.0 / 3.0) * (a[i + st] * b[i + st] - a[i - st] * b[i - st]) -
+            T(1.0 / 12.0) * (a[i + 2 * st] * b[i + 2 * st] - a[i - 2 * st] * b[i - 2 * st])) * inv_h;
+}
+
+// derivative of the flux K*g where K may be a constant (Kc) or an array
+template <typename T, bool KARR>
+__device__ __forceinline__ T ddk(const T* K, T Kc, const T* g, int i, int st, T inv_h) {
+    if (KARR) return ddp(K, g, i, st, inv_h);
+    return Kc * dd(g, i, st, inv_h);
+}
+
+// Source row / sign of a ghost-extended z index.  side: 0 interior, 1 bottom, 2 top.
+__device__ __forceinline__ int mirror_z(int gz, int nz, int& side) {
+    side = 0;
+    if (gz < 0) { side = 1; return -1 - gz; }
+    if (gz >= nz) { side = 2; return 2 * nz - 1 - gz; }
+    return gz;
+}
+
+__device__ __forceinline__ int wrap_x(int gx, int nx) {
+    int r = gx % nx;
+    return r < 0 ? r + nx : r;
+}
+
+// Stage 1: s[f][SZ][SX] <- (LOADMODE 0) u, (1) u + ev*v, (2) ev*v, ghost-extended.
+template <typename T, int LOADMODE>
+__device__ __forceinline__ void load_fields(T* s, const T* __restrict__ u, const T* __restrict__ v,
+                                            const T (&ev)[4], const Geo& G, int x0, int z0,
+                                            int SX, int SZ) {
+    const int total = SX * SZ;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int iz = idx / SX, ix = idx - iz * SX;
+        const int gz = z0 + iz - HALO, gx = x0 + ix - HALO;
+        int side;
+        const int sz = mirror_z(gz, G.nz, side);
+        const int sx = wrap_x(gx, G.nx);
+        const bool ok = sz >= 0 && sz < G.nz;
+        const size_t off = (size_t)sz * G.nx + sx;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            T val = T(0);
+            if (ok) {
+                const size_t o = (size_t)f * G.npt + off;
+                if (LOADMODE == 0) val = u[o];
+                else if (LOADMODE == 1) val = u[o] + ev[f] * v[o];
+                else val = ev[f] * v[o];
+                if (side == 1) val *= T(G.pb[f]);
+                else if (side == 2) val *= T(G.pt[f]);
+            }
+            s[(f * SZ + iz) * SX + ix] = val;
+        }
+    }
+}
+
+// Stage 2: first derivatives of u, w, theta on the halo-r region.
+template <typename T>
+__device__ __forceinline__ void first_derivs(const T* s1, T* d, int SX, int SZ, int QX, int QZ,
+                                             T idx_, T idz_) {
+    const int total = QX * QZ;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int qz = idx / QX, qx = idx - qz * QX;
+        const int i1 = (qz + R) * SX + qx + R;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const T* sf = s1 + f * SZ * SX;
+            d[(2 * f) * total + idx] = dd(sf, i1, 1, idx_);
+            d[(2 * f + 1) * total + idx] = dd(sf, i1, SX, idz_);
+        }
+    }
+}
+
+// Row of the halo-r region whose eddy value a ghost row takes (even mirror); -1 if unused.
+__device__ __forceinline__ int eddy_row(int qz, int z0, int nz, int QZ) {
+    const int gz = z0 + qz - R;
+    int iq = qz;
+    if (gz < 0) iq = (-1 - gz) - z0 + R;
+    else if (gz >= nz) iq = (gz < nz + R) ? (2 * nz - 1 - gz) - z0 + R : -1;
+    return (iq >= 0 && iq < QZ) ? iq : -1;
+}
+
+template <typename T>
+__device__ __forceinline__ T smag_nu(T ux, T uz, T wx, T wz, T cs2) {
+    const T s13 = T(0.5) * (uz + wx);
+    const T ss = ux * ux + wz * wz + T(2) * s13 * s13;
+    return cs2 * sqrt(T(2) * ss);
+}
+
+// ============================================================================
+// F, 2u/dt + F, residual and plain forward-difference Jv
+// ============================================================================
+template <typename T, int MODE, int SMAG>
+__global__ void __launch_bounds__(NTHREADS)
+stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ Fu,
+          const double* __restrict__ f, T* __restrict__ out, T* __restrict__ out2,
+          double* __restrict__ part, Ctl* ctl, int check_done) {
+    constexpr int TX = Tile<T>::TX, TZ = Tile<T>::TZ;
+    constexpr int SX = TX + 2 * HALO, SZ = TZ + 2 * HALO;
+    constexpr int QX = TX + 2 * R, QZ = TZ + 2 * R;
+    constexpr int QN = QX * QZ;
+    if (MODE == MODE_JV && check_done && ctl->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* s1 = reinterpret_cast<T*>(smem_raw);
+    T* d = s1 + 4 * SZ * SX;
+    T* nu = d + 6 * QN;
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+    const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
+
+    T ev[4] = {T(0), T(0), T(0), T(0)};
+    double eps = 0.0;
+    if (MODE == MODE_JV) {
+        eps = ctl->eps_jv;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ev[q] = T(eps * G.scale[q]);
+        load_fields<T, 1>(s1, u, v, ev, G, x0, z0, SX, SZ);
+    } else {
+        load_fields<T, 0>(s1, u, v, ev, G, x0, z0, SX, SZ);
+    }
+    __syncthreads();
+    first_derivs(s1, d, SX, SZ, QX, QZ, idx_, idz_);
+    __syncthreads();
+    if (SMAG) {
+        const T cs2 = T(G.cs2);
+        for (int idx = threadIdx.x; idx < QN; idx += blockDim.x) {
+            const int qz = idx / QX, qx = idx - qz * QX;
+            const int iq = eddy_row(qz, z0, G.nz, QZ);
+            T val = T(0);
+            if (iq >= 0) {
+                const int q = iq * QX + qx;
+                val = smag_nu(d[q], d[QN + q], d[2 * QN + q], d[3 * QN + q], cs2);
+            }
+            nu[idx] = val;
+        }
+        __syncthreads();
+    }
+
+    const T* su = s1;
+    const T* sw = s1 + SZ * SX;
+    const T* st = s1 + 2 * SZ * SX;
+    const T* sp = s1 + 3 * SZ * SX;
+    const T* dux = d;
+    const T* duz = d + QN;
+    const T* dwx = d + 2 * QN;
+    const T* dwz = d + 3 * QN;
+    const T* dtx = d + 4 * QN;
+    const T* dtz = d + 5 * QN;
+    const T KMc = T(G.K_M), KHc = T(G.K_H), iPr = T(G.inv_Pr);
+    const T th0 = T(G.theta0);
+
+    double acc[2] = {0.0, 0.0};
+    for (int idx = threadIdx.x; idx < TX * TZ; idx += blockDim.x) {
+        const int tz = idx / TX, tx = idx - tz * TX;
+        const int gz = z0 + tz, gx = x0 + tx;
+        if (gz >= G.nz || gx >= G.nx) continue;
+        const int i1 = (tz + HALO) * SX + tx + HALO;
+        const int q = (tz + R) * QX + tx + R;
+        const T uc = su[i1], wc = sw[i1], tc = st[i1], pc = sp[i1];
+        const T px = dd(sp, i1, 1, idx_), pz = dd(sp, i1, SX, idz_);
+        // skew-symmetric convection of every field
+        const T cu = T(0.5) * (ddp(su, su, i1, 1, idx_) + ddp(sw, su, i1, SX, idz_)) +
+                     T(0.5) * (uc * dux[q] + wc * duz[q]);
+        const T cw = T(0.5) * (ddp(su, sw, i1, 1, idx_) + ddp(sw, sw, i1, SX, idz_)) +
+                     T(0.5) * (uc * dwx[q] + wc * dwz[q]);
+        const T ct = T(0.5) * (ddp(su, st, i1, 1, idx_) + ddp(sw, st, i1, SX, idz_)) +
+                     T(0.5) * (uc * dtx[q] + wc * dtz[q]);
+        const T cp = T(0.5) * (ddp(su, sp, i1, 1, idx_) + ddp(sw, sp, i1, SX, idz_)) +
+                     T(0.5) * (uc * px + wc * pz);
+        // eddy diffusion sum_j D_j(K D_j phi)
+        T du, dw, dt_;
+        if (SMAG) {
+            du = ddp(nu, dux, q, 1, idx_) + ddp(nu, duz, q, QX, idz_);
+            dw = ddp(nu, dwx, q, 1, idx_) + ddp(nu, dwz, q, QX, idz_);
+            dt_ = iPr * (ddp(nu, dtx, q, 1, idx_) + ddp(nu, dtz, q, QX, idz_));
+        } else {
+            du = KMc * (dd(dux, q, 1, idx_) + dd(duz, q, QX, idz_));
+            dw = KMc * (dd(dwx, q, 1, idx_) + dd(dwz, q, QX, idz_));
+            dt_ = KHc * (dd(dtx, q, 1, idx_) + dd(dtz, q, QX, idz_));
+        }
+        T Fv[4];
+        Fv[0] = -cu - th0 * px + du;
+        Fv[1] = -cw - th0 * pz + dw + T(G.g) * tc / th0;
+        Fv[2] = -ct - T(G.beta) * wc + dt_;
+        if (G.heat != nullptr && gz == 0) Fv[2] += T(G.heat[gx] * G.heat_coef);
+        Fv[3] = -cp - T(G.gamma_p) * (T(G.pbar) + pc) * (dux[q] + dwz[q]);
+
+        const size_t off = (size_t)gz * G.nx + gx;
+#pragma unroll
+        for (int fl = 0; fl < 4; ++fl) {
+            const size_t o = (size_t)fl * G.npt + off;
+            if (MODE == MODE_F) {
+                out[o] = Fv[fl];
+            } else if (MODE == MODE_RHS) {
+                out[o] = T(G.two_over_dt * (double)u[o] + (double)Fv[fl]);
+            } else if (MODE == MODE_RES) {
+                const double uo = (double)u[o];
+                const double Rv = G.two_over_dt * uo - (double)Fv[fl] - f[o];
+                out[o] = T(Rv);
+                if (out2 != nullptr) out2[o] = Fv[fl];
+                const double rs = Rv * G.inv_scale[fl], us = uo * G.inv_scale[fl];
+                acc[0] += rs * rs;
+                acc[1] += us * us;
+            } else {  // MODE_JV: w_hat = 2 v_hat/dt - (F(u + eps V) - F(u)) / (eps scale)
+                const double vh = (double)v[o];
+                const double diff = (double)Fv[fl] - (double)Fu[o];
+                out[o] = T(G.two_over_dt * vh - diff / (eps * G.scale[fl]));
+            }
+        }
+    }
+    if (MODE == MODE_RES) {
+        const int nblk = gridDim.x * gridDim.y;
+        const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+        block_partials<2>(acc, 2, part, nblk, blk);
+        if (arrive_last(&ctl->counter[CNT_STENCIL], nblk)) {
+            __shared__ double tot[2];
+            final_sums(part, nblk, 2, tot);
+            if (threadIdx.x == 0) {
+                ctl->res2 = tot[0];
+                ctl->unorm2 = tot[1];
+                ctl->nan = !(isfinite(tot[0]) && isfinite(tot[1]));
+            }
+        }
+    }
+}
+
+// ============================================================================
+// Mixed-path Jv: the forward difference F(u + eps V) - F(u) with every term
+// expanded as a difference (a = u, b = eps V, a' = a + b), e.g.
+//   a'_j phi' - a_j phi = a_j b_phi + b_j phi',
+//   (pbar + p') div a' - (pbar + p) div a = (pbar + p') div b + b_p div a,
+//   nu(a') - nu(a) = (Cs Delta)^2 2 (S':S' - S:S) / (sqrt(2 S':S') + sqrt(2 S:S)),
+// so the float32 result carries float32 relative accuracy on the difference
+// itself instead of on F.  Same quantity as the forward difference of Eq. fd.
+// ============================================================================
+template <typename T, int SMAG>
+__global__ void __launch_bounds__(NTHREADS)
+jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict__ out,
+          Ctl* ctl, int check_done) {
+    constexpr int TX = TileD<T>::TX, TZ = TileD<T>::TZ;
+    constexpr int SX = TX + 2 * HALO, SZ = TZ + 2 * HALO;
+    constexpr int QX = TX + 2 * R, QZ = TZ + 2 * R;
+    constexpr int QN = QX * QZ;
+    if (check_done && ctl->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sa = reinterpret_cast<T*>(smem_raw);
+    T* sb = sa + 4 * SZ * SX;
+    T* da = sb + 4 * SZ * SX;
+    T* db = da + 6 * QN;
+    T* Ka = db + 6 * QN;
+    T* dK = Ka + QN;
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+    const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
+    const double eps = ctl->eps_jv;
+    T ev[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ev[q] = T(eps * G.scale[q]);
+    load_fields<T, 0>(sa, u, v, ev, G, x0, z0, SX, SZ);
+    load_fields<T, 2>(sb, u, v, ev, G, x0, z0, SX, SZ);
+    __syncthreads();
+    first_derivs(sa, da, SX, SZ, QX, QZ, idx_, idz_);
+    first_derivs(sb, db, SX, SZ, QX, QZ, idx_, idz_);
+    __syncthreads();
+    if (SMAG) {
+        const T cs2 = T(G.cs2);
+        for (int idx = threadIdx.x; idx < QN; idx += blockDim.x) {
+            const int qz = idx / QX, qx = idx - qz * QX;
+            const int iq = eddy_row(qz, z0, G.nz, QZ);
+            T ka = T(0), dk = T(0);
+            if (iq >= 0) {
+                const int q = iq * QX + qx;
+                const T aux = da[q], auz = da[QN + q], awx = da[2 * QN + q], awz = da[3 * QN + q];
+                const T bux = db[q], buz = db[QN + q], bwx = db[2 * QN + q], bwz = db[3 * QN + q];
+                const T a13 = T(0.5) * (auz + awx), b13 = T(0.5) * (buz + bwx);
+                const T ssa = aux * aux + awz * awz + T(2) * a13 * a13;
+                // S':S' - S:S = (2 S + S_b) : S_b
+                const T dss = (T(2) * aux + bux) * bux + (T(2) * awz + bwz) * bwz +
+                              T(2) * (T(2) * a13 + b13) * b13;
+                const T na = sqrt(T(2) * ssa);
+                const T np = sqrt(T(2) * (ssa + dss) > T(0) ? T(2) * (ssa + dss) : T(0));
+                ka = cs2 * na;
+                const T den = na + np;
+                dk = den > T(0) ? cs2 * T(2) * dss / den : T(0);
+            }
+            Ka[idx] = ka;
+            dK[idx] = dk;
+        }
+        __syncthreads();
+    }
+    const T* au = sa; const T* aw = sa + SZ * SX; const T* at = sa + 2 * SZ * SX; const T* ap = sa + 3 * SZ * SX;
+    const T* bu = sb; const T* bw = sb + SZ * SX; const T* bt = sb + 2 * SZ * SX; const T* bp = sb + 3 * SZ * SX;
+    const T KMc = T(G.K_M), KHc = T(G.K_H), iPr = T(G.inv_Pr), th0 = T(G.theta0);
+
+    for (int idx = threadIdx.x; idx < TX * TZ; idx += blockDim.x) {
+        const int tz = idx / TX, tx = idx - tz * TX;
+        const int gz = z0 + tz, gx = x0 + tx;
+        if (gz >= G.nz || gx >= G.nx) continue;
+        const int i1 = (tz + HALO) * SX + tx + HALO;
+        const int q = (tz + R) * QX + tx + R;
+        const T auc = au[i1], awc = aw[i1], apc = ap[i1];
+        const T buc = bu[i1], bwc = bw[i1], btc = bt[i1], bpc = bp[i1];
+        const T apx = dd(ap, i1, 1, idx_), apz = dd(ap, i1, SX, idz_);
+        const T bpx = dd(bp, i1, 1, idx_), bpz = dd(bp, i1, SX, idz_);
+        T dF[4];
+        // convection differences: 1/2 D_j(a_j b_phi + b_j phi') + 1/2 (a_j D b_phi + b_j D phi')
+        const T* as[4] = {au, aw, at, ap};
+        const T* bs[4] = {bu, bw, bt, bp};
+#pragma unroll
+        for (int fl = 0; fl < 4; ++fl) {
+            const T* A = as[fl];
+            const T* B = bs[fl];
+            T fx = T(0), fz = T(0);
+#pragma unroll
+            for (int l = 1; l <= 2; ++l) {
+                const T c = l == 1 ? T(2.0 / 3.0) : T(-1.0 / 12.0);
+                const int ip = i1 + l, im = i1 - l;
+                const int kp = i1 + l * SX, km = i1 - l * SX;
+                fx += c * ((au[ip] * B[ip] + bu[ip] * (A[ip] + B[ip])) -
+                           (au[im] * B[im] + bu[im] * (A[im] + B[im])));
+                fz += c * ((aw[kp] * B[kp] + bw[kp] * (A[kp] + B[kp])) -
+                           (aw[km] * B[km] + bw[km] * (A[km] + B[km])));
+            }
+            T dax, daz, dbx, dbz;
+            if (fl < 3) {
+                dax = da[(2 * fl) * QN + q]; daz = da[(2 * fl + 1) * QN + q];
+                dbx = db[(2 * fl) * QN + q]; dbz = db[(2 * fl + 1) * QN + q];
+            } else {
+                dax = apx; daz = apz; dbx = bpx; dbz = bpz;
+            }
+            const T adv = auc * dbx + awc * dbz + buc * (dax + dbx) + bwc * (daz + dbz);
+            dF[fl] = -(T(0.5) * (fx * idx_ + fz * idz_) + T(0.5) * adv);
+        }
+        // diffusion differences: D_j(K_a D_j b_phi + dK D_j phi')
+#pragma unroll
+        for (int fl = 0; fl < 3; ++fl) {
+            const T* dax = da + (2 * fl) * QN; const T* daz = da + (2 * fl + 1) * QN;
+            const T* dbx = db + (2 * fl) * QN; const T* dbz = db + (2 * fl + 1) * QN;
+            T sx = T(0), sz = T(0);
+            const T kc = fl == 2 ? KHc : KMc;
+#pragma unroll
+            for (int l = 1; l <= 2; ++l) {
+                const T c = l == 1 ? T(2.0 / 3.0) : T(-1.0 / 12.0);
+                const int xp = q + l, xm = q - l, zp = q + l * QX, zm = q - l * QX;
+                if (SMAG) {
+                    sx += c * ((Ka[xp] * dbx[xp] + dK[xp] * (dax[xp] + dbx[xp])) -
+                               (Ka[xm] * dbx[xm] + dK[xm] * (dax[xm] + dbx[xm])));
+                    sz += c * ((Ka[zp] * dbz[zp] + dK[zp] * (daz[zp] + dbz[zp])) -
+                               (Ka[zm] * dbz[zm] + dK[zm] * (daz[zm] + dbz[zm])));
+                } else {
+                    sx += c * (dbx[xp] - dbx[xm]);
+                    sz += c * (dbz[zp] - dbz[zm]);
+                }
+            }
+            T dif = sx * idx_ + sz * idz_;
+            if (SMAG) { if (fl == 2) dif *= iPr; } else dif *= kc;
+            dF[fl] += dif;
+        }
+        dF[0] += -th0 * bpx;
+        dF[1] += -th0 * bpz + T(G.g) * btc / th0;
+        dF[2] += -T(G.beta) * bwc;
+        const T diva = da[q] + da[3 * QN + q];
+        const T divb = db[q] + db[3 * QN + q];
+        dF[3] += -T(G.gamma_p) * ((T(G.pbar) + apc + bpc) * divb + bpc * diva);
+
+        const size_t off = (size_t)gz * G.nx + gx;
+#pragma unroll
+        for (int fl = 0; fl < 4; ++fl) {
+            const size_t o = (size_t)fl * G.npt + off;
+            const double vh = (double)v[o];
+            out[o] = T(G.two_over_dt * vh - (double)dF[fl] / (eps * G.scale[fl]));
+        }
+    }
+}
+
+// ============================================================================
+// Smagorinsky eddy field nu(u) at every point (preconditioner input) + max
+// ============================================================================
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+eddy2d(Geo G, const T* __restrict__ u, T* __restrict__ nu, double* part, Ctl* ctl) {
+    double mx[1] = {0.0};
+    const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
+    const T cs2 = T(G.cs2);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < G.npt; p += gridDim.x * blockDim.x) {
+        const int z = p / G.nx, x = p - z * G.nx;
+        T ux = T(0), uz = T(0), wx = T(0), wz = T(0);
+#pragma unroll
+        for (int l = 1; l <= 2; ++l) {
+            const T c = l == 1 ? T(2.0 / 3.0) : T(-1.0 / 12.0);
+            const int xp = wrap_x(x + l, G.nx), xm = wrap_x(x - l, G.nx);
+            int sp_, sm_;
+            const int zp = mirror_z(z + l, G.nz, sp_), zm = mirror_z(z - l, G.nz, sm_);
+            const T sgu_p = sp_ == 2 ? T(G.pt[0]) : T(1), sgu_m = sm_ == 1 ? T(G.pb[0]) : T(1);
+            const T sgw_p = sp_ == 2 ? T(G.pt[1]) : T(1), sgw_m = sm_ == 1 ? T(G.pb[1]) : T(1);
+            const T* U = u;
+            const T* W = u + G.npt;
+            ux += c * (U[z * G.nx + xp] - U[z * G.nx + xm]);
+            wx += c * (W[z * G.nx + xp] - W[z * G.nx + xm]);
+            uz += c * (sgu_p * U[zp * G.nx + x] - sgu_m * U[zm * G.nx + x]);
+            wz += c * (sgw_p * W[zp * G.nx + x] - sgw_m * W[zm * G.nx + x]);
+        }
+        const T v_ = smag_nu(ux * idx_, uz * idz_, wx * idx_, wz * idz_, cs2);
+        nu[p] = v_;
+        mx[0] = fmax(mx[0], (double)v_);
+    }
+    block_partials_max<1>(mx, 1, part, gridDim.x, blockIdx.x);
+    if (arrive_last(&ctl->counter[CNT_EDDY], gridDim.x)) {
+        __shared__ double tot[1];
+        final_maxes(part, gridDim.x, 1, tot);
+        if (threadIdx.x == 0) ctl->kmax = tot[0];
+    }
+}
+
+// ============================================================================
+// Field-block Chebyshev preconditioner (Section 2.5.2): for u, w, theta the
+// block A_f = (2/dt) I - sum_j D_j(K D_j .) with K frozen at the current
+// iterate; the p block is (2/dt) I.  Spectrum bounds from Gershgorin:
+// [2/dt, 2/dt + (3/2)^2 K_max (1/dx^2 + 1/dz^2)] ((3/2) = sum_l |phi'(l)|).
+// Sweep k (k = 1 .. s-1) of the Chebyshev semi-iteration (Saad, Alg. 12.1):
+//   res = r - A x_k;  d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) res;
+//   x_{k+1} = x_k + d_k,   with x_1 = d_0 = r / theta_c.
+// ============================================================================
+struct ChebK {
+    double inv_theta, a1, a2;   // 1/theta_c, rho_k rho_{k-1}, 2 rho_k / delta
+};
+
+__device__ __forceinline__ ChebK cheb_coef(double lo, double hi, int k) {
+    ChebK c;
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+    c.inv_theta = 1.0 / theta;
+    if (delta <= 1e-14 * theta) { c.a1 = 0.0; c.a2 = 0.0; return c; }
+    const double sigma = theta / delta;
+    double rho = 1.0 / sigma, rho_new = rho;
+    for (int i = 1; i <= k; ++i) {
+        rho_new = 1.0 / (2.0 * sigma - rho);
+        if (i < k) rho = rho_new;
+    }
+    c.a1 = rho_new * rho;
+    c.a2 = 2.0 * rho_new / delta;
+    return c;
+}
+
+template <typename T, int SMAG, int FIRST, int LAST>
+__global__ void __launch_bounds__(NTHREADS)
+cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T* __restrict__ din,
+       T* __restrict__ zout, T* __restrict__ dout, const T* __restrict__ nu, double* part, Ctl* ctl,
+       int check_done) {
+    constexpr int TX = Tile<T>::TX, TZ = Tile<T>::TZ;
+    constexpr int SX = TX + 2 * HALO, SZ = TZ + 2 * HALO;
+    constexpr int QX = TX + 2 * R, QZ = TZ + 2 * R;
+    constexpr int QN = QX * QZ;
+    if (check_done && ctl->done) return;
+    __shared__ T sz_[SZ * SX];
+    __shared__ T gx_[QN];
+    __shared__ T gz_[QN];
+    __shared__ T kk_[SMAG ? QN : 1];
+    const int fld = blockIdx.z;                 // 0 u, 1 w, 2 theta, 3 p
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+    const double lo = G.two_over_dt;
+    const double kmax = SMAG ? ctl->kmax * (fld == 2 ? G.inv_Pr : 1.0) : (fld == 2 ? G.K_H : G.K_M);
+    const double hi = fld == 3 ? lo : lo + 2.25 * kmax * (G.inv_dx * G.inv_dx + G.inv_dz * G.inv_dz);
+    const ChebK cc = cheb_coef(lo, hi, k);
+    const size_t foff = (size_t)fld * G.npt;
+    double acc[1] = {0.0};
+    if (fld == 3) {
+        // p block: (2/dt) I, exact in one step; written by the last sweep only
+        if (LAST) {
+            for (int idx = threadIdx.x; idx < TX * TZ; idx += blockDim.x) {
+                const int tz = idx / TX, tx = idx - tz * TX;
+                const int gz = z0 + tz, gx = x0 + tx;
+                if (gz >= G.nz || gx >= G.nx) continue;
+                const size_t o = foff + (size_t)gz * G.nx + gx;
+                const T zv = T((double)r[o] * cc.inv_theta);
+                zout[o] = zv;
+                acc[0] += (double)zv * (double)zv;
+            }
+        }
+    } else {
+        const T ith = T(cc.inv_theta);
+        // x_k with halo 2r (x_1 = r / theta)
+        for (int idx = threadIdx.x; idx < SZ * SX; idx += blockDim.x) {
+            const int iz = idx / SX, ix = idx - iz * SX;
+            const int gz = z0 + iz - HALO, gx = x0 + ix - HALO;
+            int side;
+            const int szr = mirror_z(gz, G.nz, side);
+            const int sxr = wrap_x(gx, G.nx);
+            T val = T(0);
+            if (szr >= 0 && szr < G.nz) {
+                const size_t o = foff + (size_t)szr * G.nx + sxr;
+                val = FIRST ? r[o] * ith : zin[o];
+                if (side == 1) val *= T(G.pb[fld]);
+                else if (side == 2) val *= T(G.pt[fld]);
+            }
+            sz_[idx] = val;
+        }
+        __syncthreads();
+        const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
+        for (int idx = threadIdx.x; idx < QN; idx += blockDim.x) {
+            const int qz = idx / QX, qx = idx - qz * QX;
+            const int i1 = (qz + R) * SX + qx + R;
+            gx_[idx] = dd(sz_, i1, 1, idx_);
+            gz_[idx] = dd(sz_, i1, SX, idz_);
+            if (SMAG) {
+                const int gzz = z0 + qz - R;
+                int side;
+                const int szr = mirror_z(gzz, G.nz, side);
+                const int sxr = wrap_x(x0 + qx - R, G.nx);
+                T kv = T(0);
+                if (szr >= 0 && szr < G.nz) kv = nu[(size_t)szr * G.nx + sxr];
+                kk_[idx] = fld == 2 ? kv * T(G.inv_Pr) : kv;
+            }
+        }
+        __syncthreads();
+        const T Kc = T(fld == 2 ? G.K_H : G.K_M);
+        const T tdt = T(G.two_over_dt);
+        for (int idx = threadIdx.x; idx < TX * TZ; idx += blockDim.x) {
+            const int tz = idx / TX, tx = idx - tz * TX;
+            const int gz = z0 + tz, gx = x0 + tx;
+            if (gz >= G.nz || gx >= G.nx) continue;
+            const int i1 = (tz + HALO) * SX + tx + HALO;
+            const int q = (tz + R) * QX + tx + R;
+            T dif = ddk<T, SMAG>(kk_, Kc, gx_, q, 1, idx_) + ddk<T, SMAG>(kk_, Kc, gz_, q, QX, idz_);
+            const T xk = sz_[i1];
+            const size_t o = foff + (size_t)gz * G.nx + gx;
+            const T rv = r[o];
+            const T res = rv - (tdt * xk - dif);
+            const T dprev = FIRST ? rv * ith : din[o];
+            const T dk = T(cc.a1) * dprev + T(cc.a2) * res;
+            const T xn = xk + dk;
+            zout[o] = xn;
+            if (!LAST) dout[o] = dk;
+            if (LAST) acc[0] += (double)xn * (double)xn;
+        }
+    }
+    if (LAST) {
+        const int nblk = gridDim.x * gridDim.y * gridDim.z;
+        const int blk = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        block_partials<1>(acc, 1, part, nblk, blk);
+        if (arrive_last(&ctl->counter[CNT_PC], nblk)) {
+            __shared__ double tot[1];
+            final_sums(part, nblk, 1, tot);
+            if (threadIdx.x == 0) {
+                const double zn = sqrt(tot[0]);
+                ctl->eps_jv = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+            }
+        }
+    }
+}
+
+// p = 1 sweep count: z = r / theta_c for every field (point-wise), + eps from ||z||
+template <typename T, int SMAG>
+__global__ void __launch_bounds__(NTHREADS)
+pc_diag(Geo G, const T* __restrict__ r, T* __restrict__ z, size_t n, double* part, Ctl* ctl,
+        int check_done) {
+    if (check_done && ctl->done) return;
+    double acc[1] = {0.0};
+    double inv_th[4];
+    for (int f = 0; f < 4; ++f) {
+        const double lo = G.two_over_dt;
+        const double kmax = f == 3 ? 0.0 : (SMAG ? ctl->kmax * (f == 2 ? G.inv_Pr : 1.0) : (f == 2 ? G.K_H : G.K_M));
+        const double hi = lo + 2.25 * kmax * (G.inv_dx * G.inv_dx + G.inv_dz * G.inv_dz);
+        inv_th[f] = 2.0 / (hi + lo);
+    }
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int f = (int)(i / G.npt);
+        const T zv = T((double)r[i] * inv_th[f]);
+        z[i] = zv;
+        acc[0] += (double)zv * (double)zv;
+    }
+    block_partials<1>(acc, 1, part, gridDim.x, blockIdx.x);
+    if (arrive_last(&ctl->counter[CNT_PC], gridDim.x)) {
+        __shared__ double tot[1];
+        final_sums(part, gridDim.x, 1, tot);
+        if (threadIdx.x == 0) {
+            const double zn = sqrt(tot[0]);
+            ctl->eps_jv = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+        }
+    }
+}
+
+// ============================================================================
+// Budgets: E_k = 1/2 sum (u^2 + w^2) dV, E_p = sum (lz - z) theta dV (Section 3.1.3),
+// sum theta dV, sum div(u) dV, max / min of every field.
+// ============================================================================
+__global__ void __launch_bounds__(NTHREADS)
+budgets2d(Geo G, const double* __restrict__ u, double dV, double dz, double lz, double* part,
+          Ctl* ctl, double* out) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    double mx[8];
+    for (int f = 0; f < 4; ++f) { mx[f] = -1e300; mx[4 + f] = -1e300; }
+    const double* U = u;
+    const double* W = u + G.npt;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < G.npt; p += gridDim.x * blockDim.x) {
+        const int z = p / G.nx, x = p - z * G.nx;
+        const double zc = (z + 0.5) * dz;
+        s[0] += 0.5 * (U[p] * U[p] + W[p] * W[p]);
+        s[1] += (lz - zc) * u[2 * G.npt + p];
+        s[2] += u[2 * G.npt + p];
+        double ux = 0.0, wz = 0.0;
+        for (int l = 1; l <= 2; ++l) {
+            const double c = l == 1 ? 2.0 / 3.0 : -1.0 / 12.0;
+            ux += c * (U[z * G.nx + wrap_x(x + l, G.nx)] - U[z * G.nx + wrap_x(x - l, G.nx)]);
+            int sp_, sm_;
+            const int zp = mirror_z(z + l, G.nz, sp_), zm = mirror_z(z - l, G.nz, sm_);
+            const double gp = sp_ == 2 ? G.pt[1] : 1.0, gm = sm_ == 1 ? G.pb[1] : 1.0;
+            wz += c * (gp * W[zp * G.nx + x] - gm * W[zm * G.nx + x]);
+        }
+        s[3] += ux * G.inv_dx + wz * G.inv_dz;
+        for (int f = 0; f < 4; ++f) {
+            const double v = u[(size_t)f * G.npt + p];
+            mx[f] = fmax(mx[f], v);
+            mx[4 + f] = fmax(mx[4 + f], -v);
+        }
+    }
+    double* pmax = part + 4 * gridDim.x;
+    block_partials<4>(s, 4, part, gridDim.x, blockIdx.x);
+    block_partials_max<8>(mx, 8, pmax, gridDim.x, blockIdx.x);
+    if (arrive_last(&ctl->counter[CNT_MISC], gridDim.x)) {
+        __shared__ double tot[12];
+        final_sums(part, gridDim.x, 4, tot);
+        final_maxes(pmax, gridDim.x, 8, tot + 4);
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < 4; ++i) out[i] = tot[i] * dV;
+            for (int f = 0; f < 4; ++f) { out[4 + f] = tot[4 + f]; out[8 + f] = -tot[8 + f]; }
+        }
+    }
+}
+
+// ============================================================================
+// launchers
+// ============================================================================
+template <typename T> int stencil_blocks(const Geo& G) {
+    return ((G.nx + Tile<T>::TX - 1) / Tile<T>::TX) * ((G.nz + Tile<T>::TZ - 1) / Tile<T>::TZ);
+}
+template int stencil_blocks<float>(const Geo&);
+template int stencil_blocks<double>(const Geo&);
+
+template <typename T>
+static size_t stencil_smem() {
+    constexpr int TX = Tile<T>::TX, TZ = Tile<T>::TZ;
+    return sizeof(T) * (4 * (TZ + 2 * HALO) * (TX + 2 * HALO) + 7 * (TX + 2 * R) * (TZ + 2 * R));
+}
+
+template <typename T>
+static size_t jvd_smem() {
+    constexpr int TX = TileD<T>::TX, TZ = TileD<T>::TZ;
+    return sizeof(T) * (8 * (TZ + 2 * HALO) * (TX + 2 * HALO) + 14 * (TX + 2 * R) * (TZ + 2 * R));
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int MODE, int SMAG>
+static cudaError_t launch_stencil_t(const Geo& G, const T* u, const T* v, const T* Fu,
+                                    const double* f, T* out, T* out2, double* part, Ctl* ctl,
+                                    int check_done, cudaStream_t s) {
+    static bool configured = false;
+    const size_t sm = stencil_smem<T>();
+    if (!configured) {
+        cudaError_t e = set_smem(stencil2d<T, MODE, SMAG>, sm);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((G.nx + Tile<T>::TX - 1) / Tile<T>::TX, (G.nz + Tile<T>::TZ - 1) / Tile<T>::TZ);
+    stencil2d<T, MODE, SMAG><<<grid, NTHREADS, sm, s>>>(G, u, v, Fu, f, out, out2, part, ctl, check_done);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_stencil(int mode, const Geo& G, const T* u, const T* v, const T* Fu,
+                           const double* f, T* out, T* out2, double* part, Ctl* ctl,
+                           int check_done, cudaStream_t s) {
+#define JF_CASE(M)                                                                           \
+    case M:                                                                                  \
+        return G.smag ? launch_stencil_t<T, M, 1>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s) \
+                      : launch_stencil_t<T, M, 0>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
+    switch (mode) {
+        JF_CASE(MODE_F)
+        JF_CASE(MODE_RHS)
+        JF_CASE(MODE_RES)
+        JF_CASE(MODE_JV)
+        default: return cudaErrorInvalidValue;
+    }
+#undef JF_CASE
+}
+template cudaError_t launch_stencil<float>(int, const Geo&, const float*, const float*, const float*,
+                                           const double*, float*, float*, double*, Ctl*, int, cudaStream_t);
+template cudaError_t launch_stencil<double>(int, const Geo&, const double*, const double*, const double*,
+                                            const double*, double*, double*, double*, Ctl*, int, cudaStream_t);
+
+template <typename T, int SMAG>
+static cudaError_t launch_jvd_t(const Geo& G, const T* u, const T* v, T* out, Ctl* ctl,
+                                int check_done, cudaStream_t s) {
+    static bool configured = false;
+    const size_t sm = jvd_smem<T>();
+    if (!configured) {
+        cudaError_t e = set_smem(jv_diff2d<T, SMAG>, sm);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((G.nx + TileD<T>::TX - 1) / TileD<T>::TX, (G.nz + TileD<T>::TZ - 1) / TileD<T>::TZ);
+    jv_diff2d<T, SMAG><<<grid, NTHREADS, sm, s>>>(G, u, v, out, ctl, check_done);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_jv_diff(const Geo& G, const T* u, const T* v, T* out, double* part, Ctl* ctl,
+                           int check_done, cudaStream_t s) {
+    (void)part;
+    return G.smag ? launch_jvd_t<T, 1>(G, u, v, out, ctl, check_done, s)
+                  : launch_jvd_t<T, 0>(G, u, v, out, ctl, check_done, s);
+}
+template cudaError_t launch_jv_diff<float>(const Geo&, const float*, const float*, float*, double*, Ctl*, int, cudaStream_t);
+template cudaError_t launch_jv_diff<double>(const Geo&, const double*, const double*, double*, double*, Ctl*, int, cudaStream_t);
+
+static int stream_blocks(size_t n) {
+    size_t b = (n + NTHREADS - 1) / NTHREADS;
+    return (int)(b < (size_t)MAX_STREAM_BLOCKS ? (b > 0 ? b : 1) : MAX_STREAM_BLOCKS);
+}
+
+template <typename T>
+cudaError_t launch_eddy(const Geo& G, const T* u, T* nu, double* part, Ctl* ctl, cudaStream_t s) {
+    eddy2d<T><<<stream_blocks(G.npt), NTHREADS, 0, s>>>(G, u, nu, part, ctl);
+    return cudaGetLastError();
+}
+template cudaError_t launch_eddy<float>(const Geo&, const float*, float*, double*, Ctl*, cudaStream_t);
+template cudaError_t launch_eddy<double>(const Geo&, const double*, double*, double*, Ctl*, cudaStream_t);
+
+template <typename T, int SMAG>
+static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da,
+                                    T* db, const T* nu, double* part, Ctl* ctl, int check_done,
+                                    cudaStream_t s, long long* launches) {
+    const size_t n = (size_t)4 * G.npt;
+    if (sweeps <= 1) {
+        pc_diag<T, SMAG><<<stream_blocks(n), NTHREADS, 0, s>>>(G, r, z, n, part, ctl, check_done);
+        if (launches) ++*launches;
+        return cudaGetLastError();
+    }
+    dim3 grid((G.nx + Tile<T>::TX - 1) / Tile<T>::TX, (G.nz + Tile<T>::TZ - 1) / Tile<T>::TZ, 4);
+    const T* zin = nullptr;
+    const T* din = nullptr;
+    T* zbuf[2] = {za, zb};
+    T* dbuf[2] = {da, db};
+    for (int k = 1; k <= sweeps - 1; ++k) {
+        const bool first = k == 1, last = k == sweeps - 1;
+        T* zo = last ? z : zbuf[k & 1];
+        T* dO = dbuf[k & 1];
+        if (first && last)
+            cheb2d<T, SMAG, 1, 1><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+        else if (first)
+            cheb2d<T, SMAG, 1, 0><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+        else if (last)
+            cheb2d<T, SMAG, 0, 1><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+        else
+            cheb2d<T, SMAG, 0, 0><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+        if (launches) ++*launches;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        zin = zo;
+        din = dO;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_precond(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da, T* db,
+                           const T* nu, double* part, Ctl* ctl, int check_done, cudaStream_t s,
+                           long long* launches) {
+    return G.smag ? launch_precond_t<T, 1>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches)
+                  : launch_precond_t<T, 0>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches);
+}
+template cudaError_t launch_precond<float>(const Geo&, int, const float*, float*, float*, float*, float*,
+                                           float*, const float*, double*, Ctl*, int, cudaStream_t, long long*);
+template cudaError_t launch_precond<double>(const Geo&, int, const double*, double*, double*, double*,
+                                            double*, double*, const double*, double*, Ctl*, int, cudaStream_t,
+                                            long long*);
+
+cudaError_t launch_budgets(const Geo& G, const double* u, double dx, double dz, double lz,
+                           double* part, Ctl* ctl, double* out, cudaStream_t s) {
+    budgets2d<<<stream_blocks(G.npt), NTHREADS, 0, s>>>(G, u, dx * dz, dz, lz, part, ctl, out);
+    return cudaGetLastError();
+}
+
+}  // namespace jfnk

@@ -56,7 +56,7 @@ def _base_case(dim, nx, nz, lx, lz, ny=1, ly=1.0):
                   "gamma_p": R_GAS / CV, "rho0": P0 / (R_GAS * theta0), "cp": CP},
         "sgs": {"mode": SGS_CONST, "K_M": 10.0, "K_H": 14.1, "Cs": 0.18, "Pr": 0.71},
         "opts": {"precision": PREC_FP64, "wavelet_p": 2, "krylov_m": 30,
-                 "flexible": 0, "precond": PC_BLOCK, "pc_sweeps": 4,
+                 "flexible": 1, "precond": PC_BLOCK, "pc_sweeps": 4,
                  "newton_rtol": 1e-8, "newton_atol_factor": 1e-13, "eta": 1e-4,
                  "max_newton": 20, "max_restarts": 20, "dt": 1.0,
                  "scale_u": 10.0, "scale_theta": 1.0, "scale_p": 0.01},
