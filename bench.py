@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Throughput of the implicit JFNK step on one GB300: Mpt*steps/s at Newton tolerance 1e-8.
+
+Workload: the 2-D dry thermal in stable stratification (N = 0.01 1/s), 1024 x 512
+grid on 20 km x 10 km, cos^2 warm bubble 2 K + seeded 0.01 K white noise,
+Smagorinsky Cs = 0.18, trapezoidal step dt = 1 s solved by inexact Newton with
+GMRES(30) and the field-block preconditioner, float32 stencils / Krylov basis
+with float64 Newton residual, Hessenberg / Givens and update.  One "step" is one
+implicit time step (every Newton correction and Krylov iteration it needs).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the float64 CPU
+oracle on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "thermal_stable_1024x512"
+METRIC = "Mpt*steps/s at Newton tol 1e-8 (2D stable dry thermal 1024x512, mixed FP32/FP64 JFNK)"
+# Krylov iterations of the first implicit step of this workload, measured with the
+# float64 oracle (3 Newton corrections: 156 + 174 + 230 GMRES(30) iterations);
+# used to scale the oracle's bounded samples to whole steps.
+ORACLE_ITERS_PER_STEP = 560
+ORACLE_NEWTON_PER_STEP = 3
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--fp64-steps", type=int, default=3, help="steps of the plain float64 path (0: skip)")
+    p.add_argument("--e2e-steps", type=int, default=3, help="host-buffer steps through jfnk_step_host")
+    p.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample (0: skip)")
+    p.add_argument("--no-kernel-timing", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def ncu_traffic() -> dict:
+    """Per-algorithmic-byte DRAM traffic of the kernels captured with ncu (profiles/ncu_traffic.txt).
+
+    Lines: ``<family> <traffic/algorithmic ratio> <source sha1 of the .cu file>``; a ratio is used
+    only when the kernel source still has that hash.
+    """
+    import hashlib
+    out = {}
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    srcs = {"krylov": os.path.join(ROOT, "paper_2007_10411_gb300", "csrc", "krylov.cu"),
+            "stencil": os.path.join(ROOT, "paper_2007_10411_gb300", "csrc", "stencil.cu")}
+    hashes = {}
+    for k, p in srcs.items():
+        try:
+            hashes[k] = hashlib.sha1(open(p, "rb").read()).hexdigest()
+        except OSError:
+            hashes[k] = None
+    try:
+        for line in open(path):
+            t = line.split()
+            if len(t) >= 4 and not t[0].startswith("#"):
+                fam, ratio, src, sha = t[0], float(t[1]), t[2], t[3]
+                if hashes.get(src) == sha:
+                    out[fam] = ratio
+    except OSError:
+        pass
+    return out
+
+
+# ---------------------------------------------------------------- oracle sample
+def oracle_sample(case: dict, seconds: float, iters_per_step: float, newton_per_step: float):
+    """Time the float64 oracle on a bounded sample of one step of the workload.
+
+    The sample is the Newton set-up (F(u^n), R, F(u)) plus as many GMRES(m)
+    iterations (preconditioner, finite-difference Jv, CGS2) of the first Newton
+    solve as fit in ``seconds``; the step time is extrapolated as
+    setup * newton + per_iteration * iterations_per_step.
+    """
+    import numpy as np
+
+    from oracle.krylov import gmres
+    from oracle.operators import Model
+    from paper_2007_10411_gb300 import synth
+
+    m = Model(case)
+    U = synth.initial_state(case)
+    t0 = time.perf_counter()
+    f = m.rhs_f(U)
+    R = m.residual(U, f)
+    FU = m.F(U)
+    t_setup = time.perf_counter() - t0
+    o = case["opts"]
+    pc = (lambda v: m.precond(U, v, o["pc_sweeps"])) if o["precond"] == 1 else None
+    probe = 2
+    t1 = time.perf_counter()
+    gmres(lambda v: m.jv_scaled(U, FU, v), -m.scale(R), probe, 1e-30, 0, precond=pc, flexible=True)
+    t_probe = (time.perf_counter() - t1) / probe
+    k = int(max(1, min(o["krylov_m"], (seconds - t_setup) / max(t_probe, 1e-9))))
+    t2 = time.perf_counter()
+    rec = {}
+    gmres(lambda v: m.jv_scaled(U, FU, v), -m.scale(R), k, 1e-30, 0, precond=pc, flexible=True, record=rec)
+    t_it = (time.perf_counter() - t2) / rec["iters"]
+    step_s = t_setup * newton_per_step + t_it * iters_per_step
+    npt = case["grid"]["nx"] * case["grid"]["nz"]
+    return {
+        "value": npt / step_s / 1e6,
+        "step_seconds": step_s,
+        "sample": "oracle (numpy float64) on the %dx%d workload: Newton set-up + %d GMRES iterations "
+                  "of step 1 (%.1f s), extrapolated to %.0f iterations and %.0f Newton corrections per step"
+                  % (case["grid"]["nx"], case["grid"]["nz"], rec["iters"], t_setup + t_it * rec["iters"],
+                     iters_per_step, newton_per_step),
+        "seconds_used": time.perf_counter() - t0,
+    }
+
+
+def cpu_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    from paper_2007_10411_gb300 import synth
+    case = synth.case(args.workload)
+    per = []
+    sample = None
+    budget = 6.0
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(case, budget, ORACLE_ITERS_PER_STEP, ORACLE_NEWTON_PER_STEP)
+        if i >= args.warmup:
+            per.append(r["step_seconds"])
+            sample = r["sample"]
+    step_s = statistics.mean(per)
+    npt = case["grid"]["nx"] * case["grid"]["nz"]
+    value = npt / step_s / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpt*steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [case["grid"]["nx"], case["grid"]["nz"]],
+                   "note": "float64 numpy oracle; each step is a bounded sample extrapolated to a whole step"},
+        "cpu_baseline": {"value": value, "unit": "Mpt*steps/s", "cores": cpu_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Mpt*steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2007_10411_gb300 import jfnk, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist = dist_
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    case = synth.case(args.workload)
+    npt = case["grid"]["nx"] * case["grid"]["nz"]
+    n = 4 * npt
+    stream = torch.cuda.current_stream()
+    solver = jfnk.Solver(case, stream=stream)
+    U0 = synth.initial_state(case)
+    u = torch.from_numpy(U0).cuda()
+    for _ in range(args.warmup):
+        solver.step(u)
+    if not args.no_kernel_timing:
+        solver.kernel_timing()
+    stats = []
+    barrier()
+    clocks = Clocks(local_rank)
+    launches0 = solver.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        stats.append(solver.step(u))
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = solver.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms)
+    kt = solver.kernel_timing_read() if not args.no_kernel_timing else None
+    solver.kernel_timing(())
+    value = npt * args.steps * world / (ms / 1e3) / 1e6
+
+    # end to end through the public API with host buffers (pinned), copies in the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        uh = torch.from_numpy(U0.copy()).pin_memory()
+        solver.step_host(uh)                       # warm
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            solver.step_host(uh)
+        barrier()
+        el = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": npt * args.e2e_steps * world / el / 1e6, "unit": "Mpt*steps/s",
+               "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
+
+    # plain float64 JFNK on the same workload (the spec comparison)
+    fp64 = None
+    if args.fp64_steps > 0:
+        c64 = synth.with_options(case, precision=synth.PREC_FP64)
+        s64 = jfnk.Solver(c64, stream=stream)
+        u64 = torch.from_numpy(U0).cuda()
+        s64.step(u64)
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        st64 = [s64.step(u64) for _ in range(args.fp64_steps)]
+        a1.record(stream)
+        a1.synchronize()
+        ms64 = max_over_ranks(a0.elapsed_time(a1))
+        fp64 = {"value": npt * args.fp64_steps * world / (ms64 / 1e3) / 1e6,
+                "ms_per_step": ms64 / args.fp64_steps,
+                "gmres_iters_per_step": statistics.mean(s["gmres_iters"] for s in st64),
+                "newton_per_step": statistics.mean(s["newton_iters"] for s in st64)}
+        s64.close()
+
+    if rank != 0:
+        return
+    iters = statistics.mean(s["gmres_iters"] for s in stats)
+    newt = statistics.mean(s["newton_iters"] for s in stats)
+    roof = None
+    kernels = None
+    if kt is not None:
+        peaks = measured_peaks()
+        ratios = ncu_traffic()
+        kernels = {}
+        for name, a in kt.items():
+            if a["launches"] == 0 or a["ms"] <= 0:
+                continue
+            kernels[name] = {"launches": a["launches"], "ms_total": a["ms"],
+                             "share_of_step": a["ms"] / ms,
+                             "achieved_gbs": a["bytes"] / (a["ms"] / 1e3) / 1e9}
+        dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+        d = kernels[dom]
+        per_launch_bytes = kt[dom]["bytes"] / kt[dom]["launches"]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": d["achieved_gbs"] / peaks["hbm_gbs"],
+                "traffic": (ratios[dom] * per_launch_bytes) if dom in ratios else None,
+                "algorithmic_bytes_per_launch": per_launch_bytes,
+                "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)"}
+    cpu = None
+    if args.cpu_seconds > 0:
+        r = oracle_sample(case, args.cpu_seconds, iters, newt)
+        cpu = {"value": r["value"], "unit": "Mpt*steps/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": r["sample"]}
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpt*steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [case["grid"]["nx"], case["grid"]["nz"]],
+                   "points": npt, "precision": "mixed", "krylov_m": case["opts"]["krylov_m"],
+                   "precond": "field-block Chebyshev (%d sweeps)" % case["opts"]["pc_sweeps"],
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set > L2: the Krylov basis and directions (%d x %.1f MB) stream "
+                         "through L2 every Arnoldi pass" % (2 * case["opts"]["krylov_m"] + 1, n * 4 / 1e6)},
+        "newton_per_step": newt, "gmres_iters_per_step": iters,
+        "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "kernels": kernels,
+        "fp64_plain": fp64, "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -193,6 +193,34 @@ jfnk_status jfnk_budgets(jfnk_handle* h, const double* u, jfnk_budget* out);
 /* Number of this library's kernel launches enqueued since the handle was created. */
 jfnk_status jfnk_get_launch_count(jfnk_handle* h, long long* out);
 
+/* Kernel families whose launches can be timed (roofline reports). */
+enum {
+    JFNK_KF_ARNOLDI_A = 0,   /* pass A: h1 = V^T w                         */
+    JFNK_KF_ARNOLDI_B = 1,   /* pass B: w' = w - V h1, h2 = V^T w', Givens  */
+    JFNK_KF_ARNOLDI_C = 2,   /* pass C: v_{j+1} = (w - V h) / h_{j+1,j}     */
+    JFNK_KF_JV = 3,          /* Jacobian-vector product stencil             */
+    JFNK_KF_PRECOND = 4,     /* preconditioner sweeps (one apply)           */
+    JFNK_KF_RESIDUAL = 5,    /* Newton residual stencil (float64)           */
+    JFNK_KF_COUNT = 6
+};
+
+/* Device time and algorithmic bytes of one kernel family. */
+typedef struct {
+    long long launches;
+    double ms;          /* summed CUDA-event time of the launches            */
+    double bytes;       /* summed algorithmic HBM bytes (inputs read once,   */
+                        /* outputs written once) of the same launches        */
+} jfnk_kernel_time;
+
+/* Enable (mask != 0, bit i = family i) or disable event timing of kernel
+ * families on the handle's stream; enabling resets the accumulators.  The
+ * events add a few microseconds of host work per timed launch. */
+jfnk_status jfnk_kernel_timing(jfnk_handle* h, unsigned int mask);
+
+/* Drain the outstanding events (synchronises the stream) and copy the
+ * accumulators of all JFNK_KF_COUNT families into out[0 .. JFNK_KF_COUNT). */
+jfnk_status jfnk_kernel_timing_read(jfnk_handle* h, jfnk_kernel_time* out);
+
 /* Static description of a status code. */
 const char* jfnk_status_str(jfnk_status s);
 

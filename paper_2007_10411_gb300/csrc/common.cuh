@@ -16,6 +16,8 @@ namespace jfnk {
 constexpr int KMAX = 32;          // largest restart length the kernels are built for
 constexpr int NTHREADS = 256;     // threads per block of every streaming kernel
 constexpr int MAX_STREAM_BLOCKS = 2 * 152;  // streaming grid: two CTAs per SM
+constexpr int MAX_REDUCE_BLOCKS = 8192;     // multi-dot grids grow so a thread sums <= 64 vectors' worth
+constexpr int MAX_PC_SWEEPS = 16;
 
 // Geometry and physics constants, passed by value to the stencil kernels.
 struct Geo {
@@ -58,6 +60,8 @@ struct Ctl {
     double cs[KMAX], sn[KMAX];
     double g[KMAX + 1];
     double y[KMAX];
+    // Chebyshev coefficients per field block and sweep: 1/theta_c, rho_k rho_{k-1}, 2 rho_k / delta
+    double cheb[4][MAX_PC_SWEEPS][3];
     unsigned int counter[8];         // last-block counters, one per kernel family
 };
 

@@ -24,6 +24,7 @@ using namespace jfnk;
 
 namespace {
 constexpr int LAG = 2;
+constexpr int KT_RING = 256;   // outstanding timed launches before a drain
 }
 
 struct jfnk_handle {
@@ -45,6 +46,14 @@ struct jfnk_handle {
     int* hdone;      // pinned ring of per-step "done" flags
     cudaEvent_t ev[KMAX];
     long long launches;
+    // kernel-family timing (roofline reports)
+    unsigned int kt_mask;
+    bool kt_ready;
+    cudaEvent_t kt_start[KT_RING], kt_stop[KT_RING];
+    int kt_fam[KT_RING];
+    double kt_b[KT_RING];
+    int kt_head, kt_count, kt_open;
+    jfnk_kernel_time kt_acc[JFNK_KF_COUNT];
 };
 
 #define CK(call)                                                                  \
@@ -82,7 +91,7 @@ static jfnk_status validate(const jfnk_grid* g, const jfnk_strat* s, const jfnk_
     if (o->precision != JFNK_FP64 && o->precision != JFNK_MIXED) return JFNK_ERR_INVALID_ARG;
     if (o->krylov_m < 1 || o->krylov_m > JFNK_MAX_KRYLOV) return JFNK_ERR_INVALID_ARG;
     if (o->precond != JFNK_PC_NONE && o->precond != JFNK_PC_BLOCK) return JFNK_ERR_INVALID_ARG;
-    if (o->pc_sweeps < 1 || o->pc_sweeps > 64) return JFNK_ERR_INVALID_ARG;
+    if (o->pc_sweeps < 1 || o->pc_sweeps > MAX_PC_SWEEPS) return JFNK_ERR_INVALID_ARG;
     if (!finite_pos(o->newton_rtol) || !(o->newton_atol_factor >= 0.0) ||
         !(o->eta > 0.0 && o->eta < 1.0))
         return JFNK_ERR_INVALID_ARG;
@@ -108,6 +117,61 @@ static void free_all(jfnk_handle* h) {
     if (h->hdone) cudaFreeHost(h->hdone);
     for (int i = 0; i < KMAX; ++i)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    if (h->kt_ready)
+        for (int i = 0; i < KT_RING; ++i) {
+            cudaEventDestroy(h->kt_start[i]);
+            cudaEventDestroy(h->kt_stop[i]);
+        }
+}
+
+// ------------------------------------------------------------ kernel timing
+static void kt_drain(jfnk_handle* h) {
+    for (int c = 0; c < h->kt_count; ++c) {
+        const int i = (h->kt_head + c) % KT_RING;
+        float ms = 0.0f;
+        if (cudaEventSynchronize(h->kt_stop[i]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, h->kt_start[i], h->kt_stop[i]) == cudaSuccess) {
+            jfnk_kernel_time& a = h->kt_acc[h->kt_fam[i]];
+            a.launches += 1;
+            a.ms += ms;
+            a.bytes += h->kt_b[i];
+        }
+    }
+    h->kt_head = 0;
+    h->kt_count = 0;
+}
+
+static inline bool kt_on(const jfnk_handle* h, int fam) { return (h->kt_mask >> fam) & 1u; }
+
+static void kt_begin(jfnk_handle* h, int fam) {
+    if (!kt_on(h, fam)) return;
+    if (h->kt_count == KT_RING) kt_drain(h);
+    const int i = (h->kt_head + h->kt_count) % KT_RING;
+    cudaEventRecord(h->kt_start[i], h->stream);
+    h->kt_open = i;
+}
+
+static void kt_end(jfnk_handle* h, int fam, double bytes) {
+    if (!kt_on(h, fam)) return;
+    const int i = h->kt_open;
+    cudaEventRecord(h->kt_stop[i], h->stream);
+    h->kt_fam[i] = fam;
+    h->kt_b[i] = bytes;
+    h->kt_count += 1;
+}
+
+// Algorithmic HBM bytes of one preconditioner apply (every input read once,
+// every output written once, per field plane).
+static double pc_bytes(const jfnk_handle* h) {
+    const double P = (double)h->npt * (h->mixed ? 4.0 : 8.0);
+    const int s = h->opts.pc_sweeps;
+    if (s <= 1) return 2.0 * 4.0 * P;
+    double b = 0.0;
+    for (int k = 1; k <= s - 1; ++k) {
+        const bool first = k == 1, last = k == s - 1;
+        b += 3.0 * P * (1.0 + (first ? 0.0 : 2.0) + 1.0 + (last ? 0.0 : 1.0) + (h->G.smag ? 1.0 : 0.0));
+    }
+    return b + 2.0 * P;
 }
 
 template <typename T>
@@ -174,6 +238,10 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     int maxblk = MAX_STREAM_BLOCKS;
     maxblk = std::max(maxblk, stencil_part_blocks<double>(G));
     maxblk = std::max(maxblk, stencil_part_blocks<float>(G));
+    {   // multi-dot grids: up to n / (4 * NTHREADS * 64) CTAs
+        const size_t rb = h->n / ((size_t)NTHREADS * 64) + 1;
+        maxblk = std::max(maxblk, (int)std::min(rb, (size_t)MAX_REDUCE_BLOCKS));
+    }
     const size_t part_len = (size_t)maxblk * (KMAX + 2) + 16 * (size_t)MAX_STREAM_BLOCKS;
 
 #define ALLOC(ptr, bytes)                                                         \
@@ -257,6 +325,28 @@ extern "C" jfnk_status jfnk_set_surface_flux(jfnk_handle* h, const double* H) {
     CK(cudaMemcpyAsync(h->heat, H, (size_t)h->grid.nx * sizeof(double), cudaMemcpyDeviceToDevice,
                        h->stream));
     h->G.heat = h->heat;
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_kernel_timing(jfnk_handle* h, unsigned int mask) {
+    if (!h) return JFNK_ERR_INVALID_ARG;
+    if (mask != 0 && !h->kt_ready) {
+        for (int i = 0; i < KT_RING; ++i) {
+            CK(cudaEventCreate(&h->kt_start[i]));
+            CK(cudaEventCreate(&h->kt_stop[i]));
+        }
+        h->kt_ready = true;
+    }
+    if (h->kt_count) kt_drain(h);
+    h->kt_mask = mask;
+    memset(h->kt_acc, 0, sizeof(h->kt_acc));
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_kernel_timing_read(jfnk_handle* h, jfnk_kernel_time* out) {
+    if (!h || !out) return JFNK_ERR_INVALID_ARG;
+    kt_drain(h);
+    memcpy(out, h->kt_acc, sizeof(h->kt_acc));
     return JFNK_OK;
 }
 
@@ -375,6 +465,8 @@ static jfnk_status precond_impl(jfnk_handle* h, const double* u, const double* r
         CK(launch_eddy<T>(G, uT, (T*)h->nu, h->part, h->ctl, s));
         h->launches += 1;
     }
+    CK(launch_pc_setup(G, h->opts.pc_sweeps, h->ctl, s));
+    h->launches += 1;
     CK(launch_precond<T>(G, h->opts.pc_sweeps, rT, zT, (T*)h->za, (T*)h->zb, (T*)h->da, (T*)h->db,
                          (const T*)h->nu, h->part, h->ctl, 0, s, &h->launches));
     if (sizeof(T) != sizeof(double)) {
@@ -399,12 +491,14 @@ static jfnk_status read_ctl(jfnk_handle* h) {
 // Jacobian-vector product of the Newton system in scaled units: w = J_hat z.
 template <typename T>
 static jfnk_status apply_jv(jfnk_handle* h, const T* uT, const T* z, T* w, int check_done) {
+    kt_begin(h, JFNK_KF_JV);
     if (sizeof(T) == sizeof(double)) {
         CK(launch_stencil<double>(MODE_JV, h->G, (const double*)uT, (const double*)z, h->Fu64,
                                   nullptr, (double*)w, nullptr, h->part, h->ctl, check_done, h->stream));
     } else {
         CK(launch_jv_diff<T>(h->G, uT, z, w, h->part, h->ctl, check_done, h->stream));
     }
+    kt_end(h, JFNK_KF_JV, (double)h->n * (h->mixed ? 3.0 * 4.0 : 4.0 * 8.0));
     h->launches += 1;
     return JFNK_OK;
 }
@@ -428,14 +522,23 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
             T* vj = V + (size_t)j * ld;
             T* zj = Z + (size_t)j * ld;
             if (pc) {
+                kt_begin(h, JFNK_KF_PRECOND);
                 CK(launch_precond<T>(G, h->opts.pc_sweeps, vj, zj, (T*)h->za, (T*)h->zb, (T*)h->da,
                                      (T*)h->db, (const T*)h->nu, h->part, h->ctl, 1, s, &h->launches));
+                kt_end(h, JFNK_KF_PRECOND, pc_bytes(h));
             }
             jfnk_status st = apply_jv<T>(h, uT, zj, w, 1);
             if (st != JFNK_OK) return st;
+            const double vb = (double)n * sizeof(T);
+            kt_begin(h, JFNK_KF_ARNOLDI_A);
             CK(launch_arnoldi_a<T>(V, ld, w, n, j + 1, h->part, h->ctl, s));
+            kt_end(h, JFNK_KF_ARNOLDI_A, (j + 2) * vb);
+            kt_begin(h, JFNK_KF_ARNOLDI_B);
             CK(launch_arnoldi_b<T>(V, ld, w, n, j + 1, m, h->part, h->ctl, s));
+            kt_end(h, JFNK_KF_ARNOLDI_B, (j + 2) * vb);
+            kt_begin(h, JFNK_KF_ARNOLDI_C);
             CK(launch_arnoldi_c<T>(V, ld, w, n, j + 1, h->ctl, s));
+            kt_end(h, JFNK_KF_ARNOLDI_C, (j + 3) * vb);
             h->launches += 3;
             CK(cudaMemcpyAsync(&h->hdone[j], &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
             CK(cudaEventRecord(h->ev[j], s));
@@ -465,8 +568,10 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
 
 template <typename T>
 static jfnk_status residual_eval(jfnk_handle* h, const double* u) {
+    kt_begin(h, JFNK_KF_RESIDUAL);
     CK(launch_stencil<double>(MODE_RES, h->G, u, nullptr, nullptr, h->f, h->R, h->mixed ? nullptr : h->Fu64,
                               h->part, h->ctl, 0, h->stream));
+    kt_end(h, JFNK_KF_RESIDUAL, (double)h->n * 8.0 * (h->mixed ? 3.0 : 4.0));
     h->launches += 1;
     return read_ctl(h);
 }
@@ -499,8 +604,12 @@ static jfnk_status step_impl(jfnk_handle* h, double* u, jfnk_stats* out) {
     double res = r0;
     int k = 0;
     while (res > tol && k < h->opts.max_newton) {
-        if (h->opts.precond == JFNK_PC_BLOCK && G.smag) {
-            CK(launch_eddy<T>(G, uT, (T*)h->nu, h->part, h->ctl, s));
+        if (h->opts.precond == JFNK_PC_BLOCK) {
+            if (G.smag) {
+                CK(launch_eddy<T>(G, uT, (T*)h->nu, h->part, h->ctl, s));
+                h->launches += 1;
+            }
+            CK(launch_pc_setup(G, h->opts.pc_sweeps, h->ctl, s));
             h->launches += 1;
         }
         CK(launch_cycle_init<T>(G, h->R, (T*)h->V, h->x, n, h->opts.eta, h->m,

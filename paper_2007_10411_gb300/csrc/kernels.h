@@ -31,6 +31,9 @@ cudaError_t launch_precond(const Geo& G, int sweeps, const T* r, T* z, T* za, T*
                            const T* nu, double* part, Ctl* ctl, int check_done, cudaStream_t s,
                            long long* launches);
 
+// Chebyshev coefficients of the preconditioner blocks from ctl->kmax (or the constant K).
+cudaError_t launch_pc_setup(const Geo& G, int sweeps, Ctl* ctl, cudaStream_t s);
+
 // Budgets (E_k, E_p, sum theta, sum div, max/min per field) into out[0..4+2nf).
 cudaError_t launch_budgets(const Geo& G, const double* u, double dx, double dz, double lz,
                            double* part, Ctl* ctl, double* out, cudaStream_t s);

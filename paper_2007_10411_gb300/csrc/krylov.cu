@@ -10,9 +10,10 @@
 //       stopping test and (when the cycle ends) the triangular solve for y
 //   C:  v_{j+1} = (w - V h) / h_{j+1,j}               (multi-axpy + scale)
 // Reductions are two-stage and deterministic: every block writes its partial
-// sums, the last block to finish adds them in a fixed order.  Per-thread
-// partials of float32 vectors are accumulated in float32 over at most FLUSH
-// elements and then folded into float64.
+// sums, the last block to finish adds them in a fixed order.  A thread
+// accumulates its partial dot products in the basis precision over at most
+// 64 vector elements (the grid grows with n), then the block and grid
+// reductions run in float64.
 #include <math.h>
 
 #include "common.cuh"
@@ -20,11 +21,16 @@
 
 namespace jfnk {
 
-constexpr int FLUSH = 16;
+constexpr int PER_THREAD = 64;   // vector loads (of one basis vector) a multi-dot thread accumulates
 
 template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; static constexpr int W = 4; };
 template <> struct V4<double> { using type = double2; static constexpr int W = 2; };
+// Pass B keeps every basis element it loads in registers for its second use
+// (the dot products after the axpys), so it works on scalars.
+template <typename T> struct V2;
+template <> struct V2<float> { using type = float; static constexpr int W = 1; };
+template <> struct V2<double> { using type = double; static constexpr int W = 1; };
 
 __device__ __forceinline__ float dotv(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
 __device__ __forceinline__ double dotv(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
@@ -34,6 +40,10 @@ __device__ __forceinline__ float4 axpyv(float4 y, float a, float4 x) {
 __device__ __forceinline__ double2 axpyv(double2 y, double a, double2 x) {
     return make_double2(y.x - a * x.x, y.y - a * x.y);
 }
+__device__ __forceinline__ float dotv(float a, float b) { return a * b; }
+__device__ __forceinline__ double dotv(double a, double b) { return a * b; }
+__device__ __forceinline__ float axpyv(float y, float a, float x) { return y - a * x; }
+__device__ __forceinline__ double axpyv(double y, double a, double x) { return y - a * x; }
 __device__ __forceinline__ float4 scalev(float4 x, float a) { return make_float4(a * x.x, a * x.y, a * x.z, a * x.w); }
 __device__ __forceinline__ double2 scalev(double2 x, double a) { return make_double2(a * x.x, a * x.y); }
 
@@ -42,39 +52,41 @@ static int stream_blocks(size_t n) {
     return (int)(b < (size_t)MAX_STREAM_BLOCKS ? (b > 0 ? b : 1) : MAX_STREAM_BLOCKS);
 }
 
+// Grid of the multi-dot kernels: >= two CTAs per SM, and enough CTAs that no
+// thread accumulates more than PER_THREAD vector elements in low precision.
+static int reduce_blocks(size_t nvec) {
+    size_t b = (nvec + (size_t)NTHREADS * PER_THREAD - 1) / ((size_t)NTHREADS * PER_THREAD);
+    if (b < (size_t)MAX_STREAM_BLOCKS) return stream_blocks(nvec);
+    return (int)(b < (size_t)MAX_REDUCE_BLOCKS ? b : MAX_REDUCE_BLOCKS);
+}
+
 // ---------------------------------------------------------------- pass A
 template <typename T, int NV>
-__global__ void __launch_bounds__(NTHREADS)
+__global__ void __launch_bounds__(NTHREADS, 2)
 arnoldi_a(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv,
           double* part, Ctl* ctl) {
     if (ctl->done) return;
     using VT = typename V4<T>::type;
     constexpr int W = V4<T>::W;
     T acc_t[NV];
-    double acc[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) { acc_t[k] = T(0); acc[k] = 0.0; }
+    for (int k = 0; k < NV; ++k) acc_t[k] = T(0);
     const size_t nvec = n / W;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    int cnt = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvec; i += stride) {
         const VT wv = reinterpret_cast<const VT*>(w)[i];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
             if (k < nv) acc_t[k] += dotv(reinterpret_cast<const VT*>(V + k * ldv)[i], wv);
-        if (++cnt == FLUSH) {
-#pragma unroll
-            for (int k = 0; k < NV; ++k) { acc[k] += (double)acc_t[k]; acc_t[k] = T(0); }
-            cnt = 0;
-        }
     }
     for (size_t i = nvec * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
 #pragma unroll
         for (int k = 0; k < NV; ++k)
             if (k < nv) acc_t[k] += V[k * ldv + i] * w[i];
     }
+    double acc[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] += (double)acc_t[k];
+    for (int k = 0; k < NV; ++k) acc[k] = (double)acc_t[k];
     block_partials<NV>(acc, nv, part, gridDim.x, blockIdx.x);
     if (arrive_last(&ctl->counter[CNT_PASSA], gridDim.x)) {
         __shared__ double tot[NV];
@@ -143,37 +155,34 @@ __device__ void givens_update(Ctl* c, int j, int m, const double* h2, double wn2
 }
 
 template <typename T, int NV>
-__global__ void __launch_bounds__(NTHREADS)
+__global__ void __launch_bounds__(NTHREADS, (sizeof(T) == 4 || NV < 32) ? 2 : 1)
 arnoldi_b(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv, int m,
           double* part, Ctl* ctl) {
     if (ctl->done) return;
-    using VT = typename V4<T>::type;
-    constexpr int W = V4<T>::W;
     __shared__ T h1s[NV];
     for (int k = threadIdx.x; k < nv; k += blockDim.x) h1s[k] = T(ctl->h1[k]);
     __syncthreads();
     // slot 0: ||w'||^2, slot 1 + k: v_k . w'
+    using VT = typename V2<T>::type;
+    constexpr int W = V2<T>::W;
     T acc_t[NV + 1];
-    double acc[NV + 1];
 #pragma unroll
-    for (int k = 0; k <= NV; ++k) { acc_t[k] = T(0); acc[k] = 0.0; }
+    for (int k = 0; k <= NV; ++k) acc_t[k] = T(0);
     const size_t nvec = n / W;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    int cnt = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvec; i += stride) {
+        VT vk[NV];
         VT wp = reinterpret_cast<const VT*>(w)[i];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
-            if (k < nv) wp = axpyv(wp, h1s[k], reinterpret_cast<const VT*>(V + k * ldv)[i]);
+            if (k < nv) {
+                vk[k] = reinterpret_cast<const VT*>(V + k * ldv)[i];
+                wp = axpyv(wp, h1s[k], vk[k]);
+            }
 #pragma unroll
         for (int k = 0; k < NV; ++k)
-            if (k < nv) acc_t[1 + k] += dotv(reinterpret_cast<const VT*>(V + k * ldv)[i], wp);
+            if (k < nv) acc_t[1 + k] += dotv(vk[k], wp);
         acc_t[0] += dotv(wp, wp);
-        if (++cnt == FLUSH) {
-#pragma unroll
-            for (int k = 0; k <= NV; ++k) { acc[k] += (double)acc_t[k]; acc_t[k] = T(0); }
-            cnt = 0;
-        }
     }
     for (size_t i = nvec * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
         T wp = w[i];
@@ -185,8 +194,9 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n
             if (k < nv) acc_t[1 + k] += V[k * ldv + i] * wp;
         acc_t[0] += wp * wp;
     }
+    double acc[NV + 1];
 #pragma unroll
-    for (int k = 0; k <= NV; ++k) acc[k] += (double)acc_t[k];
+    for (int k = 0; k <= NV; ++k) acc[k] = (double)acc_t[k];
     block_partials<NV + 1>(acc, nv + 1, part, gridDim.x, blockIdx.x);
     if (arrive_last(&ctl->counter[CNT_PASSB], gridDim.x)) {
         __shared__ double tot[NV + 1];
@@ -197,7 +207,7 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n
 
 // ---------------------------------------------------------------- pass C
 template <typename T, int NV>
-__global__ void __launch_bounds__(NTHREADS)
+__global__ void __launch_bounds__(NTHREADS, 2)
 arnoldi_c(T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv, Ctl* ctl) {
     if (ctl->done) return;
     using VT = typename V4<T>::type;
@@ -236,6 +246,8 @@ update_x(const T* __restrict__ Z, size_t ldz, double* __restrict__ x, T* __restr
     double acc[1] = {0.0};
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        // the basis-precision directions enter exactly; their combination is
+        // formed in float64 so the Newton update carries no extra rounding
         double s = x[i];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
@@ -384,7 +396,7 @@ __global__ void set_eps_k(double eps, int su, int sv, Ctl* ctl) {
 template <typename T>
 cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int nv, double* part,
                              Ctl* ctl, cudaStream_t s) {
-    const int nb = stream_blocks(n / V4<T>::W);
+    const int nb = reduce_blocks(n / V4<T>::W);
     if (nv <= 8) arnoldi_a<T, 8><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, part, ctl);
     else if (nv <= 16) arnoldi_a<T, 16><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, part, ctl);
     else arnoldi_a<T, 32><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, part, ctl);
@@ -394,7 +406,7 @@ cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int n
 template <typename T>
 cudaError_t launch_arnoldi_b(const T* V, size_t ldv, const T* w, size_t n, int nv, int m,
                              double* part, Ctl* ctl, cudaStream_t s) {
-    const int nb = stream_blocks(n / V4<T>::W);
+    const int nb = reduce_blocks(n / V2<T>::W);
     if (nv <= 8) arnoldi_b<T, 8><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);
     else if (nv <= 16) arnoldi_b<T, 16><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);
     else arnoldi_b<T, 32><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);

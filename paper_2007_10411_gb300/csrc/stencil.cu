@@ -156,11 +156,17 @@ stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
     const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
 
     T ev[4] = {T(0), T(0), T(0), T(0)};
-    double eps = 0.0;
+    __shared__ double cfs[4];            // 1 / (eps scale_f), computed once per block
+    __shared__ T evs[4];                 // eps scale_f
     if (MODE == MODE_JV) {
-        eps = ctl->eps_jv;
+        if (threadIdx.x < 4) {
+            const double e = ctl->eps_jv * G.scale[threadIdx.x];
+            evs[threadIdx.x] = T(e);
+            cfs[threadIdx.x] = e != 0.0 ? 1.0 / e : 0.0;
+        }
+        __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ev[q] = T(eps * G.scale[q]);
+        for (int q = 0; q < 4; ++q) ev[q] = evs[q];
         load_fields<T, 1>(s1, u, v, ev, G, x0, z0, SX, SZ);
     } else {
         load_fields<T, 0>(s1, u, v, ev, G, x0, z0, SX, SZ);
@@ -251,7 +257,7 @@ stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
             } else {  // MODE_JV: w_hat = 2 v_hat/dt - (F(u + eps V) - F(u)) / (eps scale)
                 const double vh = (double)v[o];
                 const double diff = (double)Fv[fl] - (double)Fu[o];
-                out[o] = T(G.two_over_dt * vh - diff / (eps * G.scale[fl]));
+                out[o] = T(G.two_over_dt * vh - diff * cfs[fl]);
             }
         }
     }
@@ -298,10 +304,17 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
     T* dK = Ka + QN;
     const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
     const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
-    const double eps = ctl->eps_jv;
+    __shared__ double cfs[4];            // 1 / (eps scale_f), computed once per block
+    __shared__ T evs[4];                 // eps scale_f
+    if (threadIdx.x < 4) {
+        const double e = ctl->eps_jv * G.scale[threadIdx.x];
+        evs[threadIdx.x] = T(e);
+        cfs[threadIdx.x] = e != 0.0 ? 1.0 / e : 0.0;
+    }
+    __syncthreads();
     T ev[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) ev[q] = T(eps * G.scale[q]);
+    for (int q = 0; q < 4; ++q) ev[q] = evs[q];
     load_fields<T, 0>(sa, u, v, ev, G, x0, z0, SX, SZ);
     load_fields<T, 2>(sb, u, v, ev, G, x0, z0, SX, SZ);
     __syncthreads();
@@ -414,7 +427,7 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
         for (int fl = 0; fl < 4; ++fl) {
             const size_t o = (size_t)fl * G.npt + off;
             const double vh = (double)v[o];
-            out[o] = T(G.two_over_dt * vh - (double)dF[fl] / (eps * G.scale[fl]));
+            out[o] = T(G.two_over_dt * vh - (double)dF[fl] * cfs[fl]);
         }
     }
 }
@@ -425,7 +438,7 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
 eddy2d(Geo G, const T* __restrict__ u, T* __restrict__ nu, double* part, Ctl* ctl) {
-    double mx[1] = {0.0};
+    T mxT = T(0);
     const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
     const T cs2 = T(G.cs2);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < G.npt; p += gridDim.x * blockDim.x) {
@@ -448,8 +461,9 @@ eddy2d(Geo G, const T* __restrict__ u, T* __restrict__ nu, double* part, Ctl* ct
         }
         const T v_ = smag_nu(ux * idx_, uz * idz_, wx * idx_, wz * idz_, cs2);
         nu[p] = v_;
-        mx[0] = fmax(mx[0], (double)v_);
+        mxT = v_ > mxT ? v_ : mxT;
     }
+    double mx[1] = {(double)mxT};
     block_partials_max<1>(mx, 1, part, gridDim.x, blockIdx.x);
     if (arrive_last(&ctl->counter[CNT_EDDY], gridDim.x)) {
         __shared__ double tot[1];
@@ -467,24 +481,31 @@ eddy2d(Geo G, const T* __restrict__ u, T* __restrict__ nu, double* part, Ctl* ct
 //   res = r - A x_k;  d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) res;
 //   x_{k+1} = x_k + d_k,   with x_1 = d_0 = r / theta_c.
 // ============================================================================
-struct ChebK {
-    double inv_theta, a1, a2;   // 1/theta_c, rho_k rho_{k-1}, 2 rho_k / delta
-};
-
-__device__ __forceinline__ ChebK cheb_coef(double lo, double hi, int k) {
-    ChebK c;
-    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
-    c.inv_theta = 1.0 / theta;
-    if (delta <= 1e-14 * theta) { c.a1 = 0.0; c.a2 = 0.0; return c; }
-    const double sigma = theta / delta;
-    double rho = 1.0 / sigma, rho_new = rho;
-    for (int i = 1; i <= k; ++i) {
-        rho_new = 1.0 / (2.0 * sigma - rho);
-        if (i < k) rho = rho_new;
+// Coefficients of every sweep of every block, computed once per Newton
+// iteration from the (frozen) eddy maximum by one thread: 1/theta_c,
+// rho_k rho_{k-1} and 2 rho_k / delta, with rho_0 = 1/sigma, sigma = theta_c/delta.
+__global__ void pc_setup(Geo G, int sweeps, Ctl* ctl) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int f = 0; f < 4; ++f) {
+        const double lo = G.two_over_dt;
+        double kmax = 0.0;
+        if (f < 3) kmax = G.smag ? ctl->kmax * (f == 2 ? G.inv_Pr : 1.0) : (f == 2 ? G.K_H : G.K_M);
+        const double hi = lo + 2.25 * kmax * (G.inv_dx * G.inv_dx + G.inv_dz * G.inv_dz);
+        const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+        const bool degenerate = delta <= 1e-14 * theta;
+        const double sigma = degenerate ? 1.0 : theta / delta;
+        double rho = 1.0 / sigma;
+        ctl->cheb[f][0][0] = 1.0 / theta;
+        ctl->cheb[f][0][1] = 0.0;
+        ctl->cheb[f][0][2] = 0.0;
+        for (int k = 1; k < sweeps && k < MAX_PC_SWEEPS; ++k) {
+            const double rho_new = 1.0 / (2.0 * sigma - rho);
+            ctl->cheb[f][k][0] = 1.0 / theta;
+            ctl->cheb[f][k][1] = degenerate ? 0.0 : rho_new * rho;
+            ctl->cheb[f][k][2] = degenerate ? 0.0 : 2.0 * rho_new / delta;
+            rho = rho_new;
+        }
     }
-    c.a1 = rho_new * rho;
-    c.a2 = 2.0 * rho_new / delta;
-    return c;
 }
 
 template <typename T, int SMAG, int FIRST, int LAST>
@@ -503,10 +524,9 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
     __shared__ T kk_[SMAG ? QN : 1];
     const int fld = blockIdx.z;                 // 0 u, 1 w, 2 theta, 3 p
     const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
-    const double lo = G.two_over_dt;
-    const double kmax = SMAG ? ctl->kmax * (fld == 2 ? G.inv_Pr : 1.0) : (fld == 2 ? G.K_H : G.K_M);
-    const double hi = fld == 3 ? lo : lo + 2.25 * kmax * (G.inv_dx * G.inv_dx + G.inv_dz * G.inv_dz);
-    const ChebK cc = cheb_coef(lo, hi, k);
+    const T c_ith = T(ctl->cheb[fld][k][0]);
+    const T c_a1 = T(ctl->cheb[fld][k][1]);
+    const T c_a2 = T(ctl->cheb[fld][k][2]);
     const size_t foff = (size_t)fld * G.npt;
     double acc[1] = {0.0};
     if (fld == 3) {
@@ -517,13 +537,13 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
                 const int gz = z0 + tz, gx = x0 + tx;
                 if (gz >= G.nz || gx >= G.nx) continue;
                 const size_t o = foff + (size_t)gz * G.nx + gx;
-                const T zv = T((double)r[o] * cc.inv_theta);
+                const T zv = r[o] * c_ith;
                 zout[o] = zv;
                 acc[0] += (double)zv * (double)zv;
             }
         }
     } else {
-        const T ith = T(cc.inv_theta);
+        const T ith = c_ith;
         // x_k with halo 2r (x_1 = r / theta)
         for (int idx = threadIdx.x; idx < SZ * SX; idx += blockDim.x) {
             const int iz = idx / SX, ix = idx - iz * SX;
@@ -572,7 +592,7 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
             const T rv = r[o];
             const T res = rv - (tdt * xk - dif);
             const T dprev = FIRST ? rv * ith : din[o];
-            const T dk = T(cc.a1) * dprev + T(cc.a2) * res;
+            const T dk = c_a1 * dprev + c_a2 * res;
             const T xn = xk + dk;
             zout[o] = xn;
             if (!LAST) dout[o] = dk;
@@ -601,16 +621,11 @@ pc_diag(Geo G, const T* __restrict__ r, T* __restrict__ z, size_t n, double* par
         int check_done) {
     if (check_done && ctl->done) return;
     double acc[1] = {0.0};
-    double inv_th[4];
-    for (int f = 0; f < 4; ++f) {
-        const double lo = G.two_over_dt;
-        const double kmax = f == 3 ? 0.0 : (SMAG ? ctl->kmax * (f == 2 ? G.inv_Pr : 1.0) : (f == 2 ? G.K_H : G.K_M));
-        const double hi = lo + 2.25 * kmax * (G.inv_dx * G.inv_dx + G.inv_dz * G.inv_dz);
-        inv_th[f] = 2.0 / (hi + lo);
-    }
+    T inv_th[4];
+    for (int f = 0; f < 4; ++f) inv_th[f] = T(ctl->cheb[f][0][0]);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int f = (int)(i / G.npt);
-        const T zv = T((double)r[i] * inv_th[f]);
+        const T zv = r[i] * inv_th[f];
         z[i] = zv;
         acc[0] += (double)zv * (double)zv;
     }
@@ -785,7 +800,7 @@ static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, 
         if (launches) ++*launches;
         return cudaGetLastError();
     }
-    dim3 grid((G.nx + Tile<T>::TX - 1) / Tile<T>::TX, (G.nz + Tile<T>::TZ - 1) / Tile<T>::TZ, 4);
+    dim3 grid((G.nx + Tile<T>::TX - 1) / Tile<T>::TX, (G.nz + Tile<T>::TZ - 1) / Tile<T>::TZ, 3);
     const T* zin = nullptr;
     const T* din = nullptr;
     T* zbuf[2] = {za, zb};
@@ -794,6 +809,7 @@ static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, 
         const bool first = k == 1, last = k == sweeps - 1;
         T* zo = last ? z : zbuf[k & 1];
         T* dO = dbuf[k & 1];
+        grid.z = last ? 4 : 3;            // the p block is written by the last sweep only
         if (first && last)
             cheb2d<T, SMAG, 1, 1><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else if (first)
@@ -823,6 +839,11 @@ template cudaError_t launch_precond<float>(const Geo&, int, const float*, float*
 template cudaError_t launch_precond<double>(const Geo&, int, const double*, double*, double*, double*,
                                             double*, double*, const double*, double*, Ctl*, int, cudaStream_t,
                                             long long*);
+
+cudaError_t launch_pc_setup(const Geo& G, int sweeps, Ctl* ctl, cudaStream_t s) {
+    pc_setup<<<1, 32, 0, s>>>(G, sweeps, ctl);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_budgets(const Geo& G, const double* u, double dx, double dz, double lz,
                            double* part, Ctl* ctl, double* out, cudaStream_t s) {

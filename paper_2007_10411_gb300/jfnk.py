@@ -27,8 +27,10 @@ MAX_NEWTON = 32
 EXPORTS = (
     "jfnk_create", "jfnk_destroy", "jfnk_set_surface_flux", "jfnk_rhs", "jfnk_residual",
     "jfnk_jv", "jfnk_precond_apply", "jfnk_step", "jfnk_step_host", "jfnk_budgets",
-    "jfnk_get_launch_count", "jfnk_status_str",
+    "jfnk_get_launch_count", "jfnk_status_str", "jfnk_kernel_timing", "jfnk_kernel_timing_read",
 )
+
+KERNEL_FAMILIES = ("arnoldi_a", "arnoldi_b", "arnoldi_c", "jv", "precond", "residual")
 
 
 class Grid(ctypes.Structure):
@@ -68,6 +70,10 @@ class Stats(ctypes.Structure):
                 "gmres_per_newton": list(self.gmres_per_newton[:k])}
 
 
+class KernelTime(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 class Budget(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("E_k", "E_p", "sum_theta", "sum_div")] + \
                [("max", ctypes.c_double * 5), ("min", ctypes.c_double * 5)]
@@ -99,6 +105,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.jfnk_step_host.argtypes = [P, P, ctypes.POINTER(Stats)]
     lib.jfnk_budgets.argtypes = [P, P, ctypes.POINTER(Budget)]
     lib.jfnk_get_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.jfnk_kernel_timing.argtypes = [P, ctypes.c_uint]
+    lib.jfnk_kernel_timing_read.argtypes = [P, ctypes.POINTER(KernelTime)]
     lib.jfnk_status_str.argtypes = [I]
     lib.jfnk_status_str.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -215,6 +223,19 @@ class Solver:
         nf = self.shape[0]
         return {"E_k": b.E_k, "E_p": b.E_p, "sum_theta": b.sum_theta, "sum_div": b.sum_div,
                 "max": list(b.max[:nf]), "min": list(b.min[:nf])}
+
+    def kernel_timing(self, families=KERNEL_FAMILIES):
+        """Start CUDA-event timing of the named kernel families (resets the accumulators)."""
+        mask = 0
+        for f in families:
+            mask |= 1 << KERNEL_FAMILIES.index(f)
+        _check(self.lib.jfnk_kernel_timing(self.h, mask), "jfnk_kernel_timing")
+
+    def kernel_timing_read(self) -> dict:
+        arr = (KernelTime * len(KERNEL_FAMILIES))()
+        _check(self.lib.jfnk_kernel_timing_read(self.h, arr), "jfnk_kernel_timing_read")
+        return {name: {"launches": a.launches, "ms": a.ms, "bytes": a.bytes}
+                for name, a in zip(KERNEL_FAMILIES, arr)}
 
     def launch_count(self) -> int:
         c = ctypes.c_longlong(0)
