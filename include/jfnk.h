@@ -167,9 +167,11 @@ jfnk_status jfnk_residual(jfnk_handle* h, const double* u_n, const double* u, do
  *   Jv = 2 v/dt - (F(u + eps v) - F(u)) / eps.
  * F_u may be NULL (then F(u) is evaluated here) or F(u) from jfnk_rhs.
  * eps > 0 is used as given; eps <= 0 selects the rule
- *   eps = sqrt(eps_mach (1 + ||W u||)) / ||W v||
- * with eps_mach = 2^-52 (FP64) or 2^-23 (MIXED).  *eps_out (host pointer,
- * may be NULL) receives the step used; this synchronises the stream. */
+ *   eps = sqrt(eps_mach (1 + ||W u||)) / ||W v||,  eps_mach = 2^-52,
+ * for both precisions (MIXED evaluates the difference F(u + eps v) - F(u)
+ * term by term without cancellation, so float32 stencils do not need a
+ * larger step).  *eps_out (host pointer, may be NULL) receives the step
+ * used; this synchronises the stream. */
 jfnk_status jfnk_jv(jfnk_handle* h, const double* u, const double* F_u, const double* v,
                     double eps, double* Jv, double* eps_out);
 

@@ -54,7 +54,7 @@ struct Ctl {
     double kmax;         // max eddy coefficient K_M (preconditioner bounds)
     double scratch[8];   // misc reductions (||x||^2, ||r||^2, ...)
     double h1[KMAX + 1];
-    double hsum[KMAX + 1];
+    double h2[KMAX + 1];      // second-projection coefficients (pass C)
     double Hbar[KMAX + 1][KMAX];     // Hessenberg as built (row, col)
     double Rt[KMAX][KMAX];           // rotated upper-triangular factor
     double cs[KMAX], sn[KMAX];

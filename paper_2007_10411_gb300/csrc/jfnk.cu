@@ -295,7 +295,10 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     }
     Ctl init;
     memset(&init, 0, sizeof(init));
-    init.eps_mach = h->mixed ? ldexp(1.0, -23) : ldexp(1.0, -52);
+    // Both paths use the float64 unit roundoff in the step rule: the mixed
+    // path forms F(u + eps V) - F(u) in difference form, without cancellation,
+    // so its step need not grow with the float32 roundoff.
+    init.eps_mach = ldexp(1.0, -52);
     init.m = m;
     if (cudaMemcpy(h->ctl, &init, sizeof(Ctl), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(h->part, 0, part_len * sizeof(double)) != cudaSuccess ||
@@ -535,7 +538,7 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
             kt_end(h, JFNK_KF_ARNOLDI_A, (j + 2) * vb);
             kt_begin(h, JFNK_KF_ARNOLDI_B);
             CK(launch_arnoldi_b<T>(V, ld, w, n, j + 1, m, h->part, h->ctl, s));
-            kt_end(h, JFNK_KF_ARNOLDI_B, (j + 2) * vb);
+            kt_end(h, JFNK_KF_ARNOLDI_B, (j + 3) * vb);   // reads v_0..v_j, w; writes w'
             kt_begin(h, JFNK_KF_ARNOLDI_C);
             CK(launch_arnoldi_c<T>(V, ld, w, n, j + 1, h->ctl, s));
             kt_end(h, JFNK_KF_ARNOLDI_C, (j + 3) * vb);

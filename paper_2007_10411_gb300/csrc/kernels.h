@@ -43,7 +43,7 @@ template <typename T>
 cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int nv, double* part,
                              Ctl* ctl, cudaStream_t s);
 template <typename T>
-cudaError_t launch_arnoldi_b(const T* V, size_t ldv, const T* w, size_t n, int nv, int m,
+cudaError_t launch_arnoldi_b(const T* V, size_t ldv, T* w, size_t n, int nv, int m,
                              double* part, Ctl* ctl, cudaStream_t s);
 template <typename T>
 cudaError_t launch_arnoldi_c(T* V, size_t ldv, const T* w, size_t n, int nv, Ctl* ctl,

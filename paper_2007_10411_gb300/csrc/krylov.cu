@@ -4,11 +4,14 @@
 // One Arnoldi step j (w = J z_j already formed) is three streaming passes over
 // the basis V = [v_0 .. v_j]:
 //   A:  h1 = V^T w                                  (multi-dot)
-//   B:  w' = w - V h1,  h2 = V^T w',  ||w'||^2        (multi-axpy fused with multi-dot)
+//   B:  w' = w - V h1 (stored over w),  h2 = V^T w',  ||w'||^2
 //       last block: h = h1 + h2, h_{j+1,j} = sqrt(||w'||^2 - ||h2||^2), Givens
 //       rotation of the Hessenberg column, residual estimate |g_{j+1}|,
 //       stopping test and (when the cycle ends) the triangular solve for y
-//   C:  v_{j+1} = (w - V h) / h_{j+1,j}               (multi-axpy + scale)
+//   C:  v_{j+1} = (w' - V h2) / h_{j+1,j}             (multi-axpy + scale)
+// The second projection is subtracted from the stored w', as in classical
+// Gram-Schmidt applied twice: the rounding of w - V h1 is then part of what
+// h2 removes, and the last rounding is relative to ||w'||, not ||w||.
 // Reductions are two-stage and deterministic: every block writes its partial
 // sums, the last block to finish adds them in a fixed order.  A thread
 // accumulates its partial dot products in the basis precision over at most
@@ -102,7 +105,7 @@ __device__ void givens_update(Ctl* c, int j, int m, const double* h2, double wn2
     double hh2 = 0.0;
     for (int k = 0; k <= j; ++k) {
         const double hk = c->h1[k] + h2[k];
-        c->hsum[k] = hk;
+        c->h2[k] = h2[k];              // pass C subtracts V h2 from the stored w'
         c->Hbar[k][j] = hk;
         col[k] = hk;
         hh2 += h2[k] * h2[k];
@@ -156,7 +159,7 @@ __device__ void givens_update(Ctl* c, int j, int m, const double* h2, double wn2
 
 template <typename T, int NV>
 __global__ void __launch_bounds__(NTHREADS, (sizeof(T) == 4 || NV < 32) ? 2 : 1)
-arnoldi_b(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv, int m,
+arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int nv, int m,
           double* part, Ctl* ctl) {
     if (ctl->done) return;
     __shared__ T h1s[NV];
@@ -183,6 +186,7 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n
         for (int k = 0; k < NV; ++k)
             if (k < nv) acc_t[1 + k] += dotv(vk[k], wp);
         acc_t[0] += dotv(wp, wp);
+        reinterpret_cast<VT*>(w)[i] = wp;
     }
     for (size_t i = nvec * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
         T wp = w[i];
@@ -193,6 +197,7 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n
         for (int k = 0; k < NV; ++k)
             if (k < nv) acc_t[1 + k] += V[k * ldv + i] * wp;
         acc_t[0] += wp * wp;
+        w[i] = wp;
     }
     double acc[NV + 1];
 #pragma unroll
@@ -213,7 +218,7 @@ arnoldi_c(T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int 
     using VT = typename V4<T>::type;
     constexpr int W = V4<T>::W;
     __shared__ T hs[NV];
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = T(ctl->hsum[k]);
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = T(ctl->h2[k]);
     __syncthreads();
     const T inv = T(ctl->inv_hn);
     const size_t nvec = n / W;
@@ -404,7 +409,7 @@ cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int n
 }
 
 template <typename T>
-cudaError_t launch_arnoldi_b(const T* V, size_t ldv, const T* w, size_t n, int nv, int m,
+cudaError_t launch_arnoldi_b(const T* V, size_t ldv, T* w, size_t n, int nv, int m,
                              double* part, Ctl* ctl, cudaStream_t s) {
     const int nb = reduce_blocks(n / V2<T>::W);
     if (nv <= 8) arnoldi_b<T, 8><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);
@@ -480,7 +485,7 @@ cudaError_t launch_set_eps(double eps, int su, int sv, Ctl* ctl, cudaStream_t s)
 #define JF_INST(T)                                                                                     \
     template cudaError_t launch_arnoldi_a<T>(const T*, size_t, const T*, size_t, int, double*, Ctl*,  \
                                              cudaStream_t);                                            \
-    template cudaError_t launch_arnoldi_b<T>(const T*, size_t, const T*, size_t, int, int, double*,   \
+    template cudaError_t launch_arnoldi_b<T>(const T*, size_t, T*, size_t, int, int, double*,         \
                                              Ctl*, cudaStream_t);                                      \
     template cudaError_t launch_arnoldi_c<T>(T*, size_t, const T*, size_t, int, Ctl*, cudaStream_t);  \
     template cudaError_t launch_update<T>(const T*, size_t, double*, T*, size_t, double*, Ctl*,       \

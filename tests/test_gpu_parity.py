@@ -135,8 +135,7 @@ def test_jv_default_eps_rule(prec):
     V = np.random.Generator(np.random.PCG64(19)).standard_normal(U.shape)
     out = torch.empty_like(dev(U))
     e_used = s.jv(dev(U), dev(V), out, eps=0.0)
-    mach = EPS64 if prec == synth.PREC_FP64 else 2.0 ** -23
-    e_ref = m.fd_epsilon(U, m.scale(V), eps_mach=mach)
+    e_ref = m.fd_epsilon(U, m.scale(V), eps_mach=EPS64)     # same rule for both precisions
     assert e_used == pytest.approx(e_ref, rel=1e-12)
     ref = m.jv(U, m.F(U), V, e_ref)
     got = host(out)
@@ -144,10 +143,7 @@ def test_jv_default_eps_rule(prec):
         bound = 1e-12 + 50 * EPS64 * np.linalg.norm(m.scale(m.F(U))) / (e_ref * np.linalg.norm(m.scale(ref)))
         assert np.linalg.norm(m.scale(got - ref)) / np.linalg.norm(m.scale(ref)) < bound
     else:
-        # the float32 difference form is more accurate than the float64 oracle's own
-        # forward difference at this eps; compare against a float64 difference at a larger step
-        ref2 = m.jv(U, m.F(U), V, 1e-4 / np.linalg.norm(m.scale(V)))
-        assert np.linalg.norm(m.scale(got - ref2)) / np.linalg.norm(m.scale(ref2)) < 1e-4
+        assert np.all(rel_per_field(got, ref) < 1e-4), rel_per_field(got, ref)
 
 
 @pytest.mark.parametrize("grid", [(16, 8), (100, 37)])
@@ -275,6 +271,8 @@ def test_full_size_step_satisfies_trapezoid_equation():
     st = s.step(u)
     got = host(u)
     assert st["converged"], st
+    # the oracle's first step takes 3 Newton corrections (156 + 174 + 230 Krylov iterations)
+    assert st["newton_iters"] <= 4, st
     R = m.residual(got, m.rhs_f(U0))
     assert np.linalg.norm(m.scale(R)) <= st["tol"] * 1.01
     b = s.budgets(u)
