@@ -68,18 +68,21 @@ struct Ctl {
 enum CounterSlot { CNT_STENCIL = 0, CNT_PASSA, CNT_PASSB, CNT_UPDATE, CNT_RESTART, CNT_PC, CNT_EDDY, CNT_MISC };
 
 // ---------------------------------------------------------------- reductions
-// Sum NV thread-local doubles over the block and store them at
-// part[k * stride + blk] (k < nv).  Deterministic (fixed shuffle tree).
-template <int NV>
-__device__ __forceinline__ void block_partials(const double (&v)[NV], int nv, double* part,
+// Sum NV thread-local values over the block and store them, as float64, at
+// part[k * stride + blk] (k < nv).  Deterministic (fixed shuffle tree).  The
+// tree runs in the type of the thread values: float32 kernels reduce their
+// float32 partials in float32 within a block (GB300's float64 rate is a small
+// fraction of its float32 rate) and switch to float64 across blocks.
+template <int NV, typename TA>
+__device__ __forceinline__ void block_partials(const TA (&v)[NV], int nv, double* part,
                                                int stride, int blk) {
-    __shared__ double red[NV][NTHREADS / 32];
+    __shared__ TA red[NV][NTHREADS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         if (k < nv) {
-            double s = v[k];
+            TA s = v[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
             if (lane == 0) red[k][warp] = s;
@@ -88,7 +91,7 @@ __device__ __forceinline__ void block_partials(const double (&v)[NV], int nv, do
     __syncthreads();
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
         double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += red[k][w];
+        for (int w = 0; w < nw; ++w) s += (double)red[k][w];
         part[(size_t)k * stride + blk] = s;
     }
 }

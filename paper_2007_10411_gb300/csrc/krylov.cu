@@ -29,11 +29,6 @@ constexpr int PER_THREAD = 64;   // vector loads (of one basis vector) a multi-d
 template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; static constexpr int W = 4; };
 template <> struct V4<double> { using type = double2; static constexpr int W = 2; };
-// Pass B keeps every basis element it loads in registers for its second use
-// (the dot products after the axpys), so it works on scalars.
-template <typename T> struct V2;
-template <> struct V2<float> { using type = float; static constexpr int W = 1; };
-template <> struct V2<double> { using type = double; static constexpr int W = 1; };
 
 __device__ __forceinline__ float dotv(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
 __device__ __forceinline__ double dotv(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
@@ -43,12 +38,20 @@ __device__ __forceinline__ float4 axpyv(float4 y, float a, float4 x) {
 __device__ __forceinline__ double2 axpyv(double2 y, double a, double2 x) {
     return make_double2(y.x - a * x.x, y.y - a * x.y);
 }
-__device__ __forceinline__ float dotv(float a, float b) { return a * b; }
-__device__ __forceinline__ double dotv(double a, double b) { return a * b; }
-__device__ __forceinline__ float axpyv(float y, float a, float x) { return y - a * x; }
-__device__ __forceinline__ double axpyv(double y, double a, double x) { return y - a * x; }
 __device__ __forceinline__ float4 scalev(float4 x, float a) { return make_float4(a * x.x, a * x.y, a * x.z, a * x.w); }
 __device__ __forceinline__ double2 scalev(double2 x, double a) { return make_double2(a * x.x, a * x.y); }
+
+__device__ __forceinline__ float4 reload(const float4* p) {
+    float4 r;
+    asm volatile("ld.global.ca.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ double2 reload(const double2* p) {
+    double2 r;
+    asm volatile("ld.global.ca.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
+    return r;
+}
 
 static int stream_blocks(size_t n) {
     size_t b = (n + NTHREADS - 1) / NTHREADS;
@@ -87,10 +90,7 @@ arnoldi_a(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n
         for (int k = 0; k < NV; ++k)
             if (k < nv) acc_t[k] += V[k * ldv + i] * w[i];
     }
-    double acc[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = (double)acc_t[k];
-    block_partials<NV>(acc, nv, part, gridDim.x, blockIdx.x);
+    block_partials<NV, T>(acc_t, nv, part, gridDim.x, blockIdx.x);
     if (arrive_last(&ctl->counter[CNT_PASSA], gridDim.x)) {
         __shared__ double tot[NV];
         final_sums(part, gridDim.x, nv, tot);
@@ -158,7 +158,7 @@ __device__ void givens_update(Ctl* c, int j, int m, const double* h2, double wn2
 }
 
 template <typename T, int NV>
-__global__ void __launch_bounds__(NTHREADS, (sizeof(T) == 4 || NV < 32) ? 2 : 1)
+__global__ void __launch_bounds__(NTHREADS, 2)
 arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int nv, int m,
           double* part, Ctl* ctl) {
     if (ctl->done) return;
@@ -166,25 +166,22 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int 
     for (int k = threadIdx.x; k < nv; k += blockDim.x) h1s[k] = T(ctl->h1[k]);
     __syncthreads();
     // slot 0: ||w'||^2, slot 1 + k: v_k . w'
-    using VT = typename V2<T>::type;
-    constexpr int W = V2<T>::W;
+    using VT = typename V4<T>::type;
+    constexpr int W = V4<T>::W;
     T acc_t[NV + 1];
 #pragma unroll
     for (int k = 0; k <= NV; ++k) acc_t[k] = T(0);
     const size_t nvec = n / W;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvec; i += stride) {
-        VT vk[NV];
         VT wp = reinterpret_cast<const VT*>(w)[i];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
-            if (k < nv) {
-                vk[k] = reinterpret_cast<const VT*>(V + k * ldv)[i];
-                wp = axpyv(wp, h1s[k], vk[k]);
-            }
+            if (k < nv) wp = axpyv(wp, h1s[k], reinterpret_cast<const VT*>(V + k * ldv)[i]);
+        // second use of v_k: re-read (L1 / L2 hit) instead of holding NV vectors in registers
 #pragma unroll
         for (int k = 0; k < NV; ++k)
-            if (k < nv) acc_t[1 + k] += dotv(vk[k], wp);
+            if (k < nv) acc_t[1 + k] += dotv(reload(reinterpret_cast<const VT*>(V + k * ldv) + i), wp);
         acc_t[0] += dotv(wp, wp);
         reinterpret_cast<VT*>(w)[i] = wp;
     }
@@ -199,10 +196,7 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int 
         acc_t[0] += wp * wp;
         w[i] = wp;
     }
-    double acc[NV + 1];
-#pragma unroll
-    for (int k = 0; k <= NV; ++k) acc[k] = (double)acc_t[k];
-    block_partials<NV + 1>(acc, nv + 1, part, gridDim.x, blockIdx.x);
+    block_partials<NV + 1, T>(acc_t, nv + 1, part, gridDim.x, blockIdx.x);
     if (arrive_last(&ctl->counter[CNT_PASSB], gridDim.x)) {
         __shared__ double tot[NV + 1];
         final_sums(part, gridDim.x, nv + 1, tot);
@@ -239,29 +233,60 @@ arnoldi_c(T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int 
 }
 
 // ---------------------------------------------------------------- update
-// x += sum_{k < K} y_k z_k (float64); xT = x rounded to T; eps_jv for J x.
+// x += sum_{k < K} y_k z_k, xT = x rounded to T, eps_jv for J x.
+// The directions z_k enter exactly and their combination carries no extra
+// rounding: float64 basis -> float64 FMAs; float32 basis -> a double-float
+// (hi + lo float32 pair) sum with error-free products and TwoSum additions
+// (Dekker 1971; Knuth TAOCP vol. 2), ~2^-44 relative, then one float64 add.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
 template <typename T, int NV>
 __global__ void __launch_bounds__(NTHREADS)
 update_x(const T* __restrict__ Z, size_t ldz, double* __restrict__ x, T* __restrict__ xT, size_t n,
          double* part, Ctl* ctl) {
     const int K = ctl->k;
     __shared__ double ys[NV];
-    for (int k = threadIdx.x; k < NV; k += blockDim.x) ys[k] = k < K ? ctl->y[k] : 0.0;
+    __shared__ float yh[NV], yl[NV];
+    for (int k = threadIdx.x; k < NV; k += blockDim.x) {
+        const double y = k < K ? ctl->y[k] : 0.0;
+        ys[k] = y;
+        yh[k] = (float)y;
+        yl[k] = (float)(y - (double)(float)y);
+    }
     __syncthreads();
-    double acc[1] = {0.0};
+    T acc[1] = {T(0)};
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        // the basis-precision directions enter exactly; their combination is
-        // formed in float64 so the Newton update carries no extra rounding
-        double s = x[i];
+        double s;
+        if (sizeof(T) == sizeof(double)) {
+            s = x[i];
 #pragma unroll
-        for (int k = 0; k < NV; ++k)
-            if (k < K) s += ys[k] * (double)Z[k * ldz + i];
+            for (int k = 0; k < NV; ++k)
+                if (k < K) s += ys[k] * (double)Z[k * ldz + i];
+        } else {
+            float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                if (k < K) {
+                    const float z = (float)Z[k * ldz + i];
+                    const float ph = yh[k] * z;
+                    const float pl = fmaf(yh[k], z, -ph);      // exact product error
+                    float t, e;
+                    two_sum(hi, ph, t, e);
+                    hi = t;
+                    lo += e + pl + yl[k] * z;
+                }
+            s = x[i] + ((double)hi + (double)lo);
+        }
         x[i] = s;
         if (xT != nullptr) xT[i] = T(s);
-        acc[0] += s * s;
+        acc[0] += T(s) * T(s);
     }
-    block_partials<1>(acc, 1, part, gridDim.x, blockIdx.x);
+    block_partials<1, T>(acc, 1, part, gridDim.x, blockIdx.x);
     if (arrive_last(&ctl->counter[CNT_UPDATE], gridDim.x)) {
         __shared__ double tot[1];
         final_sums(part, gridDim.x, 1, tot);
@@ -411,7 +436,7 @@ cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int n
 template <typename T>
 cudaError_t launch_arnoldi_b(const T* V, size_t ldv, T* w, size_t n, int nv, int m,
                              double* part, Ctl* ctl, cudaStream_t s) {
-    const int nb = reduce_blocks(n / V2<T>::W);
+    const int nb = reduce_blocks(n / V4<T>::W);
     if (nv <= 8) arnoldi_b<T, 8><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);
     else if (nv <= 16) arnoldi_b<T, 16><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);
     else arnoldi_b<T, 32><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);

@@ -68,15 +68,75 @@ __device__ __forceinline__ int mirror_z(int gz, int nz, int& side) {
 }
 
 __device__ __forceinline__ int wrap_x(int gx, int nx) {
+    if ((unsigned)gx < (unsigned)nx) return gx;        // interior: no division
     int r = gx % nx;
     return r < 0 ? r + nx : r;
 }
 
-// Stage 1: s[f][SZ][SX] <- (LOADMODE 0) u, (1) u + ev*v, (2) ev*v, ghost-extended.
-template <typename T, int LOADMODE>
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    using type = float4;
+    static constexpr int W = 4;
+    __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static float4 fma(float a, float4 x, float4 y) {
+        return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+    }
+    __device__ static float4 mul(float a, float4 x) { return make_float4(a * x.x, a * x.y, a * x.z, a * x.w); }
+};
+template <> struct Vec16<double> {
+    using type = double2;
+    static constexpr int W = 2;
+    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+    __device__ static double2 fma(double a, double2 x, double2 y) {
+        return make_double2(::fma(a, x.x, y.x), ::fma(a, x.y, y.y));
+    }
+    __device__ static double2 mul(double a, double2 x) { return make_double2(a * x.x, a * x.y); }
+};
+
+// True when the whole x-range [x0 - HALO, x0 - HALO + SX) of a tile is inside the
+// grid and rows start on 16-byte boundaries: the tile rows load as 16-byte vectors.
+template <typename T>
+__device__ __forceinline__ bool rows_vectorisable(const Geo& G, int x0, int SX) {
+    return x0 - HALO >= 0 && x0 - HALO + SX <= G.nx && (G.nx % Vec16<T>::W) == 0;
+}
+
+// Stage 1: s[f][SZ][SX] <- (LOADMODE 0) u, (1) u + ev*v, (2) ev*v for fields
+// f0 .. f0+NF-1, ghost-extended (periodic x, signed mirror z).
+template <typename T, int LOADMODE, int NF = 4>
 __device__ __forceinline__ void load_fields(T* s, const T* __restrict__ u, const T* __restrict__ v,
                                             const T (&ev)[4], const Geo& G, int x0, int z0,
-                                            int SX, int SZ) {
+                                            int SX, int SZ, int f0 = 0) {
+    using VT = typename Vec16<T>::type;
+    constexpr int VW = Vec16<T>::W;
+    if (rows_vectorisable<T>(G, x0, SX)) {
+        const int nch = SX / VW;
+        const int total = nch * SZ;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int iz = idx / nch, c = idx - iz * nch;
+            const int gz = z0 + iz - HALO;
+            int side;
+            const int sz = mirror_z(gz, G.nz, side);
+            const bool ok = sz >= 0 && sz < G.nz;
+            const size_t off = (size_t)sz * G.nx + (x0 - HALO + c * VW);
+#pragma unroll
+            for (int q = 0; q < NF; ++q) {
+                const int f = f0 + q;
+                VT val = Vec16<T>::zero();
+                if (ok) {
+                    const size_t o = (size_t)f * G.npt + off;
+                    if (LOADMODE == 0) val = *reinterpret_cast<const VT*>(u + o);
+                    else if (LOADMODE == 1)
+                        val = Vec16<T>::fma(ev[f], *reinterpret_cast<const VT*>(v + o),
+                                            *reinterpret_cast<const VT*>(u + o));
+                    else val = Vec16<T>::mul(ev[f], *reinterpret_cast<const VT*>(v + o));
+                    if (side == 1) val = Vec16<T>::mul(T(G.pb[f]), val);
+                    else if (side == 2) val = Vec16<T>::mul(T(G.pt[f]), val);
+                }
+                *reinterpret_cast<VT*>(s + (q * SZ + iz) * SX + c * VW) = val;
+            }
+        }
+        return;
+    }
     const int total = SX * SZ;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int iz = idx / SX, ix = idx - iz * SX;
@@ -87,7 +147,8 @@ __device__ __forceinline__ void load_fields(T* s, const T* __restrict__ u, const
         const bool ok = sz >= 0 && sz < G.nz;
         const size_t off = (size_t)sz * G.nx + sx;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
+        for (int q = 0; q < NF; ++q) {
+            const int f = f0 + q;
             T val = T(0);
             if (ok) {
                 const size_t o = (size_t)f * G.npt + off;
@@ -97,7 +158,7 @@ __device__ __forceinline__ void load_fields(T* s, const T* __restrict__ u, const
                 if (side == 1) val *= T(G.pb[f]);
                 else if (side == 2) val *= T(G.pt[f]);
             }
-            s[(f * SZ + iz) * SX + ix] = val;
+            s[(q * SZ + iz) * SX + ix] = val;
         }
     }
 }
@@ -304,12 +365,12 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
     T* dK = Ka + QN;
     const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
     const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
-    __shared__ double cfs[4];            // 1 / (eps scale_f), computed once per block
+    __shared__ T cfs[4];                 // 1 / (eps scale_f), computed once per block
     __shared__ T evs[4];                 // eps scale_f
     if (threadIdx.x < 4) {
         const double e = ctl->eps_jv * G.scale[threadIdx.x];
         evs[threadIdx.x] = T(e);
-        cfs[threadIdx.x] = e != 0.0 ? 1.0 / e : 0.0;
+        cfs[threadIdx.x] = T(e != 0.0 ? 1.0 / e : 0.0);
     }
     __syncthreads();
     T ev[4];
@@ -426,8 +487,9 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
 #pragma unroll
         for (int fl = 0; fl < 4; ++fl) {
             const size_t o = (size_t)fl * G.npt + off;
-            const double vh = (double)v[o];
-            out[o] = T(G.two_over_dt * vh - (double)dF[fl] * cfs[fl]);
+            // the difference dF is already free of cancellation: the quotient
+            // and the 2 v/dt term need no wider type than the result
+            out[o] = T(G.two_over_dt) * v[o] - dF[fl] * cfs[fl];
         }
     }
 }
@@ -518,91 +580,83 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
     constexpr int QX = TX + 2 * R, QZ = TZ + 2 * R;
     constexpr int QN = QX * QZ;
     if (check_done && ctl->done) return;
-    __shared__ T sz_[SZ * SX];
-    __shared__ T gx_[QN];
-    __shared__ T gz_[QN];
-    __shared__ T kk_[SMAG ? QN : 1];
-    const int fld = blockIdx.z;                 // 0 u, 1 w, 2 theta, 3 p
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* zs = reinterpret_cast<T*>(smem_raw);      // [SZ][SX] current iterate, halo 2r
+    T* gx_ = zs + SZ * SX;                          // [QN] D_x z on the halo-r region
+    T* gz_ = gx_ + QN;                              // [QN] D_z z
+    T* kk_ = gz_ + QN;                              // [QN] eddy coefficient (Smagorinsky)
+    const int fld = blockIdx.z;                     // 0 u, 1 w, 2 theta, 3 p (last sweep only)
     const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
-    const T c_ith = T(ctl->cheb[fld][k][0]);
-    const T c_a1 = T(ctl->cheb[fld][k][1]);
-    const T c_a2 = T(ctl->cheb[fld][k][2]);
+    const T ith = T(ctl->cheb[fld][k][0]);
+    const T a1 = T(ctl->cheb[fld][k][1]);
+    const T a2 = T(ctl->cheb[fld][k][2]);
     const size_t foff = (size_t)fld * G.npt;
-    double acc[1] = {0.0};
+    T acc[1] = {T(0)};
     if (fld == 3) {
-        // p block: (2/dt) I, exact in one step; written by the last sweep only
-        if (LAST) {
+        if (LAST) {          // p block: (2/dt) I, exact in one step
             for (int idx = threadIdx.x; idx < TX * TZ; idx += blockDim.x) {
                 const int tz = idx / TX, tx = idx - tz * TX;
-                const int gz = z0 + tz, gx = x0 + tx;
-                if (gz >= G.nz || gx >= G.nx) continue;
-                const size_t o = foff + (size_t)gz * G.nx + gx;
-                const T zv = r[o] * c_ith;
+                const int gz = z0 + tz, gxx = x0 + tx;
+                if (gz >= G.nz || gxx >= G.nx) continue;
+                const size_t o = foff + (size_t)gz * G.nx + gxx;
+                const T zv = r[o] * ith;
                 zout[o] = zv;
-                acc[0] += (double)zv * (double)zv;
+                acc[0] += zv * zv;
             }
         }
     } else {
-        const T ith = c_ith;
-        // x_k with halo 2r (x_1 = r / theta)
-        for (int idx = threadIdx.x; idx < SZ * SX; idx += blockDim.x) {
-            const int iz = idx / SX, ix = idx - iz * SX;
-            const int gz = z0 + iz - HALO, gx = x0 + ix - HALO;
-            int side;
-            const int szr = mirror_z(gz, G.nz, side);
-            const int sxr = wrap_x(gx, G.nx);
-            T val = T(0);
-            if (szr >= 0 && szr < G.nz) {
-                const size_t o = foff + (size_t)szr * G.nx + sxr;
-                val = FIRST ? r[o] * ith : zin[o];
-                if (side == 1) val *= T(G.pb[fld]);
-                else if (side == 2) val *= T(G.pt[fld]);
+        // x_k with halo 2r (first sweep: x_1 = r / theta_c)
+        T sc[4] = {T(0), T(0), T(0), T(0)};
+        if (FIRST) {
+            sc[fld] = ith;
+            load_fields<T, 2, 1>(zs, nullptr, r, sc, G, x0, z0, SX, SZ, fld);
+        } else {
+            load_fields<T, 0, 1>(zs, zin, nullptr, sc, G, x0, z0, SX, SZ, fld);
+        }
+        if (SMAG) {
+            for (int idx = threadIdx.x; idx < QN; idx += blockDim.x) {
+                const int qz = idx / QX, qx = idx - qz * QX;
+                int side;
+                const int szr = mirror_z(z0 + qz - R, G.nz, side);
+                const int sxr = wrap_x(x0 + qx - R, G.nx);
+                const T kv = (szr >= 0 && szr < G.nz) ? nu[(size_t)szr * G.nx + sxr] : T(0);
+                kk_[idx] = fld == 2 ? kv * T(G.inv_Pr) : kv;
             }
-            sz_[idx] = val;
         }
         __syncthreads();
         const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
         for (int idx = threadIdx.x; idx < QN; idx += blockDim.x) {
             const int qz = idx / QX, qx = idx - qz * QX;
             const int i1 = (qz + R) * SX + qx + R;
-            gx_[idx] = dd(sz_, i1, 1, idx_);
-            gz_[idx] = dd(sz_, i1, SX, idz_);
-            if (SMAG) {
-                const int gzz = z0 + qz - R;
-                int side;
-                const int szr = mirror_z(gzz, G.nz, side);
-                const int sxr = wrap_x(x0 + qx - R, G.nx);
-                T kv = T(0);
-                if (szr >= 0 && szr < G.nz) kv = nu[(size_t)szr * G.nx + sxr];
-                kk_[idx] = fld == 2 ? kv * T(G.inv_Pr) : kv;
-            }
+            gx_[idx] = dd(zs, i1, 1, idx_);
+            gz_[idx] = dd(zs, i1, SX, idz_);
         }
         __syncthreads();
         const T Kc = T(fld == 2 ? G.K_H : G.K_M);
         const T tdt = T(G.two_over_dt);
         for (int idx = threadIdx.x; idx < TX * TZ; idx += blockDim.x) {
             const int tz = idx / TX, tx = idx - tz * TX;
-            const int gz = z0 + tz, gx = x0 + tx;
-            if (gz >= G.nz || gx >= G.nx) continue;
+            const int gz = z0 + tz, gxx = x0 + tx;
+            if (gz >= G.nz || gxx >= G.nx) continue;
             const int i1 = (tz + HALO) * SX + tx + HALO;
             const int q = (tz + R) * QX + tx + R;
-            T dif = ddk<T, SMAG>(kk_, Kc, gx_, q, 1, idx_) + ddk<T, SMAG>(kk_, Kc, gz_, q, QX, idz_);
-            const T xk = sz_[i1];
-            const size_t o = foff + (size_t)gz * G.nx + gx;
+            const T dif = ddk<T, SMAG>(kk_, Kc, gx_, q, 1, idx_) + ddk<T, SMAG>(kk_, Kc, gz_, q, QX, idz_);
+            const T xk = zs[i1];
+            const size_t o = foff + (size_t)gz * G.nx + gxx;
             const T rv = r[o];
             const T res = rv - (tdt * xk - dif);
             const T dprev = FIRST ? rv * ith : din[o];
-            const T dk = c_a1 * dprev + c_a2 * res;
+            const T dk = a1 * dprev + a2 * res;
             const T xn = xk + dk;
             zout[o] = xn;
             if (!LAST) dout[o] = dk;
-            if (LAST) acc[0] += (double)xn * (double)xn;
+            if (LAST) acc[0] += xn * xn;
         }
     }
     if (LAST) {
         const int nblk = gridDim.x * gridDim.y * gridDim.z;
         const int blk = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        block_partials<1>(acc, 1, part, nblk, blk);
+        block_partials<1, T>(acc, 1, part, nblk, blk);
         if (arrive_last(&ctl->counter[CNT_PC], nblk)) {
             __shared__ double tot[1];
             final_sums(part, nblk, 1, tot);
@@ -620,16 +674,16 @@ __global__ void __launch_bounds__(NTHREADS)
 pc_diag(Geo G, const T* __restrict__ r, T* __restrict__ z, size_t n, double* part, Ctl* ctl,
         int check_done) {
     if (check_done && ctl->done) return;
-    double acc[1] = {0.0};
+    T acc[1] = {T(0)};
     T inv_th[4];
     for (int f = 0; f < 4; ++f) inv_th[f] = T(ctl->cheb[f][0][0]);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int f = (int)(i / G.npt);
         const T zv = r[i] * inv_th[f];
         z[i] = zv;
-        acc[0] += (double)zv * (double)zv;
+        acc[0] += zv * zv;
     }
-    block_partials<1>(acc, 1, part, gridDim.x, blockIdx.x);
+    block_partials<1, T>(acc, 1, part, gridDim.x, blockIdx.x);
     if (arrive_last(&ctl->counter[CNT_PC], gridDim.x)) {
         __shared__ double tot[1];
         final_sums(part, gridDim.x, 1, tot);
@@ -801,6 +855,17 @@ static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, 
         return cudaGetLastError();
     }
     dim3 grid((G.nx + Tile<T>::TX - 1) / Tile<T>::TX, (G.nz + Tile<T>::TZ - 1) / Tile<T>::TZ, 3);
+    constexpr int TX = Tile<T>::TX, TZ = Tile<T>::TZ;
+    const size_t sm = sizeof(T) * ((TZ + 2 * HALO) * (TX + 2 * HALO) + 3 * (TX + 2 * R) * (TZ + 2 * R));
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e;
+        if ((e = set_smem(cheb2d<T, SMAG, 1, 1>, sm)) != cudaSuccess) return e;
+        if ((e = set_smem(cheb2d<T, SMAG, 1, 0>, sm)) != cudaSuccess) return e;
+        if ((e = set_smem(cheb2d<T, SMAG, 0, 1>, sm)) != cudaSuccess) return e;
+        if ((e = set_smem(cheb2d<T, SMAG, 0, 0>, sm)) != cudaSuccess) return e;
+        configured = true;
+    }
     const T* zin = nullptr;
     const T* din = nullptr;
     T* zbuf[2] = {za, zb};
@@ -811,13 +876,13 @@ static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, 
         T* dO = dbuf[k & 1];
         grid.z = last ? 4 : 3;            // the p block is written by the last sweep only
         if (first && last)
-            cheb2d<T, SMAG, 1, 1><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            cheb2d<T, SMAG, 1, 1><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else if (first)
-            cheb2d<T, SMAG, 1, 0><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            cheb2d<T, SMAG, 1, 0><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else if (last)
-            cheb2d<T, SMAG, 0, 1><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            cheb2d<T, SMAG, 0, 1><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else
-            cheb2d<T, SMAG, 0, 0><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            cheb2d<T, SMAG, 0, 0><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         if (launches) ++*launches;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
