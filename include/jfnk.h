@@ -223,6 +223,37 @@ jfnk_status jfnk_kernel_timing(jfnk_handle* h, unsigned int mask);
  * accumulators of all JFNK_KF_COUNT families into out[0 .. JFNK_KF_COUNT). */
 jfnk_status jfnk_kernel_timing_read(jfnk_handle* h, jfnk_kernel_time* out);
 
+/* Largest grid (nx * nz points) accepted by jfnk_budgets_static. */
+#define JFNK_BUDGETS_STATIC_MAX_POINTS 8388608
+
+/* Budgets without a handle and without any device allocation.
+ *
+ * For callers that cannot call cudaMalloc: code that runs where device
+ * allocation is not allowed (for example inside a stream capture that must
+ * not allocate, under an allocator that owns all device memory, or in a
+ * service with a fixed memory budget) cannot create a handle, because
+ * jfnk_create allocates workspace.  This entry point computes the same
+ * values as jfnk_budgets from a 2-D grid description alone.  The paper has
+ * no counterpart; it is a deployment variant.
+ *
+ * u:   device float64 state [4][nz][nx] (2-D only; 3-D is JFNK_ERR_UNSUPPORTED).
+ * out: device float64 array of 12 values, written by the last kernel block:
+ *      E_k, E_p, sum theta dV, sum div(u) dV, max(u, w, theta, p), min(u, w, theta, p).
+ * Grids above JFNK_BUDGETS_STATIC_MAX_POINTS are rejected with
+ * JFNK_ERR_INVALID_ARG before anything is enqueued.
+ * Scratch: a file-scope device array of about 393 KB (one float64 partial per
+ * kernel block and value, plus a counter) that every GPU which loads the
+ * library holds until the process exits.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.
+ * The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls on a device share the array and it
+ * keeps the last call's contents (the counter is reset by every call);
+ * calls that overlap on the GPU (different streams without ordering) race.
+ * Asynchronous on cuda_stream (a cudaStream_t, NULL = legacy default stream). */
+jfnk_status jfnk_budgets_static(const jfnk_grid* grid, const double* u, double* out,
+                                void* cuda_stream);
+
 /* Static description of a status code. */
 const char* jfnk_status_str(jfnk_status s);
 

@@ -28,6 +28,7 @@ EXPORTS = (
     "jfnk_create", "jfnk_destroy", "jfnk_set_surface_flux", "jfnk_rhs", "jfnk_residual",
     "jfnk_jv", "jfnk_precond_apply", "jfnk_step", "jfnk_step_host", "jfnk_budgets",
     "jfnk_get_launch_count", "jfnk_status_str", "jfnk_kernel_timing", "jfnk_kernel_timing_read",
+    "jfnk_budgets_static",
 )
 
 KERNEL_FAMILIES = ("arnoldi_a", "arnoldi_b", "arnoldi_c", "jv", "precond", "residual")
@@ -107,6 +108,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.jfnk_get_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
     lib.jfnk_kernel_timing.argtypes = [P, ctypes.c_uint]
     lib.jfnk_kernel_timing_read.argtypes = [P, ctypes.POINTER(KernelTime)]
+    lib.jfnk_budgets_static.argtypes = [ctypes.POINTER(Grid), P, P, P]
     lib.jfnk_status_str.argtypes = [I]
     lib.jfnk_status_str.restype = ctypes.c_char_p
     for name in EXPORTS:
