@@ -137,6 +137,22 @@ def ncu_traffic() -> dict:
     return out
 
 
+# ---------------------------------------------------------------- multi-rank
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Largest value over all ranks of the default process group (the slowest rank's time)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(points: int, steps: int, world: int, slowest_ms: float) -> float:
+    """Whole-job Mpt*steps/s: every rank steps its own replica; time = slowest rank."""
+    return points * steps * world / (slowest_ms / 1e3) / 1e6
+
+
 # ---------------------------------------------------------------- oracle sample
 def oracle_sample(case: dict, seconds: float, iters_per_step: float, newton_per_step: float):
     """Time the float64 oracle on a bounded sample of one step of the workload.
@@ -241,12 +257,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(v: float) -> float:
+        return max_over_ranks(v, dist, "cuda")
 
     case = synth.case(args.workload)
     npt = case["grid"]["nx"] * case["grid"]["nz"]
@@ -274,10 +286,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     clk = clocks.stop()
     launches = solver.launch_count() - launches0
     ms = e0.elapsed_time(e1)
-    ms = max_over_ranks(ms)
+    ms = slowest(ms)
     kt = solver.kernel_timing_read() if not args.no_kernel_timing else None
     solver.kernel_timing(())
-    value = npt * args.steps * world / (ms / 1e3) / 1e6
+    value = job_throughput(npt, args.steps, world, ms)
 
     # end to end through the public API with host buffers (pinned), copies in the timed region
     e2e = None
@@ -289,7 +301,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         for _ in range(args.e2e_steps):
             solver.step_host(uh)
         barrier()
-        el = max_over_ranks(time.perf_counter() - t0)
+        el = slowest(time.perf_counter() - t0)
         e2e = {"value": npt * args.e2e_steps * world / el / 1e6, "unit": "Mpt*steps/s",
                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
 
@@ -307,7 +319,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         st64 = [s64.step(u64) for _ in range(args.fp64_steps)]
         a1.record(stream)
         a1.synchronize()
-        ms64 = max_over_ranks(a0.elapsed_time(a1))
+        ms64 = slowest(a0.elapsed_time(a1))
         fp64 = {"value": npt * args.fp64_steps * world / (ms64 / 1e3) / 1e6,
                 "ms_per_step": ms64 / args.fp64_steps,
                 "gmres_iters_per_step": statistics.mean(s["gmres_iters"] for s in st64),
