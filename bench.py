@@ -269,6 +269,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     u = torch.from_numpy(U0).cuda()
     for _ in range(args.warmup):
         solver.step(u)
+    tiles = solver.autotune(u)              # set-up, outside the timed region
     if not args.no_kernel_timing:
         solver.kernel_timing()
     stats = []
@@ -364,6 +365,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                    "points": npt, "precision": "mixed", "krylov_m": case["opts"]["krylov_m"],
                    "precond": "field-block Chebyshev (%d sweeps)" % case["opts"]["pc_sweeps"],
                    "parallelism": "replicas" if world > 1 else "single",
+                   "tiles": {"jv": tiles[0], "precond": tiles[1]},
                    "l2": "working set > L2: the Krylov basis and directions (%d x %.1f MB) stream "
                          "through L2 every Arnoldi pass" % (2 * case["opts"]["krylov_m"] + 1, n * 4 / 1e6)},
         "newton_per_step": newt, "gmres_iters_per_step": iters,

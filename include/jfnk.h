@@ -223,6 +223,20 @@ jfnk_status jfnk_kernel_timing(jfnk_handle* h, unsigned int mask);
  * accumulators of all JFNK_KF_COUNT families into out[0 .. JFNK_KF_COUNT). */
 jfnk_status jfnk_kernel_timing_read(jfnk_handle* h, jfnk_kernel_time* out);
 
+/* Number of tile shapes jfnk_set_tiles accepts per kernel family. */
+#define JFNK_NUM_TILE_SHAPES 4
+
+/* Choose the tile shapes of the float32 Jacobian-product and preconditioner
+ * stencils for this handle's grid: every candidate is timed on the handle's
+ * stream with inputs derived from the device state u (unchanged), and the
+ * fastest is kept.  tiles (host, may be NULL) receives {jv, pc} indices.
+ * Synchronises the stream; results of the kernels are unaffected (every
+ * shape computes the same values).  A float64 handle keeps its single shape. */
+jfnk_status jfnk_autotune(jfnk_handle* h, const double* u, int* tiles);
+
+/* Set the tile-shape indices (0 .. JFNK_NUM_TILE_SHAPES-1) directly. */
+jfnk_status jfnk_set_tiles(jfnk_handle* h, int tile_jv, int tile_pc);
+
 /* Largest grid (nx * nz points) accepted by jfnk_budgets_static. */
 #define JFNK_BUDGETS_STATIC_MAX_POINTS 8388608
 

@@ -31,7 +31,10 @@ struct Geo {
     double two_over_dt;
     double scale[5], inv_scale[5];
     const double* heat;               // surface flux H(x) or nullptr
+    int tile_jv, tile_pc;             // tile shapes of the float32 Jv / preconditioner kernels
 };
+
+constexpr int NUM_TILE_SHAPES = 4;
 
 // Solver control block in device memory.  Written by the "last block" of the
 // reduction kernels, read by later kernels and, after a stream sync, by the host.
@@ -134,31 +137,67 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int 
     return am_last;
 }
 
-// In the last block: out[k] = sum over blocks of part[k * nblk + b], fixed order.
-__device__ __forceinline__ void final_sums(const double* part, int nblk, int nv, double* out) {
+// In the last block: out[k] = sum over blocks of part[k * nblk + b], in a fixed
+// order (deterministic).  Loads are issued four at a time into independent
+// accumulators so that a lane never waits on one L2 round trip per partial;
+// a single value is reduced by the whole block, several values warp by warp.
+template <bool MAXOP>
+__device__ __forceinline__ double combine(double a, double b) { return MAXOP ? fmax(a, b) : a + b; }
+
+template <bool MAXOP>
+__device__ __forceinline__ double strided_reduce(const double* p, int n, int start, int stride) {
+    const double id = MAXOP ? -1.0e300 : 0.0;
+    double s0 = id, s1 = id, s2 = id, s3 = id;
+    int b = start;
+    for (; b + 3 * stride < n; b += 4 * stride) {
+        const double v0 = __ldcg(p + b), v1 = __ldcg(p + b + stride);
+        const double v2 = __ldcg(p + b + 2 * stride), v3 = __ldcg(p + b + 3 * stride);
+        s0 = combine<MAXOP>(s0, v0);
+        s1 = combine<MAXOP>(s1, v1);
+        s2 = combine<MAXOP>(s2, v2);
+        s3 = combine<MAXOP>(s3, v3);
+    }
+    for (; b < n; b += stride) s0 = combine<MAXOP>(s0, __ldcg(p + b));
+    return combine<MAXOP>(combine<MAXOP>(s0, s1), combine<MAXOP>(s2, s3));
+}
+
+template <bool MAXOP>
+__device__ __forceinline__ double warp_reduce(double s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = combine<MAXOP>(s, __shfl_down_sync(0xffffffffu, s, o));
+    return s;
+}
+
+template <bool MAXOP>
+__device__ __forceinline__ void final_reduce(const double* part, int nblk, int nv, double* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
+    if (nv == 1) {
+        __shared__ double red[NTHREADS / 32];
+        const double s = warp_reduce<MAXOP>(strided_reduce<MAXOP>(part, nblk, threadIdx.x, blockDim.x));
+        if (lane == 0) red[warp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = red[0];
+            for (int w = 1; w < nw; ++w) t = combine<MAXOP>(t, red[w]);
+            out[0] = t;
+        }
+        __syncthreads();
+        return;
+    }
     for (int k = warp; k < nv; k += nw) {
-        double s = 0.0;
-        for (int b = lane; b < nblk; b += 32) s += __ldcg(part + (size_t)k * nblk + b);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        const double s = warp_reduce<MAXOP>(strided_reduce<MAXOP>(part + (size_t)k * nblk, nblk, lane, 32));
         if (lane == 0) out[k] = s;
     }
     __syncthreads();
 }
 
+__device__ __forceinline__ void final_sums(const double* part, int nblk, int nv, double* out) {
+    final_reduce<false>(part, nblk, nv, out);
+}
+
 __device__ __forceinline__ void final_maxes(const double* part, int nblk, int nv, double* out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    for (int k = warp; k < nv; k += nw) {
-        double s = -1.0e300;
-        for (int b = lane; b < nblk; b += 32) s = fmax(s, __ldcg(part + (size_t)k * nblk + b));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
-        if (lane == 0) out[k] = s;
-    }
-    __syncthreads();
+    final_reduce<true>(part, nblk, nv, out);
 }
 
 }  // namespace jfnk

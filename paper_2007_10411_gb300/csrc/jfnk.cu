@@ -174,9 +174,9 @@ static double pc_bytes(const jfnk_handle* h) {
     return b + 2.0 * P;
 }
 
-template <typename T>
+// Blocks of the largest stencil grid any tile candidate can launch (4 field slices).
 static int stencil_part_blocks(const Geo& G) {
-    return stencil_blocks<T>(G) * 4;
+    return ((G.nx + 15) / 16) * ((G.nz + 7) / 8) * 4;
 }
 
 // ------------------------------------------------------------------ create
@@ -230,14 +230,15 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     const double sc[4] = {opts->scale_u, opts->scale_u, opts->scale_theta, opts->scale_p};
     for (int f = 0; f < 4; ++f) { G.scale[f] = sc[f]; G.inv_scale[f] = 1.0 / sc[f]; }
     G.heat = nullptr;
+    G.tile_jv = 0;
+    G.tile_pc = 0;
 
     const size_t eT = h->mixed ? sizeof(float) : sizeof(double);
     const size_t nb8 = h->ld * sizeof(double);
     const size_t nbT = h->ld * eT;
     const int m = h->m;
     int maxblk = MAX_STREAM_BLOCKS;
-    maxblk = std::max(maxblk, stencil_part_blocks<double>(G));
-    maxblk = std::max(maxblk, stencil_part_blocks<float>(G));
+    maxblk = std::max(maxblk, stencil_part_blocks(G));
     {   // multi-dot grids: up to n / (4 * NTHREADS * 64) CTAs
         const size_t rb = h->n / ((size_t)NTHREADS * 64) + 1;
         maxblk = std::max(maxblk, (int)std::min(rb, (size_t)MAX_REDUCE_BLOCKS));
@@ -350,6 +351,80 @@ extern "C" jfnk_status jfnk_kernel_timing_read(jfnk_handle* h, jfnk_kernel_time*
     if (!h || !out) return JFNK_ERR_INVALID_ARG;
     kt_drain(h);
     memcpy(out, h->kt_acc, sizeof(h->kt_acc));
+    return JFNK_OK;
+}
+
+// Time every tile candidate of the float32 Jacobian-product and preconditioner
+// kernels on this handle's grid (inputs: u and a direction built from it) and
+// keep the fastest; tiles[0..1] (may be NULL) receive the chosen indices.
+template <typename T>
+static jfnk_status autotune_impl(jfnk_handle* h, const double* u, int* tiles) {
+    cudaStream_t s = h->stream;
+    Geo& G = h->G;
+    T* uT = (T*)h->uT;
+    T* dir = (T*)h->tA;
+    CK((launch_convert<double, T>(u, uT, h->n, s)));
+    CK((launch_rescale<double, T>(G, u, dir, h->n, 0, s)));
+    CK(launch_norm2<double>(G, u, h->n, 1, 2, h->part, h->ctl, s));
+    CK(launch_set_eps(1e-6, 2, 3, h->ctl, s));
+    CK(launch_norm2<double>(G, u, h->n, 1, 2, h->part, h->ctl, s));
+    if (G.smag) CK(launch_eddy<T>(G, uT, (T*)h->nu, h->part, h->ctl, s));
+    CK(launch_pc_setup(G, h->opts.pc_sweeps, h->ctl, s));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int reps = 8;
+    float best_jv = 1e30f, best_pc = 1e30f;
+    int arg_jv = 0, arg_pc = 0;
+    for (int c = 0; c < NUM_TILE_SHAPES; ++c) {
+        G.tile_jv = c;
+        G.tile_pc = c;
+        for (int pass = 0; pass < 2; ++pass) {          // pass 0 warms up (and sets shared-memory limits)
+            CK(cudaEventRecord(e0, s));
+            for (int r = 0; r < reps; ++r) CK(launch_jv_diff<T>(G, uT, dir, (T*)h->w, h->part, h->ctl, 0, s));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (pass == 1 && ms < best_jv) { best_jv = ms; arg_jv = c; }
+        }
+        if (h->opts.precond == JFNK_PC_BLOCK && h->opts.pc_sweeps > 1) {
+            for (int pass = 0; pass < 2; ++pass) {
+                CK(cudaEventRecord(e0, s));
+                for (int r = 0; r < reps; ++r)
+                    CK(launch_precond<T>(G, h->opts.pc_sweeps, dir, (T*)h->tB, (T*)h->za, (T*)h->zb,
+                                         (T*)h->da, (T*)h->db, (const T*)h->nu, h->part, h->ctl, 0, s,
+                                         nullptr));
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (pass == 1 && ms < best_pc) { best_pc = ms; arg_pc = c; }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    G.tile_jv = arg_jv;
+    G.tile_pc = arg_pc;
+    if (tiles) { tiles[0] = arg_jv; tiles[1] = arg_pc; }
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_autotune(jfnk_handle* h, const double* u, int* tiles) {
+    if (!h || !u) return JFNK_ERR_INVALID_ARG;
+    if (!h->mixed) {                       // the float64 kernels have a single tile shape
+        if (tiles) { tiles[0] = h->G.tile_jv; tiles[1] = h->G.tile_pc; }
+        return JFNK_OK;
+    }
+    return autotune_impl<float>(h, u, tiles);
+}
+
+extern "C" jfnk_status jfnk_set_tiles(jfnk_handle* h, int tile_jv, int tile_pc) {
+    if (!h || tile_jv < 0 || tile_jv >= NUM_TILE_SHAPES || tile_pc < 0 || tile_pc >= NUM_TILE_SHAPES)
+        return JFNK_ERR_INVALID_ARG;
+    h->G.tile_jv = tile_jv;
+    h->G.tile_pc = tile_pc;
     return JFNK_OK;
 }
 

@@ -35,10 +35,19 @@ constexpr int HALO = 2 * R;   // input halo (derivative applied twice)
 template <typename T> struct Tile;
 template <> struct Tile<double> { static constexpr int TX = 32, TZ = 16; };
 template <> struct Tile<float>  { static constexpr int TX = 64, TZ = 16; };
-// The difference-form Jacobian product stages two states: smaller tiles.
-template <typename T> struct TileD;
-template <> struct TileD<double> { static constexpr int TX = 32, TZ = 8; };
-template <> struct TileD<float>  { static constexpr int TX = 32, TZ = 16; };
+// Candidate tiles of the Jacobian-product and preconditioner kernels (float32
+// path); jfnk_autotune times each on the handle's workload and keeps the
+// fastest (Geo::tile_jv, Geo::tile_pc).  The float64 path uses the first entry.
+template <int I> struct JvTile;
+template <> struct JvTile<0> { static constexpr int TX = 32, TZ = 16; };
+template <> struct JvTile<1> { static constexpr int TX = 32, TZ = 8; };
+template <> struct JvTile<2> { static constexpr int TX = 64, TZ = 8; };
+template <> struct JvTile<3> { static constexpr int TX = 16, TZ = 16; };
+template <int I> struct PcTile;
+template <> struct PcTile<0> { static constexpr int TX = 64, TZ = 16; };
+template <> struct PcTile<1> { static constexpr int TX = 32, TZ = 16; };
+template <> struct PcTile<2> { static constexpr int TX = 64, TZ = 8; };
+template <> struct PcTile<3> { static constexpr int TX = 32, TZ = 8; };
 
 template <typename T>
 __device__ __forceinline__ T dd(const T* s, int i, int st, T inv_h) {
@@ -347,11 +356,10 @@ stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
 // so the float32 result carries float32 relative accuracy on the difference
 // itself instead of on F.  Same quantity as the forward difference of Eq. fd.
 // ============================================================================
-template <typename T, int SMAG>
+template <typename T, int SMAG, int TX, int TZ>
 __global__ void __launch_bounds__(NTHREADS)
 jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict__ out,
           Ctl* ctl, int check_done) {
-    constexpr int TX = TileD<T>::TX, TZ = TileD<T>::TZ;
     constexpr int SX = TX + 2 * HALO, SZ = TZ + 2 * HALO;
     constexpr int QX = TX + 2 * R, QZ = TZ + 2 * R;
     constexpr int QN = QX * QZ;
@@ -570,37 +578,43 @@ __global__ void pc_setup(Geo G, int sweeps, Ctl* ctl) {
     }
 }
 
-template <typename T, int SMAG, int FIRST, int LAST>
+// One CTA = one field of one TX x TZ tile; threads laid out (TX, NTHREADS/TX)
+// so that every stage indexes rows and columns without divisions.  D_x z is
+// formed only on the tile rows (x-halo r), D_z z only on the tile columns
+// (z-halo r): exactly the taps the second application of D reads.
+template <typename T, int SMAG, int FIRST, int LAST, int TX, int TZ>
 __global__ void __launch_bounds__(NTHREADS)
 cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T* __restrict__ din,
        T* __restrict__ zout, T* __restrict__ dout, const T* __restrict__ nu, double* part, Ctl* ctl,
        int check_done) {
-    constexpr int TX = Tile<T>::TX, TZ = Tile<T>::TZ;
     constexpr int SX = TX + 2 * HALO, SZ = TZ + 2 * HALO;
     constexpr int QX = TX + 2 * R, QZ = TZ + 2 * R;
-    constexpr int QN = QX * QZ;
+    constexpr int TY = NTHREADS / TX;              // thread rows
+    static_assert(NTHREADS % TX == 0 && TZ % TY == 0, "tile must tile the block");
     if (check_done && ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* zs = reinterpret_cast<T*>(smem_raw);      // [SZ][SX] current iterate, halo 2r
-    T* gx_ = zs + SZ * SX;                          // [QN] D_x z on the halo-r region
-    T* gz_ = gx_ + QN;                              // [QN] D_z z
-    T* kk_ = gz_ + QN;                              // [QN] eddy coefficient (Smagorinsky)
+    T* gxs = zs + SZ * SX;                          // [TZ][QX] D_x z on tile rows
+    T* gzs = gxs + TZ * QX;                         // [QZ][TX] D_z z on tile columns
+    T* kk_ = gzs + QZ * TX;                         // [QZ][QX] eddy coefficient (Smagorinsky)
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int fld = blockIdx.z;                     // 0 u, 1 w, 2 theta, 3 p (last sweep only)
     const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
     const T ith = T(ctl->cheb[fld][k][0]);
     const T a1 = T(ctl->cheb[fld][k][1]);
     const T a2 = T(ctl->cheb[fld][k][2]);
-    const size_t foff = (size_t)fld * G.npt;
+    const T* rf = r + (size_t)fld * G.npt;
+    T* zf = zout + (size_t)fld * G.npt;
+    const int gxx = x0 + tx;
     T acc[1] = {T(0)};
     if (fld == 3) {
-        if (LAST) {          // p block: (2/dt) I, exact in one step
-            for (int idx = threadIdx.x; idx < TX * TZ; idx += blockDim.x) {
-                const int tz = idx / TX, tx = idx - tz * TX;
-                const int gz = z0 + tz, gxx = x0 + tx;
-                if (gz >= G.nz || gxx >= G.nx) continue;
-                const size_t o = foff + (size_t)gz * G.nx + gxx;
-                const T zv = r[o] * ith;
-                zout[o] = zv;
+        if (LAST && gxx < G.nx) {          // p block: (2/dt) I, exact in one step
+            for (int tz = ty; tz < TZ; tz += TY) {
+                const int gz = z0 + tz;
+                if (gz >= G.nz) break;
+                const int o = gz * G.nx + gxx;
+                const T zv = rf[o] * ith;
+                zf[o] = zv;
                 acc[0] += zv * zv;
             }
         }
@@ -614,43 +628,57 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
             load_fields<T, 0, 1>(zs, zin, nullptr, sc, G, x0, z0, SX, SZ, fld);
         }
         if (SMAG) {
-            for (int idx = threadIdx.x; idx < QN; idx += blockDim.x) {
-                const int qz = idx / QX, qx = idx - qz * QX;
+            const T kscale = fld == 2 ? T(G.inv_Pr) : T(1);
+            for (int qz = ty; qz < QZ; qz += TY) {
                 int side;
                 const int szr = mirror_z(z0 + qz - R, G.nz, side);
-                const int sxr = wrap_x(x0 + qx - R, G.nx);
-                const T kv = (szr >= 0 && szr < G.nz) ? nu[(size_t)szr * G.nx + sxr] : T(0);
-                kk_[idx] = fld == 2 ? kv * T(G.inv_Pr) : kv;
+                const bool ok = szr >= 0 && szr < G.nz;
+                const T* nrow = nu + szr * G.nx;
+                for (int qx = tx; qx < QX; qx += TX)
+                    kk_[qz * QX + qx] = ok ? nrow[wrap_x(x0 + qx - R, G.nx)] * kscale : T(0);
             }
         }
         __syncthreads();
         const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
-        for (int idx = threadIdx.x; idx < QN; idx += blockDim.x) {
-            const int qz = idx / QX, qx = idx - qz * QX;
-            const int i1 = (qz + R) * SX + qx + R;
-            gx_[idx] = dd(zs, i1, 1, idx_);
-            gz_[idx] = dd(zs, i1, SX, idz_);
-        }
+        for (int tz = ty; tz < TZ; tz += TY)              // D_x on tile rows, x-halo r
+            for (int qx = tx; qx < QX; qx += TX)
+                gxs[tz * QX + qx] = dd(zs, (tz + HALO) * SX + qx + R, 1, idx_);
+        for (int qz = ty; qz < QZ; qz += TY)              // D_z on tile columns, z-halo r
+            gzs[qz * TX + tx] = dd(zs, (qz + R) * SX + tx + HALO, SX, idz_);
         __syncthreads();
         const T Kc = T(fld == 2 ? G.K_H : G.K_M);
         const T tdt = T(G.two_over_dt);
-        for (int idx = threadIdx.x; idx < TX * TZ; idx += blockDim.x) {
-            const int tz = idx / TX, tx = idx - tz * TX;
-            const int gz = z0 + tz, gxx = x0 + tx;
-            if (gz >= G.nz || gxx >= G.nx) continue;
-            const int i1 = (tz + HALO) * SX + tx + HALO;
-            const int q = (tz + R) * QX + tx + R;
-            const T dif = ddk<T, SMAG>(kk_, Kc, gx_, q, 1, idx_) + ddk<T, SMAG>(kk_, Kc, gz_, q, QX, idz_);
-            const T xk = zs[i1];
-            const size_t o = foff + (size_t)gz * G.nx + gxx;
-            const T rv = r[o];
-            const T res = rv - (tdt * xk - dif);
-            const T dprev = FIRST ? rv * ith : din[o];
-            const T dk = a1 * dprev + a2 * res;
-            const T xn = xk + dk;
-            zout[o] = xn;
-            if (!LAST) dout[o] = dk;
-            if (LAST) acc[0] += xn * xn;
+        const T* df = FIRST ? nullptr : din + (size_t)fld * G.npt;
+        T* dof = LAST ? nullptr : dout + (size_t)fld * G.npt;
+        if (gxx < G.nx) {
+            for (int tz = ty; tz < TZ; tz += TY) {
+                const int gz = z0 + tz;
+                if (gz >= G.nz) break;
+                const T* gxr = gxs + tz * QX + tx + R;          // centre of the x taps
+                const T* gzc = gzs + (tz + R) * TX + tx;        // centre of the z taps
+                T difx, difz;
+                if (SMAG) {
+                    const T* kx = kk_ + (tz + R) * QX + tx + R;
+                    difx = T(2.0 / 3.0) * (kx[1] * gxr[1] - kx[-1] * gxr[-1]) -
+                           T(1.0 / 12.0) * (kx[2] * gxr[2] - kx[-2] * gxr[-2]);
+                    difz = T(2.0 / 3.0) * (kx[QX] * gzc[TX] - kx[-QX] * gzc[-TX]) -
+                           T(1.0 / 12.0) * (kx[2 * QX] * gzc[2 * TX] - kx[-2 * QX] * gzc[-2 * TX]);
+                } else {
+                    difx = Kc * (T(2.0 / 3.0) * (gxr[1] - gxr[-1]) - T(1.0 / 12.0) * (gxr[2] - gxr[-2]));
+                    difz = Kc * (T(2.0 / 3.0) * (gzc[TX] - gzc[-TX]) - T(1.0 / 12.0) * (gzc[2 * TX] - gzc[-2 * TX]));
+                }
+                const T dif = difx * idx_ + difz * idz_;
+                const T xk = zs[(tz + HALO) * SX + tx + HALO];
+                const int o = gz * G.nx + gxx;
+                const T rv = rf[o];
+                const T res = rv - (tdt * xk - dif);
+                const T dprev = FIRST ? rv * ith : df[o];
+                const T dk = a1 * dprev + a2 * res;
+                const T xn = xk + dk;
+                zf[o] = xn;
+                if (!LAST) dof[o] = dk;
+                if (LAST) acc[0] += xn * xn;
+            }
         }
     }
     if (LAST) {
@@ -757,9 +785,8 @@ static size_t stencil_smem() {
     return sizeof(T) * (4 * (TZ + 2 * HALO) * (TX + 2 * HALO) + 7 * (TX + 2 * R) * (TZ + 2 * R));
 }
 
-template <typename T>
+template <typename T, int TX, int TZ>
 static size_t jvd_smem() {
-    constexpr int TX = TileD<T>::TX, TZ = TileD<T>::TZ;
     return sizeof(T) * (8 * (TZ + 2 * HALO) * (TX + 2 * HALO) + 14 * (TX + 2 * R) * (TZ + 2 * R));
 }
 
@@ -806,27 +833,40 @@ template cudaError_t launch_stencil<float>(int, const Geo&, const float*, const 
 template cudaError_t launch_stencil<double>(int, const Geo&, const double*, const double*, const double*,
                                             const double*, double*, double*, double*, Ctl*, int, cudaStream_t);
 
-template <typename T, int SMAG>
+template <typename T, int SMAG, int TX, int TZ>
 static cudaError_t launch_jvd_t(const Geo& G, const T* u, const T* v, T* out, Ctl* ctl,
                                 int check_done, cudaStream_t s) {
     static bool configured = false;
-    const size_t sm = jvd_smem<T>();
+    const size_t sm = jvd_smem<T, TX, TZ>();
     if (!configured) {
-        cudaError_t e = set_smem(jv_diff2d<T, SMAG>, sm);
+        cudaError_t e = set_smem(jv_diff2d<T, SMAG, TX, TZ>, sm);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid((G.nx + TileD<T>::TX - 1) / TileD<T>::TX, (G.nz + TileD<T>::TZ - 1) / TileD<T>::TZ);
-    jv_diff2d<T, SMAG><<<grid, NTHREADS, sm, s>>>(G, u, v, out, ctl, check_done);
+    dim3 grid((G.nx + TX - 1) / TX, (G.nz + TZ - 1) / TZ);
+    jv_diff2d<T, SMAG, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, u, v, out, ctl, check_done);
     return cudaGetLastError();
+}
+
+template <typename T, int SMAG>
+static cudaError_t launch_jvd_tile(const Geo& G, const T* u, const T* v, T* out, Ctl* ctl,
+                                   int check_done, cudaStream_t s) {
+    if (sizeof(T) == sizeof(double))
+        return launch_jvd_t<T, SMAG, JvTile<1>::TX, JvTile<1>::TZ>(G, u, v, out, ctl, check_done, s);
+    switch (G.tile_jv) {
+        case 1: return launch_jvd_t<T, SMAG, JvTile<1>::TX, JvTile<1>::TZ>(G, u, v, out, ctl, check_done, s);
+        case 2: return launch_jvd_t<T, SMAG, JvTile<2>::TX, JvTile<2>::TZ>(G, u, v, out, ctl, check_done, s);
+        case 3: return launch_jvd_t<T, SMAG, JvTile<3>::TX, JvTile<3>::TZ>(G, u, v, out, ctl, check_done, s);
+        default: return launch_jvd_t<T, SMAG, JvTile<0>::TX, JvTile<0>::TZ>(G, u, v, out, ctl, check_done, s);
+    }
 }
 
 template <typename T>
 cudaError_t launch_jv_diff(const Geo& G, const T* u, const T* v, T* out, double* part, Ctl* ctl,
                            int check_done, cudaStream_t s) {
     (void)part;
-    return G.smag ? launch_jvd_t<T, 1>(G, u, v, out, ctl, check_done, s)
-                  : launch_jvd_t<T, 0>(G, u, v, out, ctl, check_done, s);
+    return G.smag ? launch_jvd_tile<T, 1>(G, u, v, out, ctl, check_done, s)
+                  : launch_jvd_tile<T, 0>(G, u, v, out, ctl, check_done, s);
 }
 template cudaError_t launch_jv_diff<float>(const Geo&, const float*, const float*, float*, double*, Ctl*, int, cudaStream_t);
 template cudaError_t launch_jv_diff<double>(const Geo&, const double*, const double*, double*, double*, Ctl*, int, cudaStream_t);
@@ -844,7 +884,7 @@ cudaError_t launch_eddy(const Geo& G, const T* u, T* nu, double* part, Ctl* ctl,
 template cudaError_t launch_eddy<float>(const Geo&, const float*, float*, double*, Ctl*, cudaStream_t);
 template cudaError_t launch_eddy<double>(const Geo&, const double*, double*, double*, Ctl*, cudaStream_t);
 
-template <typename T, int SMAG>
+template <typename T, int SMAG, int TX, int TZ>
 static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da,
                                     T* db, const T* nu, double* part, Ctl* ctl, int check_done,
                                     cudaStream_t s, long long* launches) {
@@ -854,16 +894,16 @@ static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, 
         if (launches) ++*launches;
         return cudaGetLastError();
     }
-    dim3 grid((G.nx + Tile<T>::TX - 1) / Tile<T>::TX, (G.nz + Tile<T>::TZ - 1) / Tile<T>::TZ, 3);
-    constexpr int TX = Tile<T>::TX, TZ = Tile<T>::TZ;
-    const size_t sm = sizeof(T) * ((TZ + 2 * HALO) * (TX + 2 * HALO) + 3 * (TX + 2 * R) * (TZ + 2 * R));
+    dim3 grid((G.nx + TX - 1) / TX, (G.nz + TZ - 1) / TZ, 3);
+    const size_t sm = sizeof(T) * ((TZ + 2 * HALO) * (TX + 2 * HALO) + TZ * (TX + 2 * R) +
+                                   (TZ + 2 * R) * TX + (TX + 2 * R) * (TZ + 2 * R));
     static bool configured = false;
     if (!configured) {
         cudaError_t e;
-        if ((e = set_smem(cheb2d<T, SMAG, 1, 1>, sm)) != cudaSuccess) return e;
-        if ((e = set_smem(cheb2d<T, SMAG, 1, 0>, sm)) != cudaSuccess) return e;
-        if ((e = set_smem(cheb2d<T, SMAG, 0, 1>, sm)) != cudaSuccess) return e;
-        if ((e = set_smem(cheb2d<T, SMAG, 0, 0>, sm)) != cudaSuccess) return e;
+        if ((e = set_smem(cheb2d<T, SMAG, 1, 1, TX, TZ>, sm)) != cudaSuccess) return e;
+        if ((e = set_smem(cheb2d<T, SMAG, 1, 0, TX, TZ>, sm)) != cudaSuccess) return e;
+        if ((e = set_smem(cheb2d<T, SMAG, 0, 1, TX, TZ>, sm)) != cudaSuccess) return e;
+        if ((e = set_smem(cheb2d<T, SMAG, 0, 0, TX, TZ>, sm)) != cudaSuccess) return e;
         configured = true;
     }
     const T* zin = nullptr;
@@ -876,13 +916,13 @@ static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, 
         T* dO = dbuf[k & 1];
         grid.z = last ? 4 : 3;            // the p block is written by the last sweep only
         if (first && last)
-            cheb2d<T, SMAG, 1, 1><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            cheb2d<T, SMAG, 1, 1, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else if (first)
-            cheb2d<T, SMAG, 1, 0><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            cheb2d<T, SMAG, 1, 0, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else if (last)
-            cheb2d<T, SMAG, 0, 1><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            cheb2d<T, SMAG, 0, 1, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else
-            cheb2d<T, SMAG, 0, 0><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            cheb2d<T, SMAG, 0, 0, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         if (launches) ++*launches;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -892,12 +932,28 @@ static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, 
     return cudaSuccess;
 }
 
+template <typename T, int SMAG>
+static cudaError_t launch_precond_tile(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da,
+                                       T* db, const T* nu, double* part, Ctl* ctl, int check_done,
+                                       cudaStream_t s, long long* launches) {
+#define JF_PC(I) launch_precond_t<T, SMAG, PcTile<I>::TX, PcTile<I>::TZ>(G, sweeps, r, z, za, zb, da, db, nu, \
+                                                                      part, ctl, check_done, s, launches)
+    if (sizeof(T) == sizeof(double)) return JF_PC(1);
+    switch (G.tile_pc) {
+        case 1: return JF_PC(1);
+        case 2: return JF_PC(2);
+        case 3: return JF_PC(3);
+        default: return JF_PC(0);
+    }
+#undef JF_PC
+}
+
 template <typename T>
 cudaError_t launch_precond(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da, T* db,
                            const T* nu, double* part, Ctl* ctl, int check_done, cudaStream_t s,
                            long long* launches) {
-    return G.smag ? launch_precond_t<T, 1>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches)
-                  : launch_precond_t<T, 0>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches);
+    return G.smag ? launch_precond_tile<T, 1>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches)
+                  : launch_precond_tile<T, 0>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches);
 }
 template cudaError_t launch_precond<float>(const Geo&, int, const float*, float*, float*, float*, float*,
                                            float*, const float*, double*, Ctl*, int, cudaStream_t, long long*);

@@ -28,7 +28,7 @@ EXPORTS = (
     "jfnk_create", "jfnk_destroy", "jfnk_set_surface_flux", "jfnk_rhs", "jfnk_residual",
     "jfnk_jv", "jfnk_precond_apply", "jfnk_step", "jfnk_step_host", "jfnk_budgets",
     "jfnk_get_launch_count", "jfnk_status_str", "jfnk_kernel_timing", "jfnk_kernel_timing_read",
-    "jfnk_budgets_static",
+    "jfnk_budgets_static", "jfnk_autotune", "jfnk_set_tiles",
 )
 
 KERNEL_FAMILIES = ("arnoldi_a", "arnoldi_b", "arnoldi_c", "jv", "precond", "residual")
@@ -109,6 +109,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.jfnk_kernel_timing.argtypes = [P, ctypes.c_uint]
     lib.jfnk_kernel_timing_read.argtypes = [P, ctypes.POINTER(KernelTime)]
     lib.jfnk_budgets_static.argtypes = [ctypes.POINTER(Grid), P, P, P]
+    lib.jfnk_autotune.argtypes = [P, P, ctypes.POINTER(ctypes.c_int)]
+    lib.jfnk_set_tiles.argtypes = [P, I, I]
     lib.jfnk_status_str.argtypes = [I]
     lib.jfnk_status_str.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -238,6 +240,15 @@ class Solver:
         _check(self.lib.jfnk_kernel_timing_read(self.h, arr), "jfnk_kernel_timing_read")
         return {name: {"launches": a.launches, "ms": a.ms, "bytes": a.bytes}
                 for name, a in zip(KERNEL_FAMILIES, arr)}
+
+    def autotune(self, u) -> tuple:
+        """Pick the fastest stencil tile shapes for this grid (times every candidate)."""
+        t = (ctypes.c_int * 2)()
+        _check(self.lib.jfnk_autotune(self.h, _ptr(u), t), "jfnk_autotune")
+        return (t[0], t[1])
+
+    def set_tiles(self, tile_jv: int, tile_pc: int):
+        _check(self.lib.jfnk_set_tiles(self.h, int(tile_jv), int(tile_pc)), "jfnk_set_tiles")
 
     def launch_count(self) -> int:
         c = ctypes.c_longlong(0)
