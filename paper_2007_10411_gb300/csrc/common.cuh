@@ -96,6 +96,7 @@ __device__ __forceinline__ void block_partials(const TA (&v)[NV], int nv, double
         double s = 0.0;
         for (int w = 0; w < nw; ++w) s += (double)red[k][w];
         part[(size_t)k * stride + blk] = s;
+        __threadfence();          // publish before the block's arrival is counted
     }
 }
 
@@ -119,14 +120,16 @@ __device__ __forceinline__ void block_partials_max(const double (&v)[NV], int nv
         double s = red[k][0];
         for (int w = 1; w < nw; ++w) s = fmax(s, red[k][w]);
         part[(size_t)k * stride + blk] = s;
+        __threadfence();          // publish before the block's arrival is counted
     }
 }
 
-// True in exactly one block: the last one to arrive.  Counters wrap to zero
-// by themselves (atomicInc limit), so no reset is needed between launches.
+// True in exactly one block: the last one to arrive.  The threads that wrote
+// the block's partial sums fenced them (block_partials); the barrier orders
+// those fences before thread 0's arrival.  Counters wrap to zero by
+// themselves (atomicInc limit), so no reset is needed between launches.
 __device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int total) {
     __shared__ bool am_last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned int t = atomicInc(counter, total - 1);

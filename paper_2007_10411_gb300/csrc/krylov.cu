@@ -175,9 +175,9 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int 
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvec; i += stride) {
         VT wp = reinterpret_cast<const VT*>(w)[i];
-#pragma unroll
-        for (int k = 0; k < NV; ++k)
-            if (k < nv) wp = axpyv(wp, h1s[k], reinterpret_cast<const VT*>(V + k * ldv)[i]);
+        // first use of v_k (runtime trip count, a few loads in flight at a time)
+#pragma unroll 4
+        for (int k = 0; k < nv; ++k) wp = axpyv(wp, h1s[k], reinterpret_cast<const VT*>(V + k * ldv)[i]);
         // second use of v_k: re-read (L1 / L2 hit) instead of holding NV vectors in registers
 #pragma unroll
         for (int k = 0; k < NV; ++k)

@@ -384,6 +384,19 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
     T ev[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) ev[q] = evs[q];
+    // the direction at this thread's outputs, fetched before the tile staging
+    constexpr int NOUT = (TX * TZ + NTHREADS - 1) / NTHREADS;
+    T vout[NOUT][4];
+#pragma unroll
+    for (int q = 0; q < NOUT; ++q) {
+        const int idx = threadIdx.x + q * NTHREADS;
+        const int tz = idx / TX, tx = idx - tz * TX;
+        const int gz = z0 + tz, gx = x0 + tx;
+        const bool ok = idx < TX * TZ && gz < G.nz && gx < G.nx;
+#pragma unroll
+        for (int fl = 0; fl < 4; ++fl)
+            vout[q][fl] = ok ? v[(size_t)fl * G.npt + (size_t)gz * G.nx + gx] : T(0);
+    }
     load_fields<T, 0>(sa, u, v, ev, G, x0, z0, SX, SZ);
     load_fields<T, 2>(sb, u, v, ev, G, x0, z0, SX, SZ);
     __syncthreads();
@@ -420,7 +433,10 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
     const T* bu = sb; const T* bw = sb + SZ * SX; const T* bt = sb + 2 * SZ * SX; const T* bp = sb + 3 * SZ * SX;
     const T KMc = T(G.K_M), KHc = T(G.K_H), iPr = T(G.inv_Pr), th0 = T(G.theta0);
 
-    for (int idx = threadIdx.x; idx < TX * TZ; idx += blockDim.x) {
+#pragma unroll
+    for (int qo = 0; qo < NOUT; ++qo) {
+        const int idx = threadIdx.x + qo * NTHREADS;
+        if (idx >= TX * TZ) break;
         const int tz = idx / TX, tx = idx - tz * TX;
         const int gz = z0 + tz, gx = x0 + tx;
         if (gz >= G.nz || gx >= G.nx) continue;
@@ -497,7 +513,7 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
             const size_t o = (size_t)fl * G.npt + off;
             // the difference dF is already free of cancellation: the quotient
             // and the 2 v/dt term need no wider type than the result
-            out[o] = T(G.two_over_dt) * v[o] - dF[fl] * cfs[fl];
+            out[o] = T(G.two_over_dt) * vout[qo][fl] - dF[fl] * cfs[fl];
         }
     }
 }
@@ -619,6 +635,19 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
             }
         }
     } else {
+        // per-output operands first: their latency overlaps the tile staging below
+        constexpr int NR = TZ / TY;
+        T rv[NR], dv[NR];
+        const T* df = FIRST ? nullptr : din + (size_t)fld * G.npt;
+        const bool colok = gxx < G.nx;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const int gz = z0 + ty + q * TY;
+            const bool ok = colok && gz < G.nz;
+            const int o = gz * G.nx + gxx;
+            rv[q] = ok ? rf[o] : T(0);
+            dv[q] = (!FIRST && ok) ? df[o] : T(0);
+        }
         // x_k with halo 2r (first sweep: x_1 = r / theta_c)
         T sc[4] = {T(0), T(0), T(0), T(0)};
         if (FIRST) {
@@ -648,10 +677,11 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
         __syncthreads();
         const T Kc = T(fld == 2 ? G.K_H : G.K_M);
         const T tdt = T(G.two_over_dt);
-        const T* df = FIRST ? nullptr : din + (size_t)fld * G.npt;
         T* dof = LAST ? nullptr : dout + (size_t)fld * G.npt;
-        if (gxx < G.nx) {
-            for (int tz = ty; tz < TZ; tz += TY) {
+        if (colok) {
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+                const int tz = ty + q * TY;
                 const int gz = z0 + tz;
                 if (gz >= G.nz) break;
                 const T* gxr = gxs + tz * QX + tx + R;          // centre of the x taps
@@ -670,9 +700,8 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
                 const T dif = difx * idx_ + difz * idz_;
                 const T xk = zs[(tz + HALO) * SX + tx + HALO];
                 const int o = gz * G.nx + gxx;
-                const T rv = rf[o];
-                const T res = rv - (tdt * xk - dif);
-                const T dprev = FIRST ? rv * ith : df[o];
+                const T res = rv[q] - (tdt * xk - dif);
+                const T dprev = FIRST ? rv[q] * ith : dv[q];
                 const T dk = a1 * dprev + a2 * res;
                 const T xn = xk + dk;
                 zf[o] = xn;
