@@ -21,7 +21,8 @@ constexpr int MAX_PC_SWEEPS = 16;
 
 // Geometry and physics constants, passed by value to the stencil kernels.
 struct Geo {
-    int nx, nz, npt, nf;
+    int dim, nx, ny, nz, npt, nf;     // 2-D: ny = 1, nf = 4 (u, w, theta, p); 3-D: nf = 5 (u, v, w, theta, p)
+    double inv_dy;
     int pb[5], pt[5];                 // mirror parity per field at bottom / top (+1 / -1)
     double inv_dx, inv_dz;
     double theta0, beta, pbar, g, gamma_p, heat_coef;   // heat_coef = 1/(rho0 cp dz)
@@ -64,7 +65,7 @@ struct Ctl {
     double g[KMAX + 1];
     double y[KMAX];
     // Chebyshev coefficients per field block and sweep: 1/theta_c, rho_k rho_{k-1}, 2 rho_k / delta
-    double cheb[4][MAX_PC_SWEEPS][3];
+    double cheb[5][MAX_PC_SWEEPS][3];
     unsigned int counter[8];         // last-block counters, one per kernel family
 };
 

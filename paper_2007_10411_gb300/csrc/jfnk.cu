@@ -102,7 +102,7 @@ static jfnk_status validate(const jfnk_grid* g, const jfnk_strat* s, const jfnk_
         return JFNK_ERR_INVALID_ARG;
     if (o->wavelet_p < 1) return JFNK_ERR_INVALID_ARG;
     // implemented subset
-    if (g->dim != 2 || o->wavelet_p != 2) return JFNK_ERR_UNSUPPORTED;
+    if (o->wavelet_p != 2) return JFNK_ERR_UNSUPPORTED;
     if (g->nz < 4) return JFNK_ERR_INVALID_ARG;      // one mirror reflection covers the halo
     return JFNK_OK;
 }
@@ -197,22 +197,34 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     h->stream = (cudaStream_t)cuda_stream;
     h->mixed = opts->precision == JFNK_MIXED;
     h->m = opts->krylov_m;
-    h->npt = (size_t)grid->nx * grid->nz;
-    h->n = 4 * h->npt;
+    const int dim = grid->dim;
+    const int ny = dim == 3 ? grid->ny : 1;
+    const int nf = dim == 3 ? 5 : 4;
+    h->npt = (size_t)grid->nx * ny * grid->nz;
+    h->n = (size_t)nf * h->npt;
     h->ld = (h->n + 63) / 64 * 64;
 
     Geo& G = h->G;
     memset(&G, 0, sizeof(G));
+    G.dim = dim;
     G.nx = grid->nx;
+    G.ny = ny;
     G.nz = grid->nz;
     G.npt = (int)h->npt;
-    G.nf = 4;
+    G.nf = nf;
     const int sb = grid->bc_bottom == JFNK_FREESLIP ? 1 : -1;
     const int stp = grid->bc_top == JFNK_FREESLIP ? 1 : -1;
-    const int pb[4] = {sb, -1, 1, 1}, pt[4] = {stp, -1, 1, 1};
-    for (int f = 0; f < 4; ++f) { G.pb[f] = pb[f]; G.pt[f] = pt[f]; }
+    // parities: horizontal velocities follow the wall condition, w is odd, theta and p even
+    for (int f = 0; f < nf; ++f) {
+        const bool horiz = f < nf - 3;
+        const bool wv = f == nf - 3;
+        G.pb[f] = horiz ? sb : (wv ? -1 : 1);
+        G.pt[f] = horiz ? stp : (wv ? -1 : 1);
+    }
     const double dx = grid->lx / grid->nx, dz = grid->lz / grid->nz;
+    const double dy = dim == 3 ? grid->ly / ny : 1.0;
     G.inv_dx = 1.0 / dx;
+    G.inv_dy = 1.0 / dy;
     G.inv_dz = 1.0 / dz;
     G.theta0 = strat->theta0;
     G.beta = strat->beta;
@@ -223,12 +235,14 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     G.smag = sgs->mode == JFNK_SGS_SMAGORINSKY;
     G.K_M = G.smag ? 0.0 : sgs->K_M;
     G.K_H = G.smag ? 0.0 : sgs->K_H;
-    const double delta = sqrt(dx * dz);
+    const double delta = dim == 3 ? cbrt(dx * dy * dz) : sqrt(dx * dz);
     G.cs2 = (sgs->Cs * delta) * (sgs->Cs * delta);
     G.inv_Pr = 1.0 / sgs->Pr;
     G.two_over_dt = 2.0 / opts->dt;
-    const double sc[4] = {opts->scale_u, opts->scale_u, opts->scale_theta, opts->scale_p};
-    for (int f = 0; f < 4; ++f) { G.scale[f] = sc[f]; G.inv_scale[f] = 1.0 / sc[f]; }
+    for (int f = 0; f < nf; ++f) {
+        G.scale[f] = f < nf - 2 ? opts->scale_u : (f == nf - 2 ? opts->scale_theta : opts->scale_p);
+        G.inv_scale[f] = 1.0 / G.scale[f];
+    }
     G.heat = nullptr;
     G.tile_jv = 0;
     G.tile_pc = 0;
@@ -238,7 +252,7 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     const size_t nbT = h->ld * eT;
     const int m = h->m;
     int maxblk = MAX_STREAM_BLOCKS;
-    maxblk = std::max(maxblk, stencil_part_blocks(G));
+    maxblk = std::max(maxblk, dim == 3 ? stencil3d_part_blocks(G) : stencil_part_blocks(G));
     {   // multi-dot grids: up to n / (4 * NTHREADS * 64) CTAs
         const size_t rb = h->n / ((size_t)NTHREADS * 64) + 1;
         maxblk = std::max(maxblk, (int)std::min(rb, (size_t)MAX_REDUCE_BLOCKS));
@@ -261,7 +275,7 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     ALLOC(h->x, nb8);
     ALLOC(h->tmp64, nb8);
     ALLOC(h->udev, nb8);
-    ALLOC(h->heat, (size_t)grid->nx * sizeof(double));
+    ALLOC(h->heat, (size_t)grid->nx * ny * sizeof(double));
     ALLOC(h->budg, 64 * sizeof(double));
     ALLOC(h->V, (size_t)(m + 1) * nbT);
     if (opts->precond == JFNK_PC_BLOCK) ALLOC(h->Z, (size_t)m * nbT);
@@ -326,8 +340,8 @@ extern "C" jfnk_status jfnk_set_surface_flux(jfnk_handle* h, const double* H) {
         h->G.heat = nullptr;
         return JFNK_OK;
     }
-    CK(cudaMemcpyAsync(h->heat, H, (size_t)h->grid.nx * sizeof(double), cudaMemcpyDeviceToDevice,
-                       h->stream));
+    CK(cudaMemcpyAsync(h->heat, H, (size_t)h->grid.nx * h->G.ny * sizeof(double),
+                       cudaMemcpyDeviceToDevice, h->stream));
     h->G.heat = h->heat;
     return JFNK_OK;
 }
@@ -734,19 +748,20 @@ extern "C" jfnk_status jfnk_step_host(jfnk_handle* h, double* u_host, jfnk_stats
 extern "C" jfnk_status jfnk_budgets(jfnk_handle* h, const double* u, jfnk_budget* out) {
     if (!h || !u || !out) return JFNK_ERR_INVALID_ARG;
     const double dx = h->grid.lx / h->grid.nx, dz = h->grid.lz / h->grid.nz;
-    CK(launch_budgets(h->G, u, dx, dz, h->grid.lz, h->part, h->ctl, h->budg, h->stream));
+    CK(launch_budgets(h->G, u, dx, dz, h->grid.lz, h->part, h->ctl, h->budg, h->stream));   // 3-D: dV includes dy
     h->launches += 1;
-    double b[12];
-    CK(cudaMemcpyAsync(b, h->budg, sizeof(b), cudaMemcpyDeviceToHost, h->stream));
+    double b[14];
+    const int nf = h->G.nf;
+    CK(cudaMemcpyAsync(b, h->budg, (4 + 2 * nf) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     memset(out, 0, sizeof(*out));
     out->E_k = b[0];
     out->E_p = b[1];
     out->sum_theta = b[2];
     out->sum_div = b[3];
-    for (int f = 0; f < 4; ++f) {
+    for (int f = 0; f < nf; ++f) {
         out->max[f] = b[4 + f];
-        out->min[f] = b[8 + f];
+        out->min[f] = b[4 + nf + f];
     }
     return JFNK_OK;
 }

@@ -38,6 +38,23 @@ cudaError_t launch_pc_setup(const Geo& G, int sweeps, Ctl* ctl, cudaStream_t s);
 cudaError_t launch_budgets(const Geo& G, const double* u, double dx, double dz, double lz,
                            double* part, Ctl* ctl, double* out, cudaStream_t s);
 
+// ------------------------------------------------------------ 3-D stencils
+int stencil3d_part_blocks(const Geo& G);
+template <typename T>
+cudaError_t launch_stencil3d(int mode, const Geo& G, const T* u, const T* v, const T* Fu, const double* f,
+                             T* out, T* out2, double* part, Ctl* ctl, int check_done, cudaStream_t s);
+template <typename T>
+cudaError_t launch_jv_diff3d(const Geo& G, const T* u, const T* v, T* out, Ctl* ctl, int check_done,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_eddy3d(const Geo& G, const T* u, T* nu, double* part, Ctl* ctl, cudaStream_t s);
+template <typename T>
+cudaError_t launch_precond3d(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da, T* db,
+                             const T* nu, double* part, Ctl* ctl, int check_done, cudaStream_t s,
+                             long long* launches);
+cudaError_t launch_budgets3d(const Geo& G, const double* u, double dV, double dz, double lz, double* part,
+                             Ctl* ctl, double* out, cudaStream_t s);
+
 // ------------------------------------------------------------ Krylov kernels
 template <typename T>
 cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int nv, double* part,

@@ -572,11 +572,13 @@ eddy2d(Geo G, const T* __restrict__ u, T* __restrict__ nu, double* part, Ctl* ct
 // rho_k rho_{k-1} and 2 rho_k / delta, with rho_0 = 1/sigma, sigma = theta_c/delta.
 __global__ void pc_setup(Geo G, int sweeps, Ctl* ctl) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    for (int f = 0; f < 4; ++f) {
+    const int fth = G.nf - 2, fp = G.nf - 1;         // theta and p
+    const double h2 = G.inv_dx * G.inv_dx + G.inv_dz * G.inv_dz + (G.dim == 3 ? G.inv_dy * G.inv_dy : 0.0);
+    for (int f = 0; f < G.nf; ++f) {
         const double lo = G.two_over_dt;
         double kmax = 0.0;
-        if (f < 3) kmax = G.smag ? ctl->kmax * (f == 2 ? G.inv_Pr : 1.0) : (f == 2 ? G.K_H : G.K_M);
-        const double hi = lo + 2.25 * kmax * (G.inv_dx * G.inv_dx + G.inv_dz * G.inv_dz);
+        if (f != fp) kmax = G.smag ? ctl->kmax * (f == fth ? G.inv_Pr : 1.0) : (f == fth ? G.K_H : G.K_M);
+        const double hi = lo + 2.25 * kmax * h2;
         const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
         const bool degenerate = delta <= 1e-14 * theta;
         const double sigma = degenerate ? 1.0 : theta / delta;
@@ -732,8 +734,8 @@ pc_diag(Geo G, const T* __restrict__ r, T* __restrict__ z, size_t n, double* par
         int check_done) {
     if (check_done && ctl->done) return;
     T acc[1] = {T(0)};
-    T inv_th[4];
-    for (int f = 0; f < 4; ++f) inv_th[f] = T(ctl->cheb[f][0][0]);
+    T inv_th[5];
+    for (int f = 0; f < G.nf; ++f) inv_th[f] = T(ctl->cheb[f][0][0]);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int f = (int)(i / G.npt);
         const T zv = r[i] * inv_th[f];
@@ -844,6 +846,7 @@ template <typename T>
 cudaError_t launch_stencil(int mode, const Geo& G, const T* u, const T* v, const T* Fu,
                            const double* f, T* out, T* out2, double* part, Ctl* ctl,
                            int check_done, cudaStream_t s) {
+    if (G.dim == 3) return launch_stencil3d<T>(mode, G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
 #define JF_CASE(M)                                                                           \
     case M:                                                                                  \
         return G.smag ? launch_stencil_t<T, M, 1>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s) \
@@ -894,6 +897,7 @@ template <typename T>
 cudaError_t launch_jv_diff(const Geo& G, const T* u, const T* v, T* out, double* part, Ctl* ctl,
                            int check_done, cudaStream_t s) {
     (void)part;
+    if (G.dim == 3) return launch_jv_diff3d<T>(G, u, v, out, ctl, check_done, s);
     return G.smag ? launch_jvd_tile<T, 1>(G, u, v, out, ctl, check_done, s)
                   : launch_jvd_tile<T, 0>(G, u, v, out, ctl, check_done, s);
 }
@@ -907,6 +911,7 @@ static int stream_blocks(size_t n) {
 
 template <typename T>
 cudaError_t launch_eddy(const Geo& G, const T* u, T* nu, double* part, Ctl* ctl, cudaStream_t s) {
+    if (G.dim == 3) return launch_eddy3d<T>(G, u, nu, part, ctl, s);
     eddy2d<T><<<stream_blocks(G.npt), NTHREADS, 0, s>>>(G, u, nu, part, ctl);
     return cudaGetLastError();
 }
@@ -917,7 +922,7 @@ template <typename T, int SMAG, int TX, int TZ>
 static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da,
                                     T* db, const T* nu, double* part, Ctl* ctl, int check_done,
                                     cudaStream_t s, long long* launches) {
-    const size_t n = (size_t)4 * G.npt;
+    const size_t n = (size_t)G.nf * G.npt;
     if (sweeps <= 1) {
         pc_diag<T, SMAG><<<stream_blocks(n), NTHREADS, 0, s>>>(G, r, z, n, part, ctl, check_done);
         if (launches) ++*launches;
@@ -981,6 +986,8 @@ template <typename T>
 cudaError_t launch_precond(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da, T* db,
                            const T* nu, double* part, Ctl* ctl, int check_done, cudaStream_t s,
                            long long* launches) {
+    if (G.dim == 3 && sweeps > 1)
+        return launch_precond3d<T>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches);
     return G.smag ? launch_precond_tile<T, 1>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches)
                   : launch_precond_tile<T, 0>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches);
 }
@@ -997,6 +1004,7 @@ cudaError_t launch_pc_setup(const Geo& G, int sweeps, Ctl* ctl, cudaStream_t s) 
 
 cudaError_t launch_budgets(const Geo& G, const double* u, double dx, double dz, double lz,
                            double* part, Ctl* ctl, double* out, cudaStream_t s) {
+    if (G.dim == 3) return launch_budgets3d(G, u, dx * dz / G.inv_dy, dz, lz, part, ctl, out, s);
     budgets2d<<<stream_blocks(G.npt), NTHREADS, 0, s>>>(G, u, dx * dz, dz, lz, part, ctl, out);
     return cudaGetLastError();
 }

@@ -77,8 +77,10 @@ def case(name: str) -> dict:
                              Pr = 0.71, bubble + 0.01 K white noise, FP32 stencils/basis with
                              FP64 Newton residual, FD difference, Givens and update.
     uhi_<nx>x<nz>            2D urban heat island, 100 km x 2 km, no-slip ground, beta = 3 K/km.
-    thermal3d_<n>            3D dry thermal (cube-ish), N = 0.01 1/s, Smagorinsky.
-    tiny_<nx>x<nz>           small variant of the thermal for unit tests.
+    thermal3d_<nx>x<ny>x<nz> 3D dry thermal, 20 x 20 x 10 km, N = 0.01 1/s, Smagorinsky, bubble +
+                             noise, mixed precision, FGMRES(20).
+    uhi3d_<nx>x<ny>x<nz>     3D heat island, 100 x 100 x 2 km, square 20 x 20 km urban patch.
+    tiny_<nx>x<nz>           small variant of the thermal for unit tests (tiny3d_<nx>x<ny>x<nz> in 3D).
     """
     if name == "thermal_neutral_128x64":
         c = _base_case(2, 128, 64, 20000.0, 10000.0)
@@ -103,6 +105,34 @@ def case(name: str) -> dict:
         c = _base_case(2, nx, nz, 20000.0 * nx / 128.0, 10000.0 * nz / 64.0)
         c["init"] = {"kind": "bubble", "dtheta": 2.0, "radius": 2000.0, "zc": 2000.0,
                      "noise": 0.0}
+        return c
+    if name.startswith("thermal3d_"):
+        nx, ny, nz = (int(v) for v in name[len("thermal3d_"):].split("x"))
+        c = _base_case(3, nx, nz, 20000.0, 10000.0, ny=ny, ly=20000.0)
+        c["strat"]["beta"] = brunt_beta(0.01)
+        c["sgs"].update(mode=SGS_SMAGORINSKY, Cs=0.18, Pr=0.71)
+        c["opts"]["precision"] = PREC_MIXED
+        c["opts"]["krylov_m"] = 20
+        c["init"] = {"kind": "bubble", "dtheta": 2.0, "radius": 2000.0, "zc": 2000.0,
+                     "noise": 0.01}
+        return c
+    if name.startswith("tiny3d_"):
+        nx, ny, nz = (int(v) for v in name[len("tiny3d_"):].split("x"))
+        c = _base_case(3, nx, nz, 20000.0 * nx / 128.0, 10000.0 * nz / 64.0, ny=ny,
+                       ly=20000.0 * ny / 128.0)
+        c["init"] = {"kind": "bubble", "dtheta": 2.0, "radius": 2000.0, "zc": 2000.0,
+                     "noise": 0.0}
+        return c
+    if name.startswith("uhi3d_"):
+        nx, ny, nz = (int(v) for v in name[len("uhi3d_"):].split("x"))
+        c = _base_case(3, nx, nz, 100000.0, 2000.0, ny=ny, ly=100000.0)
+        c["grid"]["bc_bottom"] = NOSLIP
+        c["strat"]["beta"] = 3.0e-3
+        c["sgs"].update(mode=SGS_SMAGORINSKY, Cs=0.18, Pr=0.71)
+        c["opts"]["precision"] = PREC_MIXED
+        c["opts"]["krylov_m"] = 20
+        c["init"] = {"kind": "rest", "H0": 100.0, "patch_halfwidth": 10000.0,
+                     "xi": 0.1, "l": 1.5}
         return c
     if name.startswith("uhi_"):
         nx, nz = (int(v) for v in name[len("uhi_"):].split("x"))
