@@ -27,7 +27,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = "thermal_stable_1024x512"
-METRIC = "Mpt*steps/s at Newton tol 1e-8 (2D stable dry thermal 1024x512, mixed FP32/FP64 JFNK)"
+METRICS = {
+    "thermal_stable_1024x512": "Mpt*steps/s at Newton tol 1e-8 (2D stable dry thermal 1024x512, mixed FP32/FP64 JFNK)",
+}
+
+
+def metric_name(workload: str) -> str:
+    return METRICS.get(workload, "Mpt*steps/s at Newton tol 1e-8 (%s, mixed FP32/FP64 JFNK)" % workload)
 # Krylov iterations of the first implicit step of this workload, measured with the
 # float64 oracle (3 Newton corrections: 156 + 174 + 230 GMRES(30) iterations);
 # used to scale the oracle's bounded samples to whole steps.
@@ -187,7 +193,7 @@ def oracle_sample(case: dict, seconds: float, iters_per_step: float, newton_per_
     gmres(lambda v: m.jv_scaled(U, FU, v), -m.scale(R), k, 1e-30, 0, precond=pc, flexible=True, record=rec)
     t_it = (time.perf_counter() - t2) / rec["iters"]
     step_s = t_setup * newton_per_step + t_it * iters_per_step
-    npt = case["grid"]["nx"] * case["grid"]["nz"]
+    npt = int(np.prod(synth.shape(case)[1:]))
     return {
         "value": npt / step_s / 1e6,
         "step_seconds": step_s,
@@ -221,14 +227,14 @@ def run_reference(args, rank: int):
             per.append(r["step_seconds"])
             sample = r["sample"]
     step_s = statistics.mean(per)
-    npt = case["grid"]["nx"] * case["grid"]["nz"]
+    npt = int(__import__("math").prod(synth.shape(case)[1:]))
     value = npt / step_s / 1e6
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpt*steps/s",
+        "impl": "reference", "metric": metric_name(args.workload), "value": value, "unit": "Mpt*steps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "grid": [case["grid"]["nx"], case["grid"]["nz"]],
+        "config": {"workload": args.workload, "grid": list(synth.shape(case)[:0:-1]),
                    "note": "float64 numpy oracle; each step is a bounded sample extrapolated to a whole step"},
         "cpu_baseline": {"value": value, "unit": "Mpt*steps/s", "cores": cpu_threads(), "kind": "oracle",
                          "sample": sample},
@@ -261,8 +267,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         return max_over_ranks(v, dist, "cuda")
 
     case = synth.case(args.workload)
-    npt = case["grid"]["nx"] * case["grid"]["nz"]
-    n = 4 * npt
+    npt = synth.shape(case)[1:]
+    npt = int(__import__("math").prod(npt))
+    n = synth.n_fields(case) * npt
     stream = torch.cuda.current_stream()
     solver = jfnk.Solver(case, stream=stream)
     U0 = synth.initial_state(case)
@@ -357,17 +364,18 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         cpu = {"value": r["value"], "unit": "Mpt*steps/s", "cores": cpu_threads(), "kind": "oracle",
                "sample": r["sample"]}
     line = {
-        "metric": METRIC, "value": value, "unit": "Mpt*steps/s", "n_gpus": world,
+        "metric": metric_name(args.workload), "value": value, "unit": "Mpt*steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/f64", "data": "synthetic",
-        "config": {"workload": args.workload, "grid": [case["grid"]["nx"], case["grid"]["nz"]],
+        "config": {"workload": args.workload, "grid": list(synth.shape(case)[:0:-1]),
                    "points": npt, "precision": "mixed", "krylov_m": case["opts"]["krylov_m"],
                    "precond": "field-block Chebyshev (%d sweeps)" % case["opts"]["pc_sweeps"],
                    "parallelism": "replicas" if world > 1 else "single",
                    "tiles": {"jv": tiles[0], "precond": tiles[1]},
                    "l2": "working set > L2: the Krylov basis and directions (%d x %.1f MB) stream "
-                         "through L2 every Arnoldi pass" % (2 * case["opts"]["krylov_m"] + 1, n * 4 / 1e6)},
+                         "through L2 every Arnoldi pass" % (2 * case["opts"]["krylov_m"] + 1, n * 4 / 1e6),
+                   "newton_rtol": case["opts"]["newton_rtol"], "dt": case["opts"]["dt"]},
         "newton_per_step": newt, "gmres_iters_per_step": iters,
         "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "kernels": kernels,
         "fp64_plain": fp64, "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
