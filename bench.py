@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -244,6 +245,84 @@ def run_reference(args, rank: int):
 
 
 # ---------------------------------------------------------------- our arm
+def run_batch(args, rank: int, world: int, local_rank: int):
+    """The batched heat-island workload: every instance stepped concurrently (jfnk_step_batch)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2007_10411_gb300 import jfnk, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist = dist_
+    n_inst = int(args.workload[len("uhi_batch"):] or 16)
+    cases = synth.uhi_batch(n=n_inst)
+    stream = torch.cuda.current_stream()
+    batch = jfnk.Batch(cases, stream=stream)
+    for i, c in enumerate(cases):
+        batch.set_surface_flux(i, torch.from_numpy(synth.heat_flux(c)).cuda())
+    U0 = [synth.initial_state(c) for c in cases]
+    states = [torch.from_numpy(u).cuda() for u in U0]
+    points = sum(int(np.prod(synth.shape(c)[1:])) for c in cases)
+    for _ in range(args.warmup):
+        batch.step(states)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = Clocks(local_rank)
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [batch.step(states) for _ in range(args.steps)]
+    e1.record(stream)
+    e1.synchronize()
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    clk = clocks.stop()
+    ms = max_over_ranks(max(e0.elapsed_time(e1), 0.0), dist, "cuda")
+    value = job_throughput(points, args.steps, world, ms)
+    e2e = None
+    if args.e2e_steps > 0:
+        hosts = [torch.from_numpy(u.copy()).pin_memory() for u in U0]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for h, d in zip(hosts, states):
+                d.copy_(h, non_blocking=True)
+            batch.step(states)
+            for h, d in zip(hosts, states):
+                h.copy_(d, non_blocking=True)
+            torch.cuda.synchronize()
+        el = max_over_ranks((time.perf_counter() - t0) * 1e3, dist, "cuda")
+        nbytes = sum(8 * int(np.prod(synth.shape(c))) for c in cases)
+        e2e = {"value": job_throughput(points, args.e2e_steps, world, el), "unit": "Mpt*steps/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    if rank != 0:
+        return
+    per_inst = [[s[i] for s in stats] for i in range(n_inst)]
+    line = {
+        "metric": metric_name(args.workload), "value": value, "unit": "Mpt*steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "wall_ms_per_step": wall_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "instances": n_inst, "points": points,
+                   "grids": [list(synth.shape(c)[:0:-1]) for c in cases],
+                   "H0": [round(c["init"]["H0"], 2) for c in cases],
+                   "precision": "mixed", "krylov_m": cases[0]["opts"]["krylov_m"],
+                   "execution": "one handle + stream per instance, host thread per instance",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "newton_per_step": [statistics.mean(s["newton_iters"] for s in p) for p in per_inst],
+        "gmres_iters_per_step": [statistics.mean(s["gmres_iters"] for s in p) for p in per_inst],
+        "clocks": clk, "e2e": e2e, "roofline": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, rank: int, world: int, local_rank: int):
     import numpy as np
     import torch
@@ -397,7 +476,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_ours(args, rank, world, local_rank)
+    if args.workload.startswith("uhi_batch"):
+        run_batch(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -223,6 +223,34 @@ jfnk_status jfnk_kernel_timing(jfnk_handle* h, unsigned int mask);
  * accumulators of all JFNK_KF_COUNT families into out[0 .. JFNK_KF_COUNT). */
 jfnk_status jfnk_kernel_timing_read(jfnk_handle* h, jfnk_kernel_time* out);
 
+/* ------------------------------------------------------------------ batch
+ * Many independent grids stepped together (e.g. heat-island instances of
+ * uneven sizes and surface fluxes, Section 3.2).  Each instance gets its own
+ * handle (full workspace) and a non-blocking stream created by the batch; a
+ * batch step forks the caller's stream into the instance streams, runs every
+ * instance's Newton / GMRES sequence concurrently from one host thread per
+ * instance, and joins back, so independent instances overlap on the GPU. */
+#define JFNK_MAX_BATCH 256
+typedef struct jfnk_batch jfnk_batch;
+
+/* n instances; grids, strats, sgs, opts are host arrays of n structs (same
+ * validation as jfnk_create).  cuda_stream: the caller's stream. */
+jfnk_status jfnk_create_batch(int n, const jfnk_grid* grids, const jfnk_strat* strats,
+                              const jfnk_sgs* sgs, const jfnk_opts* opts, void* cuda_stream,
+                              jfnk_batch** out);
+jfnk_status jfnk_destroy_batch(jfnk_batch* b);
+
+/* The handle of instance i (owned by the batch; e.g. for jfnk_set_surface_flux). */
+jfnk_status jfnk_batch_handle(jfnk_batch* b, int i, jfnk_handle** out);
+
+/* One implicit step of every instance: u is a host array of n device state
+ * pointers (layout of instance i's grid).  stats / status (host arrays of n,
+ * may be NULL) receive each instance's report and status.  Returns JFNK_OK
+ * when every instance converged, otherwise the first error or
+ * JFNK_ERR_NOT_CONVERGED.  Blocks the calling thread until all instances
+ * finish; the caller's stream waits for them. */
+jfnk_status jfnk_step_batch(jfnk_batch* b, double* const* u, jfnk_stats* stats, jfnk_status* status);
+
 /* Number of tile shapes jfnk_set_tiles accepts per kernel family. */
 #define JFNK_NUM_TILE_SHAPES 4
 

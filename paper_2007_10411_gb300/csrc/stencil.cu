@@ -24,6 +24,8 @@
 // in shared memory.
 #include <math.h>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -830,7 +832,7 @@ template <typename T, int MODE, int SMAG>
 static cudaError_t launch_stencil_t(const Geo& G, const T* u, const T* v, const T* Fu,
                                     const double* f, T* out, T* out2, double* part, Ctl* ctl,
                                     int check_done, cudaStream_t s) {
-    static bool configured = false;
+    static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
     const size_t sm = stencil_smem<T>();
     if (!configured) {
         cudaError_t e = set_smem(stencil2d<T, MODE, SMAG>, sm);
@@ -868,7 +870,7 @@ template cudaError_t launch_stencil<double>(int, const Geo&, const double*, cons
 template <typename T, int SMAG, int TX, int TZ>
 static cudaError_t launch_jvd_t(const Geo& G, const T* u, const T* v, T* out, Ctl* ctl,
                                 int check_done, cudaStream_t s) {
-    static bool configured = false;
+    static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
     const size_t sm = jvd_smem<T, TX, TZ>();
     if (!configured) {
         cudaError_t e = set_smem(jv_diff2d<T, SMAG, TX, TZ>, sm);
@@ -931,7 +933,7 @@ static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, 
     dim3 grid((G.nx + TX - 1) / TX, (G.nz + TZ - 1) / TZ, 3);
     const size_t sm = sizeof(T) * ((TZ + 2 * HALO) * (TX + 2 * HALO) + TZ * (TX + 2 * R) +
                                    (TZ + 2 * R) * TX + (TX + 2 * R) * (TZ + 2 * R));
-    static bool configured = false;
+    static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
     if (!configured) {
         cudaError_t e;
         if ((e = set_smem(cheb2d<T, SMAG, 1, 1, TX, TZ>, sm)) != cudaSuccess) return e;

@@ -18,6 +18,8 @@
 // assembles fluxes, diffusion and point-wise terms for the outputs.
 #include <math.h>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -716,7 +718,7 @@ static cudaError_t launch_s3(const Geo& G, const T* u, const T* v, const T* Fu, 
     constexpr int TX = FTile<T>::TX, TY = FTile<T>::TY, TZ = FTile<T>::TZ;
     using B = Box<TX, TY, TZ>;
     const size_t sm = sizeof(T) * (5 * B::PL + 5 * B::AS);
-    static bool configured = false;
+    static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
     if (!configured) {
         cudaError_t e = set_smem(stencil3d<T, MODE, SMAG, TX, TY, TZ>, sm);
         if (e != cudaSuccess) return e;
@@ -755,7 +757,7 @@ static cudaError_t launch_jvd3(const Geo& G, const T* u, const T* v, T* out, Ctl
     constexpr int TX = DTile<T>::TX, TY = DTile<T>::TY, TZ = DTile<T>::TZ;
     using B = Box<TX, TY, TZ>;
     const size_t sm = sizeof(T) * (10 * B::PL + 10 * B::AS);
-    static bool configured = false;
+    static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
     if (!configured) {
         cudaError_t e = set_smem(jv_diff3d<T, SMAG, TX, TY, TZ>, sm);
         if (e != cudaSuccess) return e;
@@ -791,7 +793,7 @@ static cudaError_t launch_pc3(const Geo& G, int sweeps, const T* r, T* z, T* za,
     constexpr int TX = CTile<T>::TX, TY = CTile<T>::TY, TZ = CTile<T>::TZ;
     using B = Box<TX, TY, TZ>;
     const size_t sm = sizeof(T) * (B::PL + 2 * B::AS);
-    static bool configured = false;
+    static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
     if (!configured) {
         cudaError_t e;
         if ((e = set_smem(cheb3d<T, SMAG, 1, 1, TX, TY, TZ>, sm)) != cudaSuccess) return e;

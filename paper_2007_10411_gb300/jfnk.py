@@ -29,6 +29,7 @@ EXPORTS = (
     "jfnk_jv", "jfnk_precond_apply", "jfnk_step", "jfnk_step_host", "jfnk_budgets",
     "jfnk_get_launch_count", "jfnk_status_str", "jfnk_kernel_timing", "jfnk_kernel_timing_read",
     "jfnk_budgets_static", "jfnk_autotune", "jfnk_set_tiles",
+    "jfnk_create_batch", "jfnk_destroy_batch", "jfnk_batch_handle", "jfnk_step_batch",
 )
 
 KERNEL_FAMILIES = ("arnoldi_a", "arnoldi_b", "arnoldi_c", "jv", "precond", "residual")
@@ -111,6 +112,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.jfnk_budgets_static.argtypes = [ctypes.POINTER(Grid), P, P, P]
     lib.jfnk_autotune.argtypes = [P, P, ctypes.POINTER(ctypes.c_int)]
     lib.jfnk_set_tiles.argtypes = [P, I, I]
+    lib.jfnk_create_batch.argtypes = [I, ctypes.POINTER(Grid), ctypes.POINTER(Strat), ctypes.POINTER(Sgs),
+                                      ctypes.POINTER(Opts), P, ctypes.POINTER(P)]
+    lib.jfnk_destroy_batch.argtypes = [P]
+    lib.jfnk_batch_handle.argtypes = [P, I, ctypes.POINTER(P)]
+    lib.jfnk_step_batch.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(Stats), ctypes.POINTER(I)]
     lib.jfnk_status_str.argtypes = [I]
     lib.jfnk_status_str.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -254,3 +260,48 @@ class Solver:
         c = ctypes.c_longlong(0)
         _check(self.lib.jfnk_get_launch_count(self.h, ctypes.byref(c)), "jfnk_get_launch_count")
         return c.value
+
+
+class Batch:
+    """Independent grids stepped together (one handle and stream per instance)."""
+
+    def __init__(self, cases, stream=None):
+        import torch
+        self.lib = load_library()
+        self.cases = list(cases)
+        n = len(self.cases)
+        structs = [structs_from_case(c) for c in self.cases]
+        arrs = [(t * n)(*[s[k] for s in structs]) for k, t in enumerate((Grid, Strat, Sgs, Opts))]
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        b = ctypes.c_void_p()
+        _check(self.lib.jfnk_create_batch(n, arrs[0], arrs[1], arrs[2], arrs[3], sp, ctypes.byref(b)),
+               "jfnk_create_batch")
+        self.b = b
+        self.n = n
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.jfnk_destroy_batch(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_surface_flux(self, i: int, H):
+        h = ctypes.c_void_p()
+        _check(self.lib.jfnk_batch_handle(self.b, i, ctypes.byref(h)), "jfnk_batch_handle")
+        _check(self.lib.jfnk_set_surface_flux(h, None if H is None else _ptr(H)), "jfnk_set_surface_flux")
+
+    def step(self, states) -> list:
+        ptrs = (ctypes.c_void_p * self.n)(*[_ptr(u) for u in states])
+        stats = (Stats * self.n)()
+        status = (ctypes.c_int * self.n)()
+        _check(self.lib.jfnk_step_batch(self.b, ptrs, stats, status), "jfnk_step_batch",
+               allow=(JFNK_OK, JFNK_ERR_NOT_CONVERGED))
+        return [s.as_dict() for s in stats]

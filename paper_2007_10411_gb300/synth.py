@@ -147,6 +147,19 @@ def case(name: str) -> dict:
     raise KeyError(name)
 
 
+def uhi_batch(n: int = 16, nx0: int = 512, nz0: int = 128) -> list:
+    """Batched urban heat island: instance i has nx = nx0 (1 + i mod 4), nz = nz0 (1 + i // 8)
+    and H0 = 25 (930/25)^(i/(n-1)) W/m^2 (log-spaced), 100 km x 2 km, 20 km-wide urban patch."""
+    out = []
+    for i in range(n):
+        nx = nx0 * (1 + i % 4)
+        nz = nz0 * (1 + i // 8)
+        c = case("uhi_%dx%d" % (nx, nz))
+        c["init"]["H0"] = 25.0 * (930.0 / 25.0) ** (i / max(n - 1, 1))
+        out.append(c)
+    return out
+
+
 def with_options(c: dict, **kw) -> dict:
     """Deep copy of a case with some entries replaced (keys searched in every section)."""
     c = copy.deepcopy(c)
