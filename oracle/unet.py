@@ -1,0 +1,204 @@
+"""Learned right preconditioner: float64 reference of the 3-level linear U-Net.
+
+TEST INFRASTRUCTURE (oracle only).  The learned preconditioner is not in the
+paper (its Section 2.5.2 preconditioner is the physics-based field-block
+one); this module fixes what the CUDA network computes so that its forward
+pass, its gradients and its training pairs can be checked:
+
+* network (no biases, no activations, zero padding, rows = z, columns = x):
+    x (4 field planes; the GPU pads them to 16 channels with zeros)
+    L0a 3x3 16->16, L0b 3x3 16->16 = s0, 2x2 average pool
+    L1a 3x3 16->32, L1b 3x3 32->32 = s1, 2x2 average pool
+    L2a 3x3 32->64, L2b 3x3 64->64, nearest upsampling x2, concat [up, s1] (96)
+    L1c 3x3 96->32, nearest upsampling x2, concat [up, s0] (48)
+    L0c 3x3 48->16, L0d 1x1 16->16; the first 4 output channels are N(x)
+* weights: one flat vector, layers in the order above, each layer stored as
+  [tap][cout][cin] with tap = ky * k + kx reading the input at offset
+  (ky - k // 2, kx - k // 2);
+* loss of a pair (x, t): L = 1/2 ||N(x) - t||^2 / ||t||^2, and its gradient
+  with respect to the flat weight vector (plain chain rule);
+* training pairs from one Newton correction (Section 2.5.1, Eq. jv): with
+  b = -W R(u_k), beta = ||b|| and x_hat the scaled correction GMRES returned,
+  X = b / beta and T = x_hat / beta - M^{-1} X, M^{-1} the field-block
+  preconditioner of Section 2.5.2 at u_k, so that a network with N(X) = T
+  makes the right preconditioner P = M^{-1} + N reproduce the correction;
+* the preconditioner itself: P v = M^{-1} v + N(v).
+
+Everything is whole-array numpy in float64 following these definitions, with
+no blocking or fusion.  Pins (tests/test_oracle_unet.py): single layers
+against scipy.signal.correlate2d, an identity network, the adjoint identities
+of pooling and upsampling, and the gradient against central differences.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# (name, cin, cout, kernel size)
+LAYERS = (
+    ("L0a", 16, 16, 3), ("L0b", 16, 16, 3),
+    ("L1a", 16, 32, 3), ("L1b", 32, 32, 3),
+    ("L2a", 32, 64, 3), ("L2b", 64, 64, 3),
+    ("L1c", 96, 32, 3), ("L0c", 48, 16, 3), ("L0d", 16, 16, 1),
+)
+NFIELDS = 4
+IN_CH = 16
+
+
+def layer_sizes():
+    return [k * k * co * ci for (_, ci, co, k) in LAYERS]
+
+
+def num_weights() -> int:
+    return int(sum(layer_sizes()))
+
+
+def split_weights(flat: np.ndarray) -> dict:
+    """Flat vector -> {name: array [k*k, cout, cin]}."""
+    flat = np.asarray(flat, dtype=np.float64)
+    assert flat.size == num_weights()
+    out, o = {}, 0
+    for (name, ci, co, k), sz in zip(LAYERS, layer_sizes()):
+        out[name] = flat[o:o + sz].reshape(k * k, co, ci)
+        o += sz
+    return out
+
+
+def join_weights(ws: dict) -> np.ndarray:
+    return np.concatenate([ws[name].reshape(-1) for (name, _, _, _) in LAYERS])
+
+
+# ------------------------------------------------------------------ layers
+def conv(x: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """out[co, y, x] = sum_tap sum_ci w[tap, co, ci] x[ci, y + dy, x + dx], zero outside."""
+    kk, co, ci = w.shape
+    k = int(round(np.sqrt(kk)))
+    hp = k // 2
+    C, H, W = x.shape
+    assert C == ci
+    xp = np.zeros((C, H + 2 * hp, W + 2 * hp))
+    xp[:, hp:hp + H, hp:hp + W] = x
+    out = np.zeros((co, H, W))
+    for tap in range(kk):
+        ky, kx = divmod(tap, k)
+        shifted = xp[:, ky:ky + H, kx:kx + W]          # x[ci, y + ky - hp, x + kx - hp]
+        out += np.einsum("oc,chw->ohw", w[tap], shifted)
+    return out
+
+
+def conv_grads(x: np.ndarray, w: np.ndarray, dout: np.ndarray):
+    """Gradients of <dout, conv(x, w)> w.r.t. x (scatter form) and w."""
+    kk, co, ci = w.shape
+    k = int(round(np.sqrt(kk)))
+    hp = k // 2
+    C, H, W = x.shape
+    xp = np.zeros((C, H + 2 * hp, W + 2 * hp))
+    xp[:, hp:hp + H, hp:hp + W] = x
+    dxp = np.zeros_like(xp)
+    dw = np.zeros_like(w)
+    for tap in range(kk):
+        ky, kx = divmod(tap, k)
+        shifted = xp[:, ky:ky + H, kx:kx + W]
+        dw[tap] = np.einsum("ohw,chw->oc", dout, shifted)
+        dxp[:, ky:ky + H, kx:kx + W] += np.einsum("oc,ohw->chw", w[tap], dout)
+    return dxp[:, hp:hp + H, hp:hp + W], dw
+
+
+def pool2(x: np.ndarray) -> np.ndarray:
+    """2x2 average."""
+    C, H, W = x.shape
+    return x.reshape(C, H // 2, 2, W // 2, 2).mean(axis=(2, 4))
+
+
+def pool2_adjoint(d: np.ndarray) -> np.ndarray:
+    return np.repeat(np.repeat(d, 2, axis=1), 2, axis=2) * 0.25
+
+
+def up2(x: np.ndarray) -> np.ndarray:
+    """Nearest-neighbour upsampling x2."""
+    return np.repeat(np.repeat(x, 2, axis=1), 2, axis=2)
+
+
+def up2_adjoint(d: np.ndarray) -> np.ndarray:
+    C, H, W = d.shape
+    return d.reshape(C, H // 2, 2, W // 2, 2).sum(axis=(2, 4))
+
+
+# ----------------------------------------------------------------- network
+def forward(flat: np.ndarray, X: np.ndarray):
+    """N(X) for X of shape (4, nz, nx); returns (y (4, nz, nx), activations)."""
+    w = split_weights(flat)
+    H, W = X.shape[1:]
+    assert H % 4 == 0 and W % 4 == 0
+    a = {}
+    a["x0"] = np.zeros((IN_CH, H, W))
+    a["x0"][:NFIELDS] = X
+    a["h0a"] = conv(a["x0"], w["L0a"])
+    a["s0"] = conv(a["h0a"], w["L0b"])
+    a["p1"] = pool2(a["s0"])
+    a["h1a"] = conv(a["p1"], w["L1a"])
+    a["s1"] = conv(a["h1a"], w["L1b"])
+    a["p2"] = pool2(a["s1"])
+    a["h2a"] = conv(a["p2"], w["L2a"])
+    a["h2b"] = conv(a["h2a"], w["L2b"])
+    a["cat1"] = np.concatenate([up2(a["h2b"]), a["s1"]])
+    a["h1c"] = conv(a["cat1"], w["L1c"])
+    a["cat0"] = np.concatenate([up2(a["h1c"]), a["s0"]])
+    a["h0c"] = conv(a["cat0"], w["L0c"])
+    a["out"] = conv(a["h0c"], w["L0d"])
+    return a["out"][:NFIELDS].copy(), a
+
+
+def backward(flat: np.ndarray, a: dict, dy: np.ndarray) -> np.ndarray:
+    """Flat gradient of <dy, N(X)> given the activations of forward()."""
+    w = split_weights(flat)
+    g = {}
+    dout = np.zeros_like(a["out"])
+    dout[:NFIELDS] = dy
+    d_h0c, g["L0d"] = conv_grads(a["h0c"], w["L0d"], dout)
+    d_cat0, g["L0c"] = conv_grads(a["cat0"], w["L0c"], d_h0c)
+    d_h1c = up2_adjoint(d_cat0[:32])
+    d_s0 = d_cat0[32:].copy()
+    d_cat1, g["L1c"] = conv_grads(a["cat1"], w["L1c"], d_h1c)
+    d_h2b = up2_adjoint(d_cat1[:64])
+    d_s1 = d_cat1[64:].copy()
+    d_h2a, g["L2b"] = conv_grads(a["h2a"], w["L2b"], d_h2b)
+    d_p2, g["L2a"] = conv_grads(a["p2"], w["L2a"], d_h2a)
+    d_s1 += pool2_adjoint(d_p2)
+    d_h1a, g["L1b"] = conv_grads(a["h1a"], w["L1b"], d_s1)
+    d_p1, g["L1a"] = conv_grads(a["p1"], w["L1a"], d_h1a)
+    d_s0 += pool2_adjoint(d_p1)
+    d_h0a, g["L0b"] = conv_grads(a["h0a"], w["L0b"], d_s0)
+    _, g["L0a"] = conv_grads(a["x0"], w["L0a"], d_h0a)
+    return join_weights(g)
+
+
+def apply(flat: np.ndarray, X: np.ndarray) -> np.ndarray:
+    return forward(flat, X)[0]
+
+
+def loss(flat: np.ndarray, X: np.ndarray, T: np.ndarray) -> float:
+    y = apply(flat, X)
+    return 0.5 * float(np.sum((y - T) ** 2)) / float(np.sum(T * T))
+
+
+def loss_grad(flat: np.ndarray, X: np.ndarray, T: np.ndarray):
+    """(L, dL/dw) for L = 1/2 ||N(X) - T||^2 / ||T||^2."""
+    y, a = forward(flat, X)
+    tn2 = float(np.sum(T * T))
+    r = y - T
+    return 0.5 * float(np.sum(r * r)) / tn2, backward(flat, a, r / tn2)
+
+
+# ------------------------------------------------------ preconditioner use
+def training_pair(model, U: np.ndarray, R: np.ndarray, xhat: np.ndarray, sweeps: int):
+    """(X, T) of one Newton correction: X = -W R / beta, T = xhat / beta - M^{-1} X."""
+    b = -model.scale(R)
+    beta = float(np.sqrt(np.sum(b * b)))
+    X = b / beta
+    T = xhat / beta - model.precond(U, X, sweeps)
+    return X, T
+
+
+def precond(model, flat: np.ndarray, U: np.ndarray, V: np.ndarray, sweeps: int) -> np.ndarray:
+    """P v = M^{-1} v + N(v) (scaled units)."""
+    return model.precond(U, V, sweeps) + apply(flat, V)

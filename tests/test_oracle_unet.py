@@ -1,0 +1,123 @@
+"""Pins of the float64 U-Net oracle (learned right preconditioner).
+
+Each check ties the oracle to something outside itself: scipy's 2-D
+correlation, closed-form outputs of hand-set networks, the adjoint identities
+of the resampling operators, and exact central differences (the loss is
+quadratic in every single weight, so a central difference reproduces the
+partial derivative up to rounding).
+"""
+import numpy as np
+import pytest
+
+scipy_signal = pytest.importorskip("scipy.signal")
+
+from oracle import unet as U  # noqa: E402
+
+
+def _rng(seed=7):
+    return np.random.default_rng(seed)
+
+
+def _random_weights(rng, scale=1.0):
+    parts = []
+    for (_, ci, co, k) in U.LAYERS:
+        parts.append(rng.standard_normal(k * k * co * ci) * scale / np.sqrt(k * k * ci))
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("k,ci,co", [(3, 5, 4), (1, 3, 2)])
+def test_conv_matches_scipy_correlate(k, ci, co):
+    rng = _rng(1)
+    x = rng.standard_normal((ci, 9, 11))
+    w = rng.standard_normal((k * k, co, ci))
+    out = U.conv(x, w)
+    ref = np.zeros((co, 9, 11))
+    for o in range(co):
+        for c in range(ci):
+            K = w[:, o, c].reshape(k, k)
+            ref[o] += scipy_signal.correlate2d(x[c], K, mode="same", boundary="fill", fillvalue=0.0)
+    np.testing.assert_allclose(out, ref, rtol=1e-13, atol=1e-13)
+
+
+def _eye_tap(k, co, ci, shift_in=0):
+    w = np.zeros((k * k, co, ci))
+    c = (k * k) // 2
+    for i in range(min(co, ci - shift_in)):
+        w[c, i, i + shift_in] = 1.0
+    return w
+
+
+def test_identity_network_is_identity():
+    rng = _rng(2)
+    ws = {name: rng.standard_normal((k * k, co, ci)) for (name, ci, co, k) in U.LAYERS}
+    ws["L0a"] = _eye_tap(3, 16, 16)
+    ws["L0b"] = _eye_tap(3, 16, 16)
+    ws["L1c"] = np.zeros_like(ws["L1c"])          # coarse path off
+    ws["L0c"] = _eye_tap(3, 16, 48, shift_in=32)  # read s0 only
+    ws["L0d"] = _eye_tap(1, 16, 16)
+    X = rng.standard_normal((4, 16, 24))
+    y = U.apply(U.join_weights(ws), X)
+    np.testing.assert_allclose(y, X, rtol=0, atol=1e-14)
+
+
+def test_coarse_path_is_4x4_block_mean():
+    rng = _rng(3)
+    ws = {name: np.zeros((k * k, co, ci)) for (name, ci, co, k) in U.LAYERS}
+    for name in ("L0a", "L0b", "L1a", "L1b", "L2a", "L2b", "L1c", "L0c"):
+        _, ci, co, k = next(l for l in U.LAYERS if l[0] == name)
+        ws[name] = _eye_tap(k, co, ci)               # first channels straight through
+    ws["L0d"] = _eye_tap(1, 16, 16)
+    X = rng.standard_normal((4, 8, 12))
+    y = U.apply(U.join_weights(ws), X)
+    ref = X.reshape(4, 2, 4, 3, 4).mean(axis=(2, 4))
+    ref = np.repeat(np.repeat(ref, 4, axis=1), 4, axis=2)
+    np.testing.assert_allclose(y, ref, rtol=0, atol=1e-14)
+
+
+def test_resampling_adjoints():
+    rng = _rng(4)
+    a = rng.standard_normal((3, 8, 6))
+    b = rng.standard_normal((3, 4, 3))
+    assert abs(np.sum(U.pool2(a) * b) - np.sum(a * U.pool2_adjoint(b))) < 1e-13
+    assert abs(np.sum(U.up2(b) * a) - np.sum(b * U.up2_adjoint(a))) < 1e-13
+    # pool(up(b)) = b
+    np.testing.assert_allclose(U.pool2(U.up2(b)), b, atol=1e-15)
+
+
+def test_linearity():
+    rng = _rng(5)
+    w = _random_weights(rng)
+    X1 = rng.standard_normal((4, 8, 8))
+    X2 = rng.standard_normal((4, 8, 8))
+    lhs = U.apply(w, 2.0 * X1 - 3.0 * X2)
+    rhs = 2.0 * U.apply(w, X1) - 3.0 * U.apply(w, X2)
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-12, atol=1e-12)
+
+
+def test_gradient_matches_central_differences():
+    rng = _rng(6)
+    w = _random_weights(rng)
+    X = rng.standard_normal((4, 8, 8))
+    T = rng.standard_normal((4, 8, 8))
+    L, g = U.loss_grad(w, X, T)
+    assert abs(L - U.loss(w, X, T)) < 1e-14 * max(1.0, abs(L))
+    sizes = U.layer_sizes()
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    for li in range(len(U.LAYERS)):
+        for idx in rng.integers(offs[li], offs[li + 1], size=4):
+            h = 1e-3
+            wp = w.copy(); wp[idx] += h
+            wm = w.copy(); wm[idx] -= h
+            fd = (U.loss(wp, X, T) - U.loss(wm, X, T)) / (2 * h)
+            assert abs(fd - g[idx]) <= 1e-8 * (abs(g[idx]) + np.max(np.abs(g[offs[li]:offs[li + 1]]))), \
+                (U.LAYERS[li][0], idx, fd, g[idx])
+
+
+def test_gradient_zero_at_exact_fit():
+    rng = _rng(8)
+    w = _random_weights(rng)
+    X = rng.standard_normal((4, 8, 8))
+    T = U.apply(w, X)
+    L, g = U.loss_grad(w, X, T)
+    assert L < 1e-28
+    assert np.max(np.abs(g)) < 1e-13
