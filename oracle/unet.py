@@ -15,19 +15,30 @@ pass, its gradients and its training pairs can be checked:
 * weights: one flat vector, layers in the order above, each layer stored as
   [tap][cout][cin] with tap = ky * k + kx reading the input at offset
   (ky - k // 2, kx - k // 2);
-* loss of a pair (x, t): L = 1/2 ||N(x) - t||^2 / ||t||^2, and its gradient
-  with respect to the flat weight vector (plain chain rule);
-* training pairs from one Newton correction (Section 2.5.1, Eq. jv): with
-  b = -W R(u_k), beta = ||b|| and x_hat the scaled correction GMRES returned,
-  X = b / beta and T = x_hat / beta - M^{-1} X, M^{-1} the field-block
-  preconditioner of Section 2.5.2 at u_k, so that a network with N(X) = T
-  makes the right preconditioner P = M^{-1} + N reproduce the correction;
+* field balance: the convolutions act in balanced units, N(x) = B^-1 net(B x)
+  with B = diag(1, 1, s_theta / Theta_b, s_p / P_b), s_* the scales of W and
+  Theta_b = s_u sqrt(|beta| theta0 / g), P_b = s_u sqrt(gamma_p pbar / theta0):
+  the units in which the buoyancy pair (g theta / theta0 in the w equation,
+  -beta w in the theta equation) and the acoustic pair (-theta0 grad p, and
+  -gamma_p pbar div u, Eqs. ch2_28-ch2_30) have equal coefficients both ways;
+* loss of a pair (x, t): L = 1/2 ||B (N(x) - t)||^2 / ||B x||^2, and its
+  gradient with respect to the flat weight vector (plain chain rule);
+* training pairs (Section 2.5.1, Eq. jv), both giving an input X and the
+  correction T that P = M^{-1} + N should add to the field-block
+  preconditioner M^{-1} of Section 2.5.2 (frozen at u_k):
+  - Arnoldi step: z_j = M^{-1} v_j and w = J_hat z_j, so J_hat^{-1} w = z_j
+    exactly: X = w / ||w||, T = (z_j - M^{-1} w) / ||w||;
+  - Newton correction: b = -W R(u_k), beta = ||b||, x_hat the scaled
+    correction GMRES returned: X = b / beta, T = x_hat / beta - M^{-1} X;
 * the preconditioner itself: P v = M^{-1} v + N(v).
 
 Everything is whole-array numpy in float64 following these definitions, with
 no blocking or fusion.  Pins (tests/test_oracle_unet.py): single layers
-against scipy.signal.correlate2d, an identity network, the adjoint identities
-of pooling and upsampling, and the gradient against central differences.
+against scipy.signal.correlate2d, an identity network (with and without a
+balance), a 4x4 block-mean network, the adjoint identities of pooling and
+upsampling, the gradient against exact central differences, the balance
+making the linearised acoustic and buoyancy couplings symmetric, and the
+training-pair identities on a linear system solved exactly.
 """
 from __future__ import annotations
 
@@ -123,15 +134,36 @@ def up2_adjoint(d: np.ndarray) -> np.ndarray:
     return d.reshape(C, H // 2, 2, W // 2, 2).sum(axis=(2, 4))
 
 
+def balance(case: dict) -> np.ndarray:
+    """Per-field factors B (velocity components, theta, p) of a 2-D case."""
+    st, op = case["strat"], case["opts"]
+    su = op["scale_u"]
+    b = np.ones(NFIELDS)
+    if st["beta"] != 0.0 and st["g"] > 0.0:
+        b[2] = op["scale_theta"] / (su * np.sqrt(abs(st["beta"]) * st["theta0"] / st["g"]))
+    if st["gamma_p"] * st["pbar"] > 0.0:
+        b[3] = op["scale_p"] / (su * np.sqrt(st["gamma_p"] * st["pbar"] / st["theta0"]))
+    return b
+
+
+def _b(B, ndim=3):
+    B = np.ones(NFIELDS) if B is None else np.asarray(B, dtype=np.float64)
+    return B.reshape((NFIELDS,) + (1,) * (ndim - 1))
+
+
 # ----------------------------------------------------------------- network
-def forward(flat: np.ndarray, X: np.ndarray):
-    """N(X) for X of shape (4, nz, nx); returns (y (4, nz, nx), activations)."""
+def forward(flat: np.ndarray, X: np.ndarray, B=None):
+    """N(X) for X of shape (4, nz, nx); returns (y (4, nz, nx), activations).
+
+    The activations hold the raw network run on B X (balanced units); y is
+    B^-1 times its first four output channels.
+    """
     w = split_weights(flat)
     H, W = X.shape[1:]
     assert H % 4 == 0 and W % 4 == 0
     a = {}
     a["x0"] = np.zeros((IN_CH, H, W))
-    a["x0"][:NFIELDS] = X
+    a["x0"][:NFIELDS] = _b(B) * X
     a["h0a"] = conv(a["x0"], w["L0a"])
     a["s0"] = conv(a["h0a"], w["L0b"])
     a["p1"] = pool2(a["s0"])
@@ -145,11 +177,11 @@ def forward(flat: np.ndarray, X: np.ndarray):
     a["cat0"] = np.concatenate([up2(a["h1c"]), a["s0"]])
     a["h0c"] = conv(a["cat0"], w["L0c"])
     a["out"] = conv(a["h0c"], w["L0d"])
-    return a["out"][:NFIELDS].copy(), a
+    return a["out"][:NFIELDS] / _b(B), a
 
 
 def backward(flat: np.ndarray, a: dict, dy: np.ndarray) -> np.ndarray:
-    """Flat gradient of <dy, N(X)> given the activations of forward()."""
+    """Flat gradient of <dy, raw output channels 0..3> given the activations of forward()."""
     w = split_weights(flat)
     g = {}
     dout = np.zeros_like(a["out"])
@@ -172,25 +204,27 @@ def backward(flat: np.ndarray, a: dict, dy: np.ndarray) -> np.ndarray:
     return join_weights(g)
 
 
-def apply(flat: np.ndarray, X: np.ndarray) -> np.ndarray:
-    return forward(flat, X)[0]
+def apply(flat: np.ndarray, X: np.ndarray, B=None) -> np.ndarray:
+    return forward(flat, X, B)[0]
 
 
-def loss(flat: np.ndarray, X: np.ndarray, T: np.ndarray) -> float:
-    y = apply(flat, X)
-    return 0.5 * float(np.sum((y - T) ** 2)) / float(np.sum(T * T))
+def loss(flat: np.ndarray, X: np.ndarray, T: np.ndarray, B=None) -> float:
+    b = _b(B)
+    d = b * (apply(flat, X, B) - T)
+    return 0.5 * float(np.sum(d * d)) / float(np.sum((b * X) ** 2))
 
 
-def loss_grad(flat: np.ndarray, X: np.ndarray, T: np.ndarray):
-    """(L, dL/dw) for L = 1/2 ||N(X) - T||^2 / ||T||^2."""
-    y, a = forward(flat, X)
-    tn2 = float(np.sum(T * T))
-    r = y - T
-    return 0.5 * float(np.sum(r * r)) / tn2, backward(flat, a, r / tn2)
+def loss_grad(flat: np.ndarray, X: np.ndarray, T: np.ndarray, B=None):
+    """(L, dL/dw) for L = 1/2 ||B (N(X) - T)||^2 / ||B X||^2."""
+    b = _b(B)
+    y, a = forward(flat, X, B)
+    xn2 = float(np.sum((b * X) ** 2))
+    r = b * (y - T)                      # raw output minus B T
+    return 0.5 * float(np.sum(r * r)) / xn2, backward(flat, a, r / xn2)
 
 
 # ------------------------------------------------------ preconditioner use
-def training_pair(model, U: np.ndarray, R: np.ndarray, xhat: np.ndarray, sweeps: int):
+def newton_pair(model, U: np.ndarray, R: np.ndarray, xhat: np.ndarray, sweeps: int):
     """(X, T) of one Newton correction: X = -W R / beta, T = xhat / beta - M^{-1} X."""
     b = -model.scale(R)
     beta = float(np.sqrt(np.sum(b * b)))
@@ -199,6 +233,12 @@ def training_pair(model, U: np.ndarray, R: np.ndarray, xhat: np.ndarray, sweeps:
     return X, T
 
 
-def precond(model, flat: np.ndarray, U: np.ndarray, V: np.ndarray, sweeps: int) -> np.ndarray:
+def arnoldi_pair(model, U: np.ndarray, z: np.ndarray, w: np.ndarray, sweeps: int):
+    """(X, T) of one Arnoldi step with w = J_hat z: X = w / ||w||, T = (z - M^{-1} w) / ||w||."""
+    nw = float(np.sqrt(np.sum(w * w)))
+    return w / nw, (z - model.precond(U, w, sweeps)) / nw
+
+
+def precond(model, flat: np.ndarray, U: np.ndarray, V: np.ndarray, sweeps: int, B=None) -> np.ndarray:
     """P v = M^{-1} v + N(v) (scaled units)."""
-    return model.precond(U, V, sweeps) + apply(flat, V)
+    return model.precond(U, V, sweeps) + apply(flat, V, B)

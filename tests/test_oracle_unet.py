@@ -121,3 +121,107 @@ def test_gradient_zero_at_exact_fit():
     L, g = U.loss_grad(w, X, T)
     assert L < 1e-28
     assert np.max(np.abs(g)) < 1e-13
+
+
+def test_identity_network_with_balance_is_identity():
+    rng = _rng(9)
+    ws = {name: np.zeros((k * k, co, ci)) for (name, ci, co, k) in U.LAYERS}
+    ws["L0a"] = _eye_tap(3, 16, 16)
+    ws["L0b"] = _eye_tap(3, 16, 16)
+    ws["L0c"] = _eye_tap(3, 16, 48, shift_in=32)
+    ws["L0d"] = _eye_tap(1, 16, 16)
+    X = rng.standard_normal((4, 8, 12))
+    B = np.array([1.0, 1.0, 0.3, 8e-4])
+    np.testing.assert_allclose(U.apply(U.join_weights(ws), X, B), X, rtol=1e-14, atol=1e-14)
+    # the raw network sees B X: a network that only scales by 2 returns 2 X
+    ws["L0d"] = 2.0 * ws["L0d"]
+    np.testing.assert_allclose(U.apply(U.join_weights(ws), X, B), 2.0 * X, rtol=1e-14, atol=1e-14)
+
+
+def test_gradient_with_balance_matches_central_differences():
+    rng = _rng(10)
+    w = _random_weights(rng)
+    B = np.array([1.0, 1.0, 0.3, 8e-4])
+    X = rng.standard_normal((4, 8, 8))
+    T = rng.standard_normal((4, 8, 8))
+    L, g = U.loss_grad(w, X, T, B)
+    assert abs(L - U.loss(w, X, T, B)) < 1e-14 * max(1.0, L)
+    for idx in rng.integers(0, w.size, size=12):
+        h = 1e-3
+        wp = w.copy(); wp[idx] += h
+        wm = w.copy(); wm[idx] -= h
+        fd = (U.loss(wp, X, T, B) - U.loss(wm, X, T, B)) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-8 * (abs(g[idx]) + np.max(np.abs(g))), (idx, fd, g[idx])
+
+
+def _linear_rest_model():
+    """Stable thermal at rest with no eddy diffusion: F is linear plus quadratic convection."""
+    from oracle.operators import Model
+    from paper_2007_10411_gb300 import synth
+    c = synth.case("thermal_stable_64x32")
+    c["sgs"] = {"mode": synth.SGS_CONST, "K_M": 0.0, "K_H": 0.0, "Cs": 0.0, "Pr": 1.0}
+    return c, Model(c)
+
+
+def test_balance_makes_acoustic_and_buoyancy_coupling_skew():
+    """In balanced units the field coupling of the linearised F at rest is skew-adjoint.
+
+    J_F e is the central difference of F at u = 0 (exact: F is linear plus a
+    quadratic convection there).  For a velocity-only vector a and a
+    (theta, p)-only vector c, <c, J a> = -<a, J c> holds in the units B W u
+    and fails by orders of magnitude in the units W u.
+    """
+    c, m = _linear_rest_model()
+    shape = (4, 32, 64)
+    rng = _rng(11)
+    Z = np.zeros(shape)
+
+    def JF(e):
+        h = 1e-4
+        return (m.F(Z + h * e) - m.F(Z - h * e)) / (2 * h)
+
+    def J_units(D, x):      # D diag per field: variables y = D u
+        Dr = D.reshape(4, 1, 1)
+        return Dr * JF(x / Dr)
+
+    a = rng.standard_normal(shape); a[2:] = 0.0
+    cc = rng.standard_normal(shape); cc[:2] = 0.0
+    W = 1.0 / m.scales
+    for D, skew in ((U.balance(c) * W, True), (W, False)):
+        lhs = float(np.sum(cc * J_units(D, a)))
+        rhs = -float(np.sum(a * J_units(D, cc)))
+        asym = abs(lhs - rhs) / max(abs(lhs), abs(rhs))
+        if skew:
+            assert asym < 1e-8, asym
+        else:
+            assert asym > 0.5, asym
+
+
+def test_training_pairs_reproduce_the_correction():
+    from oracle.krylov import gmres
+    from paper_2007_10411_gb300 import synth
+    from oracle.operators import Model
+    c = synth.case("thermal_stable_64x32")
+    m = Model(c)
+    sw = c["opts"]["pc_sweeps"]
+    Uk = synth.random_state(c, 5, amp=(0.5, 0.1, 0.002))
+    FU = m.F(Uk)
+    J = lambda v: m.jv_scaled(Uk, FU, v)
+    rng = _rng(12)
+    # Arnoldi pair: M^-1 X + T = z / ||w|| and J of it gives X back
+    z = m.precond(Uk, rng.standard_normal(Uk.shape), sw)
+    w = J(z)
+    X, T = U.arnoldi_pair(m, Uk, z, w, sw)
+    assert abs(np.linalg.norm(X) - 1.0) < 1e-14
+    Y = m.precond(Uk, X, sw) + T
+    np.testing.assert_allclose(Y, z / np.linalg.norm(w), rtol=0, atol=1e-12 * np.max(np.abs(z)) / np.linalg.norm(w))
+    assert np.linalg.norm(J(Y) - X) < 1e-6
+    # Newton pair from a tightly solved correction
+    f = m.rhs_f(Uk - 0.01)
+    R = m.residual(Uk, f)
+    b = -m.scale(R)
+    xhat = gmres(J, b, 30, 1e-10, 20, precond=lambda v: m.precond(Uk, v, sw), flexible=True)
+    X, T = U.newton_pair(m, Uk, R, xhat, sw)
+    # J_hat is a finite-difference product whose step depends on the vector,
+    # so it is linear only to ~1e-6 here: a wrong sign or scale gives O(1)
+    assert np.linalg.norm(J(m.precond(Uk, X, sw) + T) - X) < 1e-4
