@@ -62,7 +62,7 @@ typedef enum {
 enum { JFNK_FREESLIP = 0, JFNK_NOSLIP = 1 };
 enum { JFNK_SGS_CONST = 0, JFNK_SGS_SMAGORINSKY = 1 };
 enum { JFNK_FP64 = 0, JFNK_MIXED = 1 };
-enum { JFNK_PC_NONE = 0, JFNK_PC_BLOCK = 1 };
+enum { JFNK_PC_NONE = 0, JFNK_PC_BLOCK = 1, JFNK_PC_UNET = 2 };
 
 /* Largest Krylov dimension m accepted by jfnk_create. */
 #define JFNK_MAX_KRYLOV 32
@@ -106,7 +106,9 @@ typedef struct {
  * flexible    accepted for compatibility; the library always stores the
  *             preconditioned directions (FGMRES form), identical in exact
  *             arithmetic to right-preconditioned GMRES for a linear M.
- * precond     JFNK_PC_NONE or JFNK_PC_BLOCK (pc_sweeps Chebyshev steps per block).
+ * precond     JFNK_PC_NONE, JFNK_PC_BLOCK (pc_sweeps Chebyshev steps per block)
+ *             or JFNK_PC_UNET (the block preconditioner plus a learned
+ *             correction, see "Learned right preconditioner" below).
  * newton_rtol, newton_atol_factor, eta, max_newton, max_restarts: stopping rules
  *             ||W R|| <= max(rtol ||W R_0||, atol_factor ||W 2u^n/dt||);
  *             GMRES stops at ||W(R + J du)|| <= eta ||W R||.
@@ -129,6 +131,13 @@ typedef struct {
     double res0, res_final, tol;             /* ||W R|| at start / end, threshold   */
     double res_hist[JFNK_MAX_NEWTON + 1];    /* ||W R|| after each correction       */
     int gmres_per_newton[JFNK_MAX_NEWTON];   /* Krylov iterations per correction    */
+    int pc_fallback;                         /* 1: the learned preconditioner failed
+                                                and the step was redone with the
+                                                field-block one (counts above are
+                                                those of the redone step)           */
+    int pc_switches;                         /* Newton corrections whose GMRES solve
+                                                switched from the learned to the
+                                                field-block preconditioner          */
 } jfnk_stats;
 
 /* Budgets of Section 3.1.3 (literal E_k, E_p) plus conservation diagnostics. */
@@ -203,7 +212,8 @@ enum {
     JFNK_KF_JV = 3,          /* Jacobian-vector product stencil             */
     JFNK_KF_PRECOND = 4,     /* preconditioner sweeps (one apply)           */
     JFNK_KF_RESIDUAL = 5,    /* Newton residual stencil (float64)           */
-    JFNK_KF_COUNT = 6
+    JFNK_KF_UNET = 6,        /* learned preconditioner network (one apply)  */
+    JFNK_KF_COUNT = 7
 };
 
 /* Device time and algorithmic bytes of one kernel family. */
@@ -250,6 +260,97 @@ jfnk_status jfnk_batch_handle(jfnk_batch* b, int i, jfnk_handle** out);
  * JFNK_ERR_NOT_CONVERGED.  Blocks the calling thread until all instances
  * finish; the caller's stream waits for them. */
 jfnk_status jfnk_step_batch(jfnk_batch* b, double* const* u, jfnk_stats* stats, jfnk_status* status);
+
+/* ----------------------------------------------- learned preconditioner
+ * Not in the paper (its preconditioner is the field-block one of Section
+ * 2.5.2, which stays the fallback).  A linear convolutional U-Net N acts on
+ * the four scaled field planes of a Krylov vector and corrects the block
+ * preconditioner M: with precond = JFNK_PC_UNET the flexible-GMRES direction
+ * of v is z = M^-1 v + N(v).
+ *
+ * Network (no biases, no activations, zero padding; rows z, columns x):
+ *   L0a 3x3 16->16 (input: the 4 planes, zero-padded to 16 channels),
+ *   L0b 3x3 16->16 = s0, 2x2 average pool, L1a 3x3 16->32, L1b 3x3 32->32
+ *   = s1, 2x2 average pool, L2a 3x3 32->64, L2b 3x3 64->64, nearest
+ *   upsampling, concat [up, s1], L1c 3x3 96->32, nearest upsampling, concat
+ *   [up, s0], L0c 3x3 48->16, L0d 1x1 16->16 (first 4 channels = N(v)).
+ * Flat weight order (float32): layers in that order, each [tap][cout][cin]
+ * with tap = ky * k + kx reading the input at offset (ky - k/2, kx - k/2).
+ * Convolutions run on the tensor cores with bfloat16 operands and float32
+ * accumulation; training keeps float32 master weights (Adam).
+ *
+ * The convolutions work in balanced units: N(v) = B^-1 net(B v) with
+ * B = diag(1, 1, s_theta / Theta_b, s_p / P_b), s_* = scale_* of jfnk_opts,
+ * Theta_b = s_u sqrt(|beta| theta0 / g) and P_b = s_u sqrt(gamma_p pbar /
+ * theta0) (factor 1 where beta or gamma_p pbar is 0): the units in which the
+ * linearised buoyancy and acoustic couplings of Eqs. ch2_28-ch2_30 are
+ * skew-adjoint, so that errors of the network are weighted as the Jacobian
+ * weights them.
+ *
+ * Training pairs come from the solver's own GMRES solves (Section 2.5.1),
+ * the field-block M frozen at the Newton iterate u_k:
+ *   JFNK_PAIRS_ARNOLDI  every Arnoldi step: w = J_hat z_j is an exact inverse
+ *                       pair, X = w / ||w||, T = (z_j - M^-1 w) / ||w||;
+ *   JFNK_PAIRS_NEWTON   every converged Newton correction: b = -W R(u_k),
+ *                       beta = ||b||, x_hat the scaled correction,
+ *                       X = b / beta, T = x_hat / beta - M^-1 X.
+ * The loss of a pair is 1/2 ||B (N(X) - T)||^2 / ||B X||^2.
+ *
+ * Only 2-D handles with precision JFNK_MIXED and nx, nz multiples of 32
+ * accept these calls (and precond = JFNK_PC_UNET); others get
+ * JFNK_ERR_UNSUPPORTED.  Safeguards: a GMRES cycle of m steps with the learned
+ * preconditioner that reduces the residual by less than a factor 2 hands the
+ * rest of that Newton solve to the field-block preconditioner (restarting from
+ * the correction reached; jfnk_stats.pc_switches counts such solves), and a
+ * step with JFNK_PC_UNET that ends in JFNK_ERR_NOT_CONVERGED,
+ * JFNK_ERR_BREAKDOWN or JFNK_ERR_NAN is redone from u^n with the field-block
+ * preconditioner (jfnk_stats.pc_fallback = 1).
+ * Until a network is attached JFNK_PC_UNET behaves as JFNK_PC_BLOCK. */
+
+/* Attach a network with seeded random weights (N(0, 1/fan-in), last layer
+ * zero so that N = 0 until trained); replaces an attached one. */
+jfnk_status jfnk_unet_init(jfnk_handle* h, unsigned long long seed);
+
+/* Number of float32 weights of the network. */
+jfnk_status jfnk_unet_num_weights(jfnk_handle* h, size_t* count);
+
+/* Copy the float32 master weights to / from host memory (count must equal
+ * jfnk_unet_num_weights; setting resets the Adam moments). */
+jfnk_status jfnk_unet_get_weights(jfnk_handle* h, float* host, size_t count);
+jfnk_status jfnk_unet_set_weights(jfnk_handle* h, const float* host, size_t count);
+
+enum { JFNK_PAIRS_NEWTON = 1, JFNK_PAIRS_ARNOLDI = 2 };
+
+/* Record training pairs of the kinds in the bit mask `kinds` during later
+ * jfnk_step calls, until `capacity` pairs are held (device memory:
+ * 2 * capacity * 4 * nx * nz floats; every pair adds one field-block
+ * preconditioner apply to the step).  Drops the pairs held; capacity 0 or
+ * kinds 0 stops recording and frees them. */
+jfnk_status jfnk_unet_capture(jfnk_handle* h, int capacity, int kinds);
+
+/* Number of recorded pairs. */
+jfnk_status jfnk_unet_pair_count(jfnk_handle* h, int* count);
+
+/* Copy recorded pair i into device float32 arrays X, T of 4 * nx * nz. */
+jfnk_status jfnk_unet_get_pair(jfnk_handle* h, int i, float* X, float* T);
+
+/* `epochs` passes of Adam (step lr, beta1 = 0.9, beta2 = 0.999, one update
+ * per pair, fixed pair order per epoch) over the recorded pairs.
+ * loss_hist: host array of `epochs` doubles (may be NULL) receiving the mean
+ * loss of each epoch (measured before each update).  Synchronises. */
+jfnk_status jfnk_unet_train(jfnk_handle* h, int epochs, float lr, double* loss_hist);
+
+/* y = N(x) for device float32 arrays of 4 * nx * nz (field planes, x fastest). */
+jfnk_status jfnk_unet_forward(jfnk_handle* h, const float* x, float* y);
+
+/* Loss of one pair (device x, t) and, when grads (host, jfnk_unet_num_weights
+ * floats) is not NULL, its gradient with respect to the flat weights. */
+jfnk_status jfnk_unet_loss_grad(jfnk_handle* h, const float* x, const float* t, double* loss,
+                                float* grads);
+
+/* Change the preconditioner between steps: JFNK_PC_NONE, JFNK_PC_BLOCK or
+ * JFNK_PC_UNET (the latter only where the calls above are supported). */
+jfnk_status jfnk_set_precond(jfnk_handle* h, int precond);
 
 /* Number of tile shapes jfnk_set_tiles accepts per kernel family. */
 #define JFNK_NUM_TILE_SHAPES 4

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libjfnk.so")
-SOURCES = ["stencil.cu", "stencil3d.cu", "krylov.cu", "jfnk.cu", "batch.cu", "noalloc.cu"]
+SOURCES = ["stencil.cu", "stencil3d.cu", "krylov.cu", "jfnk.cu", "batch.cu", "noalloc.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

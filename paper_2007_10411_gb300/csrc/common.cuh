@@ -47,7 +47,7 @@ struct Ctl {
     int k;               // columns in the finished cycle
     int iters;           // Krylov iterations in this Newton solve
     int m;               // restart length
-    int pad_;
+    int ncap;            // training pairs recorded for the learned preconditioner
     double beta0;        // ||b|| of the Newton system
     double target;       // eta * beta0
     double res2;         // ||W R||^2 of the last residual evaluation
@@ -56,6 +56,8 @@ struct Ctl {
     double eps_jv;       // finite-difference step of the next Jacobian-vector product
     double inv_hn;       // 1 / h_{j+1,j} for pass C
     double kmax;         // max eddy coefficient K_M (preconditioner bounds)
+    double gstart;       // ||r|| at the start of the current GMRES cycle
+    double gres;         // rotated residual |g_{j+1}| after the latest Arnoldi step
     double scratch[8];   // misc reductions (||x||^2, ||r||^2, ...)
     double h1[KMAX + 1];
     double h2[KMAX + 1];      // second-projection coefficients (pass C)

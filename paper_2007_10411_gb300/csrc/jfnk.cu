@@ -19,11 +19,15 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "unet.h"
 
 using namespace jfnk;
 
 namespace {
 constexpr int LAG = 2;
+// A GMRES cycle with the learned preconditioner that reduces the residual by
+// less than this factor hands the rest of the solve to the field-block one.
+constexpr double UNET_MIN_CYCLE_REDUCTION = 0.5;
 constexpr int KT_RING = 256;   // outstanding timed launches before a drain
 }
 
@@ -54,6 +58,10 @@ struct jfnk_handle {
     double kt_b[KT_RING];
     int kt_head, kt_count, kt_open;
     jfnk_kernel_time kt_acc[JFNK_KF_COUNT];
+    // learned preconditioner: network and recorded training pairs
+    UNet* net;
+    float *capX, *capT;
+    int cap_cap, cap_kinds;
 };
 
 #define CK(call)                                                                  \
@@ -90,7 +98,8 @@ static jfnk_status validate(const jfnk_grid* g, const jfnk_strat* s, const jfnk_
         return JFNK_ERR_INVALID_ARG;
     if (o->precision != JFNK_FP64 && o->precision != JFNK_MIXED) return JFNK_ERR_INVALID_ARG;
     if (o->krylov_m < 1 || o->krylov_m > JFNK_MAX_KRYLOV) return JFNK_ERR_INVALID_ARG;
-    if (o->precond != JFNK_PC_NONE && o->precond != JFNK_PC_BLOCK) return JFNK_ERR_INVALID_ARG;
+    if (o->precond != JFNK_PC_NONE && o->precond != JFNK_PC_BLOCK && o->precond != JFNK_PC_UNET)
+        return JFNK_ERR_INVALID_ARG;
     if (o->pc_sweeps < 1 || o->pc_sweeps > MAX_PC_SWEEPS) return JFNK_ERR_INVALID_ARG;
     if (!finite_pos(o->newton_rtol) || !(o->newton_atol_factor >= 0.0) ||
         !(o->eta > 0.0 && o->eta < 1.0))
@@ -104,7 +113,16 @@ static jfnk_status validate(const jfnk_grid* g, const jfnk_strat* s, const jfnk_
     // implemented subset
     if (o->wavelet_p != 2) return JFNK_ERR_UNSUPPORTED;
     if (g->nz < 4) return JFNK_ERR_INVALID_ARG;      // one mirror reflection covers the halo
+    if (o->precond == JFNK_PC_UNET &&
+        (g->dim != 2 || o->precision != JFNK_MIXED || g->nx % 32 != 0 || g->nz % 32 != 0))
+        return JFNK_ERR_UNSUPPORTED;
     return JFNK_OK;
+}
+
+// The learned preconditioner is implemented for 2-D float32-basis handles on
+// grids whose sides are multiples of 32 (two 2x2 poolings of 8x8-aligned tiles).
+static bool unet_supported(const jfnk_handle* h) {
+    return h->G.dim == 2 && h->mixed && h->grid.nx % 32 == 0 && h->grid.nz % 32 == 0;
 }
 
 static void free_all(jfnk_handle* h) {
@@ -113,6 +131,9 @@ static void free_all(jfnk_handle* h) {
                    h->tA, h->tB, h->part, h->ctl};
     for (void* p : dev)
         if (p) cudaFree(p);
+    if (h->net) unet_destroy(h->net);
+    if (h->capX) cudaFree(h->capX);
+    if (h->capT) cudaFree(h->capT);
     if (h->hctl) cudaFreeHost(h->hctl);
     if (h->hdone) cudaFreeHost(h->hdone);
     for (int i = 0; i < KMAX; ++i)
@@ -278,7 +299,7 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     ALLOC(h->heat, (size_t)grid->nx * ny * sizeof(double));
     ALLOC(h->budg, 64 * sizeof(double));
     ALLOC(h->V, (size_t)(m + 1) * nbT);
-    if (opts->precond == JFNK_PC_BLOCK) ALLOC(h->Z, (size_t)m * nbT);
+    if (opts->precond != JFNK_PC_NONE) ALLOC(h->Z, (size_t)m * nbT);
     ALLOC(h->w, nbT);
     if (h->mixed) {
         ALLOC(h->uT, nbT);
@@ -301,6 +322,7 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
         delete h;
         return JFNK_ERR_OOM;
     }
+    memset(h->hctl, 0, sizeof(Ctl));
     for (int i = 0; i < KMAX; ++i) {
         if (cudaEventCreateWithFlags(&h->ev[i], cudaEventDisableTiming) != cudaSuccess) {
             free_all(h);
@@ -402,7 +424,7 @@ static jfnk_status autotune_impl(jfnk_handle* h, const double* u, int* tiles) {
             CK(cudaEventElapsedTime(&ms, e0, e1));
             if (pass == 1 && ms < best_jv) { best_jv = ms; arg_jv = c; }
         }
-        if (h->opts.precond == JFNK_PC_BLOCK && h->opts.pc_sweeps > 1) {
+        if (h->opts.precond != JFNK_PC_NONE && h->opts.pc_sweeps > 1) {
             for (int pass = 0; pass < 2; ++pass) {
                 CK(cudaEventRecord(e0, s));
                 for (int r = 0; r < reps; ++r)
@@ -561,6 +583,12 @@ static jfnk_status precond_impl(jfnk_handle* h, const double* u, const double* r
     h->launches += 1;
     CK(launch_precond<T>(G, h->opts.pc_sweeps, rT, zT, (T*)h->za, (T*)h->zb, (T*)h->da, (T*)h->db,
                          (const T*)h->nu, h->part, h->ctl, 0, s, &h->launches));
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (h->opts.precond == JFNK_PC_UNET && h->net) {
+            CK(unet_apply(h->net, rT, zT, 1, nullptr, s));
+            h->launches += unet_launches_per_apply();
+        }
+    }
     if (sizeof(T) != sizeof(double)) {
         CK((launch_convert<T, double>(zT, z, h->n, s)));
         h->launches += 1;
@@ -574,6 +602,12 @@ extern "C" jfnk_status jfnk_precond_apply(jfnk_handle* h, const double* u, const
 }
 
 // ------------------------------------------------------------------- step
+// Pair recording requested for these kinds and, as of the last control-block
+// read, room left in the store (the device makes the final check).
+static bool capturing(const jfnk_handle* h, int kinds) {
+    return (h->cap_kinds & kinds) && h->capX != nullptr && h->hctl->ncap < h->cap_cap;
+}
+
 static jfnk_status read_ctl(jfnk_handle* h) {
     CK(cudaMemcpyAsync(h->hctl, h->ctl, CTL_HEAD, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -597,18 +631,21 @@ static jfnk_status apply_jv(jfnk_handle* h, const T* uT, const T* z, T* w, int c
 
 // Restarted GMRES(m) on J_hat x = -W R from x = 0 (cycle_init already enqueued).
 template <typename T>
-static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* restarts, int* conv) {
+static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* restarts, int* conv, int* switched) {
     cudaStream_t s = h->stream;
     const Geo& G = h->G;
     const size_t n = h->n, ld = h->ld;
     const int m = h->m;
-    const bool pc = h->opts.precond == JFNK_PC_BLOCK;
+    const bool pc = h->opts.precond != JFNK_PC_NONE;
+    bool learned = h->opts.precond == JFNK_PC_UNET && h->net != nullptr;
+    const bool arnoldi_pairs = sizeof(T) == sizeof(float) && capturing(h, JFNK_PAIRS_ARNOLDI);
     T* V = (T*)h->V;
     T* Z = pc ? (T*)h->Z : V;
     T* w = (T*)h->w;
     T* xT = h->mixed ? (T*)h->xT : (T*)h->x;
     *restarts = 0;
     *conv = 0;
+    *switched = 0;
     for (int cycle = 0;; ++cycle) {
         for (int j = 0; j < m; ++j) {
             T* vj = V + (size_t)j * ld;
@@ -619,8 +656,28 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
                                      (T*)h->db, (const T*)h->nu, h->part, h->ctl, 1, s, &h->launches));
                 kt_end(h, JFNK_KF_PRECOND, pc_bytes(h));
             }
+            if constexpr (sizeof(T) == sizeof(float)) {
+                if (learned) {   // z_j += N(v_j), then the FD step for the new ||z_j||
+                    kt_begin(h, JFNK_KF_UNET);
+                    CK(unet_apply(h->net, vj, zj, 1, &h->ctl->done, s));
+                    kt_end(h, JFNK_KF_UNET, 3.0 * (double)n * sizeof(float));
+                    CK(launch_pc_eps(zj, n, h->part, h->ctl, s));
+                    h->launches += unet_launches_per_apply() + 1;
+                }
+            }
             jfnk_status st = apply_jv<T>(h, uT, zj, w, 1);
             if (st != JFNK_OK) return st;
+            if constexpr (sizeof(T) == sizeof(float)) {
+                if (arnoldi_pairs) {   // (J z_j, z_j) is an exact inverse pair
+                    CK(launch_pair_arnoldi(w, (float*)h->tA, n, h->part, h->ctl, s));
+                    CK(launch_precond<float>(G, h->opts.pc_sweeps, (const float*)h->tA, (float*)h->tB,
+                                             (float*)h->za, (float*)h->zb, (float*)h->da, (float*)h->db,
+                                             (const float*)h->nu, h->part, h->ctl, 1, s, &h->launches));
+                    CK(launch_pair_store<float>((const float*)h->tA, zj, (const float*)h->tB, h->capX, h->capT, n,
+                                                h->cap_cap, 1, h->ctl, s));
+                    h->launches += 4;
+                }
+            }
             const double vb = (double)n * sizeof(T);
             kt_begin(h, JFNK_KF_ARNOLDI_A);
             CK(launch_arnoldi_a<T>(V, ld, w, n, j + 1, h->part, h->ctl, s));
@@ -651,6 +708,12 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
             return JFNK_OK;
         }
         if (cycle >= h->opts.max_restarts) return JFNK_OK;
+        if (learned && c.gres > UNET_MIN_CYCLE_REDUCTION * c.gstart) {
+            // the learned directions stalled: finish this solve with the field-block
+            // preconditioner, restarting from the correction reached so far
+            learned = false;
+            *switched = 1;
+        }
         *restarts = cycle + 1;
         st = apply_jv<T>(h, uT, xT, w, 0);
         if (st != JFNK_OK) return st;
@@ -695,8 +758,9 @@ static jfnk_status step_impl(jfnk_handle* h, double* u, jfnk_stats* out) {
     stats.res_hist[0] = r0;
     double res = r0;
     int k = 0;
+    const bool capture = sizeof(T) == sizeof(float) && capturing(h, JFNK_PAIRS_NEWTON | JFNK_PAIRS_ARNOLDI);
     while (res > tol && k < h->opts.max_newton) {
-        if (h->opts.precond == JFNK_PC_BLOCK) {
+        if (h->opts.precond != JFNK_PC_NONE || capture) {
             if (G.smag) {
                 CK(launch_eddy<T>(G, uT, (T*)h->nu, h->part, h->ctl, s));
                 h->launches += 1;
@@ -707,12 +771,24 @@ static jfnk_status step_impl(jfnk_handle* h, double* u, jfnk_stats* out) {
         CK(launch_cycle_init<T>(G, h->R, (T*)h->V, h->x, n, h->opts.eta, h->m,
                                 h->opts.precond == JFNK_PC_NONE, h->ctl, s));
         h->launches += 1;
-        int it = 0, rs = 0, cv = 0;
-        st = gmres_solve<T>(h, uT, &it, &rs, &cv);
+        int it = 0, rs = 0, cv = 0, sw = 0;
+        st = gmres_solve<T>(h, uT, &it, &rs, &cv, &sw);
         if (st != JFNK_OK) return st;
+        stats.pc_switches += sw;
         stats.gmres_per_newton[k] = it;
         stats.gmres_iters += it;
         stats.restarts += rs;
+        if constexpr (sizeof(T) == sizeof(float)) {
+            if (cv && capturing(h, JFNK_PAIRS_NEWTON)) {   // training pair of this correction
+                CK(launch_pair_newton(G, h->R, (float*)h->tA, n, h->ctl, s));
+                CK(launch_precond<float>(G, h->opts.pc_sweeps, (const float*)h->tA, (float*)h->tB, (float*)h->za,
+                                         (float*)h->zb, (float*)h->da, (float*)h->db, (const float*)h->nu, h->part,
+                                         h->ctl, 0, s, &h->launches));
+                CK(launch_pair_store<double>((const float*)h->tA, h->x, (const float*)h->tB, h->capX, h->capT, n,
+                                             h->cap_cap, 0, h->ctl, s));
+                h->launches += 3;
+            }
+        }
         CK(launch_newton_update<T>(G, u, h->x, h->mixed ? uT : nullptr, n, s));
         h->launches += 1;
         st = residual_eval<T>(h, u);
@@ -731,7 +807,167 @@ static jfnk_status step_impl(jfnk_handle* h, double* u, jfnk_stats* out) {
 
 extern "C" jfnk_status jfnk_step(jfnk_handle* h, double* u, jfnk_stats* out) {
     if (!h || !u) return JFNK_ERR_INVALID_ARG;
-    return h->mixed ? step_impl<float>(h, u, out) : step_impl<double>(h, u, out);
+    if (!h->mixed) return step_impl<double>(h, u, out);
+    jfnk_status st = step_impl<float>(h, u, out);
+    if (h->opts.precond == JFNK_PC_UNET && h->net &&
+        (st == JFNK_ERR_NOT_CONVERGED || st == JFNK_ERR_BREAKDOWN || st == JFNK_ERR_NAN)) {
+        // the learned preconditioner failed: redo the step from u^n with the block one
+        CK(cudaMemcpyAsync(u, h->un, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        h->opts.precond = JFNK_PC_BLOCK;
+        st = step_impl<float>(h, u, out);
+        h->opts.precond = JFNK_PC_UNET;
+        if (out) out->pc_fallback = 1;
+    }
+    return st;
+}
+
+// ------------------------------------------------- learned preconditioner
+extern "C" jfnk_status jfnk_unet_init(jfnk_handle* h, unsigned long long seed) {
+    if (!h) return JFNK_ERR_INVALID_ARG;
+    if (!unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->net) {
+        unet_destroy(h->net);
+        h->net = nullptr;
+    }
+    // balanced units: the linearised acoustic and buoyancy couplings become skew-adjoint
+    const double su = h->opts.scale_u;
+    double bal[4] = {1.0, 1.0, 1.0, 1.0};
+    if (h->strat.beta != 0.0 && h->strat.g > 0.0)
+        bal[2] = h->opts.scale_theta / (su * sqrt(fabs(h->strat.beta) * h->strat.theta0 / h->strat.g));
+    if (h->strat.gamma_p * h->strat.pbar > 0.0)
+        bal[3] = h->opts.scale_p / (su * sqrt(h->strat.gamma_p * h->strat.pbar / h->strat.theta0));
+    cudaError_t e = cudaSuccess;
+    h->net = unet_create(h->grid.nx, h->grid.nz, bal, seed, &e);
+    if (!h->net) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? JFNK_ERR_OOM : JFNK_ERR_CUDA;
+    }
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_unet_num_weights(jfnk_handle* h, size_t* count) {
+    if (!h || !count) return JFNK_ERR_INVALID_ARG;
+    if (!unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
+    if (!h->net) return JFNK_ERR_INVALID_ARG;
+    *count = unet_num_weights(h->net);
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_unet_get_weights(jfnk_handle* h, float* host, size_t count) {
+    if (!h || !host) return JFNK_ERR_INVALID_ARG;
+    if (!unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
+    if (!h->net || count != unet_num_weights(h->net)) return JFNK_ERR_INVALID_ARG;
+    CK(unet_get_weights(h->net, host, h->stream));
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_unet_set_weights(jfnk_handle* h, const float* host, size_t count) {
+    if (!h || !host) return JFNK_ERR_INVALID_ARG;
+    if (!unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
+    if (!h->net || count != unet_num_weights(h->net)) return JFNK_ERR_INVALID_ARG;
+    for (size_t i = 0; i < count; ++i)
+        if (!isfinite(host[i])) return JFNK_ERR_INVALID_ARG;
+    CK(unet_set_weights(h->net, host, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_unet_capture(jfnk_handle* h, int capacity, int kinds) {
+    if (!h || capacity < 0 || (kinds & ~(JFNK_PAIRS_NEWTON | JFNK_PAIRS_ARNOLDI)) != 0) return JFNK_ERR_INVALID_ARG;
+    if (!unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->capX) cudaFree(h->capX);
+    if (h->capT) cudaFree(h->capT);
+    h->capX = h->capT = nullptr;
+    h->cap_cap = 0;
+    h->cap_kinds = 0;
+    const int zero = 0;
+    CK(cudaMemcpy(&h->ctl->ncap, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    h->hctl->ncap = 0;
+    if (capacity == 0 || kinds == 0) return JFNK_OK;
+    const size_t bytes = (size_t)capacity * h->n * sizeof(float);
+    if (cudaMalloc((void**)&h->capX, bytes) != cudaSuccess || cudaMalloc((void**)&h->capT, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->capX) cudaFree(h->capX);
+        h->capX = nullptr;
+        return JFNK_ERR_OOM;
+    }
+    h->cap_cap = capacity;
+    h->cap_kinds = kinds;
+    return JFNK_OK;
+}
+
+static jfnk_status pair_count(jfnk_handle* h, int* count) {
+    int c = 0;
+    CK(cudaMemcpyAsync(&c, &h->ctl->ncap, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *count = std::min(c, h->cap_cap);
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_unet_pair_count(jfnk_handle* h, int* count) {
+    if (!h || !count) return JFNK_ERR_INVALID_ARG;
+    return pair_count(h, count);
+}
+
+extern "C" jfnk_status jfnk_unet_get_pair(jfnk_handle* h, int i, float* X, float* T) {
+    if (!h || !X || !T || i < 0) return JFNK_ERR_INVALID_ARG;
+    int c = 0;
+    jfnk_status st = pair_count(h, &c);
+    if (st != JFNK_OK) return st;
+    if (i >= c) return JFNK_ERR_INVALID_ARG;
+    const size_t bytes = h->n * sizeof(float);
+    CK(cudaMemcpyAsync(X, h->capX + (size_t)i * h->n, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(T, h->capT + (size_t)i * h->n, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_unet_train(jfnk_handle* h, int epochs, float lr, double* loss_hist) {
+    if (!h || epochs < 0 || !(lr > 0.0f) || !isfinite(lr)) return JFNK_ERR_INVALID_ARG;
+    if (!unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
+    int c = 0;
+    jfnk_status st = pair_count(h, &c);
+    if (st != JFNK_OK) return st;
+    if (!h->net || c < 1) return JFNK_ERR_INVALID_ARG;
+    CK(unet_train(h->net, h->capX, h->capT, c, epochs, lr, loss_hist, h->stream));
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_unet_forward(jfnk_handle* h, const float* x, float* y) {
+    if (!h || !x || !y) return JFNK_ERR_INVALID_ARG;
+    if (!unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
+    if (!h->net) return JFNK_ERR_INVALID_ARG;
+    CK(unet_apply(h->net, x, y, 0, nullptr, h->stream));
+    h->launches += unet_launches_per_apply();
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_unet_loss_grad(jfnk_handle* h, const float* x, const float* t, double* loss,
+                                           float* grads) {
+    if (!h || !x || !t || !loss) return JFNK_ERR_INVALID_ARG;
+    if (!unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
+    if (!h->net) return JFNK_ERR_INVALID_ARG;
+    CK(unet_loss_grad(h->net, x, t, loss, grads, h->stream));
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_set_precond(jfnk_handle* h, int precond) {
+    if (!h) return JFNK_ERR_INVALID_ARG;
+    if (precond != JFNK_PC_NONE && precond != JFNK_PC_BLOCK && precond != JFNK_PC_UNET)
+        return JFNK_ERR_INVALID_ARG;
+    if (precond == JFNK_PC_UNET && !unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
+    if (precond != JFNK_PC_NONE && !h->Z) {
+        const size_t eT = h->mixed ? sizeof(float) : sizeof(double);
+        CK(cudaStreamSynchronize(h->stream));
+        if (cudaMalloc(&h->Z, (size_t)h->m * h->ld * eT) != cudaSuccess) {
+            cudaGetLastError();
+            h->Z = nullptr;
+            return JFNK_ERR_OOM;
+        }
+    }
+    h->opts.precond = precond;
+    return JFNK_OK;
 }
 
 extern "C" jfnk_status jfnk_step_host(jfnk_handle* h, double* u_host, jfnk_stats* out) {

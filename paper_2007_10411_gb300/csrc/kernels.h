@@ -91,4 +91,19 @@ cudaError_t launch_norm2(const Geo& G, const T* a, size_t n, int weighted, int s
 // ctl->eps_jv = eps > 0 ? eps : sqrt(eps_mach (1 + sqrt(scratch[su]))) / sqrt(scratch[sv])
 cudaError_t launch_set_eps(double eps, int su, int sv, Ctl* ctl, cudaStream_t s);
 
+// ------------------------------------------------- learned preconditioner
+// Training pairs.  Arnoldi step (skipped once ctl->done is set): stage
+// Xs = w / ||w||.  Newton correction: stage Xs = -W R / beta0.  Then, after
+// the caller's MX = M^-1 Xs, store slot ctl->ncap (< cap) of the pair buffers:
+// X = Xs, T = corr / ||w|| - MX (arnoldi, corr = z_j) or corr / beta0 - MX
+// (Newton, corr = x_hat), and advance ctl->ncap.
+cudaError_t launch_pair_arnoldi(const float* w, float* Xs, size_t n, double* part, Ctl* ctl, cudaStream_t s);
+cudaError_t launch_pair_newton(const Geo& G, const double* R, float* Xs, size_t n, const Ctl* ctl,
+                               cudaStream_t s);
+template <typename TC>
+cudaError_t launch_pair_store(const float* Xs, const TC* corr, const float* MX, float* Xbuf, float* Tbuf, size_t n,
+                              int cap, int arnoldi, Ctl* ctl, cudaStream_t s);
+// ctl->eps_jv from ||z|| (skipped once ctl->done is set).
+cudaError_t launch_pc_eps(const float* z, size_t n, double* part, Ctl* ctl, cudaStream_t s);
+
 }  // namespace jfnk

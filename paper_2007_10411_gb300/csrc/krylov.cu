@@ -132,6 +132,7 @@ __device__ void givens_update(Ctl* c, int j, int m, const double* h2, double wn2
     const double gj = c->g[j];
     c->g[j + 1] = -sn * gj;
     c->g[j] = cs * gj;
+    c->gres = fabs(c->g[j + 1]);
     c->iters += 1;
     const bool finite = isfinite(hn2) && isfinite(c->g[j + 1]) && isfinite(c->Rt[j][j]);
     const bool conv = fabs(c->g[j + 1]) <= c->target;
@@ -316,6 +317,8 @@ cycle_init(Geo G, const double* __restrict__ R, T* __restrict__ V0, double* __re
         ctl->beta0 = beta;
         ctl->target = eta * beta;
         ctl->g[0] = beta;
+        ctl->gstart = beta;
+        ctl->gres = beta;
         ctl->done = 0;
         ctl->converged = beta == 0.0;
         ctl->breakdown = 0;
@@ -356,6 +359,8 @@ restart_scale(T* __restrict__ V0, size_t n, int pc_none, Ctl* ctl) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) V0[i] *= inv;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->g[0] = beta;
+        ctl->gstart = beta;
+        ctl->gres = beta;
         ctl->done = 0;
         ctl->converged = 0;
         ctl->breakdown = 0;
@@ -418,6 +423,93 @@ __global__ void set_eps_k(double eps, int su, int sv, Ctl* ctl) {
     } else {
         const double vn = sqrt(ctl->scratch[sv]);
         ctl->eps_jv = vn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->scratch[su]))) / vn : 0.0;
+    }
+}
+
+// ------------------------------------------------- learned preconditioner
+// Training pairs are staged in fixed buffers and copied into slot ctl->ncap of
+// the pair store by the last kernel of the sequence, so that steps enqueued
+// after a GMRES cycle finished (ctl->done) record nothing.
+constexpr int PAIR_SLOT = 6;   // ctl->scratch slot of ||w||^2
+
+// ||w||^2 of an Arnoldi product.
+__global__ void __launch_bounds__(NTHREADS)
+pair_norm_k(const float* __restrict__ w, size_t n, double* part, Ctl* ctl) {
+    if (ctl->done) return;
+    float acc[1] = {0.f};
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) acc[0] = fmaf(w[i], w[i], acc[0]);
+    block_partials<1>(acc, 1, part, gridDim.x, blockIdx.x);
+    if (arrive_last(&ctl->counter[CNT_MISC], gridDim.x)) {
+        __shared__ double tot[1];
+        final_sums(part, gridDim.x, 1, tot);
+        if (threadIdx.x == 0) ctl->scratch[PAIR_SLOT] = tot[0];
+    }
+}
+
+// Arnoldi pair input X = w / ||w||.
+__global__ void __launch_bounds__(NTHREADS)
+pair_stage_arnoldi_k(const float* __restrict__ w, float* __restrict__ X, size_t n, const Ctl* ctl) {
+    if (ctl->done) return;
+    const double nw = sqrt(ctl->scratch[PAIR_SLOT]);
+    const float inv = (float)(nw > 0.0 ? 1.0 / nw : 0.0);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) X[i] = w[i] * inv;
+}
+
+// Newton pair input X = -W R / beta0.
+__global__ void __launch_bounds__(NTHREADS)
+pair_stage_newton_k(Geo G, const double* __restrict__ R, float* __restrict__ X, size_t n, const Ctl* ctl) {
+    const double b = ctl->beta0;
+    const double inv = b > 0.0 ? 1.0 / b : 0.0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int f = (int)(i / G.npt);
+        X[i] = (float)(-R[i] * G.inv_scale[f] * inv);
+    }
+}
+
+// Slot ctl->ncap of the store: X = staged input, T = c * corr - MX with
+// c = 1 / ||w|| (Arnoldi, corr = z_j) or 1 / beta0 (Newton, corr = x_hat).
+template <typename TC>
+__global__ void __launch_bounds__(NTHREADS)
+pair_store_k(const float* __restrict__ Xs, const TC* __restrict__ corr, const float* __restrict__ MX,
+             float* __restrict__ Xbuf, float* __restrict__ Tbuf, size_t n, int cap, int arnoldi, const Ctl* ctl) {
+    if (arnoldi && ctl->done) return;
+    const int slot = ctl->ncap;
+    if (slot < 0 || slot >= cap) return;
+    const double d = arnoldi ? sqrt(ctl->scratch[PAIR_SLOT]) : ctl->beta0;
+    const double c = d > 0.0 ? 1.0 / d : 0.0;
+    float* X = Xbuf + (size_t)slot * n;
+    float* T = Tbuf + (size_t)slot * n;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        X[i] = Xs[i];
+        T[i] = (float)((double)corr[i] * c - (double)MX[i]);
+    }
+}
+
+__global__ void pair_commit_k(int cap, int arnoldi, Ctl* ctl) {
+    if (arnoldi && ctl->done) return;
+    if (ctl->ncap < cap) ctl->ncap += 1;
+}
+
+// FD step of the next Jacobian-vector product from ||z|| once the network's
+// correction has been added to z (returns at entry once the cycle is done).
+__global__ void __launch_bounds__(NTHREADS)
+pc_eps_k(const float* __restrict__ z, size_t n, double* part, Ctl* ctl) {
+    if (ctl->done) return;
+    float acc[1] = {0.f};
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) acc[0] = fmaf(z[i], z[i], acc[0]);
+    block_partials<1>(acc, 1, part, gridDim.x, blockIdx.x);
+    if (arrive_last(&ctl->counter[CNT_MISC], gridDim.x)) {
+        __shared__ double tot[1];
+        final_sums(part, gridDim.x, 1, tot);
+        if (threadIdx.x == 0) {
+            const double zn = sqrt(tot[0]);
+            ctl->eps_jv = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+        }
     }
 }
 
@@ -504,6 +596,35 @@ cudaError_t launch_norm2(const Geo& G, const T* a, size_t n, int weighted, int s
 
 cudaError_t launch_set_eps(double eps, int su, int sv, Ctl* ctl, cudaStream_t s) {
     set_eps_k<<<1, 1, 0, s>>>(eps, su, sv, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_arnoldi(const float* w, float* Xs, size_t n, double* part, Ctl* ctl, cudaStream_t s) {
+    pair_norm_k<<<stream_blocks(n), NTHREADS, 0, s>>>(w, n, part, ctl);
+    pair_stage_arnoldi_k<<<stream_blocks(n), NTHREADS, 0, s>>>(w, Xs, n, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_newton(const Geo& G, const double* R, float* Xs, size_t n, const Ctl* ctl,
+                               cudaStream_t s) {
+    pair_stage_newton_k<<<stream_blocks(n), NTHREADS, 0, s>>>(G, R, Xs, n, ctl);
+    return cudaGetLastError();
+}
+
+template <typename TC>
+cudaError_t launch_pair_store(const float* Xs, const TC* corr, const float* MX, float* Xbuf, float* Tbuf, size_t n,
+                              int cap, int arnoldi, Ctl* ctl, cudaStream_t s) {
+    pair_store_k<TC><<<stream_blocks(n), NTHREADS, 0, s>>>(Xs, corr, MX, Xbuf, Tbuf, n, cap, arnoldi, ctl);
+    pair_commit_k<<<1, 1, 0, s>>>(cap, arnoldi, ctl);
+    return cudaGetLastError();
+}
+template cudaError_t launch_pair_store<float>(const float*, const float*, const float*, float*, float*, size_t, int,
+                                              int, Ctl*, cudaStream_t);
+template cudaError_t launch_pair_store<double>(const float*, const double*, const float*, float*, float*, size_t,
+                                               int, int, Ctl*, cudaStream_t);
+
+cudaError_t launch_pc_eps(const float* z, size_t n, double* part, Ctl* ctl, cudaStream_t s) {
+    pc_eps_k<<<stream_blocks(n), NTHREADS, 0, s>>>(z, n, part, ctl);
     return cudaGetLastError();
 }
 

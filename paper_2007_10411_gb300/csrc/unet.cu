@@ -1,0 +1,694 @@
+// Learned right preconditioner: linear 3-level U-Net (see unet.h).
+//
+// Convolutions: implicit GEMM per 16x8 pixel tile, M = 128 pixels (8 warps x 16),
+// N = output channels, K = 9 taps x input channels, using
+// mma.sync.m16n8k16.row.col.f32.bf16.bf16.f32 with ldmatrix fragments from
+// shared memory (input tile with a one-pixel halo, NHWC, and the layer's
+// weights [tap][cout][cin], resident for the CTA's lifetime).  The backward pass w.r.t. the input is the same
+// kernel with flipped, transposed weights; the weight gradient is a float32
+// reduction over pixel tiles (CUDA cores) with one atomic add per weight and
+// tile.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "unet.h"
+
+namespace jfnk {
+namespace {
+
+constexpr int NL = 9;     // layers
+enum { L0a, L0b, L1a, L1b, L2a, L2b, L1c, L0c, L0d };
+constexpr int CIN[NL] = {16, 16, 16, 32, 32, 64, 96, 48, 16};
+constexpr int COUT[NL] = {16, 16, 32, 32, 64, 64, 32, 16, 16};
+constexpr int KSZ[NL] = {3, 3, 3, 3, 3, 3, 3, 3, 1};
+
+typedef __nv_bfloat16 bf16;
+
+// convolution tile: CONV_TH rows x CONV_TW columns, one warp per pair of rows
+constexpr int CONV_TW = 8, CONV_TH = 16, CONV_THREADS = 32 * CONV_TH / 2;
+
+__device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------- convolution
+// out[p][co] = sum_tap sum_ci W[tap][co][ci] in[p + off(tap)][ci] (zero padding).
+// in / out are NHWC with pixel strides istr / ostr (channels) and channel offsets.
+//
+// Persistent CTAs: the layer's weights are copied to shared memory once per
+// CTA, which then walks over CONV_TH x CONV_TW pixel tiles with a stride of
+// gridDim.x, prefetching the next tile's input (with its halo) by cp.async
+// while the tensor cores work on the current one.  Shared rows are padded by
+// 8 channels so that the ldmatrix row addresses of a fragment fall in
+// distinct bank groups.  Warp w owns pixel rows 2w and 2w+1 of the tile: the
+// 16 rows of its mma A fragment are (2w, 0..7) and (2w+1, 0..7).
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+// 16-byte global -> shared copy; src_bytes = 0 writes zeros (src is not read).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <int CI, int CO, int KS>
+struct ConvShape {
+    static constexpr int HP = KS / 2;
+    static constexpr int IH = CONV_TH + 2 * HP, IW = CONV_TW + 2 * HP;
+    static constexpr int CIP = CI + 8;                       // padded channel stride (elements)
+    static constexpr int W_ELEMS = KS * KS * CO * CIP;
+    static constexpr int X_ELEMS = IH * IW * CIP;
+    static constexpr size_t SMEM = sizeof(bf16) * (size_t)(W_ELEMS + 2 * X_ELEMS);
+};
+
+template <int CI, int IH, int IW, int CIP>
+__device__ __forceinline__ void stage_tile(const bf16* __restrict__ in, int istr, int ioff, int H, int Wd, int y0,
+                                           int x0, int hp, uint32_t xs_addr) {
+    constexpr int VPP = CI / 8;
+    for (int idx = threadIdx.x; idx < IH * IW * VPP; idx += blockDim.x) {
+        const int pix = idx / VPP, v = idx - pix * VPP;
+        const int iy = pix / IW, ix = pix - iy * IW;
+        const int gy = y0 + iy - hp, gx = x0 + ix - hp;
+        const bool ok = gy >= 0 && gy < H && gx >= 0 && gx < Wd;
+        const bf16* src = ok ? in + ((size_t)gy * Wd + gx) * istr + ioff + v * 8 : in;
+        cp_async16(xs_addr + (uint32_t)((pix * CIP + v * 8) * sizeof(bf16)), src, ok ? 16 : 0);
+    }
+}
+
+template <int CI, int CO, int KS, bool OUTF32>
+__global__ void __launch_bounds__(CONV_THREADS)
+conv_mma(const bf16* __restrict__ in, int istr, int ioff, const bf16* __restrict__ W, void* out, int ostr,
+         int ooff, int H, int Wd, const int* skip) {
+    if (skip != nullptr && *skip) return;
+    using S = ConvShape<CI, CO, KS>;
+    constexpr int HP = S::HP, IW = S::IW, IH = S::IH, CIP = S::CIP;
+    extern __shared__ __align__(16) unsigned char sm[];
+    bf16* ws = reinterpret_cast<bf16*>(sm);
+    const uint32_t ws_addr = (uint32_t)__cvta_generic_to_shared(ws);
+    const uint32_t xs_addr0 = ws_addr + (uint32_t)(S::W_ELEMS * sizeof(bf16));
+    const uint32_t xs_bytes = (uint32_t)(S::X_ELEMS * sizeof(bf16));
+    const int ntx = (Wd + CONV_TW - 1) / CONV_TW, nty = (H + CONV_TH - 1) / CONV_TH;
+    const int ntiles = ntx * nty;
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    // weights (group 0) and the first tile (group 1)
+    for (int idx = threadIdx.x; idx < KS * KS * CO * (CI / 8); idx += blockDim.x) {
+        const int row = idx / (CI / 8), v = idx - row * (CI / 8);
+        cp_async16(ws_addr + (uint32_t)((row * CIP + v * 8) * sizeof(bf16)), W + (size_t)row * CI + v * 8, 16);
+    }
+    cp_async_commit();
+    stage_tile<CI, IH, IW, CIP>(in, istr, ioff, H, Wd, (tile / ntx) * CONV_TH, (tile % ntx) * CONV_TW, HP, xs_addr0);
+    cp_async_commit();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    // ldmatrix row of this lane: A rows 0-7 = (2w, 0..7), rows 8-15 = (2w+1, 0..7); k half = lane >> 4
+    const int arow = lane & 15;
+    const int apy = 2 * warp + (arow >> 3), apx = arow & 7;
+    const int akoff = (lane >> 4) * 8;
+    int buf = 0;
+    for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+        const int next = tile + gridDim.x;
+        if (next < ntiles)
+            stage_tile<CI, IH, IW, CIP>(in, istr, ioff, H, Wd, (next / ntx) * CONV_TH, (next % ntx) * CONV_TW, HP,
+                                        xs_addr0 + (buf ^ 1) * xs_bytes);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const uint32_t xs_addr = xs_addr0 + buf * xs_bytes;
+        float acc[CO / 8][4];
+#pragma unroll
+        for (int nb = 0; nb < CO / 8; ++nb)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[nb][q] = 0.f;
+#pragma unroll
+        for (int tap = 0; tap < KS * KS; ++tap) {
+            const int dy = tap / KS - HP, dx = tap % KS - HP;
+            const uint32_t a_base =
+                xs_addr + (uint32_t)((((apy + HP + dy) * IW + (apx + HP + dx)) * CIP + akoff) * sizeof(bf16));
+#pragma unroll
+            for (int c = 0; c < CI / 16; ++c) {
+                uint32_t a0, a1, a2, a3;
+                ldsm_x4(a_base + c * 32, a0, a1, a2, a3);
+#pragma unroll
+                for (int nb = 0; nb < CO / 8; nb += 2) {
+                    uint32_t b0, b1, b2, b3;
+                    if (nb + 1 < CO / 8) {
+                        // matrices: (nb, k0), (nb, k8), (nb+1, k0), (nb+1, k8)
+                        const int i = lane >> 3;
+                        const int co = (nb + (i >> 1)) * 8 + (lane & 7);
+                        ldsm_x4(ws_addr + (uint32_t)(((tap * CO + co) * CIP + c * 16 + (i & 1) * 8) * sizeof(bf16)),
+                                b0, b1, b2, b3);
+                        mma16816(acc[nb], a0, a1, a2, a3, b0, b1);
+                        mma16816(acc[nb + 1], a0, a1, a2, a3, b2, b3);
+                    } else {
+                        const int i = (lane >> 3) & 1;
+                        const int co = nb * 8 + (lane & 7);
+                        ldsm_x2(ws_addr + (uint32_t)(((tap * CO + co) * CIP + c * 16 + i * 8) * sizeof(bf16)), b0, b1);
+                        mma16816(acc[nb], a0, a1, a2, a3, b0, b1);
+                    }
+                }
+            }
+        }
+        const int y0 = (tile / ntx) * CONV_TH, x0 = (tile % ntx) * CONV_TW;
+        const int gyA = y0 + 2 * warp, gyB = gyA + 1, gx = x0 + g;
+#pragma unroll
+        for (int nb = 0; nb < CO / 8; ++nb) {
+            const int co = nb * 8 + 2 * t;
+            if (gx < Wd) {
+                if (OUTF32) {
+                    float* o = reinterpret_cast<float*>(out);
+                    if (gyA < H)
+                        *reinterpret_cast<float2*>(o + ((size_t)gyA * Wd + gx) * ostr + ooff + co) =
+                            make_float2(acc[nb][0], acc[nb][1]);
+                    if (gyB < H)
+                        *reinterpret_cast<float2*>(o + ((size_t)gyB * Wd + gx) * ostr + ooff + co) =
+                            make_float2(acc[nb][2], acc[nb][3]);
+                } else {
+                    bf16* o = reinterpret_cast<bf16*>(out);
+                    if (gyA < H)
+                        *reinterpret_cast<__nv_bfloat162*>(o + ((size_t)gyA * Wd + gx) * ostr + ooff + co) =
+                            __floats2bfloat162_rn(acc[nb][0], acc[nb][1]);
+                    if (gyB < H)
+                        *reinterpret_cast<__nv_bfloat162*>(o + ((size_t)gyB * Wd + gx) * ostr + ooff + co) =
+                            __floats2bfloat162_rn(acc[nb][2], acc[nb][3]);
+                }
+            }
+        }
+        __syncthreads();   // the next prefetch overwrites this buffer
+    }
+    cp_async_wait<0>();
+}
+
+// dW[tap][co][ci] += sum_p dout[p][co] in[p + off(tap)][ci] over a 16x16 pixel tile.
+template <int CI, int CO, int KS>
+__global__ void __launch_bounds__(256)
+conv_wgrad(const bf16* __restrict__ in, int istr, int ioff, const bf16* __restrict__ dout, int H, int Wd,
+           float* __restrict__ dW) {
+    constexpr int TH = 16, TW = 16, HP = KS / 2;
+    constexpr int IH = TH + 2 * HP, IW = TW + 2 * HP;
+    extern __shared__ __align__(16) unsigned char sm[];
+    bf16* xs = reinterpret_cast<bf16*>(sm);        // [IH*IW][CI]
+    bf16* ds = xs + IH * IW * CI;                  // [TH*TW][CO]
+    const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    constexpr int VPP = CI / 8;
+    for (int idx = threadIdx.x; idx < IH * IW * VPP; idx += blockDim.x) {
+        const int pix = idx / VPP, v = idx - pix * VPP;
+        const int iy = pix / IW, ix = pix - iy * IW;
+        const int gy = y0 + iy - HP, gx = x0 + ix - HP;
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        if (gy >= 0 && gy < H && gx >= 0 && gx < Wd)
+            val = *reinterpret_cast<const uint4*>(in + ((size_t)gy * Wd + gx) * istr + ioff + v * 8);
+        *reinterpret_cast<uint4*>(xs + pix * CI + v * 8) = val;
+    }
+    constexpr int VPO = CO / 8;
+    for (int idx = threadIdx.x; idx < TH * TW * VPO; idx += blockDim.x) {
+        const int pix = idx / VPO, v = idx - pix * VPO;
+        const int gy = y0 + pix / TW, gx = x0 + pix % TW;
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        if (gy < H && gx < Wd) val = *reinterpret_cast<const uint4*>(dout + ((size_t)gy * Wd + gx) * CO + v * 8);
+        *reinterpret_cast<uint4*>(ds + pix * CO + v * 8) = val;
+    }
+    __syncthreads();
+    constexpr int GROUPS = KS * KS * (CO / 4) * (CI / 4);
+    for (int grp = threadIdx.x; grp < GROUPS; grp += blockDim.x) {
+        const int ci4 = grp % (CI / 4), r1 = grp / (CI / 4);
+        const int co4 = r1 % (CO / 4), tap = r1 / (CO / 4);
+        const int dy = tap / KS - HP, dx = tap % KS - HP;
+        float a[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a[i][j] = 0.f;
+        for (int p = 0; p < TH * TW; ++p) {
+            const int py = p / TW, pxx = p % TW;
+            const bf16* dp = ds + p * CO + co4 * 4;
+            const bf16* xp = xs + ((py + HP + dy) * IW + (pxx + HP + dx)) * CI + ci4 * 4;
+            float dv[4], xv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { dv[i] = __bfloat162float(dp[i]); xv[i] = __bfloat162float(xp[i]); }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a[i][j] = fmaf(dv[i], xv[j], a[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                atomicAdd(dW + ((size_t)tap * CO + co4 * 4 + i) * CI + ci4 * 4 + j, a[i][j]);
+    }
+}
+
+// ---------------------------------------------------------------- element-wise
+// Field balance of the network: it sees B x and returns B N(x).
+struct Bal {
+    float b[4], inv[4];
+};
+
+// NHWC16 input B x from four float32 field planes (channels 4..15 zero).
+__global__ void pack_input(const float* __restrict__ x, int npix, Bal bal, bf16* __restrict__ out,
+                           const int* skip) {
+    if (skip != nullptr && *skip) return;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+        __align__(16) bf16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(c < 4 ? bal.b[c] * x[(size_t)c * npix + p] : 0.f);
+        reinterpret_cast<uint4*>(out + (size_t)p * 16)[0] = reinterpret_cast<uint4*>(v)[0];
+        reinterpret_cast<uint4*>(out + (size_t)p * 16)[1] = reinterpret_cast<uint4*>(v)[1];
+    }
+}
+
+// 2x2 average pooling: out (H/2 x W/2) from in (H x W), C channels.
+__global__ void avgpool2(const bf16* __restrict__ in, int istr, int ioff, bf16* __restrict__ out, int ostr,
+                         int ooff, int C, int H, int Wd, const int* skip) {
+    if (skip != nullptr && *skip) return;
+    const int h = H / 2, w = Wd / 2;
+    const int total = h * w * C;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int c = i % C, q = i / C;
+        const int y = q / w, x = q - y * w;
+        float s = 0.f;
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+            s += __bfloat162float(in[((size_t)(2 * y + d / 2) * Wd + 2 * x + d % 2) * istr + ioff + c]);
+        out[(size_t)q * ostr + ooff + c] = __float2bfloat16(0.25f * s);
+    }
+}
+
+// nearest upsampling x2: out (H x W) from in (H/2 x W/2), C channels.
+__global__ void upsample2(const bf16* __restrict__ in, int istr, int ioff, bf16* __restrict__ out, int ostr,
+                          int ooff, int C, int H, int Wd, const int* skip) {
+    if (skip != nullptr && *skip) return;
+    const int total = H * Wd * C;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int c = i % C, p = i / C;
+        const int y = p / Wd, x = p - y * Wd;
+        out[(size_t)p * ostr + ooff + c] = in[((size_t)(y / 2) * (Wd / 2) + x / 2) * istr + ioff + c];
+    }
+}
+
+// backward of nearest upsampling: out (H/2 x W/2) = 2x2 sums of in (H x W).
+__global__ void upsample2_bwd(const bf16* __restrict__ in, int istr, int ioff, bf16* __restrict__ out, int C,
+                              int H, int Wd) {
+    const int h = H / 2, w = Wd / 2;
+    const int total = h * w * C;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int c = i % C, q = i / C;
+        const int y = q / w, x = q - y * w;
+        float s = 0.f;
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+            s += __bfloat162float(in[((size_t)(2 * y + d / 2) * Wd + 2 * x + d % 2) * istr + ioff + c]);
+        out[(size_t)q * C + c] = __float2bfloat16(s);
+    }
+}
+
+// gradient of a skip that feeds both a concat slot and an average pool:
+// out (H x W, C) = dcat[.., off:off+C] + 1/4 up(dsmall)
+__global__ void skip_grad(const bf16* __restrict__ dcat, int cstr, int coff, const bf16* __restrict__ dsmall,
+                          bf16* __restrict__ out, int C, int H, int Wd) {
+    const int total = H * Wd * C;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int c = i % C, p = i / C;
+        const int y = p / Wd, x = p - y * Wd;
+        const float v = __bfloat162float(dcat[(size_t)p * cstr + coff + c]) +
+                        0.25f * __bfloat162float(dsmall[((size_t)(y / 2) * (Wd / 2) + x / 2) * C + c]);
+        out[(size_t)p * C + c] = __float2bfloat16(v);
+    }
+}
+
+// network output (float32 NHWC16, first 4 channels, balanced units) -> 4
+// field planes B^-1 y, stored (accumulate = 0) or added (accumulate = 1)
+__global__ void unpack_output(const float* __restrict__ y, int npix, Bal bal, float* __restrict__ out,
+                              int accumulate, const int* skip) {
+    if (skip != nullptr && *skip) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * npix; i += gridDim.x * blockDim.x) {
+        const int c = i / npix, p = i - c * npix;
+        const float v = y[(size_t)p * 16 + c] * bal.inv[c];
+        out[i] = accumulate ? out[i] + v : v;
+    }
+}
+
+// out += ||B x||^2 over the 4 field planes
+__global__ void sumsq(const float* __restrict__ x, int npix, Bal bal, double* out) {
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * npix; i += gridDim.x * blockDim.x) {
+        const double v = (double)(bal.b[i / npix] * x[i]);
+        s += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// With y the raw output (balanced units): dy = (y - B t) / ||B x||^2
+// (channels 0..3), loss += 1/2 (y - B t)^2 / ||B x||^2.
+__global__ void loss_grad(const float* __restrict__ y, const float* __restrict__ t, int npix, Bal bal,
+                          const double* xn2, bf16* __restrict__ dy, double* loss) {
+    const float inv = (float)(1.0 / fmax(*xn2, 1e-300));
+    double s = 0.0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+        __align__(16) bf16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            float d = 0.f;
+            if (c < 4) {
+                d = y[(size_t)p * 16 + c] - bal.b[c] * t[(size_t)c * npix + p];
+                s += 0.5 * (double)d * (double)d;
+            }
+            v[c] = __float2bfloat16(d * inv);
+        }
+        reinterpret_cast<uint4*>(dy + (size_t)p * 16)[0] = reinterpret_cast<uint4*>(v)[0];
+        reinterpret_cast<uint4*>(dy + (size_t)p * 16)[1] = reinterpret_cast<uint4*>(v)[1];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * (double)inv);
+}
+
+// Wt[tap'][ci][co] = W[KS*KS-1-tap'][co][ci]  (weights of the input-gradient convolution)
+__global__ void flip_transpose(const bf16* __restrict__ W, bf16* __restrict__ Wt, int CI, int CO, int KK) {
+    const int total = KK * CI * CO;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int co = i % CO, r = i / CO;
+        const int ci = r % CI, tp = r / CI;
+        Wt[i] = W[((size_t)(KK - 1 - tp) * CO + co) * CI + ci];
+    }
+}
+
+__global__ void adam_step(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                          float* __restrict__ v, bf16* __restrict__ wb, size_t n, float lr, float c1, float c2) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = 0.9f * m[i] + 0.1f * gi;
+        const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+        w[i] = wi;
+        wb[i] = __float2bfloat16(wi);
+    }
+}
+
+__global__ void to_bf16(const float* __restrict__ w, bf16* __restrict__ wb, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        wb[i] = __float2bfloat16(w[i]);
+}
+
+int grid_for(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)(b > 1216 ? 1216 : (b > 0 ? b : 1));
+}
+
+template <int CI, int CO, int KS, bool OUTF32>
+cudaError_t conv(const bf16* in, int istr, int ioff, const bf16* W, void* out, int ostr, int ooff, int H, int Wd,
+                 cudaStream_t s, const int* skip = nullptr) {
+    using S = ConvShape<CI, CO, KS>;
+    static int max_ctas = 0;   // resident CTAs on the device (persistent grid)
+    if (max_ctas == 0) {
+        cudaError_t e = cudaFuncSetAttribute(conv_mma<CI, CO, KS, OUTF32>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_mma<CI, CO, KS, OUTF32>, CONV_THREADS,
+                                                               S::SMEM)) != cudaSuccess)
+            return e;
+        max_ctas = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int ntiles = ((Wd + CONV_TW - 1) / CONV_TW) * ((H + CONV_TH - 1) / CONV_TH);
+    const int grid = ntiles < max_ctas ? ntiles : max_ctas;
+    conv_mma<CI, CO, KS, OUTF32><<<grid, CONV_THREADS, S::SMEM, s>>>(in, istr, ioff, W, out, ostr, ooff, H, Wd, skip);
+    return cudaGetLastError();
+}
+
+template <int CI, int CO, int KS>
+cudaError_t wgrad(const bf16* in, int istr, int ioff, const bf16* dout, int H, int Wd, float* dW, cudaStream_t s) {
+    constexpr int HP = KS / 2;
+    const size_t sm = sizeof(bf16) * ((16 + 2 * HP) * (16 + 2 * HP) * CI + 256 * CO);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(conv_wgrad<CI, CO, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((Wd + 15) / 16, (H + 15) / 16);
+    conv_wgrad<CI, CO, KS><<<grid, 256, sm, s>>>(in, istr, ioff, dout, H, Wd, dW);
+    return cudaGetLastError();
+}
+
+uint64_t splitmix(uint64_t& x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct UNet {
+    int nx, nz;
+    size_t nw;
+    size_t woff[NL + 1];
+    float *w32, *g32, *m32, *v32;           // master weights, gradient, Adam moments
+    bf16 *wb, *wt;                          // bfloat16 weights, flipped/transposed copies
+    // activations (NHWC bfloat16) and gradients
+    bf16 *x0, *h0a, *cat0, *p1, *h1a, *cat1, *p2, *h2a, *h2b, *h1c, *h0c;
+    bf16 *dy, *dh0c, *dcat0, *dh1c, *dcat1, *dh2b, *dh2a, *dp2, *ds1, *dh1a, *dp1, *ds0, *dh0a;
+    float* yf;                              // output NHWC16 float32
+    double* scal;                           // [0] ||B x||^2, [1] loss
+    int step;
+    Bal bal;
+};
+
+static void free_net(UNet* n) {
+    void* p[] = {n->w32, n->g32, n->m32, n->v32, n->wb, n->wt, n->x0, n->h0a, n->cat0, n->p1, n->h1a, n->cat1,
+                 n->p2, n->h2a, n->h2b, n->h1c, n->h0c, n->dy, n->dh0c, n->dcat0, n->dh1c, n->dcat1, n->dh2b,
+                 n->dh2a, n->dp2, n->ds1, n->dh1a, n->dp1, n->ds0, n->dh0a, n->yf, n->scal};
+    for (void* q : p)
+        if (q) cudaFree(q);
+}
+
+UNet* unet_create(int nx, int nz, const double balance[4], unsigned long long seed, cudaError_t* err) {
+    *err = cudaSuccess;
+    if (nx % 32 || nz % 32 || nx <= 0 || nz <= 0) { *err = cudaErrorInvalidValue; return nullptr; }
+    for (int f = 0; f < 4; ++f)
+        if (!(balance[f] > 0.0) || !isfinite(balance[f])) { *err = cudaErrorInvalidValue; return nullptr; }
+    UNet* n = new (std::nothrow) UNet;
+    if (!n) { *err = cudaErrorMemoryAllocation; return nullptr; }
+    memset(n, 0, sizeof(*n));
+    n->nx = nx;
+    n->nz = nz;
+    for (int f = 0; f < 4; ++f) {
+        n->bal.b[f] = (float)balance[f];
+        n->bal.inv[f] = (float)(1.0 / balance[f]);
+    }
+    size_t o = 0;
+    for (int l = 0; l < NL; ++l) { n->woff[l] = o; o += (size_t)KSZ[l] * KSZ[l] * COUT[l] * CIN[l]; }
+    n->woff[NL] = o;
+    n->nw = o;
+    const size_t P0 = (size_t)nx * nz, P1 = P0 / 4, P2 = P0 / 16;
+    auto A = [&](void** p, size_t bytes) {
+        if (*err == cudaSuccess) *err = cudaMalloc(p, bytes);
+    };
+    A((void**)&n->w32, o * 4); A((void**)&n->g32, o * 4); A((void**)&n->m32, o * 4); A((void**)&n->v32, o * 4);
+    A((void**)&n->wb, o * 2); A((void**)&n->wt, o * 2);
+    A((void**)&n->x0, P0 * 16 * 2); A((void**)&n->h0a, P0 * 16 * 2); A((void**)&n->cat0, P0 * 48 * 2);
+    A((void**)&n->p1, P1 * 16 * 2); A((void**)&n->h1a, P1 * 32 * 2); A((void**)&n->cat1, P1 * 96 * 2);
+    A((void**)&n->p2, P2 * 32 * 2); A((void**)&n->h2a, P2 * 64 * 2); A((void**)&n->h2b, P2 * 64 * 2);
+    A((void**)&n->h1c, P1 * 32 * 2); A((void**)&n->h0c, P0 * 16 * 2);
+    A((void**)&n->dy, P0 * 16 * 2); A((void**)&n->dh0c, P0 * 16 * 2); A((void**)&n->dcat0, P0 * 48 * 2);
+    A((void**)&n->dh1c, P1 * 32 * 2); A((void**)&n->dcat1, P1 * 96 * 2); A((void**)&n->dh2b, P2 * 64 * 2);
+    A((void**)&n->dh2a, P2 * 64 * 2); A((void**)&n->dp2, P2 * 32 * 2); A((void**)&n->ds1, P1 * 32 * 2);
+    A((void**)&n->dh1a, P1 * 32 * 2); A((void**)&n->dp1, P1 * 16 * 2); A((void**)&n->ds0, P0 * 16 * 2);
+    A((void**)&n->dh0a, P0 * 16 * 2); A((void**)&n->yf, P0 * 16 * 4); A((void**)&n->scal, 16 * 8);
+    if (*err != cudaSuccess) { free_net(n); delete n; return nullptr; }
+    // seeded init: N(0, 1/fan_in) on real input channels; the last layer and the
+    // padded input / output channels start at zero (untrained net = zero map)
+    std::vector<float> w(o, 0.f);
+    uint64_t st = seed;
+    for (int l = 0; l < NL; ++l) {
+        if (l == L0d) continue;
+        const int ci_real = l == L0a ? 4 : CIN[l];
+        const float sd = sqrtf(1.0f / (KSZ[l] * KSZ[l] * ci_real));
+        for (int tp = 0; tp < KSZ[l] * KSZ[l]; ++tp)
+            for (int co = 0; co < COUT[l]; ++co)
+                for (int ci = 0; ci < ci_real; ++ci) {
+                    const double u1 = ((splitmix(st) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+                    const double u2 = ((splitmix(st) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+                    const double z = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+                    w[n->woff[l] + ((size_t)tp * COUT[l] + co) * CIN[l] + ci] = (float)(sd * z);
+                }
+    }
+    *err = unet_set_weights(n, w.data(), 0);
+    if (*err == cudaSuccess) *err = cudaStreamSynchronize(0);
+    if (*err != cudaSuccess) { free_net(n); delete n; return nullptr; }
+    return n;
+}
+
+void unet_destroy(UNet* n) {
+    if (!n) return;
+    free_net(n);
+    delete n;
+}
+
+size_t unet_num_weights(const UNet* n) { return n->nw; }
+
+cudaError_t unet_get_weights(UNet* n, float* host, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(host, n->w32, n->nw * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t unet_set_weights(UNet* n, const float* host, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(n->w32, host, n->nw * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    to_bf16<<<grid_for(n->nw), 256, 0, s>>>(n->w32, n->wb, n->nw);
+    if ((e = cudaMemsetAsync(n->m32, 0, n->nw * 4, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(n->v32, 0, n->nw * 4, s)) != cudaSuccess) return e;
+    n->step = 0;
+    return cudaGetLastError();
+}
+
+#define UCK(x)                              \
+    do {                                    \
+        cudaError_t e_ = (x);               \
+        if (e_ != cudaSuccess) return e_;   \
+    } while (0)
+
+static cudaError_t forward(UNet* n, const float* x, cudaStream_t s, const int* skip) {
+    const int H0 = n->nz, W0 = n->nx, H1 = H0 / 2, W1 = W0 / 2, H2 = H0 / 4, W2 = W0 / 4;
+    const bf16* w = n->wb;
+    pack_input<<<grid_for((size_t)H0 * W0), 256, 0, s>>>(x, H0 * W0, n->bal, n->x0, skip);
+    UCK((conv<16, 16, 3, false>(n->x0, 16, 0, w + n->woff[L0a], n->h0a, 16, 0, H0, W0, s, skip)));
+    UCK((conv<16, 16, 3, false>(n->h0a, 16, 0, w + n->woff[L0b], n->cat0, 48, 32, H0, W0, s, skip)));
+    avgpool2<<<grid_for((size_t)H1 * W1 * 16), 256, 0, s>>>(n->cat0, 48, 32, n->p1, 16, 0, 16, H0, W0, skip);
+    UCK((conv<16, 32, 3, false>(n->p1, 16, 0, w + n->woff[L1a], n->h1a, 32, 0, H1, W1, s, skip)));
+    UCK((conv<32, 32, 3, false>(n->h1a, 32, 0, w + n->woff[L1b], n->cat1, 96, 64, H1, W1, s, skip)));
+    avgpool2<<<grid_for((size_t)H2 * W2 * 32), 256, 0, s>>>(n->cat1, 96, 64, n->p2, 32, 0, 32, H1, W1, skip);
+    UCK((conv<32, 64, 3, false>(n->p2, 32, 0, w + n->woff[L2a], n->h2a, 64, 0, H2, W2, s, skip)));
+    UCK((conv<64, 64, 3, false>(n->h2a, 64, 0, w + n->woff[L2b], n->h2b, 64, 0, H2, W2, s, skip)));
+    upsample2<<<grid_for((size_t)H1 * W1 * 64), 256, 0, s>>>(n->h2b, 64, 0, n->cat1, 96, 0, 64, H1, W1, skip);
+    UCK((conv<96, 32, 3, false>(n->cat1, 96, 0, w + n->woff[L1c], n->h1c, 32, 0, H1, W1, s, skip)));
+    upsample2<<<grid_for((size_t)H0 * W0 * 32), 256, 0, s>>>(n->h1c, 32, 0, n->cat0, 48, 0, 32, H0, W0, skip);
+    UCK((conv<48, 16, 3, false>(n->cat0, 48, 0, w + n->woff[L0c], n->h0c, 16, 0, H0, W0, s, skip)));
+    UCK((conv<16, 16, 1, true>(n->h0c, 16, 0, w + n->woff[L0d], n->yf, 16, 0, H0, W0, s, skip)));
+    return cudaGetLastError();
+}
+
+// transposed weights of layer l into wt (same offsets)
+static cudaError_t transpose_w(UNet* n, int l, cudaStream_t s) {
+    const int kk = KSZ[l] * KSZ[l];
+    flip_transpose<<<grid_for((size_t)kk * CIN[l] * COUT[l]), 256, 0, s>>>(n->wb + n->woff[l], n->wt + n->woff[l],
+                                                                           CIN[l], COUT[l], kk);
+    return cudaGetLastError();
+}
+
+static cudaError_t backward(UNet* n, cudaStream_t s) {
+    const int H0 = n->nz, W0 = n->nx, H1 = H0 / 2, W1 = W0 / 2, H2 = H0 / 4, W2 = W0 / 4;
+    float* g = n->g32;
+    const bf16* wt = n->wt;
+    UCK(cudaMemsetAsync(g, 0, n->nw * 4, s));
+    for (int l = 0; l < NL; ++l) UCK(transpose_w(n, l, s));
+    UCK((wgrad<16, 16, 1>(n->h0c, 16, 0, n->dy, H0, W0, g + n->woff[L0d], s)));
+    UCK((conv<16, 16, 1, false>(n->dy, 16, 0, wt + n->woff[L0d], n->dh0c, 16, 0, H0, W0, s)));
+    UCK((wgrad<48, 16, 3>(n->cat0, 48, 0, n->dh0c, H0, W0, g + n->woff[L0c], s)));
+    UCK((conv<16, 48, 3, false>(n->dh0c, 16, 0, wt + n->woff[L0c], n->dcat0, 48, 0, H0, W0, s)));
+    upsample2_bwd<<<grid_for((size_t)H1 * W1 * 32), 256, 0, s>>>(n->dcat0, 48, 0, n->dh1c, 32, H0, W0);
+    UCK((wgrad<96, 32, 3>(n->cat1, 96, 0, n->dh1c, H1, W1, g + n->woff[L1c], s)));
+    UCK((conv<32, 96, 3, false>(n->dh1c, 32, 0, wt + n->woff[L1c], n->dcat1, 96, 0, H1, W1, s)));
+    upsample2_bwd<<<grid_for((size_t)H2 * W2 * 64), 256, 0, s>>>(n->dcat1, 96, 0, n->dh2b, 64, H1, W1);
+    UCK((wgrad<64, 64, 3>(n->h2a, 64, 0, n->dh2b, H2, W2, g + n->woff[L2b], s)));
+    UCK((conv<64, 64, 3, false>(n->dh2b, 64, 0, wt + n->woff[L2b], n->dh2a, 64, 0, H2, W2, s)));
+    UCK((wgrad<32, 64, 3>(n->p2, 32, 0, n->dh2a, H2, W2, g + n->woff[L2a], s)));
+    UCK((conv<64, 32, 3, false>(n->dh2a, 64, 0, wt + n->woff[L2a], n->dp2, 32, 0, H2, W2, s)));
+    skip_grad<<<grid_for((size_t)H1 * W1 * 32), 256, 0, s>>>(n->dcat1, 96, 64, n->dp2, n->ds1, 32, H1, W1);
+    UCK((wgrad<32, 32, 3>(n->h1a, 32, 0, n->ds1, H1, W1, g + n->woff[L1b], s)));
+    UCK((conv<32, 32, 3, false>(n->ds1, 32, 0, wt + n->woff[L1b], n->dh1a, 32, 0, H1, W1, s)));
+    UCK((wgrad<16, 32, 3>(n->p1, 16, 0, n->dh1a, H1, W1, g + n->woff[L1a], s)));
+    UCK((conv<32, 16, 3, false>(n->dh1a, 32, 0, wt + n->woff[L1a], n->dp1, 16, 0, H1, W1, s)));
+    skip_grad<<<grid_for((size_t)H0 * W0 * 16), 256, 0, s>>>(n->dcat0, 48, 32, n->dp1, n->ds0, 16, H0, W0);
+    UCK((wgrad<16, 16, 3>(n->h0a, 16, 0, n->ds0, H0, W0, g + n->woff[L0b], s)));
+    UCK((conv<16, 16, 3, false>(n->ds0, 16, 0, wt + n->woff[L0b], n->dh0a, 16, 0, H0, W0, s)));
+    UCK((wgrad<16, 16, 3>(n->x0, 16, 0, n->dh0a, H0, W0, g + n->woff[L0a], s)));
+    return cudaGetLastError();
+}
+
+cudaError_t unet_apply(UNet* n, const float* x, float* y, int accumulate, const int* skip, cudaStream_t s) {
+    UCK(forward(n, x, s, skip));
+    unpack_output<<<grid_for((size_t)4 * n->nx * n->nz), 256, 0, s>>>(n->yf, n->nx * n->nz, n->bal, y, accumulate,
+                                                                      skip);
+    return cudaGetLastError();
+}
+
+int unet_launches_per_apply() { return 15; }
+
+static cudaError_t loss_and_dy(UNet* n, const float* x, const float* t, cudaStream_t s) {
+    const int npix = n->nx * n->nz;
+    UCK(cudaMemsetAsync(n->scal, 0, 2 * sizeof(double), s));
+    sumsq<<<grid_for((size_t)4 * npix), 256, 0, s>>>(x, npix, n->bal, n->scal);
+    loss_grad<<<grid_for(npix), 256, 0, s>>>(n->yf, t, npix, n->bal, n->scal, n->dy, n->scal + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t unet_loss_grad(UNet* n, const float* x, const float* t, double* loss, float* grads_host,
+                           cudaStream_t s) {
+    UCK(forward(n, x, s, nullptr));
+    UCK(loss_and_dy(n, x, t, s));
+    if (grads_host) UCK(backward(n, s));
+    double sc[2];
+    UCK(cudaMemcpyAsync(sc, n->scal, sizeof(sc), cudaMemcpyDeviceToHost, s));
+    if (grads_host) UCK(cudaMemcpyAsync(grads_host, n->g32, n->nw * 4, cudaMemcpyDeviceToHost, s));
+    UCK(cudaStreamSynchronize(s));
+    if (loss) *loss = sc[1];
+    return cudaSuccess;
+}
+
+cudaError_t unet_train(UNet* n, const float* X, const float* T, int npairs, int epochs, float lr,
+                       double* loss_hist, cudaStream_t s) {
+    const size_t plane = (size_t)4 * n->nx * n->nz;
+    for (int ep = 0; ep < epochs; ++ep) {
+        double tot = 0.0;
+        for (int q = 0; q < npairs; ++q) {
+            const int i = (int)((q * 7919ull + ep * 104729ull) % (unsigned long long)npairs);   // fixed shuffle
+            UCK(forward(n, X + i * plane, s, nullptr));
+            UCK(loss_and_dy(n, X + i * plane, T + i * plane, s));
+            UCK(backward(n, s));
+            n->step += 1;
+            const float c1 = 1.0f / (1.0f - powf(0.9f, (float)n->step));
+            const float c2 = 1.0f / (1.0f - powf(0.999f, (float)n->step));
+            adam_step<<<grid_for(n->nw), 256, 0, s>>>(n->w32, n->g32, n->m32, n->v32, n->wb, n->nw, lr, c1, c2);
+            UCK(cudaGetLastError());
+            if (loss_hist) {
+                double sc[2];
+                UCK(cudaMemcpyAsync(sc, n->scal, sizeof(sc), cudaMemcpyDeviceToHost, s));
+                UCK(cudaStreamSynchronize(s));
+                tot += sc[1];
+            }
+        }
+        if (loss_hist) loss_hist[ep] = tot / npairs;
+    }
+    return cudaStreamSynchronize(s);
+}
+
+}  // namespace jfnk

@@ -1,0 +1,55 @@
+// Learned right preconditioner: a linear 3-level convolutional U-Net on the
+// 2-D grid (internal interface of libjfnk).
+//
+// Network (channels 16 / 32 / 64, 3x3 convolutions, zero padding, no biases,
+// no activations, so the map is linear and fixed once trained):
+//   x (4 fields, padded to 16 channels)
+//   L0a 16->16, L0b 16->16 = s0 | avgpool 2x2
+//   L1a 16->32, L1b 32->32 = s1 | avgpool 2x2
+//   L2a 32->64, L2b 64->64       | nearest upsample x2, concat s1 (96)
+//   L1c 96->32                   | nearest upsample x2, concat s0 (48)
+//   L0c 48->16, L0d 1x1 16->16 (first 4 channels are the output fields)
+// Activations are bfloat16 in NHWC layout; convolutions are implicit GEMMs on
+// the tensor cores (mma m16n8k16, bfloat16 inputs, float32 accumulation);
+// weight gradients accumulate in float32; Adam keeps float32 master weights.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace jfnk {
+
+struct UNet;
+
+// Grid nx x nz, both multiples of 32.  Weights: seeded random, last layer zero.
+// balance[4] > 0: per-field factors B; the convolutions see B x and the map is
+// N(x) = B^-1 net(B x), so that the loss weighs the fields as the Jacobian does.
+UNet* unet_create(int nx, int nz, const double balance[4], unsigned long long seed, cudaError_t* err);
+void unet_destroy(UNet* net);
+size_t unet_num_weights(const UNet* net);
+cudaError_t unet_get_weights(UNet* net, float* host, cudaStream_t s);
+cudaError_t unet_set_weights(UNet* net, const float* host, cudaStream_t s);
+
+// Weights, flat float32 order: layers L0a, L0b, L1a, L1b, L2a, L2b, L1c, L0c,
+// L0d; within a layer [tap][cout][cin], tap = ky * k + kx for a k x k kernel
+// whose tap (ky, kx) reads the input pixel at offset (ky - k/2, kx - k/2)
+// (rows = z, columns = x).
+
+// y = N(x) (accumulate = 0) or y += N(x) (accumulate = 1) for 4 float32 field
+// planes of nz x nx points (x fastest); y must not overlap x.  When skip is
+// non-NULL and *skip != 0 at kernel run time, every kernel returns at entry.
+cudaError_t unet_apply(UNet* net, const float* x, float* y, int accumulate, const int* skip, cudaStream_t s);
+int unet_launches_per_apply();
+
+// Loss L = 1/2 ||B (N(x) - t)||^2 / ||B x||^2 and dL/dW (float32, flat order of
+// unet_get_weights) for one pair; grads may be NULL (loss only).
+cudaError_t unet_loss_grad(UNet* net, const float* x, const float* t, double* loss, float* grads_host,
+                           cudaStream_t s);
+
+// Adam on the pairs (X[i], T[i]) (each 4 planes of nx*nz floats, device),
+// epochs passes in a fixed order; loss_hist (host, epochs, may be NULL)
+// receives the mean loss of every epoch.
+cudaError_t unet_train(UNet* net, const float* X, const float* T, int npairs, int epochs, float lr,
+                       double* loss_hist, cudaStream_t s);
+
+}  // namespace jfnk

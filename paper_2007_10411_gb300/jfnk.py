@@ -30,9 +30,15 @@ EXPORTS = (
     "jfnk_get_launch_count", "jfnk_status_str", "jfnk_kernel_timing", "jfnk_kernel_timing_read",
     "jfnk_budgets_static", "jfnk_autotune", "jfnk_set_tiles",
     "jfnk_create_batch", "jfnk_destroy_batch", "jfnk_batch_handle", "jfnk_step_batch",
+    "jfnk_unet_init", "jfnk_unet_num_weights", "jfnk_unet_get_weights", "jfnk_unet_set_weights",
+    "jfnk_unet_capture", "jfnk_unet_pair_count", "jfnk_unet_get_pair", "jfnk_unet_train",
+    "jfnk_unet_forward", "jfnk_unet_loss_grad", "jfnk_set_precond",
 )
 
-KERNEL_FAMILIES = ("arnoldi_a", "arnoldi_b", "arnoldi_c", "jv", "precond", "residual")
+PC_NONE, PC_BLOCK, PC_UNET = 0, 1, 2
+PAIRS_NEWTON, PAIRS_ARNOLDI = 1, 2
+
+KERNEL_FAMILIES = ("arnoldi_a", "arnoldi_b", "arnoldi_c", "jv", "precond", "residual", "unet")
 
 
 class Grid(ctypes.Structure):
@@ -62,14 +68,16 @@ class Stats(ctypes.Structure):
                 ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
                 ("res0", ctypes.c_double), ("res_final", ctypes.c_double), ("tol", ctypes.c_double),
                 ("res_hist", ctypes.c_double * (MAX_NEWTON + 1)),
-                ("gmres_per_newton", ctypes.c_int * MAX_NEWTON)]
+                ("gmres_per_newton", ctypes.c_int * MAX_NEWTON),
+                ("pc_fallback", ctypes.c_int), ("pc_switches", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         k = self.newton_iters
         return {"newton_iters": k, "gmres_iters": self.gmres_iters, "restarts": self.restarts,
                 "converged": bool(self.converged), "res0": self.res0, "res_final": self.res_final,
                 "tol": self.tol, "residual_history": list(self.res_hist[: k + 1]),
-                "gmres_per_newton": list(self.gmres_per_newton[:k])}
+                "gmres_per_newton": list(self.gmres_per_newton[:k]), "pc_fallback": bool(self.pc_fallback),
+                "pc_switches": self.pc_switches}
 
 
 class KernelTime(ctypes.Structure):
@@ -117,6 +125,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.jfnk_destroy_batch.argtypes = [P]
     lib.jfnk_batch_handle.argtypes = [P, I, ctypes.POINTER(P)]
     lib.jfnk_step_batch.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(Stats), ctypes.POINTER(I)]
+    lib.jfnk_unet_init.argtypes = [P, ctypes.c_ulonglong]
+    lib.jfnk_unet_num_weights.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.jfnk_unet_get_weights.argtypes = [P, P, ctypes.c_size_t]
+    lib.jfnk_unet_set_weights.argtypes = [P, P, ctypes.c_size_t]
+    lib.jfnk_unet_capture.argtypes = [P, I, I]
+    lib.jfnk_unet_pair_count.argtypes = [P, ctypes.POINTER(I)]
+    lib.jfnk_unet_get_pair.argtypes = [P, I, P, P]
+    lib.jfnk_unet_train.argtypes = [P, I, ctypes.c_float, P]
+    lib.jfnk_unet_forward.argtypes = [P, P, P]
+    lib.jfnk_unet_loss_grad.argtypes = [P, P, P, ctypes.POINTER(D), P]
+    lib.jfnk_set_precond.argtypes = [P, I]
     lib.jfnk_status_str.argtypes = [I]
     lib.jfnk_status_str.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -158,6 +177,14 @@ def _ptr(t) -> int:
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
         raise ValueError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def _fptr(t) -> int:
+    """Device pointer of a contiguous float32 CUDA tensor (validated)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float32 CUDA tensor")
     return t.data_ptr()
 
 
@@ -260,6 +287,57 @@ class Solver:
         c = ctypes.c_longlong(0)
         _check(self.lib.jfnk_get_launch_count(self.h, ctypes.byref(c)), "jfnk_get_launch_count")
         return c.value
+
+    # ------------------------------------------------ learned preconditioner
+    def set_precond(self, mode: int):
+        _check(self.lib.jfnk_set_precond(self.h, int(mode)), "jfnk_set_precond")
+
+    def unet_init(self, seed: int = 0):
+        _check(self.lib.jfnk_unet_init(self.h, int(seed)), "jfnk_unet_init")
+
+    def unet_num_weights(self) -> int:
+        c = ctypes.c_size_t(0)
+        _check(self.lib.jfnk_unet_num_weights(self.h, ctypes.byref(c)), "jfnk_unet_num_weights")
+        return c.value
+
+    def unet_get_weights(self):
+        """Float32 master weights as a numpy array (flat order of include/jfnk.h)."""
+        import numpy as np
+        w = np.zeros(self.unet_num_weights(), dtype=np.float32)
+        _check(self.lib.jfnk_unet_get_weights(self.h, w.ctypes.data, w.size), "jfnk_unet_get_weights")
+        return w
+
+    def unet_set_weights(self, w):
+        import numpy as np
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(self.lib.jfnk_unet_set_weights(self.h, w.ctypes.data, w.size), "jfnk_unet_set_weights")
+
+    def unet_capture(self, capacity: int, kinds: int = PAIRS_NEWTON | PAIRS_ARNOLDI):
+        _check(self.lib.jfnk_unet_capture(self.h, int(capacity), int(kinds)), "jfnk_unet_capture")
+
+    def unet_pair_count(self) -> int:
+        c = ctypes.c_int(0)
+        _check(self.lib.jfnk_unet_pair_count(self.h, ctypes.byref(c)), "jfnk_unet_pair_count")
+        return c.value
+
+    def unet_get_pair(self, i: int, X, T):
+        _check(self.lib.jfnk_unet_get_pair(self.h, int(i), _fptr(X), _fptr(T)), "jfnk_unet_get_pair")
+
+    def unet_train(self, epochs: int, lr: float) -> list:
+        hist = (ctypes.c_double * max(1, int(epochs)))()
+        _check(self.lib.jfnk_unet_train(self.h, int(epochs), float(lr), hist), "jfnk_unet_train")
+        return list(hist[:epochs])
+
+    def unet_forward(self, x, y):
+        _check(self.lib.jfnk_unet_forward(self.h, _fptr(x), _fptr(y)), "jfnk_unet_forward")
+
+    def unet_loss_grad(self, x, t, grads: bool = True):
+        import numpy as np
+        loss = ctypes.c_double(0.0)
+        g = np.zeros(self.unet_num_weights(), dtype=np.float32) if grads else None
+        _check(self.lib.jfnk_unet_loss_grad(self.h, _fptr(x), _fptr(t), ctypes.byref(loss),
+                                            None if g is None else g.ctypes.data), "jfnk_unet_loss_grad")
+        return loss.value, g
 
 
 class Batch:
