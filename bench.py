@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3, help="host-buffer steps through jfnk_step_host")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample (0: skip)")
     p.add_argument("--no-kernel-timing", action="store_true")
+    p.add_argument("--learned", default="thermal_stable_256x128:40:3,thermal_stable_1024x512:5:2",
+                   help="learned-preconditioner legs workload:epochs:steps,... ('' skips)")
     return p.parse_args()
 
 
@@ -323,6 +325,52 @@ def run_batch(args, rank: int, world: int, local_rank: int):
     print(json.dumps(line), flush=True)
 
 
+def learned_leg(jfnk, synth, torch, stream, name: str, epochs: int, steps: int, barrier, slowest) -> dict:
+    """Learned right preconditioner against the field-block one on one workload.
+
+    Training pairs: every Arnoldi step of two plain steps from the initial
+    state (at most 900); Adam, lr 3e-4.  Then `steps` timed steps from the same
+    state with each preconditioner (CUDA events on the solver's stream).
+    """
+    c = synth.with_options(synth.case(name), precision=synth.PREC_MIXED, precond=jfnk.PC_UNET)
+    npt = c["grid"]["nx"] * c["grid"]["nz"]
+    s = jfnk.Solver(c, stream=stream)
+    s.set_precond(jfnk.PC_BLOCK)
+    s.unet_init(7)
+    s.unet_capture(900, jfnk.PAIRS_ARNOLDI)
+    u = torch.from_numpy(synth.initial_state(c).reshape(-1).copy()).cuda()
+    for _ in range(2):
+        s.step(u)
+    pairs = s.unet_pair_count()
+    barrier()
+    t0 = time.perf_counter()
+    hist = s.unet_train(epochs, 3e-4)
+    train_s = time.perf_counter() - t0
+    s.unet_capture(0, 0)
+    out = {"workload": name, "pairs": pairs, "epochs": epochs, "train_s": train_s,
+           "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "steps": steps}
+    for mode, tag in ((jfnk.PC_BLOCK, "block"), (jfnk.PC_UNET, "learned")):
+        s.set_precond(mode)
+        v = u.clone()
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        st = [s.step(v) for _ in range(steps)]
+        a1.record(stream)
+        a1.synchronize()
+        ms = slowest(a0.elapsed_time(a1))
+        out[tag] = {"value": npt * steps / (ms / 1e3) / 1e6, "ms_per_step": ms / steps,
+                    "gmres_iters_per_step": statistics.mean(x["gmres_iters"] for x in st),
+                    "newton_per_step": statistics.mean(x["newton_iters"] for x in st),
+                    "converged": all(x["converged"] for x in st),
+                    "pc_switches": sum(x.get("pc_switches", 0) for x in st),
+                    "pc_fallback": sum(int(x.get("pc_fallback", False)) for x in st)}
+    out["learned_over_block"] = out["learned"]["value"] / out["block"]["value"]
+    s.close()
+    return out
+
+
 def run_ours(args, rank: int, world: int, local_rank: int):
     import numpy as np
     import torch
@@ -413,6 +461,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "newton_per_step": statistics.mean(s["newton_iters"] for s in st64)}
         s64.close()
 
+    learned = []
+    if args.learned and case["grid"]["dim"] == 2:
+        for item in args.learned.split(","):
+            name, ep, st = item.split(":")
+            learned.append(learned_leg(jfnk, synth, torch, stream, name, int(ep), int(st), barrier, slowest))
+
     if rank != 0:
         return
     iters = statistics.mean(s["gmres_iters"] for s in stats)
@@ -458,6 +512,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "newton_per_step": newt, "gmres_iters_per_step": iters,
         "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "kernels": kernels,
         "fp64_plain": fp64, "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+        "learned_pc": learned or None,
+        "learned_over_fp64": next((L["learned"]["value"] / fp64["value"] for L in learned
+                                   if fp64 and L["workload"] == args.workload), None),
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

@@ -30,6 +30,11 @@ constexpr int KSZ[NL] = {3, 3, 3, 3, 3, 3, 3, 3, 1};
 
 typedef __nv_bfloat16 bf16;
 
+// Field balance of the network: it sees B x and returns B N(x).
+struct Bal {
+    float b[4], inv[4];
+};
+
 // convolution tile: CONV_TH rows x CONV_TW columns, one warp per pair of rows
 constexpr int CONV_TW = 8, CONV_TH = 16, CONV_THREADS = 32 * CONV_TH / 2;
 
@@ -59,10 +64,6 @@ __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r
                  : "r"(addr));
 }
 
-__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
-}
-
 // 16-byte global -> shared copy; src_bytes = 0 writes zeros (src is not read).
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes));
@@ -81,24 +82,90 @@ struct ConvShape {
     static constexpr size_t SMEM = sizeof(bf16) * (size_t)(W_ELEMS + 2 * X_ELEMS);
 };
 
-template <int CI, int IH, int IW, int CIP>
-__device__ __forceinline__ void stage_tile(const bf16* __restrict__ in, int istr, int ioff, int H, int Wd, int y0,
-                                           int x0, int hp, uint32_t xs_addr) {
+// Input staging modes of a convolution (what the CTA copies into its tile):
+//   IN_NHWC   a bfloat16 NHWC tensor (pixel stride astr, channel offset aoff)
+//   IN_PACK   B x from four float32 field planes (channels 4.. are zero)
+//   IN_POOL   2x2 average of a tensor of twice the grid's size
+//   IN_UPCAT  [nearest upsampling of a half-size tensor a (CU channels) | b]
+// Output modes: OUT_BF16 / OUT_F32 NHWC (pixel stride ostr, channel offset
+// ooff), OUT_PLANES: channels 0..3 times B^-1 into four float32 planes,
+// stored or added.
+enum { IN_NHWC = 0, IN_PACK = 1, IN_POOL = 2, IN_UPCAT = 3 };
+enum { OUT_BF16 = 0, OUT_F32 = 1, OUT_PLANES = 2 };
+
+struct ConvIn {
+    const bf16* a;
+    int astr, aoff;
+    const bf16* b;      // IN_UPCAT: the full-size part
+    int bstr, boff;
+    const float* x;     // IN_PACK: field planes
+};
+
+struct ConvOut {
+    void* o;
+    int ostr, ooff;
+    int accumulate;     // OUT_PLANES
+};
+
+template <int CI, int IH, int IW, int CIP, int INMODE, int CU>
+__device__ __forceinline__ void stage_tile(const ConvIn& in, const Bal& bal, int H, int Wd, int y0, int x0, int hp,
+                                           uint32_t xs_addr) {
     constexpr int VPP = CI / 8;
     for (int idx = threadIdx.x; idx < IH * IW * VPP; idx += blockDim.x) {
         const int pix = idx / VPP, v = idx - pix * VPP;
         const int iy = pix / IW, ix = pix - iy * IW;
         const int gy = y0 + iy - hp, gx = x0 + ix - hp;
         const bool ok = gy >= 0 && gy < H && gx >= 0 && gx < Wd;
-        const bf16* src = ok ? in + ((size_t)gy * Wd + gx) * istr + ioff + v * 8 : in;
-        cp_async16(xs_addr + (uint32_t)((pix * CIP + v * 8) * sizeof(bf16)), src, ok ? 16 : 0);
+        const uint32_t dst = xs_addr + (uint32_t)((pix * CIP + v * 8) * sizeof(bf16));
+        if constexpr (INMODE == IN_NHWC) {
+            const bf16* src = ok ? in.a + ((size_t)gy * Wd + gx) * in.astr + in.aoff + v * 8 : in.a;
+            cp_async16(dst, src, ok ? 16 : 0);
+        } else if constexpr (INMODE == IN_UPCAT) {
+            const bf16* src;
+            if (v * 8 < CU)
+                src = ok ? in.a + ((size_t)(gy >> 1) * (Wd >> 1) + (gx >> 1)) * in.astr + in.aoff + v * 8 : in.a;
+            else
+                src = ok ? in.b + ((size_t)gy * Wd + gx) * in.bstr + in.boff + (v * 8 - CU) : in.b;
+            cp_async16(dst, src, ok ? 16 : 0);
+        } else {
+            __align__(16) bf16 val[8];
+            if constexpr (INMODE == IN_PACK) {
+                const size_t npix = (size_t)H * Wd;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) val[c] = __float2bfloat16(0.f);
+                if (v == 0 && ok) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        val[c] = __float2bfloat16(bal.b[c] * in.x[(size_t)c * npix + (size_t)gy * Wd + gx]);
+                }
+            } else {   // IN_POOL: same arithmetic as the avgpool2 kernel (channels summed in d order)
+                const int W2 = 2 * Wd;
+                float sum[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) sum[c] = 0.f;
+                if (ok) {
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        const uint4 q = *reinterpret_cast<const uint4*>(
+                            in.a + ((size_t)(2 * gy + d / 2) * W2 + 2 * gx + d % 2) * in.astr + in.aoff + v * 8);
+                        const bf16* e = reinterpret_cast<const bf16*>(&q);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) sum[c] += __bfloat162float(e[c]);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) val[c] = __float2bfloat16(0.25f * sum[c]);
+            }
+            asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(dst),
+                         "r"(reinterpret_cast<uint32_t*>(val)[0]), "r"(reinterpret_cast<uint32_t*>(val)[1]),
+                         "r"(reinterpret_cast<uint32_t*>(val)[2]), "r"(reinterpret_cast<uint32_t*>(val)[3]));
+        }
     }
 }
 
-template <int CI, int CO, int KS, bool OUTF32>
+template <int CI, int CO, int KS, int INMODE, int OUTMODE, int CU>
 __global__ void __launch_bounds__(CONV_THREADS)
-conv_mma(const bf16* __restrict__ in, int istr, int ioff, const bf16* __restrict__ W, void* out, int ostr,
-         int ooff, int H, int Wd, const int* skip) {
+conv_mma(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int Wd, const int* skip) {
     if (skip != nullptr && *skip) return;
     using S = ConvShape<CI, CO, KS>;
     constexpr int HP = S::HP, IW = S::IW, IH = S::IH, CIP = S::CIP;
@@ -117,7 +184,8 @@ conv_mma(const bf16* __restrict__ in, int istr, int ioff, const bf16* __restrict
         cp_async16(ws_addr + (uint32_t)((row * CIP + v * 8) * sizeof(bf16)), W + (size_t)row * CI + v * 8, 16);
     }
     cp_async_commit();
-    stage_tile<CI, IH, IW, CIP>(in, istr, ioff, H, Wd, (tile / ntx) * CONV_TH, (tile % ntx) * CONV_TW, HP, xs_addr0);
+    stage_tile<CI, IH, IW, CIP, INMODE, CU>(in, bal, H, Wd, (tile / ntx) * CONV_TH, (tile % ntx) * CONV_TW, HP,
+                                            xs_addr0);
     cp_async_commit();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
@@ -129,8 +197,8 @@ conv_mma(const bf16* __restrict__ in, int istr, int ioff, const bf16* __restrict
     for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
         const int next = tile + gridDim.x;
         if (next < ntiles)
-            stage_tile<CI, IH, IW, CIP>(in, istr, ioff, H, Wd, (next / ntx) * CONV_TH, (next % ntx) * CONV_TW, HP,
-                                        xs_addr0 + (buf ^ 1) * xs_bytes);
+            stage_tile<CI, IH, IW, CIP, INMODE, CU>(in, bal, H, Wd, (next / ntx) * CONV_TH, (next % ntx) * CONV_TW,
+                                                    HP, xs_addr0 + (buf ^ 1) * xs_bytes);
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
@@ -150,47 +218,63 @@ conv_mma(const bf16* __restrict__ in, int istr, int ioff, const bf16* __restrict
                 uint32_t a0, a1, a2, a3;
                 ldsm_x4(a_base + c * 32, a0, a1, a2, a3);
 #pragma unroll
-                for (int nb = 0; nb < CO / 8; nb += 2) {
+                for (int nb = 0; nb < CO / 8; nb += 2) {   // CO / 8 is even for every layer
+                    // matrices: (nb, k0), (nb, k8), (nb+1, k0), (nb+1, k8)
                     uint32_t b0, b1, b2, b3;
-                    if (nb + 1 < CO / 8) {
-                        // matrices: (nb, k0), (nb, k8), (nb+1, k0), (nb+1, k8)
-                        const int i = lane >> 3;
-                        const int co = (nb + (i >> 1)) * 8 + (lane & 7);
-                        ldsm_x4(ws_addr + (uint32_t)(((tap * CO + co) * CIP + c * 16 + (i & 1) * 8) * sizeof(bf16)),
-                                b0, b1, b2, b3);
-                        mma16816(acc[nb], a0, a1, a2, a3, b0, b1);
-                        mma16816(acc[nb + 1], a0, a1, a2, a3, b2, b3);
-                    } else {
-                        const int i = (lane >> 3) & 1;
-                        const int co = nb * 8 + (lane & 7);
-                        ldsm_x2(ws_addr + (uint32_t)(((tap * CO + co) * CIP + c * 16 + i * 8) * sizeof(bf16)), b0, b1);
-                        mma16816(acc[nb], a0, a1, a2, a3, b0, b1);
-                    }
+                    const int i = lane >> 3;
+                    const int co = (nb + (i >> 1)) * 8 + (lane & 7);
+                    ldsm_x4(ws_addr + (uint32_t)(((tap * CO + co) * CIP + c * 16 + (i & 1) * 8) * sizeof(bf16)), b0,
+                            b1, b2, b3);
+                    mma16816(acc[nb], a0, a1, a2, a3, b0, b1);
+                    mma16816(acc[nb + 1], a0, a1, a2, a3, b2, b3);
                 }
             }
         }
         const int y0 = (tile / ntx) * CONV_TH, x0 = (tile % ntx) * CONV_TW;
         const int gyA = y0 + 2 * warp, gyB = gyA + 1, gx = x0 + g;
+        if (gx < Wd) {
+            if constexpr (OUTMODE == OUT_PLANES) {
+                // channels 2t, 2t+1 of block 0: lanes t = 0, 1 hold the four field channels
+                if (t < 2) {
+                    float* o = reinterpret_cast<float*>(out.o);
+                    const size_t npix = (size_t)H * Wd;
+                    const float inv[2] = {t == 0 ? bal.inv[0] : bal.inv[2], t == 0 ? bal.inv[1] : bal.inv[3]};
 #pragma unroll
-        for (int nb = 0; nb < CO / 8; ++nb) {
-            const int co = nb * 8 + 2 * t;
-            if (gx < Wd) {
-                if (OUTF32) {
-                    float* o = reinterpret_cast<float*>(out);
-                    if (gyA < H)
-                        *reinterpret_cast<float2*>(o + ((size_t)gyA * Wd + gx) * ostr + ooff + co) =
-                            make_float2(acc[nb][0], acc[nb][1]);
-                    if (gyB < H)
-                        *reinterpret_cast<float2*>(o + ((size_t)gyB * Wd + gx) * ostr + ooff + co) =
-                            make_float2(acc[nb][2], acc[nb][3]);
-                } else {
-                    bf16* o = reinterpret_cast<bf16*>(out);
-                    if (gyA < H)
-                        *reinterpret_cast<__nv_bfloat162*>(o + ((size_t)gyA * Wd + gx) * ostr + ooff + co) =
-                            __floats2bfloat162_rn(acc[nb][0], acc[nb][1]);
-                    if (gyB < H)
-                        *reinterpret_cast<__nv_bfloat162*>(o + ((size_t)gyB * Wd + gx) * ostr + ooff + co) =
-                            __floats2bfloat162_rn(acc[nb][2], acc[nb][3]);
+                    for (int q = 0; q < 2; ++q) {
+                        const int ch = 2 * t + q;
+                        if (gyA < H) {
+                            float* d = o + (size_t)ch * npix + (size_t)gyA * Wd + gx;
+                            const float v = acc[0][q] * inv[q];
+                            *d = out.accumulate ? *d + v : v;
+                        }
+                        if (gyB < H) {
+                            float* d = o + (size_t)ch * npix + (size_t)gyB * Wd + gx;
+                            const float v = acc[0][2 + q] * inv[q];
+                            *d = out.accumulate ? *d + v : v;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int nb = 0; nb < CO / 8; ++nb) {
+                    const int co = nb * 8 + 2 * t;
+                    if constexpr (OUTMODE == OUT_F32) {
+                        float* o = reinterpret_cast<float*>(out.o);
+                        if (gyA < H)
+                            *reinterpret_cast<float2*>(o + ((size_t)gyA * Wd + gx) * out.ostr + out.ooff + co) =
+                                make_float2(acc[nb][0], acc[nb][1]);
+                        if (gyB < H)
+                            *reinterpret_cast<float2*>(o + ((size_t)gyB * Wd + gx) * out.ostr + out.ooff + co) =
+                                make_float2(acc[nb][2], acc[nb][3]);
+                    } else {
+                        bf16* o = reinterpret_cast<bf16*>(out.o);
+                        if (gyA < H)
+                            *reinterpret_cast<__nv_bfloat162*>(o + ((size_t)gyA * Wd + gx) * out.ostr + out.ooff + co) =
+                                __floats2bfloat162_rn(acc[nb][0], acc[nb][1]);
+                        if (gyB < H)
+                            *reinterpret_cast<__nv_bfloat162*>(o + ((size_t)gyB * Wd + gx) * out.ostr + out.ooff + co) =
+                                __floats2bfloat162_rn(acc[nb][2], acc[nb][3]);
+                    }
                 }
             }
         }
@@ -260,11 +344,6 @@ conv_wgrad(const bf16* __restrict__ in, int istr, int ioff, const bf16* __restri
 }
 
 // ---------------------------------------------------------------- element-wise
-// Field balance of the network: it sees B x and returns B N(x).
-struct Bal {
-    float b[4], inv[4];
-};
-
 // NHWC16 input B x from four float32 field planes (channels 4..15 zero).
 __global__ void pack_input(const float* __restrict__ x, int npix, Bal bal, bf16* __restrict__ out,
                            const int* skip) {
@@ -337,18 +416,6 @@ __global__ void skip_grad(const bf16* __restrict__ dcat, int cstr, int coff, con
     }
 }
 
-// network output (float32 NHWC16, first 4 channels, balanced units) -> 4
-// field planes B^-1 y, stored (accumulate = 0) or added (accumulate = 1)
-__global__ void unpack_output(const float* __restrict__ y, int npix, Bal bal, float* __restrict__ out,
-                              int accumulate, const int* skip) {
-    if (skip != nullptr && *skip) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * npix; i += gridDim.x * blockDim.x) {
-        const int c = i / npix, p = i - c * npix;
-        const float v = y[(size_t)p * 16 + c] * bal.inv[c];
-        out[i] = accumulate ? out[i] + v : v;
-    }
-}
-
 // out += ||B x||^2 over the 4 field planes
 __global__ void sumsq(const float* __restrict__ x, int npix, Bal bal, double* out) {
     double s = 0.0;
@@ -418,27 +485,36 @@ int grid_for(size_t n) {
     return (int)(b > 1216 ? 1216 : (b > 0 ? b : 1));
 }
 
-template <int CI, int CO, int KS, bool OUTF32>
-cudaError_t conv(const bf16* in, int istr, int ioff, const bf16* W, void* out, int ostr, int ooff, int H, int Wd,
-                 cudaStream_t s, const int* skip = nullptr) {
+template <int CI, int CO, int KS, int INMODE, int OUTMODE, int CU = 0>
+cudaError_t conv_ex(const ConvIn& in, const Bal& bal, const bf16* W, const ConvOut& out, int H, int Wd,
+                    cudaStream_t s, const int* skip) {
     using S = ConvShape<CI, CO, KS>;
+    auto kern = conv_mma<CI, CO, KS, INMODE, OUTMODE, CU>;
     static int max_ctas = 0;   // resident CTAs on the device (persistent grid)
     if (max_ctas == 0) {
-        cudaError_t e = cudaFuncSetAttribute(conv_mma<CI, CO, KS, OUTF32>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
         if (e != cudaSuccess) return e;
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_mma<CI, CO, KS, OUTF32>, CONV_THREADS,
-                                                               S::SMEM)) != cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CONV_THREADS, S::SMEM)) != cudaSuccess)
             return e;
         max_ctas = sms * (per_sm > 0 ? per_sm : 1);
     }
     const int ntiles = ((Wd + CONV_TW - 1) / CONV_TW) * ((H + CONV_TH - 1) / CONV_TH);
     const int grid = ntiles < max_ctas ? ntiles : max_ctas;
-    conv_mma<CI, CO, KS, OUTF32><<<grid, CONV_THREADS, S::SMEM, s>>>(in, istr, ioff, W, out, ostr, ooff, H, Wd, skip);
+    kern<<<grid, CONV_THREADS, S::SMEM, s>>>(in, bal, W, out, H, Wd, skip);
     return cudaGetLastError();
+}
+
+// plain NHWC -> NHWC convolution (training path)
+template <int CI, int CO, int KS, bool OUTF32>
+cudaError_t conv(const bf16* in, int istr, int ioff, const bf16* W, void* out, int ostr, int ooff, int H, int Wd,
+                 cudaStream_t s, const int* skip = nullptr) {
+    ConvIn ci{in, istr, ioff, nullptr, 0, 0, nullptr};
+    ConvOut co{out, ostr, ooff, 0};
+    Bal bal{};
+    return conv_ex<CI, CO, KS, IN_NHWC, OUTF32 ? OUT_F32 : OUT_BF16>(ci, bal, W, co, H, Wd, s, skip);
 }
 
 template <int CI, int CO, int KS>
@@ -596,6 +672,40 @@ static cudaError_t forward(UNet* n, const float* x, cudaStream_t s, const int* s
     return cudaGetLastError();
 }
 
+// Inference forward with pooling, upsampling + concatenation, input packing
+// and output unpacking fused into the convolutions (9 launches; the same
+// arithmetic as forward() followed by unpack_output).
+static cudaError_t forward_fused(UNet* n, const float* x, float* y, int accumulate, cudaStream_t s,
+                                 const int* skip) {
+    const int H0 = n->nz, W0 = n->nx, H1 = H0 / 2, W1 = W0 / 2, H2 = H0 / 4, W2 = W0 / 4;
+    const bf16* w = n->wb;
+    const ConvIn none{nullptr, 0, 0, nullptr, 0, 0, nullptr};
+    auto nhwc = [&](const bf16* a, int str, int off) { ConvIn c = none; c.a = a; c.astr = str; c.aoff = off; return c; };
+    auto to = [&](void* o, int str, int off) { return ConvOut{o, str, off, 0}; };
+    ConvIn pk = none;
+    pk.x = x;
+    UCK((conv_ex<16, 16, 3, IN_PACK, OUT_BF16>(pk, n->bal, w + n->woff[L0a], to(n->h0a, 16, 0), H0, W0, s, skip)));
+    UCK((conv_ex<16, 16, 3, IN_NHWC, OUT_BF16>(nhwc(n->h0a, 16, 0), n->bal, w + n->woff[L0b], to(n->cat0, 48, 32), H0,
+                                               W0, s, skip)));
+    UCK((conv_ex<16, 32, 3, IN_POOL, OUT_BF16>(nhwc(n->cat0, 48, 32), n->bal, w + n->woff[L1a], to(n->h1a, 32, 0), H1,
+                                               W1, s, skip)));
+    UCK((conv_ex<32, 32, 3, IN_NHWC, OUT_BF16>(nhwc(n->h1a, 32, 0), n->bal, w + n->woff[L1b], to(n->cat1, 96, 64), H1,
+                                               W1, s, skip)));
+    UCK((conv_ex<32, 64, 3, IN_POOL, OUT_BF16>(nhwc(n->cat1, 96, 64), n->bal, w + n->woff[L2a], to(n->h2a, 64, 0), H2,
+                                               W2, s, skip)));
+    UCK((conv_ex<64, 64, 3, IN_NHWC, OUT_BF16>(nhwc(n->h2a, 64, 0), n->bal, w + n->woff[L2b], to(n->h2b, 64, 0), H2,
+                                               W2, s, skip)));
+    ConvIn uc1{n->h2b, 64, 0, n->cat1, 96, 64, nullptr};
+    UCK((conv_ex<96, 32, 3, IN_UPCAT, OUT_BF16, 64>(uc1, n->bal, w + n->woff[L1c], to(n->h1c, 32, 0), H1, W1, s,
+                                                    skip)));
+    ConvIn uc0{n->h1c, 32, 0, n->cat0, 48, 32, nullptr};
+    UCK((conv_ex<48, 16, 3, IN_UPCAT, OUT_BF16, 32>(uc0, n->bal, w + n->woff[L0c], to(n->h0c, 16, 0), H0, W0, s,
+                                                    skip)));
+    ConvOut pl{y, 0, 0, accumulate};
+    UCK((conv_ex<16, 16, 1, IN_NHWC, OUT_PLANES>(nhwc(n->h0c, 16, 0), n->bal, w + n->woff[L0d], pl, H0, W0, s, skip)));
+    return cudaGetLastError();
+}
+
 // transposed weights of layer l into wt (same offsets)
 static cudaError_t transpose_w(UNet* n, int l, cudaStream_t s) {
     const int kk = KSZ[l] * KSZ[l];
@@ -635,13 +745,10 @@ static cudaError_t backward(UNet* n, cudaStream_t s) {
 }
 
 cudaError_t unet_apply(UNet* n, const float* x, float* y, int accumulate, const int* skip, cudaStream_t s) {
-    UCK(forward(n, x, s, skip));
-    unpack_output<<<grid_for((size_t)4 * n->nx * n->nz), 256, 0, s>>>(n->yf, n->nx * n->nz, n->bal, y, accumulate,
-                                                                      skip);
-    return cudaGetLastError();
+    return forward_fused(n, x, y, accumulate, s, skip);
 }
 
-int unet_launches_per_apply() { return 15; }
+int unet_launches_per_apply() { return 9; }
 
 static cudaError_t loss_and_dy(UNet* n, const float* x, const float* t, cudaStream_t s) {
     const int npix = n->nx * n->nz;
