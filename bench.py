@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3, help="host-buffer steps through jfnk_step_host")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample (0: skip)")
     p.add_argument("--no-kernel-timing", action="store_true")
+    p.add_argument("--unet-forward", type=int, default=0,
+                   help="only time this many applies of the learned-preconditioner network (profiling)")
     p.add_argument("--learned", default="thermal_stable_256x128:40:3,thermal_stable_1024x512:5:2",
                    help="learned-preconditioner legs workload:epochs:steps,... ('' skips)")
     return p.parse_args()
@@ -112,9 +114,41 @@ def measured_peaks() -> dict:
     try:
         with open(path) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
     except (OSError, KeyError, ValueError):
-        return {"hbm_gbs": 6800.0, "source": "fallback"}
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# Algorithmic FLOPs of one network apply per full-resolution grid point: 2 k^2
+# cin cout per layer and output pixel (L0a counts its 4 real input channels,
+# L0d its 4 used outputs), level-1 layers / 4, level-2 layers / 16.
+UNET_FLOPS_PER_POINT = (2 * 9 * 4 * 16 + 2 * 9 * 16 * 16                      # L0a, L0b
+                        + (2 * 9 * 16 * 32 + 2 * 9 * 32 * 32) // 4            # L1a, L1b
+                        + (2 * 9 * 32 * 64 + 2 * 9 * 64 * 64) // 16           # L2a, L2b
+                        + (2 * 9 * 96 * 32) // 4 + 2 * 9 * 48 * 16 + 2 * 16 * 4)  # L1c, L0c, L0d
+
+
+def unet_apply_timing(jfnk, torch, s, npt: int, reps: int, stream) -> dict:
+    """CUDA-event time of the network apply alone (jfnk_unet_forward) and its tensor roofline."""
+    x = torch.randn(4 * npt, device="cuda", dtype=torch.float32, generator=torch.Generator("cuda").manual_seed(5))
+    y = torch.empty_like(x)
+    for _ in range(3):
+        s.unet_forward(x, y)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(reps):
+        s.unet_forward(x, y)
+    a1.record(stream)
+    a1.synchronize()
+    ms = a0.elapsed_time(a1) / reps
+    peaks = measured_peaks()
+    flops = UNET_FLOPS_PER_POINT * npt
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"ms_per_apply": ms, "flops_per_apply": flops, "bound": "tensor", "achieved": achieved,
+            "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
+            "peak_source": peaks["source"] + " (MEASURED_PEAKS.json bf16_tflops, burst)",
+            "kernel": "conv_mma (mma.sync m16n8k16 bf16, 9 launches per apply)"}
 
 
 def ncu_traffic() -> dict:
@@ -367,8 +401,32 @@ def learned_leg(jfnk, synth, torch, stream, name: str, epochs: int, steps: int, 
                     "pc_switches": sum(x.get("pc_switches", 0) for x in st),
                     "pc_fallback": sum(int(x.get("pc_fallback", False)) for x in st)}
     out["learned_over_block"] = out["learned"]["value"] / out["block"]["value"]
+    out["network_apply"] = unet_apply_timing(jfnk, torch, s, npt, 20, stream)
     s.close()
     return out
+
+
+def run_unet_forward(args):
+    """Time `--unet-forward` applies of a network with seeded random weights (profiling entry)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2007_10411_gb300 import jfnk, synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    c = synth.with_options(synth.case(args.workload), precision=synth.PREC_MIXED, precond=jfnk.PC_UNET)
+    npt = c["grid"]["nx"] * c["grid"]["nz"]
+    stream = torch.cuda.current_stream()
+    s = jfnk.Solver(c, stream=stream)
+    s.unet_init(1)
+    rng = np.random.Generator(np.random.PCG64(3))
+    s.unet_set_weights((0.05 * rng.standard_normal(s.unet_num_weights())).astype(np.float32))
+    r = unet_apply_timing(jfnk, torch, s, npt, args.unet_forward, stream)
+    r.update({"workload": args.workload, "applies": args.unet_forward})
+    print(json.dumps(r), flush=True)
+    s.close()
 
 
 def run_ours(args, rank: int, world: int, local_rank: int):
@@ -522,6 +580,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
 def main():
     args = parse()
+    if args.unet_forward > 0:
+        run_unet_forward(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
