@@ -53,6 +53,11 @@ __device__ __forceinline__ double2 reload(const double2* p) {
     return r;
 }
 
+// Field of vector entry i (planes of npt entries); 32-bit division where it fits.
+__device__ __forceinline__ int field_of(size_t i, int npt) {
+    return i <= 0xffffffffull ? (int)((unsigned)i / (unsigned)npt) : (int)(i / (size_t)npt);
+}
+
 static int stream_blocks(size_t n) {
     size_t b = (n + NTHREADS - 1) / NTHREADS;
     return (int)(b < (size_t)MAX_STREAM_BLOCKS ? (b > 0 ? b : 1) : MAX_STREAM_BLOCKS);
@@ -158,46 +163,138 @@ __device__ void givens_update(Ctl* c, int j, int m, const double* h2, double wn2
     }
 }
 
+__device__ __forceinline__ float4 shfl_xor_v(unsigned mask, float4 v, int m) {
+    return make_float4(__shfl_xor_sync(mask, v.x, m), __shfl_xor_sync(mask, v.y, m), __shfl_xor_sync(mask, v.z, m),
+                       __shfl_xor_sync(mask, v.w, m));
+}
+__device__ __forceinline__ double2 shfl_xor_v(unsigned mask, double2 v, int m) {
+    return make_double2(__shfl_xor_sync(mask, v.x, m), __shfl_xor_sync(mask, v.y, m));
+}
+__device__ __forceinline__ float shfl_xor_v(unsigned mask, float v, int m) { return __shfl_xor_sync(mask, v, m); }
+__device__ __forceinline__ double shfl_xor_v(unsigned mask, double v, int m) { return __shfl_xor_sync(mask, v, m); }
+__device__ __forceinline__ float4 addv(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+__device__ __forceinline__ double2 addv(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float addv(float a, float b) { return a + b; }
+__device__ __forceinline__ double addv(double a, double b) { return a + b; }
+__device__ __forceinline__ float4 fmav(float a, float4 x, float4 y) {
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ double2 fmav(double a, double2 x, double2 y) { return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y)); }
+__device__ __forceinline__ float fmav(float a, float x, float y) { return fmaf(a, x, y); }
+__device__ __forceinline__ double fmav(double a, double x, double y) { return fma(a, x, y); }
+__device__ __forceinline__ float4 subv(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+__device__ __forceinline__ double2 subv(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float subv(float a, float b) { return a - b; }
+__device__ __forceinline__ double subv(double a, double b) { return a - b; }
+__device__ __forceinline__ float dotv(float a, float b) { return a * b; }
+__device__ __forceinline__ double dotv(double a, double b) { return a * b; }
+template <typename VT> __device__ __forceinline__ VT zerov();
+template <> __device__ __forceinline__ float4 zerov<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ double2 zerov<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float zerov<float>() { return 0.f; }
+template <> __device__ __forceinline__ double zerov<double>() { return 0.0; }
+
+// Pass B loads of one element (a VT vector of W entries, or a scalar in the
+// tail) for lane q of its group, which owns basis vectors q*CH .. q*CH+CH-1.
+template <typename T, typename VT, int CH>
+__device__ __forceinline__ void load_b(const T* __restrict__ V, size_t ldv, size_t i, int nv, int q, VT (&v)[CH]) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int k = q * CH + c;
+        v[c] = k < nv ? reinterpret_cast<const VT*>(V + (size_t)k * ldv)[i] : zerov<VT>();
+    }
+}
+
+// Pass B arithmetic of one element: the group's partial sums of V h1 meet by
+// shuffles, w' = w - V h1 is stored by lane 0, every lane dots its vectors with w'.
+template <typename T, typename VT, int CH, int KS>
+__device__ __forceinline__ void work_b(const VT (&v)[CH], VT wv, T* __restrict__ w, size_t i, int q, const T* h1s,
+                                       T (&acc)[CH], T& accn) {
+    VT sum = zerov<VT>();
+#pragma unroll
+    for (int c = 0; c < CH; ++c) sum = fmav(h1s[q * CH + c], v[c], sum);
+    const unsigned mask = __activemask();     // the KS lanes of a group are active together
+#pragma unroll
+    for (int o = 1; o < KS; o <<= 1) sum = addv(sum, shfl_xor_v(mask, sum, o));
+    const VT wp = subv(wv, sum);
+#pragma unroll
+    for (int c = 0; c < CH; ++c) acc[c] += dotv(v[c], wp);
+    if (q == 0) {
+        accn += dotv(wp, wp);
+        reinterpret_cast<VT*>(w)[i] = wp;
+    }
+}
+
+// Pass B, split over KS lanes per element: w' = w - V h1 (stored over w),
+// ||w'||^2 and h2 = V^T w'; the last block runs the Givens update.  Each lane
+// keeps its CH basis entries in registers for both uses, so every basis vector
+// is read from memory once; the next element's loads are issued before the
+// current one is combined (software pipeline).
 template <typename T, int NV>
 __global__ void __launch_bounds__(NTHREADS, 2)
 arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int nv, int m,
           double* part, Ctl* ctl) {
     if (ctl->done) return;
+    constexpr int KS = 4, CH = NV / KS;
     __shared__ T h1s[NV];
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) h1s[k] = T(ctl->h1[k]);
+    __shared__ T red[NV + 1][NTHREADS / 32];
+    for (int k = threadIdx.x; k < NV; k += blockDim.x) h1s[k] = k < nv ? T(ctl->h1[k]) : T(0);
     __syncthreads();
-    // slot 0: ||w'||^2, slot 1 + k: v_k . w'
     using VT = typename V4<T>::type;
     constexpr int W = V4<T>::W;
-    T acc_t[NV + 1];
+    const int q = threadIdx.x & (KS - 1);
+    T acc[CH];
 #pragma unroll
-    for (int k = 0; k <= NV; ++k) acc_t[k] = T(0);
+    for (int c = 0; c < CH; ++c) acc[c] = T(0);
+    T accn = T(0);
     const size_t nvec = n / W;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvec; i += stride) {
-        VT wp = reinterpret_cast<const VT*>(w)[i];
-        // first use of v_k (runtime trip count, a few loads in flight at a time)
-#pragma unroll 4
-        for (int k = 0; k < nv; ++k) wp = axpyv(wp, h1s[k], reinterpret_cast<const VT*>(V + k * ldv)[i]);
-        // second use of v_k: re-read (L1 / L2 hit) instead of holding NV vectors in registers
-#pragma unroll
-        for (int k = 0; k < NV; ++k)
-            if (k < nv) acc_t[1 + k] += dotv(reload(reinterpret_cast<const VT*>(V + k * ldv) + i), wp);
-        acc_t[0] += dotv(wp, wp);
-        reinterpret_cast<VT*>(w)[i] = wp;
+    const size_t g0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) / KS;
+    const size_t gstride = (size_t)gridDim.x * blockDim.x / KS;
+    VT vn[CH], wn = zerov<VT>();
+    if (g0 < nvec) {
+        load_b<T, VT, CH>(V, ldv, g0, nv, q, vn);
+        wn = reinterpret_cast<const VT*>(w)[g0];
     }
-    for (size_t i = nvec * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        T wp = w[i];
+    for (size_t i = g0; i < nvec; i += gstride) {
+        VT v[CH];
 #pragma unroll
-        for (int k = 0; k < NV; ++k)
-            if (k < nv) wp -= h1s[k] * V[k * ldv + i];
-#pragma unroll
-        for (int k = 0; k < NV; ++k)
-            if (k < nv) acc_t[1 + k] += V[k * ldv + i] * wp;
-        acc_t[0] += wp * wp;
-        w[i] = wp;
+        for (int c = 0; c < CH; ++c) v[c] = vn[c];
+        const VT wv = wn;
+        const size_t inext = i + gstride;
+        if (inext < nvec) {
+            load_b<T, VT, CH>(V, ldv, inext, nv, q, vn);
+            wn = reinterpret_cast<const VT*>(w)[inext];
+        }
+        work_b<T, VT, CH, KS>(v, wv, w, i, q, h1s, acc, accn);
     }
-    block_partials<NV + 1, T>(acc_t, nv + 1, part, gridDim.x, blockIdx.x);
+    for (size_t i = nvec * W + g0; i < n; i += gstride) {
+        T v[CH];
+        load_b<T, T, CH>(V, ldv, i, nv, q, v);
+        work_b<T, T, CH, KS>(v, w[i], w, i, q, h1s, acc, accn);
+    }
+    // block sums: slot 0 = ||w'||^2, slot 1 + k = v_k . w' (fixed shuffle trees; float64 across warps)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        T x = acc[c];
+#pragma unroll
+        for (int o = KS; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane < KS) red[1 + lane * CH + c][warp] = x;
+    }
+    {
+        T x = accn;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[0][warp] = x;
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    for (int k = threadIdx.x; k < nv + 1; k += blockDim.x) {
+        double t = 0.0;
+        for (int ww = 0; ww < nw; ++ww) t += (double)red[k][ww];
+        part[(size_t)k * gridDim.x + blockIdx.x] = t;
+        __threadfence();          // publish before the block's arrival is counted
+    }
     if (arrive_last(&ctl->counter[CNT_PASSB], gridDim.x)) {
         __shared__ double tot[NV + 1];
         final_sums(part, gridDim.x, nv + 1, tot);
@@ -246,7 +343,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 template <typename T, int NV>
-__global__ void __launch_bounds__(NTHREADS)
+__global__ void __launch_bounds__(NTHREADS, 2)
 update_x(const T* __restrict__ Z, size_t ldz, double* __restrict__ x, T* __restrict__ xT, size_t n,
          double* part, Ctl* ctl) {
     const int K = ctl->k;
@@ -262,18 +359,22 @@ update_x(const T* __restrict__ Z, size_t ldz, double* __restrict__ x, T* __restr
     T acc[1] = {T(0)};
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        // all K loads of the element are issued before the (serial) combination
+        T zv[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) zv[k] = k < K ? Z[k * ldz + i] : T(0);
         double s;
         if (sizeof(T) == sizeof(double)) {
             s = x[i];
 #pragma unroll
             for (int k = 0; k < NV; ++k)
-                if (k < K) s += ys[k] * (double)Z[k * ldz + i];
+                if (k < K) s += ys[k] * (double)zv[k];
         } else {
             float hi = 0.0f, lo = 0.0f;
 #pragma unroll
             for (int k = 0; k < NV; ++k)
                 if (k < K) {
-                    const float z = (float)Z[k * ldz + i];
+                    const float z = (float)zv[k];
                     const float ph = yh[k] * z;
                     const float pl = fmaf(yh[k], z, -ph);      // exact product error
                     float t, e;
@@ -309,7 +410,7 @@ cycle_init(Geo G, const double* __restrict__ R, T* __restrict__ V0, double* __re
     const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int f = (int)(i / G.npt);
+        const int f = field_of(i, G.npt);
         V0[i] = T(-R[i] * G.inv_scale[f] * inv);
         x[i] = 0.0;
     }
@@ -337,7 +438,7 @@ restart_residual(Geo G, const double* __restrict__ R, const T* __restrict__ w, T
     double acc[1] = {0.0};
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int f = (int)(i / G.npt);
+        const int f = field_of(i, G.npt);
         const double r = -R[i] * G.inv_scale[f] - (double)w[i];
         V0[i] = T(r);
         acc[0] += r * r;
@@ -375,7 +476,7 @@ __global__ void __launch_bounds__(NTHREADS)
 newton_update(Geo G, double* __restrict__ u, const double* __restrict__ x, T* __restrict__ uT, size_t n) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int f = (int)(i / G.npt);
+        const int f = field_of(i, G.npt);
         const double v = u[i] + G.scale[f] * x[i];
         u[i] = v;
         if (uT != nullptr) uT[i] = T(v);
@@ -394,7 +495,7 @@ __global__ void __launch_bounds__(NTHREADS)
 rescale_k(Geo G, const TI* __restrict__ in, TO* __restrict__ out, size_t n, int multiply) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int f = (int)(i / G.npt);
+        const int f = field_of(i, G.npt);
         out[i] = TO((double)in[i] * (multiply ? G.scale[f] : G.inv_scale[f]));
     }
 }
@@ -406,7 +507,7 @@ norm2_k(Geo G, const T* __restrict__ a, size_t n, int weighted, int slot, double
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
         double v = (double)a[i];
-        if (weighted) v *= G.inv_scale[i / G.npt];
+        if (weighted) v *= G.inv_scale[field_of(i, G.npt)];
         acc[0] += v * v;
     }
     block_partials<1>(acc, 1, part, gridDim.x, blockIdx.x);
@@ -464,7 +565,7 @@ pair_stage_newton_k(Geo G, const double* __restrict__ R, float* __restrict__ X, 
     const double inv = b > 0.0 ? 1.0 / b : 0.0;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int f = (int)(i / G.npt);
+        const int f = field_of(i, G.npt);
         X[i] = (float)(-R[i] * G.inv_scale[f] * inv);
     }
 }
