@@ -19,6 +19,8 @@
 // reductions run in float64.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -65,6 +67,12 @@ static int stream_blocks(size_t n) {
 
 // Grid of the multi-dot kernels: >= two CTAs per SM, and enough CTAs that no
 // thread accumulates more than PER_THREAD vector elements in low precision.
+// Grid of Arnoldi passes A and C (register use fits three CTAs per SM).
+static int dot_blocks(size_t nvec) {
+    size_t b = (nvec + NTHREADS - 1) / NTHREADS;
+    return (int)(b < (size_t)MAX_DOT_BLOCKS ? (b > 0 ? b : 1) : MAX_DOT_BLOCKS);
+}
+
 static int reduce_blocks(size_t nvec) {
     size_t b = (nvec + (size_t)NTHREADS * PER_THREAD - 1) / ((size_t)NTHREADS * PER_THREAD);
     if (b < (size_t)MAX_STREAM_BLOCKS) return stream_blocks(nvec);
@@ -73,7 +81,7 @@ static int reduce_blocks(size_t nvec) {
 
 // ---------------------------------------------------------------- pass A
 template <typename T, int NV>
-__global__ void __launch_bounds__(NTHREADS, 2)
+__global__ void __launch_bounds__(NTHREADS, 3)
 arnoldi_a(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv,
           double* part, Ctl* ctl) {
     if (ctl->done) return;
@@ -304,7 +312,7 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int 
 
 // ---------------------------------------------------------------- pass C
 template <typename T, int NV>
-__global__ void __launch_bounds__(NTHREADS, 2)
+__global__ void __launch_bounds__(NTHREADS, 3)
 arnoldi_c(T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv, Ctl* ctl) {
     if (ctl->done) return;
     using VT = typename V4<T>::type;
@@ -619,7 +627,7 @@ pc_eps_k(const float* __restrict__ z, size_t n, double* part, Ctl* ctl) {
 template <typename T>
 cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int nv, double* part,
                              Ctl* ctl, cudaStream_t s) {
-    const int nb = reduce_blocks(n / V4<T>::W);
+    const int nb = std::max(dot_blocks(n / V4<T>::W), reduce_blocks(n / V4<T>::W));
     if (nv <= 8) arnoldi_a<T, 8><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, part, ctl);
     else if (nv <= 16) arnoldi_a<T, 16><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, part, ctl);
     else arnoldi_a<T, 32><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, part, ctl);
@@ -639,7 +647,7 @@ cudaError_t launch_arnoldi_b(const T* V, size_t ldv, T* w, size_t n, int nv, int
 template <typename T>
 cudaError_t launch_arnoldi_c(T* V, size_t ldv, const T* w, size_t n, int nv, Ctl* ctl,
                              cudaStream_t s) {
-    const int nb = stream_blocks(n / V4<T>::W);
+    const int nb = dot_blocks(n / V4<T>::W);
     if (nv <= 8) arnoldi_c<T, 8><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, ctl);
     else if (nv <= 16) arnoldi_c<T, 16><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, ctl);
     else arnoldi_c<T, 32><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, ctl);
