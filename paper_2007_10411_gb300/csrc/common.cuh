@@ -72,6 +72,32 @@ struct Ctl {
     unsigned int counter[8];         // last-block counters, one per kernel family
 };
 
+// Programmatic dependent launch.  Kernels of the Arnoldi step are launched
+// with launch_pdl: the next kernel may be scheduled before this one has
+// finished, so every such kernel calls pdl_wait() before its first global read
+// (it returns once the preceding grid has completed and its writes are
+// visible) and pdl_trigger() once its main loop is done (only the reduction
+// tail remains), letting the successor's launch overlap that tail.  Both are
+// no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 enum CounterSlot { CNT_STENCIL = 0, CNT_PASSA, CNT_PASSB, CNT_UPDATE, CNT_RESTART, CNT_PC, CNT_EDDY, CNT_MISC };
 
 // ---------------------------------------------------------------- reductions

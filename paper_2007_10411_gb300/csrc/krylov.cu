@@ -84,6 +84,7 @@ template <typename T, int NV>
 __global__ void __launch_bounds__(NTHREADS, 3)
 arnoldi_a(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv,
           double* part, Ctl* ctl) {
+    pdl_wait();
     if (ctl->done) return;
     using VT = typename V4<T>::type;
     constexpr int W = V4<T>::W;
@@ -103,6 +104,7 @@ arnoldi_a(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n
         for (int k = 0; k < NV; ++k)
             if (k < nv) acc_t[k] += V[k * ldv + i] * w[i];
     }
+    pdl_trigger();
     block_partials<NV, T>(acc_t, nv, part, gridDim.x, blockIdx.x);
     if (arrive_last(&ctl->counter[CNT_PASSA], gridDim.x)) {
         __shared__ double tot[NV];
@@ -242,6 +244,7 @@ template <typename T, int NV>
 __global__ void __launch_bounds__(NTHREADS, 2)
 arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int nv, int m,
           double* part, Ctl* ctl) {
+    pdl_wait();
     if (ctl->done) return;
     constexpr int KS = 4, CH = NV / KS;
     __shared__ T h1s[NV];
@@ -280,6 +283,7 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int 
         load_b<T, T, CH>(V, ldv, i, nv, q, v);
         work_b<T, T, CH, KS>(v, w[i], w, i, q, h1s, acc, accn);
     }
+    pdl_trigger();
     // block sums: slot 0 = ||w'||^2, slot 1 + k = v_k . w' (fixed shuffle trees; float64 across warps)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -314,6 +318,7 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int 
 template <typename T, int NV>
 __global__ void __launch_bounds__(NTHREADS, 3)
 arnoldi_c(T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv, Ctl* ctl) {
+    pdl_wait();
     if (ctl->done) return;
     using VT = typename V4<T>::type;
     constexpr int W = V4<T>::W;
@@ -628,30 +633,27 @@ template <typename T>
 cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int nv, double* part,
                              Ctl* ctl, cudaStream_t s) {
     const int nb = std::max(dot_blocks(n / V4<T>::W), reduce_blocks(n / V4<T>::W));
-    if (nv <= 8) arnoldi_a<T, 8><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, part, ctl);
-    else if (nv <= 16) arnoldi_a<T, 16><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, part, ctl);
-    else arnoldi_a<T, 32><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, part, ctl);
-    return cudaGetLastError();
+    if (nv <= 8) return launch_pdl(arnoldi_a<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, part, ctl);
+    if (nv <= 16) return launch_pdl(arnoldi_a<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, part, ctl);
+    return launch_pdl(arnoldi_a<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, part, ctl);
 }
 
 template <typename T>
 cudaError_t launch_arnoldi_b(const T* V, size_t ldv, T* w, size_t n, int nv, int m,
                              double* part, Ctl* ctl, cudaStream_t s) {
     const int nb = reduce_blocks(n / V4<T>::W);
-    if (nv <= 8) arnoldi_b<T, 8><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);
-    else if (nv <= 16) arnoldi_b<T, 16><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);
-    else arnoldi_b<T, 32><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, m, part, ctl);
-    return cudaGetLastError();
+    if (nv <= 8) return launch_pdl(arnoldi_b<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, m, part, ctl);
+    if (nv <= 16) return launch_pdl(arnoldi_b<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, m, part, ctl);
+    return launch_pdl(arnoldi_b<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, m, part, ctl);
 }
 
 template <typename T>
 cudaError_t launch_arnoldi_c(T* V, size_t ldv, const T* w, size_t n, int nv, Ctl* ctl,
                              cudaStream_t s) {
     const int nb = dot_blocks(n / V4<T>::W);
-    if (nv <= 8) arnoldi_c<T, 8><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, ctl);
-    else if (nv <= 16) arnoldi_c<T, 16><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, ctl);
-    else arnoldi_c<T, 32><<<nb, NTHREADS, 0, s>>>(V, ldv, w, n, nv, ctl);
-    return cudaGetLastError();
+    if (nv <= 8) return launch_pdl(arnoldi_c<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, ctl);
+    if (nv <= 16) return launch_pdl(arnoldi_c<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, ctl);
+    return launch_pdl(arnoldi_c<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, ctl);
 }
 
 template <typename T>

@@ -365,6 +365,7 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
     constexpr int SX = TX + 2 * HALO, SZ = TZ + 2 * HALO;
     constexpr int QX = TX + 2 * R, QZ = TZ + 2 * R;
     constexpr int QN = QX * QZ;
+    pdl_wait();
     if (check_done && ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sa = reinterpret_cast<T*>(smem_raw);
@@ -611,6 +612,7 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
     constexpr int QX = TX + 2 * R, QZ = TZ + 2 * R;
     constexpr int TY = NTHREADS / TX;              // thread rows
     static_assert(NTHREADS % TX == 0 && TZ % TY == 0, "tile must tile the block");
+    pdl_wait();
     if (check_done && ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* zs = reinterpret_cast<T*>(smem_raw);      // [SZ][SX] current iterate, halo 2r
@@ -714,6 +716,7 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
             }
         }
     }
+    pdl_trigger();
     if (LAST) {
         const int nblk = gridDim.x * gridDim.y * gridDim.z;
         const int blk = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -878,8 +881,7 @@ static cudaError_t launch_jvd_t(const Geo& G, const T* u, const T* v, T* out, Ct
         configured = true;
     }
     dim3 grid((G.nx + TX - 1) / TX, (G.nz + TZ - 1) / TZ);
-    jv_diff2d<T, SMAG, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, u, v, out, ctl, check_done);
-    return cudaGetLastError();
+    return launch_pdl(jv_diff2d<T, SMAG, TX, TZ>, grid, NTHREADS, sm, s, G, u, v, out, ctl, check_done);
 }
 
 template <typename T, int SMAG>
@@ -951,17 +953,17 @@ static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, 
         T* zo = last ? z : zbuf[k & 1];
         T* dO = dbuf[k & 1];
         grid.z = last ? 4 : 3;            // the p block is written by the last sweep only
+        cudaError_t le;
         if (first && last)
-            cheb2d<T, SMAG, 1, 1, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            le = launch_pdl(cheb2d<T, SMAG, 1, 1, TX, TZ>, grid, NTHREADS, sm, s, G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else if (first)
-            cheb2d<T, SMAG, 1, 0, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            le = launch_pdl(cheb2d<T, SMAG, 1, 0, TX, TZ>, grid, NTHREADS, sm, s, G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else if (last)
-            cheb2d<T, SMAG, 0, 1, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            le = launch_pdl(cheb2d<T, SMAG, 0, 1, TX, TZ>, grid, NTHREADS, sm, s, G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else
-            cheb2d<T, SMAG, 0, 0, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            le = launch_pdl(cheb2d<T, SMAG, 0, 0, TX, TZ>, grid, NTHREADS, sm, s, G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         if (launches) ++*launches;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        if (le != cudaSuccess) return le;
         zin = zo;
         din = dO;
     }
