@@ -16,7 +16,9 @@ statement of the method, with no blocking, fusion or reordering:
                  the semi-discrete right-hand side F (Eqs. ch2_28-ch2_30, Eq. ds),
                  the trapezoidal residual R (Eq. ns), the finite-difference
                  Jacobian-vector product (Eq. fd), the field-block
-                 preconditioner (Section 2.5.2) and the energy budgets (Section 3.1.3).
+                 preconditioner (Section 2.5.2), the acoustic Schur-complement
+                 preconditioner (the semi-implicit elimination Section 2.5
+                 follows) and the energy budgets (Section 3.1.3).
 * ``krylov``     restarted right-preconditioned GMRES(m) with classical
                  Gram-Schmidt applied twice and Givens rotations (Section 2.5.1).
 * ``newton``     the inexact Newton outer loop of one implicit step (Section 2.5.1).

@@ -282,6 +282,57 @@ class Model:
             Z[f] = chebyshev(lambda x: self.block_operator(K, x, f), Rhat[f], lo, hi, sweeps)
         return Z
 
+    # ------------------------------------------------- acoustic Schur complement
+    def _d_interior(self, a: np.ndarray, parity, j: int) -> np.ndarray:
+        """D_j a on the interior of a field with the given mirror parity."""
+        return self.crop(self.grad_halo(self.extend(a, self.H, parity))[j], self.r)
+
+    def helmholtz(self, p: np.ndarray) -> np.ndarray:
+        """H p = (2/dt) p - a sum_j D_j D_j p, a = gamma_p pbar theta0 dt / 2 (p even in z)."""
+        a = self.gamma_p * self.pbar * self.theta0 * self.dt / 2.0
+        P = self.extend(p, self.H, self.parity[self.ip])
+        return 2.0 * p / self.dt - a * self.div_halo(self.grad_halo(P))
+
+    def helmholtz_bounds(self):
+        """Gershgorin interval of H: [2/dt, 2/dt + (3/2)^2 a sum_j 1/h_j^2]."""
+        a = self.gamma_p * self.pbar * self.theta0 * self.dt / 2.0
+        return self.gershgorin_bounds(a)
+
+    def schur_precond(self, U_frozen: np.ndarray, Vhat: np.ndarray, sweeps: int) -> np.ndarray:
+        """Acoustic Schur-complement preconditioner z = P v (2-D, scaled units).
+
+        Section 2.5 follows the semi-implicit elimination of the fast acoustic
+        terms (Skamarock & Klemp): keeping only (2/dt) I and the pressure
+        gradient / divergence couplings of Eqs. ch2_28-ch2_30 linearised about
+        the reference pressure pbar,
+            (2/dt) du + theta0 D_x dp = r_u,  (2/dt) dw + theta0 D_z dp = r_w,
+            (2/dt) dp + gamma_p pbar (D_x du + D_z dw) = r_p,
+        the velocities are eliminated, leaving the pressure Helmholtz problem
+            H dp = r_p - gamma_p pbar (dt/2) (D_x r_u + D_z r_w),
+        solved approximately by ``sweeps`` Chebyshev steps on its Gershgorin
+        interval (a fixed linear map); then du = (dt/2)(r_u - theta0 D_x dp),
+        dw = (dt/2)(r_w - theta0 D_z dp).  Advection, diffusion and buoyancy
+        are dropped; theta gets one Chebyshev step of its field block
+        (r_theta / theta_c).  r = W^-1 v, z = W dz.
+        """
+        assert self.dim == 2
+        dt = self.dt
+        r = self.unscale(Vhat)
+        ru, rw, rth, rp = r[self.iu], r[self.iw], r[self.ith], r[self.ip]
+        div_r = self._d_interior(ru, self.parity[self.iu], 0) + self._d_interior(rw, self.parity[self.iw], 1)
+        rhs = rp - self.gamma_p * self.pbar * (dt / 2.0) * div_r
+        lo, hi = self.helmholtz_bounds()
+        dp = chebyshev(self.helmholtz, rhs, lo, hi, sweeps)
+        du = (dt / 2.0) * (ru - self.theta0 * self._d_interior(dp, self.parity[self.ip], 0))
+        dw = (dt / 2.0) * (rw - self.theta0 * self._d_interior(dp, self.parity[self.ip], 1))
+        K_M, K_H = self.frozen_eddy(U_frozen)
+        kth = float(np.max(K_H)) if not np.isscalar(K_H) else float(K_H)
+        lo_t, hi_t = self.gershgorin_bounds(kth)
+        dth = rth / (0.5 * (lo_t + hi_t))
+        Z = np.zeros_like(r)
+        Z[self.iu], Z[self.iw], Z[self.ith], Z[self.ip] = du, dw, dth, dp
+        return self.scale(Z)
+
     # ------------------------------------------------------------ budgets
     def budgets(self, U: np.ndarray) -> dict:
         """Energy budgets and extremes (Section 3.1.3, literal E_k and E_p formulas)."""
