@@ -62,7 +62,7 @@ typedef enum {
 enum { JFNK_FREESLIP = 0, JFNK_NOSLIP = 1 };
 enum { JFNK_SGS_CONST = 0, JFNK_SGS_SMAGORINSKY = 1 };
 enum { JFNK_FP64 = 0, JFNK_MIXED = 1 };
-enum { JFNK_PC_NONE = 0, JFNK_PC_BLOCK = 1, JFNK_PC_UNET = 2 };
+enum { JFNK_PC_NONE = 0, JFNK_PC_BLOCK = 1, JFNK_PC_UNET = 2, JFNK_PC_SCHUR = 3 };
 
 /* Largest Krylov dimension m accepted by jfnk_create. */
 #define JFNK_MAX_KRYLOV 32
@@ -106,9 +106,19 @@ typedef struct {
  * flexible    accepted for compatibility; the library always stores the
  *             preconditioned directions (FGMRES form), identical in exact
  *             arithmetic to right-preconditioned GMRES for a linear M.
- * precond     JFNK_PC_NONE, JFNK_PC_BLOCK (pc_sweeps Chebyshev steps per block)
- *             or JFNK_PC_UNET (the block preconditioner plus a learned
- *             correction, see "Learned right preconditioner" below).
+ * precond     JFNK_PC_NONE, JFNK_PC_BLOCK (pc_sweeps Chebyshev steps per block),
+ *             JFNK_PC_UNET (the block preconditioner plus a learned
+ *             correction, see "Learned right preconditioner" below) or
+ *             JFNK_PC_SCHUR (2-D, pc_sweeps >= 2: the acoustic Schur
+ *             complement of the semi-implicit elimination Section 2.5
+ *             follows -- only (2/dt) I and the pressure gradient / divergence
+ *             couplings linearised about pbar are kept, the velocities are
+ *             eliminated, the pressure Helmholtz operator
+ *             H = (2/dt) I - gamma_p pbar theta0 (dt/2) sum_j D_j D_j gets
+ *             pc_sweeps Chebyshev steps on its Gershgorin interval, the
+ *             velocities are back-substituted, theta gets r_theta / theta_c
+ *             of its field block; advection, diffusion and buoyancy are
+ *             dropped).
  * newton_rtol, newton_atol_factor, eta, max_newton, max_restarts: stopping rules
  *             ||W R|| <= max(rtol ||W R_0||, atol_factor ||W 2u^n/dt||);
  *             GMRES stops at ||W(R + J du)|| <= eta ||W R||.

@@ -37,6 +37,8 @@ def implicit_step(model: Model, Un: np.ndarray, opts: dict, stats: dict | None =
         b = -model.scale(R)
         if opts["precond"] == 1:
             pc = (lambda v, Uk=U: model.precond(Uk, v, opts["pc_sweeps"]))
+        elif opts["precond"] == 3:
+            pc = (lambda v, Uk=U: model.schur_precond(Uk, v, opts["pc_sweeps"]))
         else:
             pc = None
         rec = {}

@@ -34,6 +34,7 @@ struct Geo {
     double scale[5], inv_scale[5];
     const double* heat;               // surface flux H(x) or nullptr
     int tile_jv, tile_pc;             // tile shapes of the float32 Jv / preconditioner kernels
+    int pc_schur;                     // preconditioner: 0 field-block, 1 acoustic Schur complement (2-D)
 };
 
 constexpr int NUM_TILE_SHAPES = 4;

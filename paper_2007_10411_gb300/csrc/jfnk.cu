@@ -98,7 +98,8 @@ static jfnk_status validate(const jfnk_grid* g, const jfnk_strat* s, const jfnk_
         return JFNK_ERR_INVALID_ARG;
     if (o->precision != JFNK_FP64 && o->precision != JFNK_MIXED) return JFNK_ERR_INVALID_ARG;
     if (o->krylov_m < 1 || o->krylov_m > JFNK_MAX_KRYLOV) return JFNK_ERR_INVALID_ARG;
-    if (o->precond != JFNK_PC_NONE && o->precond != JFNK_PC_BLOCK && o->precond != JFNK_PC_UNET)
+    if (o->precond != JFNK_PC_NONE && o->precond != JFNK_PC_BLOCK && o->precond != JFNK_PC_UNET &&
+        o->precond != JFNK_PC_SCHUR)
         return JFNK_ERR_INVALID_ARG;
     if (o->pc_sweeps < 1 || o->pc_sweeps > MAX_PC_SWEEPS) return JFNK_ERR_INVALID_ARG;
     if (!finite_pos(o->newton_rtol) || !(o->newton_atol_factor >= 0.0) ||
@@ -116,6 +117,7 @@ static jfnk_status validate(const jfnk_grid* g, const jfnk_strat* s, const jfnk_
     if (o->precond == JFNK_PC_UNET &&
         (g->dim != 2 || o->precision != JFNK_MIXED || g->nx % 32 != 0 || g->nz % 32 != 0))
         return JFNK_ERR_UNSUPPORTED;
+    if (o->precond == JFNK_PC_SCHUR && (g->dim != 2 || o->pc_sweeps < 2)) return JFNK_ERR_UNSUPPORTED;
     return JFNK_OK;
 }
 
@@ -267,6 +269,7 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     G.heat = nullptr;
     G.tile_jv = 0;
     G.tile_pc = 0;
+    G.pc_schur = opts->precond == JFNK_PC_SCHUR;
 
     const size_t eT = h->mixed ? sizeof(float) : sizeof(double);
     const size_t nb8 = h->ld * sizeof(double);
@@ -954,9 +957,11 @@ extern "C" jfnk_status jfnk_unet_loss_grad(jfnk_handle* h, const float* x, const
 
 extern "C" jfnk_status jfnk_set_precond(jfnk_handle* h, int precond) {
     if (!h) return JFNK_ERR_INVALID_ARG;
-    if (precond != JFNK_PC_NONE && precond != JFNK_PC_BLOCK && precond != JFNK_PC_UNET)
+    if (precond != JFNK_PC_NONE && precond != JFNK_PC_BLOCK && precond != JFNK_PC_UNET &&
+        precond != JFNK_PC_SCHUR)
         return JFNK_ERR_INVALID_ARG;
     if (precond == JFNK_PC_UNET && !unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
+    if (precond == JFNK_PC_SCHUR && (h->G.dim != 2 || h->opts.pc_sweeps < 2)) return JFNK_ERR_UNSUPPORTED;
     if (precond != JFNK_PC_NONE && !h->Z) {
         const size_t eT = h->mixed ? sizeof(float) : sizeof(double);
         CK(cudaStreamSynchronize(h->stream));
@@ -967,6 +972,7 @@ extern "C" jfnk_status jfnk_set_precond(jfnk_handle* h, int precond) {
         }
     }
     h->opts.precond = precond;
+    h->G.pc_schur = precond == JFNK_PC_SCHUR;
     return JFNK_OK;
 }
 

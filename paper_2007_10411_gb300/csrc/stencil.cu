@@ -597,6 +597,26 @@ __global__ void pc_setup(Geo G, int sweeps, Ctl* ctl) {
             rho = rho_new;
         }
     }
+    if (G.nf == 4) {
+        // 2-D: slot 4 holds the pressure Helmholtz operator of the acoustic Schur
+        // complement, H = (2/dt) I - a sum_j D_j D_j, a = gamma_p pbar theta0 dt / 2
+        const double a = G.gamma_p * G.pbar * G.theta0 / G.two_over_dt;
+        const double lo = G.two_over_dt, hi = lo + 2.25 * a * h2;
+        const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+        const bool degenerate = delta <= 1e-14 * theta;
+        const double sigma = degenerate ? 1.0 : theta / delta;
+        double rho = 1.0 / sigma;
+        ctl->cheb[4][0][0] = 1.0 / theta;
+        ctl->cheb[4][0][1] = 0.0;
+        ctl->cheb[4][0][2] = 0.0;
+        for (int k = 1; k < sweeps && k < MAX_PC_SWEEPS; ++k) {
+            const double rho_new = 1.0 / (2.0 * sigma - rho);
+            ctl->cheb[4][k][0] = 1.0 / theta;
+            ctl->cheb[4][k][1] = degenerate ? 0.0 : rho_new * rho;
+            ctl->cheb[4][k][2] = degenerate ? 0.0 : 2.0 * rho_new / delta;
+            rho = rho_new;
+        }
+    }
 }
 
 // One CTA = one field of one TX x TZ tile; threads laid out (TX, NTHREADS/TX)
@@ -746,6 +766,168 @@ pc_diag(Geo G, const T* __restrict__ r, T* __restrict__ z, size_t n, double* par
         const T zv = r[i] * inv_th[f];
         z[i] = zv;
         acc[0] += zv * zv;
+    }
+    block_partials<1, T>(acc, 1, part, gridDim.x, blockIdx.x);
+    if (arrive_last(&ctl->counter[CNT_PC], gridDim.x)) {
+        __shared__ double tot[1];
+        final_sums(part, gridDim.x, 1, tot);
+        if (threadIdx.x == 0) {
+            const double zn = sqrt(tot[0]);
+            ctl->eps_jv = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+        }
+    }
+}
+
+// ============================================================================
+// Acoustic Schur-complement preconditioner (2-D, scaled units).  Keeping only
+// (2/dt) I and the pressure gradient / divergence couplings of Eqs.
+// ch2_28-ch2_30 (linearised about pbar) -- the fast terms the semi-implicit
+// scheme that Section 2.5 follows eliminates -- the velocities drop out:
+//   H dp = v_p - c_div (D_x v_u + D_z v_w),   H = (2/dt) I - a sum_j D_j D_j,
+//   z_u = (dt/2)(v_u - c_grad D_x dp),   z_w = (dt/2)(v_w - c_grad D_z dp),
+// with c_div = gamma_p pbar (dt/2) s_u / s_p, c_grad = theta0 s_p / s_u and
+// a = gamma_p pbar theta0 dt / 2.  H is inverted approximately by Chebyshev
+// sweeps on its Gershgorin interval (coefficients ctl->cheb[4], pc_setup);
+// theta gets r_theta / theta_c of its field block.
+// ============================================================================
+template <typename T>
+__device__ __forceinline__ T plane_dx(const T* __restrict__ f, const Geo& G, int gz, int gx, T inv_h) {
+    const T* row = f + (size_t)gz * G.nx;
+    return (T(2.0 / 3.0) * (row[wrap_x(gx + 1, G.nx)] - row[wrap_x(gx - 1, G.nx)]) -
+            T(1.0 / 12.0) * (row[wrap_x(gx + 2, G.nx)] - row[wrap_x(gx - 2, G.nx)])) * inv_h;
+}
+
+// value of plane f (field parity fld) at row gz, one mirror reflection at the walls
+template <typename T>
+__device__ __forceinline__ T plane_z(const T* __restrict__ f, const Geo& G, int gz, int gx, int fld) {
+    int side;
+    const int sz = mirror_z(gz, G.nz, side);
+    const T v = f[(size_t)sz * G.nx + gx];
+    return side == 1 ? T(G.pb[fld]) * v : (side == 2 ? T(G.pt[fld]) * v : v);
+}
+
+template <typename T>
+__device__ __forceinline__ T plane_dz(const T* __restrict__ f, const Geo& G, int gz, int gx, int fld, T inv_h) {
+    return (T(2.0 / 3.0) * (plane_z(f, G, gz + 1, gx, fld) - plane_z(f, G, gz - 1, gx, fld)) -
+            T(1.0 / 12.0) * (plane_z(f, G, gz + 2, gx, fld) - plane_z(f, G, gz - 2, gx, fld))) * inv_h;
+}
+
+// rhs = v_p - c_div (D_x v_u + D_z v_w)
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+schur_rhs2d(Geo G, const T* __restrict__ r, T* __restrict__ rhs, Ctl* ctl, int check_done) {
+    if (check_done && ctl->done) return;
+    const T cdiv = T(G.gamma_p * G.pbar / G.two_over_dt * G.scale[0] * G.inv_scale[3]);
+    const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < G.npt; p += gridDim.x * blockDim.x) {
+        const int gz = p / G.nx, gx = p - gz * G.nx;
+        const T du = plane_dx(r, G, gz, gx, idx_);
+        const T dw = plane_dz(r + G.npt, G, gz, gx, 1, idz_);
+        rhs[p] = r[(size_t)3 * G.npt + p] - cdiv * (du + dw);
+    }
+}
+
+// One Chebyshev sweep (k = 1 .. s-1) for H x = rhs on one plane, tiled like
+// cheb2d: x_k staged with halo 2r (even mirror of p), D_x on tile rows, D_z on
+// tile columns, then res = rhs - H x_k, d_k, x_{k+1} = x_k + d_k.
+template <typename T, int FIRST, int LAST, int TX, int TZ>
+__global__ void __launch_bounds__(NTHREADS)
+helm2d(Geo G, int k, const T* __restrict__ rhs, const T* __restrict__ xin, const T* __restrict__ din,
+       T* __restrict__ xout, T* __restrict__ dout, Ctl* ctl, int check_done) {
+    constexpr int SX = TX + 2 * HALO, SZ = TZ + 2 * HALO;
+    constexpr int QX = TX + 2 * R, QZ = TZ + 2 * R;
+    constexpr int TY = NTHREADS / TX;
+    static_assert(NTHREADS % TX == 0 && TZ % TY == 0, "tile must tile the block");
+    if (check_done && ctl->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* zs = reinterpret_cast<T*>(smem_raw);      // [SZ][SX]
+    T* gxs = zs + SZ * SX;                          // [TZ][QX]
+    T* gzs = gxs + TZ * QX;                         // [QZ][TX]
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+    const T ith = T(ctl->cheb[4][k][0]);
+    const T a1 = T(ctl->cheb[4][k][1]);
+    const T a2 = T(ctl->cheb[4][k][2]);
+    const int gxx = x0 + tx;
+    const bool colok = gxx < G.nx;
+    constexpr int NR = TZ / TY;
+    T rv[NR], dv[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        const int gz = z0 + ty + q * TY;
+        const bool ok = colok && gz < G.nz;
+        const int o = gz * G.nx + gxx;
+        rv[q] = ok ? rhs[o] : T(0);
+        dv[q] = (!FIRST && ok) ? din[o] : T(0);
+    }
+    const T* src = FIRST ? rhs : xin;
+    const T sc = FIRST ? ith : T(1);
+    const T pb = T(G.pb[3]), pt = T(G.pt[3]);
+    for (int idx = threadIdx.x; idx < SX * SZ; idx += blockDim.x) {
+        const int iz = idx / SX, ix = idx - iz * SX;
+        int side;
+        const int sz = mirror_z(z0 + iz - HALO, G.nz, side);
+        const int sx = wrap_x(x0 + ix - HALO, G.nx);
+        T val = T(0);
+        if (sz >= 0 && sz < G.nz) {
+            val = sc * src[(size_t)sz * G.nx + sx];
+            if (side == 1) val *= pb;
+            else if (side == 2) val *= pt;
+        }
+        zs[idx] = val;
+    }
+    __syncthreads();
+    const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
+    for (int tz = ty; tz < TZ; tz += TY)
+        for (int qx = tx; qx < QX; qx += TX) gxs[tz * QX + qx] = dd(zs, (tz + HALO) * SX + qx + R, 1, idx_);
+    for (int qz = ty; qz < QZ; qz += TY) gzs[qz * TX + tx] = dd(zs, (qz + R) * SX + tx + HALO, SX, idz_);
+    __syncthreads();
+    const T ah = T(G.gamma_p * G.pbar * G.theta0 / G.two_over_dt);
+    const T tdt = T(G.two_over_dt);
+    if (colok) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            const int tz = ty + q * TY;
+            const int gz = z0 + tz;
+            if (gz >= G.nz) break;
+            const T* gxr = gxs + tz * QX + tx + R;
+            const T* gzc = gzs + (tz + R) * TX + tx;
+            const T difx = T(2.0 / 3.0) * (gxr[1] - gxr[-1]) - T(1.0 / 12.0) * (gxr[2] - gxr[-2]);
+            const T difz = T(2.0 / 3.0) * (gzc[TX] - gzc[-TX]) - T(1.0 / 12.0) * (gzc[2 * TX] - gzc[-2 * TX]);
+            const T xk = zs[(tz + HALO) * SX + tx + HALO];
+            const T res = rv[q] - (tdt * xk - ah * (difx * idx_ + difz * idz_));
+            const T dprev = FIRST ? rv[q] * ith : dv[q];
+            const T dk = a1 * dprev + a2 * res;
+            const int o = gz * G.nx + gxx;
+            xout[o] = xk + dk;
+            if (!LAST) dout[o] = dk;
+        }
+    }
+}
+
+// z_u, z_w from the pressure solution (already in plane 3 of z), z_theta, and
+// the finite-difference step eps from ||z||.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+schur_back2d(Geo G, const T* __restrict__ r, T* __restrict__ z, double* part, Ctl* ctl, int check_done) {
+    if (check_done && ctl->done) return;
+    const T cgrad = T(G.theta0 * G.scale[3] * G.inv_scale[0]);
+    const T hdt = T(1.0 / G.two_over_dt);
+    const T ith_t = T(ctl->cheb[2][0][0]);
+    const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
+    const size_t np = (size_t)G.npt;
+    const T* dp = z + 3 * np;
+    T acc[1] = {T(0)};
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < G.npt; p += gridDim.x * blockDim.x) {
+        const int gz = p / G.nx, gx = p - gz * G.nx;
+        const T zu = hdt * (r[p] - cgrad * plane_dx(dp, G, gz, gx, idx_));
+        const T zw = hdt * (r[np + p] - cgrad * plane_dz(dp, G, gz, gx, 3, idz_));
+        const T zt = r[2 * np + p] * ith_t;
+        const T zp = dp[p];
+        z[p] = zu;
+        z[np + p] = zw;
+        z[2 * np + p] = zt;
+        acc[0] += zu * zu + zw * zw + zt * zt + zp * zp;
     }
     block_partials<1, T>(acc, 1, part, gridDim.x, blockIdx.x);
     if (arrive_last(&ctl->counter[CNT_PC], gridDim.x)) {
@@ -986,10 +1168,49 @@ static cudaError_t launch_precond_tile(const Geo& G, int sweeps, const T* r, T* 
 #undef JF_PC
 }
 
+// Acoustic Schur complement: rhs (plane 0 of da), sweeps - 1 Helmholtz
+// sweeps (iterates in plane 0 of za / zb, directions in planes 0 / 1 of db,
+// the last one into plane 3 of z), then the back-substitution.
+template <typename T>
+static cudaError_t launch_schur(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da, T* db,
+                                double* part, Ctl* ctl, int check_done, cudaStream_t s, long long* launches) {
+    constexpr int TX = 64, TZ = 16;
+    const size_t np = (size_t)G.npt;
+    const size_t sm = sizeof(T) * ((TZ + 2 * HALO) * (TX + 2 * HALO) + TZ * (TX + 2 * R) + (TZ + 2 * R) * TX);
+    T* rhs = da;
+    schur_rhs2d<T><<<stream_blocks(np), NTHREADS, 0, s>>>(G, r, rhs, ctl, check_done);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (launches) ++*launches;
+    dim3 grid((G.nx + TX - 1) / TX, (G.nz + TZ - 1) / TZ);
+    T* xbuf[2] = {za, zb};
+    T* dbuf[2] = {db, db + np};
+    const T* xin = nullptr;
+    const T* din = nullptr;
+    for (int k = 1; k <= sweeps - 1; ++k) {
+        const bool first = k == 1, last = k == sweeps - 1;
+        T* xo = last ? z + 3 * np : xbuf[k & 1];
+        T* dO = dbuf[k & 1];
+        if (first && last) helm2d<T, 1, 1, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+        else if (first) helm2d<T, 1, 0, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+        else if (last) helm2d<T, 0, 1, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+        else helm2d<T, 0, 0, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (launches) ++*launches;
+        xin = xo;
+        din = dO;
+    }
+    schur_back2d<T><<<stream_blocks(np), NTHREADS, 0, s>>>(G, r, z, part, ctl, check_done);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_precond(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da, T* db,
                            const T* nu, double* part, Ctl* ctl, int check_done, cudaStream_t s,
                            long long* launches) {
+    if (G.pc_schur && G.dim == 2 && sweeps > 1)
+        return launch_schur<T>(G, sweeps, r, z, za, zb, da, db, part, ctl, check_done, s, launches);
     if (G.dim == 3 && sweeps > 1)
         return launch_precond3d<T>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches);
     return G.smag ? launch_precond_tile<T, 1>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches)

@@ -44,6 +44,7 @@ PREC_MIXED = 1
 
 PC_NONE = 0
 PC_BLOCK = 1
+PC_SCHUR = 3
 
 
 def _base_case(dim, nx, nz, lx, lz, ny=1, ly=1.0):
