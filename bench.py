@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3, help="host-buffer steps through jfnk_step_host")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample (0: skip)")
     p.add_argument("--no-kernel-timing", action="store_true")
+    p.add_argument("--schur-sweeps", type=int, default=16,
+                   help="Helmholtz sweeps of the acoustic Schur-complement leg (0 skips it)")
     p.add_argument("--unet-forward", type=int, default=0,
                    help="only time this many applies of the learned-preconditioner network (profiling)")
     p.add_argument("--learned", default="thermal_stable_256x128:40:3,thermal_stable_1024x512:5:2",
@@ -429,6 +431,48 @@ def run_unet_forward(args):
     s.close()
 
 
+def schur_leg(jfnk, synth, torch, stream, case, U0, steps: int, sweeps: int, barrier, slowest, world: int) -> dict:
+    """The same workload with the acoustic Schur-complement preconditioner (JFNK_PC_SCHUR)."""
+    c = synth.with_options(case, precond=jfnk.PC_SCHUR, pc_sweeps=sweeps)
+    npt = c["grid"]["nx"] * c["grid"]["nz"]
+    s = jfnk.Solver(c, stream=stream)
+    u = torch.from_numpy(U0.reshape(-1).copy()).cuda()
+    for _ in range(3):
+        s.step(u)
+    tiles = s.autotune(u)
+    s.kernel_timing()
+    b0 = torch.cuda.Event(enable_timing=True)
+    b1 = torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    for _ in range(2):
+        s.step(u)
+    b1.record(stream)
+    b1.synchronize()
+    kt, kms = s.kernel_timing_read(), b0.elapsed_time(b1)
+    s.kernel_timing(())
+    barrier()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    st = [s.step(u) for _ in range(steps)]
+    a1.record(stream)
+    a1.synchronize()
+    ms = slowest(a0.elapsed_time(a1))
+    peaks = measured_peaks()
+    kernels = {k: {"launches": a["launches"], "ms_total": a["ms"], "share_of_step": a["ms"] / kms,
+                   "achieved_gbs": a["bytes"] / (a["ms"] / 1e3) / 1e9,
+                   "frac_of_hbm": a["bytes"] / (a["ms"] / 1e3) / 1e9 / peaks["hbm_gbs"]}
+               for k, a in kt.items() if a["launches"] and a["ms"] > 0}
+    s.close()
+    return {"precond": "acoustic Schur complement, %d Helmholtz Chebyshev sweeps" % sweeps,
+            "value": npt * steps * world / (ms / 1e3) / 1e6, "unit": "Mpt*steps/s", "steps": steps,
+            "ms_per_step": ms / steps,
+            "gmres_iters_per_step": statistics.mean(x["gmres_iters"] for x in st),
+            "newton_per_step": statistics.mean(x["newton_iters"] for x in st),
+            "converged": all(x["converged"] for x in st), "tiles": list(tiles), "kernels": kernels,
+            "kernels_timing": "per-family CUDA events over 2 steps before the timed steps"}
+
+
 def run_ours(args, rank: int, world: int, local_rank: int):
     import numpy as np
     import torch
@@ -533,6 +577,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "newton_per_step": statistics.mean(s["newton_iters"] for s in st64)}
         s64.close()
 
+    schur = None
+    if args.schur_sweeps > 1 and case["grid"]["dim"] == 2:
+        schur = schur_leg(jfnk, synth, torch, stream, case, U0, max(args.steps, 10), args.schur_sweeps,
+                          barrier, slowest, world)
+
     learned = []
     if args.learned and case["grid"]["dim"] == 2:
         for item in args.learned.split(","):
@@ -587,6 +636,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "kernels": kernels,
         "kernels_timing": "per-family CUDA events over 2 steps right before the timed region" if kernels else None,
         "fp64_plain": fp64, "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+        "schur_pc": schur,
+        "schur_over_block": (schur["value"] / value) if schur else None,
+        "schur_over_fp64": (schur["value"] / fp64["value"]) if (schur and fp64) else None,
         "learned_pc": learned or None,
         "learned_over_fp64": next((L["learned"]["value"] / fp64["value"] for L in learned
                                    if fp64 and L["workload"] == args.workload), None),

@@ -188,6 +188,12 @@ static void kt_end(jfnk_handle* h, int fam, double bytes) {
 static double pc_bytes(const jfnk_handle* h) {
     const double P = (double)h->npt * (h->mixed ? 4.0 : 8.0);
     const int s = h->opts.pc_sweeps;
+    if (h->G.pc_schur) {
+        // rhs: v_u, v_w, v_p -> rhs; sweeps: first rhs -> x, d; middle x, rhs, d -> x, d;
+        // last x, rhs, d -> x (first and last in one: rhs -> x); back: v_u, v_w, v_theta, dp -> z_u, z_w, z_theta
+        const double sweeps = s == 2 ? 2.0 : 3.0 + 5.0 * (s - 3) + 4.0;
+        return (4.0 + sweeps + 7.0) * P;
+    }
     if (s <= 1) return 2.0 * 4.0 * P;
     double b = 0.0;
     for (int k = 1; k <= s - 1; ++k) {
