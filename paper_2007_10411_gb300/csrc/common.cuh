@@ -35,6 +35,10 @@ struct Geo {
     const double* heat;               // surface flux H(x) or nullptr
     int tile_jv, tile_pc;             // tile shapes of the float32 Jv / preconditioner kernels
     int pc_schur;                     // preconditioner: 0 field-block, 1 acoustic Schur complement (2-D)
+    // acoustic Schur complement constants (host-computed): Helmholtz coefficient
+    // a = gamma_p pbar theta0 dt/2, c_div = gamma_p pbar (dt/2) s_u/s_p,
+    // c_grad = theta0 s_p/s_u, dt/2
+    double helm_a, schur_cdiv, schur_cgrad, half_dt;
 };
 
 constexpr int NUM_TILE_SHAPES = 4;

@@ -276,6 +276,10 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     G.tile_jv = 0;
     G.tile_pc = 0;
     G.pc_schur = opts->precond == JFNK_PC_SCHUR;
+    G.half_dt = 0.5 * opts->dt;
+    G.helm_a = strat->gamma_p * strat->pbar * strat->theta0 * G.half_dt;
+    G.schur_cdiv = strat->gamma_p * strat->pbar * G.half_dt * G.scale[0] * G.inv_scale[nf - 1];
+    G.schur_cgrad = strat->theta0 * G.scale[nf - 1] * G.inv_scale[0];
 
     const size_t eT = h->mixed ? sizeof(float) : sizeof(double);
     const size_t nb8 = h->ld * sizeof(double);

@@ -600,7 +600,7 @@ __global__ void pc_setup(Geo G, int sweeps, Ctl* ctl) {
     if (G.nf == 4) {
         // 2-D: slot 4 holds the pressure Helmholtz operator of the acoustic Schur
         // complement, H = (2/dt) I - a sum_j D_j D_j, a = gamma_p pbar theta0 dt / 2
-        const double a = G.gamma_p * G.pbar * G.theta0 / G.two_over_dt;
+        const double a = G.helm_a;
         const double lo = G.two_over_dt, hi = lo + 2.25 * a * h2;
         const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
         const bool degenerate = delta <= 1e-14 * theta;
@@ -817,7 +817,7 @@ template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
 schur_rhs2d(Geo G, const T* __restrict__ r, T* __restrict__ rhs, Ctl* ctl, int check_done) {
     if (check_done && ctl->done) return;
-    const T cdiv = T(G.gamma_p * G.pbar / G.two_over_dt * G.scale[0] * G.inv_scale[3]);
+    const T cdiv = T(G.schur_cdiv);
     const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < G.npt; p += gridDim.x * blockDim.x) {
         const int gz = p / G.nx, gx = p - gz * G.nx;
@@ -882,7 +882,7 @@ helm2d(Geo G, int k, const T* __restrict__ rhs, const T* __restrict__ xin, const
         for (int qx = tx; qx < QX; qx += TX) gxs[tz * QX + qx] = dd(zs, (tz + HALO) * SX + qx + R, 1, idx_);
     for (int qz = ty; qz < QZ; qz += TY) gzs[qz * TX + tx] = dd(zs, (qz + R) * SX + tx + HALO, SX, idz_);
     __syncthreads();
-    const T ah = T(G.gamma_p * G.pbar * G.theta0 / G.two_over_dt);
+    const T ah = T(G.helm_a);
     const T tdt = T(G.two_over_dt);
     if (colok) {
 #pragma unroll
@@ -911,8 +911,8 @@ template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
 schur_back2d(Geo G, const T* __restrict__ r, T* __restrict__ z, double* part, Ctl* ctl, int check_done) {
     if (check_done && ctl->done) return;
-    const T cgrad = T(G.theta0 * G.scale[3] * G.inv_scale[0]);
-    const T hdt = T(1.0 / G.two_over_dt);
+    const T cgrad = T(G.schur_cgrad);
+    const T hdt = T(G.half_dt);
     const T ith_t = T(ctl->cheb[2][0][0]);
     const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
     const size_t np = (size_t)G.npt;
