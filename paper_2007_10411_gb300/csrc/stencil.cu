@@ -318,6 +318,16 @@ stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
                 out[o] = Fv[fl];
             } else if (MODE == MODE_RHS) {
                 out[o] = T(G.two_over_dt * (double)u[o] + (double)Fv[fl]);
+            } else if (MODE == MODE_RHSRES) {
+                // at u = u^n the residual 2u/dt - F(u) - f with f = 2u/dt + F(u) is -2 F(u)
+                const double uo = (double)u[o];
+                const double Fd = (double)Fv[fl];
+                out[o] = T(G.two_over_dt * uo + Fd);
+                const double Rv = -2.0 * Fd;
+                out2[o] = T(Rv);
+                const double rs = Rv * G.inv_scale[fl], us = uo * G.inv_scale[fl];
+                acc[0] += rs * rs;
+                acc[1] += us * us;
             } else if (MODE == MODE_RES) {
                 const double uo = (double)u[o];
                 const double Rv = G.two_over_dt * uo - (double)Fv[fl] - f[o];
@@ -333,7 +343,7 @@ stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
             }
         }
     }
-    if (MODE == MODE_RES) {
+    if (MODE == MODE_RES || MODE == MODE_RHSRES) {
         const int nblk = gridDim.x * gridDim.y;
         const int blk = blockIdx.y * gridDim.x + blockIdx.x;
         block_partials<2>(acc, 2, part, nblk, blk);
@@ -1043,6 +1053,7 @@ cudaError_t launch_stencil(int mode, const Geo& G, const T* u, const T* v, const
         JF_CASE(MODE_RHS)
         JF_CASE(MODE_RES)
         JF_CASE(MODE_JV)
+        JF_CASE(MODE_RHSRES)
         default: return cudaErrorInvalidValue;
     }
 #undef JF_CASE
