@@ -189,10 +189,18 @@ static double pc_bytes(const jfnk_handle* h) {
     const double P = (double)h->npt * (h->mixed ? 4.0 : 8.0);
     const int s = h->opts.pc_sweeps;
     if (h->G.pc_schur) {
-        // rhs: v_u, v_w, v_p -> rhs; sweeps: first rhs -> x, d; middle x, rhs, d -> x, d;
-        // last x, rhs, d -> x (first and last in one: rhs -> x); back: v_u, v_w, v_theta, dp -> z_u, z_w, z_theta
-        const double sweeps = s == 2 ? 2.0 : 3.0 + 5.0 * (s - 3) + 4.0;
-        return (4.0 + sweeps + 7.0) * P;
+        // rhs: v_u, v_w, v_p -> rhs; each Helmholtz launch (one sweep, or two where
+        // nz >= 8) reads x (rhs on the first), rhs and d and writes x and d (not on
+        // the last); back: v_u, v_w, v_theta, dp -> z_u, z_w, z_theta
+        double b = 4.0 + 7.0;
+        const bool pairs = h->G.nz >= 8;
+        for (int k = 1; k <= s - 1;) {
+            const bool two = pairs && k + 1 <= s - 1;
+            const bool first = k == 1, last = (two ? k + 1 : k) == s - 1;
+            b += (first ? 1.0 : 3.0) + (last ? 1.0 : 2.0);
+            k += two ? 2 : 1;
+        }
+        return b * P;
     }
     if (s <= 1) return 2.0 * 4.0 * P;
     double b = 0.0;

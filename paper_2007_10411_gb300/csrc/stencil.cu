@@ -915,6 +915,111 @@ helm2d(Geo G, int k, const T* __restrict__ rhs, const T* __restrict__ xin, const
     }
 }
 
+// Two Chebyshev sweeps (k and k+1) per launch (temporal blocking): x_k is
+// staged with halo 4r, sweep k runs on the tile plus a ring of 2r points
+// (ghost rows included -- the mirrored data give the mirrored result), and
+// sweep k+1 on the tile from those values.  Needs nz >= 4r (one reflection).
+template <typename T, int FIRST, int LAST, int TX, int TZ>
+__global__ void __launch_bounds__(NTHREADS)
+helm2d_x2(Geo G, int k, const T* __restrict__ rhs, const T* __restrict__ xin, const T* __restrict__ din,
+          T* __restrict__ xout, T* __restrict__ dout, Ctl* ctl, int check_done) {
+    constexpr int H2 = 2 * HALO;                       // staging halo (two sweeps)
+    constexpr int SX = TX + 2 * H2, SZ = TZ + 2 * H2;
+    constexpr int EX = TX + 2 * HALO, EZ = TZ + 2 * HALO;   // first-sweep region
+    constexpr int TY = NTHREADS / TX;
+    static_assert(NTHREADS % TX == 0 && TZ % TY == 0, "tile must tile the block");
+    if (check_done && ctl->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xs = reinterpret_cast<T*>(smem_raw);   // [SZ][SX]   x_k
+    T* re = xs + SZ * SX;                        // [EZ][EX]   rhs on the first-sweep region
+    T* de = re + EZ * EX;                        // [EZ][EX]   d_{k-1}, then d_k
+    T* x1 = de + EZ * EX;                        // [EZ][EX]   x_{k+1}
+    T* gx = x1 + EZ * EX;                        // [EZ][EX + 2R]  D_x rows (reused by sweep k+1)
+    T* gz = gx + EZ * (EX + 2 * R);              // [EZ + 2R][EX]  D_z columns (reused)
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+    const T ith = T(ctl->cheb[4][k][0]);
+    const T a1 = T(ctl->cheb[4][k][1]), a2 = T(ctl->cheb[4][k][2]);
+    const T b1 = T(ctl->cheb[4][k + 1][1]), b2 = T(ctl->cheb[4][k + 1][2]);
+    const T pb = T(G.pb[3]), pt = T(G.pt[3]);
+    // staging: x_k (halo 2 HALO), rhs and d_{k-1} (halo HALO); p parity in z, periodic x
+    for (int idx = threadIdx.x; idx < SX * SZ; idx += blockDim.x) {
+        const int iz = idx / SX, ix = idx - iz * SX;
+        int side;
+        const int sz = mirror_z(z0 + iz - H2, G.nz, side);
+        const int sx = wrap_x(x0 + ix - H2, G.nx);
+        // rows beyond one reflection (tiles overhanging a wall) feed no output: zero
+        const bool ok = sz >= 0 && sz < G.nz;
+        const T sgn = side == 1 ? pb : (side == 2 ? pt : T(1));
+        const size_t o = ok ? (size_t)sz * G.nx + sx : 0;
+        const T xv = ok ? (FIRST ? ith * rhs[o] : xin[o]) : T(0);
+        xs[idx] = sgn * xv;
+        const int ez = iz - HALO, ex = ix - HALO;
+        if (ez >= 0 && ez < EZ && ex >= 0 && ex < EX) {
+            const T rv = ok ? sgn * rhs[o] : T(0);
+            re[ez * EX + ex] = rv;
+            de[ez * EX + ex] = FIRST ? ith * rv : (ok ? sgn * din[o] : T(0));
+        }
+    }
+    __syncthreads();
+    const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
+    const T ah = T(G.helm_a), tdt = T(G.two_over_dt);
+    // sweep k on the first-sweep region
+    for (int i = threadIdx.x; i < EZ * (EX + 2 * R); i += blockDim.x) {
+        const int ez = i / (EX + 2 * R), c = i - ez * (EX + 2 * R);
+        gx[i] = dd(xs, (ez + HALO) * SX + c + R, 1, idx_);
+    }
+    for (int i = threadIdx.x; i < (EZ + 2 * R) * EX; i += blockDim.x) {
+        const int r = i / EX, ex = i - r * EX;
+        gz[i] = dd(xs, (r + R) * SX + ex + HALO, SX, idz_);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < EZ * EX; i += blockDim.x) {
+        const int ez = i / EX, ex = i - ez * EX;
+        const T* gxr = gx + ez * (EX + 2 * R) + ex + R;
+        const T* gzc = gz + (ez + R) * EX + ex;
+        const T difx = T(2.0 / 3.0) * (gxr[1] - gxr[-1]) - T(1.0 / 12.0) * (gxr[2] - gxr[-2]);
+        const T difz = T(2.0 / 3.0) * (gzc[EX] - gzc[-EX]) - T(1.0 / 12.0) * (gzc[2 * EX] - gzc[-2 * EX]);
+        const T xk = xs[(ez + HALO) * SX + ex + HALO];
+        const T res = re[i] - (tdt * xk - ah * (difx * idx_ + difz * idz_));
+        const T dk = a1 * de[i] + a2 * res;
+        de[i] = dk;
+        x1[i] = xk + dk;
+    }
+    __syncthreads();
+    // sweep k+1 on the tile
+    constexpr int GX2 = TX + 2 * R;
+    for (int i = threadIdx.x; i < TZ * GX2; i += blockDim.x) {
+        const int tz = i / GX2, c = i - tz * GX2;
+        gx[i] = dd(x1, (tz + HALO) * EX + c + R, 1, idx_);
+    }
+    for (int i = threadIdx.x; i < (TZ + 2 * R) * TX; i += blockDim.x) {
+        const int r = i / TX, tx = i - r * TX;
+        gz[i] = dd(x1, (r + R) * EX + tx + HALO, EX, idz_);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int gxx = x0 + tx;
+    if (gxx < G.nx) {
+#pragma unroll
+        for (int q = 0; q < TZ / TY; ++q) {
+            const int tz = ty + q * TY;
+            const int gzz = z0 + tz;
+            if (gzz >= G.nz) break;
+            const T* gxr = gx + tz * GX2 + tx + R;
+            const T* gzc = gz + (tz + R) * TX + tx;
+            const T difx = T(2.0 / 3.0) * (gxr[1] - gxr[-1]) - T(1.0 / 12.0) * (gxr[2] - gxr[-2]);
+            const T difz = T(2.0 / 3.0) * (gzc[TX] - gzc[-TX]) - T(1.0 / 12.0) * (gzc[2 * TX] - gzc[-2 * TX]);
+            const int e = (tz + HALO) * EX + tx + HALO;
+            const T xk = x1[e];
+            const T res = re[e] - (tdt * xk - ah * (difx * idx_ + difz * idz_));
+            const T dk = b1 * de[e] + b2 * res;
+            const int o = gzz * G.nx + gxx;
+            xout[o] = xk + dk;
+            if (!LAST) dout[o] = dk;
+        }
+    }
+}
+
 // z_u, z_w from the pressure solution (already in plane 3 of z), z_theta, and
 // the finite-difference step eps from ||z||.
 template <typename T>
@@ -1198,18 +1303,41 @@ static cudaError_t launch_schur(const Geo& G, int sweeps, const T* r, T* z, T* z
     T* dbuf[2] = {db, db + np};
     const T* xin = nullptr;
     const T* din = nullptr;
-    for (int k = 1; k <= sweeps - 1; ++k) {
-        const bool first = k == 1, last = k == sweeps - 1;
-        T* xo = last ? z + 3 * np : xbuf[k & 1];
-        T* dO = dbuf[k & 1];
-        if (first && last) helm2d<T, 1, 1, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
-        else if (first) helm2d<T, 1, 0, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
-        else if (last) helm2d<T, 0, 1, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
-        else helm2d<T, 0, 0, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+    int cur = 1;                              // buffer pair the next output goes to
+    const bool pairs = G.nz >= 2 * HALO;      // fused pairs need one mirror reflection of a 2*HALO halo
+    const size_t sm2 = sizeof(T) * ((TZ + 4 * HALO) * (TX + 4 * HALO) + 3 * (TZ + 2 * HALO) * (TX + 2 * HALO) +
+                                    (TZ + 2 * HALO) * (TX + 2 * HALO + 2 * R) + (TZ + 2 * HALO + 2 * R) * (TX + 2 * HALO));
+    static std::atomic<bool> configured{false};
+    if (!configured) {
+        if ((e = set_smem(helm2d_x2<T, 1, 1, TX, TZ>, sm2)) != cudaSuccess) return e;
+        if ((e = set_smem(helm2d_x2<T, 1, 0, TX, TZ>, sm2)) != cudaSuccess) return e;
+        if ((e = set_smem(helm2d_x2<T, 0, 1, TX, TZ>, sm2)) != cudaSuccess) return e;
+        if ((e = set_smem(helm2d_x2<T, 0, 0, TX, TZ>, sm2)) != cudaSuccess) return e;
+        configured = true;
+    }
+    for (int k = 1; k <= sweeps - 1;) {
+        const bool first = k == 1;
+        const bool two = pairs && k + 1 <= sweeps - 1;
+        const bool last = (two ? k + 1 : k) == sweeps - 1;
+        T* xo = last ? z + 3 * np : xbuf[cur];
+        T* dO = dbuf[cur];
+        if (two) {
+            if (first && last) helm2d_x2<T, 1, 1, TX, TZ><<<grid, NTHREADS, sm2, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+            else if (first) helm2d_x2<T, 1, 0, TX, TZ><<<grid, NTHREADS, sm2, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+            else if (last) helm2d_x2<T, 0, 1, TX, TZ><<<grid, NTHREADS, sm2, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+            else helm2d_x2<T, 0, 0, TX, TZ><<<grid, NTHREADS, sm2, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+        } else {
+            if (first && last) helm2d<T, 1, 1, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+            else if (first) helm2d<T, 1, 0, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+            else if (last) helm2d<T, 0, 1, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+            else helm2d<T, 0, 0, TX, TZ><<<grid, NTHREADS, sm, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (launches) ++*launches;
         xin = xo;
         din = dO;
+        cur ^= 1;
+        k += two ? 2 : 1;
     }
     schur_back2d<T><<<stream_blocks(np), NTHREADS, 0, s>>>(G, r, z, part, ctl, check_done);
     if (launches) ++*launches;
