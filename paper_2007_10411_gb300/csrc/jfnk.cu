@@ -6,8 +6,9 @@
 // per GMRES cycle and once per Newton correction; every vector operation of
 // the step runs in this library's kernels.  The end of a cycle is detected
 // with a pipelined poll: after enqueueing Arnoldi step j the host waits for
-// step j - LAG and stops enqueueing once that step reports the cycle done
-// (steps enqueued after the finish return at entry).
+// step j - LAG (j - 1 with the Schur-complement preconditioner) and stops
+// enqueueing once that step reports the cycle done (steps enqueued after the
+// finish return at entry).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -659,6 +660,9 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
     const int m = h->m;
     const bool pc = h->opts.precond != JFNK_PC_NONE;
     bool learned = h->opts.precond == JFNK_PC_UNET && h->net != nullptr;
+    // A Schur-preconditioned step is long enough (tens of launches) for the host
+    // to stay ahead with a lag of one, which halves the steps enqueued past a finish.
+    const int lag = h->G.pc_schur ? 1 : LAG;
     const bool arnoldi_pairs = sizeof(T) == sizeof(float) && capturing(h, JFNK_PAIRS_ARNOLDI);
     T* V = (T*)h->V;
     T* Z = pc ? (T*)h->Z : V;
@@ -712,9 +716,9 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
             h->launches += 3;
             CK(cudaMemcpyAsync(&h->hdone[j], &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
             CK(cudaEventRecord(h->ev[j], s));
-            if (j >= LAG) {
-                CK(cudaEventSynchronize(h->ev[j - LAG]));
-                if (h->hdone[j - LAG]) break;
+            if (j >= lag) {
+                CK(cudaEventSynchronize(h->ev[j - lag]));
+                if (h->hdone[j - lag]) break;
             }
         }
         CK(launch_update<T>(Z, ld, h->x, h->mixed ? xT : nullptr, n, h->part, h->ctl, s));
