@@ -299,38 +299,38 @@ class Model:
         return self.gershgorin_bounds(a)
 
     def schur_precond(self, U_frozen: np.ndarray, Vhat: np.ndarray, sweeps: int) -> np.ndarray:
-        """Acoustic Schur-complement preconditioner z = P v (2-D, scaled units).
+        """Acoustic Schur-complement preconditioner z = P v (scaled units, 2-D and 3-D).
 
         Section 2.5 follows the semi-implicit elimination of the fast acoustic
         terms (Skamarock & Klemp): keeping only (2/dt) I and the pressure
         gradient / divergence couplings of Eqs. ch2_28-ch2_30 linearised about
         the reference pressure pbar,
-            (2/dt) du + theta0 D_x dp = r_u,  (2/dt) dw + theta0 D_z dp = r_w,
-            (2/dt) dp + gamma_p pbar (D_x du + D_z dw) = r_p,
+            (2/dt) du_i + theta0 D_i dp = r_i  (every velocity component i),
+            (2/dt) dp + gamma_p pbar sum_i D_i du_i = r_p,
         the velocities are eliminated, leaving the pressure Helmholtz problem
-            H dp = r_p - gamma_p pbar (dt/2) (D_x r_u + D_z r_w),
+            H dp = r_p - gamma_p pbar (dt/2) sum_i D_i r_i,
         solved approximately by ``sweeps`` Chebyshev steps on its Gershgorin
-        interval (a fixed linear map); then du = (dt/2)(r_u - theta0 D_x dp),
-        dw = (dt/2)(r_w - theta0 D_z dp).  Advection, diffusion and buoyancy
-        are dropped; theta gets one Chebyshev step of its field block
-        (r_theta / theta_c).  r = W^-1 v, z = W dz.
+        interval (a fixed linear map); then du_i = (dt/2)(r_i - theta0 D_i dp).
+        Advection, diffusion and buoyancy are dropped; theta gets one
+        Chebyshev step of its field block (r_theta / theta_c).  r = W^-1 v,
+        z = W dz.
         """
-        assert self.dim == 2
         dt = self.dt
         r = self.unscale(Vhat)
-        ru, rw, rth, rp = r[self.iu], r[self.iw], r[self.ith], r[self.ip]
-        div_r = self._d_interior(ru, self.parity[self.iu], 0) + self._d_interior(rw, self.parity[self.iw], 1)
-        rhs = rp - self.gamma_p * self.pbar * (dt / 2.0) * div_r
+        div_r = 0.0
+        for j, i in enumerate(self.vel):
+            div_r = div_r + self._d_interior(r[i], self.parity[i], j)
+        rhs = r[self.ip] - self.gamma_p * self.pbar * (dt / 2.0) * div_r
         lo, hi = self.helmholtz_bounds()
         dp = chebyshev(self.helmholtz, rhs, lo, hi, sweeps)
-        du = (dt / 2.0) * (ru - self.theta0 * self._d_interior(dp, self.parity[self.ip], 0))
-        dw = (dt / 2.0) * (rw - self.theta0 * self._d_interior(dp, self.parity[self.ip], 1))
+        Z = np.zeros_like(r)
+        for j, i in enumerate(self.vel):
+            Z[i] = (dt / 2.0) * (r[i] - self.theta0 * self._d_interior(dp, self.parity[self.ip], j))
         K_M, K_H = self.frozen_eddy(U_frozen)
         kth = float(np.max(K_H)) if not np.isscalar(K_H) else float(K_H)
         lo_t, hi_t = self.gershgorin_bounds(kth)
-        dth = rth / (0.5 * (lo_t + hi_t))
-        Z = np.zeros_like(r)
-        Z[self.iu], Z[self.iw], Z[self.ith], Z[self.ip] = du, dw, dth, dp
+        Z[self.ith] = r[self.ith] / (0.5 * (lo_t + hi_t))
+        Z[self.ip] = dp
         return self.scale(Z)
 
     # ------------------------------------------------------------ budgets
