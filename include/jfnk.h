@@ -109,7 +109,7 @@ typedef struct {
  * precond     JFNK_PC_NONE, JFNK_PC_BLOCK (pc_sweeps Chebyshev steps per block),
  *             JFNK_PC_UNET (the block preconditioner plus a learned
  *             correction, see "Learned right preconditioner" below) or
- *             JFNK_PC_SCHUR (2-D, pc_sweeps >= 2: the acoustic Schur
+ *             JFNK_PC_SCHUR (pc_sweeps >= 2: the acoustic Schur
  *             complement of the semi-implicit elimination Section 2.5
  *             follows -- only (2/dt) I and the pressure gradient / divergence
  *             couplings linearised about pbar are kept, the velocities are

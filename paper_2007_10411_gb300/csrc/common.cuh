@@ -73,7 +73,7 @@ struct Ctl {
     double g[KMAX + 1];
     double y[KMAX];
     // Chebyshev coefficients per field block and sweep: 1/theta_c, rho_k rho_{k-1}, 2 rho_k / delta
-    double cheb[5][MAX_PC_SWEEPS][3];
+    double cheb[6][MAX_PC_SWEEPS][3];   // slot 5: pressure Helmholtz of the Schur complement
     unsigned int counter[8];         // last-block counters, one per kernel family
 };
 

@@ -118,7 +118,7 @@ static jfnk_status validate(const jfnk_grid* g, const jfnk_strat* s, const jfnk_
     if (o->precond == JFNK_PC_UNET &&
         (g->dim != 2 || o->precision != JFNK_MIXED || g->nx % 32 != 0 || g->nz % 32 != 0))
         return JFNK_ERR_UNSUPPORTED;
-    if (o->precond == JFNK_PC_SCHUR && (g->dim != 2 || o->pc_sweeps < 2)) return JFNK_ERR_UNSUPPORTED;
+    if (o->precond == JFNK_PC_SCHUR && o->pc_sweeps < 2) return JFNK_ERR_UNSUPPORTED;
     return JFNK_OK;
 }
 
@@ -190,11 +190,12 @@ static double pc_bytes(const jfnk_handle* h) {
     const double P = (double)h->npt * (h->mixed ? 4.0 : 8.0);
     const int s = h->opts.pc_sweeps;
     if (h->G.pc_schur) {
-        // rhs: v_u, v_w, v_p -> rhs; each Helmholtz launch (one sweep, or two where
-        // nz >= 8) reads x (rhs on the first), rhs and d and writes x and d (not on
-        // the last); back: v_u, v_w, v_theta, dp -> z_u, z_w, z_theta
-        double b = 4.0 + 7.0;
-        const bool pairs = h->G.nz >= 8;
+        // rhs: velocities and v_p -> rhs; each Helmholtz launch (one sweep, or two
+        // in 2-D where nz >= 8) reads x (rhs on the first), rhs and d and writes x
+        // and d (not on the last); back: velocities, v_theta, dp -> z but z_p
+        const int nf = h->G.nf;
+        double b = nf + (2.0 * nf - 1.0);     // rhs kernel + back-substitution
+        const bool pairs = h->G.dim == 2 && h->G.nz >= 8;
         for (int k = 1; k <= s - 1;) {
             const bool two = pairs && k + 1 <= s - 1;
             const bool first = k == 1, last = (two ? k + 1 : k) == s - 1;
@@ -994,7 +995,7 @@ extern "C" jfnk_status jfnk_set_precond(jfnk_handle* h, int precond) {
         precond != JFNK_PC_SCHUR)
         return JFNK_ERR_INVALID_ARG;
     if (precond == JFNK_PC_UNET && !unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
-    if (precond == JFNK_PC_SCHUR && (h->G.dim != 2 || h->opts.pc_sweeps < 2)) return JFNK_ERR_UNSUPPORTED;
+    if (precond == JFNK_PC_SCHUR && h->opts.pc_sweeps < 2) return JFNK_ERR_UNSUPPORTED;
     if (precond != JFNK_PC_NONE && !h->Z) {
         const size_t eT = h->mixed ? sizeof(float) : sizeof(double);
         CK(cudaStreamSynchronize(h->stream));

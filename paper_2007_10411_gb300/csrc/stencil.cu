@@ -607,8 +607,8 @@ __global__ void pc_setup(Geo G, int sweeps, Ctl* ctl) {
             rho = rho_new;
         }
     }
-    if (G.nf == 4) {
-        // 2-D: slot 4 holds the pressure Helmholtz operator of the acoustic Schur
+    {
+        // slot 5 holds the pressure Helmholtz operator of the acoustic Schur
         // complement, H = (2/dt) I - a sum_j D_j D_j, a = gamma_p pbar theta0 dt / 2
         const double a = G.helm_a;
         const double lo = G.two_over_dt, hi = lo + 2.25 * a * h2;
@@ -616,14 +616,14 @@ __global__ void pc_setup(Geo G, int sweeps, Ctl* ctl) {
         const bool degenerate = delta <= 1e-14 * theta;
         const double sigma = degenerate ? 1.0 : theta / delta;
         double rho = 1.0 / sigma;
-        ctl->cheb[4][0][0] = 1.0 / theta;
-        ctl->cheb[4][0][1] = 0.0;
-        ctl->cheb[4][0][2] = 0.0;
+        ctl->cheb[5][0][0] = 1.0 / theta;
+        ctl->cheb[5][0][1] = 0.0;
+        ctl->cheb[5][0][2] = 0.0;
         for (int k = 1; k < sweeps && k < MAX_PC_SWEEPS; ++k) {
             const double rho_new = 1.0 / (2.0 * sigma - rho);
-            ctl->cheb[4][k][0] = 1.0 / theta;
-            ctl->cheb[4][k][1] = degenerate ? 0.0 : rho_new * rho;
-            ctl->cheb[4][k][2] = degenerate ? 0.0 : 2.0 * rho_new / delta;
+            ctl->cheb[5][k][0] = 1.0 / theta;
+            ctl->cheb[5][k][1] = degenerate ? 0.0 : rho_new * rho;
+            ctl->cheb[5][k][2] = degenerate ? 0.0 : 2.0 * rho_new / delta;
             rho = rho_new;
         }
     }
@@ -797,7 +797,7 @@ pc_diag(Geo G, const T* __restrict__ r, T* __restrict__ z, size_t n, double* par
 //   z_u = (dt/2)(v_u - c_grad D_x dp),   z_w = (dt/2)(v_w - c_grad D_z dp),
 // with c_div = gamma_p pbar (dt/2) s_u / s_p, c_grad = theta0 s_p / s_u and
 // a = gamma_p pbar theta0 dt / 2.  H is inverted approximately by Chebyshev
-// sweeps on its Gershgorin interval (coefficients ctl->cheb[4], pc_setup);
+// sweeps on its Gershgorin interval (coefficients ctl->cheb[5], pc_setup);
 // theta gets r_theta / theta_c of its field block.
 // ============================================================================
 template <typename T>
@@ -855,9 +855,9 @@ helm2d(Geo G, int k, const T* __restrict__ rhs, const T* __restrict__ xin, const
     T* gzs = gxs + TZ * QX;                         // [QZ][TX]
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
-    const T ith = T(ctl->cheb[4][k][0]);
-    const T a1 = T(ctl->cheb[4][k][1]);
-    const T a2 = T(ctl->cheb[4][k][2]);
+    const T ith = T(ctl->cheb[5][k][0]);
+    const T a1 = T(ctl->cheb[5][k][1]);
+    const T a2 = T(ctl->cheb[5][k][2]);
     const int gxx = x0 + tx;
     const bool colok = gxx < G.nx;
     constexpr int NR = TZ / TY;
@@ -937,9 +937,9 @@ helm2d_x2(Geo G, int k, const T* __restrict__ rhs, const T* __restrict__ xin, co
     T* gx = x1 + EZ * EX;                        // [EZ][EX + 2R]  D_x rows (reused by sweep k+1)
     T* gz = gx + EZ * (EX + 2 * R);              // [EZ + 2R][EX]  D_z columns (reused)
     const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
-    const T ith = T(ctl->cheb[4][k][0]);
-    const T a1 = T(ctl->cheb[4][k][1]), a2 = T(ctl->cheb[4][k][2]);
-    const T b1 = T(ctl->cheb[4][k + 1][1]), b2 = T(ctl->cheb[4][k + 1][2]);
+    const T ith = T(ctl->cheb[5][k][0]);
+    const T a1 = T(ctl->cheb[5][k][1]), a2 = T(ctl->cheb[5][k][2]);
+    const T b1 = T(ctl->cheb[5][k + 1][1]), b2 = T(ctl->cheb[5][k + 1][2]);
     const T pb = T(G.pb[3]), pt = T(G.pt[3]);
     // staging: x_k (halo 2 HALO), rhs and d_{k-1} (halo HALO); p parity in z, periodic x
     for (int idx = threadIdx.x; idx < SX * SZ; idx += blockDim.x) {

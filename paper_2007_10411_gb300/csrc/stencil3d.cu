@@ -695,6 +695,144 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// ---------------------------------------------------------------------------
+// Acoustic Schur-complement preconditioner in 3-D (scaled units): the 2-D
+// construction with three velocity components,
+//   H dp = v_p - c_div (D_x v_u + D_y v_v + D_z v_w),  H = (2/dt) I - a sum_j D_j D_j,
+//   z_i = (dt/2)(v_i - c_grad D_i dp),  z_theta = v_theta / theta_c,
+// with H applied point-wise as the composite stencil of the first derivative
+// taken twice along each axis (coefficients c_s = sum_{a+b=s} w_a w_b: -65/72,
+// 1/9, 4/9, -1/9, 1/144 for |s| = 0..4) on the ghost-extended plane (p even
+// at the walls), which equals D_j applied to D_j dp evaluated with its ghosts.
+// Fields: 0 u, 1 v, 2 w, 3 theta, 4 p; planes [z][y][x].
+template <typename T>
+__device__ __forceinline__ T pz(const T* __restrict__ f, const Geo& G, int gz, int gy, int gx, int fld) {
+    int side;
+    const int sz = mirror(gz, G.nz, side);
+    const T v = f[((size_t)sz * G.ny + gy) * G.nx + gx];
+    return side == 1 ? T(G.pb[fld]) * v : (side == 2 ? T(G.pt[fld]) * v : v);
+}
+
+template <typename T>
+__device__ __forceinline__ T d1x(const T* __restrict__ f, const Geo& G, int gz, int gy, int gx, T ih) {
+    const T* row = f + ((size_t)gz * G.ny + gy) * G.nx;
+    return (T(2.0 / 3.0) * (row[wrap(gx + 1, G.nx)] - row[wrap(gx - 1, G.nx)]) -
+            T(1.0 / 12.0) * (row[wrap(gx + 2, G.nx)] - row[wrap(gx - 2, G.nx)])) * ih;
+}
+template <typename T>
+__device__ __forceinline__ T d1y(const T* __restrict__ f, const Geo& G, int gz, int gy, int gx, T ih) {
+    const T* pl = f + (size_t)gz * G.ny * G.nx + gx;
+    return (T(2.0 / 3.0) * (pl[(size_t)wrap(gy + 1, G.ny) * G.nx] - pl[(size_t)wrap(gy - 1, G.ny) * G.nx]) -
+            T(1.0 / 12.0) * (pl[(size_t)wrap(gy + 2, G.ny) * G.nx] - pl[(size_t)wrap(gy - 2, G.ny) * G.nx])) * ih;
+}
+template <typename T>
+__device__ __forceinline__ T d1z(const T* __restrict__ f, const Geo& G, int gz, int gy, int gx, int fld, T ih) {
+    return (T(2.0 / 3.0) * (pz(f, G, gz + 1, gy, gx, fld) - pz(f, G, gz - 1, gy, gx, fld)) -
+            T(1.0 / 12.0) * (pz(f, G, gz + 2, gy, gx, fld) - pz(f, G, gz - 2, gy, gx, fld))) * ih;
+}
+
+// sum_j D_j D_j x at (gz, gy, gx), x taken as sc * f (p parity in z)
+template <typename T>
+__device__ __forceinline__ T lap_dd(const T* __restrict__ f, const Geo& G, int gz, int gy, int gx, T sc, T ix2,
+                                    T iy2, T iz2) {
+    const T c[5] = {T(-65.0 / 72.0), T(1.0 / 9.0), T(4.0 / 9.0), T(-1.0 / 9.0), T(1.0 / 144.0)};
+    const T* row = f + ((size_t)gz * G.ny + gy) * G.nx;
+    const T* pl = f + (size_t)gz * G.ny * G.nx + gx;
+    const T ctr = row[gx];
+    T lx = c[0] * ctr, ly = c[0] * ctr, lz = c[0] * ctr;
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+        lx += c[k] * (row[wrap(gx + k, G.nx)] + row[wrap(gx - k, G.nx)]);
+        ly += c[k] * (pl[(size_t)wrap(gy + k, G.ny) * G.nx] + pl[(size_t)wrap(gy - k, G.ny) * G.nx]);
+        lz += c[k] * (pz(f, G, gz + k, gy, gx, 4) + pz(f, G, gz - k, gy, gx, 4));
+    }
+    return sc * (lx * ix2 + ly * iy2 + lz * iz2);
+}
+
+template <typename T>
+__device__ __forceinline__ void unflat(const Geo& G, int p, int& gz, int& gy, int& gx) {
+    const int pxy = G.nx * G.ny;
+    gz = p / pxy;
+    const int rem = p - gz * pxy;
+    gy = rem / G.nx;
+    gx = rem - gy * G.nx;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+schur_rhs3d(Geo G, const T* __restrict__ r, T* __restrict__ rhs, Ctl* ctl, int check_done) {
+    if (check_done && ctl->done) return;
+    const T cdiv = T(G.schur_cdiv);
+    const T ix = T(G.inv_dx), iy = T(G.inv_dy), iz = T(G.inv_dz);
+    const size_t np = (size_t)G.npt;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < G.npt; p += gridDim.x * blockDim.x) {
+        int gz, gy, gx;
+        unflat<T>(G, p, gz, gy, gx);
+        const T div = d1x(r, G, gz, gy, gx, ix) + d1y(r + np, G, gz, gy, gx, iy) + d1z(r + 2 * np, G, gz, gy, gx, 2, iz);
+        rhs[p] = r[4 * np + p] - cdiv * div;
+    }
+}
+
+// one Chebyshev sweep k for H x = rhs (FIRST: x_k = rhs / theta_c, d_{k-1} = x_k)
+template <typename T, int FIRST, int LAST>
+__global__ void __launch_bounds__(NTHREADS)
+helm3d(Geo G, int k, const T* __restrict__ rhs, const T* __restrict__ xin, const T* __restrict__ din,
+       T* __restrict__ xout, T* __restrict__ dout, Ctl* ctl, int check_done) {
+    if (check_done && ctl->done) return;
+    const T ith = T(ctl->cheb[5][k][0]);
+    const T a1 = T(ctl->cheb[5][k][1]), a2 = T(ctl->cheb[5][k][2]);
+    const T ah = T(G.helm_a), tdt = T(G.two_over_dt);
+    const T ix2 = T(G.inv_dx * G.inv_dx), iy2 = T(G.inv_dy * G.inv_dy), iz2 = T(G.inv_dz * G.inv_dz);
+    const T* src = FIRST ? rhs : xin;
+    const T sc = FIRST ? ith : T(1);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < G.npt; p += gridDim.x * blockDim.x) {
+        int gz, gy, gx;
+        unflat<T>(G, p, gz, gy, gx);
+        const T xk = sc * src[p];
+        const T rv = rhs[p];
+        const T res = rv - (tdt * xk - ah * lap_dd(src, G, gz, gy, gx, sc, ix2, iy2, iz2));
+        const T dprev = FIRST ? rv * ith : din[p];
+        const T dk = a1 * dprev + a2 * res;
+        xout[p] = xk + dk;
+        if (!LAST) dout[p] = dk;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+schur_back3d(Geo G, const T* __restrict__ r, T* __restrict__ z, double* part, Ctl* ctl, int check_done) {
+    if (check_done && ctl->done) return;
+    const T cgrad = T(G.schur_cgrad), hdt = T(G.half_dt);
+    const T ith_t = T(ctl->cheb[3][0][0]);
+    const T ix = T(G.inv_dx), iy = T(G.inv_dy), iz = T(G.inv_dz);
+    const size_t np = (size_t)G.npt;
+    const T* dp = z + 4 * np;
+    T acc[1] = {T(0)};
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < G.npt; p += gridDim.x * blockDim.x) {
+        int gz, gy, gx;
+        unflat<T>(G, p, gz, gy, gx);
+        const T zu = hdt * (r[p] - cgrad * d1x(dp, G, gz, gy, gx, ix));
+        const T zv = hdt * (r[np + p] - cgrad * d1y(dp, G, gz, gy, gx, iy));
+        const T zw = hdt * (r[2 * np + p] - cgrad * d1z(dp, G, gz, gy, gx, 4, iz));
+        const T zt = r[3 * np + p] * ith_t;
+        const T zp = dp[p];
+        z[p] = zu;
+        z[np + p] = zv;
+        z[2 * np + p] = zw;
+        z[3 * np + p] = zt;
+        acc[0] += zu * zu + zv * zv + zw * zw + zt * zt + zp * zp;
+    }
+    block_partials<1, T>(acc, 1, part, gridDim.x, blockIdx.x);
+    if (arrive_last(&ctl->counter[CNT_PC], gridDim.x)) {
+        __shared__ double tot[1];
+        final_sums(part, gridDim.x, 1, tot);
+        if (threadIdx.x == 0) {
+            const double zn = sqrt(tot[0]);
+            ctl->eps_jv = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+        }
+    }
+}
+
 static int stream_blocks3(size_t n) {
     size_t b = (n + NTHREADS - 1) / NTHREADS;
     return (int)(b < (size_t)MAX_STREAM_BLOCKS ? (b > 0 ? b : 1) : MAX_STREAM_BLOCKS);
@@ -829,10 +967,45 @@ static cudaError_t launch_pc3(const Geo& G, int sweeps, const T* r, T* z, T* za,
     return cudaSuccess;
 }
 
+// Acoustic Schur complement (3-D): rhs in da, iterates in za / zb, directions
+// in db and db + npt, the last sweep into the p plane of z, back-substitution.
+template <typename T>
+static cudaError_t launch_schur3d(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da, T* db,
+                                  double* part, Ctl* ctl, int check_done, cudaStream_t s, long long* launches) {
+    const size_t np = (size_t)G.npt;
+    const int nb = d3::stream_blocks3(np);
+    T* rhs = da;
+    d3::schur_rhs3d<T><<<nb, NTHREADS, 0, s>>>(G, r, rhs, ctl, check_done);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (launches) ++*launches;
+    T* xbuf[2] = {za, zb};
+    T* dbuf[2] = {db, db + np};
+    const T* xin = nullptr;
+    const T* din = nullptr;
+    for (int k = 1; k <= sweeps - 1; ++k) {
+        const bool first = k == 1, last = k == sweeps - 1;
+        T* xo = last ? z + 4 * np : xbuf[k & 1];
+        T* dO = dbuf[k & 1];
+        if (first && last) d3::helm3d<T, 1, 1><<<nb, NTHREADS, 0, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+        else if (first) d3::helm3d<T, 1, 0><<<nb, NTHREADS, 0, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+        else if (last) d3::helm3d<T, 0, 1><<<nb, NTHREADS, 0, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+        else d3::helm3d<T, 0, 0><<<nb, NTHREADS, 0, s>>>(G, k, rhs, xin, din, xo, dO, ctl, check_done);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (launches) ++*launches;
+        xin = xo;
+        din = dO;
+    }
+    d3::schur_back3d<T><<<nb, NTHREADS, 0, s>>>(G, r, z, part, ctl, check_done);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_precond3d(const Geo& G, int sweeps, const T* r, T* z, T* za, T* zb, T* da, T* db,
                              const T* nu, double* part, Ctl* ctl, int check_done, cudaStream_t s,
                              long long* launches) {
+    if (G.pc_schur) return launch_schur3d<T>(G, sweeps, r, z, za, zb, da, db, part, ctl, check_done, s, launches);
     return G.smag ? launch_pc3<T, 1>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches)
                   : launch_pc3<T, 0>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches);
 }

@@ -119,13 +119,62 @@ def test_schur_cuts_krylov_iterations():
     assert counts[synth.PC_SCHUR] <= 0.25 * counts[synth.PC_BLOCK], counts
 
 
-def test_schur_rejected_in_3d_and_for_one_sweep():
-    c = synth.case("tiny3d_16x16x8")
-    c["opts"]["precond"] = synth.PC_SCHUR
-    with pytest.raises(jf().JfnkError) as e:
-        jf().Solver(c)
-    assert e.value.code == jf().JFNK_ERR_UNSUPPORTED
+def test_schur_rejected_for_one_sweep():
     c = schur_case(16, 8, synth.PREC_FP64, sweeps=1)
     with pytest.raises(jf().JfnkError) as e:
         jf().Solver(c)
     assert e.value.code == jf().JFNK_ERR_UNSUPPORTED
+
+
+def schur_case3d(nx, ny, nz, prec, sweeps=8):
+    c = synth.case("tiny3d_%dx%dx%d" % (nx, ny, nz))
+    c["opts"]["precision"] = prec
+    c["opts"]["precond"] = synth.PC_SCHUR
+    c["opts"]["pc_sweeps"] = sweeps
+    c["sgs"]["mode"] = synth.SGS_SMAGORINSKY
+    return c
+
+
+@pytest.mark.parametrize("grid", [(16, 12, 8), (20, 18, 11)])
+@pytest.mark.parametrize("prec", [synth.PREC_FP64, synth.PREC_MIXED])
+@pytest.mark.parametrize("sweeps", [2, 9])
+def test_schur3d_precond_parity(grid, prec, sweeps):
+    c = schur_case3d(*grid, prec, sweeps=sweeps)
+    U = synth.random_state(c, 5, amp=(0.5, 0.3, 0.002))
+    m = Model(c)
+    s = jf().Solver(c)
+    r = np.random.Generator(np.random.PCG64(29)).standard_normal(U.shape)
+    ref = m.schur_precond(U, r, sweeps)
+    z = torch.empty_like(dev(U))
+    s.precond_apply(dev(U), dev(r), z)
+    err = rel_per_field(host(z), ref)
+    assert np.all(err < (1e-12 if prec == synth.PREC_FP64 else 1e-5)), err
+    s.close()
+
+
+def test_schur3d_step_parity_and_reduction():
+    """FP64 step against the oracle (tight tolerances, as in 2-D), and fewer
+    Krylov iterations than the field-block preconditioner on the same step."""
+    c = schur_case3d(16, 12, 8, synth.PREC_FP64, sweeps=8)
+    c["opts"]["eta"] = 1e-8
+    c["opts"]["newton_rtol"] = 1e-11
+    U = synth.random_state(c, 41, amp=(0.3, 0.1, 0.001))
+    m = Model(c)
+    st_ref = {}
+    ref = implicit_step(m, U, c["opts"], st_ref)
+    s = jf().Solver(c)
+    u = dev(U)
+    st = s.step(u)
+    got = host(u)
+    assert st["converged"] and st_ref["converged"]
+    assert st["newton_iters"] == st_ref["newton_iters"]
+    err = np.linalg.norm(m.scale(got - ref)) / np.linalg.norm(m.scale(ref))
+    assert err < 1e-10, err
+    s.close()
+    cb = synth.with_options(c, precond=synth.PC_BLOCK, pc_sweeps=4)
+    sb = jf().Solver(cb)
+    ub = dev(U)
+    stb = sb.step(ub)
+    assert stb["converged"]
+    assert st["gmres_iters"] < stb["gmres_iters"], (st["gmres_iters"], stb["gmres_iters"])
+    sb.close()
