@@ -771,7 +771,7 @@ static jfnk_status step_impl(jfnk_handle* h, double* u, jfnk_stats* out) {
         h->launches += 1;
     }
     jfnk_status st;
-    if (h->mixed && G.dim == 2) {
+    if (h->mixed) {
         // f = 2u^n/dt + F(u^n) and the first residual R(u^n) = -2 F(u^n) in one float64 pass
         kt_begin(h, JFNK_KF_RESIDUAL);
         CK(launch_stencil<double>(MODE_RHSRES, G, h->un, nullptr, nullptr, nullptr, h->f, h->R, h->part,

@@ -6,7 +6,7 @@
 namespace jfnk {
 
 enum StencilMode { MODE_F = 0, MODE_RHS = 1, MODE_RES = 2, MODE_JV = 3,
-                   MODE_RHSRES = 4 };   // 2-D: f = 2u/dt + F(u) into out and R(u) = -2 F(u) into out2, with norms
+                   MODE_RHSRES = 4 };   // f = 2u/dt + F(u) into out and R(u) = -2 F(u) into out2, with norms
 
 // Number of blocks of the 2-D stencil grid for element type T.
 template <typename T> int stencil_blocks(const Geo& G);

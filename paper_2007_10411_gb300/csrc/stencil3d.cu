@@ -28,7 +28,7 @@ namespace d3 {
 
 constexpr int R = 2;
 constexpr int HALO = 2 * R;
-constexpr int MODE_F = 0, MODE_RHS = 1, MODE_RES = 2, MODE_JV = 3;
+constexpr int MODE_F = 0, MODE_RHS = 1, MODE_RES = 2, MODE_JV = 3, MODE_RHSRES = 4;
 
 template <typename T>
 __device__ __forceinline__ T dd(const T* s, int i, int st, T ih) {
@@ -287,6 +287,16 @@ stencil3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
                 out[o] = Fv[fl];
             } else if (MODE == MODE_RHS) {
                 out[o] = T(G.two_over_dt * (double)u[o] + (double)Fv[fl]);
+            } else if (MODE == MODE_RHSRES) {
+                // at u = u^n the residual 2u/dt - F(u) - f with f = 2u/dt + F(u) is -2 F(u)
+                const double uo = (double)u[o];
+                const double Fd = (double)Fv[fl];
+                out[o] = T(G.two_over_dt * uo + Fd);
+                const double Rv = -2.0 * Fd;
+                out2[o] = T(Rv);
+                const double rs = Rv * G.inv_scale[fl], us = uo * G.inv_scale[fl];
+                acc[0] += rs * rs;
+                acc[1] += us * us;
             } else if (MODE == MODE_RES) {
                 const double uo = (double)u[o];
                 const double Rv = G.two_over_dt * uo - (double)Fv[fl] - f[o];
@@ -302,7 +312,7 @@ stencil3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
             }
         }
     }
-    if (MODE == MODE_RES) {
+    if (MODE == MODE_RES || MODE == MODE_RHSRES) {
         const int nblk = gridDim.x * gridDim.y * gridDim.z;
         const int blk = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         block_partials<2>(acc, 2, part, nblk, blk);
@@ -879,6 +889,7 @@ cudaError_t launch_stencil3d(int mode, const Geo& G, const T* u, const T* v, con
         JF3(d3::MODE_RHS)
         JF3(d3::MODE_RES)
         JF3(d3::MODE_JV)
+        JF3(d3::MODE_RHSRES)
         default: return cudaErrorInvalidValue;
     }
 #undef JF3
