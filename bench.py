@@ -301,6 +301,8 @@ def run_batch(args, rank: int, world: int, local_rank: int):
         dist = dist_
     n_inst = int(args.workload[len("uhi_batch"):] or 16)
     cases = synth.uhi_batch(n=n_inst)
+    if args.precond == "schur":
+        cases = [synth.with_options(c, precond=jfnk.PC_SCHUR, pc_sweeps=args.schur_sweeps) for c in cases]
     stream = torch.cuda.current_stream()
     batch = jfnk.Batch(cases, stream=stream)
     for i, c in enumerate(cases):
@@ -354,10 +356,14 @@ def run_batch(args, rank: int, world: int, local_rank: int):
                    "grids": [list(synth.shape(c)[:0:-1]) for c in cases],
                    "H0": [round(c["init"]["H0"], 2) for c in cases],
                    "precision": "mixed", "krylov_m": cases[0]["opts"]["krylov_m"],
+                   "precond": ("field-block Chebyshev (%d sweeps)" % cases[0]["opts"]["pc_sweeps"]
+                               if args.precond == "block" else
+                               "acoustic Schur complement (%d Helmholtz sweeps)" % cases[0]["opts"]["pc_sweeps"]),
                    "execution": "one handle + stream per instance, host thread per instance",
                    "parallelism": "replicas" if world > 1 else "single"},
         "newton_per_step": [statistics.mean(s["newton_iters"] for s in p) for p in per_inst],
         "gmres_iters_per_step": [statistics.mean(s["gmres_iters"] for s in p) for p in per_inst],
+        "converged": all(s["converged"] for st in stats for s in st),
         "clocks": clk, "e2e": e2e, "roofline": None, "cpu_baseline": None,
     }
     print(json.dumps(line), flush=True)
