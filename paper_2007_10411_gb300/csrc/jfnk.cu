@@ -46,6 +46,7 @@ struct jfnk_handle {
     // stencil-precision buffers (double for FP64, float for MIXED)
     void *V, *Z, *w, *uT, *xT, *za, *zb, *da, *db, *nu, *tA, *tB;
     double* part;
+    double* partB;   // second partial-sum area (Arnoldi pass B), inside the part allocation
     Ctl* ctl;
     Ctl* hctl;       // pinned mirror of the control header
     int* hdone;      // pinned ring of per-step "done" flags
@@ -301,7 +302,8 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
         const size_t rb = h->n / ((size_t)NTHREADS * 64) + 1;
         maxblk = std::max(maxblk, (int)std::min(rb, (size_t)MAX_REDUCE_BLOCKS));
     }
-    const size_t part_len = (size_t)maxblk * (KMAX + 2) + 16 * (size_t)MAX_STREAM_BLOCKS;
+    const size_t partA_len = (size_t)maxblk * (KMAX + 2) + 16 * (size_t)MAX_STREAM_BLOCKS;
+    const size_t part_len = partA_len + (size_t)maxblk * (KMAX + 2);
 
 #define ALLOC(ptr, bytes)                                                         \
     do {                                                                          \
@@ -336,6 +338,7 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     ALLOC(h->tA, nbT);
     ALLOC(h->tB, nbT);
     ALLOC(h->part, part_len * sizeof(double));
+    h->partB = h->part + partA_len;
     ALLOC(h->ctl, sizeof(Ctl));
 #undef ALLOC
     if (cudaMallocHost((void**)&h->hctl, sizeof(Ctl)) != cudaSuccess ||
@@ -709,10 +712,10 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
             CK(launch_arnoldi_a<T>(V, ld, w, n, j + 1, h->part, h->ctl, s));
             kt_end(h, JFNK_KF_ARNOLDI_A, (j + 2) * vb);
             kt_begin(h, JFNK_KF_ARNOLDI_B);
-            CK(launch_arnoldi_b<T>(V, ld, w, n, j + 1, m, h->part, h->ctl, s));
+            CK(launch_arnoldi_b<T>(V, ld, w, n, j + 1, h->part, h->partB, h->ctl, s));
             kt_end(h, JFNK_KF_ARNOLDI_B, (j + 3) * vb);   // reads v_0..v_j, w; writes w'
             kt_begin(h, JFNK_KF_ARNOLDI_C);
-            CK(launch_arnoldi_c<T>(V, ld, w, n, j + 1, h->ctl, s));
+            CK(launch_arnoldi_c<T>(V, ld, w, n, j + 1, m, h->partB, h->ctl, s));
             kt_end(h, JFNK_KF_ARNOLDI_C, (j + 3) * vb);
             h->launches += 3;
             CK(cudaMemcpyAsync(&h->hdone[j], &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -57,15 +57,18 @@ cudaError_t launch_budgets3d(const Geo& G, const double* u, double dV, double dz
                              Ctl* ctl, double* out, cudaStream_t s);
 
 // ------------------------------------------------------------ Krylov kernels
+// One Arnoldi step over v_0 .. v_{nv-1}: A writes its partial sums to partA,
+// B reads them and writes its own to partB (a separate buffer), C reads partB
+// and, in one extra block, updates the Hessenberg / Givens state in ctl.
 template <typename T>
-cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int nv, double* part,
+cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int nv, double* partA,
                              Ctl* ctl, cudaStream_t s);
 template <typename T>
-cudaError_t launch_arnoldi_b(const T* V, size_t ldv, T* w, size_t n, int nv, int m,
-                             double* part, Ctl* ctl, cudaStream_t s);
+cudaError_t launch_arnoldi_b(const T* V, size_t ldv, T* w, size_t n, int nv, const double* partA,
+                             double* partB, Ctl* ctl, cudaStream_t s);
 template <typename T>
-cudaError_t launch_arnoldi_c(T* V, size_t ldv, const T* w, size_t n, int nv, Ctl* ctl,
-                             cudaStream_t s);
+cudaError_t launch_arnoldi_c(T* V, size_t ldv, const T* w, size_t n, int nv, int m, const double* partB,
+                             Ctl* ctl, cudaStream_t s);
 template <typename T>
 cudaError_t launch_update(const T* Z, size_t ldz, double* x, T* xT, size_t n, double* part,
                           Ctl* ctl, cudaStream_t s);

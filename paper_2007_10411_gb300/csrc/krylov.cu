@@ -5,18 +5,21 @@
 // the basis V = [v_0 .. v_j]:
 //   A:  h1 = V^T w                                  (multi-dot)
 //   B:  w' = w - V h1 (stored over w),  h2 = V^T w',  ||w'||^2
-//       last block: h = h1 + h2, h_{j+1,j} = sqrt(||w'||^2 - ||h2||^2), Givens
-//       rotation of the Hessenberg column, residual estimate |g_{j+1}|,
-//       stopping test and (when the cycle ends) the triangular solve for y
-//   C:  v_{j+1} = (w' - V h2) / h_{j+1,j}             (multi-axpy + scale)
+//   C:  v_{j+1} = (w' - V h2) / h_{j+1,j},  h_{j+1,j} = sqrt(||w'||^2 - ||h2||^2)
+//       (multi-axpy + scale); one extra block of the same launch forms the
+//       Hessenberg column h = h1 + h2, applies the Givens rotations, updates
+//       the residual estimate |g_{j+1}|, takes the stopping test and (when
+//       the cycle ends) solves the triangular system for y
 // The second projection is subtracted from the stored w', as in classical
 // Gram-Schmidt applied twice: the rounding of w - V h1 is then part of what
 // h2 removes, and the last rounding is relative to ||w'||, not ||w||.
-// Reductions are two-stage and deterministic: every block writes its partial
-// sums, the last block to finish adds them in a fixed order.  A thread
-// accumulates its partial dot products in the basis precision over at most
-// 64 vector elements (the grid grows with n), then the block and grid
-// reductions run in float64.
+// Reductions are two-stage and deterministic: every block of a pass writes
+// its partial sums, and every block of the NEXT pass adds all of them in one
+// fixed order (grid_sums), so that no pass ends in a serial last-block tail
+// and all blocks hold bitwise the same coefficients.  A thread accumulates
+// its partial dot products in the basis precision over at most 64 vector
+// elements (the grid grows with n), then the block and grid sums run in
+// float64.
 #include <math.h>
 
 #include <algorithm>
@@ -79,6 +82,118 @@ static int reduce_blocks(size_t nvec) {
     return (int)(b < (size_t)MAX_REDUCE_BLOCKS ? b : MAX_REDUCE_BLOCKS);
 }
 
+// Partial sums of the Arnoldi passes.  A float64 basis keeps float64
+// partials.  A float32 basis keeps each partial as an unevaluated pair of
+// float32 numbers hi + lo (double-float: Dekker 1971; TwoSum: Knuth, TAOCP
+// vol. 2), so that the grid-level sums, which every block of the next pass
+// repeats, run on the float32 pipes (GB300's float64 rate is a small
+// fraction of its float32 rate) with ~2^-44 relative rounding per addition.
+template <typename T> struct PartOf;
+template <> struct PartOf<float> { using type = float2; };     // x = hi, y = lo
+template <> struct PartOf<double> { using type = double; };
+
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b.x - bb);
+    const float lo = e + (a.y + b.y);
+    const float hi = s + lo;
+    return make_float2(hi, lo - (hi - s));
+}
+__device__ __forceinline__ double padd(double a, double b) { return a + b; }
+__device__ __forceinline__ double pval(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ double pval(double a) { return a; }
+__device__ __forceinline__ void pset(float2& p, float v) { p = make_float2(v, 0.f); }
+__device__ __forceinline__ void pset(double& p, double v) { p = v; }
+__device__ __forceinline__ float2 pzero(float2) { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ double pzero(double) { return 0.0; }
+__device__ __forceinline__ float2 pshfl_down(float2 a, int o) {
+    return make_float2(__shfl_down_sync(0xffffffffu, a.x, o), __shfl_down_sync(0xffffffffu, a.y, o));
+}
+__device__ __forceinline__ double pshfl_down(double a, int o) { return __shfl_down_sync(0xffffffffu, a, o); }
+__device__ __forceinline__ float2 pload(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ double pload(const double* p) { return __ldcg(p); }
+
+// Block partial of NV per-warp sums red[k][w] (k < nv) into part[k * stride + blk].
+template <typename T, int NV, typename P>
+__device__ __forceinline__ void store_partials(const T (*red)[NTHREADS / 32], int nv, P* part, int stride, int blk) {
+    const int nw = blockDim.x >> 5;
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        P t;
+        pset(t, red[k][0]);
+        for (int ww = 1; ww < nw; ++ww) {
+            P u;
+            pset(u, red[k][ww]);
+            t = padd(t, u);
+        }
+        part[(size_t)k * stride + blk] = t;
+    }
+}
+
+// Every block: out[k] = sum over b < nblk of part[k * nblk + b], k < nv, in one
+// fixed order, so all blocks of a launch obtain bitwise the same sums.  Warp w
+// takes the values w, w + nw (together), w + 2 nw, ...; a lane adds
+// b = lane + 32 r with all its loads of a 512-block chunk in flight, then a
+// fixed tree over r and a fixed shuffle tree over the lanes.
+template <typename P>
+__device__ __forceinline__ P chunk_sum(const P* p, int nblk, int b0, int lane) {
+    P v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int b = b0 + lane + 32 * r;
+        v[r] = b < nblk ? pload(p + b) : pzero(P());
+    }
+#pragma unroll
+    for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+        for (int r = 0; r < h; ++r) v[r] = padd(v[r], v[r + h]);
+    return v[0];
+}
+
+template <typename P, typename TO>
+__device__ void grid_sums(const P* part, int nblk, int nv, double* out, TO* outT) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int k = warp; k < nv; k += 2 * nw) {
+        const int k2 = k + nw;
+        const P* p = part + (size_t)k * nblk;
+        const P* p2 = part + (size_t)(k2 < nv ? k2 : k) * nblk;
+        P s = pzero(P()), s2 = pzero(P());
+        for (int b0 = 0; b0 < nblk; b0 += 512) {
+            const P c = chunk_sum(p, nblk, b0, lane);
+            const P c2 = chunk_sum(p2, nblk, b0, lane);
+            s = padd(s, c);
+            s2 = padd(s2, c2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s = padd(s, pshfl_down(s, o));
+            s2 = padd(s2, pshfl_down(s2, o));
+        }
+        if (lane == 0) {
+            out[k] = pval(s);
+            outT[k] = TO(out[k]);
+            if (k2 < nv) {
+                out[k2] = pval(s2);
+                outT[k2] = TO(out[k2]);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// h_{j+1,j}^2 = ||w'||^2 - ||h2||^2 by one warp (nv <= 32): every lane returns
+// the same value.  The Givens block and the streaming blocks of pass C both
+// call it, so the Hessenberg entry and the normalisation of v_{j+1} are the
+// same number.
+__device__ __forceinline__ double subdiag2(const double* h2, int nv, double wn2) {
+    const int lane = threadIdx.x & 31;
+    double q = lane < nv ? h2[lane] * h2[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    return wn2 - __shfl_sync(0xffffffffu, q, 0);
+}
+
 // ---------------------------------------------------------------- pass A
 template <typename T, int NV>
 __global__ void __launch_bounds__(NTHREADS, 3)
@@ -105,70 +220,115 @@ arnoldi_a(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n
             if (k < nv) acc_t[k] += V[k * ldv + i] * w[i];
     }
     pdl_trigger();
-    block_partials<NV, T>(acc_t, nv, part, gridDim.x, blockIdx.x);
-    if (arrive_last(&ctl->counter[CNT_PASSA], gridDim.x)) {
-        __shared__ double tot[NV];
-        final_sums(part, gridDim.x, nv, tot);
-        for (int k = threadIdx.x; k < nv; k += blockDim.x) ctl->h1[k] = tot[k];
+    __shared__ T red[NV][NTHREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        if (k < nv) {
+            T x = acc_t[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) red[k][warp] = x;
+        }
     }
+    __syncthreads();
+    store_partials<T, NV>(red, nv, reinterpret_cast<typename PartOf<T>::type*>(part), gridDim.x, blockIdx.x);
 }
 
+
+
 // ---------------------------------------------------------------- pass B
-// Serial Hessenberg / Givens update for column j (one thread).
+// Hessenberg column j, its Givens rotation, the residual estimate, the
+// stopping test and (when the cycle ends) the triangular solve R y = g, by
+// one whole block.  It runs beside the streaming blocks of pass C, whose
+// traffic makes every global round trip slow, so all threads first stage the
+// operands in shared memory with their loads in flight together; the
+// rotation sequence then runs in thread 0 on shared memory, and the stores
+// and the solve are spread over the block.
 __device__ void givens_update(Ctl* c, int j, int m, const double* h2, double wn2) {
-    double col[KMAX + 1];
-    double hh2 = 0.0;
-    for (int k = 0; k <= j; ++k) {
+    __shared__ double col[KMAX + 1], csv[KMAX], snv[KMAX], gv[KMAX + 1], ys[KMAX];
+    __shared__ double Rs[KMAX][KMAX + 1];
+    __shared__ int finish;
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) {
         const double hk = c->h1[k] + h2[k];
-        c->h2[k] = h2[k];              // pass C subtracts V h2 from the stored w'
-        c->Hbar[k][j] = hk;
         col[k] = hk;
-        hh2 += h2[k] * h2[k];
-    }
-    const double hn2 = wn2 - hh2;
-    const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
-    c->Hbar[j + 1][j] = hn;
-    col[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {
-        const double t = c->cs[i] * col[i] + c->sn[i] * col[i + 1];
-        col[i + 1] = -c->sn[i] * col[i] + c->cs[i] * col[i + 1];
-        col[i] = t;
-    }
-    double cs = 1.0, sn = 0.0;
-    if (col[j + 1] != 0.0) {
-        const double rho = hypot(col[j], col[j + 1]);
-        cs = col[j] / rho;
-        sn = col[j + 1] / rho;
-    }
-    c->cs[j] = cs;
-    c->sn[j] = sn;
-    for (int k = 0; k < j; ++k) c->Rt[k][j] = col[k];
-    c->Rt[j][j] = cs * col[j] + sn * col[j + 1];
-    const double gj = c->g[j];
-    c->g[j + 1] = -sn * gj;
-    c->g[j] = cs * gj;
-    c->gres = fabs(c->g[j + 1]);
-    c->iters += 1;
-    const bool finite = isfinite(hn2) && isfinite(c->g[j + 1]) && isfinite(c->Rt[j][j]);
-    const bool conv = fabs(c->g[j + 1]) <= c->target;
-    const bool brk = hn == 0.0;
-    c->inv_hn = hn > 0.0 ? 1.0 / hn : 0.0;
-    if (!finite) {
-        c->nan = 1;
-        c->done = 1;
-        c->k = 0;
-        return;
-    }
-    if (conv || brk || j == m - 1) {
-        const int k = j + 1;
-        for (int i = k - 1; i >= 0; --i) {     // back substitution R y = g
-            double s = c->g[i];
-            for (int l = i + 1; l < k; ++l) s -= c->Rt[i][l] * c->y[l];
-            c->y[i] = s / c->Rt[i][i];
+        gv[k] = c->g[k];
+        if (k < j) {
+            csv[k] = c->cs[k];
+            snv[k] = c->sn[k];
         }
-        c->k = k;
-        c->converged = conv || brk;
-        c->breakdown = brk && !conv;
+        c->h2[k] = h2[k];
+        c->Hbar[k][j] = hk;
+    }
+    __syncthreads();
+    double hn2 = 0.0;
+    if (threadIdx.x < 32) hn2 = subdiag2(h2, j + 1, wn2);
+    if (threadIdx.x == 0) {
+        const double target = c->target;
+        const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
+        col[j + 1] = hn;
+        for (int i = 0; i < j; ++i) {
+            const double t = csv[i] * col[i] + snv[i] * col[i + 1];
+            col[i + 1] = -snv[i] * col[i] + csv[i] * col[i + 1];
+            col[i] = t;
+        }
+        double cs = 1.0, sn = 0.0;
+        if (col[j + 1] != 0.0) {
+            const double rho = hypot(col[j], col[j + 1]);
+            cs = col[j] / rho;
+            sn = col[j + 1] / rho;
+        }
+        const double rjj = cs * col[j] + sn * col[j + 1];
+        col[j] = rjj;
+        const double gj = gv[j];
+        const double gn = -sn * gj;
+        gv[j] = cs * gj;
+        gv[j + 1] = gn;
+        c->Hbar[j + 1][j] = hn;
+        c->cs[j] = cs;
+        c->sn[j] = sn;
+        c->Rt[j][j] = rjj;
+        c->g[j + 1] = gn;
+        c->g[j] = gv[j];
+        c->gres = fabs(gn);
+        c->iters += 1;
+        c->inv_hn = hn > 0.0 ? 1.0 / hn : 0.0;
+        const bool finite = isfinite(hn2) && isfinite(gn) && isfinite(rjj);
+        const bool conv = fabs(gn) <= target;
+        const bool brk = hn == 0.0;
+        finish = 0;
+        if (!finite) {
+            c->nan = 1;
+            c->k = 0;
+            c->done = 1;
+        } else if (conv || brk || j == m - 1) {
+            c->converged = conv || brk;
+            c->breakdown = brk && !conv;
+            finish = 1;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < j; k += blockDim.x) c->Rt[k][j] = col[k];
+    if (!finish) return;
+    // back substitution R y = g, column by column (R from earlier columns in
+    // global memory, column j in col)
+    const int K = j + 1;
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+        const int i = e / K, l = e - i * K;
+        Rs[i][l] = l == j ? col[i] : (i <= l ? c->Rt[i][l] : 0.0);
+    }
+    for (int i = threadIdx.x; i < K; i += blockDim.x) ys[i] = gv[i];
+    __syncthreads();
+    for (int i = K - 1; i >= 0; --i) {
+        if (threadIdx.x == 0) ys[i] = ys[i] / Rs[i][i];
+        __syncthreads();
+        for (int l = threadIdx.x; l < i; l += blockDim.x) ys[l] -= Rs[l][i] * ys[i];
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < K; i += blockDim.x) c->y[i] = ys[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        c->k = K;
         c->done = 1;
     }
 }
@@ -235,22 +395,28 @@ __device__ __forceinline__ void work_b(const VT (&v)[CH], VT wv, T* __restrict__
     }
 }
 
-// Pass B, split over KS lanes per element: w' = w - V h1 (stored over w),
-// ||w'||^2 and h2 = V^T w'; the last block runs the Givens update.  Each lane
-// keeps its CH basis entries in registers for both uses, so every basis vector
-// is read from memory once; the next element's loads are issued before the
-// current one is combined (software pipeline).
+// Pass B, split over KS lanes per element: h1 from pass A's partials (every
+// block, grid_sums), w' = w - V h1 (stored over w), ||w'||^2 and h2 = V^T w'
+// into this pass's partials.  Each lane keeps its CH basis entries in
+// registers for both uses, so every basis vector is read from memory once;
+// the next element's loads are issued before the current one is combined
+// (software pipeline).
 template <typename T, int NV>
 __global__ void __launch_bounds__(NTHREADS, 2)
-arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int nv, int m,
-          double* part, Ctl* ctl) {
+arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int nv,
+          const double* partA, int nblkA, double* part, Ctl* ctl) {
     pdl_wait();
-    if (ctl->done) return;
+    const int done = ctl->done;     // no writer during this launch; read beside the partials
     constexpr int KS = 4, CH = NV / KS;
+    __shared__ double h1d[NV];
     __shared__ T h1s[NV];
     __shared__ T red[NV + 1][NTHREADS / 32];
-    for (int k = threadIdx.x; k < NV; k += blockDim.x) h1s[k] = k < nv ? T(ctl->h1[k]) : T(0);
-    __syncthreads();
+    using P = typename PartOf<T>::type;
+    for (int k = nv + threadIdx.x; k < NV; k += blockDim.x) h1s[k] = T(0);
+    grid_sums(reinterpret_cast<const P*>(partA), nblkA, nv, h1d, h1s);
+    if (done) return;
+    if (blockIdx.x == 0)       // h1 for the Hessenberg column
+        for (int k = threadIdx.x; k < nv; k += blockDim.x) ctl->h1[k] = h1d[k];
     using VT = typename V4<T>::type;
     constexpr int W = V4<T>::W;
     const int q = threadIdx.x & (KS - 1);
@@ -284,7 +450,7 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int 
         work_b<T, T, CH, KS>(v, w[i], w, i, q, h1s, acc, accn);
     }
     pdl_trigger();
-    // block sums: slot 0 = ||w'||^2, slot 1 + k = v_k . w' (fixed shuffle trees; float64 across warps)
+    // block sums: slot 0 = ||w'||^2, slot 1 + k = v_k . w' (fixed shuffle trees, then the partial type across warps)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -300,43 +466,55 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int 
         if (lane == 0) red[0][warp] = x;
     }
     __syncthreads();
-    const int nw = blockDim.x >> 5;
-    for (int k = threadIdx.x; k < nv + 1; k += blockDim.x) {
-        double t = 0.0;
-        for (int ww = 0; ww < nw; ++ww) t += (double)red[k][ww];
-        part[(size_t)k * gridDim.x + blockIdx.x] = t;
-        __threadfence();          // publish before the block's arrival is counted
-    }
-    if (arrive_last(&ctl->counter[CNT_PASSB], gridDim.x)) {
-        __shared__ double tot[NV + 1];
-        final_sums(part, gridDim.x, nv + 1, tot);
-        if (threadIdx.x == 0) givens_update(ctl, nv - 1, m, tot + 1, tot[0]);
-    }
+    store_partials<T, NV + 1>(red, nv + 1, reinterpret_cast<P*>(part), gridDim.x, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- pass C
+// Every block sums pass B's partials (||w'||^2, h2).  Block 0 runs the serial
+// Hessenberg / Givens update for column j = nv - 1 while blocks 1.. stream
+// v_{j+1}.  A streaming block that starts after block 0 has ended the cycle
+// (converged, breakdown or m steps) finds done set and returns: v_{j+1} is
+// not used after the cycle's last step.
 template <typename T, int NV>
 __global__ void __launch_bounds__(NTHREADS, 3)
-arnoldi_c(T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv, Ctl* ctl) {
+arnoldi_c(T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int nv, int m,
+          const double* partB, int nblkB, Ctl* ctl) {
     pdl_wait();
-    if (ctl->done) return;
     using VT = typename V4<T>::type;
     constexpr int W = V4<T>::W;
-    __shared__ T hs[NV];
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = T(ctl->h2[k]);
+    __shared__ double tot[NV + 1];
+    __shared__ T tots[NV + 1];      // tots[1 + k] = h2_k rounded to T
+    __shared__ T inv_s;
+    __shared__ int done;
+    // block 0 writes ctl->done during this launch: one thread reads it for the
+    // whole block, so that every thread of a block takes the same branch
+    if (threadIdx.x == 0) done = *(volatile int*)&ctl->done;
+    grid_sums(reinterpret_cast<const typename PartOf<T>::type*>(partB), nblkB, nv + 1, tot, tots);
+    if (done) return;
+    if (blockIdx.x == 0) {
+        givens_update(ctl, nv - 1, m, tot + 1, tot[0]);
+        return;
+    }
+    const T* hs = tots + 1;
+    if (threadIdx.x < 32) {
+        const double hn2 = subdiag2(tot + 1, nv, tot[0]);
+        const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
+        if (threadIdx.x == 0) inv_s = T(hn > 0.0 ? 1.0 / hn : 0.0);
+    }
     __syncthreads();
-    const T inv = T(ctl->inv_hn);
+    const T inv = inv_s;
     const size_t nvec = n / W;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t nblk = gridDim.x - 1, blk = blockIdx.x - 1;
+    const size_t stride = nblk * blockDim.x;
     T* vout = V + (size_t)nv * ldv;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvec; i += stride) {
+    for (size_t i = blk * blockDim.x + threadIdx.x; i < nvec; i += stride) {
         VT wp = reinterpret_cast<const VT*>(w)[i];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
             if (k < nv) wp = axpyv(wp, hs[k], reinterpret_cast<const VT*>(V + k * ldv)[i]);
         reinterpret_cast<VT*>(vout)[i] = scalev(wp, inv);
     }
-    for (size_t i = nvec * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (size_t i = nvec * W + blk * blockDim.x + threadIdx.x; i < n; i += stride) {
         T wp = w[i];
         for (int k = 0; k < nv; ++k) wp -= hs[k] * V[k * ldv + i];
         vout[i] = wp * inv;
@@ -629,31 +807,42 @@ pc_eps_k(const float* __restrict__ z, size_t n, double* part, Ctl* ctl) {
 
 // ---------------------------------------------------------------- launchers
 
+// Grids of the three passes (B and C size their reads of the previous pass's
+// partials from them).  Pass C adds one block for the Givens update and keeps
+// the whole grid within one wave of three CTAs per SM.
+template <typename T> static int grid_a(size_t n) {
+    return std::max(dot_blocks(n / V4<T>::W), reduce_blocks(n / V4<T>::W));
+}
+template <typename T> static int grid_b(size_t n) { return reduce_blocks(n / V4<T>::W); }
+template <typename T> static int grid_c(size_t n) {
+    return std::min(dot_blocks(n / V4<T>::W) + 1, MAX_DOT_BLOCKS);
+}
+
 template <typename T>
-cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int nv, double* part,
+cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int nv, double* partA,
                              Ctl* ctl, cudaStream_t s) {
-    const int nb = std::max(dot_blocks(n / V4<T>::W), reduce_blocks(n / V4<T>::W));
-    if (nv <= 8) return launch_pdl(arnoldi_a<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, part, ctl);
-    if (nv <= 16) return launch_pdl(arnoldi_a<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, part, ctl);
-    return launch_pdl(arnoldi_a<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, part, ctl);
+    const int nb = grid_a<T>(n);
+    if (nv <= 8) return launch_pdl(arnoldi_a<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, ctl);
+    if (nv <= 16) return launch_pdl(arnoldi_a<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, ctl);
+    return launch_pdl(arnoldi_a<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, ctl);
 }
 
 template <typename T>
-cudaError_t launch_arnoldi_b(const T* V, size_t ldv, T* w, size_t n, int nv, int m,
-                             double* part, Ctl* ctl, cudaStream_t s) {
-    const int nb = reduce_blocks(n / V4<T>::W);
-    if (nv <= 8) return launch_pdl(arnoldi_b<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, m, part, ctl);
-    if (nv <= 16) return launch_pdl(arnoldi_b<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, m, part, ctl);
-    return launch_pdl(arnoldi_b<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, m, part, ctl);
+cudaError_t launch_arnoldi_b(const T* V, size_t ldv, T* w, size_t n, int nv, const double* partA,
+                             double* partB, Ctl* ctl, cudaStream_t s) {
+    const int nb = grid_b<T>(n), na = grid_a<T>(n);
+    if (nv <= 8) return launch_pdl(arnoldi_b<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl);
+    if (nv <= 16) return launch_pdl(arnoldi_b<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl);
+    return launch_pdl(arnoldi_b<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl);
 }
 
 template <typename T>
-cudaError_t launch_arnoldi_c(T* V, size_t ldv, const T* w, size_t n, int nv, Ctl* ctl,
-                             cudaStream_t s) {
-    const int nb = dot_blocks(n / V4<T>::W);
-    if (nv <= 8) return launch_pdl(arnoldi_c<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, ctl);
-    if (nv <= 16) return launch_pdl(arnoldi_c<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, ctl);
-    return launch_pdl(arnoldi_c<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, ctl);
+cudaError_t launch_arnoldi_c(T* V, size_t ldv, const T* w, size_t n, int nv, int m, const double* partB,
+                             Ctl* ctl, cudaStream_t s) {
+    const int nc = grid_c<T>(n), nb = grid_b<T>(n);
+    if (nv <= 8) return launch_pdl(arnoldi_c<T, 8>, nc, NTHREADS, 0, s, V, ldv, w, n, nv, m, partB, nb, ctl);
+    if (nv <= 16) return launch_pdl(arnoldi_c<T, 16>, nc, NTHREADS, 0, s, V, ldv, w, n, nv, m, partB, nb, ctl);
+    return launch_pdl(arnoldi_c<T, 32>, nc, NTHREADS, 0, s, V, ldv, w, n, nv, m, partB, nb, ctl);
 }
 
 template <typename T>
@@ -742,9 +931,10 @@ cudaError_t launch_pc_eps(const float* z, size_t n, double* part, Ctl* ctl, cuda
 #define JF_INST(T)                                                                                     \
     template cudaError_t launch_arnoldi_a<T>(const T*, size_t, const T*, size_t, int, double*, Ctl*,  \
                                              cudaStream_t);                                            \
-    template cudaError_t launch_arnoldi_b<T>(const T*, size_t, T*, size_t, int, int, double*,         \
+    template cudaError_t launch_arnoldi_b<T>(const T*, size_t, T*, size_t, int, const double*,        \
+                                             double*, Ctl*, cudaStream_t);                             \
+    template cudaError_t launch_arnoldi_c<T>(T*, size_t, const T*, size_t, int, int, const double*,   \
                                              Ctl*, cudaStream_t);                                      \
-    template cudaError_t launch_arnoldi_c<T>(T*, size_t, const T*, size_t, int, Ctl*, cudaStream_t);  \
     template cudaError_t launch_update<T>(const T*, size_t, double*, T*, size_t, double*, Ctl*,       \
                                           cudaStream_t);                                               \
     template cudaError_t launch_cycle_init<T>(const Geo&, const double*, T*, double*, size_t, double, \
