@@ -54,6 +54,11 @@ struct Ctl {
     int iters;           // Krylov iterations in this Newton solve
     int m;               // restart length
     int ncap;            // training pairs recorded for the learned preconditioner
+    int eps_part;        // > 0: ||z||^2 of the last preconditioner apply is pending as that many
+                         // float-float partials at the head of the partial buffer (float32 2-D
+                         // field-block path); the Jacobian-product kernel forms eps from them.
+                         // 0: eps_jv holds the step.  Every writer of eps_jv clears it.
+    int pad_;
     double beta0;        // ||b|| of the Newton system
     double target;       // eta * beta0
     double res2;         // ||W R||^2 of the last residual evaluation
@@ -157,6 +162,66 @@ __device__ __forceinline__ void block_partials_max(const double (&v)[NV], int nv
         part[(size_t)k * stride + blk] = s;
         __threadfence();          // publish before the block's arrival is counted
     }
+}
+
+// Double-float addition of unevaluated float32 pairs (x = hi, y = lo): TwoSum
+// of the high parts (Knuth, TAOCP vol. 2), low parts added, renormalised
+// (Dekker 1971).  ~2^-44 relative rounding on the float32 pipes.
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b.x - bb);
+    const float lo = e + (a.y + b.y);
+    const float hi = s + lo;
+    return make_float2(hi, lo - (hi - s));
+}
+
+// One float-float partial of a block's float32 values: fixed shuffle tree per
+// warp, warps added in order by thread 0, stored at p[blk].
+__device__ __forceinline__ void block_partial_ff(float v, float2* p, int blk) {
+    __shared__ float red[NTHREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float2 t = make_float2(red[0], 0.f);
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = ff_add(t, make_float2(red[w], 0.f));
+        p[blk] = t;
+    }
+}
+
+// Finite-difference step of a Jacobian product: eps_jv, or, when ctl->eps_part
+// > 0, eps = sqrt(eps_mach (1 + ||u||)) / ||z|| with ||z||^2 summed from the
+// pending float-float partials in one fixed order (every block of the launch
+// obtains bitwise the same value).  Called by all threads of the block.
+__device__ __forceinline__ double pending_eps(const Ctl* ctl, const double* part) {
+    __shared__ double wsum[NTHREADS / 32];
+    __shared__ double eps_s;
+    const int np = ctl->eps_part;
+    if (np > 0) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const float2* p = reinterpret_cast<const float2*>(part);
+        float2 s = make_float2(0.f, 0.f);
+#pragma unroll 8
+        for (int b = threadIdx.x; b < np; b += blockDim.x) s = ff_add(s, __ldcg(p + b));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            s = ff_add(s, make_float2(__shfl_down_sync(0xffffffffu, s.x, o), __shfl_down_sync(0xffffffffu, s.y, o)));
+        if (lane == 0) wsum[warp] = (double)s.x + (double)s.y;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+            const double zn = sqrt(t);
+            eps_s = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+        }
+    } else if (threadIdx.x == 0) {
+        eps_s = ctl->eps_jv;
+    }
+    __syncthreads();
+    return eps_s;
 }
 
 // True in exactly one block: the last one to arrive.  The threads that wrote

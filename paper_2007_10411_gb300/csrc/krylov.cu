@@ -92,14 +92,7 @@ template <typename T> struct PartOf;
 template <> struct PartOf<float> { using type = float2; };     // x = hi, y = lo
 template <> struct PartOf<double> { using type = double; };
 
-__device__ __forceinline__ float2 padd(float2 a, float2 b) {
-    const float s = a.x + b.x;
-    const float bb = s - a.x;
-    const float e = (a.x - (s - bb)) + (b.x - bb);
-    const float lo = e + (a.y + b.y);
-    const float hi = s + lo;
-    return make_float2(hi, lo - (hi - s));
-}
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return ff_add(a, b); }
 __device__ __forceinline__ double padd(double a, double b) { return a + b; }
 __device__ __forceinline__ double pval(float2 a) { return (double)a.x + (double)a.y; }
 __device__ __forceinline__ double pval(double a) { return a; }
@@ -587,6 +580,7 @@ update_x(const T* __restrict__ Z, size_t ldz, double* __restrict__ x, T* __restr
             ctl->scratch[0] = tot[0];
             const double xn = sqrt(tot[0]);
             ctl->eps_jv = xn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / xn : 0.0;
+            ctl->eps_part = 0;
         }
     }
 }
@@ -617,7 +611,10 @@ cycle_init(Geo G, const double* __restrict__ R, T* __restrict__ V0, double* __re
         ctl->k = 0;
         ctl->iters = 0;
         ctl->m = m;
-        if (pc_none) ctl->eps_jv = sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2)));
+        if (pc_none) {
+            ctl->eps_jv = sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2)));
+            ctl->eps_part = 0;
+        }
     }
 }
 
@@ -657,7 +654,10 @@ restart_scale(T* __restrict__ V0, size_t n, int pc_none, Ctl* ctl) {
         ctl->converged = 0;
         ctl->breakdown = 0;
         ctl->k = 0;
-        if (pc_none) ctl->eps_jv = sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2)));
+        if (pc_none) {
+            ctl->eps_jv = sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2)));
+            ctl->eps_part = 0;
+        }
     }
 }
 
@@ -710,6 +710,7 @@ norm2_k(Geo G, const T* __restrict__ a, size_t n, int weighted, int slot, double
 }
 
 __global__ void set_eps_k(double eps, int su, int sv, Ctl* ctl) {
+    ctl->eps_part = 0;
     if (eps > 0.0) {
         ctl->eps_jv = eps;
     } else {
@@ -801,6 +802,7 @@ pc_eps_k(const float* __restrict__ z, size_t n, double* part, Ctl* ctl) {
         if (threadIdx.x == 0) {
             const double zn = sqrt(tot[0]);
             ctl->eps_jv = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+            ctl->eps_part = 0;
         }
     }
 }

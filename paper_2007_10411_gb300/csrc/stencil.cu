@@ -24,6 +24,7 @@
 // in shared memory.
 #include <math.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "common.cuh"
@@ -360,6 +361,105 @@ stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
 }
 
 // ============================================================================
+// Asynchronous tile staging (cp.async, sm_80 and later): the copies of the
+// next tile land in shared memory while the current tile is computed.
+// 16-byte chunks for rows inside the grid, element copies at the periodic x
+// seam; a source size of 0 zero-fills (rows beyond one mirror reflection).
+// ============================================================================
+__device__ __forceinline__ void cpa16(void* dst, const void* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+template <int B>
+__device__ __forceinline__ void cpa_elem(void* dst, const void* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(B), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Issue the copies of the ghost-extended u and v tiles (four fields each) into
+// s[0..4) and s[4..8) (planes of SZ x SX).  jv_stage_fix walks the same chunk
+// -> thread assignment once the copies have landed, so a thread only touches
+// what it copied itself: mirror signs on ghost rows and the eps scale on v,
+// in the order load_fields applies them.
+template <typename T>
+__device__ __forceinline__ void jv_stage_issue(T* s, const T* __restrict__ u, const T* __restrict__ v,
+                                               const Geo& G, int x0, int z0, int SX, int SZ) {
+    constexpr int VW = Vec16<T>::W;
+    const int plane = SZ * SX;
+    if (rows_vectorisable<T>(G, x0, SX)) {
+        const int nch = SX / VW;
+        const int total = nch * SZ;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int iz = idx / nch, c = idx - iz * nch;
+            int side;
+            const int sz = mirror_z(z0 + iz - HALO, G.nz, side);
+            const bool ok = sz >= 0 && sz < G.nz;
+            const size_t off = ok ? (size_t)sz * G.nx + (x0 - HALO + c * VW) : 0;
+            T* d = s + iz * SX + c * VW;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                cpa16(d + f * plane, u + (size_t)f * G.npt + off, ok ? 16 : 0);
+                cpa16(d + (4 + f) * plane, v + (size_t)f * G.npt + off, ok ? 16 : 0);
+            }
+        }
+        return;
+    }
+    const int total = SX * SZ;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int iz = idx / SX, ix = idx - iz * SX;
+        int side;
+        const int sz = mirror_z(z0 + iz - HALO, G.nz, side);
+        const bool ok = sz >= 0 && sz < G.nz;
+        const size_t off = ok ? (size_t)sz * G.nx + wrap_x(x0 + ix - HALO, G.nx) : 0;
+        T* d = s + iz * SX + ix;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            cpa_elem<sizeof(T)>(d + f * plane, u + (size_t)f * G.npt + off, ok ? (int)sizeof(T) : 0);
+            cpa_elem<sizeof(T)>(d + (4 + f) * plane, v + (size_t)f * G.npt + off, ok ? (int)sizeof(T) : 0);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void jv_stage_fix(T* s, const T (&ev)[4], const Geo& G, int x0, int z0, int SX,
+                                             int SZ) {
+    using VT = typename Vec16<T>::type;
+    constexpr int VW = Vec16<T>::W;
+    const int plane = SZ * SX;
+    const bool vec = rows_vectorisable<T>(G, x0, SX);
+    const int per = vec ? SX / VW : SX;
+    const int total = per * SZ;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int iz = idx / per, c = idx - iz * per;
+        int side;
+        const int sz = mirror_z(z0 + iz - HALO, G.nz, side);
+        if (sz < 0 || sz >= G.nz) continue;       // zero-filled row
+        T* d = s + iz * SX + (vec ? c * VW : c);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const T sg = side == 1 ? T(G.pb[f]) : side == 2 ? T(G.pt[f]) : T(1);
+            if (vec) {
+                VT* pu = reinterpret_cast<VT*>(d + f * plane);
+                VT* pv = reinterpret_cast<VT*>(d + (4 + f) * plane);
+                if (side) *pu = Vec16<T>::mul(sg, *pu);
+                VT b = Vec16<T>::mul(ev[f], *pv);
+                if (side) b = Vec16<T>::mul(sg, b);
+                *pv = b;
+            } else {
+                if (side) d[f * plane] *= sg;
+                T b = ev[f] * d[(4 + f) * plane];
+                if (side) b *= sg;
+                d[(4 + f) * plane] = b;
+            }
+        }
+    }
+}
+
+// ============================================================================
 // Mixed-path Jv: the forward difference F(u + eps V) - F(u) with every term
 // expanded as a difference (a = u, b = eps V, a' = a + b), e.g.
 //   a'_j phi' - a_j phi = a_j b_phi + b_j phi',
@@ -368,28 +468,40 @@ stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
 // so the float32 result carries float32 relative accuracy on the difference
 // itself instead of on F.  Same quantity as the forward difference of Eq. fd.
 // ============================================================================
-template <typename T, int SMAG, int TX, int TZ>
+//
+// Persistent and pipelined (NBUF = 2): a CTA walks the tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; the cp.async copies of tile t + gridDim.x go
+// into the second staging buffer while tile t is computed, so the staging
+// latency hides behind the derivative and flux stages.  NBUF = 1 stages each
+// tile before computing it (one tile per CTA, the float64 path).
+template <typename T, int SMAG, int TX, int TZ, int NBUF>
 __global__ void __launch_bounds__(NTHREADS)
 jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict__ out,
-          Ctl* ctl, int check_done) {
+          const double* part, Ctl* ctl, int check_done) {
     constexpr int SX = TX + 2 * HALO, SZ = TZ + 2 * HALO;
     constexpr int QX = TX + 2 * R, QZ = TZ + 2 * R;
     constexpr int QN = QX * QZ;
+    constexpr int STG = 8 * SZ * SX;
     pdl_wait();
     if (check_done && ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sa = reinterpret_cast<T*>(smem_raw);
-    T* sb = sa + 4 * SZ * SX;
-    T* da = sb + 4 * SZ * SX;
+    T* stg = reinterpret_cast<T*>(smem_raw);
+    T* da = stg + NBUF * STG;
     T* db = da + 6 * QN;
     T* Ka = db + 6 * QN;
     T* dK = Ka + QN;
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+    const int ntx = (G.nx + TX - 1) / TX;
+    const int ntiles = ntx * ((G.nz + TZ - 1) / TZ);
     const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
+    int t = blockIdx.x;
+    if (t < ntiles) jv_stage_issue(stg, u, v, G, (t % ntx) * TX, (t / ntx) * TZ, SX, SZ);
+    cpa_commit();
+    // the step, while the first tile's copies are in flight
+    const double eps = pending_eps(ctl, part);
     __shared__ T cfs[4];                 // 1 / (eps scale_f), computed once per block
     __shared__ T evs[4];                 // eps scale_f
     if (threadIdx.x < 4) {
-        const double e = ctl->eps_jv * G.scale[threadIdx.x];
+        const double e = eps * G.scale[threadIdx.x];
         evs[threadIdx.x] = T(e);
         cfs[threadIdx.x] = T(e != 0.0 ? 1.0 / e : 0.0);
     }
@@ -397,7 +509,11 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
     T ev[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) ev[q] = evs[q];
-    // the direction at this thread's outputs, fetched before the tile staging
+    for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+    const int x0 = (t % ntx) * TX, z0 = (t / ntx) * TZ;
+    T* sa = stg + (NBUF == 2 ? (it & 1) * STG : 0);
+    T* sb = sa + 4 * SZ * SX;
+    // the direction at this thread's outputs (consumed at the end of the tile)
     constexpr int NOUT = (TX * TZ + NTHREADS - 1) / NTHREADS;
     T vout[NOUT][4];
 #pragma unroll
@@ -410,8 +526,16 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
         for (int fl = 0; fl < 4; ++fl)
             vout[q][fl] = ok ? v[(size_t)fl * G.npt + (size_t)gz * G.nx + gx] : T(0);
     }
-    load_fields<T, 0>(sa, u, v, ev, G, x0, z0, SX, SZ);
-    load_fields<T, 2>(sb, u, v, ev, G, x0, z0, SX, SZ);
+    if (NBUF == 2) {
+        const int tn = t + gridDim.x;
+        if (tn < ntiles)
+            jv_stage_issue(stg + ((it + 1) & 1) * STG, u, v, G, (tn % ntx) * TX, (tn / ntx) * TZ, SX, SZ);
+        cpa_commit();
+        cpa_wait<1>();
+    } else {
+        cpa_wait<0>();
+    }
+    jv_stage_fix(sa, ev, G, x0, z0, SX, SZ);
     __syncthreads();
     first_derivs(sa, da, SX, SZ, QX, QZ, idx_, idz_);
     first_derivs(sb, db, SX, SZ, QX, QZ, idx_, idz_);
@@ -528,6 +652,13 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
             // and the 2 v/dt term need no wider type than the result
             out[o] = T(G.two_over_dt) * vout[qo][fl] - dF[fl] * cfs[fl];
         }
+    }
+    __syncthreads();     // staging buffer and derivative arrays are reused by the next tile
+    if (NBUF == 1) {
+        const int tn = t + gridDim.x;
+        if (tn < ntiles) jv_stage_issue(stg, u, v, G, (tn % ntx) * TX, (tn / ntx) * TZ, SX, SZ);
+        cpa_commit();
+    }
     }
 }
 
@@ -750,13 +881,22 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
     if (LAST) {
         const int nblk = gridDim.x * gridDim.y * gridDim.z;
         const int blk = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-        block_partials<1, T>(acc, 1, part, nblk, blk);
-        if (arrive_last(&ctl->counter[CNT_PC], nblk)) {
-            __shared__ double tot[1];
-            final_sums(part, nblk, 1, tot);
-            if (threadIdx.x == 0) {
-                const double zn = sqrt(tot[0]);
-                ctl->eps_jv = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+        if constexpr (sizeof(T) == sizeof(float)) {
+            // ||z||^2 stays pending, one float-float partial per block: the
+            // Jacobian product that follows adds them (pending_eps), so this
+            // launch ends without an arrival count and a serial tail
+            block_partial_ff(acc[0], reinterpret_cast<float2*>(part), blk);
+            if (blk == 0 && threadIdx.x == 0) ctl->eps_part = nblk;
+        } else {
+            block_partials<1, T>(acc, 1, part, nblk, blk);
+            if (arrive_last(&ctl->counter[CNT_PC], nblk)) {
+                __shared__ double tot[1];
+                final_sums(part, nblk, 1, tot);
+                if (threadIdx.x == 0) {
+                    const double zn = sqrt(tot[0]);
+                    ctl->eps_jv = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+                    ctl->eps_part = 0;
+                }
             }
         }
     }
@@ -784,6 +924,7 @@ pc_diag(Geo G, const T* __restrict__ r, T* __restrict__ z, size_t n, double* par
         if (threadIdx.x == 0) {
             const double zn = sqrt(tot[0]);
             ctl->eps_jv = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+            ctl->eps_part = 0;
         }
     }
 }
@@ -1051,6 +1192,7 @@ schur_back2d(Geo G, const T* __restrict__ r, T* __restrict__ z, double* part, Ct
         if (threadIdx.x == 0) {
             const double zn = sqrt(tot[0]);
             ctl->eps_jv = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+            ctl->eps_part = 0;
         }
     }
 }
@@ -1118,9 +1260,9 @@ static size_t stencil_smem() {
     return sizeof(T) * (4 * (TZ + 2 * HALO) * (TX + 2 * HALO) + 7 * (TX + 2 * R) * (TZ + 2 * R));
 }
 
-template <typename T, int TX, int TZ>
+template <typename T, int TX, int TZ, int NBUF>
 static size_t jvd_smem() {
-    return sizeof(T) * (8 * (TZ + 2 * HALO) * (TX + 2 * HALO) + 14 * (TX + 2 * R) * (TZ + 2 * R));
+    return sizeof(T) * (NBUF * 8 * (TZ + 2 * HALO) * (TX + 2 * HALO) + 14 * (TX + 2 * R) * (TZ + 2 * R));
 }
 
 template <typename K>
@@ -1168,40 +1310,50 @@ template cudaError_t launch_stencil<float>(int, const Geo&, const float*, const 
 template cudaError_t launch_stencil<double>(int, const Geo&, const double*, const double*, const double*,
                                             const double*, double*, double*, double*, Ctl*, int, cudaStream_t);
 
+// float32: persistent, double-buffered (one CTA per resident slot, capped at
+// the tile count); float64: one tile per CTA.
 template <typename T, int SMAG, int TX, int TZ>
-static cudaError_t launch_jvd_t(const Geo& G, const T* u, const T* v, T* out, Ctl* ctl,
+static cudaError_t launch_jvd_t(const Geo& G, const T* u, const T* v, T* out, const double* part, Ctl* ctl,
                                 int check_done, cudaStream_t s) {
-    static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
-    const size_t sm = jvd_smem<T, TX, TZ>();
-    if (!configured) {
-        cudaError_t e = set_smem(jv_diff2d<T, SMAG, TX, TZ>, sm);
+    constexpr int NBUF = sizeof(T) == sizeof(float) ? 2 : 1;
+    static std::atomic<int> slots{0};   // resident CTAs on the device; set once (races are benign)
+    const size_t sm = jvd_smem<T, TX, TZ, NBUF>();
+    if (slots.load() == 0) {
+        cudaError_t e = set_smem(jv_diff2d<T, SMAG, TX, TZ, NBUF>, sm);
         if (e != cudaSuccess) return e;
-        configured = true;
+        int dev = 0, nsm = 0, per = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jv_diff2d<T, SMAG, TX, TZ, NBUF>, NTHREADS,
+                                                               sm)) != cudaSuccess)
+            return e;
+        slots = std::max(1, nsm * per);
     }
-    dim3 grid((G.nx + TX - 1) / TX, (G.nz + TZ - 1) / TZ);
-    return launch_pdl(jv_diff2d<T, SMAG, TX, TZ>, grid, NTHREADS, sm, s, G, u, v, out, ctl, check_done);
+    const int ntiles = ((G.nx + TX - 1) / TX) * ((G.nz + TZ - 1) / TZ);
+    const int grid = NBUF == 2 ? std::min(ntiles, slots.load()) : ntiles;
+    return launch_pdl(jv_diff2d<T, SMAG, TX, TZ, NBUF>, dim3(grid), NTHREADS, sm, s, G, u, v, out,
+                      (const double*)part, ctl, check_done);
 }
 
 template <typename T, int SMAG>
-static cudaError_t launch_jvd_tile(const Geo& G, const T* u, const T* v, T* out, Ctl* ctl,
+static cudaError_t launch_jvd_tile(const Geo& G, const T* u, const T* v, T* out, const double* part, Ctl* ctl,
                                    int check_done, cudaStream_t s) {
     if (sizeof(T) == sizeof(double))
-        return launch_jvd_t<T, SMAG, JvTile<1>::TX, JvTile<1>::TZ>(G, u, v, out, ctl, check_done, s);
+        return launch_jvd_t<T, SMAG, JvTile<1>::TX, JvTile<1>::TZ>(G, u, v, out, part, ctl, check_done, s);
     switch (G.tile_jv) {
-        case 1: return launch_jvd_t<T, SMAG, JvTile<1>::TX, JvTile<1>::TZ>(G, u, v, out, ctl, check_done, s);
-        case 2: return launch_jvd_t<T, SMAG, JvTile<2>::TX, JvTile<2>::TZ>(G, u, v, out, ctl, check_done, s);
-        case 3: return launch_jvd_t<T, SMAG, JvTile<3>::TX, JvTile<3>::TZ>(G, u, v, out, ctl, check_done, s);
-        default: return launch_jvd_t<T, SMAG, JvTile<0>::TX, JvTile<0>::TZ>(G, u, v, out, ctl, check_done, s);
+        case 1: return launch_jvd_t<T, SMAG, JvTile<1>::TX, JvTile<1>::TZ>(G, u, v, out, part, ctl, check_done, s);
+        case 2: return launch_jvd_t<T, SMAG, JvTile<2>::TX, JvTile<2>::TZ>(G, u, v, out, part, ctl, check_done, s);
+        case 3: return launch_jvd_t<T, SMAG, JvTile<3>::TX, JvTile<3>::TZ>(G, u, v, out, part, ctl, check_done, s);
+        default: return launch_jvd_t<T, SMAG, JvTile<0>::TX, JvTile<0>::TZ>(G, u, v, out, part, ctl, check_done, s);
     }
 }
 
 template <typename T>
 cudaError_t launch_jv_diff(const Geo& G, const T* u, const T* v, T* out, double* part, Ctl* ctl,
                            int check_done, cudaStream_t s) {
-    (void)part;
     if (G.dim == 3) return launch_jv_diff3d<T>(G, u, v, out, ctl, check_done, s);
-    return G.smag ? launch_jvd_tile<T, 1>(G, u, v, out, ctl, check_done, s)
-                  : launch_jvd_tile<T, 0>(G, u, v, out, ctl, check_done, s);
+    return G.smag ? launch_jvd_tile<T, 1>(G, u, v, out, part, ctl, check_done, s)
+                  : launch_jvd_tile<T, 0>(G, u, v, out, part, ctl, check_done, s);
 }
 template cudaError_t launch_jv_diff<float>(const Geo&, const float*, const float*, float*, double*, Ctl*, int, cudaStream_t);
 template cudaError_t launch_jv_diff<double>(const Geo&, const double*, const double*, double*, double*, Ctl*, int, cudaStream_t);

@@ -632,6 +632,7 @@ cheb3d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
             if (threadIdx.x == 0) {
                 const double zn = sqrt(tot[0]);
                 ctl->eps_jv = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+                ctl->eps_part = 0;
             }
         }
     }
@@ -839,6 +840,7 @@ schur_back3d(Geo G, const T* __restrict__ r, T* __restrict__ z, double* part, Ct
         if (threadIdx.x == 0) {
             const double zn = sqrt(tot[0]);
             ctl->eps_jv = zn > 0.0 ? sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2))) / zn : 0.0;
+            ctl->eps_part = 0;
         }
     }
 }
