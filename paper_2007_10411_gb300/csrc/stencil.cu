@@ -175,13 +175,31 @@ __device__ __forceinline__ void load_fields(T* s, const T* __restrict__ u, const
     }
 }
 
+// Work item w of a QZ x QX halo region -> (qz, qx): the first 32 * (QX / 32)
+// columns of every row in 32-wide blocks (a warp stays inside one row, so its
+// shared-memory taps are consecutive words and free of bank conflicts), then
+// the remaining QX % 32 columns of all rows.
+__device__ __forceinline__ void halo_item(int w, int QX, int QZ, int& qz, int& qx) {
+    const int wide = QX & ~31, main = QZ * wide;
+    if (w < main) {
+        qz = w / wide;
+        qx = w - qz * wide;
+    } else {
+        const int rem = QX - wide, r = w - main;
+        qz = r / rem;
+        qx = wide + (r - qz * rem);
+    }
+}
+
 // Stage 2: first derivatives of u, w, theta on the halo-r region.
 template <typename T>
 __device__ __forceinline__ void first_derivs(const T* s1, T* d, int SX, int SZ, int QX, int QZ,
                                              T idx_, T idz_) {
     const int total = QX * QZ;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int qz = idx / QX, qx = idx - qz * QX;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        int qz, qx;
+        halo_item(w, QX, QZ, qz, qx);
+        const int idx = qz * QX + qx;
         const int i1 = (qz + R) * SX + qx + R;
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
@@ -249,8 +267,10 @@ stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
     __syncthreads();
     if (SMAG) {
         const T cs2 = T(G.cs2);
-        for (int idx = threadIdx.x; idx < QN; idx += blockDim.x) {
-            const int qz = idx / QX, qx = idx - qz * QX;
+        for (int w = threadIdx.x; w < QN; w += blockDim.x) {
+            int qz, qx;
+            halo_item(w, QX, QZ, qz, qx);
+            const int idx = qz * QX + qx;
             const int iq = eddy_row(qz, z0, G.nz, QZ);
             T val = T(0);
             if (iq >= 0) {
@@ -542,8 +562,10 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
     __syncthreads();
     if (SMAG) {
         const T cs2 = T(G.cs2);
-        for (int idx = threadIdx.x; idx < QN; idx += blockDim.x) {
-            const int qz = idx / QX, qx = idx - qz * QX;
+        for (int w = threadIdx.x; w < QN; w += blockDim.x) {
+            int qz, qx;
+            halo_item(w, QX, QZ, qz, qx);
+            const int idx = qz * QX + qx;
             const int iq = eddy_row(qz, z0, G.nz, QZ);
             T ka = T(0), dk = T(0);
             if (iq >= 0) {
