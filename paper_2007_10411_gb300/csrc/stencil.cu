@@ -787,7 +787,7 @@ __global__ void pc_setup(Geo G, int sweeps, Ctl* ctl) {
 // formed only on the tile rows (x-halo r), D_z z only on the tile columns
 // (z-halo r): exactly the taps the second application of D reads.
 template <typename T, int SMAG, int FIRST, int LAST, int TX, int TZ>
-__global__ void __launch_bounds__(NTHREADS)
+__global__ void __launch_bounds__(NTHREADS, 8)
 cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T* __restrict__ din,
        T* __restrict__ zout, T* __restrict__ dout, const T* __restrict__ nu, double* part, Ctl* ctl,
        int check_done) {
