@@ -65,13 +65,11 @@ struct Ctl {
     double unorm2;       // ||W u||^2 of the same state
     double eps_mach;     // unit roundoff of the stencil precision
     double eps_jv;       // finite-difference step of the next Jacobian-vector product
-    double inv_hn;       // 1 / h_{j+1,j} for pass C
     double kmax;         // max eddy coefficient K_M (preconditioner bounds)
     double gstart;       // ||r|| at the start of the current GMRES cycle
     double gres;         // rotated residual |g_{j+1}| after the latest Arnoldi step
     double scratch[8];   // misc reductions (||x||^2, ||r||^2, ...)
-    double h1[KMAX + 1];
-    double h2[KMAX + 1];      // second-projection coefficients (pass C)
+    double h1[KMAX + 1];      // first-projection coefficients (pass B block 0, for the Hessenberg column)
     double Hbar[KMAX + 1][KMAX];     // Hessenberg as built (row, col)
     double Rt[KMAX][KMAX];           // rotated upper-triangular factor
     double cs[KMAX], sn[KMAX];
@@ -108,7 +106,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
-enum CounterSlot { CNT_STENCIL = 0, CNT_PASSA, CNT_PASSB, CNT_UPDATE, CNT_RESTART, CNT_PC, CNT_EDDY, CNT_MISC };
+enum CounterSlot { CNT_STENCIL = 0, CNT_UPDATE, CNT_RESTART, CNT_PC, CNT_EDDY, CNT_MISC };
 
 // ---------------------------------------------------------------- reductions
 // Sum NV thread-local values over the block and store them, as float64, at

@@ -250,7 +250,6 @@ __device__ void givens_update(Ctl* c, int j, int m, const double* h2, double wn2
             csv[k] = c->cs[k];
             snv[k] = c->sn[k];
         }
-        c->h2[k] = h2[k];
         c->Hbar[k][j] = hk;
     }
     __syncthreads();
@@ -285,7 +284,6 @@ __device__ void givens_update(Ctl* c, int j, int m, const double* h2, double wn2
         c->g[j] = gv[j];
         c->gres = fabs(gn);
         c->iters += 1;
-        c->inv_hn = hn > 0.0 ? 1.0 / hn : 0.0;
         const bool finite = isfinite(hn2) && isfinite(gn) && isfinite(rjj);
         const bool conv = fabs(gn) <= target;
         const bool brk = hn == 0.0;
