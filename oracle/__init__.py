@@ -21,7 +21,10 @@ statement of the method, with no blocking, fusion or reordering:
                  follows) and the energy budgets (Section 3.1.3).
 * ``krylov``     restarted right-preconditioned GMRES(m) with classical
                  Gram-Schmidt applied twice and Givens rotations (Section 2.5.1).
-* ``newton``     the inexact Newton outer loop of one implicit step (Section 2.5.1).
+* ``newton``     the inexact Newton outer loop of one implicit step (Section 2.5.1),
+                 with the field block or the acoustic Schur complement on the
+                 right, or the nonlinear preconditioning of Section 2.5.2
+                 (Newton on M^{-1} W R, GMRES on M^{-1} J_hat).
 
 Parity status: every function is pinned by the tests in ``tests/test_oracle_*.py``
 (closed forms, invariants, brute force); none is "parity unpinned" except the

@@ -282,6 +282,25 @@ class Model:
             Z[f] = chebyshev(lambda x: self.block_operator(K, x, f), Rhat[f], lo, hi, sweeps)
         return Z
 
+    def block_apply(self, U_frozen: np.ndarray, Xhat: np.ndarray) -> np.ndarray:
+        """P x: the field-block operator whose blocks ``precond`` inverts (scaled units)."""
+        K_M, K_H = self.frozen_eddy(U_frozen)
+        return np.stack([self.block_operator(K_H if f == self.ith else K_M, Xhat[f], f) for f in range(self.nf)])
+
+    # ------------------------------------------------- nonlinear preconditioning
+    def nonlinear_pc_residual(self, U: np.ndarray, f: np.ndarray, sweeps: int) -> np.ndarray:
+        """The preconditioned nonlinear residual of Section 2.5.2 in scaled units,
+        R~(u) = u - P^{-1}(u) [f - L(u) + P(u) u], with P the field-block operator
+        frozen at u and P^{-1} applied by ``precond`` (R = L(u) - f)."""
+        Uh = self.scale(U)
+        Rh = self.scale(self.residual(U, f))
+        return Uh - self.precond(U, self.block_apply(U, Uh) - Rh, sweeps)
+
+    def left_pc_residual(self, U: np.ndarray, f: np.ndarray, sweeps: int) -> np.ndarray:
+        """M^{-1} W R(u): the same quantity for an exact P^{-1}; with the Chebyshev
+        approximation M^{-1} it keeps the root of R (R~ above does not)."""
+        return self.precond(U, self.scale(self.residual(U, f)), sweeps)
+
     # ------------------------------------------------- acoustic Schur complement
     def _d_interior(self, a: np.ndarray, parity, j: int) -> np.ndarray:
         """D_j a on the interior of a field with the given mirror parity."""
