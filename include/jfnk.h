@@ -62,7 +62,7 @@ typedef enum {
 enum { JFNK_FREESLIP = 0, JFNK_NOSLIP = 1 };
 enum { JFNK_SGS_CONST = 0, JFNK_SGS_SMAGORINSKY = 1 };
 enum { JFNK_FP64 = 0, JFNK_MIXED = 1 };
-enum { JFNK_PC_NONE = 0, JFNK_PC_BLOCK = 1, JFNK_PC_UNET = 2, JFNK_PC_SCHUR = 3 };
+enum { JFNK_PC_NONE = 0, JFNK_PC_BLOCK = 1, JFNK_PC_UNET = 2, JFNK_PC_SCHUR = 3, JFNK_PC_NONLINEAR = 4 };
 
 /* Largest Krylov dimension m accepted by jfnk_create. */
 #define JFNK_MAX_KRYLOV 32
@@ -118,7 +118,16 @@ typedef struct {
  *             pc_sweeps Chebyshev steps on its Gershgorin interval, the
  *             velocities are back-substituted, theta gets r_theta / theta_c
  *             of its field block; advection, diffusion and buoyancy are
- *             dropped).
+ *             dropped) or
+ *             JFNK_PC_NONLINEAR (the nonlinear preconditioning of Section
+ *             2.5.2 with P the field-block operator frozen at the Newton
+ *             iterate: Newton on the preconditioned residual M^{-1} W R, i.e.
+ *             GMRES on M^{-1} J applied from the left, M^{-1} the same
+ *             pc_sweeps-step Chebyshev field-block inverse as JFNK_PC_BLOCK.
+ *             The paper's form u - P^{-1}[f - L(u) + P u] equals P^{-1} R for
+ *             an exact inverse; M^{-1} R keeps the root of R for the
+ *             approximate one.  The Newton test stays on ||W R||; GMRES
+ *             stops at ||M^{-1} W(R + J du)|| <= eta ||M^{-1} W R||).
  * newton_rtol, newton_atol_factor, eta, max_newton, max_restarts: stopping rules
  *             ||W R|| <= max(rtol ||W R_0||, atol_factor ||W 2u^n/dt||);
  *             GMRES stops at ||W(R + J du)|| <= eta ||W R||.
@@ -358,8 +367,8 @@ jfnk_status jfnk_unet_forward(jfnk_handle* h, const float* x, float* y);
 jfnk_status jfnk_unet_loss_grad(jfnk_handle* h, const float* x, const float* t, double* loss,
                                 float* grads);
 
-/* Change the preconditioner between steps: JFNK_PC_NONE, JFNK_PC_BLOCK or
- * JFNK_PC_UNET (the latter only where the calls above are supported). */
+/* Change the preconditioner between steps: any JFNK_PC_* value accepted by
+ * jfnk_create (JFNK_PC_UNET only where the calls above are supported). */
 jfnk_status jfnk_set_precond(jfnk_handle* h, int precond);
 
 /* Number of tile shapes jfnk_set_tiles accepts per kernel family. */

@@ -101,7 +101,7 @@ static jfnk_status validate(const jfnk_grid* g, const jfnk_strat* s, const jfnk_
     if (o->precision != JFNK_FP64 && o->precision != JFNK_MIXED) return JFNK_ERR_INVALID_ARG;
     if (o->krylov_m < 1 || o->krylov_m > JFNK_MAX_KRYLOV) return JFNK_ERR_INVALID_ARG;
     if (o->precond != JFNK_PC_NONE && o->precond != JFNK_PC_BLOCK && o->precond != JFNK_PC_UNET &&
-        o->precond != JFNK_PC_SCHUR)
+        o->precond != JFNK_PC_SCHUR && o->precond != JFNK_PC_NONLINEAR)
         return JFNK_ERR_INVALID_ARG;
     if (o->pc_sweeps < 1 || o->pc_sweeps > MAX_PC_SWEEPS) return JFNK_ERR_INVALID_ARG;
     if (!finite_pos(o->newton_rtol) || !(o->newton_atol_factor >= 0.0) ||
@@ -656,18 +656,35 @@ static jfnk_status apply_jv(jfnk_handle* h, const T* uT, const T* z, T* w, int c
 }
 
 // Restarted GMRES(m) on J_hat x = -W R from x = 0 (cycle_init already enqueued).
+// Nonlinear preconditioning (left): v_0 <- M^{-1} v_0 / ||M^{-1} v_0|| and the
+// cycle's g_0, after cycle_init (first) or restart_residual left r in v_0.
+template <typename T>
+static jfnk_status left_cycle_start(jfnk_handle* h, int first) {
+    cudaStream_t s = h->stream;
+    const Geo& G = h->G;
+    T* V0 = (T*)h->V;
+    T* z = (T*)h->tA;
+    CK(launch_precond<T>(G, h->opts.pc_sweeps, V0, z, (T*)h->za, (T*)h->zb, (T*)h->da, (T*)h->db,
+                         (const T*)h->nu, h->part, h->ctl, 0, s, &h->launches));
+    CK(launch_norm2<T>(G, z, h->n, 0, 1, h->part, h->ctl, s));
+    CK(launch_left_scale<T>(z, V0, h->n, first, h->ctl, s));
+    h->launches += 2;
+    return JFNK_OK;
+}
+
 template <typename T>
 static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* restarts, int* conv, int* switched) {
     cudaStream_t s = h->stream;
     const Geo& G = h->G;
     const size_t n = h->n, ld = h->ld;
     const int m = h->m;
-    const bool pc = h->opts.precond != JFNK_PC_NONE;
+    const bool left = h->opts.precond == JFNK_PC_NONLINEAR;      // M^{-1} J from the left
+    const bool pc = h->opts.precond != JFNK_PC_NONE && !left;     // right preconditioner (stored z_j)
     bool learned = h->opts.precond == JFNK_PC_UNET && h->net != nullptr;
     // A Schur-preconditioned step is long enough (tens of launches) for the host
     // to stay ahead with a lag of one, which halves the steps enqueued past a finish.
     const int lag = h->G.pc_schur ? 1 : LAG;
-    const bool arnoldi_pairs = sizeof(T) == sizeof(float) && capturing(h, JFNK_PAIRS_ARNOLDI);
+    const bool arnoldi_pairs = !left && sizeof(T) == sizeof(float) && capturing(h, JFNK_PAIRS_ARNOLDI);
     T* V = (T*)h->V;
     T* Z = pc ? (T*)h->Z : V;
     T* w = (T*)h->w;
@@ -696,6 +713,16 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
             }
             jfnk_status st = apply_jv<T>(h, uT, zj, w, 1);
             if (st != JFNK_OK) return st;
+            T* wa = w;                      // the vector the Arnoldi step orthogonalises
+            if (left) {                     // w <- M^{-1} J v_j
+                kt_begin(h, JFNK_KF_PRECOND);
+                CK(launch_precond<T>(G, h->opts.pc_sweeps, w, (T*)h->tB, (T*)h->za, (T*)h->zb, (T*)h->da,
+                                     (T*)h->db, (const T*)h->nu, h->part, h->ctl, 1, s, &h->launches));
+                kt_end(h, JFNK_KF_PRECOND, pc_bytes(h));
+                CK(launch_unit_eps(h->ctl, s));      // the next product acts on the unit vector v_{j+1}
+                h->launches += 1;
+                wa = (T*)h->tB;
+            }
             if constexpr (sizeof(T) == sizeof(float)) {
                 if (arnoldi_pairs) {   // (J z_j, z_j) is an exact inverse pair
                     CK(launch_pair_arnoldi(w, (float*)h->tA, n, h->part, h->ctl, s));
@@ -709,13 +736,13 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
             }
             const double vb = (double)n * sizeof(T);
             kt_begin(h, JFNK_KF_ARNOLDI_A);
-            CK(launch_arnoldi_a<T>(V, ld, w, n, j + 1, h->part, h->ctl, s));
+            CK(launch_arnoldi_a<T>(V, ld, wa, n, j + 1, h->part, h->ctl, s));
             kt_end(h, JFNK_KF_ARNOLDI_A, (j + 2) * vb);
             kt_begin(h, JFNK_KF_ARNOLDI_B);
-            CK(launch_arnoldi_b<T>(V, ld, w, n, j + 1, h->part, h->partB, h->ctl, s));
+            CK(launch_arnoldi_b<T>(V, ld, wa, n, j + 1, h->part, h->partB, h->ctl, s));
             kt_end(h, JFNK_KF_ARNOLDI_B, (j + 3) * vb);   // reads v_0..v_j, w; writes w'
             kt_begin(h, JFNK_KF_ARNOLDI_C);
-            CK(launch_arnoldi_c<T>(V, ld, w, n, j + 1, m, h->partB, h->ctl, s));
+            CK(launch_arnoldi_c<T>(V, ld, wa, n, j + 1, m, h->partB, h->ctl, s));
             kt_end(h, JFNK_KF_ARNOLDI_C, (j + 3) * vb);
             h->launches += 3;
             CK(cudaMemcpyAsync(&h->hdone[j], &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -746,7 +773,14 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
         *restarts = cycle + 1;
         st = apply_jv<T>(h, uT, xT, w, 0);
         if (st != JFNK_OK) return st;
-        CK(launch_restart<T>(G, h->R, w, V, n, pc ? 0 : 1, h->part, h->ctl, s, &h->launches));
+        if (left) {
+            CK(launch_restart_residual<T>(G, h->R, w, V, n, h->part, h->ctl, s));
+            h->launches += 1;
+            st = left_cycle_start<T>(h, 0);
+            if (st != JFNK_OK) return st;
+        } else {
+            CK(launch_restart<T>(G, h->R, w, V, n, pc ? 0 : 1, h->part, h->ctl, s, &h->launches));
+        }
     }
 }
 
@@ -808,9 +842,14 @@ static jfnk_status step_impl(jfnk_handle* h, double* u, jfnk_stats* out) {
             CK(launch_pc_setup(G, h->opts.pc_sweeps, h->ctl, s));
             h->launches += 1;
         }
+        const bool left = h->opts.precond == JFNK_PC_NONLINEAR;
         CK(launch_cycle_init<T>(G, h->R, (T*)h->V, h->x, n, h->opts.eta, h->m,
-                                h->opts.precond == JFNK_PC_NONE, h->ctl, s));
+                                h->opts.precond == JFNK_PC_NONE || left, h->ctl, s));
         h->launches += 1;
+        if (left) {
+            st = left_cycle_start<T>(h, 1);
+            if (st != JFNK_OK) return st;
+        }
         int it = 0, rs = 0, cv = 0, sw = 0;
         st = gmres_solve<T>(h, uT, &it, &rs, &cv, &sw);
         if (st != JFNK_OK) return st;
@@ -995,7 +1034,7 @@ extern "C" jfnk_status jfnk_unet_loss_grad(jfnk_handle* h, const float* x, const
 extern "C" jfnk_status jfnk_set_precond(jfnk_handle* h, int precond) {
     if (!h) return JFNK_ERR_INVALID_ARG;
     if (precond != JFNK_PC_NONE && precond != JFNK_PC_BLOCK && precond != JFNK_PC_UNET &&
-        precond != JFNK_PC_SCHUR)
+        precond != JFNK_PC_SCHUR && precond != JFNK_PC_NONLINEAR)
         return JFNK_ERR_INVALID_ARG;
     if (precond == JFNK_PC_UNET && !unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
     if (precond == JFNK_PC_SCHUR && h->opts.pc_sweeps < 2) return JFNK_ERR_UNSUPPORTED;

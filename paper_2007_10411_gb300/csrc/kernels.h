@@ -72,6 +72,15 @@ cudaError_t launch_arnoldi_c(T* V, size_t ldv, const T* w, size_t n, int nv, int
 template <typename T>
 cudaError_t launch_update(const T* Z, size_t ldz, double* x, T* xT, size_t n, double* part,
                           Ctl* ctl, cudaStream_t s);
+// Left preconditioning: r = b - w unnormalised into V0 (||r||^2 in scratch[1]);
+// v_0 = z / ||z|| with ||z||^2 in scratch[1] and the cycle's g_0 (first: the
+// Newton solve's preconditioned ||b||); the unit-vector finite-difference step.
+template <typename T>
+cudaError_t launch_restart_residual(const Geo& G, const double* R, const T* w, T* V0, size_t n, double* part,
+                                    Ctl* ctl, cudaStream_t s);
+template <typename T>
+cudaError_t launch_left_scale(const T* z, T* V0, size_t n, int first, Ctl* ctl, cudaStream_t s);
+cudaError_t launch_unit_eps(Ctl* ctl, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cycle_init(const Geo& G, const double* R, T* V0, double* x, size_t n, double eta,
                               int m, int pc_none, Ctl* ctl, cudaStream_t s);

@@ -659,6 +659,47 @@ restart_scale(T* __restrict__ V0, size_t n, int pc_none, Ctl* ctl) {
     }
 }
 
+// Left preconditioning (nonlinear preconditioning): the cycle starts from
+// z = M^{-1} r with ||z||^2 in scratch[1].  v_0 = z / ||z||; on the first cycle
+// of a Newton solve (r = b / ||b|| from cycle_init) the preconditioned right-
+// hand side has norm beta0 ||z||, which rescales beta0 and the target; on a
+// restart (r = b - J x unnormalised) g_0 = ||z||.  The Jacobian products of
+// the cycle act on unit vectors: eps from ||u|| alone.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+left_scale(const T* __restrict__ z, T* __restrict__ V0, size_t n, int first, Ctl* ctl) {
+    const double zn = sqrt(ctl->scratch[1]);
+    const T inv = T(zn > 0.0 ? 1.0 / zn : 0.0);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) V0[i] = z[i] * inv;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double g0 = zn;
+        if (first) {
+            g0 = ctl->beta0 * zn;
+            ctl->beta0 = g0;
+            ctl->target *= zn;
+            ctl->converged = g0 == 0.0;
+        } else {
+            ctl->converged = 0;
+        }
+        ctl->g[0] = g0;
+        ctl->gstart = g0;
+        ctl->gres = g0;
+        ctl->done = 0;
+        ctl->breakdown = 0;
+        ctl->k = 0;
+        ctl->eps_jv = sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2)));
+        ctl->eps_part = 0;
+    }
+}
+
+// The finite-difference step of a Jacobian product on a unit vector (left
+// preconditioning: restores it after a preconditioner apply left its own).
+__global__ void unit_eps_k(Ctl* ctl) {
+    ctl->eps_jv = sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2)));
+    ctl->eps_part = 0;
+}
+
 // u += W^{-1} x (float64), uT = u rounded to T.
 template <typename T>
 __global__ void __launch_bounds__(NTHREADS)
@@ -869,6 +910,24 @@ cudaError_t launch_restart(const Geo& G, const double* R, const T* w, T* V0, siz
 }
 
 template <typename T>
+cudaError_t launch_restart_residual(const Geo& G, const double* R, const T* w, T* V0, size_t n, double* part,
+                                    Ctl* ctl, cudaStream_t s) {
+    restart_residual<T><<<stream_blocks(n), NTHREADS, 0, s>>>(G, R, w, V0, n, part, ctl);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_left_scale(const T* z, T* V0, size_t n, int first, Ctl* ctl, cudaStream_t s) {
+    left_scale<T><<<stream_blocks(n), NTHREADS, 0, s>>>(z, V0, n, first, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unit_eps(Ctl* ctl, cudaStream_t s) {
+    unit_eps_k<<<1, 1, 0, s>>>(ctl);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_newton_update(const Geo& G, double* u, const double* x, T* uT, size_t n,
                                  cudaStream_t s) {
     newton_update<T><<<stream_blocks(n), NTHREADS, 0, s>>>(G, u, x, uT, n);
@@ -943,6 +1002,9 @@ cudaError_t launch_pc_eps(const float* z, size_t n, double* part, Ctl* ctl, cuda
                                            double*, Ctl*, cudaStream_t, long long*);                  \
     template cudaError_t launch_newton_update<T>(const Geo&, double*, const double*, T*, size_t,      \
                                                  cudaStream_t);                                        \
+    template cudaError_t launch_restart_residual<T>(const Geo&, const double*, const T*, T*, size_t,  \
+                                                    double*, Ctl*, cudaStream_t);                      \
+    template cudaError_t launch_left_scale<T>(const T*, T*, size_t, int, Ctl*, cudaStream_t);         \
     template cudaError_t launch_norm2<T>(const Geo&, const T*, size_t, int, int, double*, Ctl*,       \
                                          cudaStream_t);
 JF_INST(float)

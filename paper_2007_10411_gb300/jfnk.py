@@ -35,7 +35,7 @@ EXPORTS = (
     "jfnk_unet_forward", "jfnk_unet_loss_grad", "jfnk_set_precond",
 )
 
-PC_NONE, PC_BLOCK, PC_UNET, PC_SCHUR = 0, 1, 2, 3
+PC_NONE, PC_BLOCK, PC_UNET, PC_SCHUR, PC_NONLINEAR = 0, 1, 2, 3, 4
 PAIRS_NEWTON, PAIRS_ARNOLDI = 1, 2
 
 KERNEL_FAMILIES = ("arnoldi_a", "arnoldi_b", "arnoldi_c", "jv", "precond", "residual", "unet")
