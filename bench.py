@@ -53,8 +53,12 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3, help="host-buffer steps through jfnk_step_host")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample (0: skip)")
     p.add_argument("--no-kernel-timing", action="store_true")
-    p.add_argument("--precond", default="block", choices=["block", "schur"],
-                   help="preconditioner of the main timed run (block: the paper's field-block one)")
+    p.add_argument("--precond", default="block", choices=["block", "schur", "nonlinear"],
+                   help="preconditioner of the main timed run (block: the paper's field-block one on the "
+                        "right; nonlinear: the same field block as the nonlinear preconditioning of "
+                        "Section 2.5.2, i.e. Newton on M^-1 R)")
+    p.add_argument("--nonlinear-steps", type=int, default=10,
+                   help="steps of the nonlinear-preconditioning leg on the same workload (0 skips it)")
     p.add_argument("--schur-sweeps", type=int, default=16,
                    help="Helmholtz sweeps of the acoustic Schur-complement leg (0 skips it)")
     p.add_argument("--unet-forward", type=int, default=0,
@@ -303,6 +307,8 @@ def run_batch(args, rank: int, world: int, local_rank: int):
     cases = synth.uhi_batch(n=n_inst)
     if args.precond == "schur":
         cases = [synth.with_options(c, precond=jfnk.PC_SCHUR, pc_sweeps=args.schur_sweeps) for c in cases]
+    elif args.precond == "nonlinear":
+        cases = [synth.with_options(c, precond=jfnk.PC_NONLINEAR) for c in cases]
     stream = torch.cuda.current_stream()
     batch = jfnk.Batch(cases, stream=stream)
     for i, c in enumerate(cases):
@@ -356,9 +362,7 @@ def run_batch(args, rank: int, world: int, local_rank: int):
                    "grids": [list(synth.shape(c)[:0:-1]) for c in cases],
                    "H0": [round(c["init"]["H0"], 2) for c in cases],
                    "precision": "mixed", "krylov_m": cases[0]["opts"]["krylov_m"],
-                   "precond": ("field-block Chebyshev (%d sweeps)" % cases[0]["opts"]["pc_sweeps"]
-                               if args.precond == "block" else
-                               "acoustic Schur complement (%d Helmholtz sweeps)" % cases[0]["opts"]["pc_sweeps"]),
+                   "precond": pc_label(args.precond, cases[0]),
                    "execution": "one handle + stream per instance, host thread per instance",
                    "parallelism": "replicas" if world > 1 else "single"},
         "newton_per_step": [statistics.mean(s["newton_iters"] for s in p) for p in per_inst],
@@ -439,6 +443,43 @@ def run_unet_forward(args):
     s.close()
 
 
+def pc_label(precond: str, case: dict) -> str:
+    sw = case["opts"]["pc_sweeps"]
+    if precond == "schur":
+        return "acoustic Schur complement (%d Helmholtz sweeps)" % sw
+    if precond == "nonlinear":
+        return "field-block Chebyshev (%d sweeps) as nonlinear preconditioner (Newton on M^-1 R)" % sw
+    return "field-block Chebyshev (%d sweeps)" % sw
+
+
+def nonlinear_leg(jfnk, synth, torch, stream, case, U0, steps: int, barrier, slowest, world: int) -> dict:
+    """The same workload with the nonlinear preconditioning of Section 2.5.2 (JFNK_PC_NONLINEAR:
+    Newton on M^-1 W R, GMRES on M^-1 J from the left, the same field-block M as the headline)."""
+    c = synth.with_options(case, precond=jfnk.PC_NONLINEAR)
+    npt = c["grid"]["nx"] * c["grid"]["nz"]
+    s = jfnk.Solver(c, stream=stream)
+    u = torch.from_numpy(U0.reshape(-1).copy()).cuda()
+    for _ in range(3):
+        s.step(u)
+    s.autotune(u)
+    barrier()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    st = [s.step(u) for _ in range(steps)]
+    a1.record(stream)
+    a1.synchronize()
+    ms = slowest(a0.elapsed_time(a1))
+    s.close()
+    return {"precond": "field block (%d Chebyshev sweeps) as nonlinear preconditioner: Newton on M^-1 W R"
+                       % c["opts"]["pc_sweeps"],
+            "value": npt * steps * world / (ms / 1e3) / 1e6, "unit": "Mpt*steps/s", "steps": steps,
+            "ms_per_step": ms / steps,
+            "gmres_iters_per_step": statistics.mean(x["gmres_iters"] for x in st),
+            "newton_per_step": statistics.mean(x["newton_iters"] for x in st),
+            "converged": all(x["converged"] for x in st)}
+
+
 def schur_leg(jfnk, synth, torch, stream, case, U0, steps: int, sweeps: int, barrier, slowest, world: int) -> dict:
     """The same workload with the acoustic Schur-complement preconditioner (JFNK_PC_SCHUR)."""
     c = synth.with_options(case, precond=jfnk.PC_SCHUR, pc_sweeps=sweeps)
@@ -514,6 +555,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     case = synth.case(args.workload)
     if args.precond == "schur":
         case = synth.with_options(case, precond=jfnk.PC_SCHUR, pc_sweeps=args.schur_sweeps)
+    elif args.precond == "nonlinear":
+        case = synth.with_options(case, precond=jfnk.PC_NONLINEAR)
     npt = synth.shape(case)[1:]
     npt = int(__import__("math").prod(npt))
     n = synth.n_fields(case) * npt
@@ -595,6 +638,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "newton_per_step": statistics.mean(s["newton_iters"] for s in st64)}
         s64.close()
 
+    nonlinear = None
+    if args.nonlinear_steps > 0 and args.precond == "block":
+        nonlinear = nonlinear_leg(jfnk, synth, torch, stream, case, U0, args.nonlinear_steps, barrier, slowest,
+                                  world)
+
     schur = None
     if args.schur_sweeps > 1 and case["grid"]["dim"] == 2 and args.precond == "block":
         schur = schur_leg(jfnk, synth, torch, stream, case, U0, max(args.steps, 10), args.schur_sweeps,
@@ -645,9 +693,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": list(synth.shape(case)[:0:-1]),
                    "points": npt, "precision": "mixed", "krylov_m": case["opts"]["krylov_m"],
-                   "precond": ("field-block Chebyshev (%d sweeps)" % case["opts"]["pc_sweeps"]
-                               if args.precond == "block" else
-                               "acoustic Schur complement (%d Helmholtz sweeps)" % case["opts"]["pc_sweeps"]),
+                   "precond": pc_label(args.precond, case),
                    "parallelism": "replicas" if world > 1 else "single",
                    "tiles": {"jv": tiles[0], "precond": tiles[1]},
                    "l2": "working set > L2: the Krylov basis and directions (%d x %.1f MB) stream "
@@ -657,6 +703,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "kernels": kernels,
         "kernels_timing": "per-family CUDA events over 2 steps right before the timed region" if kernels else None,
         "fp64_plain": fp64, "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+        "nonlinear_pc": nonlinear,
+        "nonlinear_over_block": (nonlinear["value"] / value) if nonlinear else None,
         "schur_pc": schur,
         "schur_over_block": (schur["value"] / value) if schur else None,
         "schur_over_fp64": (schur["value"] / fp64["value"]) if (schur and fp64) else None,
