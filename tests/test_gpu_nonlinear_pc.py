@@ -137,3 +137,24 @@ def test_set_precond_accepts_nonlinear():
     u = dev(U)
     assert s.step(u)["converged"]
     s.close()
+
+
+def test_nonlinear_pc_single_sweep_and_batch():
+    """One sweep (the point-wise 1/theta_c scaling of the field blocks) on the left,
+    and a two-instance batch whose steps equal the instances' own steps."""
+    c = nl_case("tiny_64x32", synth.PREC_MIXED, sweeps=1)
+    check_step(c, 5)
+    cb = nl_case("tiny_64x32", synth.PREC_MIXED)
+    U = [synth.random_state(cb, sd, amp=(0.3, 0.1, 0.001)) for sd in (7, 8)]
+    b = jf().Batch([cb, cb])
+    us = [dev(x) for x in U]
+    sts = b.step(us)
+    assert all(x["converged"] for x in sts)
+    got = [host(x) for x in us]
+    b.close()
+    for x, g in zip(U, got):
+        s = jf().Solver(cb)
+        u = dev(x)
+        s.step(u)
+        np.testing.assert_array_equal(host(u), g)
+        s.close()
