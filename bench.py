@@ -59,7 +59,7 @@ def parse():
                         "Section 2.5.2, i.e. Newton on M^-1 R)")
     p.add_argument("--nonlinear-steps", type=int, default=10,
                    help="steps of the nonlinear-preconditioning leg on the same workload (0 skips it)")
-    p.add_argument("--schur-sweeps", type=int, default=16,
+    p.add_argument("--schur-sweeps", type=int, default=32,
                    help="Helmholtz sweeps of the acoustic Schur-complement leg (0 skips it)")
     p.add_argument("--unet-forward", type=int, default=0,
                    help="only time this many applies of the learned-preconditioner network (profiling)")

@@ -106,6 +106,7 @@ typedef struct {
  * flexible    accepted for compatibility; the library always stores the
  *             preconditioned directions (FGMRES form), identical in exact
  *             arithmetic to right-preconditioned GMRES for a linear M.
+ * pc_sweeps   Chebyshev steps of the preconditioner, 1..64.
  * precond     JFNK_PC_NONE, JFNK_PC_BLOCK (pc_sweeps Chebyshev steps per block),
  *             JFNK_PC_UNET (the block preconditioner plus a learned
  *             correction, see "Learned right preconditioner" below) or

@@ -18,7 +18,7 @@ constexpr int NTHREADS = 256;     // threads per block of every streaming kernel
 constexpr int MAX_STREAM_BLOCKS = 2 * 152;  // streaming grid: two CTAs per SM
 constexpr int MAX_DOT_BLOCKS = 3 * 152;     // Arnoldi passes A and C: three CTAs per SM
 constexpr int MAX_REDUCE_BLOCKS = 8192;     // multi-dot grids grow so a thread sums <= 64 vectors' worth
-constexpr int MAX_PC_SWEEPS = 16;
+constexpr int MAX_PC_SWEEPS = 64;
 
 // Geometry and physics constants, passed by value to the stencil kernels.
 struct Geo {
