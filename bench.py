@@ -617,7 +617,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         e2e = {"value": npt * args.e2e_steps * world / el / 1e6, "unit": "Mpt*steps/s",
                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
 
-    # plain float64 JFNK on the same workload (the spec comparison)
+    # plain float64 JFNK on the same workload (the mixed-precision comparison)
     fp64 = None
     if args.fp64_steps > 0:
         c64 = synth.with_options(case, precision=synth.PREC_FP64)
