@@ -56,7 +56,7 @@ typedef enum {
     JFNK_ERR_BREAKDOWN = 5,     /* GMRES found no descent (zero Krylov space)     */
     JFNK_ERR_NAN = 6,           /* a residual norm was not finite                 */
     JFNK_ERR_TIMEOUT = 7,       /* a bounded device loop hit its iteration cap    */
-    JFNK_ERR_UNSUPPORTED = 8    /* valid request this build does not implement    */
+    JFNK_ERR_UNSUPPORTED = 8    /* valid request the library does not implement   */
 } jfnk_status;
 
 enum { JFNK_FREESLIP = 0, JFNK_NOSLIP = 1 };
