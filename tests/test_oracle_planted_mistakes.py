@@ -105,3 +105,79 @@ def test_wrong_stratification_sign_breaks_energy_conservation():
     m.dt = 20.0
     U1 = implicit_step(m, U, c["opts"] | {"dt": 20.0})
     assert abs(energy(U1) - energy(U)) / energy(U) > 1e-4
+
+
+# ---------------------------------------------------------------- nonlinear preconditioning
+def _diffusive_pair(K=1e4):
+    import copy
+    c = synth.case("thermal_stable_64x32")
+    c["sgs"] = {"mode": synth.SGS_CONST, "K_M": K, "K_H": K, "Cs": 0.0, "Pr": 1.0}
+    m = Model(copy.deepcopy(c))
+    U = synth.random_state(c, 31, amp=(0.3, 0.1, 0.001))
+    return m, U, m.rhs_f(U - 0.01)
+
+
+def _nl_pin_error(m, U, f):
+    a = m.nonlinear_pc_residual(U, f, 16)
+    b = m.left_pc_residual(U, f, 16)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_nonlinear_pc_pin_unmutated():
+    assert _nl_pin_error(*_diffusive_pair()) < 1e-12
+
+
+def test_nonlinear_pc_pin_catches_a_wrong_block_operator():
+    m, U, f = _diffusive_pair()
+    good = m.block_operator
+    m.block_operator = lambda K, x, fld: good(K, x, fld) * (1.0 if fld != 2 else 1.01)   # theta block 1 % off
+    # precond keeps inverting the correct operator, so the planted error only
+    # shows where block_apply is used: the paper's form carries (I - M^{-1} P) u
+    m.precond = lambda Uf, R, sw: _precond_with(m, good, Uf, R, sw)
+    assert _nl_pin_error(m, U, f) > 1e-6
+
+
+def _precond_with(m, block_operator, U_frozen, Rhat, sweeps):
+    """The field-block inverse built on a given block operator (the correct one)."""
+    from oracle.operators import chebyshev
+    K_M, K_H = m.frozen_eddy(U_frozen)
+    Z = np.zeros_like(Rhat)
+    for fld in range(m.nf):
+        K = K_H if fld == m.ith else K_M
+        kmax = float(np.max(K)) if not np.isscalar(K) else float(K)
+        lo, hi = m.gershgorin_bounds(0.0 if fld == m.ip else kmax)
+        Z[fld] = chebyshev(lambda x: block_operator(K, x, fld), Rhat[fld], lo, hi, sweeps)
+    return Z
+
+
+def test_nonlinear_pc_pin_catches_a_sign_error():
+    m, U, f = _diffusive_pair()
+    good = m.left_pc_residual
+    m.left_pc_residual = lambda Uu, ff, sw: -good(Uu, ff, sw)          # b = +M^{-1} W R by mistake
+    assert _nl_pin_error(m, U, f) > 1.0
+
+
+def test_left_gmres_step_catches_a_right_hand_side_left_unpreconditioned():
+    """Newton with GMRES on M^{-1} J but an unpreconditioned right-hand side
+    converges to a wrong correction: the step no longer reaches the root in
+    the same Newton count, or the state differs from the correct left step."""
+    import copy
+    c = synth.case("thermal_stable_64x32")
+    c["sgs"] = {"mode": synth.SGS_CONST, "K_M": 1e4, "K_H": 1e4, "Cs": 0.0, "Pr": 1.0}
+    c["opts"].update(krylov_m=12, eta=1e-8, newton_rtol=1e-11, max_newton=3, precond=4, pc_sweeps=2)
+    U = synth.random_state(c, 31, amp=(0.3, 0.1, 0.001))
+    st_good = {}
+    good = implicit_step(Model(copy.deepcopy(c)), U, c["opts"], st_good)
+    m = Model(copy.deepcopy(c))
+    orig = m.precond
+    calls = {"n": 0}
+
+    def precond_skipping_rhs(Uf, R, sw):
+        # the first application of the step is the one on the first right-hand side
+        calls["n"] += 1
+        return R if calls["n"] == 1 else orig(Uf, R, sw)
+    m.precond = precond_skipping_rhs
+    st_bad = {}
+    bad = implicit_step(m, U, c["opts"], st_bad)
+    err = float(np.linalg.norm(m.scale(bad - good)) / np.linalg.norm(m.scale(good)))
+    assert (not st_bad["converged"]) or st_bad["newton_iters"] != st_good["newton_iters"] or err > 1e-9
