@@ -50,7 +50,7 @@ def _create(lib, c):
 @pytest.mark.parametrize("key,val", [
     ("nx", 0), ("nz", 2), ("lx", -1.0), ("lz", float("nan")), ("bc_bottom", 7),
     ("theta0", 0.0), ("Pr", 0.0), ("K_M", -1.0), ("mode", 5),
-    ("precision", 3), ("krylov_m", 0), ("krylov_m", 33), ("precond", 9), ("pc_sweeps", 0), ("pc_sweeps", 65),
+    ("precision", 3), ("krylov_m", 0), ("krylov_m", 33), ("precond", 5), ("precond", 9), ("pc_sweeps", 0), ("pc_sweeps", 65),
     ("newton_rtol", 0.0), ("eta", 1.0), ("max_newton", -1), ("max_newton", 33), ("dt", 0.0),
     ("scale_p", 0.0),
 ])
