@@ -218,7 +218,8 @@ jfnk_status jfnk_step(jfnk_handle* h, double* u, jfnk_stats* out);
  * steps, and copies the result back (pinned memory recommended). */
 jfnk_status jfnk_step_host(jfnk_handle* h, double* u_host, jfnk_stats* out);
 
-/* Energy budgets and extremes of the device state u (Section 3.1.3). */
+/* Energy budgets and extremes of the device state u (Section 3.1.3).
+ * Extrema propagate NaN (a NaN anywhere in a field makes its max and min NaN). */
 jfnk_status jfnk_budgets(jfnk_handle* h, const double* u, jfnk_budget* out);
 
 /* Number of this library's kernel launches enqueued since the handle was created. */
@@ -408,12 +409,18 @@ jfnk_status jfnk_set_tiles(jfnk_handle* h, int tile_jv, int tile_pc);
  * kernel block and value, plus a counter) that every GPU which loads the
  * library holds until the process exits.  No cudaMalloc, cudaFree or
  * allocating library routine is called.
- * The first call on each device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  All calls on a device share the array and it
- * keeps the last call's contents (the counter is reset by every call);
+ * The array's device address belongs to a CUDA context: the first call in
+ * each context (the primary context of a device, or any context the caller
+ * has made current) looks it up with cudaGetSymbolAddress and caches it
+ * under that context's id; make that first call before any stream capture.
+ * A device reset (cudaDeviceReset) creates a new context, whose first call
+ * looks the address up again.  All calls in a context share the array and
+ * it keeps the last call's contents (the counter is reset by every call);
  * calls that overlap on the GPU (different streams without ordering) race.
- * Asynchronous on cuda_stream (a cudaStream_t, NULL = legacy default stream). */
+ * Extrema propagate NaN: a NaN anywhere in a field makes its max and min NaN.
+ * Asynchronous on cuda_stream (a cudaStream_t, NULL = legacy default stream):
+ * out is complete only once cuda_stream has reached the kernel (synchronise
+ * the stream, or order later work after it, before reading out). */
 jfnk_status jfnk_budgets_static(const jfnk_grid* grid, const double* u, double* out,
                                 void* cuda_stream);
 

@@ -138,6 +138,11 @@ __device__ __forceinline__ void block_partials(const TA (&v)[NV], int nv, double
     }
 }
 
+// Maximum that propagates NaN (fmax drops a NaN operand): a NaN in any value
+// makes the reduced maximum NaN, so a diagnostic cannot report finite extrema
+// for a state that holds NaN.
+__device__ __forceinline__ double max_nan(double a, double b) { return (a > b || a != a) ? a : b; }
+
 template <int NV>
 __device__ __forceinline__ void block_partials_max(const double (&v)[NV], int nv, double* part,
                                                    int stride, int blk) {
@@ -149,14 +154,14 @@ __device__ __forceinline__ void block_partials_max(const double (&v)[NV], int nv
         if (k < nv) {
             double s = v[k];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+            for (int o = 16; o > 0; o >>= 1) s = max_nan(s, __shfl_down_sync(0xffffffffu, s, o));
             if (lane == 0) red[k][warp] = s;
         }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
         double s = red[k][0];
-        for (int w = 1; w < nw; ++w) s = fmax(s, red[k][w]);
+        for (int w = 1; w < nw; ++w) s = max_nan(s, red[k][w]);
         part[(size_t)k * stride + blk] = s;
         __threadfence();          // publish before the block's arrival is counted
     }
@@ -230,6 +235,7 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int 
     __shared__ bool am_last;
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();      // cumulative: orders the block's fenced partials before the count
         unsigned int t = atomicInc(counter, total - 1);
         am_last = (t == total - 1);
     }
@@ -243,7 +249,7 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int 
 // accumulators so that a lane never waits on one L2 round trip per partial;
 // a single value is reduced by the whole block, several values warp by warp.
 template <bool MAXOP>
-__device__ __forceinline__ double combine(double a, double b) { return MAXOP ? fmax(a, b) : a + b; }
+__device__ __forceinline__ double combine(double a, double b) { return MAXOP ? max_nan(a, b) : a + b; }
 
 template <bool MAXOP>
 __device__ __forceinline__ double strided_reduce(const double* p, int n, int start, int stride) {

@@ -9,9 +9,12 @@
 // it uses -- one float64 partial sum per block and value, plus the
 // last-block counter -- lives in a file-scope __device__ array of fixed size,
 // which every GPU that loads the library holds until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
+
+#include <mutex>
 
 #include "common.cuh"
 
@@ -72,8 +75,8 @@ budgets_static_k(int nx, int nz, double inv_dx, double inv_dz, double dV,
         s[3] += ux * inv_dx + wz * inv_dz;
         for (int f = 0; f < 4; ++f) {
             const double v = u[(size_t)f * npt + p];
-            mx[f] = fmax(mx[f], v);
-            mx[4 + f] = fmax(mx[4 + f], -v);
+            mx[f] = max_nan(mx[f], v);
+            mx[4 + f] = max_nan(mx[4 + f], -v);
         }
     }
     double* pmax = part + 4 * gridDim.x;
@@ -90,22 +93,80 @@ budgets_static_k(int nx, int nz, double inv_dx, double inv_dz, double dV,
     }
 }
 
-// Device address of the scratch array, looked up once per device.
-constexpr int SB_MAX_DEVICES = 64;
-StaticScratch* g_scratch_addr[SB_MAX_DEVICES] = {nullptr};
+// Device address of the scratch array.  A __device__ symbol's address belongs
+// to a CUDA context, not to a device: it changes when the primary context is
+// reset (cudaDeviceReset) and differs in any other context a caller makes
+// current.  The cache is therefore keyed on the context's process-unique id
+// (cuCtxGetId: a reset context comes back with a new id), and it is filled
+// under a mutex so that several host threads may make their first call at
+// once.  The two driver calls are reached through the runtime's driver entry
+// points, so the library does not link libcuda itself.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
 
-cudaError_t scratch_for_current_device(StaticScratch** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+constexpr int SB_CACHE = 16;
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    StaticScratch* addr;
+};
+ScratchSlot g_slots[SB_CACHE];
+int g_nslots = 0, g_next_evict = 0;
+std::mutex g_slot_mutex;
+PfnCtxGetCurrent g_ctx_get_current = nullptr;
+PfnCtxGetId g_ctx_get_id = nullptr;
+
+cudaError_t driver_entry_points() {
+    if (g_ctx_get_current && g_ctx_get_id) return cudaSuccess;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= SB_MAX_DEVICES) return cudaErrorInvalidDevice;
-    if (g_scratch_addr[dev] == nullptr) {
-        void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_budget_scratch);
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+        return cudaErrorNotSupported;
+    g_ctx_get_current = reinterpret_cast<PfnCtxGetCurrent>(f1);
+    g_ctx_get_id = reinterpret_cast<PfnCtxGetId>(f2);
+    return cudaSuccess;
+}
+
+// Id of the context current on this thread; 0 when none is current yet.
+cudaError_t current_context_id(unsigned long long* id) {
+    *id = 0;
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    if (ctx == nullptr) return cudaSuccess;
+    return g_ctx_get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+cudaError_t scratch_for_current_context(StaticScratch** out) {
+    std::lock_guard<std::mutex> lock(g_slot_mutex);
+    cudaError_t e = driver_entry_points();
+    if (e != cudaSuccess) return e;
+    unsigned long long id = 0;
+    e = current_context_id(&id);
+    if (e != cudaSuccess) return e;
+    if (id != 0)
+        for (int i = 0; i < g_nslots; ++i)
+            if (g_slots[i].ctx_id == id) {
+                *out = g_slots[i].addr;
+                return cudaSuccess;
+            }
+    // first call in this context: the lookup makes the runtime's context
+    // current when none was (the device's primary context)
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_budget_scratch);
+    if (e != cudaSuccess) return e;
+    if (id == 0) {
+        e = current_context_id(&id);
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = static_cast<StaticScratch*>(ptr);
+        if (id == 0) return cudaErrorDeviceUninitialized;
     }
-    *out = g_scratch_addr[dev];
+    int slot = g_nslots < SB_CACHE ? g_nslots++ : g_next_evict++ % SB_CACHE;
+    g_slots[slot].ctx_id = id;
+    g_slots[slot].addr = static_cast<StaticScratch*>(ptr);
+    *out = g_slots[slot].addr;
     return cudaSuccess;
 }
 
@@ -125,7 +186,7 @@ extern "C" jfnk_status jfnk_budgets_static(const jfnk_grid* grid, const double* 
     const long long blocks = (npt + SB_POINTS_PER_BLOCK - 1) / SB_POINTS_PER_BLOCK;
     if (npt > JFNK_BUDGETS_STATIC_MAX_POINTS || blocks > SB_MAX_BLOCKS) return JFNK_ERR_INVALID_ARG;
     StaticScratch* scratch = nullptr;
-    if (scratch_for_current_device(&scratch) != cudaSuccess) return JFNK_ERR_CUDA;
+    if (scratch_for_current_context(&scratch) != cudaSuccess) return JFNK_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     // the counter must start at zero; the partial sums are fully overwritten
     if (cudaMemsetAsync(&scratch->counter, 0, sizeof(unsigned int), s) != cudaSuccess) return JFNK_ERR_CUDA;

@@ -1249,8 +1249,8 @@ budgets2d(Geo G, const double* __restrict__ u, double dV, double dz, double lz, 
         s[3] += ux * G.inv_dx + wz * G.inv_dz;
         for (int f = 0; f < 4; ++f) {
             const double v = u[(size_t)f * G.npt + p];
-            mx[f] = fmax(mx[f], v);
-            mx[4 + f] = fmax(mx[4 + f], -v);
+            mx[f] = max_nan(mx[f], v);
+            mx[4 + f] = max_nan(mx[4 + f], -v);
         }
     }
     double* pmax = part + 4 * gridDim.x;

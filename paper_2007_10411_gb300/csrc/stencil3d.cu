@@ -672,8 +672,8 @@ budgets3d(Geo G, const double* __restrict__ u, double dV, double dz, double lz, 
         s[3] += ux * G.inv_dx + vy * G.inv_dy + wz * G.inv_dz;
         for (int f = 0; f < 5; ++f) {
             const double val = u[(size_t)f * G.npt + p];
-            mx[f] = fmax(mx[f], val);
-            mx[5 + f] = fmax(mx[5 + f], -val);
+            mx[f] = max_nan(mx[f], val);
+            mx[5 + f] = max_nan(mx[5 + f], -val);
         }
     }
     double* pmax = part + 4 * gridDim.x;

@@ -23,6 +23,7 @@ JFNK_ERR_TIMEOUT = 7
 JFNK_ERR_UNSUPPORTED = 8
 MAX_KRYLOV = 32
 MAX_NEWTON = 32
+BUDGETS_STATIC_MAX_POINTS = 8388608   # JFNK_BUDGETS_STATIC_MAX_POINTS
 
 EXPORTS = (
     "jfnk_create", "jfnk_destroy", "jfnk_set_surface_flux", "jfnk_rhs", "jfnk_residual",

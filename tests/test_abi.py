@@ -73,3 +73,21 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.jfnk_step(None, P(1), None) == jfnk.JFNK_ERR_INVALID_ARG
     assert lib.jfnk_jv(None, P(1), None, P(1), 0.0, P(1), None) == jfnk.JFNK_ERR_INVALID_ARG
     assert lib.jfnk_destroy(None) == jfnk.JFNK_OK
+
+
+def test_budgets_static_size_limit(lib):
+    """jfnk_budgets_static rejects a grid past JFNK_BUDGETS_STATIC_MAX_POINTS before any CUDA call."""
+    m = re.search(r"#define\s+JFNK_BUDGETS_STATIC_MAX_POINTS\s+(\d+)", open(HEADER).read())
+    nmax = int(m.group(1))
+    assert jfnk.BUDGETS_STATIC_MAX_POINTS == nmax
+    P = ctypes.c_void_p
+    # the smallest grid with nz >= 4 and more points than the limit: nz = 4, nx = nmax / 4 + 1
+    c = synth.with_options(synth.case("tiny_16x8"), nx=nmax // 4 + 1, nz=4)
+    g = jfnk.structs_from_case(c)[0]
+    assert lib.jfnk_budgets_static(ctypes.byref(g), P(16), P(16), None) == jfnk.JFNK_ERR_INVALID_ARG
+    # malformed grids and null pointers are rejected the same way
+    c = synth.with_options(synth.case("tiny_16x8"), nz=3)
+    g = jfnk.structs_from_case(c)[0]
+    assert lib.jfnk_budgets_static(ctypes.byref(g), P(16), P(16), None) == jfnk.JFNK_ERR_INVALID_ARG
+    g = jfnk.structs_from_case(synth.case("tiny_16x8"))[0]
+    assert lib.jfnk_budgets_static(ctypes.byref(g), None, P(16), None) == jfnk.JFNK_ERR_INVALID_ARG

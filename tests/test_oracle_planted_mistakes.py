@@ -181,3 +181,86 @@ def test_left_gmres_step_catches_a_right_hand_side_left_unpreconditioned():
     bad = implicit_step(m, U, c["opts"], st_bad)
     err = float(np.linalg.norm(m.scale(bad - good)) / np.linalg.norm(m.scale(good)))
     assert (not st_bad["converged"]) or st_bad["newton_iters"] != st_good["newton_iters"] or err > 1e-9
+
+
+# ------------------------------------------------- eddy viscosity and heat source
+# Mistakes planted in copies of the oracle's Smagorinsky coefficient (Section 2.4)
+# and surface heat source (Section 3.2) make the closed-form pins of
+# test_oracle_sgs_heat fail.
+import test_oracle_sgs_heat as sh    # noqa: E402
+
+
+def _shear_nu_error(m, c):
+    x, z, dx, dz = sh.grid_xyz(c)
+    kz = math.pi * 2 / c["grid"]["lz"]
+    U = np.zeros(synth.shape(c))
+    U[0] = 0.7 * np.cos(kz * z)[:, None] * np.ones_like(x)[None, :]
+    nu, _ = sh.interior_nu(m, U)
+    expect = (0.18 * math.sqrt(dx * dz)) ** 2 * 0.7 * sh.ktil(kz, dz) * np.abs(np.sin(kz * z))[:, None]
+    return np.max(np.abs(nu - expect)) / np.max(expect)
+
+
+def test_smagorinsky_pin_unmutated():
+    c = sh.smag_case()
+    assert _shear_nu_error(Model(c), c) < 1e-12
+
+
+def test_smagorinsky_without_the_factor_two_is_caught():
+    c = sh.smag_case()
+    m = Model(c)
+    plain = m.smagorinsky_nu
+    m.smagorinsky_nu = lambda g: plain(g) / math.sqrt(2.0)     # sqrt(S:S) instead of sqrt(2 S:S)
+    assert _shear_nu_error(m, c) > 0.2
+
+
+def test_smagorinsky_with_delta_dx_is_caught():
+    c = sh.smag_case()
+    m = Model(c)
+    m.delta_les = m.dx
+    assert _shear_nu_error(m, c) > 0.2
+
+
+def test_smagorinsky_with_unsquared_cs_is_caught():
+    c = sh.smag_case()
+    m = Model(c)
+    m.Cs = math.sqrt(m.Cs)            # (Cs Delta)^2 -> Cs Delta^2
+    assert _shear_nu_error(m, c) > 0.2
+
+
+class _HeatWithoutDz(Model):
+    """Oracle copy whose surface source forgets the 1/dz of the bottom row."""
+
+    def F(self, U):
+        H = self.heat
+        self.heat = None
+        out = super().F(U)
+        self.heat = H
+        if H is not None:
+            out[self.ith][0] += H / (self.rho0 * self.cp)
+        return out
+
+
+def _heat_pin_error(m, c):
+    x, z, dx, dz = sh.grid_xyz(c)
+    H = 50.0 + 40.0 * np.cos(2 * math.pi * x / c["grid"]["lx"]) ** 2
+    m.set_heat_flux(H)
+    F = m.F(np.zeros(synth.shape(c)))
+    expect = H / (sh.RHO0 * sh.CP * dz)
+    return np.max(np.abs(F[m.ith][0] - expect)) / np.max(expect)
+
+
+def test_heat_source_pin_unmutated():
+    c = sh.heat_case()
+    assert _heat_pin_error(Model(c), c) < 1e-14
+
+
+def test_heat_source_without_dz_is_caught():
+    c = sh.heat_case()
+    assert _heat_pin_error(_HeatWithoutDz(c), c) > 0.5
+
+
+def test_heat_source_with_wrong_density_is_caught():
+    c = sh.heat_case()
+    m = Model(c)
+    m.rho0 = 1.0e5 / (287.0 * 288.15)     # density at a standard 288 K, not theta0
+    assert _heat_pin_error(m, c) > 1e-2
