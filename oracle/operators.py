@@ -14,7 +14,10 @@ throughout this project:
   mean of flux and advective forms (Section 2.2), applied to every field.
 * D_j is the Deslauriers-Dubuc collocation derivative (Section 2.3).
 * Constant exchange coefficients (Table 1) or Smagorinsky
-  nu = (Cs Delta)^2 sqrt(2 S_ij S_ij), K_M = nu, K_H = nu/Pr (Section 2.4).
+  nu = (Cs Delta)^2 sqrt(2 S_ij S_ij), K_M = nu, K_H = nu/Pr (Section 2.4), or
+  the anisotropic Deardorff closure of Section 2.4 (Eq. KmM): horizontal
+  and vertical coefficients K_m, K_M for momentum and K_h, K_H for heat,
+  each acting along its own directions (``deardorff``).
 * The stress divergence is taken in per-component Laplacian form
   sum_j D_j(K D_j phi) (symmetric negative semi-definite); p is not diffused.
 * S_H = H(x)/(rho0 cp dz) in the bottom row of theta (surface heat flux of
@@ -39,6 +42,7 @@ FREESLIP = 0
 NOSLIP = 1
 SGS_CONST = 0
 SGS_SMAGORINSKY = 1
+SGS_DEARDORFF = 2
 EPS_FP64 = 2.0 ** -52
 
 
@@ -89,6 +93,9 @@ class Model:
         self.scales = np.array([op["scale_u"]] * self.dim + [op["scale_theta"], op["scale_p"]])
         self.delta_les = (self.dx * self.dz) ** 0.5 if self.dim == 2 else \
             (self.dx * self.dy * self.dz) ** (1.0 / 3.0)
+        # horizontal cell size of the Deardorff closure: Delta_y reads as Delta_x in 2-D
+        self.dy_h = self.dx if self.dim == 2 else self.dy
+        self.N2 = self.g * self.beta / self.theta0          # background Brunt-Vaisala frequency squared
 
     # ------------------------------------------------------------------ ghosts
     def extend(self, a: np.ndarray, halo: int, parity) -> np.ndarray:
@@ -161,8 +168,47 @@ class Model:
                 ss = ss + s_ij * s_ij
         return (self.Cs * self.delta_les) ** 2 * np.sqrt(2.0 * ss)
 
+    def strain_magnitude(self, grads_vel_int: list) -> np.ndarray:
+        """s = sqrt(2 S_ij S_ij) from velocity gradients at interior points."""
+        n = self.dim
+        ss = 0.0
+        for i in range(n):
+            for j in range(n):
+                s_ij = 0.5 * (grads_vel_int[i][j] + grads_vel_int[j][i])
+                ss = ss + s_ij * s_ij
+        return np.sqrt(2.0 * ss)
+
+    def deardorff(self, s: np.ndarray):
+        """Anisotropic exchange coefficients of Section 2.4 from the strain magnitude s.
+
+        nu_tau = (Delta Cs)^2 s, epsilon = nu_tau S_ij S_ij = nu_tau s^2 / 2,
+        K_m = Cs^(4/3) epsilon^(1/3) (Dx Dy)^(2/3),  K_M = Cs^(4/3) epsilon^(1/3) Dz^(4/3)   (Eq. KmM),
+        K_h = (1 + 2 l / sqrt(Dx Dy)) K_m,  K_H = (1 + 2 l / Dz) K_M  (Deardorff's diffusivity ratios),
+        l = 0.75 sqrt(e) / N, the subgrid mixing length, capped at Delta and equal to Delta
+        where N^2 <= 0.  The subgrid kinetic energy e (tau_kk in Section 2.4) comes from
+        Deardorff's eddy-viscosity relation nu_tau = 0.1 l e^(1/2) taken with l = Delta.
+        Returns (K_m, K_M, K_h, K_H).
+        """
+        nu = (self.Cs * self.delta_les) ** 2 * s
+        eps = nu * s * s / 2.0
+        c = self.Cs ** (4.0 / 3.0) * np.cbrt(eps)
+        Km = c * (self.dx * self.dy_h) ** (2.0 / 3.0)
+        KM = c * self.dz ** (4.0 / 3.0)
+        if self.N2 > 0.0:
+            sqrt_e = nu / (0.1 * self.delta_les)
+            l = np.minimum(self.delta_les, 0.75 * sqrt_e / math.sqrt(self.N2))
+        else:
+            l = self.delta_les * np.ones_like(s)
+        Kh = (1.0 + 2.0 * l / math.sqrt(self.dx * self.dy_h)) * Km
+        KH = (1.0 + 2.0 * l / self.dz) * KM
+        return Km, KM, Kh, KH
+
     def eddy(self, U: np.ndarray):
-        """(K_M, K_H) on the halo-r region: scalars (constant mode) or mirrored-even fields."""
+        """(K_M, K_H) on the halo-r region: scalars (constant mode) or mirrored-even fields.
+
+        In the Deardorff mode each is a list with one coefficient field per
+        direction (x, [y,] z): momentum [K_m, (K_m,) K_M], heat [K_h, (K_h,) K_H].
+        """
         if self.sgs_mode == SGS_CONST:
             return self.K_M, self.K_H
         r = self.r
@@ -170,13 +216,20 @@ class Model:
         for i in self.vel:
             P = self.extend(U[i], self.H, self.parity[i])
             grads.append([self.crop(g, r) for g in self.grad_halo(P)])
+        if self.sgs_mode == SGS_DEARDORFF:
+            Km, KM, Kh, KH = (self.extend(k, r, (1.0, 1.0)) for k in self.deardorff(self.strain_magnitude(grads)))
+            horiz = self.dim - 1
+            return [Km] * horiz + [KM], [Kh] * horiz + [KH]
         nu = self.smagorinsky_nu(grads)
         nu_r = self.extend(nu, r, (1.0, 1.0))
         return nu_r, nu_r / self.Pr
 
     # -------------------------------------------------------------- diffusion
     def diffusion(self, K_r, grad_phi_r: list) -> np.ndarray:
-        """sum_j D_j(K D_j phi) on the interior; K scalar or a field on the halo-r region."""
+        """sum_j D_j(K_j D_j phi) on the interior; K scalar, a field on the halo-r region, or
+        a list of one such coefficient per direction (anisotropic closure)."""
+        if isinstance(K_r, list):
+            return self.div_halo([k * g for k, g in zip(K_r, grad_phi_r)])
         return self.div_halo([K_r * g for g in grad_phi_r])
 
     # ---------------------------------------------------------------------- F
@@ -258,11 +311,20 @@ class Model:
         P = self.extend(phi, self.H, self.parity[f])
         return out - self.diffusion(K_r, self.grad_halo(P))
 
-    def gershgorin_bounds(self, K_max: float):
-        """Eigenvalue bounds of A_f: [2/dt, 2/dt + (sum_l |d_l|)^2 K_max sum_j 1/h_j^2]."""
+    def gershgorin_bounds(self, K_max):
+        """Eigenvalue bounds of A_f: [2/dt, 2/dt + (sum_l |d_l|)^2 sum_j K_max,j / h_j^2], with
+        K_max the largest exchange coefficient (one number, or one per direction)."""
         c = sum(abs(v) for v in self.d.values())
         lo = 2.0 / self.dt
-        return lo, lo + c * c * K_max * sum(1.0 / (h * h) for h in self.spacing)
+        kj = K_max if isinstance(K_max, (list, tuple)) else [K_max] * len(self.spacing)
+        return lo, lo + c * c * sum(k / (h * h) for k, h in zip(kj, self.spacing))
+
+    @staticmethod
+    def kmax_of(K):
+        """Largest value of an exchange coefficient (scalar, field, or per-direction list)."""
+        if isinstance(K, list):
+            return [Model.kmax_of(k) for k in K]
+        return float(K) if np.isscalar(K) else float(np.max(K))
 
     def precond(self, U_frozen: np.ndarray, Rhat: np.ndarray, sweeps: int) -> np.ndarray:
         """Field-block physics-based preconditioner z = M^{-1} r (Section 2.5.2).
@@ -277,8 +339,7 @@ class Model:
         Z = np.zeros_like(Rhat)
         for f in range(self.nf):
             K = K_H if f == self.ith else K_M
-            kmax = float(np.max(K)) if not np.isscalar(K) else float(K)
-            lo, hi = self.gershgorin_bounds(0.0 if f == self.ip else kmax)
+            lo, hi = self.gershgorin_bounds(0.0 if f == self.ip else self.kmax_of(K))
             Z[f] = chebyshev(lambda x: self.block_operator(K, x, f), Rhat[f], lo, hi, sweeps)
         return Z
 
@@ -346,8 +407,7 @@ class Model:
         for j, i in enumerate(self.vel):
             Z[i] = (dt / 2.0) * (r[i] - self.theta0 * self._d_interior(dp, self.parity[self.ip], j))
         K_M, K_H = self.frozen_eddy(U_frozen)
-        kth = float(np.max(K_H)) if not np.isscalar(K_H) else float(K_H)
-        lo_t, hi_t = self.gershgorin_bounds(kth)
+        lo_t, hi_t = self.gershgorin_bounds(self.kmax_of(K_H))
         Z[self.ith] = r[self.ith] / (0.5 * (lo_t + hi_t))
         Z[self.ip] = dp
         return self.scale(Z)

@@ -264,3 +264,93 @@ def test_heat_source_with_wrong_density_is_caught():
     m = Model(c)
     m.rho0 = 1.0e5 / (287.0 * 288.15)     # density at a standard 288 K, not theta0
     assert _heat_pin_error(m, c) > 1e-2
+
+
+# ------------------------------------------------------------- Deardorff closure
+import test_oracle_deardorff as tdd    # noqa: E402
+from oracle.operators import SGS_DEARDORFF  # noqa: E402
+
+
+class _DDMutant(Model):
+    """Oracle copy whose Deardorff coefficients carry one planted mistake."""
+
+    def __init__(self, case, mistake):
+        super().__init__(case)
+        self.mistake = mistake
+
+    def deardorff(self, s):
+        nu = (self.Cs * self.delta_les) ** 2 * s
+        eps = nu * s * s / 2.0
+        if self.mistake == "eps_2SS":
+            eps = nu * s * s                       # nu 2 S_ij S_ij instead of nu S_ij S_ij
+        c = self.Cs ** (4.0 / 3.0) * np.cbrt(eps)
+        Km = c * (self.dx * self.dy_h) ** (2.0 / 3.0)
+        KM = c * self.dz ** (2.0 / 3.0 if self.mistake == "dz_exponent" else 4.0 / 3.0)
+        sqrt_e = nu / (0.1 * self.delta_les)
+        if self.N2 > 0.0:
+            l = 0.75 * sqrt_e / math.sqrt(self.N2)
+            if self.mistake != "no_cap":
+                l = np.minimum(self.delta_les, l)
+        else:
+            l = self.delta_les * np.ones_like(s)
+        hh = self.dz if self.mistake == "ratio_dz" else math.sqrt(self.dx * self.dy_h)
+        return Km, KM, (1.0 + 2.0 * l / hh) * Km, (1.0 + 2.0 * l / self.dz) * KM
+
+
+def _dd_isotropic_error(m, c):
+    U, s = tdd.shear_state(c, 0.9)
+    (Kmx, KMz), (Khx, KHz) = (tdd.interior(m, K) for K in m.eddy(U))
+    nu = (0.18 * m.dx) ** 2 * s
+    return np.max(np.abs(Kmx - 2.0 ** (-1.0 / 3.0) * nu)) / nu.max()
+
+
+def _dd_ratio_error(m):
+    U, s = tdd.shear_state(m.case, 0.8, mode=2)
+    (Kmx, KMz), (Khx, KHz) = (tdd.interior(m, K) for K in m.eddy(U))
+    mask = s > 1e-3 * s.max()
+    return max(np.max(np.abs(Kmx[mask] / KMz[mask] / (m.dx / m.dz) ** (4.0 / 3.0) - 1.0)),
+               np.max(np.abs(Khx[mask] / Kmx[mask] - (1.0 + 2.0 * m.delta_les / m.dx))))
+
+
+def _dd_cap_error(m, c):
+    N = 0.01
+    delta = m.delta_les
+    s_cap = 0.1 * delta ** 2 * N / 0.75 / (0.18 * delta) ** 2
+    U, s = tdd.shear_state(c, 1.0)
+    U *= 4.0 * s_cap / s.max()
+    s *= 4.0 * s_cap / s.max()
+    (Kmx, _), (Khx, _) = (tdd.interior(m, K) for K in m.eddy(U))
+    above = s > 1.1 * s_cap
+    return np.max(np.abs(Khx[above] / Kmx[above] - (1.0 + 2.0 * delta / m.dx)))
+
+
+def _mutant(case, mistake):
+    m = _DDMutant(case, mistake) if mistake else Model(case)
+    m.case = case
+    return m
+
+
+def test_deardorff_pins_unmutated():
+    c = tdd.dd_case()
+    assert _dd_isotropic_error(_mutant(c, None), c) < 1e-12
+    assert _dd_ratio_error(_mutant(tdd.dd_case(dz_ratio=0.6), None)) < 1e-12
+    cs = tdd.dd_case(beta=synth.brunt_beta(0.01))
+    assert _dd_cap_error(_mutant(cs, None), cs) < 1e-12
+
+
+def test_deardorff_dissipation_with_2SS_is_caught():
+    c = tdd.dd_case()
+    assert _dd_isotropic_error(_mutant(c, "eps_2SS"), c) > 0.1
+
+
+def test_deardorff_vertical_exponent_is_caught():
+    assert _dd_ratio_error(_mutant(tdd.dd_case(dz_ratio=0.6), "dz_exponent")) > 0.1
+
+
+def test_deardorff_heat_ratio_length_is_caught():
+    assert _dd_ratio_error(_mutant(tdd.dd_case(dz_ratio=0.6), "ratio_dz")) > 0.1
+
+
+def test_deardorff_uncapped_mixing_length_is_caught():
+    cs = tdd.dd_case(beta=synth.brunt_beta(0.01))
+    assert _dd_cap_error(_mutant(cs, "no_cap"), cs) > 0.1
