@@ -53,6 +53,11 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3, help="host-buffer steps through jfnk_step_host")
     p.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample (0: skip)")
     p.add_argument("--no-kernel-timing", action="store_true")
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                   help="precision of the main timed run (fp64: the plain float64 path, for profiling it)")
+    p.add_argument("--precision-check", type=int, default=1,
+                   help="1: report the per-field error of the mixed step against the oracle (256x128, same "
+                        "physics) and against the float64 GPU step (the workload itself); 0 skips it")
     p.add_argument("--precond", default="block", choices=["block", "schur", "nonlinear"],
                    help="preconditioner of the main timed run (block: the paper's field-block one on the "
                         "right; nonlinear: the same field block as the nonlinear preconditioning of "
@@ -137,26 +142,34 @@ UNET_FLOPS_PER_POINT = (2 * 9 * 4 * 16 + 2 * 9 * 16 * 16                      # 
 
 
 def unet_apply_timing(jfnk, torch, s, npt: int, reps: int, stream) -> dict:
-    """CUDA-event time of the network apply alone (jfnk_unet_forward) and its tensor roofline."""
+    """CUDA-event time of the network apply alone (jfnk_unet_forward) and its tensor roofline,
+    for the tcgen05 convolutions (the default engine) and, beside them, the mma.sync ones."""
     x = torch.randn(4 * npt, device="cuda", dtype=torch.float32, generator=torch.Generator("cuda").manual_seed(5))
     y = torch.empty_like(x)
-    for _ in range(3):
-        s.unet_forward(x, y)
-    a0 = torch.cuda.Event(enable_timing=True)
-    a1 = torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    for _ in range(reps):
-        s.unet_forward(x, y)
-    a1.record(stream)
-    a1.synchronize()
-    ms = a0.elapsed_time(a1) / reps
     peaks = measured_peaks()
     flops = UNET_FLOPS_PER_POINT * npt
-    achieved = flops / (ms / 1e3) / 1e12
-    return {"ms_per_apply": ms, "flops_per_apply": flops, "bound": "tensor", "achieved": achieved,
-            "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
+    out = {}
+    for engine, tag in ((jfnk.UNET_MMA_SYNC, "mma_sync"), (jfnk.UNET_TCGEN05, "tcgen05")):
+        s.unet_set_engine(engine)
+        for _ in range(3):
+            s.unet_forward(x, y)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            s.unet_forward(x, y)
+        a1.record(stream)
+        a1.synchronize()
+        s.unet_status()
+        ms = a0.elapsed_time(a1) / reps
+        out[tag] = {"ms_per_apply": ms, "achieved": flops / (ms / 1e3) / 1e12}
+    achieved = out["tcgen05"]["achieved"]
+    return {"ms_per_apply": out["tcgen05"]["ms_per_apply"], "flops_per_apply": flops, "bound": "tensor",
+            "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / peaks["bf16_tflops"],
             "peak_source": peaks["source"] + " (MEASURED_PEAKS.json bf16_tflops, burst)",
-            "kernel": "conv_mma (mma.sync m16n8k16 bf16, 9 launches per apply)"}
+            "kernel": "conv_tc (tcgen05.mma kind::f16, bf16 in TMEM-accumulated float32, 9 launches per apply)",
+            "mma_sync": out["mma_sync"]}
 
 
 def ncu_traffic() -> dict:
@@ -220,6 +233,8 @@ def oracle_sample(case: dict, seconds: float, iters_per_step: float, newton_per_
     from paper_2007_10411_gb300 import synth
 
     m = Model(case)
+    if case.get("init", {}).get("kind") == "rest" and "H0" in case["init"]:
+        m.set_heat_flux(synth.heat_flux(case))          # heat island: the surface flux drives the step
     U = synth.initial_state(case)
     t0 = time.perf_counter()
     f = m.rhs_f(U)
@@ -312,8 +327,13 @@ def run_batch(args, rank: int, world: int, local_rank: int):
     if world > 1:
         import torch.distributed as dist_
         dist = dist_
-    n_inst = int(args.workload[len("uhi_batch"):] or 16)
-    cases = synth.uhi_batch(n=n_inst)
+    three_d = args.workload.startswith("uhi3d_batch")
+    if three_d:
+        n_inst = int(args.workload[len("uhi3d_batch"):] or 4)
+        cases = synth.uhi3d_batch(n=n_inst)
+    else:
+        n_inst = int(args.workload[len("uhi_batch"):] or 16)
+        cases = synth.uhi_batch(n=n_inst)
     if args.precond == "schur":
         cases = [synth.with_options(c, precond=jfnk.PC_SCHUR, pc_sweeps=args.schur_sweeps) for c in cases]
     elif args.precond == "nonlinear":
@@ -325,9 +345,26 @@ def run_batch(args, rank: int, world: int, local_rank: int):
     U0 = [synth.initial_state(c) for c in cases]
     states = [torch.from_numpy(u).cuda() for u in U0]
     points = sum(int(np.prod(synth.shape(c)[1:])) for c in cases)
+    # heat-content budget: the surface flux adds mean(H) * area * dt / (rho0 cp) to
+    # sum(theta) dV every step; its drift is what the step adds beyond that
+    heat_in = []
+    for c in cases:
+        H = synth.heat_flux(c)
+        area = c["grid"]["lx"] * (c["grid"]["ly"] if c["grid"]["dim"] == 3 else 1.0)
+        heat_in.append(float(np.mean(H)) * area * c["opts"]["dt"] / (c["strat"]["rho0"] * c["strat"]["cp"]))
+    b_start = [batch.budgets(i, states[i]) for i in range(n_inst)]
     for _ in range(args.warmup):
         batch.step(states)
     torch.cuda.synchronize()
+    # kernel breakdown: one more warm batch step with CUDA events around every launch of
+    # every family (the instances run concurrently, so a launch shares the GPU with others)
+    kbreak = None
+    if not args.no_kernel_timing:
+        batch.kernel_timing()
+        batch.step([s.clone() for s in states])
+        torch.cuda.synchronize()
+        kbreak = batch.kernel_timing_read()
+        batch.kernel_timing(())
     if dist is not None:
         dist.barrier()
     clocks = Clocks(local_rank)
@@ -342,6 +379,14 @@ def run_batch(args, rank: int, world: int, local_rank: int):
     clk = clocks.stop()
     ms = max_over_ranks(max(e0.elapsed_time(e1), 0.0), dist, "cuda")
     value = job_throughput(points, args.steps, world, ms)
+    b_end = [batch.budgets(i, states[i]) for i in range(n_inst)]
+    nsteps = args.warmup + args.steps
+    budget = []
+    for i in range(n_inst):
+        gained = b_end[i]["sum_theta"] - b_start[i]["sum_theta"]
+        budget.append({"heat_gained": gained, "heat_input": heat_in[i] * nsteps,
+                       "heat_drift_rel": (gained - heat_in[i] * nsteps) / (heat_in[i] * nsteps) if heat_in[i] else None,
+                       "sum_div": b_end[i]["sum_div"], "E_k": b_end[i]["E_k"], "E_p": b_end[i]["E_p"]})
     e2e = None
     if args.e2e_steps > 0:
         hosts = [torch.from_numpy(u.copy()).pin_memory() for u in U0]
@@ -358,9 +403,60 @@ def run_batch(args, rank: int, world: int, local_rank: int):
         nbytes = sum(8 * int(np.prod(synth.shape(c))) for c in cases)
         e2e = {"value": job_throughput(points, args.e2e_steps, world, el), "unit": "Mpt*steps/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    precision = None
+    if args.precision_check and rank == 0:
+        # instance 0: one mixed step against the float64 GPU step from the same state
+        batch.close()
+        del states
+        torch.cuda.empty_cache()
+        c0 = cases[0]
+        H0 = torch.from_numpy(synth.heat_flux(c0)).cuda()
+        outs = []
+        for prec in (synth.PREC_MIXED, synth.PREC_FP64):
+            s_ = jfnk.Solver(synth.with_options(c0, precision=prec), stream=stream)
+            s_.set_surface_flux(H0)
+            u_ = torch.from_numpy(U0[0].copy()).cuda()
+            st_ = s_.step(u_)
+            torch.cuda.synchronize()
+            outs.append((u_.cpu().numpy(), st_))
+            s_.close()
+            del u_
+            torch.cuda.empty_cache()
+        (gm, stm), (gd, std) = outs
+        names = ["u", "w", "theta", "p"] if c0["grid"]["dim"] == 2 else ["u", "v", "w", "theta", "p"]
+        precision = {"fields": names, "instance": 0, "tolerance": 1e-4,
+                     "vs_fp64_gpu": {"state": _rel_per_field(gm, gd), "increment": _rel_per_field(gm - U0[0], gd - U0[0]),
+                                     "converged": stm["converged"] and std["converged"]}}
     if rank != 0:
         return
     per_inst = [[s[i] for s in stats] for i in range(n_inst)]
+    roof, kernels = None, None
+    if kbreak:
+        peaks = measured_peaks()
+        kernels = {k: {"launches": a["launches"], "ms_total": a["ms"],
+                       "achieved_gbs": a["bytes"] / (a["ms"] / 1e3) / 1e9}
+                   for k, a in kbreak.items() if a["launches"] and a["ms"] > 0}
+        dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+        roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["achieved_gbs"], "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": kernels[dom]["achieved_gbs"] / peaks["hbm_gbs"], "traffic": None,
+                "algorithmic_bytes_per_launch": kbreak[dom]["bytes"] / kbreak[dom]["launches"],
+                "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)",
+                "timing": "CUDA events around every launch of this family over one batch step, instances "
+                          "running concurrently (a launch shares the GPU with the other instances' kernels)"}
+    cpu = None
+    if args.cpu_seconds > 0:
+        c0 = cases[0]
+        it0 = statistics.mean(s["gmres_iters"] for s in per_inst[0])
+        nw0 = statistics.mean(s["newton_iters"] for s in per_inst[0])
+        where = "instance 0 of the batch"
+        if three_d:
+            # a 384 x 384 x 128 residual alone takes the oracle minutes: sample the same
+            # physics on a 96 x 96 x 32 grid
+            c0 = synth.with_options(c0, nx=96, ny=96, nz=32)
+            where = "instance 0's physics on a 96x96x32 grid"
+        r = oracle_sample(c0, args.cpu_seconds, max(it0, 1.0), max(nw0, 1.0))
+        cpu = {"value": r["value"], "unit": "Mpt*steps/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": where + ": " + r["sample"]}
     line = {
         "metric": metric_name(args.workload), "value": value, "unit": "Mpt*steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -374,10 +470,14 @@ def run_batch(args, rank: int, world: int, local_rank: int):
                    "precond": pc_label(args.precond, cases[0]),
                    "execution": "one handle + stream per instance, host thread per instance",
                    "parallelism": "replicas" if world > 1 else "single"},
+        "precision_error": precision,
+        "budgets": {"steps": nsteps, "per_instance": budget,
+                    "note": "sum(theta) dV gained over all steps against the surface heat input "
+                            "mean(H) area dt / (rho0 cp) per step; sum_div = global mass flux"},
         "newton_per_step": [statistics.mean(s["newton_iters"] for s in p) for p in per_inst],
         "gmres_iters_per_step": [statistics.mean(s["gmres_iters"] for s in p) for p in per_inst],
         "converged": all(s["converged"] for st in stats for s in st),
-        "clocks": clk, "e2e": e2e, "roofline": None, "cpu_baseline": None,
+        "clocks": clk, "e2e": e2e, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
 
@@ -459,6 +559,43 @@ def pc_label(precond: str, case: dict) -> str:
     if precond == "nonlinear":
         return "field-block Chebyshev (%d sweeps) as nonlinear preconditioner (Newton on M^-1 R)" % sw
     return "field-block Chebyshev (%d sweeps)" % sw
+
+
+def _rel_per_field(got, ref):
+    import numpy as np
+    return [float(np.linalg.norm(got[f] - ref[f]) / max(np.linalg.norm(ref[f]), 1e-300)) for f in range(ref.shape[0])]
+
+
+def precision_leg(jfnk, synth, torch, stream, case, U0) -> dict:
+    """Per-field relative L2 error of one mixed-precision step (u, w, theta, p), on the state
+    and on the step's increment: (a) at 256x128 with the workload's physics, against the
+    float64 oracle's step; (b) on the workload itself, against the float64 GPU step from the
+    same state (a whole oracle step of the workload takes minutes)."""
+    from oracle.newton import implicit_step
+    from oracle.operators import Model
+
+    def gpu_step(c, U):
+        s = jfnk.Solver(c, stream=stream)
+        u = torch.from_numpy(U.copy()).cuda()
+        st = s.step(u)
+        torch.cuda.synchronize()
+        out = u.cpu().numpy()
+        s.close()
+        return out, st
+
+    out = {"fields": ["u", "w", "theta", "p"][:U0.shape[0]], "tolerance": 1e-4}
+    small = synth.case("thermal_stable_256x128")
+    Us = synth.initial_state(small)
+    ref = implicit_step(Model(small), Us, small["opts"], {})
+    got, st = gpu_step(small, Us)
+    out["vs_oracle_256x128"] = {"state": _rel_per_field(got, ref), "increment": _rel_per_field(got - Us, ref - Us),
+                                "converged": st["converged"]}
+    got, st = gpu_step(case, U0)
+    ref, st64 = gpu_step(synth.with_options(case, precision=synth.PREC_FP64), U0)
+    out["vs_fp64_gpu_" + "x".join(str(v) for v in synth.shape(case)[:0:-1])] = {
+        "state": _rel_per_field(got, ref), "increment": _rel_per_field(got - U0, ref - U0),
+        "converged": st["converged"] and st64["converged"]}
+    return out
 
 
 def nonlinear_leg(jfnk, synth, torch, stream, case, U0, steps: int, barrier, slowest, world: int) -> dict:
@@ -562,6 +699,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         return max_over_ranks(v, dist, "cuda")
 
     case = synth.case(args.workload)
+    if args.precision == "fp64":
+        case = synth.with_options(case, precision=synth.PREC_FP64)
     if args.precond == "schur":
         case = synth.with_options(case, precond=jfnk.PC_SCHUR, pc_sweeps=args.schur_sweeps)
     elif args.precond == "nonlinear":
@@ -647,6 +786,10 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "newton_per_step": statistics.mean(s["newton_iters"] for s in st64)}
         s64.close()
 
+    precision = None
+    if args.precision_check and args.precision == "mixed" and case["grid"]["dim"] == 2 and rank == 0:
+        precision = precision_leg(jfnk, synth, torch, stream, case, U0)
+
     nonlinear = None
     if args.nonlinear_steps > 0 and args.precond == "block":
         nonlinear = nonlinear_leg(jfnk, synth, torch, stream, case, U0, args.nonlinear_steps, barrier, slowest,
@@ -699,9 +842,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "metric": metric_name(args.workload), "value": value, "unit": "Mpt*steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32/f64", "data": "synthetic",
+        "dtype": "f32/f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": list(synth.shape(case)[:0:-1]),
-                   "points": npt, "precision": "mixed", "krylov_m": case["opts"]["krylov_m"],
+                   "points": npt, "precision": args.precision, "krylov_m": case["opts"]["krylov_m"],
                    "precond": pc_label(args.precond, case),
                    "parallelism": "replicas" if world > 1 else "single",
                    "tiles": {"jv": tiles[0], "precond": tiles[1]},
@@ -712,6 +855,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "clocks": clk, "gpu_launches": launches, "e2e": e2e, "roofline": roof, "kernels": kernels,
         "kernels_timing": "per-family CUDA events over 2 steps right before the timed region" if kernels else None,
         "fp64_plain": fp64, "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
+        "precision_error": precision,
         "nonlinear_pc": nonlinear,
         "nonlinear_over_block": (nonlinear["value"] / value) if nonlinear else None,
         "schur_pc": schur,
@@ -741,7 +885,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.workload.startswith("uhi_batch"):
+    if args.workload.startswith("uhi_batch") or args.workload.startswith("uhi3d_batch"):
         run_batch(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)

@@ -60,7 +60,7 @@ typedef enum {
 } jfnk_status;
 
 enum { JFNK_FREESLIP = 0, JFNK_NOSLIP = 1 };
-enum { JFNK_SGS_CONST = 0, JFNK_SGS_SMAGORINSKY = 1 };
+enum { JFNK_SGS_CONST = 0, JFNK_SGS_SMAGORINSKY = 1, JFNK_SGS_DEARDORFF = 2 };
 enum { JFNK_FP64 = 0, JFNK_MIXED = 1 };
 enum { JFNK_PC_NONE = 0, JFNK_PC_BLOCK = 1, JFNK_PC_UNET = 2, JFNK_PC_SCHUR = 3, JFNK_PC_NONLINEAR = 4 };
 
@@ -90,7 +90,15 @@ typedef struct {
 
 /* Sub-grid closure (Section 2.4).  mode JFNK_SGS_CONST uses K_M, K_H [m^2/s]
  * (Table 1); JFNK_SGS_SMAGORINSKY uses nu = (Cs Delta)^2 sqrt(2 S:S),
- * Delta = (dx dz)^(1/2) in 2D, (dx dy dz)^(1/3) in 3D, K_M = nu, K_H = nu/Pr. */
+ * Delta = (dx dz)^(1/2) in 2D, (dx dy dz)^(1/3) in 3D, K_M = nu, K_H = nu/Pr.
+ * JFNK_SGS_DEARDORFF is the anisotropic closure of Section 2.4 (Eq. KmM):
+ * with s = sqrt(2 S:S) and
+ * eps = nu S:S, K_m = Cs^(4/3) eps^(1/3) (dx dy)^(2/3) acts along x (and y)
+ * and K_M = Cs^(4/3) eps^(1/3) dz^(4/3) along z for momentum; heat takes
+ * K_h = (1 + 2l/sqrt(dx dy)) K_m and K_H = (1 + 2l/dz) K_M, with the mixing
+ * length l = min(Delta, 0.75 sqrt(e)/N), sqrt(e) = nu/(0.1 Delta) and N the
+ * background Brunt-Vaisala frequency (l = Delta where beta <= 0); dy reads as
+ * dx in 2-D.  K_M, K_H and Pr are not used by this mode (Pr must still be > 0). */
 typedef struct {
     int mode;
     double K_M, K_H, Cs, Pr;
@@ -365,9 +373,25 @@ jfnk_status jfnk_unet_train(jfnk_handle* h, int epochs, float lr, double* loss_h
 jfnk_status jfnk_unet_forward(jfnk_handle* h, const float* x, float* y);
 
 /* Loss of one pair (device x, t) and, when grads (host, jfnk_unet_num_weights
- * floats) is not NULL, its gradient with respect to the flat weights. */
+ * floats) is not NULL, its gradient with respect to the flat weights.
+ * Synchronises; JFNK_ERR_TIMEOUT as for jfnk_unet_status. */
 jfnk_status jfnk_unet_loss_grad(jfnk_handle* h, const float* x, const float* t, double* loss,
                                 float* grads);
+
+/* Engine of the network's convolutions (not in the paper; the network itself
+ * is this project's addition): JFNK_UNET_TCGEN05 (default) runs them as
+ * implicit GEMMs on the tcgen05 tensor cores with TMEM accumulators,
+ * JFNK_UNET_MMA_SYNC on the mma.sync path; both compute the same layers in
+ * bfloat16 with float32 accumulation.  Synchronises the handle's stream. */
+#define JFNK_UNET_TCGEN05 0
+#define JFNK_UNET_MMA_SYNC 1
+jfnk_status jfnk_unet_set_engine(jfnk_handle* h, int engine);
+
+/* Synchronises the stream and returns JFNK_ERR_TIMEOUT when a tensor-core
+ * wait inside a network convolution ran past its iteration limit since the
+ * network was created (that convolution's output is not valid; the flag
+ * stays set), else JFNK_OK. */
+jfnk_status jfnk_unet_status(jfnk_handle* h);
 
 /* Change the preconditioner between steps: any JFNK_PC_* value accepted by
  * jfnk_create (JFNK_PC_UNET only where the calls above are supported). */

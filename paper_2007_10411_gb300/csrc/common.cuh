@@ -27,8 +27,15 @@ struct Geo {
     int pb[5], pt[5];                 // mirror parity per field at bottom / top (+1 / -1)
     double inv_dx, inv_dz;
     double theta0, beta, pbar, g, gamma_p, heat_coef;   // heat_coef = 1/(rho0 cp dz)
-    int smag;
+    int smag;                         // eddy coefficients from the strain (Smagorinsky or Deardorff)
+    int sgs;                          // 0 constant K, 1 Smagorinsky, 2 Deardorff (anisotropic)
     double K_M, K_H, cs2;             // cs2 = (Cs Delta)^2
+    // Deardorff closure in terms of s = sqrt(2 S:S): K_m = dd_cm s, K_M = dd_cM s,
+    // K_h = K_m (1 + dd_ah l), K_H = K_M (1 + dd_az l), l = min(dd_delta, dd_cl s)
+    // (dd_cl < 0: l = dd_delta)
+    double dd_cm, dd_cM, dd_cl, dd_delta, dd_ah, dd_az;
+    // float32 derivative weights with 1/h folded in: D f = w1 (f_{+1} - f_{-1}) + w2 (f_{+2} - f_{-2})
+    float fx1, fx2, fz1, fz2;
     double inv_Pr;
     double two_over_dt;
     double scale[5], inv_scale[5];
@@ -75,6 +82,8 @@ struct Ctl {
     double cs[KMAX], sn[KMAX];
     double g[KMAX + 1];
     double y[KMAX];
+    double zscale[KMAX];      // direction k of the cycle enters the update as zscale[k] y_k z_k
+                              // (1 unless the lagged second projection normalised w_k on the fly)
     // Chebyshev coefficients per field block and sweep: 1/theta_c, rho_k rho_{k-1}, 2 rho_k / delta
     double cheb[6][MAX_PC_SWEEPS][3];   // slot 5: pressure Helmholtz of the Schur complement
     unsigned int counter[8];         // last-block counters, one per kernel family

@@ -45,6 +45,7 @@ struct jfnk_handle {
     double *un, *f, *R, *Fu64, *x, *tmp64, *udev, *heat, *budg;
     // stencil-precision buffers (double for FP64, float for MIXED)
     void *V, *Z, *w, *uT, *xT, *za, *zb, *da, *db, *nu, *tA, *tB;
+    void* w2;        // second Jacobian-product buffer (right preconditioning: w'_{j-1} and w_j coexist)
     double* part;
     double* partB;   // second partial-sum area (Arnoldi pass B), inside the part allocation
     Ctl* ctl;
@@ -94,7 +95,8 @@ static jfnk_status validate(const jfnk_grid* g, const jfnk_strat* s, const jfnk_
     if (!finite_pos(s->theta0) || !isfinite(s->beta) || !isfinite(s->pbar) || !isfinite(s->g) ||
         !isfinite(s->gamma_p) || !finite_pos(s->rho0) || !finite_pos(s->cp))
         return JFNK_ERR_INVALID_ARG;
-    if (q->mode != JFNK_SGS_CONST && q->mode != JFNK_SGS_SMAGORINSKY) return JFNK_ERR_INVALID_ARG;
+    if (q->mode != JFNK_SGS_CONST && q->mode != JFNK_SGS_SMAGORINSKY && q->mode != JFNK_SGS_DEARDORFF)
+        return JFNK_ERR_INVALID_ARG;
     if (!(q->K_M >= 0.0) || !(q->K_H >= 0.0) || !(q->Cs >= 0.0) || !finite_pos(q->Pr) ||
         !isfinite(q->K_M) || !isfinite(q->K_H) || !isfinite(q->Cs))
         return JFNK_ERR_INVALID_ARG;
@@ -131,7 +133,7 @@ static bool unet_supported(const jfnk_handle* h) {
 
 static void free_all(jfnk_handle* h) {
     void* dev[] = {h->un, h->f, h->R, h->Fu64, h->x, h->tmp64, h->udev, h->heat, h->budg,
-                   h->V, h->Z, h->w, h->uT, h->xT, h->za, h->zb, h->da, h->db, h->nu,
+                   h->V, h->Z, h->w, h->w2, h->uT, h->xT, h->za, h->zb, h->da, h->db, h->nu,
                    h->tA, h->tB, h->part, h->ctl};
     for (void* p : dev)
         if (p) cudaFree(p);
@@ -266,17 +268,36 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     G.inv_dx = 1.0 / dx;
     G.inv_dy = 1.0 / dy;
     G.inv_dz = 1.0 / dz;
+    G.fx1 = (float)(2.0 / 3.0 / dx);
+    G.fx2 = (float)(-1.0 / 12.0 / dx);
+    G.fz1 = (float)(2.0 / 3.0 / dz);
+    G.fz2 = (float)(-1.0 / 12.0 / dz);
     G.theta0 = strat->theta0;
     G.beta = strat->beta;
     G.pbar = strat->pbar;
     G.g = strat->g;
     G.gamma_p = strat->gamma_p;
     G.heat_coef = 1.0 / (strat->rho0 * strat->cp * dz);
-    G.smag = sgs->mode == JFNK_SGS_SMAGORINSKY;
+    G.sgs = sgs->mode;
+    G.smag = sgs->mode != JFNK_SGS_CONST;
     G.K_M = G.smag ? 0.0 : sgs->K_M;
     G.K_H = G.smag ? 0.0 : sgs->K_H;
     const double delta = dim == 3 ? cbrt(dx * dy * dz) : sqrt(dx * dz);
     G.cs2 = (sgs->Cs * delta) * (sgs->Cs * delta);
+    {
+        // Deardorff (Section 2.4, Eq. KmM): eps^(1/3) = (cs2 / 2)^(1/3) s, so every
+        // coefficient is a constant times s (times 1 + 2l/h for heat)
+        const double dyh = dim == 3 ? dy : dx;              // dy reads as dx in 2-D
+        const double c = pow(sgs->Cs, 4.0 / 3.0) * cbrt(0.5 * G.cs2);
+        G.dd_cm = c * pow(dx * dyh, 2.0 / 3.0);
+        G.dd_cM = c * pow(dz, 4.0 / 3.0);
+        G.dd_delta = delta;
+        const double n2 = strat->g * strat->beta / strat->theta0;
+        // l = 0.75 sqrt(e) / N with sqrt(e) = nu / (0.1 Delta) = cs2 s / (0.1 Delta)
+        G.dd_cl = n2 > 0.0 ? 0.75 * G.cs2 / (0.1 * delta) / sqrt(n2) : -1.0;
+        G.dd_ah = 2.0 / sqrt(dx * dyh);
+        G.dd_az = 2.0 / dz;
+    }
     G.inv_Pr = 1.0 / sgs->Pr;
     G.two_over_dt = 2.0 / opts->dt;
     for (int f = 0; f < nf; ++f) {
@@ -326,6 +347,7 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     ALLOC(h->V, (size_t)(m + 1) * nbT);
     if (opts->precond != JFNK_PC_NONE) ALLOC(h->Z, (size_t)m * nbT);
     ALLOC(h->w, nbT);
+    if (opts->precond != JFNK_PC_NONE && opts->precond != JFNK_PC_NONLINEAR) ALLOC(h->w2, nbT);
     if (h->mixed) {
         ALLOC(h->uT, nbT);
         ALLOC(h->xT, nbT);
@@ -655,6 +677,83 @@ static jfnk_status apply_jv(jfnk_handle* h, const T* uT, const T* z, T* w, int c
     return JFNK_OK;
 }
 
+// One GMRES cycle of the right-preconditioned path with the second projection
+// of CGS2 lagged behind the next Jacobian product (Arnoldi passes CA and B per
+// step, see arnoldi_ca): step j takes the direction d_j = v_0 (j = 0) or
+// w'_{j-1}, z_j = M^{-1} d_j (+ N(d_j) for the learned correction), w_j = J z_j;
+// pass CA forms v_j, updates column j-1 of the Hessenberg / Givens state and
+// projects w_j once; pass B projects it again into w'_j.  The last column of a
+// full cycle gets its Givens update alone.  The w'_{j-1} / w_j buffers
+// alternate between w and w2.
+template <typename T>
+static jfnk_status fused_cycle(jfnk_handle* h, const T* uT, bool learned, bool arnoldi_pairs, int lag) {
+    cudaStream_t s = h->stream;
+    const Geo& G = h->G;
+    const size_t n = h->n, ld = h->ld;
+    const int m = h->m;
+    T* V = (T*)h->V;
+    T* Z = (T*)h->Z;
+    T* wb[2] = {(T*)h->w, (T*)h->w2};
+    const double vb = (double)n * sizeof(T);
+    int j = 0;
+    for (; j < m; ++j) {
+        const T* dj = j == 0 ? V : wb[(j - 1) & 1];
+        T* zj = Z + (size_t)j * ld;
+        T* wj = wb[j & 1];
+        kt_begin(h, JFNK_KF_PRECOND);
+        CK(launch_precond<T>(G, h->opts.pc_sweeps, dj, zj, (T*)h->za, (T*)h->zb, (T*)h->da, (T*)h->db,
+                             (const T*)h->nu, h->part, h->ctl, 1, s, &h->launches));
+        kt_end(h, JFNK_KF_PRECOND, pc_bytes(h));
+        if constexpr (sizeof(T) == sizeof(float)) {
+            if (learned) {   // z_j += N(d_j), then the FD step for the new ||z_j||
+                kt_begin(h, JFNK_KF_UNET);
+                CK(unet_apply(h->net, (const float*)dj, (float*)zj, 1, &h->ctl->done, s));
+                kt_end(h, JFNK_KF_UNET, 3.0 * (double)n * sizeof(float));
+                CK(launch_pc_eps(zj, n, h->part, h->ctl, s));
+                h->launches += unet_launches_per_apply() + 1;
+            }
+        }
+        jfnk_status st = apply_jv<T>(h, uT, zj, wj, 1);
+        if (st != JFNK_OK) return st;
+        if constexpr (sizeof(T) == sizeof(float)) {
+            if (arnoldi_pairs) {   // (J z_j, z_j) is an exact inverse pair
+                CK(launch_pair_arnoldi(wj, (float*)h->tA, n, h->part, h->ctl, s));
+                CK(launch_precond<float>(G, h->opts.pc_sweeps, (const float*)h->tA, (float*)h->tB,
+                                         (float*)h->za, (float*)h->zb, (float*)h->da, (float*)h->db,
+                                         (const float*)h->nu, h->part, h->ctl, 1, s, &h->launches));
+                CK(launch_pair_store<float>((const float*)h->tA, zj, (const float*)h->tB, h->capX, h->capT, n,
+                                            h->cap_cap, 1, h->ctl, s));
+                h->launches += 4;
+            }
+        }
+        kt_begin(h, JFNK_KF_ARNOLDI_A);
+        int nblkA;
+        if (j == 0) {
+            CK(launch_arnoldi_a<T>(V, ld, wj, n, 1, h->part, h->ctl, s));
+            nblkA = arnoldi_a_parts<T>(n);
+            kt_end(h, JFNK_KF_ARNOLDI_A, 2 * vb);
+        } else {
+            CK(launch_arnoldi_ca<T>(V, ld, wb[(j - 1) & 1], wj, n, j, m, h->partB, h->part, h->ctl, s));
+            nblkA = arnoldi_ca_parts<T>(n);
+            kt_end(h, JFNK_KF_ARNOLDI_A, (j + 3) * vb);   // reads v_0..v_{j-1}, w'_{j-1}, w_j; writes v_j
+        }
+        kt_begin(h, JFNK_KF_ARNOLDI_B);
+        CK(launch_arnoldi_b_from<T>(V, ld, wj, n, j + 1, h->part, nblkA, h->partB, h->ctl, s));
+        kt_end(h, JFNK_KF_ARNOLDI_B, (j + 3) * vb);      // reads v_0..v_j, w_j; writes w'_j
+        h->launches += 2;
+        CK(cudaMemcpyAsync(&h->hdone[j], &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(h->ev[j], s));
+        if (j >= lag) {
+            CK(cudaEventSynchronize(h->ev[j - lag]));
+            if (h->hdone[j - lag]) break;
+        }
+    }
+    // Givens update of the cycle's last column (returns at once when the cycle ended earlier)
+    CK(launch_arnoldi_givens<T>(n, std::min(j + 1, m), m, h->partB, h->ctl, s));
+    h->launches += 1;
+    return JFNK_OK;
+}
+
 // Restarted GMRES(m) on J_hat x = -W R from x = 0 (cycle_init already enqueued).
 // Nonlinear preconditioning (left): v_0 <- M^{-1} v_0 / ||M^{-1} v_0|| and the
 // cycle's g_0, after cycle_init (first) or restart_residual left r in v_0.
@@ -693,7 +792,11 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
     *conv = 0;
     *switched = 0;
     for (int cycle = 0;; ++cycle) {
-        for (int j = 0; j < m; ++j) {
+        if (pc) {
+            jfnk_status st = fused_cycle<T>(h, uT, learned, arnoldi_pairs, lag);
+            if (st != JFNK_OK) return st;
+        }
+        for (int j = 0; j < m && !pc; ++j) {
             T* vj = V + (size_t)j * ld;
             T* zj = Z + (size_t)j * ld;
             if (pc) {
@@ -1009,7 +1112,9 @@ extern "C" jfnk_status jfnk_unet_train(jfnk_handle* h, int epochs, float lr, dou
     jfnk_status st = pair_count(h, &c);
     if (st != JFNK_OK) return st;
     if (!h->net || c < 1) return JFNK_ERR_INVALID_ARG;
-    CK(unet_train(h->net, h->capX, h->capT, c, epochs, lr, loss_hist, h->stream));
+    const cudaError_t e = unet_train(h->net, h->capX, h->capT, c, epochs, lr, loss_hist, h->stream);
+    if (e == cudaErrorLaunchTimeout) return JFNK_ERR_TIMEOUT;
+    CK(e);
     return JFNK_OK;
 }
 
@@ -1027,7 +1132,27 @@ extern "C" jfnk_status jfnk_unet_loss_grad(jfnk_handle* h, const float* x, const
     if (!h || !x || !t || !loss) return JFNK_ERR_INVALID_ARG;
     if (!unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
     if (!h->net) return JFNK_ERR_INVALID_ARG;
-    CK(unet_loss_grad(h->net, x, t, loss, grads, h->stream));
+    const cudaError_t e = unet_loss_grad(h->net, x, t, loss, grads, h->stream);
+    if (e == cudaErrorLaunchTimeout) return JFNK_ERR_TIMEOUT;
+    CK(e);
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_unet_set_engine(jfnk_handle* h, int engine) {
+    if (!h || (engine != JFNK_UNET_TCGEN05 && engine != JFNK_UNET_MMA_SYNC)) return JFNK_ERR_INVALID_ARG;
+    if (!unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
+    if (!h->net) return JFNK_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    CK(unet_set_engine(h->net, engine));
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_unet_status(jfnk_handle* h) {
+    if (!h) return JFNK_ERR_INVALID_ARG;
+    if (!h->net) return JFNK_OK;
+    const cudaError_t e = unet_check(h->net, h->stream);
+    if (e == cudaErrorLaunchTimeout) return JFNK_ERR_TIMEOUT;
+    CK(e);
     return JFNK_OK;
 }
 
@@ -1038,12 +1163,21 @@ extern "C" jfnk_status jfnk_set_precond(jfnk_handle* h, int precond) {
         return JFNK_ERR_INVALID_ARG;
     if (precond == JFNK_PC_UNET && !unet_supported(h)) return JFNK_ERR_UNSUPPORTED;
     if (precond == JFNK_PC_SCHUR && h->opts.pc_sweeps < 2) return JFNK_ERR_UNSUPPORTED;
+    const size_t eT = h->mixed ? sizeof(float) : sizeof(double);
     if (precond != JFNK_PC_NONE && !h->Z) {
-        const size_t eT = h->mixed ? sizeof(float) : sizeof(double);
         CK(cudaStreamSynchronize(h->stream));
         if (cudaMalloc(&h->Z, (size_t)h->m * h->ld * eT) != cudaSuccess) {
             cudaGetLastError();
             h->Z = nullptr;
+            return JFNK_ERR_OOM;
+        }
+    }
+    // the right-preconditioned cycle keeps w'_{j-1} and w_j in two buffers
+    if (precond != JFNK_PC_NONE && precond != JFNK_PC_NONLINEAR && !h->w2) {
+        CK(cudaStreamSynchronize(h->stream));
+        if (cudaMalloc(&h->w2, h->ld * eT) != cudaSuccess) {
+            cudaGetLastError();
+            h->w2 = nullptr;
             return JFNK_ERR_OOM;
         }
     }

@@ -69,6 +69,23 @@ cudaError_t launch_arnoldi_b(const T* V, size_t ldv, T* w, size_t n, int nv, con
 template <typename T>
 cudaError_t launch_arnoldi_c(T* V, size_t ldv, const T* w, size_t n, int nv, int m, const double* partB,
                              Ctl* ctl, cudaStream_t s);
+// Right-preconditioned path, lagged second projection: pass CA of step j
+// forms v_j from w'_{j-1} (wprev) and pass B's partials of step j-1, runs the
+// Givens update of column j-1, and leaves h1 = [v_0..v_j]^T w_j as partials of
+// arnoldi_ca_parts(n) blocks for launch_arnoldi_b_from.
+template <typename T>
+cudaError_t launch_arnoldi_ca(T* V, size_t ldv, const T* wprev, const T* w, size_t n, int j, int m,
+                              const double* partB, double* partA, Ctl* ctl, cudaStream_t s);
+template <typename T>
+int arnoldi_ca_parts(size_t n);
+template <typename T>
+cudaError_t launch_arnoldi_b_from(const T* V, size_t ldv, T* w, size_t n, int nv, const double* partA, int nblkA,
+                                  double* partB, Ctl* ctl, cudaStream_t s);
+template <typename T>
+int arnoldi_a_parts(size_t n);
+// Givens update of column nv - 1 alone (the last column of a full cycle).
+template <typename T>
+cudaError_t launch_arnoldi_givens(size_t n, int nv, int m, const double* partB, Ctl* ctl, cudaStream_t s);
 template <typename T>
 cudaError_t launch_update(const T* Z, size_t ldz, double* x, T* xT, size_t n, double* part,
                           Ctl* ctl, cudaStream_t s);

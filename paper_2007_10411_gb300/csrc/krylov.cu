@@ -63,6 +63,25 @@ __device__ __forceinline__ int field_of(size_t i, int npt) {
     return i <= 0xffffffffull ? (int)((unsigned)i / (unsigned)npt) : (int)(i / (size_t)npt);
 }
 
+// Order in which a grid-stride loop visits its elements.  The Arnoldi passes
+// alternate direction (A and C backwards on odd j + 1, B backwards on even):
+// each pass then starts on the basis lines the previous pass touched last,
+// which the 129 MB L2 still holds, instead of on the ones it evicted first.
+// A thread visits the same elements either way (only their order changes).
+struct Walk {
+    size_t first, stride, cnt;
+    bool rev;
+    __device__ __forceinline__ size_t at(size_t c) const { return first + (rev ? cnt - 1 - c : c) * stride; }
+};
+__device__ __forceinline__ Walk make_walk(size_t first, size_t stride, size_t n, bool rev) {
+    Walk w;
+    w.first = first;
+    w.stride = stride;
+    w.cnt = first < n ? (n - 1 - first) / stride + 1 : 0;
+    w.rev = rev;
+    return w;
+}
+
 static int stream_blocks(size_t n) {
     size_t b = (n + NTHREADS - 1) / NTHREADS;
     return (int)(b < (size_t)MAX_STREAM_BLOCKS ? (b > 0 ? b : 1) : MAX_STREAM_BLOCKS);
@@ -201,7 +220,9 @@ arnoldi_a(const T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n
     for (int k = 0; k < NV; ++k) acc_t[k] = T(0);
     const size_t nvec = n / W;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvec; i += stride) {
+    const Walk wk = make_walk(blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride, nvec, nv & 1);
+    for (size_t c = 0; c < wk.cnt; ++c) {
+        const size_t i = wk.at(c);
         const VT wv = reinterpret_cast<const VT*>(w)[i];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
@@ -395,9 +416,11 @@ __device__ __forceinline__ void work_b(const VT (&v)[CH], VT wv, T* __restrict__
 template <typename T, int NV>
 __global__ void __launch_bounds__(NTHREADS, 2)
 arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int nv,
-          const double* partA, int nblkA, double* part, Ctl* ctl) {
+          const double* partA, int nblkA, double* part, Ctl* ctl, int jscale) {
     pdl_wait();
     const int done = ctl->done;     // no writer during this launch; read beside the partials
+    // jscale >= 0: w is used as zscale[jscale] w (lagged second projection, see arnoldi_ca)
+    const T sig = jscale >= 0 ? T(ctl->zscale[jscale]) : T(1);
     constexpr int KS = 4, CH = NV / KS;
     __shared__ double h1d[NV];
     __shared__ T h1s[NV];
@@ -419,26 +442,28 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int 
     const size_t g0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) / KS;
     const size_t gstride = (size_t)gridDim.x * blockDim.x / KS;
     VT vn[CH], wn = zerov<VT>();
-    if (g0 < nvec) {
-        load_b<T, VT, CH>(V, ldv, g0, nv, q, vn);
-        wn = reinterpret_cast<const VT*>(w)[g0];
+    const Walk wk = make_walk(g0, gstride, nvec, !(nv & 1));
+    if (wk.cnt > 0) {
+        load_b<T, VT, CH>(V, ldv, wk.at(0), nv, q, vn);
+        wn = scalev(reinterpret_cast<const VT*>(w)[wk.at(0)], sig);
     }
-    for (size_t i = g0; i < nvec; i += gstride) {
+    for (size_t cc = 0; cc < wk.cnt; ++cc) {
+        const size_t i = wk.at(cc);
         VT v[CH];
 #pragma unroll
         for (int c = 0; c < CH; ++c) v[c] = vn[c];
         const VT wv = wn;
-        const size_t inext = i + gstride;
-        if (inext < nvec) {
+        if (cc + 1 < wk.cnt) {
+            const size_t inext = wk.at(cc + 1);
             load_b<T, VT, CH>(V, ldv, inext, nv, q, vn);
-            wn = reinterpret_cast<const VT*>(w)[inext];
+            wn = scalev(reinterpret_cast<const VT*>(w)[inext], sig);
         }
         work_b<T, VT, CH, KS>(v, wv, w, i, q, h1s, acc, accn);
     }
     for (size_t i = nvec * W + g0; i < n; i += gstride) {
         T v[CH];
         load_b<T, T, CH>(V, ldv, i, nv, q, v);
-        work_b<T, T, CH, KS>(v, w[i], w, i, q, h1s, acc, accn);
+        work_b<T, T, CH, KS>(v, sig * w[i], w, i, q, h1s, acc, accn);
     }
     pdl_trigger();
     // block sums: slot 0 = ||w'||^2, slot 1 + k = v_k . w' (fixed shuffle trees, then the partial type across warps)
@@ -498,7 +523,9 @@ arnoldi_c(T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int 
     const size_t nblk = gridDim.x - 1, blk = blockIdx.x - 1;
     const size_t stride = nblk * blockDim.x;
     T* vout = V + (size_t)nv * ldv;
-    for (size_t i = blk * blockDim.x + threadIdx.x; i < nvec; i += stride) {
+    const Walk wk = make_walk(blk * blockDim.x + threadIdx.x, stride, nvec, nv & 1);
+    for (size_t c = 0; c < wk.cnt; ++c) {
+        const size_t i = wk.at(c);
         VT wp = reinterpret_cast<const VT*>(w)[i];
 #pragma unroll
         for (int k = 0; k < NV; ++k)
@@ -510,6 +537,117 @@ arnoldi_c(T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int 
         for (int k = 0; k < nv; ++k) wp -= hs[k] * V[k * ldv + i];
         vout[i] = wp * inv;
     }
+}
+
+// ---------------------------------------------------------------- pass CA
+// Right-preconditioned path: pass C of step j-1 fused with pass A of step j
+// (the second projection of CGS2 is lagged behind the next Jacobian
+// product).  Step j takes as its direction the once-projected vector of the
+// previous step instead of v_j:  z_j = M^{-1} w'_{j-1},  w_j = J z_j,  with
+// w'_{j-1} = w_{j-1} - V h1 from pass B.  Flexible GMRES accepts any z_j
+// (x = x_0 + Z y minimises ||b - J x|| over span Z for every choice), and for
+// a fixed linear M the span is that of M^{-1} v_0 .. M^{-1} v_j, because
+// w'_{j-1} = h_{j,j-1} v_j + V h2 with V h2 in the span of the earlier basis:
+// the iterates are those of right-preconditioned GMRES in exact arithmetic.
+// One sweep then forms v_j = (w'_{j-1} - V h2) / h_{j,j-1} and the first
+// projection h1 = [v_0 .. v_j]^T w_j of step j, reading every basis vector
+// once; block 0 runs the Hessenberg / Givens update of column j-1 (as pass
+// C's block 0 does).  Partials (j + 1 values) are indexed by streaming block.
+template <typename T, int NV>
+__global__ void __launch_bounds__(NTHREADS, 2)
+arnoldi_ca(T* __restrict__ V, size_t ldv, const T* __restrict__ wprev, const T* __restrict__ w, size_t n,
+           int j, int m, const double* partB, int nblkB, double* partA, Ctl* ctl) {
+    pdl_wait();
+    using VT = typename V4<T>::type;
+    using P = typename PartOf<T>::type;
+    constexpr int W = V4<T>::W;
+    __shared__ double tot[NV + 1];
+    __shared__ T tots[NV + 1];      // tots[1 + k] = h2_k rounded to T
+    __shared__ T inv_s;
+    __shared__ int done;
+    __shared__ T red[NV + 1][NTHREADS / 32];
+    // block 0 writes ctl->done during this launch: one thread reads it for the whole block
+    if (threadIdx.x == 0) done = *(volatile int*)&ctl->done;
+    grid_sums(reinterpret_cast<const P*>(partB), nblkB, j + 1, tot, tots);   // ||w'||^2, h2_0 .. h2_{j-1}
+    if (done) return;
+    if (blockIdx.x == 0) {
+        givens_update(ctl, j - 1, m, tot + 1, tot[0]);
+        return;
+    }
+    const T* hs = tots + 1;
+    __shared__ T sig_s;
+    if (threadIdx.x < 32) {
+        const double hn2 = subdiag2(tot + 1, j, tot[0]);
+        const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
+        if (threadIdx.x == 0) {
+            inv_s = T(hn > 0.0 ? 1.0 / hn : 0.0);
+            // z_j = M^{-1} w'_{j-1} carries the scale ||w'_{j-1}||: w_j = J z_j is used
+            // as sigma w_j with sigma = 1 / ||w'_{j-1}||, and z_j enters the update as sigma z_j
+            const double sg = tot[0] > 0.0 ? 1.0 / sqrt(tot[0]) : 0.0;
+            sig_s = T(sg);
+            if (blockIdx.x == 1) ctl->zscale[j] = (double)T(sg);
+        }
+    }
+    __syncthreads();
+    const T inv = inv_s;
+    const T sig = sig_s;
+    T acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = T(0);
+    T accn = T(0);                  // v_j . w_j (v_j is formed in registers)
+    const size_t nvec = n / W;
+    const size_t nblk = gridDim.x - 1, blk = blockIdx.x - 1;
+    const size_t stride = nblk * blockDim.x;
+    T* vout = V + (size_t)j * ldv;
+    const Walk wk = make_walk(blk * blockDim.x + threadIdx.x, stride, nvec, (j + 1) & 1);
+    for (size_t c = 0; c < wk.cnt; ++c) {
+        const size_t i = wk.at(c);
+        VT wp = reinterpret_cast<const VT*>(wprev)[i];
+        const VT wv = scalev(reinterpret_cast<const VT*>(w)[i], sig);
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < j) {
+                const VT vk = reinterpret_cast<const VT*>(V + k * ldv)[i];
+                wp = axpyv(wp, hs[k], vk);
+                acc[k] += dotv(vk, wv);
+            }
+        const VT vn = scalev(wp, inv);
+        reinterpret_cast<VT*>(vout)[i] = vn;
+        accn += dotv(vn, wv);
+    }
+    for (size_t i = nvec * W + blk * blockDim.x + threadIdx.x; i < n; i += stride) {
+        T wp = wprev[i];
+        const T wv = sig * w[i];
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+            if (k < j) {
+                const T vk = V[k * ldv + i];
+                wp -= hs[k] * vk;
+                acc[k] += vk * wv;
+            }
+        const T vn = wp * inv;
+        vout[i] = vn;
+        accn += vn * wv;
+    }
+    pdl_trigger();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        if (k < j) {
+            T x = acc[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) red[k][warp] = x;
+        }
+    }
+    {
+        T x = accn;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[j][warp] = x;
+    }
+    __syncthreads();
+    store_partials<T, NV + 1>(red, j + 1, reinterpret_cast<P*>(partA), (int)nblk, (int)blk);
 }
 
 // ---------------------------------------------------------------- update
@@ -532,7 +670,7 @@ update_x(const T* __restrict__ Z, size_t ldz, double* __restrict__ x, T* __restr
     __shared__ double ys[NV];
     __shared__ float yh[NV], yl[NV];
     for (int k = threadIdx.x; k < NV; k += blockDim.x) {
-        const double y = k < K ? ctl->y[k] : 0.0;
+        const double y = k < K ? ctl->y[k] * ctl->zscale[k] : 0.0;
         ys[k] = y;
         yh[k] = (float)y;
         yl[k] = (float)(y - (double)(float)y);
@@ -609,6 +747,7 @@ cycle_init(Geo G, const double* __restrict__ R, T* __restrict__ V0, double* __re
         ctl->k = 0;
         ctl->iters = 0;
         ctl->m = m;
+        for (int k = 0; k < KMAX; ++k) ctl->zscale[k] = 1.0;
         if (pc_none) {
             ctl->eps_jv = sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2)));
             ctl->eps_part = 0;
@@ -652,6 +791,7 @@ restart_scale(T* __restrict__ V0, size_t n, int pc_none, Ctl* ctl) {
         ctl->converged = 0;
         ctl->breakdown = 0;
         ctl->k = 0;
+        for (int k = 0; k < KMAX; ++k) ctl->zscale[k] = 1.0;
         if (pc_none) {
             ctl->eps_jv = sqrt(ctl->eps_mach * (1.0 + sqrt(ctl->unorm2)));
             ctl->eps_part = 0;
@@ -860,6 +1000,13 @@ template <typename T> static int grid_c(size_t n) {
 }
 
 template <typename T>
+int arnoldi_a_parts(size_t n) {
+    return grid_a<T>(n);
+}
+template int arnoldi_a_parts<float>(size_t);
+template int arnoldi_a_parts<double>(size_t);
+
+template <typename T>
 cudaError_t launch_arnoldi_a(const T* V, size_t ldv, const T* w, size_t n, int nv, double* partA,
                              Ctl* ctl, cudaStream_t s) {
     const int nb = grid_a<T>(n);
@@ -872,9 +1019,9 @@ template <typename T>
 cudaError_t launch_arnoldi_b(const T* V, size_t ldv, T* w, size_t n, int nv, const double* partA,
                              double* partB, Ctl* ctl, cudaStream_t s) {
     const int nb = grid_b<T>(n), na = grid_a<T>(n);
-    if (nv <= 8) return launch_pdl(arnoldi_b<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl);
-    if (nv <= 16) return launch_pdl(arnoldi_b<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl);
-    return launch_pdl(arnoldi_b<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl);
+    if (nv <= 8) return launch_pdl(arnoldi_b<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl, -1);
+    if (nv <= 16) return launch_pdl(arnoldi_b<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl, -1);
+    return launch_pdl(arnoldi_b<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl, -1);
 }
 
 template <typename T>
@@ -885,6 +1032,64 @@ cudaError_t launch_arnoldi_c(T* V, size_t ldv, const T* w, size_t n, int nv, int
     if (nv <= 16) return launch_pdl(arnoldi_c<T, 16>, nc, NTHREADS, 0, s, V, ldv, w, n, nv, m, partB, nb, ctl);
     return launch_pdl(arnoldi_c<T, 32>, nc, NTHREADS, 0, s, V, ldv, w, n, nv, m, partB, nb, ctl);
 }
+
+// Fused pass CA of step j (1 <= j < KMAX): the partials it leaves for pass B
+// come from grid_ca_parts() blocks.
+// Two CTAs per SM are resident (register use): the Givens block and the
+// streaming blocks fit one wave.
+constexpr int MAX_CA_BLOCKS = 2 * 152;
+template <typename T> static int grid_ca(size_t n) {
+    return std::min(dot_blocks(n / V4<T>::W), MAX_CA_BLOCKS - 1) + 1;
+}
+template <typename T>
+int arnoldi_ca_parts(size_t n) {
+    return grid_ca<T>(n) - 1;
+}
+template int arnoldi_ca_parts<float>(size_t);
+template int arnoldi_ca_parts<double>(size_t);
+
+template <typename T>
+cudaError_t launch_arnoldi_ca(T* V, size_t ldv, const T* wprev, const T* w, size_t n, int j, int m,
+                              const double* partB, double* partA, Ctl* ctl, cudaStream_t s) {
+    const int nc = grid_ca<T>(n), nb = grid_b<T>(n);
+    if (j + 1 <= 8)
+        return launch_pdl(arnoldi_ca<T, 8>, nc, NTHREADS, 0, s, V, ldv, wprev, w, n, j, m, partB, nb, partA, ctl);
+    if (j + 1 <= 16)
+        return launch_pdl(arnoldi_ca<T, 16>, nc, NTHREADS, 0, s, V, ldv, wprev, w, n, j, m, partB, nb, partA, ctl);
+    return launch_pdl(arnoldi_ca<T, 32>, nc, NTHREADS, 0, s, V, ldv, wprev, w, n, j, m, partB, nb, partA, ctl);
+}
+template cudaError_t launch_arnoldi_ca<float>(float*, size_t, const float*, const float*, size_t, int, int,
+                                              const double*, double*, Ctl*, cudaStream_t);
+template cudaError_t launch_arnoldi_ca<double>(double*, size_t, const double*, const double*, size_t, int, int,
+                                               const double*, double*, Ctl*, cudaStream_t);
+
+// Pass B whose h1 partials come from nblkA blocks (pass A: grid_a; pass CA: arnoldi_ca_parts).
+template <typename T>
+cudaError_t launch_arnoldi_b_from(const T* V, size_t ldv, T* w, size_t n, int nv, const double* partA, int nblkA,
+                                  double* partB, Ctl* ctl, cudaStream_t s) {
+    const int nb = grid_b<T>(n);
+    const int js = nv > 1 ? nv - 1 : -1;    // step j = nv - 1 >= 1 follows pass CA: w is scaled
+    if (nv <= 8) return launch_pdl(arnoldi_b<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, nblkA, partB, ctl, js);
+    if (nv <= 16) return launch_pdl(arnoldi_b<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, nblkA, partB, ctl, js);
+    return launch_pdl(arnoldi_b<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, nblkA, partB, ctl, js);
+}
+template cudaError_t launch_arnoldi_b_from<float>(const float*, size_t, float*, size_t, int, const double*, int,
+                                                  double*, Ctl*, cudaStream_t);
+template cudaError_t launch_arnoldi_b_from<double>(const double*, size_t, double*, size_t, int, const double*, int,
+                                                   double*, Ctl*, cudaStream_t);
+
+// The Hessenberg / Givens update of the last column of a cycle alone (pass C
+// with its Givens block and no streaming blocks), after pass B of step nv - 1.
+template <typename T>
+cudaError_t launch_arnoldi_givens(size_t n, int nv, int m, const double* partB, Ctl* ctl, cudaStream_t s) {
+    const int nb = grid_b<T>(n);
+    T* none = nullptr;
+    if (nv <= 8) return launch_pdl(arnoldi_c<T, 8>, 1, NTHREADS, 0, s, none, (size_t)0, (const T*)none, n, nv, m, partB, nb, ctl);
+    if (nv <= 16) return launch_pdl(arnoldi_c<T, 16>, 1, NTHREADS, 0, s, none, (size_t)0, (const T*)none, n, nv, m, partB, nb, ctl);
+    return launch_pdl(arnoldi_c<T, 32>, 1, NTHREADS, 0, s, none, (size_t)0, (const T*)none, n, nv, m, partB, nb, ctl);
+}
+template cudaError_t launch_arnoldi_givens<float>(size_t, int, int, const double*, Ctl*, cudaStream_t);
+template cudaError_t launch_arnoldi_givens<double>(size_t, int, int, const double*, Ctl*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_update(const T* Z, size_t ldz, double* x, T* xT, size_t n, double* part,

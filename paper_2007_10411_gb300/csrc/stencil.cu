@@ -41,11 +41,14 @@ template <> struct Tile<float>  { static constexpr int TX = 64, TZ = 16; };
 // Candidate tiles of the Jacobian-product and preconditioner kernels (float32
 // path); jfnk_autotune times each on the handle's workload and keeps the
 // fastest (Geo::tile_jv, Geo::tile_pc).  The float64 path uses the first entry.
-template <int I> struct JvTile;
+template <int I> struct JvTile;          // float64 Jacobian product (jv_diff2d): entry 1
 template <> struct JvTile<0> { static constexpr int TX = 32, TZ = 16; };
 template <> struct JvTile<1> { static constexpr int TX = 32, TZ = 8; };
-template <> struct JvTile<2> { static constexpr int TX = 64, TZ = 8; };
-template <> struct JvTile<3> { static constexpr int TX = 16, TZ = 16; };
+template <int I> struct JvcTile;         // float32 Jacobian product (jvc2d): tile and staging buffers
+template <> struct JvcTile<0> { static constexpr int TX = 32, TZ = 16, NBUF = 1; };
+template <> struct JvcTile<1> { static constexpr int TX = 32, TZ = 16, NBUF = 2; };
+template <> struct JvcTile<2> { static constexpr int TX = 64, TZ = 8, NBUF = 1; };
+template <> struct JvcTile<3> { static constexpr int TX = 32, TZ = 8, NBUF = 1; };
 template <int I> struct PcTile;
 template <> struct PcTile<0> { static constexpr int TX = 64, TZ = 16; };
 template <> struct PcTile<1> { static constexpr int TX = 32, TZ = 16; };
@@ -219,6 +222,21 @@ __device__ __forceinline__ int eddy_row(int qz, int z0, int nz, int QZ) {
     return (iq >= 0 && iq < QZ) ? iq : -1;
 }
 
+// Explicitly rounded product and fused multiply-add: expressions written with
+// them round the same way in every instantiation (tile shape) of a kernel.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Deardorff heat factor s (1 + a l(s)), l = min(Delta, c_l s) (c_l < 0: l = Delta).
+template <typename T>
+__device__ __forceinline__ T dd_heat(T s, T a, const Geo& G) {
+    const T cls = rmul(T(G.dd_cl), s);
+    const T l = G.dd_cl < 0.0 ? T(G.dd_delta) : (cls < T(G.dd_delta) ? cls : T(G.dd_delta));
+    return rmul(s, rfma(a, l, T(1)));
+}
+
 template <typename T>
 __device__ __forceinline__ T smag_nu(T ux, T uz, T wx, T wz, T cs2) {
     const T s13 = T(0.5) * (uz + wx);
@@ -242,7 +260,9 @@ stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s1 = reinterpret_cast<T*>(smem_raw);
     T* d = s1 + 4 * SZ * SX;
-    T* nu = d + 6 * QN;
+    T* nu = d + 6 * QN;                  // Smagorinsky nu, or the strain s (Deardorff)
+    T* gh = nu + QN;                     // Deardorff: s (1 + a_h l) and s (1 + a_z l)
+    T* gH = gh + QN;
     const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
     const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
 
@@ -266,7 +286,7 @@ stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
     first_derivs(s1, d, SX, SZ, QX, QZ, idx_, idz_);
     __syncthreads();
     if (SMAG) {
-        const T cs2 = T(G.cs2);
+        const T cs2 = SMAG == 2 ? T(1) : T(G.cs2);     // Deardorff: the strain s = sqrt(2 S:S) itself
         for (int w = threadIdx.x; w < QN; w += blockDim.x) {
             int qz, qx;
             halo_item(w, QX, QZ, qz, qx);
@@ -278,6 +298,10 @@ stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
                 val = smag_nu(d[q], d[QN + q], d[2 * QN + q], d[3 * QN + q], cs2);
             }
             nu[idx] = val;
+            if (SMAG == 2) {
+                gh[idx] = dd_heat(val, T(G.dd_ah), G);
+                gH[idx] = dd_heat(val, T(G.dd_az), G);
+            }
         }
         __syncthreads();
     }
@@ -315,7 +339,13 @@ stencil2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
                      T(0.5) * (uc * px + wc * pz);
         // eddy diffusion sum_j D_j(K D_j phi)
         T du, dw, dt_;
-        if (SMAG) {
+        if (SMAG == 2) {
+            // anisotropic: D_x(K_m D_x phi) + D_z(K_M D_z phi), heat with K_h, K_H
+            const T cm = T(G.dd_cm), cM = T(G.dd_cM);
+            du = cm * ddp(nu, dux, q, 1, idx_) + cM * ddp(nu, duz, q, QX, idz_);
+            dw = cm * ddp(nu, dwx, q, 1, idx_) + cM * ddp(nu, dwz, q, QX, idz_);
+            dt_ = cm * ddp(gh, dtx, q, 1, idx_) + cM * ddp(gH, dtz, q, QX, idz_);
+        } else if (SMAG) {
             du = ddp(nu, dux, q, 1, idx_) + ddp(nu, duz, q, QX, idz_);
             dw = ddp(nu, dwx, q, 1, idx_) + ddp(nu, dwz, q, QX, idz_);
             dt_ = iPr * (ddp(nu, dtx, q, 1, idx_) + ddp(nu, dtz, q, QX, idz_));
@@ -685,6 +715,376 @@ jv_diff2d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
 }
 
 // ============================================================================
+// Mixed-path Jv, compute-once form (float32 path).
+//
+// Same quantity as jv_diff2d, organised so that every flux is formed once per
+// point and only then differentiated.  With a = u and b = eps V (per field
+// eps scale_f), the difference of F(a + b) - F(a) is, term by term,
+//   convection  1/2 [D_x P_phi + D_z Q_phi] + 1/2 adv_phi,
+//               P_phi = a_u b_phi + b_u (a_phi + b_phi)   (x-flux difference)
+//               Q_phi = a_w b_phi + b_w (a_phi + b_phi)   (z-flux difference)
+//               adv_phi = a_u D_x b_phi + a_w D_z b_phi + b_u D_x phi' + b_w D_z phi'
+//   diffusion   D_x Fx_phi + D_z Fz_phi,
+//               Fx_phi = K_a D_x b_phi + dK D_x phi'  (dK = K(a + b) - K(a), cancellation-free),
+//   point-wise  pressure gradient, buoyancy, stratification, (pbar + p) div u,
+// with phi' = a_phi + b_phi.  Phase 1 stages u and the raw direction v of a
+// TX x TZ tile with a halo of 4 (cp.async, the next tile's copies in flight
+// while this one is computed; the eps scale is applied in registers, so only
+// ghost rows need a pass over the staged planes, for the mirror signs).
+// Phase 2 forms, at every point where they are differentiated, the x-fluxes
+// P, Fx (tile rows, columns -2 .. TX+1) and the z-fluxes Q, Fz (rows -2 ..
+// TZ+1, tile columns), and, at the tile's own points, the point-wise part S
+// (kept in registers).  Phase 3 differentiates the fluxes and writes Jv.
+// Phases 2 and 3 give a thread the same PPT vertically adjacent points of
+// one column (warps run along x: conflict-free shared-memory rows).  Every
+// value at a point is computed by the same expression whatever the tile
+// shape, so all shapes give bitwise the same result.
+// The eddy coefficient at a ghost row is the mirror image of the interior
+// value (K mirrored even): the Smagorinsky step of a flux point in a ghost
+// row is evaluated at its image row.
+// ============================================================================
+template <int TX, int TZ>
+struct JvcShape {
+    static constexpr int SX = TX + 2 * HALO, SZ = TZ + 2 * HALO;
+    static constexpr int PLANE = SX * SZ;
+    static constexpr int STG = 8 * PLANE;                 // u (planes 0-3) and raw v (planes 4-7)
+    static constexpr int PXW = TX + 2 * R;                // x-flux rows: columns -2 .. TX+1
+    static constexpr int PXN = TZ * PXW;                  // per flux field
+    static constexpr int QZN = (TZ + 2 * R) * TX;         // z-flux columns: rows -2 .. TZ+1
+    static constexpr int PPT = TX * TZ / NTHREADS;        // points per thread (one column, PPT rows)
+    static constexpr int NARM = 4 * TX + 4 * TZ;          // z-arm items, then x-arm items
+    static_assert(NTHREADS % TX == 0 && PPT * (NTHREADS / TX) == TZ && PPT >= 1, "tile / thread mapping");
+    static constexpr size_t smem(int nbuf) { return sizeof(float) * ((size_t)nbuf * STG + 7 * PXN + 7 * QZN); }
+};
+
+// Tile row (in staged coordinates, relative to the tile origin) whose eddy
+// value a flux point in tile row iz takes: its mirror image where the global
+// row is a ghost row (-2, -1 or nz, nz+1), else itself.
+__device__ __forceinline__ int jvc_smag_row(int iz, int z0, int nz) {
+    const int gz = z0 + iz;
+    if (gz < 0) return (-1 - gz) - z0;
+    if (gz >= nz && gz <= nz + 1) return (2 * nz - 1 - gz) - z0;
+    return iz;
+}
+
+struct JvcConst {
+    float ev[4];        // eps scale_f: b = ev * v
+    float idx, idz;
+    float cs2, iPr, KM, KH;
+    float cm, cM, cl, dlt, ah, az;   // Deardorff constants (Geo::dd_*)
+};
+
+// The flux and derivative arithmetic of jvc2d is written with explicitly
+// rounded operations (no contraction left to the compiler), so a flux formed
+// in the tile centre and the same flux formed in a neighbouring tile's arm
+// are bitwise equal, and every tile shape gives the same result.
+// w1 = (2/3)/h, w2 = -(1/12)/h (Geo::fx1 .. fz2)
+__device__ __forceinline__ float ddf(const float* s, int i, int st, float w1, float w2) {
+    const float d1 = __fsub_rn(s[i + st], s[i - st]), d2 = __fsub_rn(s[i + 2 * st], s[i - 2 * st]);
+    return __fmaf_rn(w1, d1, __fmul_rn(w2, d2));
+}
+// a0 b + b0 (a + b): the flux difference a'_j phi' - a_j phi
+__device__ __forceinline__ float flux_diff(float a0, float b0, float a, float b) {
+    return __fmaf_rn(a0, b, __fmul_rn(b0, __fadd_rn(a, b)));
+}
+// K b' + dK (a' + b'): the diffusive flux difference
+__device__ __forceinline__ float kflux_diff(float kk, float dk, float da, float db) {
+    return __fmaf_rn(kk, db, __fmul_rn(dk, __fadd_rn(da, db)));
+}
+
+// The strain magnitude s = sqrt(2 S:S) at a, at a' = a + b, and their
+// difference ds = s' - s in cancellation-free form, from the velocity
+// gradients of a (ux, uz, wx, wz) and of b.
+__device__ __forceinline__ void jvc_strain(float aux, float auz, float awx, float awz, float bux, float buz,
+                                           float bwx, float bwz, float& sa, float& sp, float& ds) {
+    const float a13 = __fmul_rn(0.5f, __fadd_rn(auz, awx)), b13 = __fmul_rn(0.5f, __fadd_rn(buz, bwx));
+    const float ssa = __fmaf_rn(aux, aux, __fmaf_rn(awz, awz, __fmul_rn(2.f, __fmul_rn(a13, a13))));
+    // S':S' - S:S = (2 S + S_b) : S_b
+    const float dss = __fmaf_rn(__fmaf_rn(2.f, aux, bux), bux,
+                                __fmaf_rn(__fmaf_rn(2.f, awz, bwz), bwz,
+                                          __fmul_rn(2.f, __fmul_rn(__fmaf_rn(2.f, a13, b13), b13))));
+    // square roots and the quotient by the special-function unit (x rsqrt(x), a / b via
+    // the approximate reciprocal): a few ulp, deterministic
+    const float s1 = __fmul_rn(2.f, ssa);
+    sa = s1 > 0.f ? __fmul_rn(s1, rsqrtf(s1)) : 0.f;
+    const float s2 = __fmul_rn(2.f, __fadd_rn(ssa, dss));
+    sp = s2 > 0.f ? __fmul_rn(s2, rsqrtf(s2)) : 0.f;
+    // s' - s = 2 (S':S' - S:S) / (s' + s)
+    const float den = __fadd_rn(sa, sp);
+    ds = den > 0.f ? __fdividef(__fmul_rn(2.f, dss), den) : 0.f;
+}
+
+// Deardorff heat factor g(s) = s (1 + a l(s)), l = min(Delta, c_l s), at s and
+// its difference g(s') - g(s) = ds (1 + a l') + a s (l' - l), with l' - l = c_l ds
+// where neither side is capped (0 where both are; direct where they straddle).
+__device__ __forceinline__ void jvc_heat(float sa, float sp, float ds, float a, const JvcConst& k, float& g,
+                                         float& dg) {
+    float la = k.dlt, lp = k.dlt, dl = 0.f;
+    if (k.cl >= 0.f) {
+        const float ta = __fmul_rn(k.cl, sa), tp = __fmul_rn(k.cl, sp);
+        la = ta < k.dlt ? ta : k.dlt;
+        lp = tp < k.dlt ? tp : k.dlt;
+        if (ta < k.dlt && tp < k.dlt) dl = __fmul_rn(k.cl, ds);
+        else if (ta < k.dlt || tp < k.dlt) dl = __fsub_rn(lp, la);
+    }
+    g = __fmul_rn(sa, __fmaf_rn(a, la, 1.f));
+    dg = __fmaf_rn(ds, __fmaf_rn(a, lp, 1.f), __fmul_rn(__fmul_rn(a, sa), dl));
+}
+
+// Phase 2 at one point.  i: staged index of the point; is: staged index of the
+// point whose eddy coefficient it takes (its image in a ghost row).  XF: the
+// x-fluxes P, Fx; ZF: the z-fluxes Q, Fz; CEN: also the point-wise part S.
+template <int SMAG, bool XF, bool ZF, bool CEN, int SX, int PLANE>
+__device__ __forceinline__ void jvc_point(const float* __restrict__ st, int i, int is, const JvcConst& k,
+                                          const Geo& G, float (&P)[4], float (&Fx)[3], float (&Q)[4],
+                                          float (&Fz)[3], float (&S)[4], float (&vraw)[4]) {
+    const float* A = st;                 // a planes 0..3
+    const float* V = st + 4 * PLANE;     // raw v planes 0..3
+    float a[4], b[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        a[f] = A[f * PLANE + i];
+        vraw[f] = V[f * PLANE + i];
+        b[f] = __fmul_rn(k.ev[f], vraw[f]);
+    }
+    // first derivatives at the point (b-derivatives scaled by ev in registers)
+    constexpr bool DXUW = XF || CEN || SMAG, DZUW = ZF || CEN || SMAG;
+    constexpr bool DXT = XF || CEN, DZT = ZF || CEN;
+    float dax[4] = {0.f, 0.f, 0.f, 0.f}, daz[4] = {0.f, 0.f, 0.f, 0.f};
+    float dbx[4] = {0.f, 0.f, 0.f, 0.f}, dbz[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const bool wx = f < 2 ? DXUW : (f == 2 ? DXT : CEN);
+        const bool wz = f < 2 ? DZUW : (f == 2 ? DZT : CEN);
+        if (wx) {
+            dax[f] = ddf(A + f * PLANE, i, 1, G.fx1, G.fx2);
+            dbx[f] = __fmul_rn(k.ev[f], ddf(V + f * PLANE, i, 1, G.fx1, G.fx2));
+        }
+        if (wz) {
+            daz[f] = ddf(A + f * PLANE, i, SX, G.fz1, G.fz2);
+            dbz[f] = __fmul_rn(k.ev[f], ddf(V + f * PLANE, i, SX, G.fz1, G.fz2));
+        }
+    }
+    // exchange coefficients along x and z, momentum [0] and heat [1], and their differences
+    float kx[2], dkx[2], kz[2], dkz[2];
+    if (SMAG) {
+        float sa, sp, ds;
+        if (is == i) {
+            jvc_strain(dax[0], daz[0], dax[1], daz[1], dbx[0], dbz[0], dbx[1], dbz[1], sa, sp, ds);
+        } else {
+            jvc_strain(ddf(A, is, 1, G.fx1, G.fx2), ddf(A, is, SX, G.fz1, G.fz2), ddf(A + PLANE, is, 1, G.fx1, G.fx2),
+                       ddf(A + PLANE, is, SX, G.fz1, G.fz2), __fmul_rn(k.ev[0], ddf(V, is, 1, G.fx1, G.fx2)),
+                       __fmul_rn(k.ev[0], ddf(V, is, SX, G.fz1, G.fz2)),
+                       __fmul_rn(k.ev[1], ddf(V + PLANE, is, 1, G.fx1, G.fx2)),
+                       __fmul_rn(k.ev[1], ddf(V + PLANE, is, SX, G.fz1, G.fz2)), sa, sp, ds);
+        }
+        if (SMAG == 2) {
+            kx[0] = __fmul_rn(k.cm, sa); dkx[0] = __fmul_rn(k.cm, ds);
+            kz[0] = __fmul_rn(k.cM, sa); dkz[0] = __fmul_rn(k.cM, ds);
+            float g, dg;
+            jvc_heat(sa, sp, ds, k.ah, k, g, dg);
+            kx[1] = __fmul_rn(k.cm, g); dkx[1] = __fmul_rn(k.cm, dg);
+            jvc_heat(sa, sp, ds, k.az, k, g, dg);
+            kz[1] = __fmul_rn(k.cM, g); dkz[1] = __fmul_rn(k.cM, dg);
+        } else {
+            const float ka = __fmul_rn(k.cs2, sa), dk = __fmul_rn(k.cs2, ds);
+            kx[0] = kz[0] = ka; dkx[0] = dkz[0] = dk;
+            kx[1] = kz[1] = __fmul_rn(ka, k.iPr); dkx[1] = dkz[1] = __fmul_rn(dk, k.iPr);
+        }
+    } else {
+        kx[0] = kz[0] = k.KM; kx[1] = kz[1] = k.KH;
+        dkx[0] = dkz[0] = dkx[1] = dkz[1] = 0.f;
+    }
+    if (XF) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) P[f] = flux_diff(a[0], b[0], a[f], b[f]);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const int c = f == 2 ? 1 : 0;
+            Fx[f] = SMAG ? kflux_diff(kx[c], dkx[c], dax[f], dbx[f]) : __fmul_rn(kx[c], dbx[f]);
+        }
+    }
+    if (ZF) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) Q[f] = flux_diff(a[1], b[1], a[f], b[f]);
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            const int c = f == 2 ? 1 : 0;
+            Fz[f] = SMAG ? kflux_diff(kz[c], dkz[c], daz[f], dbz[f]) : __fmul_rn(kz[c], dbz[f]);
+        }
+    }
+    if (CEN) {
+        const float th0 = (float)G.theta0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            // a_u D_x b + a_w D_z b + b_u D_x phi' + b_w D_z phi'
+            const float adv = __fmaf_rn(a[0], dbx[f], __fmaf_rn(a[1], dbz[f],
+                              __fmaf_rn(b[0], __fadd_rn(dax[f], dbx[f]), __fmul_rn(b[1], __fadd_rn(daz[f], dbz[f])))));
+            S[f] = __fmul_rn(-0.5f, adv);
+        }
+        const float gth = (float)(G.g / G.theta0);
+        S[0] = __fmaf_rn(-th0, dbx[3], S[0]);
+        S[1] = __fmaf_rn(-th0, dbz[3], __fmaf_rn(gth, b[2], S[1]));
+        S[2] = __fmaf_rn(-(float)G.beta, b[1], S[2]);
+        const float diva = __fadd_rn(dax[0], daz[1]), divb = __fadd_rn(dbx[0], dbz[1]);
+        const float pp = __fadd_rn(__fadd_rn((float)G.pbar, a[3]), b[3]);
+        S[3] = __fmaf_rn(-(float)G.gamma_p, __fmaf_rn(pp, divb, __fmul_rn(b[3], diva)), S[3]);
+    }
+}
+
+template <int SMAG, int TX, int TZ, int NBUF>
+__global__ void __launch_bounds__(NTHREADS)
+jvc2d(Geo G, const float* __restrict__ u, const float* __restrict__ v, float* __restrict__ out,
+      const double* part, Ctl* ctl, int check_done) {
+    using SH = JvcShape<TX, TZ>;
+    constexpr int SX = SH::SX, PLANE = SH::PLANE, PXW = SH::PXW, PXN = SH::PXN, QZN = SH::QZN;
+    constexpr int PPT = SH::PPT;
+    pdl_wait();
+    if (check_done && ctl->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* stg = reinterpret_cast<float*>(smem_raw);
+    float* PX = stg + NBUF * SH::STG;    // [4][TZ][PXW] then Fx [3][TZ][PXW]
+    float* FX = PX + 4 * PXN;
+    float* QZ = FX + 3 * PXN;            // [4][TZ+4][TX] then Fz [3][TZ+4][TX]
+    float* FZ = QZ + 4 * QZN;
+    const int ntx = (G.nx + TX - 1) / TX;
+    const int ntiles = ntx * ((G.nz + TZ - 1) / TZ);
+    int t = blockIdx.x;
+    if (t < ntiles) jv_stage_issue(stg, u, v, G, (t % ntx) * TX, (t / ntx) * TZ, SX, SH::SZ);
+    cpa_commit();
+    const double eps = pending_eps(ctl, part);
+    __shared__ float evs[4], cfs[4];
+    if (threadIdx.x < 4) {
+        const double e = eps * G.scale[threadIdx.x];
+        evs[threadIdx.x] = (float)e;
+        cfs[threadIdx.x] = (float)(e != 0.0 ? 1.0 / e : 0.0);
+    }
+    __syncthreads();
+    JvcConst k;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) k.ev[f] = evs[f];
+    k.idx = (float)G.inv_dx;
+    k.idz = (float)G.inv_dz;
+    k.cs2 = (float)G.cs2;
+    k.iPr = (float)G.inv_Pr;
+    k.KM = (float)G.K_M;
+    k.KH = (float)G.K_H;
+    k.cm = (float)G.dd_cm;
+    k.cM = (float)G.dd_cM;
+    k.cl = (float)G.dd_cl;
+    k.dlt = (float)G.dd_delta;
+    k.ah = (float)G.dd_ah;
+    k.az = (float)G.dd_az;
+    const float tdt = (float)G.two_over_dt;
+    const int col = threadIdx.x % TX, r0 = (threadIdx.x / TX) * PPT;
+    for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+        const int x0 = (t % ntx) * TX, z0 = (t / ntx) * TZ;
+        float* sa = stg + (NBUF == 2 ? (it & 1) * SH::STG : 0);
+        if (NBUF == 2) {
+            // double buffer: the next tile's copies go out before this tile is computed
+            const int tn = t + gridDim.x;
+            if (tn < ntiles)
+                jv_stage_issue(stg + ((it + 1) & 1) * SH::STG, u, v, G, (tn % ntx) * TX, (tn / ntx) * TZ, SX,
+                               SH::SZ);
+            cpa_commit();
+            cpa_wait<1>();
+        } else {
+            cpa_wait<0>();
+        }
+        __syncthreads();
+        if (z0 - HALO < 0 || z0 + TZ + HALO > G.nz) {
+            // mirror signs of the ghost rows (u and v planes alike)
+            for (int e = threadIdx.x; e < SH::SZ * SX; e += blockDim.x) {
+                const int iz = e / SX;
+                int side;
+                const int sz = mirror_z(z0 + iz - HALO, G.nz, side);
+                if (side == 0 || sz < 0 || sz >= G.nz) continue;
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    const float sg = side == 1 ? (float)G.pb[f] : (float)G.pt[f];
+                    if (sg != 1.f) {
+                        sa[f * PLANE + e] *= sg;
+                        sa[(4 + f) * PLANE + e] *= sg;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // phase 2a: this thread's points (fluxes of every kind, S and the raw direction)
+        float Sv[PPT][4], Vc[PPT][4];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            const int iz = r0 + q;
+            const int i = (iz + HALO) * SX + col + HALO;
+            const int is = SMAG ? (jvc_smag_row(iz, z0, G.nz) + HALO) * SX + col + HALO : i;
+            float P[4], Fx[3], Q[4], Fz[3];
+            jvc_point<SMAG, true, true, true, SX, PLANE>(sa, i, is, k, G, P, Fx, Q, Fz, Sv[q], Vc[q]);
+            const int ip = iz * PXW + col + R, iq = (iz + R) * TX + col;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) { PX[f * PXN + ip] = P[f]; QZ[f * QZN + iq] = Q[f]; }
+#pragma unroll
+            for (int f = 0; f < 3; ++f) { FX[f * PXN + ip] = Fx[f]; FZ[f * QZN + iq] = Fz[f]; }
+        }
+        // phase 2b: the arms -- z-fluxes of rows -2, -1, TZ, TZ+1; x-fluxes of columns -2, -1, TX, TX+1
+        for (int w = threadIdx.x; w < SH::NARM; w += blockDim.x) {
+            float P[4], Fx[3], Q[4], Fz[3], S_[4], V_[4];
+            if (w < 4 * TX) {
+                const int a = w / TX, cx = w - a * TX;
+                const int iz = a < 2 ? a - 2 : TZ + a - 2;
+                const int i = (iz + HALO) * SX + cx + HALO;
+                const int is = SMAG ? (jvc_smag_row(iz, z0, G.nz) + HALO) * SX + cx + HALO : i;
+                jvc_point<SMAG, false, true, false, SX, PLANE>(sa, i, is, k, G, P, Fx, Q, Fz, S_, V_);
+                const int iq = (iz + R) * TX + cx;
+#pragma unroll
+                for (int f = 0; f < 4; ++f) QZ[f * QZN + iq] = Q[f];
+#pragma unroll
+                for (int f = 0; f < 3; ++f) FZ[f * QZN + iq] = Fz[f];
+            } else {
+                const int w2 = w - 4 * TX;
+                const int a = w2 / TZ, iz = w2 - a * TZ;
+                const int cx = a < 2 ? a - 2 : TX + a - 2;
+                const int i = (iz + HALO) * SX + cx + HALO;
+                const int is = SMAG ? (jvc_smag_row(iz, z0, G.nz) + HALO) * SX + cx + HALO : i;
+                jvc_point<SMAG, true, false, false, SX, PLANE>(sa, i, is, k, G, P, Fx, Q, Fz, S_, V_);
+                const int ip = iz * PXW + cx + R;
+#pragma unroll
+                for (int f = 0; f < 4; ++f) PX[f * PXN + ip] = P[f];
+#pragma unroll
+                for (int f = 0; f < 3; ++f) FX[f * PXN + ip] = Fx[f];
+            }
+        }
+        __syncthreads();
+        if (NBUF == 1) {
+            // single buffer: the staged planes are dead now; the next tile's copies
+            // land while this one's fluxes are differentiated
+            const int tn = t + gridDim.x;
+            if (tn < ntiles) jv_stage_issue(stg, u, v, G, (tn % ntx) * TX, (tn / ntx) * TZ, SX, SH::SZ);
+            cpa_commit();
+        }
+        // phase 3: differentiate the fluxes, add S, write J v = 2 v / dt - dF / (eps scale_f)
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            const int iz = r0 + q;
+            const int gz = z0 + iz, gx = x0 + col;
+            if (gz >= G.nz || gx >= G.nx) continue;
+            const int ip = iz * PXW + col + R, iq = (iz + R) * TX + col;
+            const size_t o = (size_t)gz * G.nx + gx;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const float conv = __fadd_rn(ddf(PX + f * PXN, ip, 1, G.fx1, G.fx2),
+                                             ddf(QZ + f * QZN, iq, TX, G.fz1, G.fz2));
+                float dF = __fmaf_rn(-0.5f, conv, Sv[q][f]);
+                if (f < 3)
+                    dF = __fadd_rn(dF, __fadd_rn(ddf(FX + f * PXN, ip, 1, G.fx1, G.fx2),
+                                                 ddf(FZ + f * QZN, iq, TX, G.fz1, G.fz2)));
+                out[(size_t)f * G.npt + o] = __fmaf_rn(tdt, Vc[q][f], __fmul_rn(-cfs[f], dF));
+            }
+        }
+        __syncthreads();     // staging buffer and flux arrays are reused by the next tile
+    }
+}
+
+// ============================================================================
 // Smagorinsky eddy field nu(u) at every point (preconditioner input) + max
 // ============================================================================
 template <typename T>
@@ -692,7 +1092,7 @@ __global__ void __launch_bounds__(NTHREADS)
 eddy2d(Geo G, const T* __restrict__ u, T* __restrict__ nu, double* part, Ctl* ctl) {
     T mxT = T(0);
     const T idx_ = T(G.inv_dx), idz_ = T(G.inv_dz);
-    const T cs2 = T(G.cs2);
+    const T cs2 = G.sgs == 2 ? T(1) : T(G.cs2);     // Deardorff: the strain s (coefficients follow from it)
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < G.npt; p += gridDim.x * blockDim.x) {
         const int z = p / G.nx, x = p - z * G.nx;
         T ux = T(0), uz = T(0), wx = T(0), wz = T(0);
@@ -740,11 +1140,23 @@ __global__ void pc_setup(Geo G, int sweeps, Ctl* ctl) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     const int fth = G.nf - 2, fp = G.nf - 1;         // theta and p
     const double h2 = G.inv_dx * G.inv_dx + G.inv_dz * G.inv_dz + (G.dim == 3 ? G.inv_dy * G.inv_dy : 0.0);
+    // Deardorff: ctl->kmax is the largest strain s; every coefficient grows with s
+    const double smax = ctl->kmax;
+    const double lmax = G.dd_cl < 0.0 ? G.dd_delta : fmin(G.dd_delta, G.dd_cl * smax);
+    const double hh2 = G.inv_dx * G.inv_dx + (G.dim == 3 ? G.inv_dy * G.inv_dy : 0.0);
     for (int f = 0; f < G.nf; ++f) {
         const double lo = G.two_over_dt;
-        double kmax = 0.0;
-        if (f != fp) kmax = G.smag ? ctl->kmax * (f == fth ? G.inv_Pr : 1.0) : (f == fth ? G.K_H : G.K_M);
-        const double hi = lo + 2.25 * kmax * h2;
+        double kh2 = 0.0;        // sum_j max K_j / h_j^2
+        if (f != fp) {
+            if (G.sgs == 2) {
+                const double fh = f == fth ? 1.0 + G.dd_ah * lmax : 1.0;
+                const double fz = f == fth ? 1.0 + G.dd_az * lmax : 1.0;
+                kh2 = G.dd_cm * smax * fh * hh2 + G.dd_cM * smax * fz * G.inv_dz * G.inv_dz;
+            } else {
+                kh2 = (G.smag ? ctl->kmax * (f == fth ? G.inv_Pr : 1.0) : (f == fth ? G.K_H : G.K_M)) * h2;
+            }
+        }
+        const double hi = lo + 2.25 * kh2;
         const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
         const bool degenerate = delta <= 1e-14 * theta;
         const double sigma = degenerate ? 1.0 : theta / delta;
@@ -801,7 +1213,8 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
     T* zs = reinterpret_cast<T*>(smem_raw);      // [SZ][SX] current iterate, halo 2r
     T* gxs = zs + SZ * SX;                          // [TZ][QX] D_x z on tile rows
     T* gzs = gxs + TZ * QX;                         // [QZ][TX] D_z z on tile columns
-    T* kk_ = gzs + QZ * TX;                         // [QZ][QX] eddy coefficient (Smagorinsky)
+    T* kk_ = gzs + QZ * TX;                         // [QZ][QX] eddy coefficient (along x for Deardorff)
+    T* kz_ = SMAG == 2 ? kk_ + QZ * QX : kk_;       // [QZ][QX] Deardorff coefficient along z
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int fld = blockIdx.z;                     // 0 u, 1 w, 2 theta, 3 p (last sweep only)
     const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
@@ -845,7 +1258,22 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
         } else {
             load_fields<T, 0, 1>(zs, zin, nullptr, sc, G, x0, z0, SX, SZ, fld);
         }
-        if (SMAG) {
+        if (SMAG == 2) {
+            // Deardorff: nu holds the strain s; K_m = c_m s along x, K_M = c_M s along z,
+            // heat K_h = c_m s (1 + a_h l), K_H = c_M s (1 + a_z l)
+            const T cm = T(G.dd_cm), cM = T(G.dd_cM);
+            for (int qz = ty; qz < QZ; qz += TY) {
+                int side;
+                const int szr = mirror_z(z0 + qz - R, G.nz, side);
+                const bool ok = szr >= 0 && szr < G.nz;
+                const T* nrow = nu + szr * G.nx;
+                for (int qx = tx; qx < QX; qx += TX) {
+                    const T sv = ok ? nrow[wrap_x(x0 + qx - R, G.nx)] : T(0);
+                    kk_[qz * QX + qx] = rmul(cm, fld == 2 ? dd_heat(sv, T(G.dd_ah), G) : sv);
+                    kz_[qz * QX + qx] = rmul(cM, fld == 2 ? dd_heat(sv, T(G.dd_az), G) : sv);
+                }
+            }
+        } else if (SMAG) {
             const T kscale = fld == 2 ? T(G.inv_Pr) : T(1);
             for (int qz = ty; qz < QZ; qz += TY) {
                 int side;
@@ -878,10 +1306,11 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
                 T difx, difz;
                 if (SMAG) {
                     const T* kx = kk_ + (tz + R) * QX + tx + R;
+                    const T* kz = kz_ + (tz + R) * QX + tx + R;
                     difx = T(2.0 / 3.0) * (kx[1] * gxr[1] - kx[-1] * gxr[-1]) -
                            T(1.0 / 12.0) * (kx[2] * gxr[2] - kx[-2] * gxr[-2]);
-                    difz = T(2.0 / 3.0) * (kx[QX] * gzc[TX] - kx[-QX] * gzc[-TX]) -
-                           T(1.0 / 12.0) * (kx[2 * QX] * gzc[2 * TX] - kx[-2 * QX] * gzc[-2 * TX]);
+                    difz = T(2.0 / 3.0) * (kz[QX] * gzc[TX] - kz[-QX] * gzc[-TX]) -
+                           T(1.0 / 12.0) * (kz[2 * QX] * gzc[2 * TX] - kz[-2 * QX] * gzc[-2 * TX]);
                 } else {
                     difx = Kc * (T(2.0 / 3.0) * (gxr[1] - gxr[-1]) - T(1.0 / 12.0) * (gxr[2] - gxr[-2]));
                     difz = Kc * (T(2.0 / 3.0) * (gzc[TX] - gzc[-TX]) - T(1.0 / 12.0) * (gzc[2 * TX] - gzc[-2 * TX]));
@@ -1276,10 +1705,11 @@ template <typename T> int stencil_blocks(const Geo& G) {
 template int stencil_blocks<float>(const Geo&);
 template int stencil_blocks<double>(const Geo&);
 
-template <typename T>
+template <typename T, int SMAG>
 static size_t stencil_smem() {
     constexpr int TX = Tile<T>::TX, TZ = Tile<T>::TZ;
-    return sizeof(T) * (4 * (TZ + 2 * HALO) * (TX + 2 * HALO) + 7 * (TX + 2 * R) * (TZ + 2 * R));
+    constexpr int NQ = SMAG == 2 ? 9 : 7;        // derivatives (6) + eddy field(s)
+    return sizeof(T) * (4 * (TZ + 2 * HALO) * (TX + 2 * HALO) + NQ * (TX + 2 * R) * (TZ + 2 * R));
 }
 
 template <typename T, int TX, int TZ, int NBUF>
@@ -1297,7 +1727,7 @@ static cudaError_t launch_stencil_t(const Geo& G, const T* u, const T* v, const 
                                     const double* f, T* out, T* out2, double* part, Ctl* ctl,
                                     int check_done, cudaStream_t s) {
     static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
-    const size_t sm = stencil_smem<T>();
+    const size_t sm = stencil_smem<T, SMAG>();
     if (!configured) {
         cudaError_t e = set_smem(stencil2d<T, MODE, SMAG>, sm);
         if (e != cudaSuccess) return e;
@@ -1315,8 +1745,9 @@ cudaError_t launch_stencil(int mode, const Geo& G, const T* u, const T* v, const
     if (G.dim == 3) return launch_stencil3d<T>(mode, G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
 #define JF_CASE(M)                                                                           \
     case M:                                                                                  \
-        return G.smag ? launch_stencil_t<T, M, 1>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s) \
-                      : launch_stencil_t<T, M, 0>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
+        return G.sgs == 2 ? launch_stencil_t<T, M, 2>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s) \
+             : G.smag     ? launch_stencil_t<T, M, 1>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s) \
+                          : launch_stencil_t<T, M, 0>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
     switch (mode) {
         JF_CASE(MODE_F)
         JF_CASE(MODE_RHS)
@@ -1357,16 +1788,50 @@ static cudaError_t launch_jvd_t(const Geo& G, const T* u, const T* v, T* out, co
                       (const double*)part, ctl, check_done);
 }
 
+// float32: the compute-once kernel jvc2d, persistent (one CTA per resident
+// slot, capped at the tile count), double-buffered staging.
+template <int SMAG, int TX, int TZ, int NBUF>
+static cudaError_t launch_jvc_t(const Geo& G, const float* u, const float* v, float* out, const double* part,
+                                Ctl* ctl, int check_done, cudaStream_t s) {
+    static std::atomic<int> slots{0};   // resident CTAs on the device; set once (races are benign)
+    const size_t sm = JvcShape<TX, TZ>::smem(NBUF);
+    if (slots.load() == 0) {
+        cudaError_t e = set_smem(jvc2d<SMAG, TX, TZ, NBUF>, sm);
+        if (e != cudaSuccess) return e;
+        int dev = 0, nsm = 0, per = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jvc2d<SMAG, TX, TZ, NBUF>, NTHREADS, sm)) !=
+                cudaSuccess)
+            return e;
+        slots = std::max(1, nsm * per);
+    }
+    const int ntiles = ((G.nx + TX - 1) / TX) * ((G.nz + TZ - 1) / TZ);
+    const int grid = std::min(ntiles, slots.load());
+    return launch_pdl(jvc2d<SMAG, TX, TZ, NBUF>, dim3(grid), NTHREADS, sm, s, G, u, v, out, part, ctl, check_done);
+}
+
+template <int SMAG>
+static cudaError_t launch_jvc_tile(const Geo& G, const float* u, const float* v, float* out, const double* part,
+                                   Ctl* ctl, int check_done, cudaStream_t s) {
+#define JF_JVC(I) launch_jvc_t<SMAG, JvcTile<I>::TX, JvcTile<I>::TZ, JvcTile<I>::NBUF>(G, u, v, out, part, ctl, \
+                                                                                     check_done, s)
+    switch (G.tile_jv) {
+        case 1: return JF_JVC(1);
+        case 2: return JF_JVC(2);
+        case 3: return JF_JVC(3);
+        default: return JF_JVC(0);
+    }
+#undef JF_JVC
+}
+
 template <typename T, int SMAG>
 static cudaError_t launch_jvd_tile(const Geo& G, const T* u, const T* v, T* out, const double* part, Ctl* ctl,
                                    int check_done, cudaStream_t s) {
-    if (sizeof(T) == sizeof(double))
+    if constexpr (sizeof(T) == sizeof(double)) {
         return launch_jvd_t<T, SMAG, JvTile<1>::TX, JvTile<1>::TZ>(G, u, v, out, part, ctl, check_done, s);
-    switch (G.tile_jv) {
-        case 1: return launch_jvd_t<T, SMAG, JvTile<1>::TX, JvTile<1>::TZ>(G, u, v, out, part, ctl, check_done, s);
-        case 2: return launch_jvd_t<T, SMAG, JvTile<2>::TX, JvTile<2>::TZ>(G, u, v, out, part, ctl, check_done, s);
-        case 3: return launch_jvd_t<T, SMAG, JvTile<3>::TX, JvTile<3>::TZ>(G, u, v, out, part, ctl, check_done, s);
-        default: return launch_jvd_t<T, SMAG, JvTile<0>::TX, JvTile<0>::TZ>(G, u, v, out, part, ctl, check_done, s);
+    } else {
+        return launch_jvc_tile<SMAG>(G, u, v, out, part, ctl, check_done, s);
     }
 }
 
@@ -1374,6 +1839,15 @@ template <typename T>
 cudaError_t launch_jv_diff(const Geo& G, const T* u, const T* v, T* out, double* part, Ctl* ctl,
                            int check_done, cudaStream_t s) {
     if (G.dim == 3) return launch_jv_diff3d<T>(G, u, v, out, ctl, check_done, s);
+    if (G.sgs == 2) {
+        // Deardorff: the float32 compute-once kernel only (float64 handles take the
+        // plain forward difference of stencil2d)
+        if constexpr (sizeof(T) == sizeof(float)) {
+            return launch_jvc_tile<2>(G, u, v, out, part, ctl, check_done, s);
+        } else {
+            return cudaErrorNotSupported;
+        }
+    }
     return G.smag ? launch_jvd_tile<T, 1>(G, u, v, out, part, ctl, check_done, s)
                   : launch_jvd_tile<T, 0>(G, u, v, out, part, ctl, check_done, s);
 }
@@ -1406,7 +1880,7 @@ static cudaError_t launch_precond_t(const Geo& G, int sweeps, const T* r, T* z, 
     }
     dim3 grid((G.nx + TX - 1) / TX, (G.nz + TZ - 1) / TZ, 3);
     const size_t sm = sizeof(T) * ((TZ + 2 * HALO) * (TX + 2 * HALO) + TZ * (TX + 2 * R) +
-                                   (TZ + 2 * R) * TX + (TX + 2 * R) * (TZ + 2 * R));
+                                   (TZ + 2 * R) * TX + (SMAG == 2 ? 2 : 1) * (TX + 2 * R) * (TZ + 2 * R));
     static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
     if (!configured) {
         cudaError_t e;
@@ -1526,6 +2000,8 @@ cudaError_t launch_precond(const Geo& G, int sweeps, const T* r, T* z, T* za, T*
         return launch_schur<T>(G, sweeps, r, z, za, zb, da, db, part, ctl, check_done, s, launches);
     if (G.dim == 3 && sweeps > 1)
         return launch_precond3d<T>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches);
+    if (G.sgs == 2)
+        return launch_precond_tile<T, 2>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches);
     return G.smag ? launch_precond_tile<T, 1>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches)
                   : launch_precond_tile<T, 0>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches);
 }

@@ -166,6 +166,18 @@ __device__ __forceinline__ void grad3(const T* U, const T* V, const T* W, int c,
     }
 }
 
+// Deardorff coefficient along an arm (Section 2.4, Eq. KmM) from the strain s:
+// momentum c s with c = K_m / s along x and y, K_M / s along z; heat times
+// 1 + a l(s), a = 2 / sqrt(dx dy) horizontally, 2 / dz vertically.
+template <typename T>
+__device__ __forceinline__ T dd3_coef(T s, bool zarm, bool heat, const Geo& G) {
+    const T c = T(zarm ? G.dd_cM : G.dd_cm);
+    if (!heat) return c * s;
+    const T cls = T(G.dd_cl) * s;
+    const T l = G.dd_cl < 0.0 ? T(G.dd_delta) : (cls < T(G.dd_delta) ? cls : T(G.dd_delta));
+    return c * (s * (T(1) + T(zarm ? G.dd_az : G.dd_ah) * l));
+}
+
 template <typename T>
 __device__ __forceinline__ T strain_sq(const T (&g)[3][3]) {    // S_ij S_ij
     T ss = T(0);
@@ -193,6 +205,7 @@ stencil3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
     T* s1 = reinterpret_cast<T*>(smem_raw);        // [5][PL]
     T* g = s1 + 5 * B::PL;                          // [4][AS] derivative arms of u, v, w, theta
     T* nu = g + 4 * B::AS;                          // [AS] eddy coefficient on the arms
+    T* kh = nu + B::AS;                             // [AS] Deardorff: heat coefficient on the arms
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const T ix_ = T(G.inv_dx), iy_ = T(G.inv_dy), iz_ = T(G.inv_dz);
     __shared__ double cfs[5];
@@ -222,12 +235,21 @@ stencil3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
             arm_point<TX, TY, TZ>(idx, bx, by, bz, zarm);
             T val = T(0);
             const int bzz = zarm ? eddy_box_row(bz, z0, G.nz) : bz;
+            T hv = T(0);
             if (bzz >= 0) {
                 T gr[3][3];
                 grad3<T, B::SX, B::SXY>(s1, s1 + B::PL, s1 + 2 * B::PL, B::b(bx, by, bzz), ix_, iy_, iz_, gr);
-                val = cs2 * sqrt(T(2) * strain_sq(gr));
+                if (SMAG == 2) {
+                    // Deardorff: the arm's own direction picks K_m / K_M and K_h / K_H
+                    const T sv = sqrt(T(2) * strain_sq(gr));
+                    val = dd3_coef(sv, zarm, false, G);
+                    hv = dd3_coef(sv, zarm, true, G);
+                } else {
+                    val = cs2 * sqrt(T(2) * strain_sq(gr));
+                }
             }
             nu[idx] = val;
+            if (SMAG == 2) kh[idx] = hv;
         }
     }
     __syncthreads();
@@ -263,7 +285,10 @@ stencil3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
             T dif = T(0);
             if (fl < 4) {
                 const T* gf = g + fl * B::AS;
-                if (SMAG) {
+                if (SMAG == 2) {
+                    const T* kf = fl == 3 ? kh : nu;
+                    dif = ddp(kf, gf, cx, 1, ix_) + ddp(kf, gf, cy, TX, iy_) + ddp(kf, gf, cz, TX * TY, iz_);
+                } else if (SMAG) {
                     dif = ddp(nu, gf, cx, 1, ix_) + ddp(nu, gf, cy, TX, iy_) + ddp(nu, gf, cz, TX * TY, iz_);
                     if (fl == 3) dif *= iPr;
                 } else {
@@ -345,6 +370,8 @@ jv_diff3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
     T* gb = ga + 4 * B::AS;                         // [4][AS]
     T* Ka = gb + 4 * B::AS;                         // [AS]
     T* dK = Ka + B::AS;                             // [AS]
+    T* Kh = dK + B::AS;                             // [AS] Deardorff: heat coefficient and its difference
+    T* dKh = Kh + B::AS;                            // [AS]
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
     const T ix_ = T(G.inv_dx), iy_ = T(G.inv_dy), iz_ = T(G.inv_dz);
     __shared__ T cfs[5];
@@ -372,7 +399,7 @@ jv_diff3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
             int bx, by, bz;
             bool zarm;
             arm_point<TX, TY, TZ>(idx, bx, by, bz, zarm);
-            T ka = T(0), dk = T(0);
+            T ka = T(0), dk = T(0), kh_ = T(0), dkh_ = T(0);
             const int bzz = zarm ? eddy_box_row(bz, z0, G.nz) : bz;
             if (bzz >= 0) {
                 const int c = B::b(bx, by, bzz);
@@ -392,12 +419,35 @@ jv_diff3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
                 const T na = sqrt(T(2) * ssa);
                 const T tp = T(2) * (ssa + dss);
                 const T np = sqrt(tp > T(0) ? tp : T(0));
-                ka = cs2 * na;
                 const T den = na + np;
-                dk = den > T(0) ? cs2 * T(2) * dss / den : T(0);
+                const T ds = den > T(0) ? T(2) * dss / den : T(0);     // s' - s, cancellation-free
+                if (SMAG == 2) {
+                    // Deardorff: the arm's direction picks the coefficient; heat by its difference
+                    // form g(s') - g(s) = ds (1 + a l') + a s (l' - l) (l' - l = c_l ds below the cap)
+                    ka = dd3_coef(na, zarm, false, G);
+                    dk = dd3_coef(ds, zarm, false, G);
+                    const T c = T(zarm ? G.dd_cM : G.dd_cm), a = T(zarm ? G.dd_az : G.dd_ah);
+                    T la = T(G.dd_delta), lp = T(G.dd_delta), dl = T(0);
+                    if (G.dd_cl >= 0.0) {
+                        const T ta = T(G.dd_cl) * na, tq = T(G.dd_cl) * np;
+                        la = ta < T(G.dd_delta) ? ta : T(G.dd_delta);
+                        lp = tq < T(G.dd_delta) ? tq : T(G.dd_delta);
+                        if (ta < T(G.dd_delta) && tq < T(G.dd_delta)) dl = T(G.dd_cl) * ds;
+                        else if (ta < T(G.dd_delta) || tq < T(G.dd_delta)) dl = lp - la;
+                    }
+                    kh_ = c * (na * (T(1) + a * la));
+                    dkh_ = c * (ds * (T(1) + a * lp) + a * na * dl);
+                } else {
+                    ka = cs2 * na;
+                    dk = cs2 * ds;
+                }
             }
             Ka[idx] = ka;
             dK[idx] = dk;
+            if (SMAG == 2) {
+                Kh[idx] = kh_;
+                dKh[idx] = dkh_;
+            }
         }
     }
     __syncthreads();
@@ -460,15 +510,18 @@ jv_diff3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict
                     for (int l = 1; l <= 2; ++l) {
                         const T cl = l == 1 ? T(2.0 / 3.0) : T(-1.0 / 12.0);
                         const int p1 = q + l * st, m1 = q - l * st;
-                        if (SMAG)
-                            sj += cl * ((Ka[p1] * gbf[p1] + dK[p1] * (gaf[p1] + gbf[p1])) -
-                                        (Ka[m1] * gbf[m1] + dK[m1] * (gaf[m1] + gbf[m1])));
-                        else
+                        if (SMAG) {
+                            const T* K1 = (SMAG == 2 && fl == 3) ? Kh : Ka;
+                            const T* d1 = (SMAG == 2 && fl == 3) ? dKh : dK;
+                            sj += cl * ((K1[p1] * gbf[p1] + d1[p1] * (gaf[p1] + gbf[p1])) -
+                                        (K1[m1] * gbf[m1] + d1[m1] * (gaf[m1] + gbf[m1])));
+                        } else {
                             sj += cl * (gbf[p1] - gbf[m1]);
+                        }
                     }
                     dif += sj * ihs[j];
                 }
-                if (SMAG) { if (fl == 3) dif *= iPr; } else dif *= (fl == 3 ? KHc : KMc);
+                if (SMAG == 1) { if (fl == 3) dif *= iPr; } else if (!SMAG) dif *= (fl == 3 ? KHc : KMc);
                 dF[fl] += dif;
             }
         }
@@ -496,7 +549,7 @@ __global__ void __launch_bounds__(NTHREADS)
 eddy3d(Geo G, const T* __restrict__ u, T* __restrict__ nu, double* part, Ctl* ctl) {
     T mxT = T(0);
     const T ih[3] = {T(G.inv_dx), T(G.inv_dy), T(G.inv_dz)};
-    const T cs2 = T(G.cs2);
+    const T cs2 = G.sgs == 2 ? T(1) : T(G.cs2);     // Deardorff: the strain s itself
     const int nxy = G.nx * G.ny;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < G.npt; p += gridDim.x * blockDim.x) {
         const int z = p / nxy, rem = p - z * nxy;
@@ -588,7 +641,9 @@ cheb3d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
                 int side;
                 const int sz = mirror(z0 + bz - HALO, G.nz, side);    // even mirror of nu
                 const int sy = wrap(y0 + by - HALO, G.ny), sx = wrap(x0 + bx - HALO, G.nx);
-                kk[idx] = (sz >= 0 && sz < G.nz) ? nu[((size_t)sz * G.ny + sy) * G.nx + sx] * kscale : T(0);
+                const T nv = (sz >= 0 && sz < G.nz) ? nu[((size_t)sz * G.ny + sy) * G.nx + sx] : T(0);
+                // Deardorff: nu holds the strain and the arm's direction picks the coefficient
+                kk[idx] = SMAG == 2 ? dd3_coef(nv, zarm, fld == 3, G) : nv * kscale;
             }
         }
         __syncthreads();
@@ -867,7 +922,7 @@ static cudaError_t launch_s3(const Geo& G, const T* u, const T* v, const T* Fu, 
     using namespace d3;
     constexpr int TX = FTile<T>::TX, TY = FTile<T>::TY, TZ = FTile<T>::TZ;
     using B = Box<TX, TY, TZ>;
-    const size_t sm = sizeof(T) * (5 * B::PL + 5 * B::AS);
+    const size_t sm = sizeof(T) * (5 * B::PL + (SMAG == 2 ? 6 : 5) * B::AS);
     static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
     if (!configured) {
         cudaError_t e = set_smem(stencil3d<T, MODE, SMAG, TX, TY, TZ>, sm);
@@ -884,8 +939,9 @@ cudaError_t launch_stencil3d(int mode, const Geo& G, const T* u, const T* v, con
                              T* out, T* out2, double* part, Ctl* ctl, int check_done, cudaStream_t s) {
 #define JF3(M)                                                                                         \
     case M:                                                                                            \
-        return G.smag ? launch_s3<T, M, 1>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s)       \
-                      : launch_s3<T, M, 0>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
+        return G.sgs == 2 ? launch_s3<T, M, 2>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s)   \
+             : G.smag     ? launch_s3<T, M, 1>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s)   \
+                          : launch_s3<T, M, 0>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
     switch (mode) {
         JF3(d3::MODE_F)
         JF3(d3::MODE_RHS)
@@ -907,7 +963,7 @@ static cudaError_t launch_jvd3(const Geo& G, const T* u, const T* v, T* out, Ctl
     using namespace d3;
     constexpr int TX = DTile<T>::TX, TY = DTile<T>::TY, TZ = DTile<T>::TZ;
     using B = Box<TX, TY, TZ>;
-    const size_t sm = sizeof(T) * (10 * B::PL + 10 * B::AS);
+    const size_t sm = sizeof(T) * (10 * B::PL + (SMAG == 2 ? 12 : 10) * B::AS);
     static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
     if (!configured) {
         cudaError_t e = set_smem(jv_diff3d<T, SMAG, TX, TY, TZ>, sm);
@@ -922,6 +978,7 @@ static cudaError_t launch_jvd3(const Geo& G, const T* u, const T* v, T* out, Ctl
 template <typename T>
 cudaError_t launch_jv_diff3d(const Geo& G, const T* u, const T* v, T* out, Ctl* ctl, int check_done,
                              cudaStream_t s) {
+    if (G.sgs == 2) return launch_jvd3<T, 2>(G, u, v, out, ctl, check_done, s);
     return G.smag ? launch_jvd3<T, 1>(G, u, v, out, ctl, check_done, s)
                   : launch_jvd3<T, 0>(G, u, v, out, ctl, check_done, s);
 }
@@ -1019,6 +1076,7 @@ cudaError_t launch_precond3d(const Geo& G, int sweeps, const T* r, T* z, T* za, 
                              const T* nu, double* part, Ctl* ctl, int check_done, cudaStream_t s,
                              long long* launches) {
     if (G.pc_schur) return launch_schur3d<T>(G, sweeps, r, z, za, zb, da, db, part, ctl, check_done, s, launches);
+    if (G.sgs == 2) return launch_pc3<T, 2>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches);
     return G.smag ? launch_pc3<T, 1>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches)
                   : launch_pc3<T, 0>(G, sweeps, r, z, za, zb, da, db, nu, part, ctl, check_done, s, launches);
 }

@@ -107,7 +107,11 @@ struct ConvOut {
     int accumulate;     // OUT_PLANES
 };
 
-template <int CI, int IH, int IW, int CIP, int INMODE, int CU>
+// LAYOUT 0: pixel-major rows padded to CIP channels (ldmatrix operands of conv_mma).
+// LAYOUT 1: the canonical K-major, no-swizzle operand layout of tcgen05.mma
+// (conv_tc): for every tile row iy and 8-channel group v, the IW pixels' 16-byte
+// groups lie contiguously, at iy * (CI/8) * IW * 16 + v * IW * 16 + ix * 16 bytes.
+template <int CI, int IH, int IW, int CIP, int INMODE, int CU, int LAYOUT = 0>
 __device__ __forceinline__ void stage_tile(const ConvIn& in, const Bal& bal, int H, int Wd, int y0, int x0, int hp,
                                            uint32_t xs_addr) {
     constexpr int VPP = CI / 8;
@@ -116,7 +120,8 @@ __device__ __forceinline__ void stage_tile(const ConvIn& in, const Bal& bal, int
         const int iy = pix / IW, ix = pix - iy * IW;
         const int gy = y0 + iy - hp, gx = x0 + ix - hp;
         const bool ok = gy >= 0 && gy < H && gx >= 0 && gx < Wd;
-        const uint32_t dst = xs_addr + (uint32_t)((pix * CIP + v * 8) * sizeof(bf16));
+        const uint32_t dst = LAYOUT == 0 ? xs_addr + (uint32_t)((pix * CIP + v * 8) * sizeof(bf16))
+                                         : xs_addr + (uint32_t)(((iy * VPP + v) * IW + ix) * 16);
         if constexpr (INMODE == IN_NHWC) {
             const bf16* src = ok ? in.a + ((size_t)gy * Wd + gx) * in.astr + in.aoff + v * 8 : in.a;
             cp_async16(dst, src, ok ? 16 : 0);
@@ -281,6 +286,218 @@ conv_mma(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int
         __syncthreads();   // the next prefetch overwrites this buffer
     }
     cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------- tcgen05 convolution
+// The same convolution as conv_mma on the fifth-generation tensor cores: one
+// CTA computes a CONV_TH x CONV_TW = 16 x 8 pixel tile as the M = 128 rows of
+// the implicit GEMM D[pixel][co] = sum_tap sum_ci A_tap[pixel][ci] W[tap][co][ci].
+// The staged input tile (halo included) is kept in the canonical K-major,
+// no-swizzle layout (stage_tile LAYOUT 1), so the A operand of tap (ky, kx) is
+// the same tile at a descriptor offset of ky rows and kx pixels: no im2col
+// copy.  The layer's weights stay resident as the B operand (K-major core
+// matrices).  One thread issues the K / 16 tcgen05.mma.kind::f16 instructions
+// (bfloat16 operands, float32 accumulation) of a tile into one of two TMEM
+// accumulators and commits them to an mbarrier; while they run, the CTA
+// stages the next tile into the other input buffer; then every warp reads its
+// 32 TMEM lanes (= 32 pixels) with tcgen05.ld and writes the output.  Waits on
+// the mbarrier are bounded: on a time-out the CTA records an error, lets its
+// copies drain, frees its TMEM and returns.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor of tcgen05.mma: start address, leading
+// (K-direction core matrix) and stride (M/N-direction core matrix) byte
+// offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: D float32, A and B bfloat16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ bool mbar_test(uint32_t addr, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(addr), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// 8 float32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int CI, int CO, int KS>
+struct TcShape {
+    static constexpr int HP = KS / 2;
+    static constexpr int IH = CONV_TH + 2 * HP, IW = CONV_TW + 2 * HP;
+    static constexpr int C8 = CI / 8;
+    static constexpr uint32_t A_LBO = IW * 16;              // next 8 input channels
+    static constexpr uint32_t A_SBO = C8 * IW * 16;         // next pixel row of the tile
+    static constexpr uint32_t A_BYTES = IH * A_SBO;
+    static constexpr uint32_t B_LBO = 128;                  // next 8 input channels
+    static constexpr uint32_t B_SBO = C8 * 128;             // next 8 output channels
+    static constexpr uint32_t B_TAP = CO * CI * 2;
+    static constexpr uint32_t W_BYTES = KS * KS * B_TAP;
+    static constexpr int TCOLS = 2 * CO <= 32 ? 32 : (2 * CO <= 64 ? 64 : (2 * CO <= 128 ? 128 : 256));
+    static constexpr size_t SMEM = W_BYTES + 2 * A_BYTES;
+    static_assert(CI % 16 == 0 && CO % 16 == 0 && CO <= 256, "tcgen05 shape");
+};
+
+constexpr long long TC_WAIT_LIMIT = 1ll << 26;    // mbarrier polls before a tile is declared lost
+
+template <int CI, int CO, int KS, int INMODE, int OUTMODE, int CU>
+__global__ void __launch_bounds__(CONV_THREADS)
+conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int Wd, const int* skip, int* err) {
+    if (skip != nullptr && *skip) return;
+    using S = TcShape<CI, CO, KS>;
+    constexpr uint32_t IDESC = tc_idesc(128, CO);
+    extern __shared__ __align__(16) unsigned char sm[];    // no-swizzle operands need 16-byte alignment
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) unsigned long long mbar[2];
+    const int ntx = (Wd + CONV_TW - 1) / CONV_TW, nty = (H + CONV_TH - 1) / CONV_TH;
+    const int ntiles = ntx * nty;
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t ws = smem_u32(sm);
+    const uint32_t xs0 = ws + S::W_BYTES;
+    const uint32_t mb[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"((uint32_t)S::TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb[0]), "r"(1u) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb[1]), "r"(1u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // weights into K-major core matrices: (tap, co, 8 channels v) -> tap*B_TAP + (co/8)*B_SBO + v*128 + (co%8)*16
+    for (int idx = threadIdx.x; idx < KS * KS * CO * S::C8; idx += blockDim.x) {
+        const int row = idx / S::C8, v = idx - row * S::C8;
+        const int tap = row / CO, co = row - tap * CO;
+        cp_async16(ws + (uint32_t)(tap * S::B_TAP + (co >> 3) * S::B_SBO + v * S::B_LBO + (co & 7) * 16),
+                   W + (size_t)row * CI + v * 8, 16);
+    }
+    stage_tile<CI, S::IH, S::IW, 0, INMODE, CU, 1>(in, bal, H, Wd, (tile / ntx) * CONV_TH, (tile % ntx) * CONV_TW,
+                                                   S::HP, xs0);
+    cp_async_commit();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    uint32_t parity[2] = {0u, 0u};
+    int failed = 0;
+    int buf = 0;
+    // epilogue split: warps w and w + 4 share TMEM lanes 32 (w % 4) .. +31, each takes half the columns
+    const int lanebase = (warp & 3) * 32;
+    const int m = lanebase + lane;                       // GEMM row = pixel (m / 8, m % 8) of the tile
+    const int cbeg = (warp >> 2) * (CO / 2);
+    for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+        cp_async_wait<0>();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // staged data -> tensor-core reads
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const uint32_t xs = xs0 + buf * S::A_BYTES;
+        if (threadIdx.x == 0) {
+            uint32_t acc = 0u;
+#pragma unroll
+            for (int tap = 0; tap < KS * KS; ++tap) {
+                const int ky = tap / KS, kx = tap - ky * KS;
+#pragma unroll
+                for (int kc = 0; kc < CI / 16; ++kc) {
+                    const uint64_t ad = tc_sdesc(xs + ky * S::A_SBO + 2 * kc * S::A_LBO + kx * 16, S::A_LBO, S::A_SBO);
+                    const uint64_t bd = tc_sdesc(ws + tap * S::B_TAP + 2 * kc * S::B_LBO, S::B_LBO, S::B_SBO);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + buf * CO),
+                        "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+                        : "memory");
+                    acc = 1u;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb[buf])
+                         : "memory");
+        }
+        // the other input buffer is free (its tile's MMAs completed before its epilogue)
+        const int next = tile + gridDim.x;
+        if (next < ntiles)
+            stage_tile<CI, S::IH, S::IW, 0, INMODE, CU, 1>(in, bal, H, Wd, (next / ntx) * CONV_TH,
+                                                           (next % ntx) * CONV_TW, S::HP, xs0 + (buf ^ 1) * S::A_BYTES);
+        cp_async_commit();
+        bool ready = false;
+        for (long long it = 0; it < TC_WAIT_LIMIT && !ready; ++it) ready = mbar_test(mb[buf], parity[buf]);
+        parity[buf] ^= 1u;
+        if (__syncthreads_or(!ready)) {
+            failed = 1;
+            break;
+        }
+        tc_fence_after();
+        const int y0 = (tile / ntx) * CONV_TH, x0 = (tile % ntx) * CONV_TW;
+        const int gy = y0 + (m >> 3), gx = x0 + (m & 7);
+        const bool inside = gy < H && gx < Wd;
+        const uint32_t taddr = tmem + ((uint32_t)lanebase << 16) + buf * CO;
+        if constexpr (OUTMODE == OUT_PLANES) {
+            if (warp < 4) {
+                float v[8];
+                tmem_ld8(taddr, v);
+                if (inside) {
+                    float* o = reinterpret_cast<float*>(out.o);
+                    const size_t npix = (size_t)H * Wd;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        float* d = o + (size_t)c * npix + (size_t)gy * Wd + gx;
+                        const float val = v[c] * bal.inv[c];
+                        *d = out.accumulate ? *d + val : val;
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c0 = 0; c0 < CO / 2; c0 += 8) {
+                float v[8];
+                tmem_ld8(taddr + cbeg + c0, v);      // whole warp (collective); stores guarded below
+                if (inside) {
+                    const size_t base = ((size_t)gy * Wd + gx) * out.ostr + out.ooff + cbeg + c0;
+                    if constexpr (OUTMODE == OUT_F32) {
+                        float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(out.o) + base);
+                        o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                        o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    } else {
+                        __align__(16) __nv_bfloat162 h[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                        *reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(out.o) + base) =
+                            *reinterpret_cast<uint4*>(h);
+                    }
+                }
+            }
+        }
+    }
+    if (failed && threadIdx.x == 0 && err != nullptr) atomicExch(err, 1);
+    cp_async_wait<0>();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::TCOLS)
+                     : "memory");
 }
 
 // dW[tap][co][ci] += sum_p dout[p][co] in[p + off(tap)][ci] over a 16x16 pixel tile.
@@ -485,9 +702,38 @@ int grid_for(size_t n) {
     return (int)(b > 1216 ? 1216 : (b > 0 ? b : 1));
 }
 
+// Convolution engines: tcgen05.mma (conv_tc, the default) or the legacy
+// mma.sync path (conv_mma); both compute the same layer.
+enum { ENGINE_TCGEN05 = 0, ENGINE_MMA_SYNC = 1 };
+
+template <int CI, int CO, int KS, int INMODE, int OUTMODE, int CU = 0>
+cudaError_t conv_ex_tc(const ConvIn& in, const Bal& bal, const bf16* W, const ConvOut& out, int H, int Wd,
+                       cudaStream_t s, const int* skip, int* err) {
+    using S = TcShape<CI, CO, KS>;
+    auto kern = conv_tc<CI, CO, KS, INMODE, OUTMODE, CU>;
+    static int max_ctas = 0;   // resident CTAs on the device (persistent grid)
+    if (max_ctas == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CONV_THREADS, S::SMEM)) != cudaSuccess)
+            return e;
+        // at most 512 TMEM columns per SM: more CTAs would wait in tcgen05.alloc
+        per_sm = per_sm < 512 / S::TCOLS ? per_sm : 512 / S::TCOLS;
+        max_ctas = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int ntiles = ((Wd + CONV_TW - 1) / CONV_TW) * ((H + CONV_TH - 1) / CONV_TH);
+    const int grid = ntiles < max_ctas ? ntiles : max_ctas;
+    kern<<<grid, CONV_THREADS, S::SMEM, s>>>(in, bal, W, out, H, Wd, skip, err);
+    return cudaGetLastError();
+}
+
 template <int CI, int CO, int KS, int INMODE, int OUTMODE, int CU = 0>
 cudaError_t conv_ex(const ConvIn& in, const Bal& bal, const bf16* W, const ConvOut& out, int H, int Wd,
-                    cudaStream_t s, const int* skip) {
+                    cudaStream_t s, const int* skip, int engine = ENGINE_TCGEN05, int* err = nullptr) {
+    if (engine == ENGINE_TCGEN05) return conv_ex_tc<CI, CO, KS, INMODE, OUTMODE, CU>(in, bal, W, out, H, Wd, s, skip, err);
     using S = ConvShape<CI, CO, KS>;
     auto kern = conv_mma<CI, CO, KS, INMODE, OUTMODE, CU>;
     static int max_ctas = 0;   // resident CTAs on the device (persistent grid)
@@ -510,11 +756,11 @@ cudaError_t conv_ex(const ConvIn& in, const Bal& bal, const bf16* W, const ConvO
 // plain NHWC -> NHWC convolution (training path)
 template <int CI, int CO, int KS, bool OUTF32>
 cudaError_t conv(const bf16* in, int istr, int ioff, const bf16* W, void* out, int ostr, int ooff, int H, int Wd,
-                 cudaStream_t s, const int* skip = nullptr) {
+                 cudaStream_t s, const int* skip, int engine, int* err) {
     ConvIn ci{in, istr, ioff, nullptr, 0, 0, nullptr};
     ConvOut co{out, ostr, ooff, 0};
     Bal bal{};
-    return conv_ex<CI, CO, KS, IN_NHWC, OUTF32 ? OUT_F32 : OUT_BF16>(ci, bal, W, co, H, Wd, s, skip);
+    return conv_ex<CI, CO, KS, IN_NHWC, OUTF32 ? OUT_F32 : OUT_BF16>(ci, bal, W, co, H, Wd, s, skip, engine, err);
 }
 
 template <int CI, int CO, int KS>
@@ -553,6 +799,8 @@ struct UNet {
     bf16 *dy, *dh0c, *dcat0, *dh1c, *dcat1, *dh2b, *dh2a, *dp2, *ds1, *dh1a, *dp1, *ds0, *dh0a;
     float* yf;                              // output NHWC16 float32
     double* scal;                           // [0] ||B x||^2, [1] loss
+    int* derr;                              // set by a convolution whose tensor-core wait timed out
+    int engine;                             // ENGINE_TCGEN05 or ENGINE_MMA_SYNC
     int step;
     Bal bal;
 };
@@ -560,7 +808,7 @@ struct UNet {
 static void free_net(UNet* n) {
     void* p[] = {n->w32, n->g32, n->m32, n->v32, n->wb, n->wt, n->x0, n->h0a, n->cat0, n->p1, n->h1a, n->cat1,
                  n->p2, n->h2a, n->h2b, n->h1c, n->h0c, n->dy, n->dh0c, n->dcat0, n->dh1c, n->dcat1, n->dh2b,
-                 n->dh2a, n->dp2, n->ds1, n->dh1a, n->dp1, n->ds0, n->dh0a, n->yf, n->scal};
+                 n->dh2a, n->dp2, n->ds1, n->dh1a, n->dp1, n->ds0, n->dh0a, n->yf, n->scal, n->derr};
     for (void* q : p)
         if (q) cudaFree(q);
 }
@@ -598,6 +846,9 @@ UNet* unet_create(int nx, int nz, const double balance[4], unsigned long long se
     A((void**)&n->dh2a, P2 * 64 * 2); A((void**)&n->dp2, P2 * 32 * 2); A((void**)&n->ds1, P1 * 32 * 2);
     A((void**)&n->dh1a, P1 * 32 * 2); A((void**)&n->dp1, P1 * 16 * 2); A((void**)&n->ds0, P0 * 16 * 2);
     A((void**)&n->dh0a, P0 * 16 * 2); A((void**)&n->yf, P0 * 16 * 4); A((void**)&n->scal, 16 * 8);
+    A((void**)&n->derr, sizeof(int));
+    if (*err == cudaSuccess) *err = cudaMemset(n->derr, 0, sizeof(int));
+    n->engine = ENGINE_TCGEN05;
     if (*err != cudaSuccess) { free_net(n); delete n; return nullptr; }
     // seeded init: N(0, 1/fan_in) on real input channels; the last layer and the
     // padded input / output channels start at zero (untrained net = zero map)
@@ -656,19 +907,19 @@ static cudaError_t forward(UNet* n, const float* x, cudaStream_t s, const int* s
     const int H0 = n->nz, W0 = n->nx, H1 = H0 / 2, W1 = W0 / 2, H2 = H0 / 4, W2 = W0 / 4;
     const bf16* w = n->wb;
     pack_input<<<grid_for((size_t)H0 * W0), 256, 0, s>>>(x, H0 * W0, n->bal, n->x0, skip);
-    UCK((conv<16, 16, 3, false>(n->x0, 16, 0, w + n->woff[L0a], n->h0a, 16, 0, H0, W0, s, skip)));
-    UCK((conv<16, 16, 3, false>(n->h0a, 16, 0, w + n->woff[L0b], n->cat0, 48, 32, H0, W0, s, skip)));
+    UCK((conv<16, 16, 3, false>(n->x0, 16, 0, w + n->woff[L0a], n->h0a, 16, 0, H0, W0, s, skip, n->engine, n->derr)));
+    UCK((conv<16, 16, 3, false>(n->h0a, 16, 0, w + n->woff[L0b], n->cat0, 48, 32, H0, W0, s, skip, n->engine, n->derr)));
     avgpool2<<<grid_for((size_t)H1 * W1 * 16), 256, 0, s>>>(n->cat0, 48, 32, n->p1, 16, 0, 16, H0, W0, skip);
-    UCK((conv<16, 32, 3, false>(n->p1, 16, 0, w + n->woff[L1a], n->h1a, 32, 0, H1, W1, s, skip)));
-    UCK((conv<32, 32, 3, false>(n->h1a, 32, 0, w + n->woff[L1b], n->cat1, 96, 64, H1, W1, s, skip)));
+    UCK((conv<16, 32, 3, false>(n->p1, 16, 0, w + n->woff[L1a], n->h1a, 32, 0, H1, W1, s, skip, n->engine, n->derr)));
+    UCK((conv<32, 32, 3, false>(n->h1a, 32, 0, w + n->woff[L1b], n->cat1, 96, 64, H1, W1, s, skip, n->engine, n->derr)));
     avgpool2<<<grid_for((size_t)H2 * W2 * 32), 256, 0, s>>>(n->cat1, 96, 64, n->p2, 32, 0, 32, H1, W1, skip);
-    UCK((conv<32, 64, 3, false>(n->p2, 32, 0, w + n->woff[L2a], n->h2a, 64, 0, H2, W2, s, skip)));
-    UCK((conv<64, 64, 3, false>(n->h2a, 64, 0, w + n->woff[L2b], n->h2b, 64, 0, H2, W2, s, skip)));
+    UCK((conv<32, 64, 3, false>(n->p2, 32, 0, w + n->woff[L2a], n->h2a, 64, 0, H2, W2, s, skip, n->engine, n->derr)));
+    UCK((conv<64, 64, 3, false>(n->h2a, 64, 0, w + n->woff[L2b], n->h2b, 64, 0, H2, W2, s, skip, n->engine, n->derr)));
     upsample2<<<grid_for((size_t)H1 * W1 * 64), 256, 0, s>>>(n->h2b, 64, 0, n->cat1, 96, 0, 64, H1, W1, skip);
-    UCK((conv<96, 32, 3, false>(n->cat1, 96, 0, w + n->woff[L1c], n->h1c, 32, 0, H1, W1, s, skip)));
+    UCK((conv<96, 32, 3, false>(n->cat1, 96, 0, w + n->woff[L1c], n->h1c, 32, 0, H1, W1, s, skip, n->engine, n->derr)));
     upsample2<<<grid_for((size_t)H0 * W0 * 32), 256, 0, s>>>(n->h1c, 32, 0, n->cat0, 48, 0, 32, H0, W0, skip);
-    UCK((conv<48, 16, 3, false>(n->cat0, 48, 0, w + n->woff[L0c], n->h0c, 16, 0, H0, W0, s, skip)));
-    UCK((conv<16, 16, 1, true>(n->h0c, 16, 0, w + n->woff[L0d], n->yf, 16, 0, H0, W0, s, skip)));
+    UCK((conv<48, 16, 3, false>(n->cat0, 48, 0, w + n->woff[L0c], n->h0c, 16, 0, H0, W0, s, skip, n->engine, n->derr)));
+    UCK((conv<16, 16, 1, true>(n->h0c, 16, 0, w + n->woff[L0d], n->yf, 16, 0, H0, W0, s, skip, n->engine, n->derr)));
     return cudaGetLastError();
 }
 
@@ -684,25 +935,25 @@ static cudaError_t forward_fused(UNet* n, const float* x, float* y, int accumula
     auto to = [&](void* o, int str, int off) { return ConvOut{o, str, off, 0}; };
     ConvIn pk = none;
     pk.x = x;
-    UCK((conv_ex<16, 16, 3, IN_PACK, OUT_BF16>(pk, n->bal, w + n->woff[L0a], to(n->h0a, 16, 0), H0, W0, s, skip)));
+    UCK((conv_ex<16, 16, 3, IN_PACK, OUT_BF16>(pk, n->bal, w + n->woff[L0a], to(n->h0a, 16, 0), H0, W0, s, skip, n->engine, n->derr)));
     UCK((conv_ex<16, 16, 3, IN_NHWC, OUT_BF16>(nhwc(n->h0a, 16, 0), n->bal, w + n->woff[L0b], to(n->cat0, 48, 32), H0,
-                                               W0, s, skip)));
+                                               W0, s, skip, n->engine, n->derr)));
     UCK((conv_ex<16, 32, 3, IN_POOL, OUT_BF16>(nhwc(n->cat0, 48, 32), n->bal, w + n->woff[L1a], to(n->h1a, 32, 0), H1,
-                                               W1, s, skip)));
+                                               W1, s, skip, n->engine, n->derr)));
     UCK((conv_ex<32, 32, 3, IN_NHWC, OUT_BF16>(nhwc(n->h1a, 32, 0), n->bal, w + n->woff[L1b], to(n->cat1, 96, 64), H1,
-                                               W1, s, skip)));
+                                               W1, s, skip, n->engine, n->derr)));
     UCK((conv_ex<32, 64, 3, IN_POOL, OUT_BF16>(nhwc(n->cat1, 96, 64), n->bal, w + n->woff[L2a], to(n->h2a, 64, 0), H2,
-                                               W2, s, skip)));
+                                               W2, s, skip, n->engine, n->derr)));
     UCK((conv_ex<64, 64, 3, IN_NHWC, OUT_BF16>(nhwc(n->h2a, 64, 0), n->bal, w + n->woff[L2b], to(n->h2b, 64, 0), H2,
-                                               W2, s, skip)));
+                                               W2, s, skip, n->engine, n->derr)));
     ConvIn uc1{n->h2b, 64, 0, n->cat1, 96, 64, nullptr};
     UCK((conv_ex<96, 32, 3, IN_UPCAT, OUT_BF16, 64>(uc1, n->bal, w + n->woff[L1c], to(n->h1c, 32, 0), H1, W1, s,
-                                                    skip)));
+                                                    skip, n->engine, n->derr)));
     ConvIn uc0{n->h1c, 32, 0, n->cat0, 48, 32, nullptr};
     UCK((conv_ex<48, 16, 3, IN_UPCAT, OUT_BF16, 32>(uc0, n->bal, w + n->woff[L0c], to(n->h0c, 16, 0), H0, W0, s,
-                                                    skip)));
+                                                    skip, n->engine, n->derr)));
     ConvOut pl{y, 0, 0, accumulate};
-    UCK((conv_ex<16, 16, 1, IN_NHWC, OUT_PLANES>(nhwc(n->h0c, 16, 0), n->bal, w + n->woff[L0d], pl, H0, W0, s, skip)));
+    UCK((conv_ex<16, 16, 1, IN_NHWC, OUT_PLANES>(nhwc(n->h0c, 16, 0), n->bal, w + n->woff[L0d], pl, H0, W0, s, skip, n->engine, n->derr)));
     return cudaGetLastError();
 }
 
@@ -721,27 +972,42 @@ static cudaError_t backward(UNet* n, cudaStream_t s) {
     UCK(cudaMemsetAsync(g, 0, n->nw * 4, s));
     for (int l = 0; l < NL; ++l) UCK(transpose_w(n, l, s));
     UCK((wgrad<16, 16, 1>(n->h0c, 16, 0, n->dy, H0, W0, g + n->woff[L0d], s)));
-    UCK((conv<16, 16, 1, false>(n->dy, 16, 0, wt + n->woff[L0d], n->dh0c, 16, 0, H0, W0, s)));
+    UCK((conv<16, 16, 1, false>(n->dy, 16, 0, wt + n->woff[L0d], n->dh0c, 16, 0, H0, W0, s, nullptr, n->engine, n->derr)));
     UCK((wgrad<48, 16, 3>(n->cat0, 48, 0, n->dh0c, H0, W0, g + n->woff[L0c], s)));
-    UCK((conv<16, 48, 3, false>(n->dh0c, 16, 0, wt + n->woff[L0c], n->dcat0, 48, 0, H0, W0, s)));
+    UCK((conv<16, 48, 3, false>(n->dh0c, 16, 0, wt + n->woff[L0c], n->dcat0, 48, 0, H0, W0, s, nullptr, n->engine, n->derr)));
     upsample2_bwd<<<grid_for((size_t)H1 * W1 * 32), 256, 0, s>>>(n->dcat0, 48, 0, n->dh1c, 32, H0, W0);
     UCK((wgrad<96, 32, 3>(n->cat1, 96, 0, n->dh1c, H1, W1, g + n->woff[L1c], s)));
-    UCK((conv<32, 96, 3, false>(n->dh1c, 32, 0, wt + n->woff[L1c], n->dcat1, 96, 0, H1, W1, s)));
+    UCK((conv<32, 96, 3, false>(n->dh1c, 32, 0, wt + n->woff[L1c], n->dcat1, 96, 0, H1, W1, s, nullptr, n->engine, n->derr)));
     upsample2_bwd<<<grid_for((size_t)H2 * W2 * 64), 256, 0, s>>>(n->dcat1, 96, 0, n->dh2b, 64, H1, W1);
     UCK((wgrad<64, 64, 3>(n->h2a, 64, 0, n->dh2b, H2, W2, g + n->woff[L2b], s)));
-    UCK((conv<64, 64, 3, false>(n->dh2b, 64, 0, wt + n->woff[L2b], n->dh2a, 64, 0, H2, W2, s)));
+    UCK((conv<64, 64, 3, false>(n->dh2b, 64, 0, wt + n->woff[L2b], n->dh2a, 64, 0, H2, W2, s, nullptr, n->engine, n->derr)));
     UCK((wgrad<32, 64, 3>(n->p2, 32, 0, n->dh2a, H2, W2, g + n->woff[L2a], s)));
-    UCK((conv<64, 32, 3, false>(n->dh2a, 64, 0, wt + n->woff[L2a], n->dp2, 32, 0, H2, W2, s)));
+    UCK((conv<64, 32, 3, false>(n->dh2a, 64, 0, wt + n->woff[L2a], n->dp2, 32, 0, H2, W2, s, nullptr, n->engine, n->derr)));
     skip_grad<<<grid_for((size_t)H1 * W1 * 32), 256, 0, s>>>(n->dcat1, 96, 64, n->dp2, n->ds1, 32, H1, W1);
     UCK((wgrad<32, 32, 3>(n->h1a, 32, 0, n->ds1, H1, W1, g + n->woff[L1b], s)));
-    UCK((conv<32, 32, 3, false>(n->ds1, 32, 0, wt + n->woff[L1b], n->dh1a, 32, 0, H1, W1, s)));
+    UCK((conv<32, 32, 3, false>(n->ds1, 32, 0, wt + n->woff[L1b], n->dh1a, 32, 0, H1, W1, s, nullptr, n->engine, n->derr)));
     UCK((wgrad<16, 32, 3>(n->p1, 16, 0, n->dh1a, H1, W1, g + n->woff[L1a], s)));
-    UCK((conv<32, 16, 3, false>(n->dh1a, 32, 0, wt + n->woff[L1a], n->dp1, 16, 0, H1, W1, s)));
+    UCK((conv<32, 16, 3, false>(n->dh1a, 32, 0, wt + n->woff[L1a], n->dp1, 16, 0, H1, W1, s, nullptr, n->engine, n->derr)));
     skip_grad<<<grid_for((size_t)H0 * W0 * 16), 256, 0, s>>>(n->dcat0, 48, 32, n->dp1, n->ds0, 16, H0, W0);
     UCK((wgrad<16, 16, 3>(n->h0a, 16, 0, n->ds0, H0, W0, g + n->woff[L0b], s)));
-    UCK((conv<16, 16, 3, false>(n->ds0, 16, 0, wt + n->woff[L0b], n->dh0a, 16, 0, H0, W0, s)));
+    UCK((conv<16, 16, 3, false>(n->ds0, 16, 0, wt + n->woff[L0b], n->dh0a, 16, 0, H0, W0, s, nullptr, n->engine, n->derr)));
     UCK((wgrad<16, 16, 3>(n->x0, 16, 0, n->dh0a, H0, W0, g + n->woff[L0a], s)));
     return cudaGetLastError();
+}
+
+cudaError_t unet_set_engine(UNet* n, int engine) {
+    if (engine != ENGINE_TCGEN05 && engine != ENGINE_MMA_SYNC) return cudaErrorInvalidValue;
+    n->engine = engine;
+    return cudaSuccess;
+}
+
+int unet_engine(const UNet* n) { return n->engine; }
+
+cudaError_t unet_check(UNet* n, cudaStream_t s) {
+    int e = 0;
+    UCK(cudaMemcpyAsync(&e, n->derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    UCK(cudaStreamSynchronize(s));
+    return e ? cudaErrorLaunchTimeout : cudaSuccess;
 }
 
 cudaError_t unet_apply(UNet* n, const float* x, float* y, int accumulate, const int* skip, cudaStream_t s) {
@@ -768,7 +1034,7 @@ cudaError_t unet_loss_grad(UNet* n, const float* x, const float* t, double* loss
     if (grads_host) UCK(cudaMemcpyAsync(grads_host, n->g32, n->nw * 4, cudaMemcpyDeviceToHost, s));
     UCK(cudaStreamSynchronize(s));
     if (loss) *loss = sc[1];
-    return cudaSuccess;
+    return unet_check(n, s);
 }
 
 cudaError_t unet_train(UNet* n, const float* X, const float* T, int npairs, int epochs, float lr,
@@ -795,7 +1061,8 @@ cudaError_t unet_train(UNet* n, const float* X, const float* T, int npairs, int 
         }
         if (loss_hist) loss_hist[ep] = tot / npairs;
     }
-    return cudaStreamSynchronize(s);
+    UCK(cudaStreamSynchronize(s));
+    return unet_check(n, s);
 }
 
 }  // namespace jfnk

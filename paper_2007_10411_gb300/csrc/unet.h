@@ -41,6 +41,15 @@ cudaError_t unet_set_weights(UNet* net, const float* host, cudaStream_t s);
 cudaError_t unet_apply(UNet* net, const float* x, float* y, int accumulate, const int* skip, cudaStream_t s);
 int unet_launches_per_apply();
 
+// Convolution engine: 0 tcgen05.mma with TMEM accumulators (default), 1 the
+// mma.sync path.  Both compute the same layers (float32 accumulation).
+cudaError_t unet_set_engine(UNet* net, int engine);
+int unet_engine(const UNet* net);
+
+// Synchronises s and reports cudaErrorLaunchTimeout when a tensor-core wait of
+// an earlier convolution timed out (the flag stays set).
+cudaError_t unet_check(UNet* net, cudaStream_t s);
+
 // Loss L = 1/2 ||B (N(x) - t)||^2 / ||B x||^2 and dL/dW (float32, flat order of
 // unet_get_weights) for one pair; grads may be NULL (loss only).
 cudaError_t unet_loss_grad(UNet* net, const float* x, const float* t, double* loss, float* grads_host,

@@ -33,8 +33,10 @@ EXPORTS = (
     "jfnk_create_batch", "jfnk_destroy_batch", "jfnk_batch_handle", "jfnk_step_batch",
     "jfnk_unet_init", "jfnk_unet_num_weights", "jfnk_unet_get_weights", "jfnk_unet_set_weights",
     "jfnk_unet_capture", "jfnk_unet_pair_count", "jfnk_unet_get_pair", "jfnk_unet_train",
-    "jfnk_unet_forward", "jfnk_unet_loss_grad", "jfnk_set_precond",
+    "jfnk_unet_forward", "jfnk_unet_loss_grad", "jfnk_set_precond", "jfnk_unet_set_engine",
+    "jfnk_unet_status",
 )
+UNET_TCGEN05, UNET_MMA_SYNC = 0, 1
 
 PC_NONE, PC_BLOCK, PC_UNET, PC_SCHUR, PC_NONLINEAR = 0, 1, 2, 3, 4
 PAIRS_NEWTON, PAIRS_ARNOLDI = 1, 2
@@ -137,6 +139,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.jfnk_unet_forward.argtypes = [P, P, P]
     lib.jfnk_unet_loss_grad.argtypes = [P, P, P, ctypes.POINTER(D), P]
     lib.jfnk_set_precond.argtypes = [P, I]
+    lib.jfnk_unet_set_engine.argtypes = [P, I]
+    lib.jfnk_unet_status.argtypes = [P]
     lib.jfnk_status_str.argtypes = [I]
     lib.jfnk_status_str.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -332,6 +336,14 @@ class Solver:
     def unet_forward(self, x, y):
         _check(self.lib.jfnk_unet_forward(self.h, _fptr(x), _fptr(y)), "jfnk_unet_forward")
 
+    def unet_set_engine(self, engine: int):
+        """Convolution engine of the network: UNET_TCGEN05 (default) or UNET_MMA_SYNC."""
+        _check(self.lib.jfnk_unet_set_engine(self.h, int(engine)), "jfnk_unet_set_engine")
+
+    def unet_status(self):
+        """Raises JfnkError (JFNK_ERR_TIMEOUT) if a tensor-core wait of a convolution timed out."""
+        _check(self.lib.jfnk_unet_status(self.h), "jfnk_unet_status")
+
     def unet_loss_grad(self, x, t, grads: bool = True):
         import numpy as np
         loss = ctypes.c_double(0.0)
@@ -376,6 +388,39 @@ class Batch:
         h = ctypes.c_void_p()
         _check(self.lib.jfnk_batch_handle(self.b, i, ctypes.byref(h)), "jfnk_batch_handle")
         _check(self.lib.jfnk_set_surface_flux(h, None if H is None else _ptr(H)), "jfnk_set_surface_flux")
+
+    def handle(self, i: int):
+        h = ctypes.c_void_p()
+        _check(self.lib.jfnk_batch_handle(self.b, i, ctypes.byref(h)), "jfnk_batch_handle")
+        return h
+
+    def kernel_timing(self, families=KERNEL_FAMILIES):
+        """CUDA-event timing of the named kernel families on every instance's handle."""
+        mask = 0
+        for f in families:
+            mask |= 1 << KERNEL_FAMILIES.index(f)
+        for i in range(self.n):
+            _check(self.lib.jfnk_kernel_timing(self.handle(i), mask), "jfnk_kernel_timing")
+
+    def kernel_timing_read(self) -> dict:
+        """Per-family launches, summed launch time and algorithmic bytes over all instances."""
+        out = {name: {"launches": 0, "ms": 0.0, "bytes": 0.0} for name in KERNEL_FAMILIES}
+        for i in range(self.n):
+            arr = (KernelTime * len(KERNEL_FAMILIES))()
+            _check(self.lib.jfnk_kernel_timing_read(self.handle(i), arr), "jfnk_kernel_timing_read")
+            for name, a in zip(KERNEL_FAMILIES, arr):
+                out[name]["launches"] += a.launches
+                out[name]["ms"] += a.ms
+                out[name]["bytes"] += a.bytes
+        return out
+
+    def budgets(self, i: int, u) -> dict:
+        """jfnk_budgets on instance i's handle (its stream is synchronised)."""
+        b = Budget()
+        _check(self.lib.jfnk_budgets(self.handle(i), _ptr(u), ctypes.byref(b)), "jfnk_budgets")
+        nf = 4 if self.cases[i]["grid"]["dim"] == 2 else 5
+        return {"E_k": b.E_k, "E_p": b.E_p, "sum_theta": b.sum_theta, "sum_div": b.sum_div,
+                "max": list(b.max[:nf]), "min": list(b.min[:nf])}
 
     def step(self, states) -> list:
         ptrs = (ctypes.c_void_p * self.n)(*[_ptr(u) for u in states])

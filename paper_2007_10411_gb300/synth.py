@@ -38,6 +38,7 @@ NOSLIP = 1
 
 SGS_CONST = 0
 SGS_SMAGORINSKY = 1
+SGS_DEARDORFF = 2      # anisotropic closure of Section 2.4 (Eq. KmM)
 
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -163,6 +164,17 @@ def uhi_batch(n: int = 16, nx0: int = 512, nz0: int = 128) -> list:
         nz = nz0 * (1 + i // 8)
         c = case("uhi_%dx%d" % (nx, nz))
         c["init"]["H0"] = 25.0 * (930.0 / 25.0) ** (i / max(n - 1, 1))
+        out.append(c)
+    return out
+
+
+def uhi3d_batch(n: int = 4, nx: int = 384, ny: int = 384, nz: int = 128, H0=(25.0, 100.0, 400.0, 930.0)) -> list:
+    """Batched 3-D urban heat island: n instances of nx x ny x nz on 100 x 100 x 2 km with a
+    20 x 20 km urban patch, surface heat flux H0[i] W/m^2, rest initial state."""
+    out = []
+    for i in range(n):
+        c = case("uhi3d_%dx%dx%d" % (nx, ny, nz))
+        c["init"]["H0"] = float(H0[i % len(H0)])
         out.append(c)
     return out
 

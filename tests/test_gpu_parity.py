@@ -52,7 +52,7 @@ def rel_per_field(got, ref):
 
 
 def make_case(nx, nz, smag=False, bc=synth.FREESLIP, beta=3.058e-3, prec=synth.PREC_FP64, heat=False,
-              precond=synth.PC_BLOCK):
+              precond=synth.PC_BLOCK, dear=False):
     c = synth.case("tiny_%dx%d" % (nx, nz))
     c["grid"]["bc_bottom"] = bc
     c["strat"]["beta"] = beta
@@ -60,13 +60,18 @@ def make_case(nx, nz, smag=False, bc=synth.FREESLIP, beta=3.058e-3, prec=synth.P
     c["opts"]["precond"] = precond
     if smag:
         c["sgs"]["mode"] = synth.SGS_SMAGORINSKY
+    if dear:
+        # anisotropic cells (dz = 0.6 dx), so that K_m != K_M and K_h != K_H
+        c["sgs"]["mode"] = synth.SGS_DEARDORFF
+        c["grid"]["lz"] *= 0.6
     if heat:
         c["init"] = {"kind": "rest", "H0": 200.0, "patch_halfwidth": c["grid"]["lx"] / 5, "xi": 0.1, "l": 1.5}
     return c
 
 
 GRIDS = [(16, 8), (100, 37), (130, 70)]          # one tile, ragged multi-tile, ragged in x and z
-VARIANTS = [dict(), dict(smag=True), dict(smag=True, bc=synth.NOSLIP, heat=True)]
+VARIANTS = [dict(), dict(smag=True), dict(smag=True, bc=synth.NOSLIP, heat=True),
+            dict(dear=True, bc=synth.NOSLIP, heat=True)]
 
 
 def _setup(c, seed=5):
@@ -182,6 +187,7 @@ STEP_CASES = [
     ("smag", dict(smag=True)),
     ("noslip_heat", dict(smag=True, bc=synth.NOSLIP, heat=True)),
     ("no_pc", dict(precond=synth.PC_NONE)),
+    ("deardorff", dict(dear=True)),
 ]
 
 
@@ -279,11 +285,14 @@ def test_full_size_step_satisfies_trapezoid_equation():
     assert abs(b["sum_div"]) < 1e-9 * np.max(np.abs(got[:2])) * m.nx * m.nz * m.dx
 
 
-@pytest.mark.parametrize("smag", [False, True])
-def test_tile_shapes_give_identical_results(smag):
+@pytest.mark.parametrize("smag", [False, True, "deardorff"])
+@pytest.mark.parametrize("grid", [(130, 70), (70, 33)])
+def test_tile_shapes_give_identical_results(smag, grid):
     """Every tile shape of the float32 Jv and preconditioner kernels computes the same values
-    (bitwise), on a grid with ragged tiles in x and z; autotune picks a valid shape."""
-    c = make_case(130, 70, smag=smag, prec=synth.PREC_MIXED)
+    (bitwise), on grids with ragged tiles in x and z (nz = 33: the top tile holds one row, so
+    the flux rows above it are ghost rows whose eddy coefficient comes from the rows below);
+    autotune picks a valid shape."""
+    c = make_case(*grid, smag=smag is True, dear=smag == "deardorff", prec=synth.PREC_MIXED, bc=synth.NOSLIP)
     U, m, s = _setup(c)
     V = np.random.Generator(np.random.PCG64(29)).standard_normal(U.shape)
     outs_jv, outs_pc = [], []

@@ -43,13 +43,19 @@ def rel_per_field(got, ref):
                      for f in range(ref.shape[0])])
 
 
-def make3(nx, ny, nz, smag=False, bc=synth.FREESLIP, prec=synth.PREC_FP64, heat=False, beta=3.058e-3):
+def make3(nx, ny, nz, smag=False, bc=synth.FREESLIP, prec=synth.PREC_FP64, heat=False, beta=3.058e-3,
+          dear=False):
     c = synth.case("tiny3d_%dx%dx%d" % (nx, ny, nz))
     c["grid"]["bc_bottom"] = bc
     c["strat"]["beta"] = beta
     c["opts"]["precision"] = prec
     if smag:
         c["sgs"]["mode"] = synth.SGS_SMAGORINSKY
+    if dear:
+        # anisotropic closure on anisotropic cells (dy = 0.8 dx, dz = 0.6 dx)
+        c["sgs"]["mode"] = synth.SGS_DEARDORFF
+        c["grid"]["ly"] *= 0.8
+        c["grid"]["lz"] *= 0.6
     if heat:
         c["init"] = {"kind": "rest", "H0": 200.0, "patch_halfwidth": c["grid"]["lx"] / 5, "xi": 0.1, "l": 1.5}
     return c
@@ -67,7 +73,8 @@ def setup(c, seed=5):
 
 
 GRIDS3 = [(16, 8, 8), (21, 13, 9)]          # one tile; ragged, several tiles in x, y, z
-VARS3 = [dict(), dict(smag=True), dict(smag=True, bc=synth.NOSLIP, heat=True)]
+VARS3 = [dict(), dict(smag=True), dict(smag=True, bc=synth.NOSLIP, heat=True),
+         dict(dear=True, bc=synth.NOSLIP, heat=True)]
 
 
 @pytest.mark.parametrize("grid", GRIDS3)
@@ -142,7 +149,8 @@ def test_budgets_parity_3d():
     assert got["max"] == ref["max"] and got["min"] == ref["min"]
 
 
-@pytest.mark.parametrize("var", [dict(), dict(smag=True), dict(smag=True, bc=synth.NOSLIP, heat=True)])
+@pytest.mark.parametrize("var", [dict(), dict(smag=True), dict(smag=True, bc=synth.NOSLIP, heat=True),
+                                 dict(dear=True)])
 @pytest.mark.parametrize("prec", [synth.PREC_FP64, synth.PREC_MIXED])
 def test_step_parity_3d(var, prec):
     c = make3(16, 12, 8, prec=prec, **var)

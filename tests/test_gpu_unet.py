@@ -9,8 +9,9 @@ deepest path rounds 12 times, so the expected relative error of the output
 is about sqrt(12) u ~ 7e-3 for well-scaled weights; the forward bound is
 2e-2.  Gradients add the rounding of the output gradient and of the
 back-propagated activations (about twice as many roundings) and a float32
-sum over every pixel: bound 5e-2 per layer (relative L2 of the layer's
-gradient block).
+sum over every pixel: the expected per-layer error is about sqrt(24) u ~ 1e-2
+at most; the bound is 1e-2 per layer (relative L2 of the layer's gradient
+block), the tolerance set for the bfloat16 network (measured: 6e-4 .. 6e-3).
 """
 import numpy as np
 import pytest
@@ -60,12 +61,17 @@ def rel(a, b) -> float:
     return float(np.linalg.norm(np.asarray(a, float) - np.asarray(b, float)) / np.linalg.norm(np.asarray(b, float)))
 
 
+ENGINES = [0, 1]     # jfnk.UNET_TCGEN05 (default), jfnk.UNET_MMA_SYNC
+
+
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("name", ["tiny_64x32", "tiny_96x64"])
-def test_forward_matches_oracle(name):
+def test_forward_matches_oracle(name, engine):
     from paper_2007_10411_gb300 import jfnk
     c = learned_case(name)
     s = jfnk.Solver(c)
     s.unet_init(1)
+    s.unet_set_engine(engine)
     w = random_weights(11)
     assert s.unet_num_weights() == w.size == ou.num_weights()
     s.unet_set_weights(w)
@@ -83,6 +89,7 @@ def test_forward_matches_oracle(name):
     # per field as well (no field may be badly off while the total is fine)
     for f in range(4):
         assert rel(y[f], ref[f]) < 3e-2, (f, rel(y[f], ref[f]))
+    s.unet_status()
     s.close()
 
 
@@ -100,11 +107,13 @@ def test_zero_init_network_is_zero_and_block_pc_unchanged():
     s.close()
 
 
-def test_gradient_matches_oracle():
+@pytest.mark.parametrize("engine", ENGINES)
+def test_gradient_matches_oracle(engine):
     from paper_2007_10411_gb300 import jfnk
     c = learned_case("tiny_64x32")
     s = jfnk.Solver(c)
     s.unet_init(2)
+    s.unet_set_engine(engine)
     w = random_weights(12)
     s.unet_set_weights(w)
     nz, nx = c["grid"]["nz"], c["grid"]["nx"]
@@ -115,12 +124,16 @@ def test_gradient_matches_oracle():
     L_ref, g_ref = ou.loss_grad(w.astype(np.float64), X.astype(np.float64), T.astype(np.float64), ou.balance(c))
     assert abs(loss - L_ref) <= 2e-2 * L_ref, (loss, L_ref)
     offs = np.concatenate([[0], np.cumsum(ou.layer_sizes())])
+    errs = {}
     for li, (name, ci, co, k) in enumerate(ou.LAYERS):
         a, b = g[offs[li]:offs[li + 1]], g_ref[offs[li]:offs[li + 1]]
         if name == "L0a":   # padded input channels: both zero
             a = a.reshape(k * k, co, ci)[:, :, :4]
             b = b.reshape(k * k, co, ci)[:, :, :4]
-        assert rel(a, b) < 5e-2, (name, rel(a, b))
+        errs[name] = rel(a, b)
+    print("per-layer gradient relative L2:", {k: "%.2e" % v for k, v in errs.items()})
+    for name, e in errs.items():
+        assert e < 1e-2, (name, e)
     s.close()
 
 
@@ -275,4 +288,27 @@ def test_trained_network_gain_over_block_preconditioner():
     assert sum(x["pc_switches"] for x in sl) == 0
     assert gl <= 0.7 * gb, (gb, gl)
     assert float((vb - vl).norm() / vb.norm()) < 1e-6
+    s.close()
+
+
+def test_engines_agree_on_the_benchmark_grid():
+    """The tcgen05 and mma.sync convolutions compute the same network: on the 1024 x 512
+    grid (several persistent tiles per CTA, every layer shape) their outputs differ only
+    by the bfloat16 rounding of activations that sit on a rounding boundary."""
+    from paper_2007_10411_gb300 import jfnk
+    c = learned_case("thermal_stable_1024x512")
+    s = jfnk.Solver(c)
+    s.unet_init(3)
+    w = random_weights(13)
+    s.unet_set_weights(w)
+    nz, nx = c["grid"]["nz"], c["grid"]["nx"]
+    x = torch.randn(4 * nz * nx, device="cuda", dtype=torch.float32, generator=torch.Generator("cuda").manual_seed(9))
+    ys = []
+    for engine in ENGINES:
+        s.unet_set_engine(engine)
+        y = torch.empty_like(x)
+        s.unet_forward(x, y)
+        s.unet_status()
+        ys.append(y.cpu().numpy())
+    assert rel(ys[0], ys[1]) < 1e-2, rel(ys[0], ys[1])
     s.close()
