@@ -172,6 +172,23 @@ def unet_apply_timing(jfnk, torch, s, npt: int, reps: int, stream) -> dict:
             "mma_sync": out["mma_sync"]}
 
 
+def ncu_fp64_pipe():
+    """(pipe fraction, ncu launch time in us) of the float64 Jacobian product from
+    profiles/ncu_traffic.txt, when the captured source still has that hash; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    src = os.path.join(ROOT, "paper_2007_10411_gb300", "csrc", "stencil.cu")
+    try:
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        for line in open(path):
+            t = line.split()
+            if len(t) >= 5 and t[0] == "fp64_pipe_jv" and t[4] == sha:
+                return float(t[1]), float(t[2])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
 def ncu_traffic() -> dict:
     """Per-algorithmic-byte DRAM traffic of the kernels captured with ncu (profiles/ncu_traffic.txt).
 
@@ -192,7 +209,7 @@ def ncu_traffic() -> dict:
     try:
         for line in open(path):
             t = line.split()
-            if len(t) >= 4 and not t[0].startswith("#"):
+            if len(t) >= 4 and not t[0].startswith("#") and t[0] != "fp64_pipe_jv":
                 fam, ratio, src, sha = t[0], float(t[1]), t[2], t[3]
                 if hashes.get(src) == sha:
                     out[fam] = ratio
@@ -773,6 +790,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         u64 = torch.from_numpy(U0).cuda()
         s64.step(u64)
         barrier()
+        s64.kernel_timing(("jv",))
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
@@ -780,10 +798,21 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         a1.record(stream)
         a1.synchronize()
         ms64 = slowest(a0.elapsed_time(a1))
+        kj = s64.kernel_timing_read()["jv"]
+        s64.kernel_timing(())
         fp64 = {"value": npt * args.fp64_steps * world / (ms64 / 1e3) / 1e6,
                 "ms_per_step": ms64 / args.fp64_steps,
                 "gmres_iters_per_step": statistics.mean(s["gmres_iters"] for s in st64),
                 "newton_per_step": statistics.mean(s["newton_iters"] for s in st64)}
+        pipe = ncu_fp64_pipe()
+        if kj["launches"] and pipe is not None:
+            live_us = kj["ms"] / kj["launches"] * 1e3
+            fp64["fp64_pipe"] = {
+                "kernel": "stencil2d<double, MODE_JV> (float64 Jacobian product)", "bound": "fp64 pipe",
+                "live_us_per_launch": live_us, "ncu_us_per_launch": pipe[1], "ncu_pipe_frac": pipe[0],
+                "frac": pipe[0] * pipe[1] / live_us,
+                "how": "FP64-pipe busy fraction from one ncu capture (profiles/ncu_traffic.txt), scaled by the "
+                       "ratio of that launch time to the live per-launch time of this leg (CUDA events)"}
         s64.close()
 
     precision = None

@@ -791,12 +791,18 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
     *restarts = 0;
     *conv = 0;
     *switched = 0;
+    // Two-pass Arnoldi steps (fused_cycle) pay for themselves where a solve runs
+    // many Krylov steps per expensive preconditioner apply; the Schur-complement
+    // preconditioner converges in a few steps per solve, where the lagged scheme's
+    // one extra (speculative) preconditioner apply and Jacobian product per cycle
+    // cost more than the basis passes it saves: it keeps three passes.
+    const bool fused = pc && !h->G.pc_schur;
     for (int cycle = 0;; ++cycle) {
-        if (pc) {
+        if (fused) {
             jfnk_status st = fused_cycle<T>(h, uT, learned, arnoldi_pairs, lag);
             if (st != JFNK_OK) return st;
         }
-        for (int j = 0; j < m && !pc; ++j) {
+        for (int j = 0; j < m && !fused; ++j) {
             T* vj = V + (size_t)j * ld;
             T* zj = Z + (size_t)j * ld;
             if (pc) {

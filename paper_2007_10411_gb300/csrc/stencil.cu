@@ -55,16 +55,25 @@ template <> struct PcTile<1> { static constexpr int TX = 32, TZ = 16; };
 template <> struct PcTile<2> { static constexpr int TX = 64, TZ = 8; };
 template <> struct PcTile<3> { static constexpr int TX = 32, TZ = 8; };
 
+// Explicitly rounded product and fused multiply-add: expressions written with
+// them round the same way in every instantiation (tile shape) of a kernel.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename T>
 __device__ __forceinline__ T dd(const T* s, int i, int st, T inv_h) {
-    return (T(2.0 / 3.0) * (s[i + st] - s[i - st]) - T(1.0 / 12.0) * (s[i + 2 * st] - s[i - 2 * st])) * inv_h;
+    const T d1 = s[i + st] - s[i - st], d2 = s[i + 2 * st] - s[i - 2 * st];
+    return rmul(rfma(T(2.0 / 3.0), d1, rmul(T(-1.0 / 12.0), d2)), inv_h);
 }
 
 // derivative of the point-wise product a*b
 template <typename T>
 __device__ __forceinline__ T ddp(const T* a, const T* b, int i, int st, T inv_h) {
-    return (T(2.0 / 3.0) * (a[i + st] * b[i + st] - a[i - st] * b[i - st]) -
-            T(1.0 / 12.0) * (a[i + 2 * st] * b[i + 2 * st] - a[i - 2 * st] * b[i - 2 * st])) * inv_h;
+    const T d1 = rfma(a[i + st], b[i + st], -rmul(a[i - st], b[i - st]));
+    const T d2 = rfma(a[i + 2 * st], b[i + 2 * st], -rmul(a[i - 2 * st], b[i - 2 * st]));
+    return rmul(rfma(T(2.0 / 3.0), d1, rmul(T(-1.0 / 12.0), d2)), inv_h);
 }
 
 // derivative of the flux K*g where K may be a constant (Kc) or an array
@@ -221,13 +230,6 @@ __device__ __forceinline__ int eddy_row(int qz, int z0, int nz, int QZ) {
     else if (gz >= nz) iq = (gz < nz + R) ? (2 * nz - 1 - gz) - z0 + R : -1;
     return (iq >= 0 && iq < QZ) ? iq : -1;
 }
-
-// Explicitly rounded product and fused multiply-add: expressions written with
-// them round the same way in every instantiation (tile shape) of a kernel.
-__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Deardorff heat factor s (1 + a l(s)), l = min(Delta, c_l s) (c_l < 0: l = Delta).
 template <typename T>
@@ -1303,24 +1305,27 @@ cheb2d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
                 if (gz >= G.nz) break;
                 const T* gxr = gxs + tz * QX + tx + R;          // centre of the x taps
                 const T* gzc = gzs + (tz + R) * TX + tx;        // centre of the z taps
+                // explicitly rounded (rmul / rfma): every tile shape computes the same bits
                 T difx, difz;
                 if (SMAG) {
                     const T* kx = kk_ + (tz + R) * QX + tx + R;
                     const T* kz = kz_ + (tz + R) * QX + tx + R;
-                    difx = T(2.0 / 3.0) * (kx[1] * gxr[1] - kx[-1] * gxr[-1]) -
-                           T(1.0 / 12.0) * (kx[2] * gxr[2] - kx[-2] * gxr[-2]);
-                    difz = T(2.0 / 3.0) * (kz[QX] * gzc[TX] - kz[-QX] * gzc[-TX]) -
-                           T(1.0 / 12.0) * (kz[2 * QX] * gzc[2 * TX] - kz[-2 * QX] * gzc[-2 * TX]);
+                    const T x1 = rfma(kx[1], gxr[1], -rmul(kx[-1], gxr[-1]));
+                    const T x2 = rfma(kx[2], gxr[2], -rmul(kx[-2], gxr[-2]));
+                    const T z1 = rfma(kz[QX], gzc[TX], -rmul(kz[-QX], gzc[-TX]));
+                    const T z2 = rfma(kz[2 * QX], gzc[2 * TX], -rmul(kz[-2 * QX], gzc[-2 * TX]));
+                    difx = rfma(T(2.0 / 3.0), x1, rmul(T(-1.0 / 12.0), x2));
+                    difz = rfma(T(2.0 / 3.0), z1, rmul(T(-1.0 / 12.0), z2));
                 } else {
-                    difx = Kc * (T(2.0 / 3.0) * (gxr[1] - gxr[-1]) - T(1.0 / 12.0) * (gxr[2] - gxr[-2]));
-                    difz = Kc * (T(2.0 / 3.0) * (gzc[TX] - gzc[-TX]) - T(1.0 / 12.0) * (gzc[2 * TX] - gzc[-2 * TX]));
+                    difx = rmul(Kc, rfma(T(2.0 / 3.0), gxr[1] - gxr[-1], rmul(T(-1.0 / 12.0), gxr[2] - gxr[-2])));
+                    difz = rmul(Kc, rfma(T(2.0 / 3.0), gzc[TX] - gzc[-TX], rmul(T(-1.0 / 12.0), gzc[2 * TX] - gzc[-2 * TX])));
                 }
-                const T dif = difx * idx_ + difz * idz_;
+                const T dif = rfma(difx, idx_, rmul(difz, idz_));
                 const T xk = zs[(tz + HALO) * SX + tx + HALO];
                 const int o = gz * G.nx + gxx;
-                const T res = rv[q] - (tdt * xk - dif);
-                const T dprev = FIRST ? rv[q] * ith : dv[q];
-                const T dk = a1 * dprev + a2 * res;
+                const T res = rv[q] - rfma(tdt, xk, -dif);
+                const T dprev = FIRST ? rmul(rv[q], ith) : dv[q];
+                const T dk = rfma(a1, dprev, rmul(a2, res));
                 const T xn = xk + dk;
                 zf[o] = xn;
                 if (!LAST) dof[o] = dk;

@@ -14,6 +14,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -62,6 +63,29 @@ __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                  : "r"(addr));
+}
+
+// Programmatic dependent launch between the layers: a convolution is launched
+// before its predecessor has finished, prefetches its weights (which do not
+// depend on the predecessor), and waits (griddepcontrol.wait) before it reads
+// the previous layer's output or the skip flag; each CTA releases the next
+// layer's launch (griddepcontrol.launch_dependents) when it starts its last tile.
+__device__ __forceinline__ void net_pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void net_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t net_launch(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 // 16-byte global -> shared copy; src_bytes = 0 writes zeros (src is not read).
@@ -171,7 +195,6 @@ __device__ __forceinline__ void stage_tile(const ConvIn& in, const Bal& bal, int
 template <int CI, int CO, int KS, int INMODE, int OUTMODE, int CU>
 __global__ void __launch_bounds__(CONV_THREADS)
 conv_mma(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int Wd, const int* skip) {
-    if (skip != nullptr && *skip) return;
     using S = ConvShape<CI, CO, KS>;
     constexpr int HP = S::HP, IW = S::IW, IH = S::IH, CIP = S::CIP;
     extern __shared__ __align__(16) unsigned char sm[];
@@ -183,12 +206,17 @@ conv_mma(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int
     const int ntiles = ntx * nty;
     int tile = blockIdx.x;
     if (tile >= ntiles) return;
-    // weights (group 0) and the first tile (group 1)
+    // weights (group 0, before the wait for the previous layer) and the first tile (group 1)
     for (int idx = threadIdx.x; idx < KS * KS * CO * (CI / 8); idx += blockDim.x) {
         const int row = idx / (CI / 8), v = idx - row * (CI / 8);
         cp_async16(ws_addr + (uint32_t)((row * CIP + v * 8) * sizeof(bf16)), W + (size_t)row * CI + v * 8, 16);
     }
     cp_async_commit();
+    net_pdl_wait();
+    if (skip != nullptr && *skip) {
+        cp_async_wait<0>();
+        return;
+    }
     stage_tile<CI, IH, IW, CIP, INMODE, CU>(in, bal, H, Wd, (tile / ntx) * CONV_TH, (tile % ntx) * CONV_TW, HP,
                                             xs_addr0);
     cp_async_commit();
@@ -201,6 +229,7 @@ conv_mma(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int
     int buf = 0;
     for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
         const int next = tile + gridDim.x;
+        if (next >= ntiles) net_pdl_trigger();     // last tile of this CTA
         if (next < ntiles)
             stage_tile<CI, IH, IW, CIP, INMODE, CU>(in, bal, H, Wd, (next / ntx) * CONV_TH, (next % ntx) * CONV_TW,
                                                     HP, xs_addr0 + (buf ^ 1) * xs_bytes);
@@ -363,7 +392,6 @@ constexpr long long TC_WAIT_LIMIT = 1ll << 26;    // mbarrier polls before a til
 template <int CI, int CO, int KS, int INMODE, int OUTMODE, int CU>
 __global__ void __launch_bounds__(CONV_THREADS)
 conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int Wd, const int* skip, int* err) {
-    if (skip != nullptr && *skip) return;
     using S = TcShape<CI, CO, KS>;
     constexpr uint32_t IDESC = tc_idesc(128, CO);
     extern __shared__ __align__(16) unsigned char sm[];    // no-swizzle operands need 16-byte alignment
@@ -377,6 +405,20 @@ conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int 
     const uint32_t ws = smem_u32(sm);
     const uint32_t xs0 = ws + S::W_BYTES;
     const uint32_t mb[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
+    // weights into K-major core matrices: (tap, co, 8 channels v) -> tap*B_TAP + (co/8)*B_SBO + v*128 + (co%8)*16;
+    // issued before the wait for the previous layer (they do not depend on it)
+    for (int idx = threadIdx.x; idx < KS * KS * CO * S::C8; idx += blockDim.x) {
+        const int row = idx / S::C8, v = idx - row * S::C8;
+        const int tap = row / CO, co = row - tap * CO;
+        cp_async16(ws + (uint32_t)(tap * S::B_TAP + (co >> 3) * S::B_SBO + v * S::B_LBO + (co & 7) * 16),
+                   W + (size_t)row * CI + v * 8, 16);
+    }
+    net_pdl_wait();
+    if (skip != nullptr && *skip) {
+        cp_async_commit();           // the weight copies must be part of a group for the wait to cover them
+        cp_async_wait<0>();
+        return;
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                      "r"((uint32_t)S::TCOLS)
@@ -387,13 +429,6 @@ conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int 
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb[0]), "r"(1u) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb[1]), "r"(1u) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    // weights into K-major core matrices: (tap, co, 8 channels v) -> tap*B_TAP + (co/8)*B_SBO + v*128 + (co%8)*16
-    for (int idx = threadIdx.x; idx < KS * KS * CO * S::C8; idx += blockDim.x) {
-        const int row = idx / S::C8, v = idx - row * S::C8;
-        const int tap = row / CO, co = row - tap * CO;
-        cp_async16(ws + (uint32_t)(tap * S::B_TAP + (co >> 3) * S::B_SBO + v * S::B_LBO + (co & 7) * 16),
-                   W + (size_t)row * CI + v * 8, 16);
     }
     stage_tile<CI, S::IH, S::IW, 0, INMODE, CU, 1>(in, bal, H, Wd, (tile / ntx) * CONV_TH, (tile % ntx) * CONV_TW,
                                                    S::HP, xs0);
@@ -438,6 +473,7 @@ conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int 
         }
         // the other input buffer is free (its tile's MMAs completed before its epilogue)
         const int next = tile + gridDim.x;
+        if (next >= ntiles) net_pdl_trigger();     // last tile of this CTA: release the next layer
         if (next < ntiles)
             stage_tile<CI, S::IH, S::IW, 0, INMODE, CU, 1>(in, bal, H, Wd, (next / ntx) * CONV_TH,
                                                            (next % ntx) * CONV_TW, S::HP, xs0 + (buf ^ 1) * S::A_BYTES);
@@ -715,19 +751,34 @@ cudaError_t conv_ex_tc(const ConvIn& in, const Bal& bal, const bf16* W, const Co
     if (max_ctas == 0) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CONV_THREADS, S::SMEM)) != cudaSuccess)
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
             return e;
-        // at most 512 TMEM columns per SM: more CTAs would wait in tcgen05.alloc
-        per_sm = per_sm < 512 / S::TCOLS ? per_sm : 512 / S::TCOLS;
-        max_ctas = sms * (per_sm > 0 ? per_sm : 1);
+        int dev = 0, sms = 0, regs_sm = 0, smem_sm = 0, thr_sm = 0, smem_res = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess)
+            return e;
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        // The runtime's occupancy calculator reports one CTA per SM for any kernel
+        // that allocates tensor memory; the SM holds as many as its registers,
+        // threads and shared memory allow, and tcgen05.alloc waits only when the
+        // 512 TMEM columns are taken, so the grid is sized from those limits and
+        // from 512 / TCOLS.
+        const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * CONV_THREADS;
+        int per_sm = regs_cta > 0 ? regs_sm / regs_cta : 1;
+        per_sm = std::min(per_sm, thr_sm / CONV_THREADS);
+        per_sm = std::min(per_sm, smem_sm / (int)(S::SMEM + fa.sharedSizeBytes + smem_res));
+        per_sm = std::min(per_sm, 512 / S::TCOLS);
+        max_ctas = sms * std::max(per_sm, 1);
     }
     const int ntiles = ((Wd + CONV_TW - 1) / CONV_TW) * ((H + CONV_TH - 1) / CONV_TH);
     const int grid = ntiles < max_ctas ? ntiles : max_ctas;
-    kern<<<grid, CONV_THREADS, S::SMEM, s>>>(in, bal, W, out, H, Wd, skip, err);
-    return cudaGetLastError();
+    return net_launch(kern, grid, CONV_THREADS, S::SMEM, s, in, bal, W, out, H, Wd, skip, err);
 }
 
 template <int CI, int CO, int KS, int INMODE, int OUTMODE, int CU = 0>
@@ -749,8 +800,7 @@ cudaError_t conv_ex(const ConvIn& in, const Bal& bal, const bf16* W, const ConvO
     }
     const int ntiles = ((Wd + CONV_TW - 1) / CONV_TW) * ((H + CONV_TH - 1) / CONV_TH);
     const int grid = ntiles < max_ctas ? ntiles : max_ctas;
-    kern<<<grid, CONV_THREADS, S::SMEM, s>>>(in, bal, W, out, H, Wd, skip);
-    return cudaGetLastError();
+    return net_launch(kern, grid, CONV_THREADS, S::SMEM, s, in, bal, W, out, H, Wd, skip);
 }
 
 // plain NHWC -> NHWC convolution (training path)

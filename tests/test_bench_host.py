@@ -24,9 +24,13 @@ def test_traffic_table_lists_every_family_with_sane_ratios():
     then reports the roofline's traffic as null until the counters are re-taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     fams = {l.split()[0] for l in open(path) if l.strip() and not l.startswith("#")}
-    assert {"jv", "precond", "precond_schur", "arnoldi_a", "arnoldi_b", "arnoldi_c"} <= fams
+    # the right-preconditioned step runs passes CA (family arnoldi_a) and B
+    assert {"jv", "precond", "arnoldi_a", "arnoldi_b", "fp64_pipe_jv"} <= fams
     for fam, r in bench.ncu_traffic().items():
         assert 0.2 < r < 1.5, (fam, r)
+    pipe = bench.ncu_fp64_pipe()
+    if pipe is not None:
+        assert 0.0 < pipe[0] <= 1.0 and pipe[1] > 0.0
 
 
 def test_traffic_table_ignores_stale_hashes(tmp_path, monkeypatch):
