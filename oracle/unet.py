@@ -31,6 +31,11 @@ pass, its gradients and its training pairs can be checked:
   - Newton correction: b = -W R(u_k), beta = ||b||, x_hat the scaled
     correction GMRES returned: X = b / beta, T = x_hat / beta - M^{-1} X;
 * the preconditioner itself: P v = M^{-1} v + N(v).
+* 3-D grids (5 fields u, v, w, theta, p on [z][y][x]): the same graph with
+  every 3x3 convolution applied to each horizontal (y, x) plane (zero padding
+  at the plane's edges), 2x2x2 average pooling and 2x2x2 nearest upsampling,
+  so that the vertical coupling enters through the coarser levels; the
+  balance is B = diag(1, 1, 1, s_theta / Theta_b, s_p / P_b).
 
 Everything is whole-array numpy in float64 following these definitions, with
 no blocking or fusion.  Pins (tests/test_oracle_unet.py): single layers
@@ -38,7 +43,12 @@ against scipy.signal.correlate2d, an identity network (with and without a
 balance), a 4x4 block-mean network, the adjoint identities of pooling and
 upsampling, the gradient against exact central differences, the balance
 making the linearised acoustic and buoyancy couplings symmetric, and the
-training-pair identities on a linear system solved exactly.
+training-pair identities on a linear system solved exactly; for 3-D grids,
+the per-plane convolution against scipy's 3-D correlation with a kernel one
+plane deep, the identity network, the 4x4x4 block mean of the coarse path,
+planes that stay uncoupled without the coarse levels, the 3-D adjoints, the
+gradient with a five-field balance, and the five-field balance making the
+couplings skew.
 """
 from __future__ import annotations
 
@@ -51,8 +61,13 @@ LAYERS = (
     ("L2a", 32, 64, 3), ("L2b", 64, 64, 3),
     ("L1c", 96, 32, 3), ("L0c", 48, 16, 3), ("L0d", 16, 16, 1),
 )
-NFIELDS = 4
+NFIELDS = 4           # 2-D fields (u, w, theta, p); 3-D adds v
 IN_CH = 16
+
+
+def nfields(X: np.ndarray) -> int:
+    """Field count of a state of shape (nf, nz, nx) (2-D) or (nf, nz, ny, nx) (3-D)."""
+    return 4 if X.ndim == 3 else 5
 
 
 def layer_sizes():
@@ -114,93 +129,121 @@ def conv_grads(x: np.ndarray, w: np.ndarray, dout: np.ndarray):
     return dxp[:, hp:hp + H, hp:hp + W], dw
 
 
+def conv_planes(x: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """conv() on every horizontal plane of x (C, nz, ny, nx) (3-D), or conv() itself (2-D)."""
+    if x.ndim == 3:
+        return conv(x, w)
+    return np.stack([conv(x[:, z], w) for z in range(x.shape[1])], axis=1)
+
+
+def conv_grads_planes(x: np.ndarray, w: np.ndarray, dout: np.ndarray):
+    if x.ndim == 3:
+        return conv_grads(x, w, dout)
+    dx = np.zeros_like(x)
+    dw = np.zeros_like(w)
+    for z in range(x.shape[1]):
+        dxz, dwz = conv_grads(x[:, z], w, dout[:, z])
+        dx[:, z] = dxz
+        dw += dwz
+    return dx, dw
+
+
 def pool2(x: np.ndarray) -> np.ndarray:
-    """2x2 average."""
-    C, H, W = x.shape
-    return x.reshape(C, H // 2, 2, W // 2, 2).mean(axis=(2, 4))
-
-
-def pool2_adjoint(d: np.ndarray) -> np.ndarray:
-    return np.repeat(np.repeat(d, 2, axis=1), 2, axis=2) * 0.25
+    """2x2 average (2-D) or 2x2x2 average (3-D)."""
+    if x.ndim == 3:
+        C, H, W = x.shape
+        return x.reshape(C, H // 2, 2, W // 2, 2).mean(axis=(2, 4))
+    C, D, H, W = x.shape
+    return x.reshape(C, D // 2, 2, H // 2, 2, W // 2, 2).mean(axis=(2, 4, 6))
 
 
 def up2(x: np.ndarray) -> np.ndarray:
-    """Nearest-neighbour upsampling x2."""
-    return np.repeat(np.repeat(x, 2, axis=1), 2, axis=2)
+    """Nearest-neighbour upsampling x2 along every spatial axis."""
+    for ax in range(1, x.ndim):
+        x = np.repeat(x, 2, axis=ax)
+    return x
+
+
+def pool2_adjoint(d: np.ndarray) -> np.ndarray:
+    return up2(d) / 2.0 ** (d.ndim - 1)
 
 
 def up2_adjoint(d: np.ndarray) -> np.ndarray:
-    C, H, W = d.shape
-    return d.reshape(C, H // 2, 2, W // 2, 2).sum(axis=(2, 4))
+    if d.ndim == 3:
+        C, H, W = d.shape
+        return d.reshape(C, H // 2, 2, W // 2, 2).sum(axis=(2, 4))
+    C, D, H, W = d.shape
+    return d.reshape(C, D // 2, 2, H // 2, 2, W // 2, 2).sum(axis=(2, 4, 6))
 
 
 def balance(case: dict) -> np.ndarray:
-    """Per-field factors B (velocity components, theta, p) of a 2-D case."""
+    """Per-field factors B (velocity components, theta, p) of a 2-D or 3-D case."""
     st, op = case["strat"], case["opts"]
     su = op["scale_u"]
-    b = np.ones(NFIELDS)
+    nf = 4 if case["grid"]["dim"] == 2 else 5
+    b = np.ones(nf)
     if st["beta"] != 0.0 and st["g"] > 0.0:
-        b[2] = op["scale_theta"] / (su * np.sqrt(abs(st["beta"]) * st["theta0"] / st["g"]))
+        b[nf - 2] = op["scale_theta"] / (su * np.sqrt(abs(st["beta"]) * st["theta0"] / st["g"]))
     if st["gamma_p"] * st["pbar"] > 0.0:
-        b[3] = op["scale_p"] / (su * np.sqrt(st["gamma_p"] * st["pbar"] / st["theta0"]))
+        b[nf - 1] = op["scale_p"] / (su * np.sqrt(st["gamma_p"] * st["pbar"] / st["theta0"]))
     return b
 
 
-def _b(B, ndim=3):
-    B = np.ones(NFIELDS) if B is None else np.asarray(B, dtype=np.float64)
-    return B.reshape((NFIELDS,) + (1,) * (ndim - 1))
+def _b(B, nf, ndim):
+    B = np.ones(nf) if B is None else np.asarray(B, dtype=np.float64)
+    return B.reshape((nf,) + (1,) * (ndim - 1))
 
 
 # ----------------------------------------------------------------- network
 def forward(flat: np.ndarray, X: np.ndarray, B=None):
-    """N(X) for X of shape (4, nz, nx); returns (y (4, nz, nx), activations).
+    """N(X) for X of shape (4, nz, nx) (2-D) or (5, nz, ny, nx) (3-D); returns (y, activations).
 
     The activations hold the raw network run on B X (balanced units); y is
-    B^-1 times its first four output channels.
+    B^-1 times its first nf output channels.
     """
     w = split_weights(flat)
-    H, W = X.shape[1:]
-    assert H % 4 == 0 and W % 4 == 0
+    nf = nfields(X)
+    assert all(n % 4 == 0 for n in X.shape[1:])
     a = {}
-    a["x0"] = np.zeros((IN_CH, H, W))
-    a["x0"][:NFIELDS] = _b(B) * X
-    a["h0a"] = conv(a["x0"], w["L0a"])
-    a["s0"] = conv(a["h0a"], w["L0b"])
+    a["x0"] = np.zeros((IN_CH,) + X.shape[1:])
+    a["x0"][:nf] = _b(B, nf, X.ndim) * X
+    a["h0a"] = conv_planes(a["x0"], w["L0a"])
+    a["s0"] = conv_planes(a["h0a"], w["L0b"])
     a["p1"] = pool2(a["s0"])
-    a["h1a"] = conv(a["p1"], w["L1a"])
-    a["s1"] = conv(a["h1a"], w["L1b"])
+    a["h1a"] = conv_planes(a["p1"], w["L1a"])
+    a["s1"] = conv_planes(a["h1a"], w["L1b"])
     a["p2"] = pool2(a["s1"])
-    a["h2a"] = conv(a["p2"], w["L2a"])
-    a["h2b"] = conv(a["h2a"], w["L2b"])
+    a["h2a"] = conv_planes(a["p2"], w["L2a"])
+    a["h2b"] = conv_planes(a["h2a"], w["L2b"])
     a["cat1"] = np.concatenate([up2(a["h2b"]), a["s1"]])
-    a["h1c"] = conv(a["cat1"], w["L1c"])
+    a["h1c"] = conv_planes(a["cat1"], w["L1c"])
     a["cat0"] = np.concatenate([up2(a["h1c"]), a["s0"]])
-    a["h0c"] = conv(a["cat0"], w["L0c"])
-    a["out"] = conv(a["h0c"], w["L0d"])
-    return a["out"][:NFIELDS] / _b(B), a
+    a["h0c"] = conv_planes(a["cat0"], w["L0c"])
+    a["out"] = conv_planes(a["h0c"], w["L0d"])
+    return a["out"][:nf] / _b(B, nf, X.ndim), a
 
 
 def backward(flat: np.ndarray, a: dict, dy: np.ndarray) -> np.ndarray:
-    """Flat gradient of <dy, raw output channels 0..3> given the activations of forward()."""
+    """Flat gradient of <dy, raw output channels 0..nf-1> given the activations of forward()."""
     w = split_weights(flat)
     g = {}
     dout = np.zeros_like(a["out"])
-    dout[:NFIELDS] = dy
-    d_h0c, g["L0d"] = conv_grads(a["h0c"], w["L0d"], dout)
-    d_cat0, g["L0c"] = conv_grads(a["cat0"], w["L0c"], d_h0c)
+    dout[:dy.shape[0]] = dy
+    d_h0c, g["L0d"] = conv_grads_planes(a["h0c"], w["L0d"], dout)
+    d_cat0, g["L0c"] = conv_grads_planes(a["cat0"], w["L0c"], d_h0c)
     d_h1c = up2_adjoint(d_cat0[:32])
     d_s0 = d_cat0[32:].copy()
-    d_cat1, g["L1c"] = conv_grads(a["cat1"], w["L1c"], d_h1c)
+    d_cat1, g["L1c"] = conv_grads_planes(a["cat1"], w["L1c"], d_h1c)
     d_h2b = up2_adjoint(d_cat1[:64])
     d_s1 = d_cat1[64:].copy()
-    d_h2a, g["L2b"] = conv_grads(a["h2a"], w["L2b"], d_h2b)
-    d_p2, g["L2a"] = conv_grads(a["p2"], w["L2a"], d_h2a)
+    d_h2a, g["L2b"] = conv_grads_planes(a["h2a"], w["L2b"], d_h2b)
+    d_p2, g["L2a"] = conv_grads_planes(a["p2"], w["L2a"], d_h2a)
     d_s1 += pool2_adjoint(d_p2)
-    d_h1a, g["L1b"] = conv_grads(a["h1a"], w["L1b"], d_s1)
-    d_p1, g["L1a"] = conv_grads(a["p1"], w["L1a"], d_h1a)
+    d_h1a, g["L1b"] = conv_grads_planes(a["h1a"], w["L1b"], d_s1)
+    d_p1, g["L1a"] = conv_grads_planes(a["p1"], w["L1a"], d_h1a)
     d_s0 += pool2_adjoint(d_p1)
-    d_h0a, g["L0b"] = conv_grads(a["h0a"], w["L0b"], d_s0)
-    _, g["L0a"] = conv_grads(a["x0"], w["L0a"], d_h0a)
+    d_h0a, g["L0b"] = conv_grads_planes(a["h0a"], w["L0b"], d_s0)
+    _, g["L0a"] = conv_grads_planes(a["x0"], w["L0a"], d_h0a)
     return join_weights(g)
 
 
@@ -209,14 +252,14 @@ def apply(flat: np.ndarray, X: np.ndarray, B=None) -> np.ndarray:
 
 
 def loss(flat: np.ndarray, X: np.ndarray, T: np.ndarray, B=None) -> float:
-    b = _b(B)
+    b = _b(B, nfields(X), X.ndim)
     d = b * (apply(flat, X, B) - T)
     return 0.5 * float(np.sum(d * d)) / float(np.sum((b * X) ** 2))
 
 
 def loss_grad(flat: np.ndarray, X: np.ndarray, T: np.ndarray, B=None):
     """(L, dL/dw) for L = 1/2 ||B (N(X) - T)||^2 / ||B X||^2."""
-    b = _b(B)
+    b = _b(B, nfields(X), X.ndim)
     y, a = forward(flat, X, B)
     xn2 = float(np.sum((b * X) ** 2))
     r = b * (y - T)                      # raw output minus B T

@@ -354,3 +354,65 @@ def test_deardorff_heat_ratio_length_is_caught():
 def test_deardorff_uncapped_mixing_length_is_caught():
     cs = tdd.dd_case(beta=synth.brunt_beta(0.01))
     assert _dd_cap_error(_mutant(cs, "no_cap"), cs) > 0.1
+
+
+# ------------------------------------------------- 3-D network (oracle/unet.py)
+def _expect_pin_failure(pin, monkeypatch, name, fake):
+    from oracle import unet
+    monkeypatch.setattr(unet, name, fake)
+    try:
+        pin()
+    except AssertionError:
+        return
+    raise AssertionError("pin %s passed with a mutated %s" % (pin.__name__, name))
+
+
+def test_3d_pool_that_subsamples_z_is_caught(monkeypatch):
+    from oracle import unet
+    from tests import test_oracle_unet as pins
+    orig = unet.pool2
+
+    def pool_even_plane(x):          # averages (y, x) but takes every other z plane
+        if x.ndim == 3:
+            return orig(x)
+        return orig(x[:, 0::2].repeat(2, axis=1))
+    _expect_pin_failure(pins.test_coarse_path_is_4x4x4_block_mean, monkeypatch, "pool2", pool_even_plane)
+
+
+def test_3d_conv_over_the_wrong_planes_is_caught(monkeypatch):
+    from oracle import unet
+    from tests import test_oracle_unet as pins
+
+    def conv_xz_planes(x, w):        # 3x3 over (z, x) for every y instead of (y, x) for every z
+        if x.ndim == 3:
+            return unet.conv(x, w)
+        return np.stack([unet.conv(x[:, :, y], w) for y in range(x.shape[2])], axis=2)
+    _expect_pin_failure(pins.test_conv_planes_matches_scipy_3d_correlate, monkeypatch, "conv_planes",
+                        conv_xz_planes)
+
+
+def test_3d_balance_on_the_2d_field_indices_is_caught(monkeypatch):
+    from oracle import unet
+    from tests import test_oracle_unet as pins
+    orig = unet.balance
+
+    def balance_2d_indices(case):    # theta / p factors on fields 2 and 3 (w, theta) in 3-D
+        b = orig(case)
+        if b.size == 5:
+            b = np.array([1.0, 1.0, b[3], b[4], 1.0])
+        return b
+    _expect_pin_failure(pins.test_balance_3d_makes_the_couplings_skew, monkeypatch, "balance",
+                        balance_2d_indices)
+
+
+def test_3d_upsampling_that_skips_z_adjoint_is_caught(monkeypatch):
+    from oracle import unet
+    from tests import test_oracle_unet as pins
+    orig = unet.up2_adjoint
+
+    def adjoint_first_plane(d):      # sums the (y, x) children but reads only even z planes, twice
+        if d.ndim == 3:
+            return orig(d)
+        return orig(d[:, 0::2].repeat(2, axis=1))
+    _expect_pin_failure(pins.test_gradient_3d_with_balance_matches_central_differences, monkeypatch,
+                        "up2_adjoint", adjoint_first_plane)
