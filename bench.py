@@ -70,6 +70,9 @@ def parse():
                    help="only time this many applies of the learned-preconditioner network (profiling)")
     p.add_argument("--learned", default="thermal_stable_256x128:40:3,thermal_stable_1024x512:5:2",
                    help="learned-preconditioner legs workload:epochs:steps,... ('' skips)")
+    p.add_argument("--learned3d", default="thermal3d_256x256x128:4:2:48",
+                   help="3-D learned-preconditioner leg workload:epochs:steps:pairs, with the Schur-complement "
+                        "and plain float64 arms ('' skips)")
     return p.parse_args()
 
 
@@ -132,22 +135,29 @@ def measured_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
-# Algorithmic FLOPs of one network apply per full-resolution grid point: 2 k^2
-# cin cout per layer and output pixel (L0a counts its 4 real input channels,
-# L0d its 4 used outputs), level-1 layers / 4, level-2 layers / 16.
-UNET_FLOPS_PER_POINT = (2 * 9 * 4 * 16 + 2 * 9 * 16 * 16                      # L0a, L0b
-                        + (2 * 9 * 16 * 32 + 2 * 9 * 32 * 32) // 4            # L1a, L1b
-                        + (2 * 9 * 32 * 64 + 2 * 9 * 64 * 64) // 16           # L2a, L2b
-                        + (2 * 9 * 96 * 32) // 4 + 2 * 9 * 48 * 16 + 2 * 16 * 4)  # L1c, L0c, L0d
+def unet_flops_per_point(dim: int = 2) -> float:
+    """Algorithmic FLOPs of one network apply per full-resolution grid point: 2 k^2
+    cin cout per layer and output pixel (L0a counts its nf real input channels,
+    L0d its nf used outputs); level-1 layers are on 1/4 of the points (1/8 in 3-D),
+    level-2 layers on 1/16 (1/64)."""
+    nf, r1, r2 = (4, 1 / 4, 1 / 16) if dim == 2 else (5, 1 / 8, 1 / 64)
+    return (2 * 9 * nf * 16 + 2 * 9 * 16 * 16                                  # L0a, L0b
+            + (2 * 9 * 16 * 32 + 2 * 9 * 32 * 32) * r1                         # L1a, L1b
+            + (2 * 9 * 32 * 64 + 2 * 9 * 64 * 64) * r2                         # L2a, L2b
+            + 2 * 9 * 96 * 32 * r1 + 2 * 9 * 48 * 16 + 2 * 16 * nf)            # L1c, L0c, L0d
 
 
-def unet_apply_timing(jfnk, torch, s, npt: int, reps: int, stream) -> dict:
+UNET_FLOPS_PER_POINT = unet_flops_per_point(2)
+
+
+def unet_apply_timing(jfnk, torch, s, npt: int, reps: int, stream, dim: int = 2) -> dict:
     """CUDA-event time of the network apply alone (jfnk_unet_forward) and its tensor roofline,
     for the tcgen05 convolutions (the default engine) and, beside them, the mma.sync ones."""
-    x = torch.randn(4 * npt, device="cuda", dtype=torch.float32, generator=torch.Generator("cuda").manual_seed(5))
+    nf = 4 if dim == 2 else 5
+    x = torch.randn(nf * npt, device="cuda", dtype=torch.float32, generator=torch.Generator("cuda").manual_seed(5))
     y = torch.empty_like(x)
     peaks = measured_peaks()
-    flops = UNET_FLOPS_PER_POINT * npt
+    flops = unet_flops_per_point(dim) * npt
     out = {}
     for engine, tag in ((jfnk.UNET_MMA_SYNC, "mma_sync"), (jfnk.UNET_TCGEN05, "tcgen05")):
         s.unet_set_engine(engine)
@@ -499,19 +509,28 @@ def run_batch(args, rank: int, world: int, local_rank: int):
     print(json.dumps(line), flush=True)
 
 
-def learned_leg(jfnk, synth, torch, stream, name: str, epochs: int, steps: int, barrier, slowest) -> dict:
+def grid_points(c: dict) -> int:
+    g = c["grid"]
+    return g["nx"] * g["nz"] * (g["ny"] if g["dim"] == 3 else 1)
+
+
+def learned_leg(jfnk, synth, torch, stream, name: str, epochs: int, steps: int, barrier, slowest,
+                capacity: int = 900, others: bool = False) -> dict:
     """Learned right preconditioner against the field-block one on one workload.
 
     Training pairs: every Arnoldi step of two plain steps from the initial
-    state (at most 900); Adam, lr 3e-4.  Then `steps` timed steps from the same
-    state with each preconditioner (CUDA events on the solver's stream).
+    state (at most `capacity`); Adam, lr 3e-4.  Then `steps` timed steps from
+    the same state with each preconditioner (CUDA events on the solver's
+    stream).  With `others`, the same steps with the acoustic Schur-complement
+    preconditioner (16 sweeps) and with the plain float64 path (field block).
     """
     c = synth.with_options(synth.case(name), precision=synth.PREC_MIXED, precond=jfnk.PC_UNET)
-    npt = c["grid"]["nx"] * c["grid"]["nz"]
+    npt = grid_points(c)
+    dim = c["grid"]["dim"]
     s = jfnk.Solver(c, stream=stream)
     s.set_precond(jfnk.PC_BLOCK)
     s.unet_init(7)
-    s.unet_capture(900, jfnk.PAIRS_ARNOLDI)
+    s.unet_capture(capacity, jfnk.PAIRS_ARNOLDI)
     u = torch.from_numpy(synth.initial_state(c).reshape(-1).copy()).cuda()
     for _ in range(2):
         s.step(u)
@@ -541,8 +560,30 @@ def learned_leg(jfnk, synth, torch, stream, name: str, epochs: int, steps: int, 
                     "pc_switches": sum(x.get("pc_switches", 0) for x in st),
                     "pc_fallback": sum(int(x.get("pc_fallback", False)) for x in st)}
     out["learned_over_block"] = out["learned"]["value"] / out["block"]["value"]
-    out["network_apply"] = unet_apply_timing(jfnk, torch, s, npt, 20, stream)
+    out["network_apply"] = unet_apply_timing(jfnk, torch, s, npt, 20 if dim == 2 else 5, stream, dim)
     s.close()
+    if others:
+        arms = (("schur", synth.with_options(c, precond=jfnk.PC_SCHUR, pc_sweeps=16)),
+                ("fp64", synth.with_options(c, precision=synth.PREC_FP64, precond=jfnk.PC_BLOCK)))
+        for tag, co in arms:
+            so = jfnk.Solver(co, stream=stream)
+            v = u.clone()
+            so.step(v.clone())                        # warm (first-call set-up)
+            barrier()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            st = [so.step(v) for _ in range(steps)]
+            a1.record(stream)
+            a1.synchronize()
+            ms = slowest(a0.elapsed_time(a1))
+            so.close()
+            out[tag] = {"value": npt * steps / (ms / 1e3) / 1e6, "ms_per_step": ms / steps,
+                        "gmres_iters_per_step": statistics.mean(x["gmres_iters"] for x in st),
+                        "newton_per_step": statistics.mean(x["newton_iters"] for x in st),
+                        "converged": all(x["converged"] for x in st)}
+        out["learned_over_fp64"] = out["learned"]["value"] / out["fp64"]["value"]
+        out["learned_over_schur"] = out["learned"]["value"] / out["schur"]["value"]
     return out
 
 
@@ -557,13 +598,13 @@ def run_unet_forward(args):
     __graft_entry__.build()
     torch.cuda.set_device(0)
     c = synth.with_options(synth.case(args.workload), precision=synth.PREC_MIXED, precond=jfnk.PC_UNET)
-    npt = c["grid"]["nx"] * c["grid"]["nz"]
+    npt = grid_points(c)
     stream = torch.cuda.current_stream()
     s = jfnk.Solver(c, stream=stream)
     s.unet_init(1)
     rng = np.random.Generator(np.random.PCG64(3))
     s.unet_set_weights((0.05 * rng.standard_normal(s.unet_num_weights())).astype(np.float32))
-    r = unet_apply_timing(jfnk, torch, s, npt, args.unet_forward, stream)
+    r = unet_apply_timing(jfnk, torch, s, npt, args.unet_forward, stream, c["grid"]["dim"])
     r.update({"workload": args.workload, "applies": args.unet_forward})
     print(json.dumps(r), flush=True)
     s.close()
@@ -835,6 +876,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             name, ep, st = item.split(":")
             learned.append(learned_leg(jfnk, synth, torch, stream, name, int(ep), int(st), barrier, slowest))
 
+    learned3d = None
+    if args.learned3d and case["grid"]["dim"] == 2:
+        name, ep, st, cap = args.learned3d.split(":")
+        learned3d = learned_leg(jfnk, synth, torch, stream, name, int(ep), int(st), barrier, slowest,
+                                capacity=int(cap), others=True)
+
     if rank != 0:
         return
     iters = statistics.mean(s["gmres_iters"] for s in stats)
@@ -891,6 +938,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "schur_over_block": (schur["value"] / value) if schur else None,
         "schur_over_fp64": (schur["value"] / fp64["value"]) if (schur and fp64) else None,
         "learned_pc": learned or None,
+        "learned_pc_3d": learned3d,
         "learned_over_fp64": next((L["learned"]["value"] / fp64["value"] for L in learned
                                    if fp64 and L["workload"] == args.workload), None),
         "cpu_baseline": cpu,

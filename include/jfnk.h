@@ -293,7 +293,7 @@ jfnk_status jfnk_step_batch(jfnk_batch* b, double* const* u, jfnk_stats* stats, 
 /* ----------------------------------------------- learned preconditioner
  * Not in the paper (its preconditioner is the field-block one of Section
  * 2.5.2, which stays the fallback).  A linear convolutional U-Net N acts on
- * the four scaled field planes of a Krylov vector and corrects the block
+ * the scaled field planes of a Krylov vector (4 in 2-D, 5 in 3-D) and corrects the block
  * preconditioner M: with precond = JFNK_PC_UNET the flexible-GMRES direction
  * of v is z = M^-1 v + N(v).
  *
@@ -303,13 +303,19 @@ jfnk_status jfnk_step_batch(jfnk_batch* b, double* const* u, jfnk_stats* stats, 
  *   = s1, 2x2 average pool, L2a 3x3 32->64, L2b 3x3 64->64, nearest
  *   upsampling, concat [up, s1], L1c 3x3 96->32, nearest upsampling, concat
  *   [up, s0], L0c 3x3 48->16, L0d 1x1 16->16 (first 4 channels = N(v)).
+ * 3-D grids: input and output have 5 channels (u, v, w, theta, p); every 3x3
+ * convolution acts on each horizontal (y, x) plane (rows y, columns x, zero
+ * padding at the plane's edges), pooling averages 2x2x2 blocks and the
+ * upsampling repeats each point 2x2x2, so that the vertical coupling enters
+ * through the coarser levels.
  * Flat weight order (float32): layers in that order, each [tap][cout][cin]
  * with tap = ky * k + kx reading the input at offset (ky - k/2, kx - k/2).
  * Convolutions run on the tensor cores with bfloat16 operands and float32
  * accumulation; training keeps float32 master weights (Adam).
  *
  * The convolutions work in balanced units: N(v) = B^-1 net(B v) with
- * B = diag(1, 1, s_theta / Theta_b, s_p / P_b), s_* = scale_* of jfnk_opts,
+ * B = diag(1, 1, s_theta / Theta_b, s_p / P_b) (3-D: diag(1, 1, 1, s_theta /
+ * Theta_b, s_p / P_b)), s_* = scale_* of jfnk_opts,
  * Theta_b = s_u sqrt(|beta| theta0 / g) and P_b = s_u sqrt(gamma_p pbar /
  * theta0) (factor 1 where beta or gamma_p pbar is 0): the units in which the
  * linearised buoyancy and acoustic couplings of Eqs. ch2_28-ch2_30 are
@@ -325,8 +331,9 @@ jfnk_status jfnk_step_batch(jfnk_batch* b, double* const* u, jfnk_stats* stats, 
  *                       X = b / beta, T = x_hat / beta - M^-1 X.
  * The loss of a pair is 1/2 ||B (N(X) - T)||^2 / ||B X||^2.
  *
- * Only 2-D handles with precision JFNK_MIXED and nx, nz multiples of 32
- * accept these calls (and precond = JFNK_PC_UNET); others get
+ * Only handles with precision JFNK_MIXED on 2-D grids with nx, nz multiples of
+ * 32, or on 3-D grids with nx a multiple of 32, ny of 64 and nz of 4, accept
+ * these calls (and precond = JFNK_PC_UNET); others get
  * JFNK_ERR_UNSUPPORTED.  Safeguards: a GMRES cycle of m steps with the learned
  * preconditioner that reduces the residual by less than a factor 2 hands the
  * rest of that Newton solve to the field-block preconditioner (restarting from

@@ -119,16 +119,17 @@ static jfnk_status validate(const jfnk_grid* g, const jfnk_strat* s, const jfnk_
     if (o->wavelet_p != 2) return JFNK_ERR_UNSUPPORTED;
     if (g->nz < 4) return JFNK_ERR_INVALID_ARG;      // one mirror reflection covers the halo
     if (o->precond == JFNK_PC_UNET &&
-        (g->dim != 2 || o->precision != JFNK_MIXED || g->nx % 32 != 0 || g->nz % 32 != 0))
+        (o->precision != JFNK_MIXED || !unet_grid_ok(g->dim, g->nx, g->dim == 3 ? g->ny : 1, g->nz)))
         return JFNK_ERR_UNSUPPORTED;
     if (o->precond == JFNK_PC_SCHUR && o->pc_sweeps < 2) return JFNK_ERR_UNSUPPORTED;
     return JFNK_OK;
 }
 
-// The learned preconditioner is implemented for 2-D float32-basis handles on
-// grids whose sides are multiples of 32 (two 2x2 poolings of 8x8-aligned tiles).
+// The learned preconditioner is implemented for float32-basis handles on the
+// grids unet_grid_ok accepts (2-D: nx, nz multiples of 32; 3-D: nx of 32, ny of
+// 64, nz of 4).
 static bool unet_supported(const jfnk_handle* h) {
-    return h->G.dim == 2 && h->mixed && h->grid.nx % 32 == 0 && h->grid.nz % 32 == 0;
+    return h->mixed && unet_grid_ok(h->G.dim, h->grid.nx, h->G.ny, h->grid.nz);
 }
 
 static void free_all(jfnk_handle* h) {
@@ -1020,13 +1021,15 @@ extern "C" jfnk_status jfnk_unet_init(jfnk_handle* h, unsigned long long seed) {
     }
     // balanced units: the linearised acoustic and buoyancy couplings become skew-adjoint
     const double su = h->opts.scale_u;
-    double bal[4] = {1.0, 1.0, 1.0, 1.0};
+    // (velocity components 1, theta factor, p factor)
+    const int nf = h->G.dim == 2 ? 4 : 5;
+    double bal[5] = {1.0, 1.0, 1.0, 1.0, 1.0};
     if (h->strat.beta != 0.0 && h->strat.g > 0.0)
-        bal[2] = h->opts.scale_theta / (su * sqrt(fabs(h->strat.beta) * h->strat.theta0 / h->strat.g));
+        bal[nf - 2] = h->opts.scale_theta / (su * sqrt(fabs(h->strat.beta) * h->strat.theta0 / h->strat.g));
     if (h->strat.gamma_p * h->strat.pbar > 0.0)
-        bal[3] = h->opts.scale_p / (su * sqrt(h->strat.gamma_p * h->strat.pbar / h->strat.theta0));
+        bal[nf - 1] = h->opts.scale_p / (su * sqrt(h->strat.gamma_p * h->strat.pbar / h->strat.theta0));
     cudaError_t e = cudaSuccess;
-    h->net = unet_create(h->grid.nx, h->grid.nz, bal, seed, &e);
+    h->net = unet_create(h->G.dim, h->grid.nx, h->G.ny, h->grid.nz, bal, seed, &e);
     if (!h->net) {
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? JFNK_ERR_OOM : JFNK_ERR_CUDA;

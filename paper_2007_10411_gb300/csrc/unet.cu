@@ -1,5 +1,9 @@
 // Learned right preconditioner: linear 3-level U-Net (see unet.h).
 //
+// A 3-D grid is handled as the image of its nz * ny rows (z, y) by nx columns,
+// cut into slices of ny rows: the 3x3 convolutions read only rows of their
+// own slice, and pooling / upsampling pair slices as well as rows and columns.
+//
 // Convolutions: implicit GEMM per 16x8 pixel tile, M = 128 pixels (8 warps x 16),
 // N = output channels, K = 9 taps x input channels, using
 // mma.sync.m16n8k16.row.col.f32.bf16.bf16.f32 with ldmatrix fragments from
@@ -31,10 +35,35 @@ constexpr int KSZ[NL] = {3, 3, 3, 3, 3, 3, 3, 3, 1};
 
 typedef __nv_bfloat16 bf16;
 
+constexpr int MAXF = 5;   // field planes of a 3-D state (u, v, w, theta, p); 2-D has 4
+
 // Field balance of the network: it sees B x and returns B N(x).
 struct Bal {
-    float b[4], inv[4];
+    float b[MAXF], inv[MAXF];
+    int nf;
 };
+
+// Geometry of one level of the network.  A 2-D grid is one slice of H rows
+// (z) by Wd columns (x).  A 3-D grid [z][y][x] is a stack of H / Hs slices of
+// Hs rows (y) each: row r holds (z, y) = (r / Hs, r % Hs).  The 3x3
+// convolutions act within a slice (zero padding at its first and last rows);
+// pooling and upsampling pair slices 2z, 2z+1 as well when d3 = 1.
+struct Lv {
+    int H, Wd, Hs, d3;
+};
+
+// row of the coarser level holding the parent of fine row r
+__host__ __device__ __forceinline__ int coarse_row(int r, const Lv& f) {
+    const int z = r / f.Hs, y = r - z * f.Hs;
+    return (z >> 1) * (f.Hs >> 1) + (y >> 1);
+}
+
+// fine row of child (dz, dy) of coarse row q (f: the fine level)
+__host__ __device__ __forceinline__ int fine_row(int q, int dz, int dy, const Lv& f) {
+    const int hc = f.Hs >> 1;
+    const int z = q / hc, y = q - z * hc;
+    return (2 * z + dz) * f.Hs + 2 * y + dy;
+}
 
 // convolution tile: CONV_TH rows x CONV_TW columns, one warp per pair of rows
 constexpr int CONV_TW = 8, CONV_TH = 16, CONV_THREADS = 32 * CONV_TH / 2;
@@ -136,14 +165,17 @@ struct ConvOut {
 // (conv_tc): for every tile row iy and 8-channel group v, the IW pixels' 16-byte
 // groups lie contiguously, at iy * (CI/8) * IW * 16 + v * IW * 16 + ix * 16 bytes.
 template <int CI, int IH, int IW, int CIP, int INMODE, int CU, int LAYOUT = 0>
-__device__ __forceinline__ void stage_tile(const ConvIn& in, const Bal& bal, int H, int Wd, int y0, int x0, int hp,
+__device__ __forceinline__ void stage_tile(const ConvIn& in, const Bal& bal, const Lv& g, int y0, int x0, int hp,
                                            uint32_t xs_addr) {
     constexpr int VPP = CI / 8;
+    const int H = g.H, Wd = g.Wd;
+    const int sy0 = (y0 / g.Hs) * g.Hs;              // first row of the tile's slice
+    const int sy1 = min(sy0 + g.Hs, H);
     for (int idx = threadIdx.x; idx < IH * IW * VPP; idx += blockDim.x) {
         const int pix = idx / VPP, v = idx - pix * VPP;
         const int iy = pix / IW, ix = pix - iy * IW;
         const int gy = y0 + iy - hp, gx = x0 + ix - hp;
-        const bool ok = gy >= 0 && gy < H && gx >= 0 && gx < Wd;
+        const bool ok = gy >= sy0 && gy < sy1 && gx >= 0 && gx < Wd;
         const uint32_t dst = LAYOUT == 0 ? xs_addr + (uint32_t)((pix * CIP + v * 8) * sizeof(bf16))
                                          : xs_addr + (uint32_t)(((iy * VPP + v) * IW + ix) * 16);
         if constexpr (INMODE == IN_NHWC) {
@@ -152,7 +184,8 @@ __device__ __forceinline__ void stage_tile(const ConvIn& in, const Bal& bal, int
         } else if constexpr (INMODE == IN_UPCAT) {
             const bf16* src;
             if (v * 8 < CU)
-                src = ok ? in.a + ((size_t)(gy >> 1) * (Wd >> 1) + (gx >> 1)) * in.astr + in.aoff + v * 8 : in.a;
+                src = ok ? in.a + ((size_t)coarse_row(gy, g) * (Wd >> 1) + (gx >> 1)) * in.astr + in.aoff + v * 8
+                         : in.a;
             else
                 src = ok ? in.b + ((size_t)gy * Wd + gx) * in.bstr + in.boff + (v * 8 - CU) : in.b;
             cp_async16(dst, src, ok ? 16 : 0);
@@ -164,26 +197,31 @@ __device__ __forceinline__ void stage_tile(const ConvIn& in, const Bal& bal, int
                 for (int c = 0; c < 8; ++c) val[c] = __float2bfloat16(0.f);
                 if (v == 0 && ok) {
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        val[c] = __float2bfloat16(bal.b[c] * in.x[(size_t)c * npix + (size_t)gy * Wd + gx]);
+                    for (int c = 0; c < MAXF; ++c)
+                        if (c < bal.nf)
+                            val[c] = __float2bfloat16(bal.b[c] * in.x[(size_t)c * npix + (size_t)gy * Wd + gx]);
                 }
-            } else {   // IN_POOL: same arithmetic as the avgpool2 kernel (channels summed in d order)
+            } else {   // IN_POOL: same arithmetic as the avgpool2 kernel (children summed in (dz, d) order)
+                const Lv f{2 * g.H * (1 + g.d3), 2 * Wd, 2 * g.Hs, g.d3};     // the fine level
                 const int W2 = 2 * Wd;
                 float sum[8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) sum[c] = 0.f;
                 if (ok) {
+                    for (int dz = 0; dz <= g.d3; ++dz)
 #pragma unroll
-                    for (int d = 0; d < 4; ++d) {
-                        const uint4 q = *reinterpret_cast<const uint4*>(
-                            in.a + ((size_t)(2 * gy + d / 2) * W2 + 2 * gx + d % 2) * in.astr + in.aoff + v * 8);
-                        const bf16* e = reinterpret_cast<const bf16*>(&q);
+                        for (int d = 0; d < 4; ++d) {
+                            const uint4 q = *reinterpret_cast<const uint4*>(
+                                in.a + ((size_t)fine_row(gy, dz, d / 2, f) * W2 + 2 * gx + d % 2) * in.astr + in.aoff +
+                                v * 8);
+                            const bf16* e = reinterpret_cast<const bf16*>(&q);
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) sum[c] += __bfloat162float(e[c]);
-                    }
+                            for (int c = 0; c < 8; ++c) sum[c] += __bfloat162float(e[c]);
+                        }
                 }
+                const float wgt = g.d3 ? 0.125f : 0.25f;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) val[c] = __float2bfloat16(0.25f * sum[c]);
+                for (int c = 0; c < 8; ++c) val[c] = __float2bfloat16(wgt * sum[c]);
             }
             asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(dst),
                          "r"(reinterpret_cast<uint32_t*>(val)[0]), "r"(reinterpret_cast<uint32_t*>(val)[1]),
@@ -194,7 +232,7 @@ __device__ __forceinline__ void stage_tile(const ConvIn& in, const Bal& bal, int
 
 template <int CI, int CO, int KS, int INMODE, int OUTMODE, int CU>
 __global__ void __launch_bounds__(CONV_THREADS)
-conv_mma(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int Wd, const int* skip) {
+conv_mma(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, Lv lv, const int* skip) {
     using S = ConvShape<CI, CO, KS>;
     constexpr int HP = S::HP, IW = S::IW, IH = S::IH, CIP = S::CIP;
     extern __shared__ __align__(16) unsigned char sm[];
@@ -202,6 +240,7 @@ conv_mma(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int
     const uint32_t ws_addr = (uint32_t)__cvta_generic_to_shared(ws);
     const uint32_t xs_addr0 = ws_addr + (uint32_t)(S::W_ELEMS * sizeof(bf16));
     const uint32_t xs_bytes = (uint32_t)(S::X_ELEMS * sizeof(bf16));
+    const int H = lv.H, Wd = lv.Wd;
     const int ntx = (Wd + CONV_TW - 1) / CONV_TW, nty = (H + CONV_TH - 1) / CONV_TH;
     const int ntiles = ntx * nty;
     int tile = blockIdx.x;
@@ -217,7 +256,7 @@ conv_mma(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int
         cp_async_wait<0>();
         return;
     }
-    stage_tile<CI, IH, IW, CIP, INMODE, CU>(in, bal, H, Wd, (tile / ntx) * CONV_TH, (tile % ntx) * CONV_TW, HP,
+    stage_tile<CI, IH, IW, CIP, INMODE, CU>(in, bal, lv, (tile / ntx) * CONV_TH, (tile % ntx) * CONV_TW, HP,
                                             xs_addr0);
     cp_async_commit();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -231,7 +270,7 @@ conv_mma(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int
         const int next = tile + gridDim.x;
         if (next >= ntiles) net_pdl_trigger();     // last tile of this CTA
         if (next < ntiles)
-            stage_tile<CI, IH, IW, CIP, INMODE, CU>(in, bal, H, Wd, (next / ntx) * CONV_TH, (next % ntx) * CONV_TW,
+            stage_tile<CI, IH, IW, CIP, INMODE, CU>(in, bal, lv, (next / ntx) * CONV_TH, (next % ntx) * CONV_TW,
                                                     HP, xs_addr0 + (buf ^ 1) * xs_bytes);
         cp_async_commit();
         cp_async_wait<1>();
@@ -268,14 +307,15 @@ conv_mma(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int
         const int gyA = y0 + 2 * warp, gyB = gyA + 1, gx = x0 + g;
         if (gx < Wd) {
             if constexpr (OUTMODE == OUT_PLANES) {
-                // channels 2t, 2t+1 of block 0: lanes t = 0, 1 hold the four field channels
-                if (t < 2) {
+                // channels 2t, 2t+1 of block 0: lanes t = 0, 1, 2 hold the field channels
+                if (t < 3) {
                     float* o = reinterpret_cast<float*>(out.o);
                     const size_t npix = (size_t)H * Wd;
-                    const float inv[2] = {t == 0 ? bal.inv[0] : bal.inv[2], t == 0 ? bal.inv[1] : bal.inv[3]};
+                    const float inv[2] = {bal.inv[min(2 * t, MAXF - 1)], bal.inv[min(2 * t + 1, MAXF - 1)]};
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
                         const int ch = 2 * t + q;
+                        if (ch >= bal.nf) continue;
                         if (gyA < H) {
                             float* d = o + (size_t)ch * npix + (size_t)gyA * Wd + gx;
                             const float v = acc[0][q] * inv[q];
@@ -391,12 +431,13 @@ constexpr long long TC_WAIT_LIMIT = 1ll << 26;    // mbarrier polls before a til
 
 template <int CI, int CO, int KS, int INMODE, int OUTMODE, int CU>
 __global__ void __launch_bounds__(CONV_THREADS)
-conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int Wd, const int* skip, int* err) {
+conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, Lv lv, const int* skip, int* err) {
     using S = TcShape<CI, CO, KS>;
     constexpr uint32_t IDESC = tc_idesc(128, CO);
     extern __shared__ __align__(16) unsigned char sm[];    // no-swizzle operands need 16-byte alignment
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) unsigned long long mbar[2];
+    const int H = lv.H, Wd = lv.Wd;
     const int ntx = (Wd + CONV_TW - 1) / CONV_TW, nty = (H + CONV_TH - 1) / CONV_TH;
     const int ntiles = ntx * nty;
     int tile = blockIdx.x;
@@ -430,7 +471,7 @@ conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int 
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb[1]), "r"(1u) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    stage_tile<CI, S::IH, S::IW, 0, INMODE, CU, 1>(in, bal, H, Wd, (tile / ntx) * CONV_TH, (tile % ntx) * CONV_TW,
+    stage_tile<CI, S::IH, S::IW, 0, INMODE, CU, 1>(in, bal, lv, (tile / ntx) * CONV_TH, (tile % ntx) * CONV_TW,
                                                    S::HP, xs0);
     cp_async_commit();
     tc_fence_before();
@@ -475,7 +516,7 @@ conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int 
         const int next = tile + gridDim.x;
         if (next >= ntiles) net_pdl_trigger();     // last tile of this CTA: release the next layer
         if (next < ntiles)
-            stage_tile<CI, S::IH, S::IW, 0, INMODE, CU, 1>(in, bal, H, Wd, (next / ntx) * CONV_TH,
+            stage_tile<CI, S::IH, S::IW, 0, INMODE, CU, 1>(in, bal, lv, (next / ntx) * CONV_TH,
                                                            (next % ntx) * CONV_TW, S::HP, xs0 + (buf ^ 1) * S::A_BYTES);
         cp_async_commit();
         bool ready = false;
@@ -498,7 +539,8 @@ conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int 
                     float* o = reinterpret_cast<float*>(out.o);
                     const size_t npix = (size_t)H * Wd;
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
+                    for (int c = 0; c < MAXF; ++c) {
+                        if (c >= bal.nf) break;
                         float* d = o + (size_t)c * npix + (size_t)gy * Wd + gx;
                         const float val = v[c] * bal.inv[c];
                         *d = out.accumulate ? *d + val : val;
@@ -539,7 +581,7 @@ conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, int H, int 
 // dW[tap][co][ci] += sum_p dout[p][co] in[p + off(tap)][ci] over a 16x16 pixel tile.
 template <int CI, int CO, int KS>
 __global__ void __launch_bounds__(256)
-conv_wgrad(const bf16* __restrict__ in, int istr, int ioff, const bf16* __restrict__ dout, int H, int Wd,
+conv_wgrad(const bf16* __restrict__ in, int istr, int ioff, const bf16* __restrict__ dout, Lv lv,
            float* __restrict__ dW) {
     constexpr int TH = 16, TW = 16, HP = KS / 2;
     constexpr int IH = TH + 2 * HP, IW = TW + 2 * HP;
@@ -547,13 +589,15 @@ conv_wgrad(const bf16* __restrict__ in, int istr, int ioff, const bf16* __restri
     bf16* xs = reinterpret_cast<bf16*>(sm);        // [IH*IW][CI]
     bf16* ds = xs + IH * IW * CI;                  // [TH*TW][CO]
     const int x0 = blockIdx.x * TW, y0 = blockIdx.y * TH;
+    const int H = lv.H, Wd = lv.Wd;
+    const int sy0 = (y0 / lv.Hs) * lv.Hs, sy1 = min(sy0 + lv.Hs, H);   // the tile's slice
     constexpr int VPP = CI / 8;
     for (int idx = threadIdx.x; idx < IH * IW * VPP; idx += blockDim.x) {
         const int pix = idx / VPP, v = idx - pix * VPP;
         const int iy = pix / IW, ix = pix - iy * IW;
         const int gy = y0 + iy - HP, gx = x0 + ix - HP;
         uint4 val = make_uint4(0u, 0u, 0u, 0u);
-        if (gy >= 0 && gy < H && gx >= 0 && gx < Wd)
+        if (gy >= sy0 && gy < sy1 && gx >= 0 && gx < Wd)
             val = *reinterpret_cast<const uint4*>(in + ((size_t)gy * Wd + gx) * istr + ioff + v * 8);
         *reinterpret_cast<uint4*>(xs + pix * CI + v * 8) = val;
     }
@@ -597,82 +641,102 @@ conv_wgrad(const bf16* __restrict__ in, int istr, int ioff, const bf16* __restri
 }
 
 // ---------------------------------------------------------------- element-wise
-// NHWC16 input B x from four float32 field planes (channels 4..15 zero).
+// NHWC16 input B x from nf float32 field planes (channels nf..15 zero).
 __global__ void pack_input(const float* __restrict__ x, int npix, Bal bal, bf16* __restrict__ out,
                            const int* skip) {
     if (skip != nullptr && *skip) return;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
         __align__(16) bf16 v[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(c < 4 ? bal.b[c] * x[(size_t)c * npix + p] : 0.f);
+        for (int c = 0; c < 16; ++c)
+            v[c] = __float2bfloat16(c < MAXF && c < bal.nf ? bal.b[c] * x[(size_t)c * npix + p] : 0.f);
         reinterpret_cast<uint4*>(out + (size_t)p * 16)[0] = reinterpret_cast<uint4*>(v)[0];
         reinterpret_cast<uint4*>(out + (size_t)p * 16)[1] = reinterpret_cast<uint4*>(v)[1];
     }
 }
 
-// 2x2 average pooling: out (H/2 x W/2) from in (H x W), C channels.
+// Coarse level of a fine level f: half the columns and slice rows, half the
+// slices when d3 = 1.
+__host__ __device__ __forceinline__ Lv coarser(const Lv& f) {
+    return Lv{f.H / (f.d3 ? 4 : 2), f.Wd / 2, f.Hs / 2, f.d3};
+}
+
+// average pooling (2x2, or 2x2x2 when f.d3): out (coarse level) from in (fine level f), C channels.
 __global__ void avgpool2(const bf16* __restrict__ in, int istr, int ioff, bf16* __restrict__ out, int ostr,
-                         int ooff, int C, int H, int Wd, const int* skip) {
+                         int ooff, int C, Lv f, const int* skip) {
     if (skip != nullptr && *skip) return;
-    const int h = H / 2, w = Wd / 2;
-    const int total = h * w * C;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int c = i % C, q = i / C;
-        const int y = q / w, x = q - y * w;
+    const Lv c_ = coarser(f);
+    const int w = c_.Wd, Wd = f.Wd;
+    const size_t total = (size_t)c_.H * w * C;
+    const float wgt = f.d3 ? 0.125f : 0.25f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const size_t q = i / C;
+        const int y = (int)(q / w), x = (int)(q - (size_t)y * w);
         float s = 0.f;
+        for (int dz = 0; dz <= f.d3; ++dz)
 #pragma unroll
-        for (int d = 0; d < 4; ++d)
-            s += __bfloat162float(in[((size_t)(2 * y + d / 2) * Wd + 2 * x + d % 2) * istr + ioff + c]);
-        out[(size_t)q * ostr + ooff + c] = __float2bfloat16(0.25f * s);
+            for (int d = 0; d < 4; ++d)
+                s += __bfloat162float(in[((size_t)fine_row(y, dz, d / 2, f) * Wd + 2 * x + d % 2) * istr + ioff + c]);
+        out[q * ostr + ooff + c] = __float2bfloat16(wgt * s);
     }
 }
 
-// nearest upsampling x2: out (H x W) from in (H/2 x W/2), C channels.
+// nearest upsampling x2 (x2x2 when f.d3): out (fine level f) from in (its coarse level), C channels.
 __global__ void upsample2(const bf16* __restrict__ in, int istr, int ioff, bf16* __restrict__ out, int ostr,
-                          int ooff, int C, int H, int Wd, const int* skip) {
+                          int ooff, int C, Lv f, const int* skip) {
     if (skip != nullptr && *skip) return;
-    const int total = H * Wd * C;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int c = i % C, p = i / C;
-        const int y = p / Wd, x = p - y * Wd;
-        out[(size_t)p * ostr + ooff + c] = in[((size_t)(y / 2) * (Wd / 2) + x / 2) * istr + ioff + c];
+    const int Wd = f.Wd;
+    const size_t total = (size_t)f.H * Wd * C;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const size_t p = i / C;
+        const int y = (int)(p / Wd), x = (int)(p - (size_t)y * Wd);
+        out[p * ostr + ooff + c] = in[((size_t)coarse_row(y, f) * (Wd / 2) + x / 2) * istr + ioff + c];
     }
 }
 
-// backward of nearest upsampling: out (H/2 x W/2) = 2x2 sums of in (H x W).
+// backward of nearest upsampling: out (coarse level of f) = sums over the children of in (fine level f).
 __global__ void upsample2_bwd(const bf16* __restrict__ in, int istr, int ioff, bf16* __restrict__ out, int C,
-                              int H, int Wd) {
-    const int h = H / 2, w = Wd / 2;
-    const int total = h * w * C;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int c = i % C, q = i / C;
-        const int y = q / w, x = q - y * w;
+                              Lv f) {
+    const Lv c_ = coarser(f);
+    const int w = c_.Wd, Wd = f.Wd;
+    const size_t total = (size_t)c_.H * w * C;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const size_t q = i / C;
+        const int y = (int)(q / w), x = (int)(q - (size_t)y * w);
         float s = 0.f;
+        for (int dz = 0; dz <= f.d3; ++dz)
 #pragma unroll
-        for (int d = 0; d < 4; ++d)
-            s += __bfloat162float(in[((size_t)(2 * y + d / 2) * Wd + 2 * x + d % 2) * istr + ioff + c]);
-        out[(size_t)q * C + c] = __float2bfloat16(s);
+            for (int d = 0; d < 4; ++d)
+                s += __bfloat162float(in[((size_t)fine_row(y, dz, d / 2, f) * Wd + 2 * x + d % 2) * istr + ioff + c]);
+        out[q * C + c] = __float2bfloat16(s);
     }
 }
 
 // gradient of a skip that feeds both a concat slot and an average pool:
-// out (H x W, C) = dcat[.., off:off+C] + 1/4 up(dsmall)
+// out (fine level f, C) = dcat[.., off:off+C] + w up(dsmall), w = 1/4 (1/8 when f.d3)
 __global__ void skip_grad(const bf16* __restrict__ dcat, int cstr, int coff, const bf16* __restrict__ dsmall,
-                          bf16* __restrict__ out, int C, int H, int Wd) {
-    const int total = H * Wd * C;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-        const int c = i % C, p = i / C;
-        const int y = p / Wd, x = p - y * Wd;
-        const float v = __bfloat162float(dcat[(size_t)p * cstr + coff + c]) +
-                        0.25f * __bfloat162float(dsmall[((size_t)(y / 2) * (Wd / 2) + x / 2) * C + c]);
-        out[(size_t)p * C + c] = __float2bfloat16(v);
+                          bf16* __restrict__ out, int C, Lv f) {
+    const int Wd = f.Wd;
+    const size_t total = (size_t)f.H * Wd * C;
+    const float wgt = f.d3 ? 0.125f : 0.25f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const size_t p = i / C;
+        const int y = (int)(p / Wd), x = (int)(p - (size_t)y * Wd);
+        const float v = __bfloat162float(dcat[p * cstr + coff + c]) +
+                        wgt * __bfloat162float(dsmall[((size_t)coarse_row(y, f) * (Wd / 2) + x / 2) * C + c]);
+        out[p * C + c] = __float2bfloat16(v);
     }
 }
 
-// out += ||B x||^2 over the 4 field planes
+// out += ||B x||^2 over the nf field planes
 __global__ void sumsq(const float* __restrict__ x, int npix, Bal bal, double* out) {
     double s = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * npix; i += gridDim.x * blockDim.x) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)bal.nf * npix;
+         i += (size_t)gridDim.x * blockDim.x) {
         const double v = (double)(bal.b[i / npix] * x[i]);
         s += v * v;
     }
@@ -681,7 +745,7 @@ __global__ void sumsq(const float* __restrict__ x, int npix, Bal bal, double* ou
 }
 
 // With y the raw output (balanced units): dy = (y - B t) / ||B x||^2
-// (channels 0..3), loss += 1/2 (y - B t)^2 / ||B x||^2.
+// (channels 0..nf-1), loss += 1/2 (y - B t)^2 / ||B x||^2.
 __global__ void loss_grad(const float* __restrict__ y, const float* __restrict__ t, int npix, Bal bal,
                           const double* xn2, bf16* __restrict__ dy, double* loss) {
     const float inv = (float)(1.0 / fmax(*xn2, 1e-300));
@@ -691,7 +755,7 @@ __global__ void loss_grad(const float* __restrict__ y, const float* __restrict__
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             float d = 0.f;
-            if (c < 4) {
+            if (c < MAXF && c < bal.nf) {
                 d = y[(size_t)p * 16 + c] - bal.b[c] * t[(size_t)c * npix + p];
                 s += 0.5 * (double)d * (double)d;
             }
@@ -743,7 +807,7 @@ int grid_for(size_t n) {
 enum { ENGINE_TCGEN05 = 0, ENGINE_MMA_SYNC = 1 };
 
 template <int CI, int CO, int KS, int INMODE, int OUTMODE, int CU = 0>
-cudaError_t conv_ex_tc(const ConvIn& in, const Bal& bal, const bf16* W, const ConvOut& out, int H, int Wd,
+cudaError_t conv_ex_tc(const ConvIn& in, const Bal& bal, const bf16* W, const ConvOut& out, const Lv& lv,
                        cudaStream_t s, const int* skip, int* err) {
     using S = TcShape<CI, CO, KS>;
     auto kern = conv_tc<CI, CO, KS, INMODE, OUTMODE, CU>;
@@ -776,15 +840,15 @@ cudaError_t conv_ex_tc(const ConvIn& in, const Bal& bal, const bf16* W, const Co
         per_sm = std::min(per_sm, 512 / S::TCOLS);
         max_ctas = sms * std::max(per_sm, 1);
     }
-    const int ntiles = ((Wd + CONV_TW - 1) / CONV_TW) * ((H + CONV_TH - 1) / CONV_TH);
+    const int ntiles = ((lv.Wd + CONV_TW - 1) / CONV_TW) * ((lv.H + CONV_TH - 1) / CONV_TH);
     const int grid = ntiles < max_ctas ? ntiles : max_ctas;
-    return net_launch(kern, grid, CONV_THREADS, S::SMEM, s, in, bal, W, out, H, Wd, skip, err);
+    return net_launch(kern, grid, CONV_THREADS, S::SMEM, s, in, bal, W, out, lv, skip, err);
 }
 
 template <int CI, int CO, int KS, int INMODE, int OUTMODE, int CU = 0>
-cudaError_t conv_ex(const ConvIn& in, const Bal& bal, const bf16* W, const ConvOut& out, int H, int Wd,
+cudaError_t conv_ex(const ConvIn& in, const Bal& bal, const bf16* W, const ConvOut& out, const Lv& lv,
                     cudaStream_t s, const int* skip, int engine = ENGINE_TCGEN05, int* err = nullptr) {
-    if (engine == ENGINE_TCGEN05) return conv_ex_tc<CI, CO, KS, INMODE, OUTMODE, CU>(in, bal, W, out, H, Wd, s, skip, err);
+    if (engine == ENGINE_TCGEN05) return conv_ex_tc<CI, CO, KS, INMODE, OUTMODE, CU>(in, bal, W, out, lv, s, skip, err);
     using S = ConvShape<CI, CO, KS>;
     auto kern = conv_mma<CI, CO, KS, INMODE, OUTMODE, CU>;
     static int max_ctas = 0;   // resident CTAs on the device (persistent grid)
@@ -798,23 +862,23 @@ cudaError_t conv_ex(const ConvIn& in, const Bal& bal, const bf16* W, const ConvO
             return e;
         max_ctas = sms * (per_sm > 0 ? per_sm : 1);
     }
-    const int ntiles = ((Wd + CONV_TW - 1) / CONV_TW) * ((H + CONV_TH - 1) / CONV_TH);
+    const int ntiles = ((lv.Wd + CONV_TW - 1) / CONV_TW) * ((lv.H + CONV_TH - 1) / CONV_TH);
     const int grid = ntiles < max_ctas ? ntiles : max_ctas;
-    return net_launch(kern, grid, CONV_THREADS, S::SMEM, s, in, bal, W, out, H, Wd, skip);
+    return net_launch(kern, grid, CONV_THREADS, S::SMEM, s, in, bal, W, out, lv, skip);
 }
 
 // plain NHWC -> NHWC convolution (training path)
 template <int CI, int CO, int KS, bool OUTF32>
-cudaError_t conv(const bf16* in, int istr, int ioff, const bf16* W, void* out, int ostr, int ooff, int H, int Wd,
+cudaError_t conv(const bf16* in, int istr, int ioff, const bf16* W, void* out, int ostr, int ooff, const Lv& lv,
                  cudaStream_t s, const int* skip, int engine, int* err) {
     ConvIn ci{in, istr, ioff, nullptr, 0, 0, nullptr};
     ConvOut co{out, ostr, ooff, 0};
     Bal bal{};
-    return conv_ex<CI, CO, KS, IN_NHWC, OUTF32 ? OUT_F32 : OUT_BF16>(ci, bal, W, co, H, Wd, s, skip, engine, err);
+    return conv_ex<CI, CO, KS, IN_NHWC, OUTF32 ? OUT_F32 : OUT_BF16>(ci, bal, W, co, lv, s, skip, engine, err);
 }
 
 template <int CI, int CO, int KS>
-cudaError_t wgrad(const bf16* in, int istr, int ioff, const bf16* dout, int H, int Wd, float* dW, cudaStream_t s) {
+cudaError_t wgrad(const bf16* in, int istr, int ioff, const bf16* dout, const Lv& lv, float* dW, cudaStream_t s) {
     constexpr int HP = KS / 2;
     const size_t sm = sizeof(bf16) * ((16 + 2 * HP) * (16 + 2 * HP) * CI + 256 * CO);
     static bool configured = false;
@@ -824,8 +888,8 @@ cudaError_t wgrad(const bf16* in, int istr, int ioff, const bf16* dout, int H, i
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid((Wd + 15) / 16, (H + 15) / 16);
-    conv_wgrad<CI, CO, KS><<<grid, 256, sm, s>>>(in, istr, ioff, dout, H, Wd, dW);
+    dim3 grid((lv.Wd + 15) / 16, (lv.H + 15) / 16);
+    conv_wgrad<CI, CO, KS><<<grid, 256, sm, s>>>(in, istr, ioff, dout, lv, dW);
     return cudaGetLastError();
 }
 
@@ -839,7 +903,9 @@ uint64_t splitmix(uint64_t& x) {
 }  // namespace
 
 struct UNet {
-    int nx, nz;
+    int nx, ny, nz, dim;
+    Lv lv[3];                               // levels 0 (the grid), 1, 2
+    size_t npix;                            // points of the grid
     size_t nw;
     size_t woff[NL + 1];
     float *w32, *g32, *m32, *v32;           // master weights, gradient, Adam moments
@@ -863,25 +929,41 @@ static void free_net(UNet* n) {
         if (q) cudaFree(q);
 }
 
-UNet* unet_create(int nx, int nz, const double balance[4], unsigned long long seed, cudaError_t* err) {
+bool unet_grid_ok(int dim, int nx, int ny, int nz) {
+    if (nx <= 0 || ny <= 0 || nz <= 0 || nx % 32) return false;
+    if (dim == 2) return ny == 1 && nz % 32 == 0;
+    // slices of ny rows hold whole 16-row tiles at every level; z pools twice
+    return dim == 3 && ny % 64 == 0 && nz % 4 == 0 && (long long)nx * ny * nz < (1ll << 31);
+}
+
+UNet* unet_create(int dim, int nx, int ny, int nz, const double* balance, unsigned long long seed,
+                  cudaError_t* err) {
     *err = cudaSuccess;
-    if (nx % 32 || nz % 32 || nx <= 0 || nz <= 0) { *err = cudaErrorInvalidValue; return nullptr; }
-    for (int f = 0; f < 4; ++f)
+    if (!unet_grid_ok(dim, nx, ny, nz)) { *err = cudaErrorInvalidValue; return nullptr; }
+    const int nf = dim == 2 ? 4 : 5;
+    for (int f = 0; f < nf; ++f)
         if (!(balance[f] > 0.0) || !isfinite(balance[f])) { *err = cudaErrorInvalidValue; return nullptr; }
     UNet* n = new (std::nothrow) UNet;
     if (!n) { *err = cudaErrorMemoryAllocation; return nullptr; }
     memset(n, 0, sizeof(*n));
     n->nx = nx;
+    n->ny = ny;
     n->nz = nz;
-    for (int f = 0; f < 4; ++f) {
-        n->bal.b[f] = (float)balance[f];
-        n->bal.inv[f] = (float)(1.0 / balance[f]);
+    n->dim = dim;
+    n->lv[0] = dim == 2 ? Lv{nz, nx, nz, 0} : Lv{nz * ny, nx, ny, 1};
+    n->lv[1] = coarser(n->lv[0]);
+    n->lv[2] = coarser(n->lv[1]);
+    n->npix = (size_t)nx * ny * nz;
+    n->bal.nf = nf;
+    for (int f = 0; f < MAXF; ++f) {
+        n->bal.b[f] = f < nf ? (float)balance[f] : 0.f;
+        n->bal.inv[f] = f < nf ? (float)(1.0 / balance[f]) : 0.f;
     }
     size_t o = 0;
     for (int l = 0; l < NL; ++l) { n->woff[l] = o; o += (size_t)KSZ[l] * KSZ[l] * COUT[l] * CIN[l]; }
     n->woff[NL] = o;
     n->nw = o;
-    const size_t P0 = (size_t)nx * nz, P1 = P0 / 4, P2 = P0 / 16;
+    const size_t P0 = n->npix, P1 = (size_t)n->lv[1].H * n->lv[1].Wd, P2 = (size_t)n->lv[2].H * n->lv[2].Wd;
     auto A = [&](void** p, size_t bytes) {
         if (*err == cudaSuccess) *err = cudaMalloc(p, bytes);
     };
@@ -906,7 +988,7 @@ UNet* unet_create(int nx, int nz, const double balance[4], unsigned long long se
     uint64_t st = seed;
     for (int l = 0; l < NL; ++l) {
         if (l == L0d) continue;
-        const int ci_real = l == L0a ? 4 : CIN[l];
+        const int ci_real = l == L0a ? nf : CIN[l];
         const float sd = sqrtf(1.0f / (KSZ[l] * KSZ[l] * ci_real));
         for (int tp = 0; tp < KSZ[l] * KSZ[l]; ++tp)
             for (int co = 0; co < COUT[l]; ++co)
@@ -954,22 +1036,23 @@ cudaError_t unet_set_weights(UNet* n, const float* host, cudaStream_t s) {
     } while (0)
 
 static cudaError_t forward(UNet* n, const float* x, cudaStream_t s, const int* skip) {
-    const int H0 = n->nz, W0 = n->nx, H1 = H0 / 2, W1 = W0 / 2, H2 = H0 / 4, W2 = W0 / 4;
+    const Lv L0 = n->lv[0], L1 = n->lv[1], L2 = n->lv[2];
+    const size_t P0 = n->npix, P1 = (size_t)L1.H * L1.Wd, P2 = (size_t)L2.H * L2.Wd;
     const bf16* w = n->wb;
-    pack_input<<<grid_for((size_t)H0 * W0), 256, 0, s>>>(x, H0 * W0, n->bal, n->x0, skip);
-    UCK((conv<16, 16, 3, false>(n->x0, 16, 0, w + n->woff[L0a], n->h0a, 16, 0, H0, W0, s, skip, n->engine, n->derr)));
-    UCK((conv<16, 16, 3, false>(n->h0a, 16, 0, w + n->woff[L0b], n->cat0, 48, 32, H0, W0, s, skip, n->engine, n->derr)));
-    avgpool2<<<grid_for((size_t)H1 * W1 * 16), 256, 0, s>>>(n->cat0, 48, 32, n->p1, 16, 0, 16, H0, W0, skip);
-    UCK((conv<16, 32, 3, false>(n->p1, 16, 0, w + n->woff[L1a], n->h1a, 32, 0, H1, W1, s, skip, n->engine, n->derr)));
-    UCK((conv<32, 32, 3, false>(n->h1a, 32, 0, w + n->woff[L1b], n->cat1, 96, 64, H1, W1, s, skip, n->engine, n->derr)));
-    avgpool2<<<grid_for((size_t)H2 * W2 * 32), 256, 0, s>>>(n->cat1, 96, 64, n->p2, 32, 0, 32, H1, W1, skip);
-    UCK((conv<32, 64, 3, false>(n->p2, 32, 0, w + n->woff[L2a], n->h2a, 64, 0, H2, W2, s, skip, n->engine, n->derr)));
-    UCK((conv<64, 64, 3, false>(n->h2a, 64, 0, w + n->woff[L2b], n->h2b, 64, 0, H2, W2, s, skip, n->engine, n->derr)));
-    upsample2<<<grid_for((size_t)H1 * W1 * 64), 256, 0, s>>>(n->h2b, 64, 0, n->cat1, 96, 0, 64, H1, W1, skip);
-    UCK((conv<96, 32, 3, false>(n->cat1, 96, 0, w + n->woff[L1c], n->h1c, 32, 0, H1, W1, s, skip, n->engine, n->derr)));
-    upsample2<<<grid_for((size_t)H0 * W0 * 32), 256, 0, s>>>(n->h1c, 32, 0, n->cat0, 48, 0, 32, H0, W0, skip);
-    UCK((conv<48, 16, 3, false>(n->cat0, 48, 0, w + n->woff[L0c], n->h0c, 16, 0, H0, W0, s, skip, n->engine, n->derr)));
-    UCK((conv<16, 16, 1, true>(n->h0c, 16, 0, w + n->woff[L0d], n->yf, 16, 0, H0, W0, s, skip, n->engine, n->derr)));
+    pack_input<<<grid_for(P0), 256, 0, s>>>(x, (int)P0, n->bal, n->x0, skip);
+    UCK((conv<16, 16, 3, false>(n->x0, 16, 0, w + n->woff[L0a], n->h0a, 16, 0, L0, s, skip, n->engine, n->derr)));
+    UCK((conv<16, 16, 3, false>(n->h0a, 16, 0, w + n->woff[L0b], n->cat0, 48, 32, L0, s, skip, n->engine, n->derr)));
+    avgpool2<<<grid_for(P1 * 16), 256, 0, s>>>(n->cat0, 48, 32, n->p1, 16, 0, 16, L0, skip);
+    UCK((conv<16, 32, 3, false>(n->p1, 16, 0, w + n->woff[L1a], n->h1a, 32, 0, L1, s, skip, n->engine, n->derr)));
+    UCK((conv<32, 32, 3, false>(n->h1a, 32, 0, w + n->woff[L1b], n->cat1, 96, 64, L1, s, skip, n->engine, n->derr)));
+    avgpool2<<<grid_for(P2 * 32), 256, 0, s>>>(n->cat1, 96, 64, n->p2, 32, 0, 32, L1, skip);
+    UCK((conv<32, 64, 3, false>(n->p2, 32, 0, w + n->woff[L2a], n->h2a, 64, 0, L2, s, skip, n->engine, n->derr)));
+    UCK((conv<64, 64, 3, false>(n->h2a, 64, 0, w + n->woff[L2b], n->h2b, 64, 0, L2, s, skip, n->engine, n->derr)));
+    upsample2<<<grid_for(P1 * 64), 256, 0, s>>>(n->h2b, 64, 0, n->cat1, 96, 0, 64, L1, skip);
+    UCK((conv<96, 32, 3, false>(n->cat1, 96, 0, w + n->woff[L1c], n->h1c, 32, 0, L1, s, skip, n->engine, n->derr)));
+    upsample2<<<grid_for(P0 * 32), 256, 0, s>>>(n->h1c, 32, 0, n->cat0, 48, 0, 32, L0, skip);
+    UCK((conv<48, 16, 3, false>(n->cat0, 48, 0, w + n->woff[L0c], n->h0c, 16, 0, L0, s, skip, n->engine, n->derr)));
+    UCK((conv<16, 16, 1, true>(n->h0c, 16, 0, w + n->woff[L0d], n->yf, 16, 0, L0, s, skip, n->engine, n->derr)));
     return cudaGetLastError();
 }
 
@@ -978,32 +1061,28 @@ static cudaError_t forward(UNet* n, const float* x, cudaStream_t s, const int* s
 // arithmetic as forward() followed by unpack_output).
 static cudaError_t forward_fused(UNet* n, const float* x, float* y, int accumulate, cudaStream_t s,
                                  const int* skip) {
-    const int H0 = n->nz, W0 = n->nx, H1 = H0 / 2, W1 = W0 / 2, H2 = H0 / 4, W2 = W0 / 4;
+    const Lv L0 = n->lv[0], L1 = n->lv[1], L2 = n->lv[2];
+    const size_t P0 = n->npix, P1 = (size_t)L1.H * L1.Wd, P2 = (size_t)L2.H * L2.Wd;
     const bf16* w = n->wb;
     const ConvIn none{nullptr, 0, 0, nullptr, 0, 0, nullptr};
     auto nhwc = [&](const bf16* a, int str, int off) { ConvIn c = none; c.a = a; c.astr = str; c.aoff = off; return c; };
     auto to = [&](void* o, int str, int off) { return ConvOut{o, str, off, 0}; };
     ConvIn pk = none;
     pk.x = x;
-    UCK((conv_ex<16, 16, 3, IN_PACK, OUT_BF16>(pk, n->bal, w + n->woff[L0a], to(n->h0a, 16, 0), H0, W0, s, skip, n->engine, n->derr)));
-    UCK((conv_ex<16, 16, 3, IN_NHWC, OUT_BF16>(nhwc(n->h0a, 16, 0), n->bal, w + n->woff[L0b], to(n->cat0, 48, 32), H0,
-                                               W0, s, skip, n->engine, n->derr)));
-    UCK((conv_ex<16, 32, 3, IN_POOL, OUT_BF16>(nhwc(n->cat0, 48, 32), n->bal, w + n->woff[L1a], to(n->h1a, 32, 0), H1,
-                                               W1, s, skip, n->engine, n->derr)));
-    UCK((conv_ex<32, 32, 3, IN_NHWC, OUT_BF16>(nhwc(n->h1a, 32, 0), n->bal, w + n->woff[L1b], to(n->cat1, 96, 64), H1,
-                                               W1, s, skip, n->engine, n->derr)));
-    UCK((conv_ex<32, 64, 3, IN_POOL, OUT_BF16>(nhwc(n->cat1, 96, 64), n->bal, w + n->woff[L2a], to(n->h2a, 64, 0), H2,
-                                               W2, s, skip, n->engine, n->derr)));
-    UCK((conv_ex<64, 64, 3, IN_NHWC, OUT_BF16>(nhwc(n->h2a, 64, 0), n->bal, w + n->woff[L2b], to(n->h2b, 64, 0), H2,
-                                               W2, s, skip, n->engine, n->derr)));
+    UCK((conv_ex<16, 16, 3, IN_PACK, OUT_BF16>(pk, n->bal, w + n->woff[L0a], to(n->h0a, 16, 0), L0, s, skip, n->engine, n->derr)));
+    UCK((conv_ex<16, 16, 3, IN_NHWC, OUT_BF16>(nhwc(n->h0a, 16, 0), n->bal, w + n->woff[L0b], to(n->cat0, 48, 32), L0, s, skip, n->engine, n->derr)));
+    UCK((conv_ex<16, 32, 3, IN_POOL, OUT_BF16>(nhwc(n->cat0, 48, 32), n->bal, w + n->woff[L1a], to(n->h1a, 32, 0), L1, s, skip, n->engine, n->derr)));
+    UCK((conv_ex<32, 32, 3, IN_NHWC, OUT_BF16>(nhwc(n->h1a, 32, 0), n->bal, w + n->woff[L1b], to(n->cat1, 96, 64), L1, s, skip, n->engine, n->derr)));
+    UCK((conv_ex<32, 64, 3, IN_POOL, OUT_BF16>(nhwc(n->cat1, 96, 64), n->bal, w + n->woff[L2a], to(n->h2a, 64, 0), L2, s, skip, n->engine, n->derr)));
+    UCK((conv_ex<64, 64, 3, IN_NHWC, OUT_BF16>(nhwc(n->h2a, 64, 0), n->bal, w + n->woff[L2b], to(n->h2b, 64, 0), L2, s, skip, n->engine, n->derr)));
     ConvIn uc1{n->h2b, 64, 0, n->cat1, 96, 64, nullptr};
-    UCK((conv_ex<96, 32, 3, IN_UPCAT, OUT_BF16, 64>(uc1, n->bal, w + n->woff[L1c], to(n->h1c, 32, 0), H1, W1, s,
+    UCK((conv_ex<96, 32, 3, IN_UPCAT, OUT_BF16, 64>(uc1, n->bal, w + n->woff[L1c], to(n->h1c, 32, 0), L1, s,
                                                     skip, n->engine, n->derr)));
     ConvIn uc0{n->h1c, 32, 0, n->cat0, 48, 32, nullptr};
-    UCK((conv_ex<48, 16, 3, IN_UPCAT, OUT_BF16, 32>(uc0, n->bal, w + n->woff[L0c], to(n->h0c, 16, 0), H0, W0, s,
+    UCK((conv_ex<48, 16, 3, IN_UPCAT, OUT_BF16, 32>(uc0, n->bal, w + n->woff[L0c], to(n->h0c, 16, 0), L0, s,
                                                     skip, n->engine, n->derr)));
     ConvOut pl{y, 0, 0, accumulate};
-    UCK((conv_ex<16, 16, 1, IN_NHWC, OUT_PLANES>(nhwc(n->h0c, 16, 0), n->bal, w + n->woff[L0d], pl, H0, W0, s, skip, n->engine, n->derr)));
+    UCK((conv_ex<16, 16, 1, IN_NHWC, OUT_PLANES>(nhwc(n->h0c, 16, 0), n->bal, w + n->woff[L0d], pl, L0, s, skip, n->engine, n->derr)));
     return cudaGetLastError();
 }
 
@@ -1016,32 +1095,33 @@ static cudaError_t transpose_w(UNet* n, int l, cudaStream_t s) {
 }
 
 static cudaError_t backward(UNet* n, cudaStream_t s) {
-    const int H0 = n->nz, W0 = n->nx, H1 = H0 / 2, W1 = W0 / 2, H2 = H0 / 4, W2 = W0 / 4;
+    const Lv L0 = n->lv[0], L1 = n->lv[1], L2 = n->lv[2];
+    const size_t P0 = n->npix, P1 = (size_t)L1.H * L1.Wd, P2 = (size_t)L2.H * L2.Wd;
     float* g = n->g32;
     const bf16* wt = n->wt;
     UCK(cudaMemsetAsync(g, 0, n->nw * 4, s));
     for (int l = 0; l < NL; ++l) UCK(transpose_w(n, l, s));
-    UCK((wgrad<16, 16, 1>(n->h0c, 16, 0, n->dy, H0, W0, g + n->woff[L0d], s)));
-    UCK((conv<16, 16, 1, false>(n->dy, 16, 0, wt + n->woff[L0d], n->dh0c, 16, 0, H0, W0, s, nullptr, n->engine, n->derr)));
-    UCK((wgrad<48, 16, 3>(n->cat0, 48, 0, n->dh0c, H0, W0, g + n->woff[L0c], s)));
-    UCK((conv<16, 48, 3, false>(n->dh0c, 16, 0, wt + n->woff[L0c], n->dcat0, 48, 0, H0, W0, s, nullptr, n->engine, n->derr)));
-    upsample2_bwd<<<grid_for((size_t)H1 * W1 * 32), 256, 0, s>>>(n->dcat0, 48, 0, n->dh1c, 32, H0, W0);
-    UCK((wgrad<96, 32, 3>(n->cat1, 96, 0, n->dh1c, H1, W1, g + n->woff[L1c], s)));
-    UCK((conv<32, 96, 3, false>(n->dh1c, 32, 0, wt + n->woff[L1c], n->dcat1, 96, 0, H1, W1, s, nullptr, n->engine, n->derr)));
-    upsample2_bwd<<<grid_for((size_t)H2 * W2 * 64), 256, 0, s>>>(n->dcat1, 96, 0, n->dh2b, 64, H1, W1);
-    UCK((wgrad<64, 64, 3>(n->h2a, 64, 0, n->dh2b, H2, W2, g + n->woff[L2b], s)));
-    UCK((conv<64, 64, 3, false>(n->dh2b, 64, 0, wt + n->woff[L2b], n->dh2a, 64, 0, H2, W2, s, nullptr, n->engine, n->derr)));
-    UCK((wgrad<32, 64, 3>(n->p2, 32, 0, n->dh2a, H2, W2, g + n->woff[L2a], s)));
-    UCK((conv<64, 32, 3, false>(n->dh2a, 64, 0, wt + n->woff[L2a], n->dp2, 32, 0, H2, W2, s, nullptr, n->engine, n->derr)));
-    skip_grad<<<grid_for((size_t)H1 * W1 * 32), 256, 0, s>>>(n->dcat1, 96, 64, n->dp2, n->ds1, 32, H1, W1);
-    UCK((wgrad<32, 32, 3>(n->h1a, 32, 0, n->ds1, H1, W1, g + n->woff[L1b], s)));
-    UCK((conv<32, 32, 3, false>(n->ds1, 32, 0, wt + n->woff[L1b], n->dh1a, 32, 0, H1, W1, s, nullptr, n->engine, n->derr)));
-    UCK((wgrad<16, 32, 3>(n->p1, 16, 0, n->dh1a, H1, W1, g + n->woff[L1a], s)));
-    UCK((conv<32, 16, 3, false>(n->dh1a, 32, 0, wt + n->woff[L1a], n->dp1, 16, 0, H1, W1, s, nullptr, n->engine, n->derr)));
-    skip_grad<<<grid_for((size_t)H0 * W0 * 16), 256, 0, s>>>(n->dcat0, 48, 32, n->dp1, n->ds0, 16, H0, W0);
-    UCK((wgrad<16, 16, 3>(n->h0a, 16, 0, n->ds0, H0, W0, g + n->woff[L0b], s)));
-    UCK((conv<16, 16, 3, false>(n->ds0, 16, 0, wt + n->woff[L0b], n->dh0a, 16, 0, H0, W0, s, nullptr, n->engine, n->derr)));
-    UCK((wgrad<16, 16, 3>(n->x0, 16, 0, n->dh0a, H0, W0, g + n->woff[L0a], s)));
+    UCK((wgrad<16, 16, 1>(n->h0c, 16, 0, n->dy, L0, g + n->woff[L0d], s)));
+    UCK((conv<16, 16, 1, false>(n->dy, 16, 0, wt + n->woff[L0d], n->dh0c, 16, 0, L0, s, nullptr, n->engine, n->derr)));
+    UCK((wgrad<48, 16, 3>(n->cat0, 48, 0, n->dh0c, L0, g + n->woff[L0c], s)));
+    UCK((conv<16, 48, 3, false>(n->dh0c, 16, 0, wt + n->woff[L0c], n->dcat0, 48, 0, L0, s, nullptr, n->engine, n->derr)));
+    upsample2_bwd<<<grid_for(P1 * 32), 256, 0, s>>>(n->dcat0, 48, 0, n->dh1c, 32, L0);
+    UCK((wgrad<96, 32, 3>(n->cat1, 96, 0, n->dh1c, L1, g + n->woff[L1c], s)));
+    UCK((conv<32, 96, 3, false>(n->dh1c, 32, 0, wt + n->woff[L1c], n->dcat1, 96, 0, L1, s, nullptr, n->engine, n->derr)));
+    upsample2_bwd<<<grid_for(P2 * 64), 256, 0, s>>>(n->dcat1, 96, 0, n->dh2b, 64, L1);
+    UCK((wgrad<64, 64, 3>(n->h2a, 64, 0, n->dh2b, L2, g + n->woff[L2b], s)));
+    UCK((conv<64, 64, 3, false>(n->dh2b, 64, 0, wt + n->woff[L2b], n->dh2a, 64, 0, L2, s, nullptr, n->engine, n->derr)));
+    UCK((wgrad<32, 64, 3>(n->p2, 32, 0, n->dh2a, L2, g + n->woff[L2a], s)));
+    UCK((conv<64, 32, 3, false>(n->dh2a, 64, 0, wt + n->woff[L2a], n->dp2, 32, 0, L2, s, nullptr, n->engine, n->derr)));
+    skip_grad<<<grid_for(P1 * 32), 256, 0, s>>>(n->dcat1, 96, 64, n->dp2, n->ds1, 32, L1);
+    UCK((wgrad<32, 32, 3>(n->h1a, 32, 0, n->ds1, L1, g + n->woff[L1b], s)));
+    UCK((conv<32, 32, 3, false>(n->ds1, 32, 0, wt + n->woff[L1b], n->dh1a, 32, 0, L1, s, nullptr, n->engine, n->derr)));
+    UCK((wgrad<16, 32, 3>(n->p1, 16, 0, n->dh1a, L1, g + n->woff[L1a], s)));
+    UCK((conv<32, 16, 3, false>(n->dh1a, 32, 0, wt + n->woff[L1a], n->dp1, 16, 0, L1, s, nullptr, n->engine, n->derr)));
+    skip_grad<<<grid_for(P0 * 16), 256, 0, s>>>(n->dcat0, 48, 32, n->dp1, n->ds0, 16, L0);
+    UCK((wgrad<16, 16, 3>(n->h0a, 16, 0, n->ds0, L0, g + n->woff[L0b], s)));
+    UCK((conv<16, 16, 3, false>(n->ds0, 16, 0, wt + n->woff[L0b], n->dh0a, 16, 0, L0, s, nullptr, n->engine, n->derr)));
+    UCK((wgrad<16, 16, 3>(n->x0, 16, 0, n->dh0a, L0, g + n->woff[L0a], s)));
     return cudaGetLastError();
 }
 
@@ -1067,9 +1147,9 @@ cudaError_t unet_apply(UNet* n, const float* x, float* y, int accumulate, const 
 int unet_launches_per_apply() { return 9; }
 
 static cudaError_t loss_and_dy(UNet* n, const float* x, const float* t, cudaStream_t s) {
-    const int npix = n->nx * n->nz;
+    const int npix = (int)n->npix;
     UCK(cudaMemsetAsync(n->scal, 0, 2 * sizeof(double), s));
-    sumsq<<<grid_for((size_t)4 * npix), 256, 0, s>>>(x, npix, n->bal, n->scal);
+    sumsq<<<grid_for((size_t)n->bal.nf * npix), 256, 0, s>>>(x, npix, n->bal, n->scal);
     loss_grad<<<grid_for(npix), 256, 0, s>>>(n->yf, t, npix, n->bal, n->scal, n->dy, n->scal + 1);
     return cudaGetLastError();
 }
@@ -1089,7 +1169,7 @@ cudaError_t unet_loss_grad(UNet* n, const float* x, const float* t, double* loss
 
 cudaError_t unet_train(UNet* n, const float* X, const float* T, int npairs, int epochs, float lr,
                        double* loss_hist, cudaStream_t s) {
-    const size_t plane = (size_t)4 * n->nx * n->nz;
+    const size_t plane = (size_t)n->bal.nf * n->npix;
     for (int ep = 0; ep < epochs; ++ep) {
         double tot = 0.0;
         for (int q = 0; q < npairs; ++q) {

@@ -1,14 +1,18 @@
 // Learned right preconditioner: a linear 3-level convolutional U-Net on the
-// 2-D grid (internal interface of libjfnk).
+// 2-D or 3-D grid (internal interface of libjfnk).
 //
 // Network (channels 16 / 32 / 64, 3x3 convolutions, zero padding, no biases,
 // no activations, so the map is linear and fixed once trained):
-//   x (4 fields, padded to 16 channels)
+//   x (nf fields, padded to 16 channels)
 //   L0a 16->16, L0b 16->16 = s0 | avgpool 2x2
 //   L1a 16->32, L1b 32->32 = s1 | avgpool 2x2
 //   L2a 32->64, L2b 64->64       | nearest upsample x2, concat s1 (96)
 //   L1c 96->32                   | nearest upsample x2, concat s0 (48)
-//   L0c 48->16, L0d 1x1 16->16 (first 4 channels are the output fields)
+//   L0c 48->16, L0d 1x1 16->16 (first nf channels are the output fields)
+// 2-D: nf = 4 (u, w, theta, p) on nz x nx.  3-D: nf = 5 (u, v, w, theta, p) on
+// nz x ny x nx; every 3x3 convolution acts on each horizontal (y, x) plane,
+// pooling averages 2x2x2 blocks and upsampling repeats each point 2x2x2, so
+// the vertical coupling comes from the coarser levels.
 // Activations are bfloat16 in NHWC layout; convolutions are implicit GEMMs on
 // the tensor cores (mma m16n8k16, bfloat16 inputs, float32 accumulation);
 // weight gradients accumulate in float32; Adam keeps float32 master weights.
@@ -21,10 +25,15 @@ namespace jfnk {
 
 struct UNet;
 
-// Grid nx x nz, both multiples of 32.  Weights: seeded random, last layer zero.
-// balance[4] > 0: per-field factors B; the convolutions see B x and the map is
-// N(x) = B^-1 net(B x), so that the loss weighs the fields as the Jacobian does.
-UNet* unet_create(int nx, int nz, const double balance[4], unsigned long long seed, cudaError_t* err);
+// Supported grids: 2-D (ny = 1) with nx, nz multiples of 32; 3-D with nx a
+// multiple of 32, ny of 64 and nz of 4.
+bool unet_grid_ok(int dim, int nx, int ny, int nz);
+
+// Weights: seeded random, last layer zero.  balance[nf] > 0: per-field factors
+// B; the convolutions see B x and the map is N(x) = B^-1 net(B x), so that the
+// loss weighs the fields as the Jacobian does.
+UNet* unet_create(int dim, int nx, int ny, int nz, const double* balance, unsigned long long seed,
+                  cudaError_t* err);
 void unet_destroy(UNet* net);
 size_t unet_num_weights(const UNet* net);
 cudaError_t unet_get_weights(UNet* net, float* host, cudaStream_t s);
@@ -35,8 +44,9 @@ cudaError_t unet_set_weights(UNet* net, const float* host, cudaStream_t s);
 // whose tap (ky, kx) reads the input pixel at offset (ky - k/2, kx - k/2)
 // (rows = z, columns = x).
 
-// y = N(x) (accumulate = 0) or y += N(x) (accumulate = 1) for 4 float32 field
-// planes of nz x nx points (x fastest); y must not overlap x.  When skip is
+// y = N(x) (accumulate = 0) or y += N(x) (accumulate = 1) for nf float32 field
+// planes of nz x nx (2-D) or nz x ny x nx (3-D) points, x fastest; y must not
+// overlap x.  When skip is
 // non-NULL and *skip != 0 at kernel run time, every kernel returns at entry.
 cudaError_t unet_apply(UNet* net, const float* x, float* y, int accumulate, const int* skip, cudaStream_t s);
 int unet_launches_per_apply();
@@ -55,7 +65,7 @@ cudaError_t unet_check(UNet* net, cudaStream_t s);
 cudaError_t unet_loss_grad(UNet* net, const float* x, const float* t, double* loss, float* grads_host,
                            cudaStream_t s);
 
-// Adam on the pairs (X[i], T[i]) (each 4 planes of nx*nz floats, device),
+// Adam on the pairs (X[i], T[i]) (each nf field planes, device),
 // epochs passes in a fixed order; loss_hist (host, epochs, may be NULL)
 // receives the mean loss of every epoch.
 cudaError_t unet_train(UNet* net, const float* X, const float* T, int npairs, int epochs, float lr,

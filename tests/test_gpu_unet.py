@@ -38,14 +38,14 @@ def bf16_round(a: np.ndarray) -> np.ndarray:
     return b.astype(np.uint32).view(np.float32)
 
 
-def random_weights(seed: int) -> np.ndarray:
+def random_weights(seed: int, nf: int = 4) -> np.ndarray:
     rng = np.random.default_rng(seed)
     parts = []
     for (name, ci, co, k) in ou.LAYERS:
-        fan = k * k * (4 if name == "L0a" else ci)
+        fan = k * k * (nf if name == "L0a" else ci)
         w = rng.standard_normal((k * k, co, ci)) / np.sqrt(fan)
         if name == "L0a":
-            w[:, :, 4:] = 0.0            # padded input channels carry zeros
+            w[:, :, nf:] = 0.0           # padded input channels carry zeros
         parts.append(w.reshape(-1))
     return bf16_round(np.concatenate(parts).astype(np.float32))
 
@@ -312,3 +312,107 @@ def test_engines_agree_on_the_benchmark_grid():
         ys.append(y.cpu().numpy())
     assert rel(ys[0], ys[1]) < 1e-2, rel(ys[0], ys[1])
     s.close()
+
+
+# ------------------------------------------------------------------ 3-D grids
+# thermal3d_<nx>x<ny>x<nz>: stable stratification, so both balance factors are
+# non-trivial; 32x64x8 has several 16-row tiles per slice at level 0 and one at
+# level 2, 64x128x4 a single slice at level 2 (nz = 4 pools twice).
+CASES_3D = ["thermal3d_32x64x8", "thermal3d_64x128x4"]
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("name", CASES_3D)
+def test_forward_3d_matches_oracle(name, engine):
+    from paper_2007_10411_gb300 import jfnk
+    c = learned_case(name)
+    s = jfnk.Solver(c)
+    s.unet_init(1)
+    s.unet_set_engine(engine)
+    w = random_weights(21, nf=5)
+    s.unet_set_weights(w)
+    shape = synth.shape(c)
+    assert shape[0] == 5
+    X = np.random.default_rng(5).standard_normal(shape).astype(np.float32)
+    xd = torch.from_numpy(X).cuda().reshape(-1)
+    yd = torch.empty_like(xd)
+    s.unet_forward(xd, yd)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy().reshape(shape)
+    ref = ou.apply(w.astype(np.float64), X.astype(np.float64), ou.balance(c))
+    e = rel(y, ref)
+    assert e < 2e-2, e
+    for f in range(5):
+        assert rel(y[f], ref[f]) < 3e-2, (f, rel(y[f], ref[f]))
+    s.unet_forward(xd, yd)      # same output again: bitwise reproducible
+    torch.cuda.synchronize()
+    assert np.array_equal(yd.cpu().numpy().reshape(shape), y)
+    s.unet_status()
+    s.close()
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_gradient_3d_matches_oracle(engine):
+    from paper_2007_10411_gb300 import jfnk
+    c = learned_case("thermal3d_32x64x8")
+    s = jfnk.Solver(c)
+    s.unet_init(2)
+    s.unet_set_engine(engine)
+    w = random_weights(22, nf=5)
+    s.unet_set_weights(w)
+    shape = synth.shape(c)
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal(shape).astype(np.float32)
+    T = rng.standard_normal(shape).astype(np.float32)
+    loss, g = s.unet_loss_grad(torch.from_numpy(X).cuda().reshape(-1), torch.from_numpy(T).cuda().reshape(-1))
+    L_ref, g_ref = ou.loss_grad(w.astype(np.float64), X.astype(np.float64), T.astype(np.float64), ou.balance(c))
+    assert abs(loss - L_ref) <= 2e-2 * L_ref, (loss, L_ref)
+    offs = np.concatenate([[0], np.cumsum(ou.layer_sizes())])
+    errs = {}
+    for li, (name, ci, co, k) in enumerate(ou.LAYERS):
+        a, b = g[offs[li]:offs[li + 1]], g_ref[offs[li]:offs[li + 1]]
+        if name == "L0a":
+            a = a.reshape(k * k, co, ci)[:, :, :5]
+            b = b.reshape(k * k, co, ci)[:, :, :5]
+        errs[name] = rel(a, b)
+    print("3-D per-layer gradient relative L2:", {k: "%.2e" % v for k, v in errs.items()})
+    for name, e in errs.items():
+        assert e < 1e-2, (name, e)
+    s.close()
+
+
+def test_3d_untrained_network_matches_block_and_trained_network_converges():
+    """3-D learned preconditioner on a small stable thermal: with N = 0 the
+    solver follows the field-block path; after training on its own Arnoldi
+    pairs the learned steps still meet the Newton tolerance (same state)."""
+    from paper_2007_10411_gb300 import jfnk
+    c = learned_case("thermal3d_64x64x32")
+    s = jfnk.Solver(c)
+    s.unet_init(3)
+    u = torch.from_numpy(synth.initial_state(c).reshape(-1).copy()).cuda()
+    vb, sb = _run_steps(s, u, jfnk.PC_BLOCK, 1)
+    vl, sl = _run_steps(s, u, jfnk.PC_UNET, 1)
+    assert sb[0]["converged"] and sl[0]["converged"]
+    assert abs(sb[0]["gmres_iters"] - sl[0]["gmres_iters"]) <= 2
+    assert float((vb - vl).norm() / vb.norm()) < 1e-6
+    s.set_precond(jfnk.PC_BLOCK)
+    s.unet_capture(64, jfnk.PAIRS_ARNOLDI)
+    s.step(u.clone())
+    assert s.unet_pair_count() >= 16
+    hist = s.unet_train(10, 3e-4)
+    assert hist[-1] < 0.5 * hist[0], hist
+    s.unet_capture(0, 0)
+    vl, sl = _run_steps(s, u, jfnk.PC_UNET, 1)
+    print("3-D gmres iterations: block %d, learned %d" % (sb[0]["gmres_iters"], sl[0]["gmres_iters"]))
+    assert sl[0]["converged"] and not sl[0]["pc_fallback"]
+    assert float((vb - vl).norm() / vb.norm()) < 1e-6
+    s.close()
+
+
+def test_3d_unsupported_grids():
+    from paper_2007_10411_gb300 import jfnk
+    for name in ("thermal3d_32x48x8", "thermal3d_48x64x8", "thermal3d_32x64x6"):
+        c = learned_case(name)
+        with pytest.raises(jfnk.JfnkError) as e:
+            jfnk.Solver(c)
+        assert e.value.code == jfnk.JFNK_ERR_UNSUPPORTED, name
