@@ -46,6 +46,7 @@ struct Geo {
     // a = gamma_p pbar theta0 dt/2, c_div = gamma_p pbar (dt/2) s_u/s_p,
     // c_grad = theta0 s_p/s_u, dt/2
     double helm_a, schur_cdiv, schur_cgrad, half_dt;
+    void* s3;                         // 3-D: scratch of the split stencil passes (stencil3d_scratch_bytes)
 };
 
 constexpr int NUM_TILE_SHAPES = 4;

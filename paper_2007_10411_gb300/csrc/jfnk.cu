@@ -46,6 +46,7 @@ struct jfnk_handle {
     // stencil-precision buffers (double for FP64, float for MIXED)
     void *V, *Z, *w, *uT, *xT, *za, *zb, *da, *db, *nu, *tA, *tB;
     void* w2;        // second Jacobian-product buffer (right preconditioning: w'_{j-1} and w_j coexist)
+    void* s3;        // 3-D: scratch of the split stencil passes
     double* part;
     double* partB;   // second partial-sum area (Arnoldi pass B), inside the part allocation
     Ctl* ctl;
@@ -134,7 +135,7 @@ static bool unet_supported(const jfnk_handle* h) {
 
 static void free_all(jfnk_handle* h) {
     void* dev[] = {h->un, h->f, h->R, h->Fu64, h->x, h->tmp64, h->udev, h->heat, h->budg,
-                   h->V, h->Z, h->w, h->w2, h->uT, h->xT, h->za, h->zb, h->da, h->db, h->nu,
+                   h->V, h->Z, h->w, h->w2, h->s3, h->uT, h->xT, h->za, h->zb, h->da, h->db, h->nu,
                    h->tA, h->tB, h->part, h->ctl};
     for (void* p : dev)
         if (p) cudaFree(p);
@@ -358,6 +359,10 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     ALLOC(h->da, nbT);
     ALLOC(h->db, nbT);
     ALLOC(h->nu, h->npt * eT);
+    if (dim == 3) {
+        ALLOC(h->s3, stencil3d_scratch_bytes(G));
+        G.s3 = h->s3;
+    }
     ALLOC(h->tA, nbT);
     ALLOC(h->tB, nbT);
     ALLOC(h->part, part_len * sizeof(double));

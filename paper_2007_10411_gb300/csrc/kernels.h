@@ -41,6 +41,7 @@ cudaError_t launch_budgets(const Geo& G, const double* u, double dx, double dz, 
 
 // ------------------------------------------------------------ 3-D stencils
 int stencil3d_part_blocks(const Geo& G);
+size_t stencil3d_scratch_bytes(const Geo& G);
 template <typename T>
 cudaError_t launch_stencil3d(int mode, const Geo& G, const T* u, const T* v, const T* Fu, const double* f,
                              T* out, T* out2, double* part, Ctl* ctl, int check_done, cudaStream_t s);

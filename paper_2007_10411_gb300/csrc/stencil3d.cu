@@ -1,21 +1,41 @@
 // 3-D stencil kernels of libjfnk: F(u), R(u), the Jacobian-vector products,
-// the Smagorinsky eddy field, the field-block Chebyshev preconditioner and the
-// budgets, for fields (u, v, w, theta, p) on [z][y][x] (x, y periodic; z
-// cell-centred with signed mirror ghosts: w odd, theta and p even, u and v even
-// for free slip / odd for no slip; the eddy field is mirrored even).
+// the eddy field, the field-block Chebyshev preconditioner, the acoustic
+// Schur complement and the budgets, for fields (u, v, w, theta, p) on
+// [z][y][x] (x, y periodic; z cell-centred with signed mirror ghosts: w odd,
+// theta and p even, u and v even for free slip / odd for no slip; the eddy
+// field is mirrored even).
 //
 // Same discretisation as the 2-D kernels (Deslauriers-Dubuc p = 2 derivative,
 // Section 2.3; skew-symmetric convection of every field, Section 2.2;
 // Eqs. ch2_28-ch2_30 with Laplacian-form eddy diffusion, Section 2.4), with
-// the Smagorinsky filter width Delta = (dx dy dz)^(1/3) and the full 3x3 strain.
+// the filter width Delta = (dx dy dz)^(1/3) and the full 3x3 strain.
 //
-// Tiling: one CTA computes TX x TY x TZ outputs.  Stage 1 stages the fields in
-// a box with a halo of 2r = 4 in shared memory.  Stage 2 forms the first
-// derivatives only on the three "arms" the second application of D reads:
-// D_x on (tile + x-halo r), D_y on (tile + y-halo r), D_z on (tile + z-halo r),
-// and the eddy coefficient on the same arms (from the 9 velocity gradients at
-// each arm point; a ghost z row takes the value of its mirror image).  Stage 3
-// assembles fluxes, diffusion and point-wise terms for the outputs.
+// Every term of F is a sum over the three axes of a one-dimensional stencil
+// once the eddy coefficient is known at each point (convection flux and
+// advective form along j, D_j(K D_j phi), the pressure gradient and the
+// divergence of the pressure equation), plus point-wise terms.  The operator
+// is therefore evaluated in three passes that each stage only what their axis
+// needs:
+//   strain  |S| (and, for the difference-form Jacobian product, |S(a+b)| - |S(a)|
+//           without cancellation) at every point: a plane tile with a halo of
+//           r = 2 in x, y in shared memory, z neighbours read directly;
+//   plane   the x and y terms and the point-wise ones for a TX x TY tile of one
+//           plane: the fields with a halo of 2r = 4 in x and y, the first
+//           derivatives on the x / y arms (tile + r) computed once, the eddy
+//           coefficients on the arms from the strain pass; writes the partial sum;
+//   slab    the z terms for a TX x TZ slab of one y row: the fields with a halo
+//           of 4 in z (mirror ghosts), z derivatives on the z arms, then the
+//           partial sum of the plane pass is added and the mode's output
+//           (F, 2u/dt + F, the residual with its norms, or the Jacobian product)
+//           written.
+// Loads are coalesced along x in every pass; the halos are re-read from L2.
+//
+// Difference form (float32 Jacobian product): with a = u and b = eps v every
+// term of F(a + b) - F(a) is written as a difference (products a_j b_phi +
+// b_j (a_phi + b_phi), K(a) D b + (K(a + b) - K(a)) D(a + b)), so no O(1)
+// quantity is cancelled in float32.  The other modes evaluate F(b) with
+// a = 0 (b = u, or b = u + eps v for the plain forward difference), for
+// which the same formulas reduce to F term by term.
 #include <math.h>
 
 #include <atomic>
@@ -28,7 +48,10 @@ namespace d3 {
 
 constexpr int R = 2;
 constexpr int HALO = 2 * R;
-constexpr int MODE_F = 0, MODE_RHS = 1, MODE_RES = 2, MODE_JV = 3, MODE_RHSRES = 4;
+constexpr int MODE_F = 0, MODE_RHS = 1, MODE_RES = 2, MODE_JV = 3, MODE_RHSRES = 4, MODE_DJV = 5;
+
+template <int MODE>
+struct Two { static constexpr bool v = MODE == MODE_DJV; };   // two states a, b (else a = 0)
 
 template <typename T>
 __device__ __forceinline__ T dd(const T* s, int i, int st, T ih) {
@@ -38,6 +61,11 @@ template <typename T>
 __device__ __forceinline__ T ddp(const T* a, const T* b, int i, int st, T ih) {
     return (T(2.0 / 3.0) * (a[i + st] * b[i + st] - a[i - st] * b[i - st]) -
             T(1.0 / 12.0) * (a[i + 2 * st] * b[i + 2 * st] - a[i - 2 * st] * b[i - 2 * st])) * ih;
+}
+// D f from the four neighbours f(-2), f(-1), f(+1), f(+2)
+template <typename T>
+__device__ __forceinline__ T d5(T m2, T m1, T p1, T p2, T ih) {
+    return (T(2.0 / 3.0) * (p1 - m1) - T(1.0 / 12.0) * (p2 - m2)) * ih;
 }
 
 __device__ __forceinline__ int mirror(int gz, int nz, int& side) {
@@ -51,119 +79,11 @@ __device__ __forceinline__ int wrap(int g, int n) {
     int r = g % n;
     return r < 0 ? r + n : r;
 }
-
-// Box geometry of a TX x TY x TZ tile.
-template <int TX, int TY, int TZ>
-struct Box {
-    static constexpr int SX = TX + 2 * HALO, SY = TY + 2 * HALO, SZ = TZ + 2 * HALO;
-    static constexpr int SXY = SX * SY, PL = SX * SY * SZ;
-    static constexpr int QX = TX + 2 * R, QY = TY + 2 * R, QZ = TZ + 2 * R;
-    static constexpr int AX = QX * TY * TZ, AY = TX * QY * TZ, AZ = TX * TY * QZ;
-    static constexpr int AS = AX + AY + AZ;              // one field's three arms
-    // box index of box coordinates
-    __device__ static int b(int ix, int iy, int iz) { return (iz * SY + iy) * SX + ix; }
-    // arm indices (centre of output (tx,ty,tz) is qx = tx + R etc.)
-    __device__ static int ax(int qx, int ty, int tz) { return (tz * TY + ty) * QX + qx; }
-    __device__ static int ay(int tx, int qy, int tz) { return AX + (tz * QY + qy) * TX + tx; }
-    __device__ static int az(int tx, int ty, int qz) { return AX + AY + (qz * TY + ty) * TX + tx; }
-};
-
-// Stage 1: NF fields from f0 into s[q][PL]; LOADMODE 0: u, 1: u + ev v, 2: ev v.
-template <typename T, int LOADMODE, int NF, int TX, int TY, int TZ>
-__device__ __forceinline__ void load_box(T* s, const T* __restrict__ u, const T* __restrict__ v,
-                                         const T (&ev)[5], const Geo& G, int x0, int y0, int z0,
-                                         int f0) {
-    using B = Box<TX, TY, TZ>;
-    for (int idx = threadIdx.x; idx < B::PL; idx += blockDim.x) {
-        const int ix = idx % B::SX, r1 = idx / B::SX;
-        const int iy = r1 % B::SY, iz = r1 / B::SY;
-        int side;
-        const int sz = mirror(z0 + iz - HALO, G.nz, side);
-        const int sy = wrap(y0 + iy - HALO, G.ny);
-        const int sx = wrap(x0 + ix - HALO, G.nx);
-        const bool ok = sz >= 0 && sz < G.nz;
-        const size_t off = ((size_t)sz * G.ny + sy) * G.nx + sx;
-#pragma unroll
-        for (int q = 0; q < NF; ++q) {
-            const int f = f0 + q;
-            T val = T(0);
-            if (ok) {
-                const size_t o = (size_t)f * G.npt + off;
-                if (LOADMODE == 0) val = u[o];
-                else if (LOADMODE == 1) val = u[o] + ev[f] * v[o];
-                else val = ev[f] * v[o];
-                if (side == 1) val *= T(G.pb[f]);
-                else if (side == 2) val *= T(G.pt[f]);
-            }
-            s[q * B::PL + idx] = val;
-        }
-    }
-}
-
-// Stage 2: derivative arms of field box s into g (one field: AS values).
-template <typename T, int TX, int TY, int TZ>
-__device__ __forceinline__ void arms(const T* s, T* g, T ix_, T iy_, T iz_) {
-    using B = Box<TX, TY, TZ>;
-    for (int idx = threadIdx.x; idx < B::AS; idx += blockDim.x) {
-        int bx, by, bz, st;
-        T ih;
-        if (idx < B::AX) {
-            const int qx = idx % B::QX, r1 = idx / B::QX;
-            bx = qx + R; by = r1 % TY + HALO; bz = r1 / TY + HALO; st = 1; ih = ix_;
-        } else if (idx < B::AX + B::AY) {
-            const int j = idx - B::AX;
-            const int tx = j % TX, r1 = j / TX;
-            bx = tx + HALO; by = r1 % B::QY + R; bz = r1 / B::QY + HALO; st = B::SX; ih = iy_;
-        } else {
-            const int j = idx - B::AX - B::AY;
-            const int tx = j % TX, r1 = j / TX;
-            bx = tx + HALO; by = r1 % TY + HALO; bz = r1 / TY + R; st = B::SXY; ih = iz_;
-        }
-        g[idx] = dd(s, B::b(bx, by, bz), st, ih);
-    }
-}
-
-// Box coordinates of arm point idx (and whether it is a z arm).
-template <int TX, int TY, int TZ>
-__device__ __forceinline__ void arm_point(int idx, int& bx, int& by, int& bz, bool& zarm) {
-    using B = Box<TX, TY, TZ>;
-    zarm = false;
-    if (idx < B::AX) {
-        const int qx = idx % B::QX, r1 = idx / B::QX;
-        bx = qx + R; by = r1 % TY + HALO; bz = r1 / TY + HALO;
-    } else if (idx < B::AX + B::AY) {
-        const int j = idx - B::AX;
-        const int tx = j % TX, r1 = j / TX;
-        bx = tx + HALO; by = r1 % B::QY + R; bz = r1 / B::QY + HALO;
-    } else {
-        const int j = idx - B::AX - B::AY;
-        const int tx = j % TX, r1 = j / TX;
-        bx = tx + HALO; by = r1 % TY + HALO; bz = r1 / TY + R;
-        zarm = true;
-    }
-}
-
-// For a z-arm point in a ghost row, the box row of its mirror image (even
-// reflection of the eddy field); -1 if the row is never read.
-__device__ __forceinline__ int eddy_box_row(int bz, int z0, int nz) {
-    const int gz = z0 + bz - HALO;
-    if (gz >= 0 && gz < nz) return bz;
-    if (gz < 0) return (-1 - gz) - z0 + HALO;
-    if (gz < nz + R) return (2 * nz - 1 - gz) - z0 + HALO;
-    return -1;
-}
-
-// Velocity gradient at box point c of boxes U, V, W: g[i][j] = D_j u_i.
-template <typename T, int SX, int SXY>
-__device__ __forceinline__ void grad3(const T* U, const T* V, const T* W, int c, T ix_, T iy_, T iz_,
-                                      T (&g)[3][3]) {
-    const T* comp[3] = {U, V, W};
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        g[i][0] = dd(comp[i], c, 1, ix_);
-        g[i][1] = dd(comp[i], c, SX, iy_);
-        g[i][2] = dd(comp[i], c, SXY, iz_);
-    }
+// even mirror of a row of the eddy field (-1: beyond one reflection, never read)
+__device__ __forceinline__ int eddy_row(int gz, int nz) {
+    if (gz >= 0 && gz < nz) return gz;
+    if (gz < 0) return -1 - gz < nz ? -1 - gz : -1;
+    return 2 * nz - 1 - gz >= 0 ? 2 * nz - 1 - gz : -1;
 }
 
 // Deardorff coefficient along an arm (Section 2.4, Eq. KmM) from the strain s:
@@ -178,144 +98,542 @@ __device__ __forceinline__ T dd3_coef(T s, bool zarm, bool heat, const Geo& G) {
     return c * (s * (T(1) + T(zarm ? G.dd_az : G.dd_ah) * l));
 }
 
+// Coefficient pair (K(a), K(a + b) - K(a)) of one field at an arm point from
+// na = |S(a)| and ds = |S(a + b)| - |S(a)| (na = 0: the coefficient K(b) of
+// the one-state modes in the second slot).  SMAG 1: Smagorinsky (the caller
+// applies 1/Pr for theta); SMAG 2: Deardorff, the arm's direction and the
+// field (momentum / heat) picking the coefficient.
+template <typename T, int SMAG>
+__device__ __forceinline__ void kpair(const Geo& G, T na, T ds, bool zarm, bool heat, T& k, T& dk) {
+    if (SMAG == 1) {
+        const T c = T(G.cs2);
+        k = c * na;
+        dk = c * ds;
+        return;
+    }
+    const T c = T(zarm ? G.dd_cM : G.dd_cm);
+    if (!heat) {
+        k = c * na;
+        dk = c * ds;
+        return;
+    }
+    // heat: g(s) = c s (1 + a l(s)); g(s') - g(s) = ds (1 + a l') + a s (l' - l),
+    // l' - l = c_l ds while both are below the cap
+    const T a = T(zarm ? G.dd_az : G.dd_ah);
+    const T dl_cap = T(G.dd_delta);
+    T la = dl_cap, lp = dl_cap, dl = T(0);
+    if (G.dd_cl >= 0.0) {
+        const T ta = T(G.dd_cl) * na, tq = T(G.dd_cl) * (na + ds);
+        la = ta < dl_cap ? ta : dl_cap;
+        lp = tq < dl_cap ? tq : dl_cap;
+        if (ta < dl_cap && tq < dl_cap) dl = T(G.dd_cl) * ds;
+        else if (ta < dl_cap || tq < dl_cap) dl = lp - la;
+    }
+    k = c * (na * (T(1) + a * la));
+    dk = c * (ds * (T(1) + a * lp) + a * na * dl);
+}
+
+// The two states of field f at flat index o: DJV a = u, b = eps_f v;
+// JV a = 0, b = u + eps_f v; other modes a = 0, b = u.
+template <typename T, int MODE>
+__device__ __forceinline__ void load_ab(const T* __restrict__ u, const T* __restrict__ v, T ev, size_t o, T& a,
+                                        T& b) {
+    if constexpr (MODE == MODE_DJV) {
+        a = u[o];
+        b = ev * v[o];
+    } else if constexpr (MODE == MODE_JV) {
+        a = T(0);
+        b = u[o] + ev * v[o];
+    } else {
+        a = T(0);
+        b = u[o];
+    }
+}
+
+// eps_f = eps_jv * scale_f (Jacobian-product modes)
 template <typename T>
-__device__ __forceinline__ T strain_sq(const T (&g)[3][3]) {    // S_ij S_ij
-    T ss = T(0);
+__device__ __forceinline__ T eps_field(const Ctl* ctl, const Geo& G, int f) {
+    return T(ctl->eps_jv * G.scale[f]);
+}
+
+// ------------------------------------------------------------------ tiles
+constexpr int PX = 32, PY = 8;                 // plane tile (one output per thread)
+constexpr int KX = 32, KY = 8;                 // strain tile
+template <typename T> struct SlabT;            // slab tile TX x TZ
+template <> struct SlabT<float>  { static constexpr int TX = 32, TZ = 16; };
+template <> struct SlabT<double> { static constexpr int TX = 32, TZ = 8; };
+static_assert(PX * PY == NTHREADS && KX * KY == NTHREADS, "one output per thread");
+
+// ============================================================================
+// Strain pass: s = sqrt(2 S:S) of b (one-state modes) or, for the difference
+// form, sa = |S(a)| and ds = |S(a + b)| - |S(a)| = (S':S' - S:S) * 2 / (s + s')
+// at every point.  EDDY: the eddy field of u instead (nu = cs2 s, Deardorff:
+// s itself), with its maximum.
+// ============================================================================
+template <typename T, int MODE, int EDDY>
+__global__ void __launch_bounds__(NTHREADS)
+strain3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict__ s0, T* __restrict__ s1,
+         double* part, Ctl* ctl, int check_done) {
+    constexpr bool TWO = Two<MODE>::v;
+    constexpr int SX = KX + 2 * R, SY = KY + 2 * R, SP = SX * SY;
+    constexpr int NA = TWO ? 6 : 3;               // (b u, b v, b w) [, (a u, a v, a w)]
+    if ((MODE == MODE_JV || MODE == MODE_DJV) && check_done && ctl->done) return;
+    __shared__ T st[NA][SP];
+    const int x0 = blockIdx.x * KX, y0 = blockIdx.y * KY, gz = blockIdx.z;
+    const T ix = T(G.inv_dx), iy = T(G.inv_dy), iz = T(G.inv_dz);
+    T ev[3] = {T(0), T(0), T(0)};
+    if (MODE == MODE_JV || MODE == MODE_DJV) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+        for (int f = 0; f < 3; ++f) ev[f] = eps_field<T>(ctl, G, f);
+    }
+    const size_t plane = (size_t)gz * G.ny * G.nx;
+    for (int idx = threadIdx.x; idx < SP; idx += NTHREADS) {
+        const int ixl = idx % SX, iyl = idx / SX;
+        const size_t o = plane + (size_t)wrap(y0 + iyl - R, G.ny) * G.nx + wrap(x0 + ixl - R, G.nx);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const T s = T(0.5) * (g[i][j] + g[j][i]);
-            ss += s * s;
+        for (int f = 0; f < 3; ++f) {
+            T a, b;
+            load_ab<T, MODE>(u, v, ev[f], (size_t)f * G.npt + o, a, b);
+            st[f][idx] = b;
+            if (TWO) st[3 + f][idx] = a;
         }
-    return ss;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % KX, ty = threadIdx.x / KX;
+    const int gx = x0 + tx, gy = y0 + ty;
+    T mx = T(0);
+    if (gx < G.nx && gy < G.ny) {
+        const int c = (ty + R) * SX + tx + R;
+        // z neighbours of the three components (mirror ghosts with their parity)
+        T zb[3][4], za[3][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int dz = k < 2 ? k - 2 : k - 1;        // -2, -1, +1, +2
+            int side;
+            const int sz = mirror(gz + dz, G.nz, side);
+            const size_t o = ((size_t)sz * G.ny + gy) * G.nx + gx;
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                T a, b;
+                load_ab<T, MODE>(u, v, ev[f], (size_t)f * G.npt + o, a, b);
+                const T sg = side == 1 ? T(G.pb[f]) : (side == 2 ? T(G.pt[f]) : T(1));
+                zb[f][k] = sg * b;
+                za[f][k] = sg * a;
+            }
+        }
+        T gB[3][3], gA[3][3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            gB[f][0] = dd(st[f], c, 1, ix);
+            gB[f][1] = dd(st[f], c, SX, iy);
+            gB[f][2] = d5(zb[f][0], zb[f][1], zb[f][2], zb[f][3], iz);
+            if (TWO) {
+                gA[f][0] = dd(st[3 + f], c, 1, ix);
+                gA[f][1] = dd(st[3 + f], c, SX, iy);
+                gA[f][2] = d5(za[f][0], za[f][1], za[f][2], za[f][3], iz);
+            }
+        }
+        const size_t p = plane + (size_t)gy * G.nx + gx;
+        if (TWO) {
+            T ssa = T(0), dss = T(0);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const T sA = T(0.5) * (gA[i][j] + gA[j][i]);
+                    const T sB = T(0.5) * (gB[i][j] + gB[j][i]);
+                    ssa += sA * sA;
+                    dss += (T(2) * sA + sB) * sB;       // S':S' - S:S
+                }
+            const T na = sqrt(T(2) * ssa);
+            const T tp = T(2) * (ssa + dss);
+            const T np = sqrt(tp > T(0) ? tp : T(0));
+            const T den = na + np;
+            s0[p] = na;
+            s1[p] = den > T(0) ? T(2) * dss / den : T(0);
+        } else {
+            T ss = T(0);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const T sB = T(0.5) * (gB[i][j] + gB[j][i]);
+                    ss += sB * sB;
+                }
+            const T sv = sqrt(T(2) * ss);
+            if (EDDY) {
+                const T val = (G.sgs == 2 ? T(1) : T(G.cs2)) * sv;
+                s1[p] = val;
+                mx = val;
+            } else {
+                s1[p] = sv;
+            }
+        }
+    }
+    if (EDDY) {
+        double m1[1] = {(double)mx};
+        const int nblk = gridDim.x * gridDim.y * gridDim.z;
+        const int blk = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        block_partials_max<1>(m1, 1, part, nblk, blk);
+        if (arrive_last(&ctl->counter[CNT_EDDY], nblk)) {
+            __shared__ double tot[1];
+            final_maxes(part, nblk, 1, tot);
+            if (threadIdx.x == 0) ctl->kmax = tot[0];
+        }
+    }
 }
 
 // ============================================================================
-// F, 2u/dt + F, residual and plain forward-difference Jv
+// Plane pass: x and y terms of every field and the point-wise terms, for a
+// PX x PY tile of plane z = blockIdx.z; writes their sum to P.
 // ============================================================================
-template <typename T, int MODE, int SMAG, int TX, int TY, int TZ>
+template <typename T, int MODE, int SMAG>
 __global__ void __launch_bounds__(NTHREADS)
-stencil3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ Fu,
-          const double* __restrict__ f, T* __restrict__ out, T* __restrict__ out2,
-          double* __restrict__ part, Ctl* ctl, int check_done) {
-    using B = Box<TX, TY, TZ>;
-    if (MODE == MODE_JV && check_done && ctl->done) return;
+plane3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ s0,
+        const T* __restrict__ s1, T* __restrict__ P, Ctl* ctl, int check_done) {
+    constexpr bool TWO = Two<MODE>::v;
+    constexpr int SX = PX + 2 * HALO, SY = PY + 2 * HALO, SP = SX * SY;
+    constexpr int AXN = (PX + 2 * R) * PY, AYN = PX * (PY + 2 * R), AN = AXN + AYN;   // x arms, y arms
+    constexpr int NS = TWO ? 2 : 1;                  // states staged (b [, a])
+    constexpr int NK = SMAG ? (TWO ? 2 : 1) : 0;     // strain values on the arms (ds [, sa])
+    if ((MODE == MODE_JV || MODE == MODE_DJV) && check_done && ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* s1 = reinterpret_cast<T*>(smem_raw);        // [5][PL]
-    T* g = s1 + 5 * B::PL;                          // [4][AS] derivative arms of u, v, w, theta
-    T* nu = g + 4 * B::AS;                          // [AS] eddy coefficient on the arms
-    T* kh = nu + B::AS;                             // [AS] Deardorff: heat coefficient on the arms
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-    const T ix_ = T(G.inv_dx), iy_ = T(G.inv_dy), iz_ = T(G.inv_dz);
-    __shared__ double cfs[5];
-    __shared__ T evs[5];
+    T* st = reinterpret_cast<T*>(smem_raw);          // [NS][5][SP]: b fields, then a fields
+    T* ga = st + NS * 5 * SP;                        // [NS][4][AN] first derivatives on the arms
+    T* ks = ga + NS * 4 * AN;                        // [NK][AN] strain on the arms
+    const int x0 = blockIdx.x * PX, y0 = blockIdx.y * PY, gz = blockIdx.z;
+    const T ix = T(G.inv_dx), iy = T(G.inv_dy);
     T ev[5] = {T(0), T(0), T(0), T(0), T(0)};
-    if (MODE == MODE_JV) {
-        if (threadIdx.x < 5) {
-            const double e = ctl->eps_jv * G.scale[threadIdx.x];
-            evs[threadIdx.x] = T(e);
-            cfs[threadIdx.x] = e != 0.0 ? 1.0 / e : 0.0;
-        }
-        __syncthreads();
+    if (MODE == MODE_JV || MODE == MODE_DJV) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) ev[q] = evs[q];
-        load_box<T, 1, 5, TX, TY, TZ>(s1, u, v, ev, G, x0, y0, z0, 0);
-    } else {
-        load_box<T, 0, 5, TX, TY, TZ>(s1, u, v, ev, G, x0, y0, z0, 0);
+        for (int f = 0; f < 5; ++f) ev[f] = eps_field<T>(ctl, G, f);
     }
-    __syncthreads();
+    const size_t plane = (size_t)gz * G.ny * G.nx;
+    for (int idx = threadIdx.x; idx < SP; idx += NTHREADS) {
+        const int ixl = idx % SX, iyl = idx / SX;
+        const size_t o = plane + (size_t)wrap(y0 + iyl - HALO, G.ny) * G.nx + wrap(x0 + ixl - HALO, G.nx);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) arms<T, TX, TY, TZ>(s1 + q * B::PL, g + q * B::AS, ix_, iy_, iz_);
+        for (int f = 0; f < 5; ++f) {
+            T a, b;
+            load_ab<T, MODE>(u, v, ev[f], (size_t)f * G.npt + o, a, b);
+            st[f * SP + idx] = b;
+            if (TWO) st[(5 + f) * SP + idx] = a;
+        }
+    }
     if (SMAG) {
-        const T cs2 = T(G.cs2);
-        for (int idx = threadIdx.x; idx < B::AS; idx += blockDim.x) {
-            int bx, by, bz;
-            bool zarm;
-            arm_point<TX, TY, TZ>(idx, bx, by, bz, zarm);
-            T val = T(0);
-            const int bzz = zarm ? eddy_box_row(bz, z0, G.nz) : bz;
-            T hv = T(0);
-            if (bzz >= 0) {
-                T gr[3][3];
-                grad3<T, B::SX, B::SXY>(s1, s1 + B::PL, s1 + 2 * B::PL, B::b(bx, by, bzz), ix_, iy_, iz_, gr);
-                if (SMAG == 2) {
-                    // Deardorff: the arm's own direction picks K_m / K_M and K_h / K_H
-                    const T sv = sqrt(T(2) * strain_sq(gr));
-                    val = dd3_coef(sv, zarm, false, G);
-                    hv = dd3_coef(sv, zarm, true, G);
-                } else {
-                    val = cs2 * sqrt(T(2) * strain_sq(gr));
-                }
-            }
-            nu[idx] = val;
-            if (SMAG == 2) kh[idx] = hv;
+        for (int idx = threadIdx.x; idx < AN; idx += NTHREADS) {
+            int qx, qy;
+            if (idx < AXN) { qx = idx % (PX + 2 * R) - R; qy = idx / (PX + 2 * R); }
+            else { const int j = idx - AXN; qx = j % PX; qy = j / PX - R; }
+            const size_t o = plane + (size_t)wrap(y0 + qy, G.ny) * G.nx + wrap(x0 + qx, G.nx);
+            ks[idx] = s1[o];
+            if (TWO) ks[AN + idx] = s0[o];
         }
     }
     __syncthreads();
+    // first derivatives of u, v, w, theta (each state) on the arms
+    for (int idx = threadIdx.x; idx < AN; idx += NTHREADS) {
+        int c, stp;
+        T ih;
+        if (idx < AXN) {
+            const int qx = idx % (PX + 2 * R), qy = idx / (PX + 2 * R);
+            c = (qy + HALO) * SX + qx + R;
+            stp = 1;
+            ih = ix;
+        } else {
+            const int j = idx - AXN;
+            const int qx = j % PX, qy = j / PX;
+            c = (qy + R) * SX + qx + HALO;
+            stp = SX;
+            ih = iy;
+        }
+#pragma unroll
+        for (int q = 0; q < NS * 4; ++q) {
+            const int arr = q < 4 ? q : 5 + (q - 4);          // b: fields 0..3, a: fields 0..3
+            ga[q * AN + idx] = dd(st + arr * SP, c, stp, ih);
+        }
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % PX, ty = threadIdx.x / PX;
+    const int gx = x0 + tx, gy = y0 + ty;
+    if (gx >= G.nx || gy >= G.ny) return;
+    const int c = (ty + HALO) * SX + tx + HALO;
+    const int cax = ty * (PX + 2 * R) + tx + R;               // x arm at the output point
+    const int cay = AXN + (ty + R) * PX + tx;                 // y arm at the output point
+    const int astr[2] = {1, PX};
+    const int carm[2] = {cax, cay};
+    const int sst[2] = {1, SX};
+    const T ihs[2] = {ix, iy};
+    const T* Bf = st;                                         // b fields
+    const T* Af = st + 5 * SP;                                // a fields (TWO)
+    T dF[5];
+    T dbp[2], dap[2];                                         // D_j of p (b, a) at the point
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        dbp[j] = dd(Bf + 4 * SP, c, sst[j], ihs[j]);
+        dap[j] = TWO ? dd(Af + 4 * SP, c, sst[j], ihs[j]) : T(0);
+    }
+#pragma unroll
+    for (int fl = 0; fl < 5; ++fl) {
+        const T* B = Bf + fl * SP;
+        const T* A = Af + fl * SP;
+        T flux = T(0), adv = T(0);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const T* bj = Bf + j * SP;                        // b_u (x) or b_v (y)
+            const T* aj = Af + j * SP;
+            const int s = sst[j];
+            T fj = T(0);
+#pragma unroll
+            for (int l = 1; l <= 2; ++l) {
+                const T cl = l == 1 ? T(2.0 / 3.0) : T(-1.0 / 12.0);
+                const int ip = c + l * s, im = c - l * s;
+                if (TWO)
+                    fj += cl * ((aj[ip] * B[ip] + bj[ip] * (A[ip] + B[ip])) - (aj[im] * B[im] + bj[im] * (A[im] + B[im])));
+                else
+                    fj += cl * (bj[ip] * B[ip] - bj[im] * B[im]);
+            }
+            flux += fj * ihs[j];
+            T daj, dbj;
+            if (fl < 4) {
+                dbj = ga[fl * AN + carm[j]];
+                daj = TWO ? ga[(4 + fl) * AN + carm[j]] : T(0);
+            } else {
+                dbj = dbp[j];
+                daj = dap[j];
+            }
+            adv += TWO ? (aj[c] * dbj + bj[c] * (daj + dbj)) : bj[c] * dbj;
+        }
+        dF[fl] = -(T(0.5) * flux + T(0.5) * adv);
+        if (fl < 4) {
+            const T* gb = ga + fl * AN;
+            const T* gA = ga + (4 + fl) * AN;
+            T dif = T(0);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int q = carm[j], s = astr[j];
+                T sj = T(0);
+#pragma unroll
+                for (int l = 1; l <= 2; ++l) {
+                    const T cl = l == 1 ? T(2.0 / 3.0) : T(-1.0 / 12.0);
+                    const int p1 = q + l * s, m1 = q - l * s;
+                    if (SMAG) {
+                        T kp, dkp, km, dkm;
+                        kpair<T, SMAG>(G, TWO ? ks[AN + p1] : T(0), ks[p1], false, fl == 3, kp, dkp);
+                        kpair<T, SMAG>(G, TWO ? ks[AN + m1] : T(0), ks[m1], false, fl == 3, km, dkm);
+                        if (TWO)
+                            sj += cl * ((kp * gb[p1] + dkp * (gA[p1] + gb[p1])) - (km * gb[m1] + dkm * (gA[m1] + gb[m1])));
+                        else
+                            sj += cl * (dkp * gb[p1] - dkm * gb[m1]);
+                    } else {
+                        sj += cl * (gb[p1] - gb[m1]);
+                    }
+                }
+                dif += sj * ihs[j];
+            }
+            if (SMAG == 1) {
+                if (fl == 3) dif *= T(G.inv_Pr);
+            } else if (!SMAG) {
+                dif *= T(fl == 3 ? G.K_H : G.K_M);
+            }
+            dF[fl] += dif;
+        }
+    }
+    const T th0 = T(G.theta0);
+    dF[0] += -th0 * dbp[0];
+    dF[1] += -th0 * dbp[1];
+    dF[2] += T(G.g) * Bf[3 * SP + c] / th0;
+    dF[3] += -T(G.beta) * Bf[2 * SP + c];
+    if (MODE != MODE_DJV && G.heat != nullptr && gz == 0)
+        dF[3] += T(G.heat[(size_t)gy * G.nx + gx] * G.heat_coef);
+    {   // pressure equation, x and y parts of the divergence
+        const T divb = ga[cax] + ga[AN + cay];
+        const T pa = TWO ? Af[4 * SP + c] : T(0), pb = Bf[4 * SP + c];
+        T t = (T(G.pbar) + pa + pb) * divb;
+        if (TWO) t += pb * (ga[4 * AN + cax] + ga[5 * AN + cay]);
+        dF[4] += -T(G.gamma_p) * t;
+    }
+    const size_t off = plane + (size_t)gy * G.nx + gx;
+#pragma unroll
+    for (int fl = 0; fl < 5; ++fl) P[(size_t)fl * G.npt + off] = dF[fl];
+}
 
-    const T* U = s1;
-    const T* Vv = s1 + B::PL;
-    const T* W = s1 + 2 * B::PL;
-    const T* P = s1 + 4 * B::PL;
-    const T KMc = T(G.K_M), KHc = T(G.K_H), iPr = T(G.inv_Pr), th0 = T(G.theta0);
+// ============================================================================
+// Slab pass: z terms for a TX x TZ slab of row y = blockIdx.z (z tiles along
+// blockIdx.x so that consecutive CTAs share their z halos in L2), plus the
+// plane pass's sum; writes the mode's output.
+// ============================================================================
+template <typename T, int MODE, int SMAG>
+__global__ void __launch_bounds__(NTHREADS)
+slab3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ Fu,
+       const double* __restrict__ f, const T* __restrict__ s0, const T* __restrict__ s1,
+       const T* __restrict__ P, T* __restrict__ out, T* __restrict__ out2, double* __restrict__ part, Ctl* ctl,
+       int check_done) {
+    constexpr bool TWO = Two<MODE>::v;
+    constexpr int TX = SlabT<T>::TX, TZ = SlabT<T>::TZ;
+    constexpr int SZ = TZ + 2 * HALO, SP = TX * SZ;          // staged rows [row][x]
+    constexpr int QZ = TZ + 2 * R, AN = TX * QZ;             // z arms
+    constexpr int NS = TWO ? 2 : 1;
+    constexpr int NK = SMAG ? (TWO ? 2 : 1) : 0;
+    constexpr int PER = TX * TZ / NTHREADS;                  // outputs per thread
+    if ((MODE == MODE_JV || MODE == MODE_DJV) && check_done && ctl->done) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* st = reinterpret_cast<T*>(smem_raw);                  // [NS][5][SP]
+    T* ga = st + NS * 5 * SP;                                // [NS][4][AN]
+    T* ks = ga + NS * 4 * AN;                                // [NK][AN]
+    const int z0 = blockIdx.x * TZ, x0 = blockIdx.y * TX, gy = blockIdx.z;
+    const T iz = T(G.inv_dz);
+    T ev[5] = {T(0), T(0), T(0), T(0), T(0)};
+    if (MODE == MODE_JV || MODE == MODE_DJV) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) ev[q] = eps_field<T>(ctl, G, q);
+    }
+    const size_t row = (size_t)gy * G.nx;
+    for (int idx = threadIdx.x; idx < SP; idx += NTHREADS) {
+        const int xl = idx % TX, rl = idx / TX;
+        int side;
+        const int sz = mirror(z0 + rl - HALO, G.nz, side);
+        const bool ok = sz >= 0 && sz < G.nz;
+        const size_t o = (size_t)sz * G.ny * G.nx + row + wrap(x0 + xl, G.nx);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            T a = T(0), b = T(0);
+            if (ok) {
+                load_ab<T, MODE>(u, v, ev[q], (size_t)q * G.npt + o, a, b);
+                const T sg = side == 1 ? T(G.pb[q]) : (side == 2 ? T(G.pt[q]) : T(1));
+                a *= sg;
+                b *= sg;
+            }
+            st[q * SP + idx] = b;
+            if (TWO) st[(5 + q) * SP + idx] = a;
+        }
+    }
+    if (SMAG) {
+        for (int idx = threadIdx.x; idx < AN; idx += NTHREADS) {
+            const int xl = idx % TX, ql = idx / TX;
+            const int sz = eddy_row(z0 + ql - R, G.nz);
+            T kv1 = T(0), kv0 = T(0);
+            if (sz >= 0) {
+                const size_t o = (size_t)sz * G.ny * G.nx + row + wrap(x0 + xl, G.nx);
+                kv1 = s1[o];
+                if (TWO) kv0 = s0[o];
+            }
+            ks[idx] = kv1;
+            if (TWO) ks[AN + idx] = kv0;
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < AN; idx += NTHREADS) {
+        const int xl = idx % TX, ql = idx / TX;
+        const int c = (ql + R) * TX + xl;
+#pragma unroll
+        for (int q = 0; q < NS * 4; ++q) {
+            const int arr = q < 4 ? q : 5 + (q - 4);
+            ga[q * AN + idx] = dd(st + arr * SP, c, TX, iz);
+        }
+    }
+    __syncthreads();
+    const T th0 = T(G.theta0);
     double acc[2] = {0.0, 0.0};
-    for (int idx = threadIdx.x; idx < TX * TY * TZ; idx += blockDim.x) {
-        const int tx = idx % TX, r1 = idx / TX;
-        const int ty = r1 % TY, tz = r1 / TY;
-        const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-        if (gx >= G.nx || gy >= G.ny || gz >= G.nz) continue;
-        const int c = B::b(tx + HALO, ty + HALO, tz + HALO);
-        const int cx = B::ax(tx + R, ty, tz), cy = B::ay(tx, ty + R, tz), cz = B::az(tx, ty, tz + R);
-        const T uc = U[c], vc = Vv[c], wc = W[c];
-        const T px = dd(P, c, 1, ix_), py = dd(P, c, B::SX, iy_), pz = dd(P, c, B::SXY, iz_);
-        T Fv[5];
+    const T* Bf = st;
+    const T* Af = st + 5 * SP;
+    double cf[5] = {0.0, 0.0, 0.0, 0.0, 0.0};          // 1 / eps_f of the Jacobian-product modes
+    if (MODE == MODE_JV || MODE == MODE_DJV) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const double e = ctl->eps_jv * G.scale[q];
+            cf[q] = e != 0.0 ? 1.0 / e : 0.0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int idx = threadIdx.x + k * NTHREADS;
+        const int xl = idx % TX, zl = idx / TX;
+        const int gx = x0 + xl, gz = z0 + zl;
+        if (gx >= G.nx || gz >= G.nz) continue;
+        const int c = (zl + HALO) * TX + xl;
+        const int ca = (zl + R) * TX + xl;                 // z arm at the output point
+        const T* bw = Bf + 2 * SP;
+        const T* aw = Af + 2 * SP;
+        const T dbpz = dd(Bf + 4 * SP, c, TX, iz);
+        const T dapz = TWO ? dd(Af + 4 * SP, c, TX, iz) : T(0);
+        T dF[5];
 #pragma unroll
         for (int fl = 0; fl < 5; ++fl) {
-            const T* Ph = s1 + fl * B::PL;
-            T dxp, dyp, dzp;
+            const T* B = Bf + fl * SP;
+            const T* A = Af + fl * SP;
+            T fj = T(0);
+#pragma unroll
+            for (int l = 1; l <= 2; ++l) {
+                const T cl = l == 1 ? T(2.0 / 3.0) : T(-1.0 / 12.0);
+                const int ip = c + l * TX, im = c - l * TX;
+                if (TWO)
+                    fj += cl * ((aw[ip] * B[ip] + bw[ip] * (A[ip] + B[ip])) - (aw[im] * B[im] + bw[im] * (A[im] + B[im])));
+                else
+                    fj += cl * (bw[ip] * B[ip] - bw[im] * B[im]);
+            }
+            const T flux = fj * iz;
+            T daz, dbz;
             if (fl < 4) {
-                const T* gf = g + fl * B::AS;
-                dxp = gf[cx]; dyp = gf[cy]; dzp = gf[cz];
+                dbz = ga[fl * AN + ca];
+                daz = TWO ? ga[(4 + fl) * AN + ca] : T(0);
             } else {
-                dxp = px; dyp = py; dzp = pz;
+                dbz = dbpz;
+                daz = dapz;
             }
-            const T conv = T(0.5) * (ddp(U, Ph, c, 1, ix_) + ddp(Vv, Ph, c, B::SX, iy_) + ddp(W, Ph, c, B::SXY, iz_)) +
-                           T(0.5) * (uc * dxp + vc * dyp + wc * dzp);
-            T dif = T(0);
+            const T adv = TWO ? (aw[c] * dbz + bw[c] * (daz + dbz)) : bw[c] * dbz;
+            dF[fl] = -(T(0.5) * flux + T(0.5) * adv);
             if (fl < 4) {
-                const T* gf = g + fl * B::AS;
-                if (SMAG == 2) {
-                    const T* kf = fl == 3 ? kh : nu;
-                    dif = ddp(kf, gf, cx, 1, ix_) + ddp(kf, gf, cy, TX, iy_) + ddp(kf, gf, cz, TX * TY, iz_);
-                } else if (SMAG) {
-                    dif = ddp(nu, gf, cx, 1, ix_) + ddp(nu, gf, cy, TX, iy_) + ddp(nu, gf, cz, TX * TY, iz_);
-                    if (fl == 3) dif *= iPr;
-                } else {
-                    dif = (fl == 3 ? KHc : KMc) * (dd(gf, cx, 1, ix_) + dd(gf, cy, TX, iy_) + dd(gf, cz, TX * TY, iz_));
+                const T* gb = ga + fl * AN;
+                const T* gA = ga + (4 + fl) * AN;
+                T sj = T(0);
+#pragma unroll
+                for (int l = 1; l <= 2; ++l) {
+                    const T cl = l == 1 ? T(2.0 / 3.0) : T(-1.0 / 12.0);
+                    const int p1 = ca + l * TX, m1 = ca - l * TX;
+                    if (SMAG) {
+                        T kp, dkp, km, dkm;
+                        kpair<T, SMAG>(G, TWO ? ks[AN + p1] : T(0), ks[p1], true, fl == 3, kp, dkp);
+                        kpair<T, SMAG>(G, TWO ? ks[AN + m1] : T(0), ks[m1], true, fl == 3, km, dkm);
+                        if (TWO)
+                            sj += cl * ((kp * gb[p1] + dkp * (gA[p1] + gb[p1])) - (km * gb[m1] + dkm * (gA[m1] + gb[m1])));
+                        else
+                            sj += cl * (dkp * gb[p1] - dkm * gb[m1]);
+                    } else {
+                        sj += cl * (gb[p1] - gb[m1]);
+                    }
                 }
+                T dif = sj * iz;
+                if (SMAG == 1) {
+                    if (fl == 3) dif *= T(G.inv_Pr);
+                } else if (!SMAG) {
+                    dif *= T(fl == 3 ? G.K_H : G.K_M);
+                }
+                dF[fl] += dif;
             }
-            Fv[fl] = -conv + dif;
         }
-        const T div = g[cx] + g[B::AS + cy] + g[2 * B::AS + cz];
-        Fv[0] += -th0 * px;
-        Fv[1] += -th0 * py;
-        Fv[2] += -th0 * pz + T(G.g) * s1[3 * B::PL + c] / th0;
-        Fv[3] += -T(G.beta) * wc;
-        if (G.heat != nullptr && gz == 0) Fv[3] += T(G.heat[(size_t)gy * G.nx + gx] * G.heat_coef);
-        Fv[4] += -T(G.gamma_p) * (T(G.pbar) + P[c]) * div;
-        const size_t off = ((size_t)gz * G.ny + gy) * G.nx + gx;
+        dF[2] += -th0 * dbpz;
+        {
+            const T pa = TWO ? Af[4 * SP + c] : T(0), pb = Bf[4 * SP + c];
+            T t = (T(G.pbar) + pa + pb) * ga[2 * AN + ca];
+            if (TWO) t += pb * ga[6 * AN + ca];
+            dF[4] += -T(G.gamma_p) * t;
+        }
+        const size_t off = (size_t)gz * G.ny * G.nx + row + gx;
 #pragma unroll
         for (int fl = 0; fl < 5; ++fl) {
             const size_t o = (size_t)fl * G.npt + off;
-            if (MODE == MODE_F) {
-                out[o] = Fv[fl];
+            const T Fv = P[o] + dF[fl];
+            if (MODE == MODE_DJV) {
+                out[o] = T(G.two_over_dt) * v[o] - Fv * T(cf[fl]);
+            } else if (MODE == MODE_F) {
+                out[o] = Fv;
             } else if (MODE == MODE_RHS) {
-                out[o] = T(G.two_over_dt * (double)u[o] + (double)Fv[fl]);
+                out[o] = T(G.two_over_dt * (double)u[o] + (double)Fv);
             } else if (MODE == MODE_RHSRES) {
                 // at u = u^n the residual 2u/dt - F(u) - f with f = 2u/dt + F(u) is -2 F(u)
                 const double uo = (double)u[o];
-                const double Fd = (double)Fv[fl];
+                const double Fd = (double)Fv;
                 out[o] = T(G.two_over_dt * uo + Fd);
                 const double Rv = -2.0 * Fd;
                 out2[o] = T(Rv);
@@ -324,16 +642,15 @@ stencil3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
                 acc[1] += us * us;
             } else if (MODE == MODE_RES) {
                 const double uo = (double)u[o];
-                const double Rv = G.two_over_dt * uo - (double)Fv[fl] - f[o];
+                const double Rv = G.two_over_dt * uo - (double)Fv - f[o];
                 out[o] = T(Rv);
-                if (out2 != nullptr) out2[o] = Fv[fl];
+                if (out2 != nullptr) out2[o] = Fv;
                 const double rs = Rv * G.inv_scale[fl], us = uo * G.inv_scale[fl];
                 acc[0] += rs * rs;
                 acc[1] += us * us;
-            } else {
-                const double vh = (double)v[o];
-                const double diff = (double)Fv[fl] - (double)Fu[o];
-                out[o] = T(G.two_over_dt * vh - diff * cfs[fl]);
+            } else {   // MODE_JV: plain forward difference against F(u)
+                const double diff = (double)Fv - (double)Fu[o];
+                out[o] = T(G.two_over_dt * (double)v[o] - diff * cf[fl]);
             }
         }
     }
@@ -354,321 +671,122 @@ stencil3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __re
 }
 
 // ============================================================================
-// Mixed-path Jv in difference form (a = u, b = eps V, a' = a + b): every term
-// of F(a') - F(a) expanded as a difference, as in the 2-D kernel.
+// Field-block Chebyshev sweep (same recurrence as the 2-D kernel, Section 2.5.2)
+// for a PX x PY tile of one plane and one field: blockIdx.z = z * 5 + field.
+// The iterate is staged with a halo of 4 in x and y, the eddy coefficient on
+// the x / y arms; the z part D_z(K D_z x) is formed from the point's own
+// column (iterate at z-4 .. z+4 with mirror ghosts, coefficient at z-2 .. z+2
+// mirrored even), read directly.  p (field 4) is written by the last sweep.
 // ============================================================================
-template <typename T, int SMAG, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(NTHREADS)
-jv_diff3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict__ out, Ctl* ctl,
-          int check_done) {
-    using B = Box<TX, TY, TZ>;
-    if (check_done && ctl->done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sa = reinterpret_cast<T*>(smem_raw);        // [5][PL]
-    T* sb = sa + 5 * B::PL;                         // [5][PL]
-    T* ga = sb + 5 * B::PL;                         // [4][AS]
-    T* gb = ga + 4 * B::AS;                         // [4][AS]
-    T* Ka = gb + 4 * B::AS;                         // [AS]
-    T* dK = Ka + B::AS;                             // [AS]
-    T* Kh = dK + B::AS;                             // [AS] Deardorff: heat coefficient and its difference
-    T* dKh = Kh + B::AS;                            // [AS]
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
-    const T ix_ = T(G.inv_dx), iy_ = T(G.inv_dy), iz_ = T(G.inv_dz);
-    __shared__ T cfs[5];
-    __shared__ T evs[5];
-    if (threadIdx.x < 5) {
-        const double e = ctl->eps_jv * G.scale[threadIdx.x];
-        evs[threadIdx.x] = T(e);
-        cfs[threadIdx.x] = T(e != 0.0 ? 1.0 / e : 0.0);
-    }
-    __syncthreads();
-    T ev[5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) ev[q] = evs[q];
-    load_box<T, 0, 5, TX, TY, TZ>(sa, u, v, ev, G, x0, y0, z0, 0);
-    load_box<T, 2, 5, TX, TY, TZ>(sb, u, v, ev, G, x0, y0, z0, 0);
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        arms<T, TX, TY, TZ>(sa + q * B::PL, ga + q * B::AS, ix_, iy_, iz_);
-        arms<T, TX, TY, TZ>(sb + q * B::PL, gb + q * B::AS, ix_, iy_, iz_);
-    }
-    if (SMAG) {
-        const T cs2 = T(G.cs2);
-        for (int idx = threadIdx.x; idx < B::AS; idx += blockDim.x) {
-            int bx, by, bz;
-            bool zarm;
-            arm_point<TX, TY, TZ>(idx, bx, by, bz, zarm);
-            T ka = T(0), dk = T(0), kh_ = T(0), dkh_ = T(0);
-            const int bzz = zarm ? eddy_box_row(bz, z0, G.nz) : bz;
-            if (bzz >= 0) {
-                const int c = B::b(bx, by, bzz);
-                T gA[3][3], gB[3][3];
-                grad3<T, B::SX, B::SXY>(sa, sa + B::PL, sa + 2 * B::PL, c, ix_, iy_, iz_, gA);
-                grad3<T, B::SX, B::SXY>(sb, sb + B::PL, sb + 2 * B::PL, c, ix_, iy_, iz_, gB);
-                T ssa = T(0), dss = T(0);
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        const T sA = T(0.5) * (gA[i][j] + gA[j][i]);
-                        const T sB = T(0.5) * (gB[i][j] + gB[j][i]);
-                        ssa += sA * sA;
-                        dss += (T(2) * sA + sB) * sB;       // S':S' - S:S
-                    }
-                const T na = sqrt(T(2) * ssa);
-                const T tp = T(2) * (ssa + dss);
-                const T np = sqrt(tp > T(0) ? tp : T(0));
-                const T den = na + np;
-                const T ds = den > T(0) ? T(2) * dss / den : T(0);     // s' - s, cancellation-free
-                if (SMAG == 2) {
-                    // Deardorff: the arm's direction picks the coefficient; heat by its difference
-                    // form g(s') - g(s) = ds (1 + a l') + a s (l' - l) (l' - l = c_l ds below the cap)
-                    ka = dd3_coef(na, zarm, false, G);
-                    dk = dd3_coef(ds, zarm, false, G);
-                    const T c = T(zarm ? G.dd_cM : G.dd_cm), a = T(zarm ? G.dd_az : G.dd_ah);
-                    T la = T(G.dd_delta), lp = T(G.dd_delta), dl = T(0);
-                    if (G.dd_cl >= 0.0) {
-                        const T ta = T(G.dd_cl) * na, tq = T(G.dd_cl) * np;
-                        la = ta < T(G.dd_delta) ? ta : T(G.dd_delta);
-                        lp = tq < T(G.dd_delta) ? tq : T(G.dd_delta);
-                        if (ta < T(G.dd_delta) && tq < T(G.dd_delta)) dl = T(G.dd_cl) * ds;
-                        else if (ta < T(G.dd_delta) || tq < T(G.dd_delta)) dl = lp - la;
-                    }
-                    kh_ = c * (na * (T(1) + a * la));
-                    dkh_ = c * (ds * (T(1) + a * lp) + a * na * dl);
-                } else {
-                    ka = cs2 * na;
-                    dk = cs2 * ds;
-                }
-            }
-            Ka[idx] = ka;
-            dK[idx] = dk;
-            if (SMAG == 2) {
-                Kh[idx] = kh_;
-                dKh[idx] = dkh_;
-            }
-        }
-    }
-    __syncthreads();
-    const T KMc = T(G.K_M), KHc = T(G.K_H), iPr = T(G.inv_Pr), th0 = T(G.theta0);
-    const T* AU[3] = {sa, sa + B::PL, sa + 2 * B::PL};
-    const T* BU[3] = {sb, sb + B::PL, sb + 2 * B::PL};
-    const int sts[3] = {1, B::SX, B::SXY};
-    const T ihs[3] = {ix_, iy_, iz_};
-    for (int idx = threadIdx.x; idx < TX * TY * TZ; idx += blockDim.x) {
-        const int tx = idx % TX, r1 = idx / TX;
-        const int ty = r1 % TY, tz = r1 / TY;
-        const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-        if (gx >= G.nx || gy >= G.ny || gz >= G.nz) continue;
-        const int c = B::b(tx + HALO, ty + HALO, tz + HALO);
-        const int ca[3] = {B::ax(tx + R, ty, tz), B::ay(tx, ty + R, tz), B::az(tx, ty, tz + R)};
-        const int ast[3] = {1, TX, TX * TY};       // arm strides along x, y, z
-        T dapc[3], dbpc[3];
-        const T* AP = sa + 4 * B::PL;
-        const T* BP = sb + 4 * B::PL;
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            dapc[j] = dd(AP, c, sts[j], ihs[j]);
-            dbpc[j] = dd(BP, c, sts[j], ihs[j]);
-        }
-        T dF[5];
-#pragma unroll
-        for (int fl = 0; fl < 5; ++fl) {
-            const T* A = sa + fl * B::PL;
-            const T* Bf = sb + fl * B::PL;
-            T flux = T(0), adv = T(0);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const T* aj = AU[j];
-                const T* bj = BU[j];
-                const int st = sts[j];
-                T fj = T(0);
-#pragma unroll
-                for (int l = 1; l <= 2; ++l) {
-                    const T cl = l == 1 ? T(2.0 / 3.0) : T(-1.0 / 12.0);
-                    const int ip = c + l * st, im = c - l * st;
-                    fj += cl * ((aj[ip] * Bf[ip] + bj[ip] * (A[ip] + Bf[ip])) -
-                                (aj[im] * Bf[im] + bj[im] * (A[im] + Bf[im])));
-                }
-                flux += fj * ihs[j];
-                T daj, dbj;
-                if (fl < 4) { daj = ga[fl * B::AS + ca[j]]; dbj = gb[fl * B::AS + ca[j]]; }
-                else { daj = dapc[j]; dbj = dbpc[j]; }
-                adv += aj[c] * dbj + bj[c] * (daj + dbj);
-            }
-            dF[fl] = -(T(0.5) * flux + T(0.5) * adv);
-            if (fl < 4) {
-                const T* gaf = ga + fl * B::AS;
-                const T* gbf = gb + fl * B::AS;
-                T dif = T(0);
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const int q = ca[j], st = ast[j];
-                    T sj = T(0);
-#pragma unroll
-                    for (int l = 1; l <= 2; ++l) {
-                        const T cl = l == 1 ? T(2.0 / 3.0) : T(-1.0 / 12.0);
-                        const int p1 = q + l * st, m1 = q - l * st;
-                        if (SMAG) {
-                            const T* K1 = (SMAG == 2 && fl == 3) ? Kh : Ka;
-                            const T* d1 = (SMAG == 2 && fl == 3) ? dKh : dK;
-                            sj += cl * ((K1[p1] * gbf[p1] + d1[p1] * (gaf[p1] + gbf[p1])) -
-                                        (K1[m1] * gbf[m1] + d1[m1] * (gaf[m1] + gbf[m1])));
-                        } else {
-                            sj += cl * (gbf[p1] - gbf[m1]);
-                        }
-                    }
-                    dif += sj * ihs[j];
-                }
-                if (SMAG == 1) { if (fl == 3) dif *= iPr; } else if (!SMAG) dif *= (fl == 3 ? KHc : KMc);
-                dF[fl] += dif;
-            }
-        }
-        dF[0] += -th0 * dbpc[0];
-        dF[1] += -th0 * dbpc[1];
-        dF[2] += -th0 * dbpc[2] + T(G.g) * sb[3 * B::PL + c] / th0;
-        dF[3] += -T(G.beta) * sb[2 * B::PL + c];
-        const T diva = ga[ca[0]] + ga[B::AS + ca[1]] + ga[2 * B::AS + ca[2]];
-        const T divb = gb[ca[0]] + gb[B::AS + ca[1]] + gb[2 * B::AS + ca[2]];
-        dF[4] += -T(G.gamma_p) * ((T(G.pbar) + AP[c] + BP[c]) * divb + BP[c] * diva);
-        const size_t off = ((size_t)gz * G.ny + gy) * G.nx + gx;
-#pragma unroll
-        for (int fl = 0; fl < 5; ++fl) {
-            const size_t o = (size_t)fl * G.npt + off;
-            out[o] = T(G.two_over_dt) * v[o] - dF[fl] * cfs[fl];
-        }
-    }
-}
-
-// ============================================================================
-// Smagorinsky eddy field at every point (preconditioner input) and its maximum
-// ============================================================================
-template <typename T>
-__global__ void __launch_bounds__(NTHREADS)
-eddy3d(Geo G, const T* __restrict__ u, T* __restrict__ nu, double* part, Ctl* ctl) {
-    T mxT = T(0);
-    const T ih[3] = {T(G.inv_dx), T(G.inv_dy), T(G.inv_dz)};
-    const T cs2 = G.sgs == 2 ? T(1) : T(G.cs2);     // Deardorff: the strain s itself
-    const int nxy = G.nx * G.ny;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < G.npt; p += gridDim.x * blockDim.x) {
-        const int z = p / nxy, rem = p - z * nxy;
-        const int y = rem / G.nx, x = rem - y * G.nx;
-        T gr[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const T* C = u + (size_t)i * G.npt;
-            T dxv = T(0), dyv = T(0), dzv = T(0);
-#pragma unroll
-            for (int l = 1; l <= 2; ++l) {
-                const T cl = l == 1 ? T(2.0 / 3.0) : T(-1.0 / 12.0);
-                dxv += cl * (C[(size_t)z * nxy + y * G.nx + wrap(x + l, G.nx)] -
-                             C[(size_t)z * nxy + y * G.nx + wrap(x - l, G.nx)]);
-                dyv += cl * (C[(size_t)z * nxy + wrap(y + l, G.ny) * G.nx + x] -
-                             C[(size_t)z * nxy + wrap(y - l, G.ny) * G.nx + x]);
-                int sp_, sm_;
-                const int zp = mirror(z + l, G.nz, sp_), zm = mirror(z - l, G.nz, sm_);
-                const T gp = sp_ == 2 ? T(G.pt[i]) : T(1), gm = sm_ == 1 ? T(G.pb[i]) : T(1);
-                dzv += cl * (gp * C[(size_t)zp * nxy + y * G.nx + x] - gm * C[(size_t)zm * nxy + y * G.nx + x]);
-            }
-            gr[i][0] = dxv * ih[0];
-            gr[i][1] = dyv * ih[1];
-            gr[i][2] = dzv * ih[2];
-        }
-        const T val = cs2 * sqrt(T(2) * strain_sq(gr));
-        nu[p] = val;
-        mxT = val > mxT ? val : mxT;
-    }
-    double mx[1] = {(double)mxT};
-    block_partials_max<1>(mx, 1, part, gridDim.x, blockIdx.x);
-    if (arrive_last(&ctl->counter[CNT_EDDY], gridDim.x)) {
-        __shared__ double tot[1];
-        final_maxes(part, gridDim.x, 1, tot);
-        if (threadIdx.x == 0) ctl->kmax = tot[0];
-    }
-}
-
-// ============================================================================
-// Field-block Chebyshev sweep (same recurrence as the 2-D kernel, Section 2.5.2):
-// one CTA = one field of one tile; p (field 4) is written by the last sweep.
-// ============================================================================
-template <typename T, int SMAG, int FIRST, int LAST, int TX, int TY, int TZ>
+template <typename T, int SMAG, int FIRST, int LAST>
 __global__ void __launch_bounds__(NTHREADS)
 cheb3d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T* __restrict__ din,
        T* __restrict__ zout, T* __restrict__ dout, const T* __restrict__ nu, double* part, Ctl* ctl,
        int check_done) {
-    using B = Box<TX, TY, TZ>;
+    constexpr int SX = PX + 2 * HALO, SY = PY + 2 * HALO, SP = SX * SY;
+    constexpr int AXN = (PX + 2 * R) * PY, AYN = PX * (PY + 2 * R), AN = AXN + AYN;
     if (check_done && ctl->done) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* zs = reinterpret_cast<T*>(smem_raw);      // [PL]
-    T* g = zs + B::PL;                              // [AS] derivative arms of x_k
-    T* kk = g + B::AS;                              // [AS] eddy coefficient on the arms
+    __shared__ T xs[SP];
+    __shared__ T g[AN];        // D_x on the x arms, D_y on the y arms
+    __shared__ T kk[AN];       // eddy coefficient on the arms
     const int fld = blockIdx.z % 5;
-    const int zt = blockIdx.z / 5;                  // z tile
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = zt * TZ;
+    const int gz = blockIdx.z / 5;
+    const int x0 = blockIdx.x * PX, y0 = blockIdx.y * PY;
     const T ith = T(ctl->cheb[fld][k][0]);
     const T a1 = T(ctl->cheb[fld][k][1]);
     const T a2 = T(ctl->cheb[fld][k][2]);
     const size_t foff = (size_t)fld * G.npt;
+    const size_t nxy = (size_t)G.ny * G.nx;
+    const int tx = threadIdx.x % PX, ty = threadIdx.x / PX;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool inside = gx < G.nx && gy < G.ny;
     T acc[1] = {T(0)};
     if (fld == 4) {
-        if (LAST) {
-            for (int idx = threadIdx.x; idx < TX * TY * TZ; idx += blockDim.x) {
-                const int tx = idx % TX, r1 = idx / TX;
-                const int ty = r1 % TY, tz = r1 / TY;
-                const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-                if (gx >= G.nx || gy >= G.ny || gz >= G.nz) continue;
-                const size_t o = foff + ((size_t)gz * G.ny + gy) * G.nx + gx;
-                const T zv = r[o] * ith;
-                zout[o] = zv;
-                acc[0] += zv * zv;
-            }
+        if (LAST && inside) {
+            const size_t o = foff + (size_t)gz * nxy + (size_t)gy * G.nx + gx;
+            const T zv = r[o] * ith;
+            zout[o] = zv;
+            acc[0] += zv * zv;
         }
     } else {
-        T sc[5] = {T(0), T(0), T(0), T(0), T(0)};
-        if (FIRST) {
-            sc[fld] = ith;
-            load_box<T, 2, 1, TX, TY, TZ>(zs, nullptr, r, sc, G, x0, y0, z0, fld);
-        } else {
-            load_box<T, 0, 1, TX, TY, TZ>(zs, zin, nullptr, sc, G, x0, y0, z0, fld);
+        // x_k: r / theta (first sweep) or the previous iterate
+        const T* src = FIRST ? r : zin;
+        const T sc = FIRST ? ith : T(1);
+        for (int idx = threadIdx.x; idx < SP; idx += NTHREADS) {
+            const int ixl = idx % SX, iyl = idx / SX;
+            const size_t o = foff + (size_t)gz * nxy + (size_t)wrap(y0 + iyl - HALO, G.ny) * G.nx +
+                             wrap(x0 + ixl - HALO, G.nx);
+            xs[idx] = sc * src[o];
         }
+        const T kscale = fld == 3 ? T(G.inv_Pr) : T(1);
         if (SMAG) {
-            const T kscale = fld == 3 ? T(G.inv_Pr) : T(1);
-            for (int idx = threadIdx.x; idx < B::AS; idx += blockDim.x) {
-                int bx, by, bz;
-                bool zarm;
-                arm_point<TX, TY, TZ>(idx, bx, by, bz, zarm);
-                int side;
-                const int sz = mirror(z0 + bz - HALO, G.nz, side);    // even mirror of nu
-                const int sy = wrap(y0 + by - HALO, G.ny), sx = wrap(x0 + bx - HALO, G.nx);
-                const T nv = (sz >= 0 && sz < G.nz) ? nu[((size_t)sz * G.ny + sy) * G.nx + sx] : T(0);
+            for (int idx = threadIdx.x; idx < AN; idx += NTHREADS) {
+                int qx, qy;
+                if (idx < AXN) { qx = idx % (PX + 2 * R) - R; qy = idx / (PX + 2 * R); }
+                else { const int j = idx - AXN; qx = j % PX; qy = j / PX - R; }
+                const T nv = nu[(size_t)gz * nxy + (size_t)wrap(y0 + qy, G.ny) * G.nx + wrap(x0 + qx, G.nx)];
                 // Deardorff: nu holds the strain and the arm's direction picks the coefficient
-                kk[idx] = SMAG == 2 ? dd3_coef(nv, zarm, fld == 3, G) : nv * kscale;
+                kk[idx] = SMAG == 2 ? dd3_coef(nv, false, fld == 3, G) : nv * kscale;
             }
         }
         __syncthreads();
-        arms<T, TX, TY, TZ>(zs, g, T(G.inv_dx), T(G.inv_dy), T(G.inv_dz));
-        __syncthreads();
-        const T Kc = T(fld == 3 ? G.K_H : G.K_M);
-        const T tdt = T(G.two_over_dt);
-        const T ihs[3] = {T(G.inv_dx), T(G.inv_dy), T(G.inv_dz)};
-        for (int idx = threadIdx.x; idx < TX * TY * TZ; idx += blockDim.x) {
-            const int tx = idx % TX, r1 = idx / TX;
-            const int ty = r1 % TY, tz = r1 / TY;
-            const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
-            if (gx >= G.nx || gy >= G.ny || gz >= G.nz) continue;
-            const int ca[3] = {B::ax(tx + R, ty, tz), B::ay(tx, ty + R, tz), B::az(tx, ty, tz + R)};
-            const int ast[3] = {1, TX, TX * TY};
-            T dif = T(0);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                if (SMAG) dif += ddp(kk, g, ca[j], ast[j], ihs[j]);
-                else dif += Kc * dd(g, ca[j], ast[j], ihs[j]);
+        for (int idx = threadIdx.x; idx < AN; idx += NTHREADS) {
+            if (idx < AXN) {
+                const int qx = idx % (PX + 2 * R), qy = idx / (PX + 2 * R);
+                g[idx] = dd(xs, (qy + HALO) * SX + qx + R, 1, T(G.inv_dx));
+            } else {
+                const int j = idx - AXN;
+                const int qx = j % PX, qy = j / PX;
+                g[idx] = dd(xs, (qy + R) * SX + qx + HALO, SX, T(G.inv_dy));
             }
-            const T xk = zs[B::b(tx + HALO, ty + HALO, tz + HALO)];
-            const size_t o = foff + ((size_t)gz * G.ny + gy) * G.nx + gx;
+        }
+        __syncthreads();
+        if (inside) {
+            const T iz = T(G.inv_dz);
+            // the point's column: x_k at z-4 .. z+4 (mirror ghosts with the field's parity)
+            T col[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                if (q == 4) {
+                    col[q] = xs[(ty + HALO) * SX + tx + HALO];
+                    continue;
+                }
+                int side;
+                const int sz = mirror(gz + q - 4, G.nz, side);
+                const T sg = side == 1 ? T(G.pb[fld]) : (side == 2 ? T(G.pt[fld]) : T(1));
+                col[q] = sg * sc * src[foff + (size_t)sz * nxy + (size_t)gy * G.nx + gx];
+            }
+            // D_z x on the z arms z-2, z-1, z+1, z+2 and the coefficient there
+            T gzv[5], kz[5];
+#pragma unroll
+            for (int l = -2; l <= 2; ++l) {
+                if (l == 0) { gzv[2] = T(0); kz[2] = T(0); continue; }
+                const int q = l + 4;
+                gzv[l + 2] = d5(col[q - 2], col[q - 1], col[q + 1], col[q + 2], iz);
+                if (SMAG) {
+                    const int sz = eddy_row(gz + l, G.nz);
+                    const T nv = sz >= 0 ? nu[(size_t)sz * nxy + (size_t)gy * G.nx + gx] : T(0);
+                    kz[l + 2] = SMAG == 2 ? dd3_coef(nv, true, fld == 3, G) : nv * kscale;
+                } else {
+                    kz[l + 2] = T(0);
+                }
+            }
+            const int cax = ty * (PX + 2 * R) + tx + R;
+            const int cay = AXN + (ty + R) * PX + tx;
+            const T Kc = T(fld == 3 ? G.K_H : G.K_M);
+            T dif;
+            if (SMAG) {
+                dif = ddp(kk, g, cax, 1, T(G.inv_dx)) + ddp(kk, g, cay, PX, T(G.inv_dy)) +
+                      (T(2.0 / 3.0) * (kz[3] * gzv[3] - kz[1] * gzv[1]) -
+                       T(1.0 / 12.0) * (kz[4] * gzv[4] - kz[0] * gzv[0])) * iz;
+            } else {
+                dif = Kc * dd(g, cax, 1, T(G.inv_dx)) + Kc * dd(g, cay, PX, T(G.inv_dy)) +
+                      Kc * d5(gzv[0], gzv[1], gzv[3], gzv[4], iz);
+            }
+            const T xk = col[4];
+            const size_t o = foff + (size_t)gz * nxy + (size_t)gy * G.nx + gx;
             const T rv = r[o];
-            const T res = rv - (tdt * xk - dif);
+            const T res = rv - (T(G.two_over_dt) * xk - dif);
             const T dprev = FIRST ? rv * ith : din[o];
             const T dk = a1 * dprev + a2 * res;
             const T xn = xk + dk;
@@ -745,22 +863,86 @@ budgets3d(Geo G, const double* __restrict__ u, double dV, double dz, double lz, 
     }
 }
 
-// ------------------------------------------------------------------ tiles
-template <typename T> struct FTile;          // F / residual / plain Jv
-template <> struct FTile<float>  { static constexpr int TX = 16, TY = 8, TZ = 4; };
-template <> struct FTile<double> { static constexpr int TX = 8, TY = 8, TZ = 4; };
-template <typename T> struct DTile;          // difference-form Jv (two states staged)
-template <> struct DTile<float>  { static constexpr int TX = 8, TY = 8, TZ = 4; };
-template <> struct DTile<double> { static constexpr int TX = 4, TY = 4, TZ = 4; };
-template <typename T> struct CTile;          // Chebyshev sweep (one field)
-template <> struct CTile<float>  { static constexpr int TX = 16, TY = 8, TZ = 4; };
-template <> struct CTile<double> { static constexpr int TX = 16, TY = 8, TZ = 4; };
 
+// ------------------------------------------------------------------ launchers
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <typename T, int MODE>
+constexpr size_t plane_smem(int smag) {
+    constexpr int SP = (PX + 2 * HALO) * (PY + 2 * HALO);
+    constexpr int AN = (PX + 2 * R) * PY + PX * (PY + 2 * R);
+    constexpr int NS = Two<MODE>::v ? 2 : 1;
+    return sizeof(T) * ((size_t)NS * 5 * SP + (size_t)NS * 4 * AN + (smag ? (size_t)NS * AN : 0));
+}
+
+template <typename T, int MODE>
+constexpr size_t slab_smem(int smag) {
+    constexpr int TX = SlabT<T>::TX, TZ = SlabT<T>::TZ;
+    constexpr int SP = TX * (TZ + 2 * HALO), AN = TX * (TZ + 2 * R);
+    constexpr int NS = Two<MODE>::v ? 2 : 1;
+    return sizeof(T) * ((size_t)NS * 5 * SP + (size_t)NS * 4 * AN + (smag ? (size_t)NS * AN : 0));
+}
+
+static int stream_blocks3(size_t n) {
+    size_t b = (n + NTHREADS - 1) / NTHREADS;
+    return (int)(b < (size_t)MAX_STREAM_BLOCKS ? (b > 0 ? b : 1) : MAX_STREAM_BLOCKS);
+}
+
+// Scratch of the split passes inside G.s3 (7 npt values of T): the plane
+// pass's partial sums (5 npt), then the strain values s1, s0 (npt each).
+template <typename T>
+struct S3 {
+    T *P, *s1, *s0;
+    explicit S3(const Geo& G) {
+        T* b = reinterpret_cast<T*>(G.s3);
+        P = b;
+        s1 = b + 5 * (size_t)G.npt;
+        s0 = b + 6 * (size_t)G.npt;
+    }
+};
+
+template <typename T, int MODE, int SMAG>
+static cudaError_t launch_split(const Geo& G, const T* u, const T* v, const T* Fu, const double* f, T* out,
+                                T* out2, double* part, Ctl* ctl, int check_done, cudaStream_t s) {
+    if (G.s3 == nullptr) return cudaErrorInvalidValue;
+    S3<T> sc(G);
+    const size_t smp = plane_smem<T, MODE>(SMAG), sms = slab_smem<T, MODE>(SMAG);
+    static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
+    if (!configured) {
+        cudaError_t e = set_smem(plane3d<T, MODE, SMAG>, smp);
+        if (e != cudaSuccess) return e;
+        if ((e = set_smem(slab3d<T, MODE, SMAG>, sms)) != cudaSuccess) return e;
+        configured = true;
+    }
+    if (SMAG) {
+        dim3 gk((G.nx + KX - 1) / KX, (G.ny + KY - 1) / KY, G.nz);
+        strain3d<T, MODE, 0><<<gk, NTHREADS, 0, s>>>(G, u, v, sc.s0, sc.s1, part, ctl, check_done);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    dim3 gp((G.nx + PX - 1) / PX, (G.ny + PY - 1) / PY, G.nz);
+    plane3d<T, MODE, SMAG><<<gp, NTHREADS, smp, s>>>(G, u, v, sc.s0, sc.s1, sc.P, ctl, check_done);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    constexpr int TX = SlabT<T>::TX, TZ = SlabT<T>::TZ;
+    dim3 gs((G.nz + TZ - 1) / TZ, (G.nx + TX - 1) / TX, G.ny);
+    slab3d<T, MODE, SMAG><<<gs, NTHREADS, sms, s>>>(G, u, v, Fu, f, sc.s0, sc.s1, sc.P, out, out2, part, ctl,
+                                                     check_done);
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+static cudaError_t launch_split_m(const Geo& G, const T* u, const T* v, const T* Fu, const double* f, T* out,
+                                  T* out2, double* part, Ctl* ctl, int check_done, cudaStream_t s) {
+    if (G.sgs == 2) return launch_split<T, MODE, 2>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
+    return G.smag ? launch_split<T, MODE, 1>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s)
+                  : launch_split<T, MODE, 0>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
+}
+
+// ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // Acoustic Schur-complement preconditioner in 3-D (scaled units): the 2-D
 // construction with three velocity components,
@@ -900,94 +1082,59 @@ schur_back3d(Geo G, const T* __restrict__ r, T* __restrict__ z, double* part, Ct
     }
 }
 
-static int stream_blocks3(size_t n) {
-    size_t b = (n + NTHREADS - 1) / NTHREADS;
-    return (int)(b < (size_t)MAX_STREAM_BLOCKS ? (b > 0 ? b : 1) : MAX_STREAM_BLOCKS);
-}
-
 }  // namespace d3
 
-// ------------------------------------------------------------------ launchers
+// ------------------------------------------------------------------ entry points
 int stencil3d_part_blocks(const Geo& G) {
-    // largest reduction grid any 3-D kernel launches (Chebyshev: 5 field slices)
+    // largest reduction grid any 3-D kernel launches
     using namespace d3;
-    const int a = ((G.nx + 7) / 8) * ((G.ny + 7) / 8) * ((G.nz + 3) / 4);
-    const int c = ((G.nx + 15) / 16) * ((G.ny + 7) / 8) * ((G.nz + 3) / 4) * 5;
-    return a > c ? a : c;
+    const long long slab = (long long)((G.nz + SlabT<float>::TZ - 1) / SlabT<float>::TZ) *
+                           ((G.nx + SlabT<float>::TX - 1) / SlabT<float>::TX) * G.ny;
+    const long long slab64 = (long long)((G.nz + SlabT<double>::TZ - 1) / SlabT<double>::TZ) *
+                             ((G.nx + SlabT<double>::TX - 1) / SlabT<double>::TX) * G.ny;
+    const long long cheb = (long long)((G.nx + PX - 1) / PX) * ((G.ny + PY - 1) / PY) * G.nz * 5;
+    const long long strain = (long long)((G.nx + KX - 1) / KX) * ((G.ny + KY - 1) / KY) * G.nz;
+    long long m = slab > slab64 ? slab : slab64;
+    if (cheb > m) m = cheb;
+    if (strain > m) m = strain;
+    return (int)m;
 }
 
-template <typename T, int MODE, int SMAG>
-static cudaError_t launch_s3(const Geo& G, const T* u, const T* v, const T* Fu, const double* f, T* out,
-                             T* out2, double* part, Ctl* ctl, int check_done, cudaStream_t s) {
-    using namespace d3;
-    constexpr int TX = FTile<T>::TX, TY = FTile<T>::TY, TZ = FTile<T>::TZ;
-    using B = Box<TX, TY, TZ>;
-    const size_t sm = sizeof(T) * (5 * B::PL + (SMAG == 2 ? 6 : 5) * B::AS);
-    static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
-    if (!configured) {
-        cudaError_t e = set_smem(stencil3d<T, MODE, SMAG, TX, TY, TZ>, sm);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    dim3 grid((G.nx + TX - 1) / TX, (G.ny + TY - 1) / TY, (G.nz + TZ - 1) / TZ);
-    stencil3d<T, MODE, SMAG, TX, TY, TZ><<<grid, NTHREADS, sm, s>>>(G, u, v, Fu, f, out, out2, part, ctl, check_done);
-    return cudaGetLastError();
-}
+size_t stencil3d_scratch_bytes(const Geo& G) { return 7 * (size_t)G.npt * sizeof(double); }
 
 template <typename T>
 cudaError_t launch_stencil3d(int mode, const Geo& G, const T* u, const T* v, const T* Fu, const double* f,
                              T* out, T* out2, double* part, Ctl* ctl, int check_done, cudaStream_t s) {
-#define JF3(M)                                                                                         \
-    case M:                                                                                            \
-        return G.sgs == 2 ? launch_s3<T, M, 2>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s)   \
-             : G.smag     ? launch_s3<T, M, 1>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s)   \
-                          : launch_s3<T, M, 0>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
+    using namespace d3;
     switch (mode) {
-        JF3(d3::MODE_F)
-        JF3(d3::MODE_RHS)
-        JF3(d3::MODE_RES)
-        JF3(d3::MODE_JV)
-        JF3(d3::MODE_RHSRES)
+        case d3::MODE_F: return launch_split_m<T, d3::MODE_F>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
+        case d3::MODE_RHS: return launch_split_m<T, d3::MODE_RHS>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
+        case d3::MODE_RES: return launch_split_m<T, d3::MODE_RES>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
+        case d3::MODE_JV: return launch_split_m<T, d3::MODE_JV>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
+        case d3::MODE_RHSRES:
+            return launch_split_m<T, d3::MODE_RHSRES>(G, u, v, Fu, f, out, out2, part, ctl, check_done, s);
         default: return cudaErrorInvalidValue;
     }
-#undef JF3
 }
 template cudaError_t launch_stencil3d<float>(int, const Geo&, const float*, const float*, const float*,
                                              const double*, float*, float*, double*, Ctl*, int, cudaStream_t);
 template cudaError_t launch_stencil3d<double>(int, const Geo&, const double*, const double*, const double*,
                                               const double*, double*, double*, double*, Ctl*, int, cudaStream_t);
 
-template <typename T, int SMAG>
-static cudaError_t launch_jvd3(const Geo& G, const T* u, const T* v, T* out, Ctl* ctl, int check_done,
-                               cudaStream_t s) {
-    using namespace d3;
-    constexpr int TX = DTile<T>::TX, TY = DTile<T>::TY, TZ = DTile<T>::TZ;
-    using B = Box<TX, TY, TZ>;
-    const size_t sm = sizeof(T) * (10 * B::PL + (SMAG == 2 ? 12 : 10) * B::AS);
-    static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
-    if (!configured) {
-        cudaError_t e = set_smem(jv_diff3d<T, SMAG, TX, TY, TZ>, sm);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    dim3 grid((G.nx + TX - 1) / TX, (G.ny + TY - 1) / TY, (G.nz + TZ - 1) / TZ);
-    jv_diff3d<T, SMAG, TX, TY, TZ><<<grid, NTHREADS, sm, s>>>(G, u, v, out, ctl, check_done);
-    return cudaGetLastError();
-}
-
 template <typename T>
 cudaError_t launch_jv_diff3d(const Geo& G, const T* u, const T* v, T* out, Ctl* ctl, int check_done,
                              cudaStream_t s) {
-    if (G.sgs == 2) return launch_jvd3<T, 2>(G, u, v, out, ctl, check_done, s);
-    return G.smag ? launch_jvd3<T, 1>(G, u, v, out, ctl, check_done, s)
-                  : launch_jvd3<T, 0>(G, u, v, out, ctl, check_done, s);
+    using namespace d3;
+    return launch_split_m<T, d3::MODE_DJV>(G, u, v, nullptr, nullptr, out, nullptr, nullptr, ctl, check_done, s);
 }
 template cudaError_t launch_jv_diff3d<float>(const Geo&, const float*, const float*, float*, Ctl*, int, cudaStream_t);
 template cudaError_t launch_jv_diff3d<double>(const Geo&, const double*, const double*, double*, Ctl*, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_eddy3d(const Geo& G, const T* u, T* nu, double* part, Ctl* ctl, cudaStream_t s) {
-    d3::eddy3d<T><<<d3::stream_blocks3(G.npt), NTHREADS, 0, s>>>(G, u, nu, part, ctl);
+    using namespace d3;
+    dim3 gk((G.nx + KX - 1) / KX, (G.ny + KY - 1) / KY, G.nz);
+    strain3d<T, d3::MODE_F, 1><<<gk, NTHREADS, 0, s>>>(G, u, nullptr, nullptr, nu, part, ctl, 0);
     return cudaGetLastError();
 }
 template cudaError_t launch_eddy3d<float>(const Geo&, const float*, float*, double*, Ctl*, cudaStream_t);
@@ -998,20 +1145,7 @@ static cudaError_t launch_pc3(const Geo& G, int sweeps, const T* r, T* z, T* za,
                               const T* nu, double* part, Ctl* ctl, int check_done, cudaStream_t s,
                               long long* launches) {
     using namespace d3;
-    constexpr int TX = CTile<T>::TX, TY = CTile<T>::TY, TZ = CTile<T>::TZ;
-    using B = Box<TX, TY, TZ>;
-    const size_t sm = sizeof(T) * (B::PL + 2 * B::AS);
-    static std::atomic<bool> configured{false};   // set once; concurrent first calls are harmless
-    if (!configured) {
-        cudaError_t e;
-        if ((e = set_smem(cheb3d<T, SMAG, 1, 1, TX, TY, TZ>, sm)) != cudaSuccess) return e;
-        if ((e = set_smem(cheb3d<T, SMAG, 1, 0, TX, TY, TZ>, sm)) != cudaSuccess) return e;
-        if ((e = set_smem(cheb3d<T, SMAG, 0, 1, TX, TY, TZ>, sm)) != cudaSuccess) return e;
-        if ((e = set_smem(cheb3d<T, SMAG, 0, 0, TX, TY, TZ>, sm)) != cudaSuccess) return e;
-        configured = true;
-    }
-    const int ntz = (G.nz + TZ - 1) / TZ;
-    dim3 grid((G.nx + TX - 1) / TX, (G.ny + TY - 1) / TY, ntz * 5);
+    dim3 grid((G.nx + PX - 1) / PX, (G.ny + PY - 1) / PY, G.nz * 5);
     const T* zin = nullptr;
     const T* din = nullptr;
     T* zbuf[2] = {za, zb};
@@ -1021,13 +1155,13 @@ static cudaError_t launch_pc3(const Geo& G, int sweeps, const T* r, T* z, T* za,
         T* zo = last ? z : zbuf[k & 1];
         T* dO = dbuf[k & 1];
         if (first && last)
-            cheb3d<T, SMAG, 1, 1, TX, TY, TZ><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            cheb3d<T, SMAG, 1, 1><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else if (first)
-            cheb3d<T, SMAG, 1, 0, TX, TY, TZ><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            cheb3d<T, SMAG, 1, 0><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else if (last)
-            cheb3d<T, SMAG, 0, 1, TX, TY, TZ><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            cheb3d<T, SMAG, 0, 1><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         else
-            cheb3d<T, SMAG, 0, 0, TX, TY, TZ><<<grid, NTHREADS, sm, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
+            cheb3d<T, SMAG, 0, 0><<<grid, NTHREADS, 0, s>>>(G, k, r, zin, din, zo, dO, nu, part, ctl, check_done);
         if (launches) ++*launches;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -72,7 +72,8 @@ def setup(c, seed=5):
     return U, m, s
 
 
-GRIDS3 = [(16, 8, 8), (21, 13, 9)]          # one tile; ragged, several tiles in x, y, z
+# one tile; ragged; several plane tiles (32 x 8) in x and y and slab tiles (16 / 8 planes) in z, ragged
+GRIDS3 = [(16, 8, 8), (21, 13, 9), (40, 18, 21)]
 VARS3 = [dict(), dict(smag=True), dict(smag=True, bc=synth.NOSLIP, heat=True),
          dict(dear=True, bc=synth.NOSLIP, heat=True)]
 
@@ -101,10 +102,11 @@ def test_residual_parity_3d(grid, var):
     assert np.all(err < 1e-12), err
 
 
+@pytest.mark.parametrize("grid", GRIDS3[1:])
 @pytest.mark.parametrize("var", range(len(VARS3)))
 @pytest.mark.parametrize("prec", [synth.PREC_FP64, synth.PREC_MIXED])
-def test_jv_parity_3d(var, prec):
-    c = make3(21, 13, 9, prec=prec, **VARS3[var])
+def test_jv_parity_3d(grid, var, prec):
+    c = make3(*grid, prec=prec, **VARS3[var])
     U, m, s = setup(c)
     V = np.random.Generator(np.random.PCG64(17)).standard_normal(U.shape)
     V = m.unscale(m.scale(V) / np.linalg.norm(m.scale(V)))
@@ -121,11 +123,12 @@ def test_jv_parity_3d(var, prec):
         assert np.all(rel_per_field(got, ref) < 1e-4), rel_per_field(got, ref)
 
 
+@pytest.mark.parametrize("grid", GRIDS3[1:])
 @pytest.mark.parametrize("var", range(len(VARS3)))
 @pytest.mark.parametrize("prec", [synth.PREC_FP64, synth.PREC_MIXED])
 @pytest.mark.parametrize("sweeps", [1, 4])
-def test_precond_parity_3d(var, prec, sweeps):
-    c = make3(21, 13, 9, prec=prec, **VARS3[var])
+def test_precond_parity_3d(grid, var, prec, sweeps):
+    c = make3(*grid, prec=prec, **VARS3[var])
     c["opts"]["pc_sweeps"] = sweeps
     if not VARS3[var].get("smag"):
         c["sgs"]["K_M"], c["sgs"]["K_H"] = 5.0e3, 7.0e3
