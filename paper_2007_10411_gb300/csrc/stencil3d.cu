@@ -168,8 +168,13 @@ static_assert(PX * PY == NTHREADS && KX * KY == NTHREADS, "one output per thread
 // Strain pass: s = sqrt(2 S:S) of b (one-state modes) or, for the difference
 // form, sa = |S(a)| and ds = |S(a + b)| - |S(a)| = (S':S' - S:S) * 2 / (s + s')
 // at every point.  EDDY: the eddy field of u instead (nu = cs2 s, Deardorff:
-// s itself), with its maximum.
+// s itself), with its maximum.  One CTA marches up a KX x KY column of SZB
+// planes: each thread keeps its point's velocity components at z-2 .. z+2 in
+// registers (one new plane per step); the plane itself is staged with a halo
+// of r = 2 in x and y for the horizontal derivatives.
 // ============================================================================
+constexpr int SZB = 16;      // planes per CTA of the strain pass
+
 template <typename T, int MODE, int EDDY>
 __global__ void __launch_bounds__(NTHREADS)
 strain3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict__ s0, T* __restrict__ s1,
@@ -177,98 +182,121 @@ strain3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, T* __restrict_
     constexpr bool TWO = Two<MODE>::v;
     constexpr int SX = KX + 2 * R, SY = KY + 2 * R, SP = SX * SY;
     constexpr int NA = TWO ? 6 : 3;               // (b u, b v, b w) [, (a u, a v, a w)]
+    constexpr int XS = (SP + NTHREADS - 1) / NTHREADS;
     if ((MODE == MODE_JV || MODE == MODE_DJV) && check_done && ctl->done) return;
     __shared__ T st[NA][SP];
-    const int x0 = blockIdx.x * KX, y0 = blockIdx.y * KY, gz = blockIdx.z;
+    const int x0 = blockIdx.x * KX, y0 = blockIdx.y * KY;
+    const int z0 = blockIdx.z * SZB, z1 = min(z0 + SZB, G.nz);
     const T ix = T(G.inv_dx), iy = T(G.inv_dy), iz = T(G.inv_dz);
     T ev[3] = {T(0), T(0), T(0)};
     if (MODE == MODE_JV || MODE == MODE_DJV) {
 #pragma unroll
         for (int f = 0; f < 3; ++f) ev[f] = eps_field<T>(ctl, G, f);
     }
-    const size_t plane = (size_t)gz * G.ny * G.nx;
-    for (int idx = threadIdx.x; idx < SP; idx += NTHREADS) {
-        const int ixl = idx % SX, iyl = idx / SX;
-        const size_t o = plane + (size_t)wrap(y0 + iyl - R, G.ny) * G.nx + wrap(x0 + ixl - R, G.nx);
+    const size_t nxy = (size_t)G.ny * G.nx;
+    int xoff[XS];
 #pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            T a, b;
-            load_ab<T, MODE>(u, v, ev[f], (size_t)f * G.npt + o, a, b);
-            st[f][idx] = b;
-            if (TWO) st[3 + f][idx] = a;
-        }
+    for (int q = 0; q < XS; ++q) {
+        const int idx = threadIdx.x + q * NTHREADS;
+        xoff[q] = idx < SP ? wrap(y0 + idx / SX - R, G.ny) * G.nx + wrap(x0 + idx % SX - R, G.nx) : -1;
     }
-    __syncthreads();
     const int tx = threadIdx.x % KX, ty = threadIdx.x / KX;
     const int gx = x0 + tx, gy = y0 + ty;
-    T mx = T(0);
-    if (gx < G.nx && gy < G.ny) {
-        const int c = (ty + R) * SX + tx + R;
-        // z neighbours of the three components (mirror ghosts with their parity)
-        T zb[3][4], za[3][4];
+    const bool inside = gx < G.nx && gy < G.ny;
+    const size_t own = inside ? (size_t)gy * G.nx + gx : 0;
+    // the column's components at z-2 .. z+2 (mirror ghosts with each component's parity)
+    T wb[3][5], wa[3][5];
+    auto col = [&](int z, int f, T& a, T& b) {
+        int side;
+        const int sz = mirror(z, G.nz, side);
+        load_ab<T, MODE>(u, v, ev[f], (size_t)f * G.npt + (size_t)sz * nxy + own, a, b);
+        const T sg = side == 1 ? T(G.pb[f]) : (side == 2 ? T(G.pt[f]) : T(1));
+        a *= sg;
+        b *= sg;
+    };
+    if (inside) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int dz = k < 2 ? k - 2 : k - 1;        // -2, -1, +1, +2
-            int side;
-            const int sz = mirror(gz + dz, G.nz, side);
-            const size_t o = ((size_t)sz * G.ny + gy) * G.nx + gx;
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int f = 0; f < 3; ++f) col(z0 - 2 + q, f, wa[f][q], wb[f][q]);
+    }
+    T mx = T(0);
+    for (int z = z0; z < z1; ++z) {
+        const size_t pz = (size_t)z * nxy;
+#pragma unroll
+        for (int q = 0; q < XS; ++q) {
+            if (xoff[q] < 0) continue;
+            const size_t o = pz + xoff[q];
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
                 T a, b;
                 load_ab<T, MODE>(u, v, ev[f], (size_t)f * G.npt + o, a, b);
-                const T sg = side == 1 ? T(G.pb[f]) : (side == 2 ? T(G.pt[f]) : T(1));
-                zb[f][k] = sg * b;
-                za[f][k] = sg * a;
+                st[f][threadIdx.x + q * NTHREADS] = b;
+                if (TWO) st[3 + f][threadIdx.x + q * NTHREADS] = a;
             }
         }
-        T gB[3][3], gA[3][3];
+        __syncthreads();
+        if (inside) {
 #pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            gB[f][0] = dd(st[f], c, 1, ix);
-            gB[f][1] = dd(st[f], c, SX, iy);
-            gB[f][2] = d5(zb[f][0], zb[f][1], zb[f][2], zb[f][3], iz);
+            for (int f = 0; f < 3; ++f) col(z + 2, f, wa[f][4], wb[f][4]);
+            const int c = (ty + R) * SX + tx + R;
+            T gB[3][3], gA[3][3];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                gB[f][0] = dd(st[f], c, 1, ix);
+                gB[f][1] = dd(st[f], c, SX, iy);
+                gB[f][2] = d5(wb[f][0], wb[f][1], wb[f][3], wb[f][4], iz);
+                if (TWO) {
+                    gA[f][0] = dd(st[3 + f], c, 1, ix);
+                    gA[f][1] = dd(st[3 + f], c, SX, iy);
+                    gA[f][2] = d5(wa[f][0], wa[f][1], wa[f][3], wa[f][4], iz);
+                }
+            }
+            const size_t p = pz + own;
             if (TWO) {
-                gA[f][0] = dd(st[3 + f], c, 1, ix);
-                gA[f][1] = dd(st[3 + f], c, SX, iy);
-                gA[f][2] = d5(za[f][0], za[f][1], za[f][2], za[f][3], iz);
-            }
-        }
-        const size_t p = plane + (size_t)gy * G.nx + gx;
-        if (TWO) {
-            T ssa = T(0), dss = T(0);
+                T ssa = T(0), dss = T(0);
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+                for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const T sA = T(0.5) * (gA[i][j] + gA[j][i]);
-                    const T sB = T(0.5) * (gB[i][j] + gB[j][i]);
-                    ssa += sA * sA;
-                    dss += (T(2) * sA + sB) * sB;       // S':S' - S:S
-                }
-            const T na = sqrt(T(2) * ssa);
-            const T tp = T(2) * (ssa + dss);
-            const T np = sqrt(tp > T(0) ? tp : T(0));
-            const T den = na + np;
-            s0[p] = na;
-            s1[p] = den > T(0) ? T(2) * dss / den : T(0);
-        } else {
-            T ss = T(0);
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const T sB = T(0.5) * (gB[i][j] + gB[j][i]);
-                    ss += sB * sB;
-                }
-            const T sv = sqrt(T(2) * ss);
-            if (EDDY) {
-                const T val = (G.sgs == 2 ? T(1) : T(G.cs2)) * sv;
-                s1[p] = val;
-                mx = val;
+                    for (int j = 0; j < 3; ++j) {
+                        const T sA = T(0.5) * (gA[i][j] + gA[j][i]);
+                        const T sB = T(0.5) * (gB[i][j] + gB[j][i]);
+                        ssa += sA * sA;
+                        dss += (T(2) * sA + sB) * sB;       // S':S' - S:S
+                    }
+                const T na = sqrt(T(2) * ssa);
+                const T tp = T(2) * (ssa + dss);
+                const T np = sqrt(tp > T(0) ? tp : T(0));
+                const T den = na + np;
+                s0[p] = na;
+                s1[p] = den > T(0) ? T(2) * dss / den : T(0);
             } else {
-                s1[p] = sv;
+                T ss = T(0);
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const T sB = T(0.5) * (gB[i][j] + gB[j][i]);
+                        ss += sB * sB;
+                    }
+                const T sv = sqrt(T(2) * ss);
+                if (EDDY) {
+                    const T val = (G.sgs == 2 ? T(1) : T(G.cs2)) * sv;
+                    s1[p] = val;
+                    mx = val > mx ? val : mx;
+                } else {
+                    s1[p] = sv;
+                }
             }
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    wb[f][q] = wb[f][q + 1];
+                    wa[f][q] = wa[f][q + 1];
+                }
         }
+        __syncthreads();      // the next plane overwrites the staged one
     }
     if (EDDY) {
         double m1[1] = {(double)mx};
@@ -671,128 +699,177 @@ slab3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __restr
 }
 
 // ============================================================================
-// Field-block Chebyshev sweep (same recurrence as the 2-D kernel, Section 2.5.2)
-// for a PX x PY tile of one plane and one field: blockIdx.z = z * 5 + field.
-// The iterate is staged with a halo of 4 in x and y, the eddy coefficient on
-// the x / y arms; the z part D_z(K D_z x) is formed from the point's own
-// column (iterate at z-4 .. z+4 with mirror ghosts, coefficient at z-2 .. z+2
-// mirrored even), read directly.  p (field 4) is written by the last sweep.
+// Field-block Chebyshev sweep (same recurrence as the 2-D kernel, Section 2.5.2).
+// One CTA = one field of a PX x PY column of ZB planes: blockIdx.z = zblock * 5
+// + field.  The CTA marches up its planes; each thread owns one (x, y) column
+// and keeps, in registers, the iterate at z-4 .. z+4 and the vertical fluxes
+// K D_z x at z-2 .. z+2 (each computed once, when its plane enters the
+// window).  Per plane the iterate is staged with a halo of 4 in x and y and
+// the eddy field with a halo of 2; the horizontal fluxes K D_x x, K D_y x are
+// formed once per arm point in shared memory.  The staging offsets are
+// computed once per CTA.  p (field 4) is written by the last sweep.
 // ============================================================================
+constexpr int CZB = 16;      // planes per CTA of the Chebyshev sweep
+
 template <typename T, int SMAG, int FIRST, int LAST>
 __global__ void __launch_bounds__(NTHREADS)
 cheb3d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T* __restrict__ din,
        T* __restrict__ zout, T* __restrict__ dout, const T* __restrict__ nu, double* part, Ctl* ctl,
        int check_done) {
-    constexpr int SX = PX + 2 * HALO, SY = PY + 2 * HALO, SP = SX * SY;
+    constexpr int SX = PX + 2 * HALO, SY = PY + 2 * HALO, SP = SX * SY;      // iterate plane
+    constexpr int NX = PX + 2 * R, NY = PY + 2 * R, NP = NX * NY;            // eddy plane
     constexpr int AXN = (PX + 2 * R) * PY, AYN = PX * (PY + 2 * R), AN = AXN + AYN;
+    constexpr int XS = (SP + NTHREADS - 1) / NTHREADS;    // staging slots per thread
+    constexpr int NS = (NP + NTHREADS - 1) / NTHREADS;
+    constexpr int AS = (AN + NTHREADS - 1) / NTHREADS;
     if (check_done && ctl->done) return;
     __shared__ T xs[SP];
-    __shared__ T g[AN];        // D_x on the x arms, D_y on the y arms
-    __shared__ T kk[AN];       // eddy coefficient on the arms
+    __shared__ T ns[SMAG ? NP : 1];
+    __shared__ T kg[AN];       // K D_x x on the x arms, K D_y x on the y arms (D only when K is constant)
     const int fld = blockIdx.z % 5;
-    const int gz = blockIdx.z / 5;
+    const int z0 = (blockIdx.z / 5) * CZB;
+    const int z1 = min(z0 + CZB, G.nz);
     const int x0 = blockIdx.x * PX, y0 = blockIdx.y * PY;
     const T ith = T(ctl->cheb[fld][k][0]);
     const T a1 = T(ctl->cheb[fld][k][1]);
     const T a2 = T(ctl->cheb[fld][k][2]);
-    const size_t foff = (size_t)fld * G.npt;
     const size_t nxy = (size_t)G.ny * G.nx;
+    const T* fr = r + (size_t)fld * G.npt;
+    const T* fsrc = (FIRST ? r : zin) + (size_t)fld * G.npt;
+    const T* fdin = FIRST ? nullptr : din + (size_t)fld * G.npt;
+    T* fzo = zout + (size_t)fld * G.npt;
+    T* fdo = dout + (size_t)fld * G.npt;
+    const T sc = FIRST ? ith : T(1);
     const int tx = threadIdx.x % PX, ty = threadIdx.x / PX;
     const int gx = x0 + tx, gy = y0 + ty;
     const bool inside = gx < G.nx && gy < G.ny;
+    const size_t own = inside ? (size_t)gy * G.nx + gx : 0;       // in-plane offset of the thread's column
     T acc[1] = {T(0)};
     if (fld == 4) {
         if (LAST && inside) {
-            const size_t o = foff + (size_t)gz * nxy + (size_t)gy * G.nx + gx;
-            const T zv = r[o] * ith;
-            zout[o] = zv;
-            acc[0] += zv * zv;
+            for (int z = z0; z < z1; ++z) {
+                const size_t o = (size_t)z * nxy + own;
+                const T zv = fr[o] * ith;
+                fzo[o] = zv;
+                acc[0] += zv * zv;
+            }
         }
     } else {
-        // x_k: r / theta (first sweep) or the previous iterate
-        const T* src = FIRST ? r : zin;
-        const T sc = FIRST ? ith : T(1);
-        for (int idx = threadIdx.x; idx < SP; idx += NTHREADS) {
-            const int ixl = idx % SX, iyl = idx / SX;
-            const size_t o = foff + (size_t)gz * nxy + (size_t)wrap(y0 + iyl - HALO, G.ny) * G.nx +
-                             wrap(x0 + ixl - HALO, G.nx);
-            xs[idx] = sc * src[o];
+        // in-plane offsets of this thread's staging slots (-1: unused slot)
+        int xoff[XS], noff[NS], acen[AS], anu[AS];
+#pragma unroll
+        for (int q = 0; q < XS; ++q) {
+            const int idx = threadIdx.x + q * NTHREADS;
+            xoff[q] = idx < SP ? wrap(y0 + idx / SX - HALO, G.ny) * G.nx + wrap(x0 + idx % SX - HALO, G.nx) : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const int idx = threadIdx.x + q * NTHREADS;
+            noff[q] = (SMAG && idx < NP) ? wrap(y0 + idx / NX - R, G.ny) * G.nx + wrap(x0 + idx % NX - R, G.nx) : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < AS; ++q) {
+            const int idx = threadIdx.x + q * NTHREADS;
+            if (idx < AXN) {
+                const int qx = idx % NX, qy = idx / NX;          // x arm at tile (qx - R, qy)
+                acen[q] = (qy + HALO) * SX + qx + R;
+                anu[q] = (qy + R) * NX + qx;
+            } else if (idx < AN) {
+                const int j = idx - AXN;
+                const int qx = j % PX, qy = j / PX;               // y arm at tile (qx, qy - R)
+                acen[q] = -((qy + R) * SX + qx + HALO) - 1;       // negative: a y arm
+                anu[q] = qy * NX + qx + R;
+            } else {
+                acen[q] = 0;
+                anu[q] = -1;
+            }
         }
         const T kscale = fld == 3 ? T(G.inv_Pr) : T(1);
-        if (SMAG) {
-            for (int idx = threadIdx.x; idx < AN; idx += NTHREADS) {
-                int qx, qy;
-                if (idx < AXN) { qx = idx % (PX + 2 * R) - R; qy = idx / (PX + 2 * R); }
-                else { const int j = idx - AXN; qx = j % PX; qy = j / PX - R; }
-                const T nv = nu[(size_t)gz * nxy + (size_t)wrap(y0 + qy, G.ny) * G.nx + wrap(x0 + qx, G.nx)];
-                // Deardorff: nu holds the strain and the arm's direction picks the coefficient
-                kk[idx] = SMAG == 2 ? dd3_coef(nv, false, fld == 3, G) : nv * kscale;
-            }
-        }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < AN; idx += NTHREADS) {
-            if (idx < AXN) {
-                const int qx = idx % (PX + 2 * R), qy = idx / (PX + 2 * R);
-                g[idx] = dd(xs, (qy + HALO) * SX + qx + R, 1, T(G.inv_dx));
-            } else {
-                const int j = idx - AXN;
-                const int qx = j % PX, qy = j / PX;
-                g[idx] = dd(xs, (qy + R) * SX + qx + HALO, SX, T(G.inv_dy));
-            }
-        }
-        __syncthreads();
+        const T ix = T(G.inv_dx), iy = T(G.inv_dy), iz = T(G.inv_dz);
+        const T Kc = T(fld == 3 ? G.K_H : G.K_M);
+        auto xval = [&](int z) -> T {          // iterate at row z of the column (mirror ghosts)
+            int side;
+            const int sz = mirror(z, G.nz, side);
+            const T sg = side == 1 ? T(G.pb[fld]) : (side == 2 ? T(G.pt[fld]) : T(1));
+            return sg * sc * fsrc[(size_t)sz * nxy + own];
+        };
+        auto zflux = [&](T d, int z) -> T {    // K D_z x at row z (eddy field mirrored even)
+            if (!SMAG) return d;
+            const int sz = eddy_row(z, G.nz);
+            const T nv = sz >= 0 ? nu[(size_t)sz * nxy + own] : T(0);
+            return (SMAG == 2 ? dd3_coef(nv, true, fld == 3, G) : nv * kscale) * d;
+        };
+        T xw[9], fw[5];
         if (inside) {
-            const T iz = T(G.inv_dz);
-            // the point's column: x_k at z-4 .. z+4 (mirror ghosts with the field's parity)
-            T col[9];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                if (q == 4) {
-                    col[q] = xs[(ty + HALO) * SX + tx + HALO];
-                    continue;
-                }
-                int side;
-                const int sz = mirror(gz + q - 4, G.nz, side);
-                const T sg = side == 1 ? T(G.pb[fld]) : (side == 2 ? T(G.pt[fld]) : T(1));
-                col[q] = sg * sc * src[foff + (size_t)sz * nxy + (size_t)gy * G.nx + gx];
-            }
-            // D_z x on the z arms z-2, z-1, z+1, z+2 and the coefficient there
-            T gzv[5], kz[5];
+            for (int q = 0; q < 8; ++q) xw[q] = xval(z0 - 4 + q);
 #pragma unroll
-            for (int l = -2; l <= 2; ++l) {
-                if (l == 0) { gzv[2] = T(0); kz[2] = T(0); continue; }
-                const int q = l + 4;
-                gzv[l + 2] = d5(col[q - 2], col[q - 1], col[q + 1], col[q + 2], iz);
-                if (SMAG) {
-                    const int sz = eddy_row(gz + l, G.nz);
-                    const T nv = sz >= 0 ? nu[(size_t)sz * nxy + (size_t)gy * G.nx + gx] : T(0);
-                    kz[l + 2] = SMAG == 2 ? dd3_coef(nv, true, fld == 3, G) : nv * kscale;
-                } else {
-                    kz[l + 2] = T(0);
-                }
-            }
-            const int cax = ty * (PX + 2 * R) + tx + R;
-            const int cay = AXN + (ty + R) * PX + tx;
-            const T Kc = T(fld == 3 ? G.K_H : G.K_M);
-            T dif;
+            for (int q = 0; q < 4; ++q) fw[q] = zflux(d5(xw[q], xw[q + 1], xw[q + 3], xw[q + 4], iz), z0 - 2 + q);
+        }
+        // the plane's staged values are loaded one plane ahead (registers), so that
+        // their latency overlaps the previous plane's arithmetic
+        T px[XS], pn[NS];
+        auto prefetch = [&](int z) {
+            const size_t pz = (size_t)z * nxy;
+#pragma unroll
+            for (int q = 0; q < XS; ++q) px[q] = xoff[q] >= 0 ? fsrc[pz + xoff[q]] : T(0);
+#pragma unroll
+            for (int q = 0; q < NS; ++q) pn[q] = (SMAG && noff[q] >= 0) ? nu[pz + noff[q]] : T(0);
+        };
+        prefetch(z0);
+        for (int z = z0; z < z1; ++z) {
+            const size_t pz = (size_t)z * nxy;
+#pragma unroll
+            for (int q = 0; q < XS; ++q)
+                if (xoff[q] >= 0) xs[threadIdx.x + q * NTHREADS] = sc * px[q];
             if (SMAG) {
-                dif = ddp(kk, g, cax, 1, T(G.inv_dx)) + ddp(kk, g, cay, PX, T(G.inv_dy)) +
-                      (T(2.0 / 3.0) * (kz[3] * gzv[3] - kz[1] * gzv[1]) -
-                       T(1.0 / 12.0) * (kz[4] * gzv[4] - kz[0] * gzv[0])) * iz;
-            } else {
-                dif = Kc * dd(g, cax, 1, T(G.inv_dx)) + Kc * dd(g, cay, PX, T(G.inv_dy)) +
-                      Kc * d5(gzv[0], gzv[1], gzv[3], gzv[4], iz);
+#pragma unroll
+                for (int q = 0; q < NS; ++q)
+                    if (noff[q] >= 0) ns[threadIdx.x + q * NTHREADS] = pn[q];
             }
-            const T xk = col[4];
-            const size_t o = foff + (size_t)gz * nxy + (size_t)gy * G.nx + gx;
-            const T rv = r[o];
-            const T res = rv - (T(G.two_over_dt) * xk - dif);
-            const T dprev = FIRST ? rv * ith : din[o];
-            const T dk = a1 * dprev + a2 * res;
-            const T xn = xk + dk;
-            zout[o] = xn;
-            if (!LAST) dout[o] = dk;
-            if (LAST) acc[0] += xn * xn;
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < AS; ++q) {
+                if (anu[q] < 0) continue;
+                const bool xarm = acen[q] >= 0;
+                const int c = xarm ? acen[q] : -acen[q] - 1;
+                const T d = xarm ? dd(xs, c, 1, ix) : dd(xs, c, SX, iy);
+                T kv = T(1);
+                if (SMAG) {
+                    const T nv = ns[anu[q]];
+                    kv = SMAG == 2 ? dd3_coef(nv, false, fld == 3, G) : nv * kscale;
+                }
+                kg[threadIdx.x + q * NTHREADS] = SMAG ? kv * d : d;
+            }
+            __syncthreads();
+            if (z + 1 < z1) prefetch(z + 1);
+            if (inside) {
+                xw[8] = xval(z + 4);
+                fw[4] = zflux(d5(xw[4], xw[5], xw[7], xw[8], iz), z + 2);
+                const int cax = ty * NX + tx + R;
+                const int cay = AXN + (ty + R) * PX + tx;
+                T dif;
+                if (SMAG) {
+                    dif = dd(kg, cax, 1, ix) + dd(kg, cay, PX, iy) +
+                          (T(2.0 / 3.0) * (fw[3] - fw[1]) - T(1.0 / 12.0) * (fw[4] - fw[0])) * iz;
+                } else {
+                    dif = Kc * dd(kg, cax, 1, ix) + Kc * dd(kg, cay, PX, iy) + Kc * d5(fw[0], fw[1], fw[3], fw[4], iz);
+                }
+                const T xk = xw[4];
+                const size_t o = pz + own;
+                const T rv = fr[o];
+                const T res = rv - (T(G.two_over_dt) * xk - dif);
+                const T dprev = FIRST ? rv * ith : fdin[o];
+                const T dk = a1 * dprev + a2 * res;
+                const T xn = xk + dk;
+                fzo[o] = xn;
+                if (!LAST) fdo[o] = dk;
+                if (LAST) acc[0] += xn * xn;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) xw[q] = xw[q + 1];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) fw[q] = fw[q + 1];
+            }
         }
     }
     if (LAST) {
@@ -918,7 +995,7 @@ static cudaError_t launch_split(const Geo& G, const T* u, const T* v, const T* F
         configured = true;
     }
     if (SMAG) {
-        dim3 gk((G.nx + KX - 1) / KX, (G.ny + KY - 1) / KY, G.nz);
+        dim3 gk((G.nx + KX - 1) / KX, (G.ny + KY - 1) / KY, (G.nz + SZB - 1) / SZB);
         strain3d<T, MODE, 0><<<gk, NTHREADS, 0, s>>>(G, u, v, sc.s0, sc.s1, part, ctl, check_done);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1133,7 +1210,7 @@ template cudaError_t launch_jv_diff3d<double>(const Geo&, const double*, const d
 template <typename T>
 cudaError_t launch_eddy3d(const Geo& G, const T* u, T* nu, double* part, Ctl* ctl, cudaStream_t s) {
     using namespace d3;
-    dim3 gk((G.nx + KX - 1) / KX, (G.ny + KY - 1) / KY, G.nz);
+    dim3 gk((G.nx + KX - 1) / KX, (G.ny + KY - 1) / KY, (G.nz + SZB - 1) / SZB);
     strain3d<T, d3::MODE_F, 1><<<gk, NTHREADS, 0, s>>>(G, u, nullptr, nullptr, nu, part, ctl, 0);
     return cudaGetLastError();
 }
@@ -1145,7 +1222,7 @@ static cudaError_t launch_pc3(const Geo& G, int sweeps, const T* r, T* z, T* za,
                               const T* nu, double* part, Ctl* ctl, int check_done, cudaStream_t s,
                               long long* launches) {
     using namespace d3;
-    dim3 grid((G.nx + PX - 1) / PX, (G.ny + PY - 1) / PY, G.nz * 5);
+    dim3 grid((G.nx + PX - 1) / PX, (G.ny + PY - 1) / PY, ((G.nz + CZB - 1) / CZB) * 5);
     const T* zin = nullptr;
     const T* din = nullptr;
     T* zbuf[2] = {za, zb};
