@@ -178,7 +178,7 @@ def unet_apply_timing(jfnk, torch, s, npt: int, reps: int, stream, dim: int = 2)
             "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
             "frac": achieved / peaks["bf16_tflops"],
             "peak_source": peaks["source"] + " (MEASURED_PEAKS.json bf16_tflops, burst)",
-            "kernel": "conv_tc (tcgen05.mma kind::f16, bf16 in TMEM-accumulated float32, 9 launches per apply)",
+            "kernel": "conv_tc (tcgen05.mma kind::f16, bf16 in TMEM-accumulated float32, 8 launches per apply: L0d composed into L0c)",
             "mma_sync": out["mma_sync"]}
 
 
@@ -939,6 +939,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "schur_over_fp64": (schur["value"] / fp64["value"]) if (schur and fp64) else None,
         "learned_pc": learned or None,
         "learned_pc_3d": learned3d,
+        "learned_over_fp64_3d": learned3d["learned_over_fp64"] if learned3d else None,
         "learned_over_fp64": next((L["learned"]["value"] / fp64["value"] for L in learned
                                    if fp64 and L["workload"] == args.workload), None),
         "cpu_baseline": cpu,

@@ -423,7 +423,10 @@ struct TcShape {
     static constexpr uint32_t B_TAP = CO * CI * 2;
     static constexpr uint32_t W_BYTES = KS * KS * B_TAP;
     static constexpr int TCOLS = 2 * CO <= 32 ? 32 : (2 * CO <= 64 ? 64 : (2 * CO <= 128 ? 128 : 256));
-    static constexpr size_t SMEM = W_BYTES + 2 * A_BYTES;
+    // input-tile buffers: three (two tiles in flight while one is computed) where
+    // they fit in 72 KB with the weights, else two
+    static constexpr int NBUF = W_BYTES + 3 * A_BYTES <= 72 * 1024 ? 3 : 2;
+    static constexpr size_t SMEM = W_BYTES + NBUF * A_BYTES;
     static_assert(CI % 16 == 0 && CO % 16 == 0 && CO <= 256, "tcgen05 shape");
 };
 
@@ -471,27 +474,34 @@ conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, Lv lv, cons
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb[1]), "r"(1u) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    stage_tile<CI, S::IH, S::IW, 0, INMODE, CU, 1>(in, bal, lv, (tile / ntx) * CONV_TH, (tile % ntx) * CONV_TW,
-                                                   S::HP, xs0);
-    cp_async_commit();
+    // the first NBUF - 1 tiles of this CTA, one commit group each
+#pragma unroll
+    for (int q = 0; q < S::NBUF - 1; ++q) {
+        const int t = tile + q * gridDim.x;
+        if (t < ntiles)
+            stage_tile<CI, S::IH, S::IW, 0, INMODE, CU, 1>(in, bal, lv, (t / ntx) * CONV_TH, (t % ntx) * CONV_TW,
+                                                           S::HP, xs0 + q * S::A_BYTES);
+        cp_async_commit();
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     uint32_t parity[2] = {0u, 0u};
     int failed = 0;
-    int buf = 0;
+    int buf = 0;       // accumulator (and mbarrier) of this tile: alternates
+    int xb = 0;        // input buffer of this tile: cycles through NBUF
     // epilogue split: warps w and w + 4 share TMEM lanes 32 (w % 4) .. +31, each takes half the columns
     const int lanebase = (warp & 3) * 32;
     const int m = lanebase + lane;                       // GEMM row = pixel (m / 8, m % 8) of the tile
     const int cbeg = (warp >> 2) * (CO / 2);
-    for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
-        cp_async_wait<0>();
+    for (; tile < ntiles; tile += gridDim.x, buf ^= 1, xb = xb + 1 == S::NBUF ? 0 : xb + 1) {
+        cp_async_wait<S::NBUF - 2>();        // this tile's group is complete; later ones may be in flight
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // staged data -> tensor-core reads
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        const uint32_t xs = xs0 + buf * S::A_BYTES;
+        const uint32_t xs = xs0 + xb * S::A_BYTES;
         if (threadIdx.x == 0) {
             uint32_t acc = 0u;
 #pragma unroll
@@ -512,12 +522,15 @@ conv_tc(ConvIn in, Bal bal, const bf16* __restrict__ W, ConvOut out, Lv lv, cons
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb[buf])
                          : "memory");
         }
-        // the other input buffer is free (its tile's MMAs completed before its epilogue)
-        const int next = tile + gridDim.x;
-        if (next >= ntiles) net_pdl_trigger();     // last tile of this CTA: release the next layer
-        if (next < ntiles)
-            stage_tile<CI, S::IH, S::IW, 0, INMODE, CU, 1>(in, bal, lv, (next / ntx) * CONV_TH,
-                                                           (next % ntx) * CONV_TW, S::HP, xs0 + (buf ^ 1) * S::A_BYTES);
+        // the buffer of the previous tile is free (its MMAs completed before its epilogue):
+        // stage the tile NBUF - 1 ahead into it
+        if (tile + gridDim.x >= ntiles) net_pdl_trigger();     // last tile of this CTA: release the next layer
+        const int pre = tile + (S::NBUF - 1) * gridDim.x;
+        if (pre < ntiles) {
+            const int pb = xb == 0 ? S::NBUF - 1 : xb - 1;
+            stage_tile<CI, S::IH, S::IW, 0, INMODE, CU, 1>(in, bal, lv, (pre / ntx) * CONV_TH,
+                                                           (pre % ntx) * CONV_TW, S::HP, xs0 + pb * S::A_BYTES);
+        }
         cp_async_commit();
         bool ready = false;
         for (long long it = 0; it < TC_WAIT_LIMIT && !ready; ++it) ready = mbar_test(mb[buf], parity[buf]);
@@ -792,6 +805,20 @@ __global__ void adam_step(float* __restrict__ w, const float* __restrict__ g, fl
     }
 }
 
+// wc[tap][co][ci] = sum_m W0d[co][m] W0c[tap][m][ci] (float32 sums, rounded once), rows co >= nf zero:
+// the 1x1 layer L0d applied after L0c, as one 3x3 48 -> 16 layer.
+__global__ void compose_l0(const float* __restrict__ w0c, const float* __restrict__ w0d, int nf,
+                           bf16* __restrict__ wc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 9 * 16 * 48; i += gridDim.x * blockDim.x) {
+        const int ci = i % 48, r = i / 48;
+        const int co = r % 16, tap = r / 16;
+        float acc = 0.f;
+        if (co < nf)
+            for (int m = 0; m < 16; ++m) acc = fmaf(w0d[co * 16 + m], w0c[((size_t)tap * 16 + m) * 48 + ci], acc);
+        wc[i] = __float2bfloat16(acc);
+    }
+}
+
 __global__ void to_bf16(const float* __restrict__ w, bf16* __restrict__ wb, size_t n) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         wb[i] = __float2bfloat16(w[i]);
@@ -910,6 +937,8 @@ struct UNet {
     size_t woff[NL + 1];
     float *w32, *g32, *m32, *v32;           // master weights, gradient, Adam moments
     bf16 *wb, *wt;                          // bfloat16 weights, flipped/transposed copies
+    bf16* wc;                               // L0d composed with L0c (inference), [tap][16][48]
+    bool wc_stale;                          // the composition predates the current weights
     // activations (NHWC bfloat16) and gradients
     bf16 *x0, *h0a, *cat0, *p1, *h1a, *cat1, *p2, *h2a, *h2b, *h1c, *h0c;
     bf16 *dy, *dh0c, *dcat0, *dh1c, *dcat1, *dh2b, *dh2a, *dp2, *ds1, *dh1a, *dp1, *ds0, *dh0a;
@@ -922,7 +951,7 @@ struct UNet {
 };
 
 static void free_net(UNet* n) {
-    void* p[] = {n->w32, n->g32, n->m32, n->v32, n->wb, n->wt, n->x0, n->h0a, n->cat0, n->p1, n->h1a, n->cat1,
+    void* p[] = {n->w32, n->g32, n->m32, n->v32, n->wb, n->wt, n->wc, n->x0, n->h0a, n->cat0, n->p1, n->h1a, n->cat1,
                  n->p2, n->h2a, n->h2b, n->h1c, n->h0c, n->dy, n->dh0c, n->dcat0, n->dh1c, n->dcat1, n->dh2b,
                  n->dh2a, n->dp2, n->ds1, n->dh1a, n->dp1, n->ds0, n->dh0a, n->yf, n->scal, n->derr};
     for (void* q : p)
@@ -969,6 +998,7 @@ UNet* unet_create(int dim, int nx, int ny, int nz, const double* balance, unsign
     };
     A((void**)&n->w32, o * 4); A((void**)&n->g32, o * 4); A((void**)&n->m32, o * 4); A((void**)&n->v32, o * 4);
     A((void**)&n->wb, o * 2); A((void**)&n->wt, o * 2);
+    A((void**)&n->wc, (size_t)9 * 16 * 48 * 2);
     A((void**)&n->x0, P0 * 16 * 2); A((void**)&n->h0a, P0 * 16 * 2); A((void**)&n->cat0, P0 * 48 * 2);
     A((void**)&n->p1, P1 * 16 * 2); A((void**)&n->h1a, P1 * 32 * 2); A((void**)&n->cat1, P1 * 96 * 2);
     A((void**)&n->p2, P2 * 32 * 2); A((void**)&n->h2a, P2 * 64 * 2); A((void**)&n->h2b, P2 * 64 * 2);
@@ -1023,6 +1053,7 @@ cudaError_t unet_set_weights(UNet* n, const float* host, cudaStream_t s) {
     cudaError_t e = cudaMemcpyAsync(n->w32, host, n->nw * 4, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     to_bf16<<<grid_for(n->nw), 256, 0, s>>>(n->w32, n->wb, n->nw);
+    n->wc_stale = true;
     if ((e = cudaMemsetAsync(n->m32, 0, n->nw * 4, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(n->v32, 0, n->nw * 4, s)) != cudaSuccess) return e;
     n->step = 0;
@@ -1057,8 +1088,9 @@ static cudaError_t forward(UNet* n, const float* x, cudaStream_t s, const int* s
 }
 
 // Inference forward with pooling, upsampling + concatenation, input packing
-// and output unpacking fused into the convolutions (9 launches; the same
-// arithmetic as forward() followed by unpack_output).
+// and output unpacking fused into the convolutions, and L0d composed into
+// L0c (8 launches; forward() computes the same map layer by layer, rounding
+// the L0c output to bfloat16 where this one rounds the composed weights).
 static cudaError_t forward_fused(UNet* n, const float* x, float* y, int accumulate, cudaStream_t s,
                                  const int* skip) {
     const Lv L0 = n->lv[0], L1 = n->lv[1], L2 = n->lv[2];
@@ -1078,11 +1110,11 @@ static cudaError_t forward_fused(UNet* n, const float* x, float* y, int accumula
     ConvIn uc1{n->h2b, 64, 0, n->cat1, 96, 64, nullptr};
     UCK((conv_ex<96, 32, 3, IN_UPCAT, OUT_BF16, 64>(uc1, n->bal, w + n->woff[L1c], to(n->h1c, 32, 0), L1, s,
                                                     skip, n->engine, n->derr)));
+    // L0c and the 1x1 L0d are one linear map: the composed 3x3 48 -> 16 layer writes the field planes
     ConvIn uc0{n->h1c, 32, 0, n->cat0, 48, 32, nullptr};
-    UCK((conv_ex<48, 16, 3, IN_UPCAT, OUT_BF16, 32>(uc0, n->bal, w + n->woff[L0c], to(n->h0c, 16, 0), L0, s,
-                                                    skip, n->engine, n->derr)));
     ConvOut pl{y, 0, 0, accumulate};
-    UCK((conv_ex<16, 16, 1, IN_NHWC, OUT_PLANES>(nhwc(n->h0c, 16, 0), n->bal, w + n->woff[L0d], pl, L0, s, skip, n->engine, n->derr)));
+    UCK((conv_ex<48, 16, 3, IN_UPCAT, OUT_PLANES, 32>(uc0, n->bal, n->wc, pl, L0, s,
+                                                    skip, n->engine, n->derr)));
     return cudaGetLastError();
 }
 
@@ -1141,10 +1173,15 @@ cudaError_t unet_check(UNet* n, cudaStream_t s) {
 }
 
 cudaError_t unet_apply(UNet* n, const float* x, float* y, int accumulate, const int* skip, cudaStream_t s) {
+    if (n->wc_stale) {
+        compose_l0<<<27, 256, 0, s>>>(n->w32 + n->woff[L0c], n->w32 + n->woff[L0d], n->bal.nf, n->wc);
+        UCK(cudaGetLastError());
+        n->wc_stale = false;
+    }
     return forward_fused(n, x, y, accumulate, s, skip);
 }
 
-int unet_launches_per_apply() { return 9; }
+int unet_launches_per_apply() { return 8; }
 
 static cudaError_t loss_and_dy(UNet* n, const float* x, const float* t, cudaStream_t s) {
     const int npix = (int)n->npix;
@@ -1181,6 +1218,7 @@ cudaError_t unet_train(UNet* n, const float* X, const float* T, int npairs, int 
             const float c1 = 1.0f / (1.0f - powf(0.9f, (float)n->step));
             const float c2 = 1.0f / (1.0f - powf(0.999f, (float)n->step));
             adam_step<<<grid_for(n->nw), 256, 0, s>>>(n->w32, n->g32, n->m32, n->v32, n->wb, n->nw, lr, c1, c2);
+            n->wc_stale = true;
             UCK(cudaGetLastError());
             if (loss_hist) {
                 double sc[2];
