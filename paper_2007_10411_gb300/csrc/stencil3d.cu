@@ -806,15 +806,27 @@ cheb3d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
 #pragma unroll
             for (int q = 0; q < 4; ++q) fw[q] = zflux(d5(xw[q], xw[q + 1], xw[q + 3], xw[q + 4], iz), z0 - 2 + q);
         }
-        // the plane's staged values are loaded one plane ahead (registers), so that
-        // their latency overlaps the previous plane's arithmetic
+        // every global value a plane needs (its staged tile and eddy plane, the
+        // point's r, d, the iterate at z+4 and the eddy field at z+2) is loaded one
+        // plane ahead into registers, so that the latency overlaps the previous
+        // plane's arithmetic
         T px[XS], pn[NS];
+        T pr = T(0), pd = T(0), px4 = T(0), pnu2 = T(0);
         auto prefetch = [&](int z) {
             const size_t pz = (size_t)z * nxy;
 #pragma unroll
             for (int q = 0; q < XS; ++q) px[q] = xoff[q] >= 0 ? fsrc[pz + xoff[q]] : T(0);
 #pragma unroll
             for (int q = 0; q < NS; ++q) pn[q] = (SMAG && noff[q] >= 0) ? nu[pz + noff[q]] : T(0);
+            if (inside) {
+                pr = fr[pz + own];
+                if (!FIRST) pd = fdin[pz + own];
+                px4 = xval(z + 4);
+                if (SMAG) {
+                    const int sz = eddy_row(z + 2, G.nz);
+                    pnu2 = sz >= 0 ? nu[(size_t)sz * nxy + own] : T(0);
+                }
+            }
         };
         prefetch(z0);
         for (int z = z0; z < z1; ++z) {
@@ -842,10 +854,14 @@ cheb3d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
                 kg[threadIdx.x + q * NTHREADS] = SMAG ? kv * d : d;
             }
             __syncthreads();
+            const T rv = pr, dv = pd, nu2 = pnu2;
+            xw[8] = px4;
             if (z + 1 < z1) prefetch(z + 1);
             if (inside) {
-                xw[8] = xval(z + 4);
-                fw[4] = zflux(d5(xw[4], xw[5], xw[7], xw[8], iz), z + 2);
+                {
+                    const T dz2 = d5(xw[4], xw[5], xw[7], xw[8], iz);
+                    fw[4] = SMAG ? (SMAG == 2 ? dd3_coef(nu2, true, fld == 3, G) : nu2 * kscale) * dz2 : dz2;
+                }
                 const int cax = ty * NX + tx + R;
                 const int cay = AXN + (ty + R) * PX + tx;
                 T dif;
@@ -857,9 +873,8 @@ cheb3d(Geo G, int k, const T* __restrict__ r, const T* __restrict__ zin, const T
                 }
                 const T xk = xw[4];
                 const size_t o = pz + own;
-                const T rv = fr[o];
                 const T res = rv - (T(G.two_over_dt) * xk - dif);
-                const T dprev = FIRST ? rv * ith : fdin[o];
+                const T dprev = FIRST ? rv * ith : dv;
                 const T dk = a1 * dprev + a2 * res;
                 const T xn = xk + dk;
                 fzo[o] = xn;
