@@ -174,3 +174,35 @@ def test_step_parity_3d(var, prec):
         assert np.all(rel_per_field(got, ref) < 1e-4), rel_per_field(got, ref)
     R = m.residual(got, m.rhs_f(U))
     assert np.linalg.norm(m.scale(R)) <= st["tol"] * 1.01
+
+
+def test_full_size_3d_operators_and_step():
+    """The config-4 grid (256x256x128 stable thermal, the 3-D bench workload):
+    F and the mixed Jacobian product elementwise against the oracle, then one
+    mixed step whose state the oracle checks against Eq. ns (property at full size)."""
+    c = synth.case("thermal3d_256x256x128")
+    m = Model(c)
+    s = jf().Solver(c)
+    U0 = synth.initial_state(c)
+    U = U0 + synth.random_state(c, 2, amp=(0.5, 0.3, 0.001)) - synth.initial_state(synth.with_options(c, noise=0.0))
+    F = torch.empty_like(dev(U))
+    s.rhs(dev(U), F)
+    FU = m.F(U)
+    assert np.all(rel_per_field(host(F), FU) < 1e-4), rel_per_field(host(F), FU)
+    V = np.random.Generator(np.random.PCG64(3)).standard_normal(U.shape)
+    V = m.unscale(m.scale(V) / np.linalg.norm(m.scale(V)))
+    out = torch.empty_like(F)
+    s.jv(dev(U), dev(V), out, eps=1e-3)
+    ref = m.jv(U, FU, V, 1e-3)
+    err = np.linalg.norm(m.scale(host(out) - ref)) / np.linalg.norm(m.scale(ref))
+    assert err < 1e-4, err
+    del F, out, FU, ref
+    u = dev(U0)
+    st = s.step(u)
+    got = host(u)
+    assert st["converged"], st
+    R = m.residual(got, m.rhs_f(U0))
+    assert np.linalg.norm(m.scale(R)) <= st["tol"] * 1.01
+    b = s.budgets(u)
+    assert abs(b["sum_div"]) < 1e-9 * np.max(np.abs(got[:3])) * m.nx * m.ny * m.nz * m.dx
+    s.close()
