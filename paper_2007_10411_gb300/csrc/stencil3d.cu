@@ -57,11 +57,6 @@ template <typename T>
 __device__ __forceinline__ T dd(const T* s, int i, int st, T ih) {
     return (T(2.0 / 3.0) * (s[i + st] - s[i - st]) - T(1.0 / 12.0) * (s[i + 2 * st] - s[i - 2 * st])) * ih;
 }
-template <typename T>
-__device__ __forceinline__ T ddp(const T* a, const T* b, int i, int st, T ih) {
-    return (T(2.0 / 3.0) * (a[i + st] * b[i + st] - a[i - st] * b[i - st]) -
-            T(1.0 / 12.0) * (a[i + 2 * st] * b[i + 2 * st] - a[i - 2 * st] * b[i - 2 * st])) * ih;
-}
 // D f from the four neighbours f(-2), f(-1), f(+1), f(+2)
 template <typename T>
 __device__ __forceinline__ T d5(T m2, T m1, T p1, T p2, T ih) {
@@ -323,12 +318,11 @@ plane3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __rest
     constexpr int SX = PX + 2 * HALO, SY = PY + 2 * HALO, SP = SX * SY;
     constexpr int AXN = (PX + 2 * R) * PY, AYN = PX * (PY + 2 * R), AN = AXN + AYN;   // x arms, y arms
     constexpr int NS = TWO ? 2 : 1;                  // states staged (b [, a])
-    constexpr int NK = SMAG ? (TWO ? 2 : 1) : 0;     // strain values on the arms (ds [, sa])
     if ((MODE == MODE_JV || MODE == MODE_DJV) && check_done && ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* st = reinterpret_cast<T*>(smem_raw);          // [NS][5][SP]: b fields, then a fields
     T* ga = st + NS * 5 * SP;                        // [NS][4][AN] first derivatives on the arms
-    T* ks = ga + NS * 4 * AN;                        // [NK][AN] strain on the arms
+    T* ks = ga + NS * 4 * AN;                        // [NS][AN] strain on the arms (SMAG)
     const int x0 = blockIdx.x * PX, y0 = blockIdx.y * PY, gz = blockIdx.z;
     const T ix = T(G.inv_dx), iy = T(G.inv_dy);
     T ev[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -502,13 +496,12 @@ slab3d(Geo G, const T* __restrict__ u, const T* __restrict__ v, const T* __restr
     constexpr int SZ = TZ + 2 * HALO, SP = TX * SZ;          // staged rows [row][x]
     constexpr int QZ = TZ + 2 * R, AN = TX * QZ;             // z arms
     constexpr int NS = TWO ? 2 : 1;
-    constexpr int NK = SMAG ? (TWO ? 2 : 1) : 0;
     constexpr int PER = TX * TZ / NTHREADS;                  // outputs per thread
     if ((MODE == MODE_JV || MODE == MODE_DJV) && check_done && ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* st = reinterpret_cast<T*>(smem_raw);                  // [NS][5][SP]
     T* ga = st + NS * 5 * SP;                                // [NS][4][AN]
-    T* ks = ga + NS * 4 * AN;                                // [NK][AN]
+    T* ks = ga + NS * 4 * AN;                                // [NS][AN] strain on the z arms (SMAG)
     const int z0 = blockIdx.x * TZ, x0 = blockIdx.y * TX, gy = blockIdx.z;
     const T iz = T(G.inv_dz);
     T ev[5] = {T(0), T(0), T(0), T(0), T(0)};

@@ -1094,7 +1094,6 @@ static cudaError_t forward(UNet* n, const float* x, cudaStream_t s, const int* s
 static cudaError_t forward_fused(UNet* n, const float* x, float* y, int accumulate, cudaStream_t s,
                                  const int* skip) {
     const Lv L0 = n->lv[0], L1 = n->lv[1], L2 = n->lv[2];
-    const size_t P0 = n->npix, P1 = (size_t)L1.H * L1.Wd, P2 = (size_t)L2.H * L2.Wd;
     const bf16* w = n->wb;
     const ConvIn none{nullptr, 0, 0, nullptr, 0, 0, nullptr};
     auto nhwc = [&](const bf16* a, int str, int off) { ConvIn c = none; c.a = a; c.astr = str; c.aoff = off; return c; };
