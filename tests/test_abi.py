@@ -91,3 +91,19 @@ def test_budgets_static_size_limit(lib):
     assert lib.jfnk_budgets_static(ctypes.byref(g), P(16), P(16), None) == jfnk.JFNK_ERR_INVALID_ARG
     g = jfnk.structs_from_case(synth.case("tiny_16x8"))[0]
     assert lib.jfnk_budgets_static(ctypes.byref(g), None, P(16), None) == jfnk.JFNK_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name,prec", [
+    ("thermal3d_32x48x8", synth.PREC_MIXED),     # ny not a multiple of 64
+    ("thermal3d_48x64x8", synth.PREC_MIXED),     # nx not a multiple of 32
+    ("thermal3d_32x64x6", synth.PREC_MIXED),     # nz not a multiple of 4
+    ("thermal3d_32x64x8", synth.PREC_FP64),      # the network runs on the float32 basis only
+    ("tiny_48x32", synth.PREC_MIXED),            # 2-D: nx not a multiple of 32
+])
+def test_learned_preconditioner_grid_rules(lib, name, prec):
+    """The learned preconditioner's grid rules (2-D: nx, nz multiples of 32; 3-D: nx of 32,
+    ny of 64, nz of 4; mixed precision) are checked before any CUDA call."""
+    c = synth.with_options(synth.case(name), precision=prec, precond=jfnk.PC_UNET)
+    st, h = _create(lib, c)
+    assert st == jfnk.JFNK_ERR_UNSUPPORTED, st
+    assert not h.value
