@@ -255,8 +255,18 @@ typedef struct {
 
 /* Enable (mask != 0, bit i = family i) or disable event timing of kernel
  * families on the handle's stream; enabling resets the accumulators.  The
- * events add a few microseconds of host work per timed launch. */
+ * events add a few microseconds of host work per timed launch.  Launches of
+ * a GMRES cycle's Krylov steps after the cycle has ended (they return at
+ * entry) are not counted. */
 jfnk_status jfnk_kernel_timing(jfnk_handle* h, unsigned int mask);
+
+/* jfnk_kernel_timing with the launches inside GMRES cycles timed only at
+ * Krylov steps j with j % every == every / 2 (every >= 1; other launches are
+ * always timed; the offset centres the sample on the cycle, whose passes
+ * grow with j).  Each pair of events splits the programmatic dependent
+ * launch of its kernel from its neighbours; sampling keeps that cost off most
+ * steps.  Returns JFNK_ERR_INVALID_ARG for h NULL or every < 1. */
+jfnk_status jfnk_kernel_timing_sampled(jfnk_handle* h, unsigned int mask, int every);
 
 /* Drain the outstanding events (synchronises the stream) and copy the
  * accumulators of all JFNK_KF_COUNT families into out[0 .. JFNK_KF_COUNT). */
@@ -417,6 +427,29 @@ jfnk_status jfnk_autotune(jfnk_handle* h, const double* u, int* tiles);
 
 /* Set the tile-shape indices (0 .. JFNK_NUM_TILE_SHAPES-1) directly. */
 jfnk_status jfnk_set_tiles(jfnk_handle* h, int tile_jv, int tile_pc);
+
+/* Launch the Krylov steps of a GMRES cycle as CUDA graphs (Section 2.5.1's
+ * restarted FGMRES(m), right-preconditioned path with the field-block
+ * preconditioner, float32 or float64).  steps > 0: the cycle's m steps are
+ * captured once into segments of `steps` steps each (steps > m is taken as
+ * m) and each segment is one graph launch; the host polls for the end of the
+ * cycle once per segment instead of once per step.  steps = 0: every kernel
+ * is a separate stream launch.  jfnk_create sets min(m,
+ * JFNK_CYCLE_GRAPH_SEGMENT) for grids of at most
+ * JFNK_CYCLE_GRAPH_SEGMENT_POINTS points and m above.  Results are
+ * bit-identical either way: every kernel of a step returns at entry once the
+ * cycle has ended, so steps launched past the end change nothing.  The
+ * segments are captured on a private stream (the handle's first fused cycle
+ * runs as stream launches) and again whenever the grid description, tiles,
+ * surface flux, sweep count, preconditioner or kernel-timing mask change;
+ * timed families are timed by event nodes inside the graphs.  The learned
+ * preconditioner and pair recording use stream launches.  Returns
+ * JFNK_ERR_INVALID_ARG for h NULL or steps < 0. */
+jfnk_status jfnk_set_cycle_graph(jfnk_handle* h, int steps);
+
+/* Default graph segment length and the grid size up to which it applies. */
+#define JFNK_CYCLE_GRAPH_SEGMENT 8
+#define JFNK_CYCLE_GRAPH_SEGMENT_POINTS 262144
 
 /* Largest grid (nx * nz points) accepted by jfnk_budgets_static. */
 #define JFNK_BUDGETS_STATIC_MAX_POINTS 8388608

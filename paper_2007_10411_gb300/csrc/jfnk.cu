@@ -59,13 +59,33 @@ struct jfnk_handle {
     bool kt_ready;
     cudaEvent_t kt_start[KT_RING], kt_stop[KT_RING];
     int kt_fam[KT_RING];
+    int kt_stepi[KT_RING];        // Krylov step of the timed launch (-1: outside a cycle)
     double kt_b[KT_RING];
     int kt_head, kt_count, kt_open;
+    int kt_step;                  // Krylov step being enqueued (-1: outside a cycle)
+    int kt_every;                 // in-cycle launches are timed at steps j = kt_every / 2 mod kt_every
+    // timing inside captured cycles: one event pair per (step, family), recorded
+    // by event nodes of the graph and read after each cycle
+    bool gkt_ready, gcapturing;
+    cudaEvent_t gkt_start[KMAX][JFNK_KF_COUNT], gkt_stop[KMAX][JFNK_KF_COUNT];
+    double gkt_b[KMAX][JFNK_KF_COUNT];
     jfnk_kernel_time kt_acc[JFNK_KF_COUNT];
     // learned preconditioner: network and recorded training pairs
     UNet* net;
     float *capX, *capT;
     int cap_cap, cap_kinds;
+    // graph-captured Krylov steps of the fused cycle: gseg steps per segment
+    // (0: one stream launch per kernel), captured on a private stream and
+    // keyed on everything the captured launches read from the host
+    int gseg, gnseg, gwarm;
+    cudaStream_t gstream;
+    cudaGraphExec_t gexec[KMAX];
+    long long gnl[KMAX];          // kernel launches per segment
+    Geo gG;
+    int gsweeps, gseg_key;
+    unsigned int gkt_mask;
+    int gkt_every;
+    const void *guT, *gZ, *gw2;
 };
 
 #define CK(call)                                                                  \
@@ -146,34 +166,81 @@ static void free_all(jfnk_handle* h) {
     if (h->hdone) cudaFreeHost(h->hdone);
     for (int i = 0; i < KMAX; ++i)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    for (int i = 0; i < KMAX; ++i)
+        if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
     if (h->kt_ready)
         for (int i = 0; i < KT_RING; ++i) {
             cudaEventDestroy(h->kt_start[i]);
             cudaEventDestroy(h->kt_stop[i]);
         }
+    if (h->gkt_ready)
+        for (int j = 0; j < KMAX; ++j)
+            for (int f = 0; f < JFNK_KF_COUNT; ++f) {
+                cudaEventDestroy(h->gkt_start[j][f]);
+                cudaEventDestroy(h->gkt_stop[j][f]);
+            }
 }
 
 // ------------------------------------------------------------ kernel timing
-static void kt_drain(jfnk_handle* h) {
+static void kt_add(jfnk_handle* h, int fam, cudaEvent_t e0, cudaEvent_t e1, double bytes) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+        jfnk_kernel_time& a = h->kt_acc[fam];
+        a.launches += 1;
+        a.ms += ms;
+        a.bytes += bytes;
+    } else {
+        cudaGetLastError();
+    }
+}
+
+// Whether the timed launch of family fam in Krylov step `step` did its work in
+// a cycle that processed `cols` Hessenberg columns.  Every kernel of a step
+// returns at entry once the cycle has ended, so launches past the end take
+// no time and move no bytes and are left out of the averages.  In the
+// fused cycle the preconditioner and Jacobian product of step cols still run
+// (the cycle ends inside that step's pass CA); elsewhere the end comes with
+// the Givens update of step cols - 1.
+static bool kt_valid(int fam, int step, int cols, bool fused) {
+    if (step < 0) return true;
+    if (fused && (fam == JFNK_KF_PRECOND || fam == JFNK_KF_JV || fam == JFNK_KF_UNET)) return step <= cols;
+    return step < cols;
+}
+
+static void kt_drain_cycle(jfnk_handle* h, int cols, bool fused) {
     for (int c = 0; c < h->kt_count; ++c) {
         const int i = (h->kt_head + c) % KT_RING;
-        float ms = 0.0f;
-        if (cudaEventSynchronize(h->kt_stop[i]) == cudaSuccess &&
-            cudaEventElapsedTime(&ms, h->kt_start[i], h->kt_stop[i]) == cudaSuccess) {
-            jfnk_kernel_time& a = h->kt_acc[h->kt_fam[i]];
-            a.launches += 1;
-            a.ms += ms;
-            a.bytes += h->kt_b[i];
-        }
+        if (cols < 0 || kt_valid(h->kt_fam[i], h->kt_stepi[i], cols, fused))
+            kt_add(h, h->kt_fam[i], h->kt_start[i], h->kt_stop[i], h->kt_b[i]);
+        else
+            cudaEventSynchronize(h->kt_stop[i]);
     }
     h->kt_head = 0;
     h->kt_count = 0;
 }
 
-static inline bool kt_on(const jfnk_handle* h, int fam) { return (h->kt_mask >> fam) & 1u; }
+static void kt_drain(jfnk_handle* h) { kt_drain_cycle(h, -1, false); }
+
+// Timings of a captured cycle's steps (valid launches only), after the cycle.
+static void kt_drain_graph(jfnk_handle* h, int cols) {
+    if (!h->gkt_mask) return;
+    for (int j = 0; j <= std::min(cols, h->m - 1); ++j)
+        for (int f = 0; f < JFNK_KF_COUNT; ++f)
+            if (((h->gkt_mask >> f) & 1u) && j % h->gkt_every == h->gkt_every / 2 && kt_valid(f, j, cols, true))
+                kt_add(h, f, h->gkt_start[j][f], h->gkt_stop[j][f], h->gkt_b[j][f]);
+}
+
+static inline bool kt_on(const jfnk_handle* h, int fam) {
+    return ((h->kt_mask >> fam) & 1u) && (h->kt_step < 0 || h->kt_step % h->kt_every == h->kt_every / 2);
+}
 
 static void kt_begin(jfnk_handle* h, int fam) {
     if (!kt_on(h, fam)) return;
+    if (h->gcapturing) {   // an event node of the graph being captured
+        cudaEventRecordWithFlags(h->gkt_start[h->kt_step][fam], h->stream, cudaEventRecordExternal);
+        return;
+    }
     if (h->kt_count == KT_RING) kt_drain(h);
     const int i = (h->kt_head + h->kt_count) % KT_RING;
     cudaEventRecord(h->kt_start[i], h->stream);
@@ -182,9 +249,15 @@ static void kt_begin(jfnk_handle* h, int fam) {
 
 static void kt_end(jfnk_handle* h, int fam, double bytes) {
     if (!kt_on(h, fam)) return;
+    if (h->gcapturing) {
+        cudaEventRecordWithFlags(h->gkt_stop[h->kt_step][fam], h->stream, cudaEventRecordExternal);
+        h->gkt_b[h->kt_step][fam] = bytes;
+        return;
+    }
     const int i = h->kt_open;
     cudaEventRecord(h->kt_stop[i], h->stream);
     h->kt_fam[i] = fam;
+    h->kt_stepi[i] = h->kt_step;
     h->kt_b[i] = bytes;
     h->kt_count += 1;
 }
@@ -241,6 +314,11 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     h->stream = (cudaStream_t)cuda_stream;
     h->mixed = opts->precision == JFNK_MIXED;
     h->m = opts->krylov_m;
+    h->kt_step = -1;
+    h->kt_every = 1;
+    h->gseg = (size_t)grid->nx * (grid->dim == 3 ? grid->ny : 1) * grid->nz <= JFNK_CYCLE_GRAPH_SEGMENT_POINTS
+                  ? std::min(h->m, JFNK_CYCLE_GRAPH_SEGMENT)
+                  : h->m;
     const int dim = grid->dim;
     const int ny = dim == 3 ? grid->ny : 1;
     const int nf = dim == 3 ? 5 : 4;
@@ -423,7 +501,11 @@ extern "C" jfnk_status jfnk_set_surface_flux(jfnk_handle* h, const double* H) {
 }
 
 extern "C" jfnk_status jfnk_kernel_timing(jfnk_handle* h, unsigned int mask) {
-    if (!h) return JFNK_ERR_INVALID_ARG;
+    return jfnk_kernel_timing_sampled(h, mask, 1);
+}
+
+extern "C" jfnk_status jfnk_kernel_timing_sampled(jfnk_handle* h, unsigned int mask, int every) {
+    if (!h || every < 1) return JFNK_ERR_INVALID_ARG;
     if (mask != 0 && !h->kt_ready) {
         for (int i = 0; i < KT_RING; ++i) {
             CK(cudaEventCreate(&h->kt_start[i]));
@@ -433,6 +515,7 @@ extern "C" jfnk_status jfnk_kernel_timing(jfnk_handle* h, unsigned int mask) {
     }
     if (h->kt_count) kt_drain(h);
     h->kt_mask = mask;
+    h->kt_every = every;
     memset(h->kt_acc, 0, sizeof(h->kt_acc));
     return JFNK_OK;
 }
@@ -515,6 +598,12 @@ extern "C" jfnk_status jfnk_set_tiles(jfnk_handle* h, int tile_jv, int tile_pc) 
         return JFNK_ERR_INVALID_ARG;
     h->G.tile_jv = tile_jv;
     h->G.tile_pc = tile_pc;
+    return JFNK_OK;
+}
+
+extern "C" jfnk_status jfnk_set_cycle_graph(jfnk_handle* h, int steps) {
+    if (!h || steps < 0) return JFNK_ERR_INVALID_ARG;
+    h->gseg = std::min(steps, h->m);
     return JFNK_OK;
 }
 
@@ -692,7 +781,7 @@ static jfnk_status apply_jv(jfnk_handle* h, const T* uT, const T* z, T* w, int c
 // full cycle gets its Givens update alone.  The w'_{j-1} / w_j buffers
 // alternate between w and w2.
 template <typename T>
-static jfnk_status fused_cycle(jfnk_handle* h, const T* uT, bool learned, bool arnoldi_pairs, int lag) {
+static jfnk_status fused_step(jfnk_handle* h, const T* uT, bool learned, bool arnoldi_pairs, int j) {
     cudaStream_t s = h->stream;
     const Geo& G = h->G;
     const size_t n = h->n, ld = h->ld;
@@ -701,52 +790,179 @@ static jfnk_status fused_cycle(jfnk_handle* h, const T* uT, bool learned, bool a
     T* Z = (T*)h->Z;
     T* wb[2] = {(T*)h->w, (T*)h->w2};
     const double vb = (double)n * sizeof(T);
+    h->kt_step = j;
+    const T* dj = j == 0 ? V : wb[(j - 1) & 1];
+    T* zj = Z + (size_t)j * ld;
+    T* wj = wb[j & 1];
+    kt_begin(h, JFNK_KF_PRECOND);
+    CK(launch_precond<T>(G, h->opts.pc_sweeps, dj, zj, (T*)h->za, (T*)h->zb, (T*)h->da, (T*)h->db,
+                         (const T*)h->nu, h->part, h->ctl, 1, s, &h->launches));
+    kt_end(h, JFNK_KF_PRECOND, pc_bytes(h));
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (learned) {   // z_j += N(d_j), then the FD step for the new ||z_j||
+            kt_begin(h, JFNK_KF_UNET);
+            CK(unet_apply(h->net, (const float*)dj, (float*)zj, 1, &h->ctl->done, s));
+            kt_end(h, JFNK_KF_UNET, 3.0 * (double)n * sizeof(float));
+            CK(launch_pc_eps(zj, n, h->part, h->ctl, s));
+            h->launches += unet_launches_per_apply() + 1;
+        }
+    }
+    jfnk_status st = apply_jv<T>(h, uT, zj, wj, 1);
+    if (st != JFNK_OK) return st;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (arnoldi_pairs) {   // (J z_j, z_j) is an exact inverse pair
+            CK(launch_pair_arnoldi(wj, (float*)h->tA, n, h->part, h->ctl, s));
+            CK(launch_precond<float>(G, h->opts.pc_sweeps, (const float*)h->tA, (float*)h->tB,
+                                     (float*)h->za, (float*)h->zb, (float*)h->da, (float*)h->db,
+                                     (const float*)h->nu, h->part, h->ctl, 1, s, &h->launches));
+            CK(launch_pair_store<float>((const float*)h->tA, zj, (const float*)h->tB, h->capX, h->capT, n,
+                                        h->cap_cap, 1, h->ctl, s));
+            h->launches += 4;
+        }
+    }
+    kt_begin(h, JFNK_KF_ARNOLDI_A);
+    int nblkA;
+    if (j == 0) {
+        CK(launch_arnoldi_a<T>(V, ld, wj, n, 1, h->part, h->ctl, s));
+        nblkA = arnoldi_a_parts<T>(n);
+        kt_end(h, JFNK_KF_ARNOLDI_A, 2 * vb);
+    } else {
+        CK(launch_arnoldi_ca<T>(V, ld, wb[(j - 1) & 1], wj, n, j, m, h->partB, h->part, h->ctl, s));
+        nblkA = arnoldi_ca_parts<T>(n);
+        kt_end(h, JFNK_KF_ARNOLDI_A, (j + 3) * vb);   // reads v_0..v_{j-1}, w'_{j-1}, w_j; writes v_j
+    }
+    kt_begin(h, JFNK_KF_ARNOLDI_B);
+    CK(launch_arnoldi_b_from<T>(V, ld, wj, n, j + 1, h->part, nblkA, h->partB, h->ctl, s));
+    kt_end(h, JFNK_KF_ARNOLDI_B, (j + 3) * vb);      // reads v_0..v_j, w_j; writes w'_j
+    h->launches += 2;
+    return JFNK_OK;
+}
+
+static void graph_release(jfnk_handle* h) {
+    if (h->gnseg > 0) cudaStreamSynchronize(h->stream);   // no launch of them in flight
+    for (int k = 0; k < KMAX; ++k)
+        if (h->gexec[k]) {
+            cudaGraphExecDestroy(h->gexec[k]);
+            h->gexec[k] = nullptr;
+        }
+    h->gnseg = 0;
+}
+
+// Capture the cycle's m Krylov steps as segments of gseg steps.  Every kernel
+// of a step returns at entry once the device has ended the cycle (ctl->done),
+// so a segment launched past the end leaves the state untouched, and the
+// captured launches read nothing from the host but the Geo, the sweep count
+// and the buffer pointers, which form the key a later cycle compares.
+template <typename T>
+static jfnk_status graph_capture(jfnk_handle* h, const T* uT) {
+    graph_release(h);
+    if (!h->gstream) CK(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+    if (h->kt_mask && !h->gkt_ready) {
+        for (int j = 0; j < KMAX; ++j)
+            for (int f = 0; f < JFNK_KF_COUNT; ++f) {
+                CK(cudaEventCreate(&h->gkt_start[j][f]));
+                CK(cudaEventCreate(&h->gkt_stop[j][f]));
+            }
+        h->gkt_ready = true;
+    }
+    const int m = h->m, S = h->gseg;
+    const int nseg = (m + S - 1) / S;
+    cudaStream_t user = h->stream;
+    h->stream = h->gstream;
+    h->gcapturing = true;
+    jfnk_status st = JFNK_OK;
+    for (int k = 0; k < nseg && st == JFNK_OK; ++k) {
+        const long long l0 = h->launches;
+        cudaError_t e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) {
+            st = JFNK_ERR_CUDA;
+            break;
+        }
+        for (int j = k * S; j < std::min(m, (k + 1) * S) && st == JFNK_OK; ++j)
+            st = fused_step<T>(h, uT, false, false, j);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(h->gstream, &g);
+        h->gnl[k] = h->launches - l0;
+        h->launches = l0;
+        if (st == JFNK_OK && e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec[k], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (st == JFNK_OK && e != cudaSuccess) {
+            fprintf(stderr, "libjfnk: cycle capture failed: %s\n", cudaGetErrorString(e));
+            st = JFNK_ERR_CUDA;
+        }
+    }
+    h->stream = user;
+    h->gcapturing = false;
+    h->kt_step = -1;
+    if (st != JFNK_OK) {
+        cudaGetLastError();
+        graph_release(h);
+        return st;
+    }
+    h->gnseg = nseg;
+    memcpy(&h->gG, &h->G, sizeof(Geo));
+    h->gsweeps = h->opts.pc_sweeps;
+    h->gseg_key = S;
+    h->guT = uT;
+    h->gZ = h->Z;
+    h->gw2 = h->w2;
+    h->gkt_mask = h->kt_mask;
+    h->gkt_every = h->kt_every;
+    return JFNK_OK;
+}
+
+template <typename T>
+static bool graph_current(const jfnk_handle* h, const T* uT) {
+    return h->gnseg > 0 && h->gseg_key == h->gseg && h->gsweeps == h->opts.pc_sweeps && h->guT == uT &&
+           h->gZ == h->Z && h->gw2 == h->w2 && h->gkt_mask == h->kt_mask &&
+           h->gkt_every == h->kt_every &&
+           memcmp(&h->gG, &h->G, sizeof(Geo)) == 0;
+}
+
+// One GMRES cycle of the right-preconditioned path with the second projection
+// of CGS2 lagged behind the next Jacobian product (Arnoldi passes CA and B per
+// step, see arnoldi_ca): step j takes the direction d_j = v_0 (j = 0) or
+// w'_{j-1}, z_j = M^{-1} d_j (+ N(d_j) for the learned correction), w_j = J z_j;
+// pass CA forms v_j, updates column j-1 of the Hessenberg / Givens state and
+// projects w_j once; pass B projects it again into w'_j.  The last column of a
+// full cycle gets its Givens update alone.  The w'_{j-1} / w_j buffers
+// alternate between w and w2.  The host learns that the cycle ended from a
+// copy of ctl->done made after each step (stream launches) or each captured
+// segment (graph launches), read with a lag so that the GPU never waits for it.
+template <typename T>
+static jfnk_status fused_cycle(jfnk_handle* h, const T* uT, bool learned, bool arnoldi_pairs, int lag,
+                               bool* used_graph) {
+    cudaStream_t s = h->stream;
+    const int m = h->m;
+    // the first fused cycle of a handle runs as stream launches (one-time kernel
+    // attribute set-up happens outside any capture); later ones may use graphs
+    const bool graph = h->gseg > 0 && h->gwarm && !learned && !arnoldi_pairs;
+    h->gwarm = 1;
+    *used_graph = graph;
+    if (graph) {
+        if (!graph_current<T>(h, uT)) {
+            jfnk_status st = graph_capture<T>(h, uT);
+            if (st != JFNK_OK) return st;
+        }
+        for (int k = 0; k < h->gnseg; ++k) {
+            CK(cudaGraphLaunch(h->gexec[k], s));
+            h->launches += h->gnl[k];
+            CK(cudaMemcpyAsync(&h->hdone[k], &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaEventRecord(h->ev[k], s));
+            if (k >= 1) {
+                CK(cudaEventSynchronize(h->ev[k - 1]));
+                if (h->hdone[k - 1]) break;
+            }
+        }
+        // Givens update of the last column (returns at once when the cycle ended earlier)
+        CK(launch_arnoldi_givens<T>(h->n, m, m, h->partB, h->ctl, s));
+        h->launches += 1;
+        return JFNK_OK;
+    }
     int j = 0;
     for (; j < m; ++j) {
-        const T* dj = j == 0 ? V : wb[(j - 1) & 1];
-        T* zj = Z + (size_t)j * ld;
-        T* wj = wb[j & 1];
-        kt_begin(h, JFNK_KF_PRECOND);
-        CK(launch_precond<T>(G, h->opts.pc_sweeps, dj, zj, (T*)h->za, (T*)h->zb, (T*)h->da, (T*)h->db,
-                             (const T*)h->nu, h->part, h->ctl, 1, s, &h->launches));
-        kt_end(h, JFNK_KF_PRECOND, pc_bytes(h));
-        if constexpr (sizeof(T) == sizeof(float)) {
-            if (learned) {   // z_j += N(d_j), then the FD step for the new ||z_j||
-                kt_begin(h, JFNK_KF_UNET);
-                CK(unet_apply(h->net, (const float*)dj, (float*)zj, 1, &h->ctl->done, s));
-                kt_end(h, JFNK_KF_UNET, 3.0 * (double)n * sizeof(float));
-                CK(launch_pc_eps(zj, n, h->part, h->ctl, s));
-                h->launches += unet_launches_per_apply() + 1;
-            }
-        }
-        jfnk_status st = apply_jv<T>(h, uT, zj, wj, 1);
+        jfnk_status st = fused_step<T>(h, uT, learned, arnoldi_pairs, j);
         if (st != JFNK_OK) return st;
-        if constexpr (sizeof(T) == sizeof(float)) {
-            if (arnoldi_pairs) {   // (J z_j, z_j) is an exact inverse pair
-                CK(launch_pair_arnoldi(wj, (float*)h->tA, n, h->part, h->ctl, s));
-                CK(launch_precond<float>(G, h->opts.pc_sweeps, (const float*)h->tA, (float*)h->tB,
-                                         (float*)h->za, (float*)h->zb, (float*)h->da, (float*)h->db,
-                                         (const float*)h->nu, h->part, h->ctl, 1, s, &h->launches));
-                CK(launch_pair_store<float>((const float*)h->tA, zj, (const float*)h->tB, h->capX, h->capT, n,
-                                            h->cap_cap, 1, h->ctl, s));
-                h->launches += 4;
-            }
-        }
-        kt_begin(h, JFNK_KF_ARNOLDI_A);
-        int nblkA;
-        if (j == 0) {
-            CK(launch_arnoldi_a<T>(V, ld, wj, n, 1, h->part, h->ctl, s));
-            nblkA = arnoldi_a_parts<T>(n);
-            kt_end(h, JFNK_KF_ARNOLDI_A, 2 * vb);
-        } else {
-            CK(launch_arnoldi_ca<T>(V, ld, wb[(j - 1) & 1], wj, n, j, m, h->partB, h->part, h->ctl, s));
-            nblkA = arnoldi_ca_parts<T>(n);
-            kt_end(h, JFNK_KF_ARNOLDI_A, (j + 3) * vb);   // reads v_0..v_{j-1}, w'_{j-1}, w_j; writes v_j
-        }
-        kt_begin(h, JFNK_KF_ARNOLDI_B);
-        CK(launch_arnoldi_b_from<T>(V, ld, wj, n, j + 1, h->part, nblkA, h->partB, h->ctl, s));
-        kt_end(h, JFNK_KF_ARNOLDI_B, (j + 3) * vb);      // reads v_0..v_j, w_j; writes w'_j
-        h->launches += 2;
         CK(cudaMemcpyAsync(&h->hdone[j], &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaEventRecord(h->ev[j], s));
         if (j >= lag) {
@@ -754,8 +970,9 @@ static jfnk_status fused_cycle(jfnk_handle* h, const T* uT, bool learned, bool a
             if (h->hdone[j - lag]) break;
         }
     }
+    h->kt_step = -1;
     // Givens update of the cycle's last column (returns at once when the cycle ended earlier)
-    CK(launch_arnoldi_givens<T>(n, std::min(j + 1, m), m, h->partB, h->ctl, s));
+    CK(launch_arnoldi_givens<T>(h->n, std::min(j + 1, m), m, h->partB, h->ctl, s));
     h->launches += 1;
     return JFNK_OK;
 }
@@ -803,12 +1020,15 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
     // one extra (speculative) preconditioner apply and Jacobian product per cycle
     // cost more than the basis passes it saves: it keeps three passes.
     const bool fused = pc && !h->G.pc_schur;
+    int iters_before = 0;
     for (int cycle = 0;; ++cycle) {
+        bool graph = false;
         if (fused) {
-            jfnk_status st = fused_cycle<T>(h, uT, learned, arnoldi_pairs, lag);
+            jfnk_status st = fused_cycle<T>(h, uT, learned, arnoldi_pairs, lag, &graph);
             if (st != JFNK_OK) return st;
         }
         for (int j = 0; j < m && !fused; ++j) {
+            h->kt_step = j;
             T* vj = V + (size_t)j * ld;
             T* zj = Z + (size_t)j * ld;
             if (pc) {
@@ -867,12 +1087,19 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
                 if (h->hdone[j - lag]) break;
             }
         }
+        h->kt_step = -1;
         CK(launch_update<T>(Z, ld, h->x, h->mixed ? xT : nullptr, n, h->part, h->ctl, s));
         h->launches += 1;
         jfnk_status st = read_ctl(h);
         if (st != JFNK_OK) return st;
         const Ctl& c = *h->hctl;
         *iters = c.iters;
+        if (h->kt_mask) {   // this cycle's timed launches, those past its end left out
+            const int cols = c.iters - iters_before;
+            if (graph) kt_drain_graph(h, cols);
+            kt_drain_cycle(h, cols, fused);
+        }
+        iters_before = c.iters;
         if (c.nan) return JFNK_ERR_NAN;
         if (c.converged) {
             *conv = 1;

@@ -29,7 +29,8 @@ EXPORTS = (
     "jfnk_create", "jfnk_destroy", "jfnk_set_surface_flux", "jfnk_rhs", "jfnk_residual",
     "jfnk_jv", "jfnk_precond_apply", "jfnk_step", "jfnk_step_host", "jfnk_budgets",
     "jfnk_get_launch_count", "jfnk_status_str", "jfnk_kernel_timing", "jfnk_kernel_timing_read",
-    "jfnk_budgets_static", "jfnk_autotune", "jfnk_set_tiles",
+    "jfnk_kernel_timing_sampled",
+    "jfnk_budgets_static", "jfnk_autotune", "jfnk_set_tiles", "jfnk_set_cycle_graph",
     "jfnk_create_batch", "jfnk_destroy_batch", "jfnk_batch_handle", "jfnk_step_batch",
     "jfnk_unet_init", "jfnk_unet_num_weights", "jfnk_unet_get_weights", "jfnk_unet_set_weights",
     "jfnk_unet_capture", "jfnk_unet_pair_count", "jfnk_unet_get_pair", "jfnk_unet_train",
@@ -120,9 +121,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.jfnk_get_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
     lib.jfnk_kernel_timing.argtypes = [P, ctypes.c_uint]
     lib.jfnk_kernel_timing_read.argtypes = [P, ctypes.POINTER(KernelTime)]
+    lib.jfnk_kernel_timing_sampled.argtypes = [P, ctypes.c_uint, I]
     lib.jfnk_budgets_static.argtypes = [ctypes.POINTER(Grid), P, P, P]
     lib.jfnk_autotune.argtypes = [P, P, ctypes.POINTER(ctypes.c_int)]
     lib.jfnk_set_tiles.argtypes = [P, I, I]
+    lib.jfnk_set_cycle_graph.argtypes = [P, I]
     lib.jfnk_create_batch.argtypes = [I, ctypes.POINTER(Grid), ctypes.POINTER(Strat), ctypes.POINTER(Sgs),
                                       ctypes.POINTER(Opts), P, ctypes.POINTER(P)]
     lib.jfnk_destroy_batch.argtypes = [P]
@@ -266,12 +269,13 @@ class Solver:
         return {"E_k": b.E_k, "E_p": b.E_p, "sum_theta": b.sum_theta, "sum_div": b.sum_div,
                 "max": list(b.max[:nf]), "min": list(b.min[:nf])}
 
-    def kernel_timing(self, families=KERNEL_FAMILIES):
-        """Start CUDA-event timing of the named kernel families (resets the accumulators)."""
+    def kernel_timing(self, families=KERNEL_FAMILIES, every: int = 1):
+        """Start CUDA-event timing of the named kernel families (resets the accumulators);
+        launches inside GMRES cycles are timed at Krylov steps j = 0 mod `every`."""
         mask = 0
         for f in families:
             mask |= 1 << KERNEL_FAMILIES.index(f)
-        _check(self.lib.jfnk_kernel_timing(self.h, mask), "jfnk_kernel_timing")
+        _check(self.lib.jfnk_kernel_timing_sampled(self.h, mask, int(every)), "jfnk_kernel_timing_sampled")
 
     def kernel_timing_read(self) -> dict:
         arr = (KernelTime * len(KERNEL_FAMILIES))()
@@ -287,6 +291,10 @@ class Solver:
 
     def set_tiles(self, tile_jv: int, tile_pc: int):
         _check(self.lib.jfnk_set_tiles(self.h, int(tile_jv), int(tile_pc)), "jfnk_set_tiles")
+
+    def set_cycle_graph(self, steps: int):
+        """Krylov steps per captured graph segment of a GMRES cycle (0: stream launches)."""
+        _check(self.lib.jfnk_set_cycle_graph(self.h, int(steps)), "jfnk_set_cycle_graph")
 
     def launch_count(self) -> int:
         c = ctypes.c_longlong(0)
