@@ -371,6 +371,8 @@ def run_batch(args, rank: int, world: int, local_rank: int):
         cases = [synth.with_options(c, precond=jfnk.PC_NONLINEAR) for c in cases]
     stream = torch.cuda.current_stream()
     batch = jfnk.Batch(cases, stream=stream)
+    if args.cycle_graph >= 0:
+        batch.set_cycle_graph(args.cycle_graph)
     for i, c in enumerate(cases):
         batch.set_surface_flux(i, torch.from_numpy(synth.heat_flux(c)).cuda())
     U0 = [synth.initial_state(c) for c in cases]

@@ -278,7 +278,9 @@ jfnk_status jfnk_kernel_timing_read(jfnk_handle* h, jfnk_kernel_time* out);
  * handle (full workspace) and a non-blocking stream created by the batch; a
  * batch step forks the caller's stream into the instance streams, runs every
  * instance's Newton / GMRES sequence concurrently from one host thread per
- * instance, and joins back, so independent instances overlap on the GPU. */
+ * instance, and joins back, so independent instances overlap on the GPU.
+ * Instance handles launch their GMRES cycles as stream launches
+ * (jfnk_set_cycle_graph(h, 0)); jfnk_batch_handle gives access to change it. */
 #define JFNK_MAX_BATCH 256
 typedef struct jfnk_batch jfnk_batch;
 
@@ -428,26 +430,28 @@ jfnk_status jfnk_autotune(jfnk_handle* h, const double* u, int* tiles);
 /* Set the tile-shape indices (0 .. JFNK_NUM_TILE_SHAPES-1) directly. */
 jfnk_status jfnk_set_tiles(jfnk_handle* h, int tile_jv, int tile_pc);
 
-/* Launch the Krylov steps of a GMRES cycle as CUDA graphs (Section 2.5.1's
- * restarted FGMRES(m), right-preconditioned path with the field-block
- * preconditioner, float32 or float64).  steps > 0: the cycle's m steps are
- * captured once into segments of `steps` steps each (steps > m is taken as
- * m) and each segment is one graph launch; the host polls for the end of the
- * cycle once per segment instead of once per step.  steps = 0: every kernel
- * is a separate stream launch.  jfnk_create sets min(m,
- * JFNK_CYCLE_GRAPH_SEGMENT) for grids of at most
+/* Launch the Krylov steps of GMRES cycles as CUDA graphs (Section 2.5.1's
+ * restarted FGMRES(m), every preconditioner but the learned one, float32
+ * or float64).  steps > 0: the cycle's m steps are captured once into
+ * segments of `steps` steps each (steps > m is taken as m) and each segment
+ * is one graph launch; the host polls for the end of the cycle once per
+ * segment instead of once per step.  steps = 0: every kernel is a separate
+ * stream launch.  steps = JFNK_CYCLE_GRAPH_AUTO (the default of jfnk_create):
+ * one step per segment with the Schur complement, min(m,
+ * JFNK_CYCLE_GRAPH_SEGMENT) on grids of at most
  * JFNK_CYCLE_GRAPH_SEGMENT_POINTS points and m above.  Results are
  * bit-identical either way: every kernel of a step returns at entry once the
  * cycle has ended, so steps launched past the end change nothing.  The
- * segments are captured on a private stream (the handle's first fused cycle
- * runs as stream launches) and again whenever the grid description, tiles,
- * surface flux, sweep count, preconditioner or kernel-timing mask change;
- * timed families are timed by event nodes inside the graphs.  The learned
- * preconditioner and pair recording use stream launches.  Returns
- * JFNK_ERR_INVALID_ARG for h NULL or steps < 0. */
+ * segments are captured on a private stream (the first cycle with each
+ * preconditioner runs as stream launches) and again whenever the grid
+ * description, tiles, surface flux, sweep count, preconditioner or
+ * kernel-timing settings change; timed families are timed by event nodes
+ * inside the graphs.  The learned preconditioner and pair recording use
+ * stream launches.  Returns JFNK_ERR_INVALID_ARG for h NULL or steps < -1. */
 jfnk_status jfnk_set_cycle_graph(jfnk_handle* h, int steps);
 
-/* Default graph segment length and the grid size up to which it applies. */
+#define JFNK_CYCLE_GRAPH_AUTO (-1)
+/* Default segment length (not the Schur complement) and the grid size up to which it applies. */
 #define JFNK_CYCLE_GRAPH_SEGMENT 8
 #define JFNK_CYCLE_GRAPH_SEGMENT_POINTS 262144
 

@@ -68,6 +68,10 @@ extern "C" jfnk_status jfnk_create_batch(int n, const jfnk_grid* grids, const jf
             delete b;
             return st;
         }
+        // Concurrent instances keep the GPU busy between one instance's launches,
+        // and graph segments would run Krylov steps past a cycle's end that take
+        // time from the other instances: stream launches by default.
+        jfnk_set_cycle_graph(b->h[i], 0);
     }
     *out = b;
     return JFNK_OK;

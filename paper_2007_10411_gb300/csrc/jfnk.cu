@@ -74,17 +74,19 @@ struct jfnk_handle {
     UNet* net;
     float *capX, *capT;
     int cap_cap, cap_kinds;
-    // graph-captured Krylov steps of the fused cycle: gseg steps per segment
+    // graph-captured Krylov steps of a cycle: gseg steps per segment (-1: the
+    // default of the cycle's kind, see cycle_segment)
     // (0: one stream launch per kernel), captured on a private stream and
     // keyed on everything the captured launches read from the host
-    int gseg, gnseg, gwarm;
+    int gseg, gnseg;
     cudaStream_t gstream;
     cudaGraphExec_t gexec[KMAX];
     long long gnl[KMAX];          // kernel launches per segment
     Geo gG;
     int gsweeps, gseg_key;
     unsigned int gkt_mask;
-    int gkt_every;
+    int gkt_every, gprecond;
+    unsigned int gwarm_modes;     // preconditioner modes whose cycles have run once as stream launches
     const void *guT, *gZ, *gw2;
 };
 
@@ -223,11 +225,11 @@ static void kt_drain_cycle(jfnk_handle* h, int cols, bool fused) {
 static void kt_drain(jfnk_handle* h) { kt_drain_cycle(h, -1, false); }
 
 // Timings of a captured cycle's steps (valid launches only), after the cycle.
-static void kt_drain_graph(jfnk_handle* h, int cols) {
+static void kt_drain_graph(jfnk_handle* h, int cols, bool fused) {
     if (!h->gkt_mask) return;
     for (int j = 0; j <= std::min(cols, h->m - 1); ++j)
         for (int f = 0; f < JFNK_KF_COUNT; ++f)
-            if (((h->gkt_mask >> f) & 1u) && j % h->gkt_every == h->gkt_every / 2 && kt_valid(f, j, cols, true))
+            if (((h->gkt_mask >> f) & 1u) && j % h->gkt_every == h->gkt_every / 2 && kt_valid(f, j, cols, fused))
                 kt_add(h, f, h->gkt_start[j][f], h->gkt_stop[j][f], h->gkt_b[j][f]);
 }
 
@@ -316,9 +318,7 @@ extern "C" jfnk_status jfnk_create(const jfnk_grid* grid, const jfnk_strat* stra
     h->m = opts->krylov_m;
     h->kt_step = -1;
     h->kt_every = 1;
-    h->gseg = (size_t)grid->nx * (grid->dim == 3 ? grid->ny : 1) * grid->nz <= JFNK_CYCLE_GRAPH_SEGMENT_POINTS
-                  ? std::min(h->m, JFNK_CYCLE_GRAPH_SEGMENT)
-                  : h->m;
+    h->gseg = JFNK_CYCLE_GRAPH_AUTO;
     const int dim = grid->dim;
     const int ny = dim == 3 ? grid->ny : 1;
     const int nf = dim == 3 ? 5 : 4;
@@ -602,8 +602,8 @@ extern "C" jfnk_status jfnk_set_tiles(jfnk_handle* h, int tile_jv, int tile_pc) 
 }
 
 extern "C" jfnk_status jfnk_set_cycle_graph(jfnk_handle* h, int steps) {
-    if (!h || steps < 0) return JFNK_ERR_INVALID_ARG;
-    h->gseg = std::min(steps, h->m);
+    if (!h || steps < JFNK_CYCLE_GRAPH_AUTO) return JFNK_ERR_INVALID_ARG;
+    h->gseg = steps < 0 ? JFNK_CYCLE_GRAPH_AUTO : std::min(steps, h->m);
     return JFNK_OK;
 }
 
@@ -772,14 +772,14 @@ static jfnk_status apply_jv(jfnk_handle* h, const T* uT, const T* z, T* w, int c
     return JFNK_OK;
 }
 
-// One GMRES cycle of the right-preconditioned path with the second projection
-// of CGS2 lagged behind the next Jacobian product (Arnoldi passes CA and B per
-// step, see arnoldi_ca): step j takes the direction d_j = v_0 (j = 0) or
-// w'_{j-1}, z_j = M^{-1} d_j (+ N(d_j) for the learned correction), w_j = J z_j;
-// pass CA forms v_j, updates column j-1 of the Hessenberg / Givens state and
-// projects w_j once; pass B projects it again into w'_j.  The last column of a
-// full cycle gets its Givens update alone.  The w'_{j-1} / w_j buffers
-// alternate between w and w2.
+// One Krylov step of the fused cycle (right preconditioner but the Schur
+// complement), with the second projection of CGS2 lagged behind the next
+// Jacobian product (Arnoldi passes CA and B per step, see arnoldi_ca): step j
+// takes the direction d_j = v_0 (j = 0) or w'_{j-1}, z_j = M^{-1} d_j
+// (+ N(d_j) for the learned correction), w_j = J z_j; pass CA forms v_j,
+// updates column j-1 of the Hessenberg / Givens state and projects w_j once;
+// pass B projects it again into w'_j.  The w'_{j-1} / w_j buffers alternate
+// between w and w2.
 template <typename T>
 static jfnk_status fused_step(jfnk_handle* h, const T* uT, bool learned, bool arnoldi_pairs, int j) {
     cudaStream_t s = h->stream;
@@ -838,6 +838,88 @@ static jfnk_status fused_step(jfnk_handle* h, const T* uT, bool learned, bool ar
     return JFNK_OK;
 }
 
+// One Krylov step of the three-pass cycle (no preconditioner, the Schur
+// complement, or nonlinear preconditioning from the left): z_j = M^{-1} v_j
+// (right) or v_j, w = J z_j (left: w <- M^{-1} w), pass A h1 = V^T w, pass B
+// w' = w - V h1 and h2 = V^T w', pass C (block 0: Hessenberg / Givens update
+// of column j) v_{j+1} = (w' - V h2) / h_{j+1,j}.
+template <typename T>
+static jfnk_status plain_step(jfnk_handle* h, const T* uT, bool learned, bool arnoldi_pairs, int j) {
+    cudaStream_t s = h->stream;
+    const Geo& G = h->G;
+    const size_t n = h->n, ld = h->ld;
+    const int m = h->m;
+    const bool left = h->opts.precond == JFNK_PC_NONLINEAR;
+    const bool pc = h->opts.precond != JFNK_PC_NONE && !left;
+    T* V = (T*)h->V;
+    T* Z = pc ? (T*)h->Z : V;
+    T* w = (T*)h->w;
+    h->kt_step = j;
+    T* vj = V + (size_t)j * ld;
+    T* zj = Z + (size_t)j * ld;
+    if (pc) {
+        kt_begin(h, JFNK_KF_PRECOND);
+        CK(launch_precond<T>(G, h->opts.pc_sweeps, vj, zj, (T*)h->za, (T*)h->zb, (T*)h->da, (T*)h->db,
+                             (const T*)h->nu, h->part, h->ctl, 1, s, &h->launches));
+        kt_end(h, JFNK_KF_PRECOND, pc_bytes(h));
+    }
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (learned) {   // z_j += N(v_j), then the FD step for the new ||z_j||
+            kt_begin(h, JFNK_KF_UNET);
+            CK(unet_apply(h->net, vj, zj, 1, &h->ctl->done, s));
+            kt_end(h, JFNK_KF_UNET, 3.0 * (double)n * sizeof(float));
+            CK(launch_pc_eps(zj, n, h->part, h->ctl, s));
+            h->launches += unet_launches_per_apply() + 1;
+        }
+    }
+    jfnk_status st = apply_jv<T>(h, uT, zj, w, 1);
+    if (st != JFNK_OK) return st;
+    T* wa = w;                      // the vector the Arnoldi step orthogonalises
+    if (left) {                     // w <- M^{-1} J v_j
+        kt_begin(h, JFNK_KF_PRECOND);
+        CK(launch_precond<T>(G, h->opts.pc_sweeps, w, (T*)h->tB, (T*)h->za, (T*)h->zb, (T*)h->da, (T*)h->db,
+                             (const T*)h->nu, h->part, h->ctl, 1, s, &h->launches));
+        kt_end(h, JFNK_KF_PRECOND, pc_bytes(h));
+        CK(launch_unit_eps(h->ctl, s));      // the next product acts on the unit vector v_{j+1}
+        h->launches += 1;
+        wa = (T*)h->tB;
+    }
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (arnoldi_pairs) {   // (J z_j, z_j) is an exact inverse pair
+            CK(launch_pair_arnoldi(w, (float*)h->tA, n, h->part, h->ctl, s));
+            CK(launch_precond<float>(G, h->opts.pc_sweeps, (const float*)h->tA, (float*)h->tB, (float*)h->za,
+                                     (float*)h->zb, (float*)h->da, (float*)h->db, (const float*)h->nu, h->part,
+                                     h->ctl, 1, s, &h->launches));
+            CK(launch_pair_store<float>((const float*)h->tA, zj, (const float*)h->tB, h->capX, h->capT, n,
+                                        h->cap_cap, 1, h->ctl, s));
+            h->launches += 4;
+        }
+    }
+    const double vb = (double)n * sizeof(T);
+    kt_begin(h, JFNK_KF_ARNOLDI_A);
+    CK(launch_arnoldi_a<T>(V, ld, wa, n, j + 1, h->part, h->ctl, s));
+    kt_end(h, JFNK_KF_ARNOLDI_A, (j + 2) * vb);
+    kt_begin(h, JFNK_KF_ARNOLDI_B);
+    CK(launch_arnoldi_b<T>(V, ld, wa, n, j + 1, h->part, h->partB, h->ctl, s));
+    kt_end(h, JFNK_KF_ARNOLDI_B, (j + 3) * vb);   // reads v_0..v_j, w; writes w'
+    kt_begin(h, JFNK_KF_ARNOLDI_C);
+    CK(launch_arnoldi_c<T>(V, ld, wa, n, j + 1, m, h->partB, h->ctl, s));
+    kt_end(h, JFNK_KF_ARNOLDI_C, (j + 3) * vb);
+    h->launches += 3;
+    return JFNK_OK;
+}
+
+// Krylov steps per captured segment.  By default one for the Schur
+// complement (a solve takes a few steps, and a longer segment runs its
+// expensive steps past the end), otherwise JFNK_CYCLE_GRAPH_SEGMENT on grids
+// up to JFNK_CYCLE_GRAPH_SEGMENT_POINTS points and the whole cycle above,
+// where the steps are long enough that those past the end cost little.
+static int cycle_segment(const jfnk_handle* h) {
+    if (h->gseg >= 0) return h->gseg;
+    if (h->G.pc_schur) return 1;
+    return h->npt <= (size_t)JFNK_CYCLE_GRAPH_SEGMENT_POINTS ? std::min(h->m, JFNK_CYCLE_GRAPH_SEGMENT) : h->m;
+}
+
 static void graph_release(jfnk_handle* h) {
     if (h->gnseg > 0) cudaStreamSynchronize(h->stream);   // no launch of them in flight
     for (int k = 0; k < KMAX; ++k)
@@ -854,7 +936,7 @@ static void graph_release(jfnk_handle* h) {
 // captured launches read nothing from the host but the Geo, the sweep count
 // and the buffer pointers, which form the key a later cycle compares.
 template <typename T>
-static jfnk_status graph_capture(jfnk_handle* h, const T* uT) {
+static jfnk_status graph_capture(jfnk_handle* h, const T* uT, bool fused) {
     graph_release(h);
     if (!h->gstream) CK(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
     if (h->kt_mask && !h->gkt_ready) {
@@ -865,7 +947,7 @@ static jfnk_status graph_capture(jfnk_handle* h, const T* uT) {
             }
         h->gkt_ready = true;
     }
-    const int m = h->m, S = h->gseg;
+    const int m = h->m, S = cycle_segment(h);
     const int nseg = (m + S - 1) / S;
     cudaStream_t user = h->stream;
     h->stream = h->gstream;
@@ -879,7 +961,7 @@ static jfnk_status graph_capture(jfnk_handle* h, const T* uT) {
             break;
         }
         for (int j = k * S; j < std::min(m, (k + 1) * S) && st == JFNK_OK; ++j)
-            st = fused_step<T>(h, uT, false, false, j);
+            st = fused ? fused_step<T>(h, uT, false, false, j) : plain_step<T>(h, uT, false, false, j);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(h->gstream, &g);
         h->gnl[k] = h->launches - l0;
@@ -908,40 +990,38 @@ static jfnk_status graph_capture(jfnk_handle* h, const T* uT) {
     h->gw2 = h->w2;
     h->gkt_mask = h->kt_mask;
     h->gkt_every = h->kt_every;
+    h->gprecond = h->opts.precond;
     return JFNK_OK;
 }
 
 template <typename T>
 static bool graph_current(const jfnk_handle* h, const T* uT) {
-    return h->gnseg > 0 && h->gseg_key == h->gseg && h->gsweeps == h->opts.pc_sweeps && h->guT == uT &&
+    return h->gnseg > 0 && h->gseg_key == cycle_segment(h) && h->gsweeps == h->opts.pc_sweeps && h->guT == uT &&
            h->gZ == h->Z && h->gw2 == h->w2 && h->gkt_mask == h->kt_mask &&
-           h->gkt_every == h->kt_every &&
+           h->gkt_every == h->kt_every && h->gprecond == h->opts.precond &&
            memcmp(&h->gG, &h->G, sizeof(Geo)) == 0;
 }
 
-// One GMRES cycle of the right-preconditioned path with the second projection
-// of CGS2 lagged behind the next Jacobian product (Arnoldi passes CA and B per
-// step, see arnoldi_ca): step j takes the direction d_j = v_0 (j = 0) or
-// w'_{j-1}, z_j = M^{-1} d_j (+ N(d_j) for the learned correction), w_j = J z_j;
-// pass CA forms v_j, updates column j-1 of the Hessenberg / Givens state and
-// projects w_j once; pass B projects it again into w'_j.  The last column of a
-// full cycle gets its Givens update alone.  The w'_{j-1} / w_j buffers
-// alternate between w and w2.  The host learns that the cycle ended from a
-// copy of ctl->done made after each step (stream launches) or each captured
-// segment (graph launches), read with a lag so that the GPU never waits for it.
+// One GMRES cycle: fused steps (fused_step; the last column of a full cycle
+// then gets its Givens update alone) or three-pass steps (plain_step).  The
+// host learns that the cycle ended from a copy of ctl->done made after each
+// step (stream launches) or each captured segment of steps (graph launches),
+// read with a lag so that the GPU never waits for it.
 template <typename T>
-static jfnk_status fused_cycle(jfnk_handle* h, const T* uT, bool learned, bool arnoldi_pairs, int lag,
-                               bool* used_graph) {
+static jfnk_status run_cycle(jfnk_handle* h, const T* uT, bool fused, bool learned, bool arnoldi_pairs, int lag,
+                             bool* used_graph) {
     cudaStream_t s = h->stream;
     const int m = h->m;
-    // the first fused cycle of a handle runs as stream launches (one-time kernel
-    // attribute set-up happens outside any capture); later ones may use graphs
-    const bool graph = h->gseg > 0 && h->gwarm && !learned && !arnoldi_pairs;
-    h->gwarm = 1;
+    // the first cycle of each preconditioner mode runs as stream launches (one-time
+    // kernel attribute set-up happens outside any capture); later ones may use graphs
+    const unsigned int mode_bit = 1u << h->opts.precond;
+    const bool graph = cycle_segment(h) > 0 && (h->gwarm_modes & mode_bit) && !learned && !arnoldi_pairs;
+    h->gwarm_modes |= mode_bit;
     *used_graph = graph;
+    int ncol = m;   // columns the closing Givens update of a fused cycle may cover
     if (graph) {
         if (!graph_current<T>(h, uT)) {
-            jfnk_status st = graph_capture<T>(h, uT);
+            jfnk_status st = graph_capture<T>(h, uT, fused);
             if (st != JFNK_OK) return st;
         }
         for (int k = 0; k < h->gnseg; ++k) {
@@ -954,26 +1034,26 @@ static jfnk_status fused_cycle(jfnk_handle* h, const T* uT, bool learned, bool a
                 if (h->hdone[k - 1]) break;
             }
         }
-        // Givens update of the last column (returns at once when the cycle ended earlier)
-        CK(launch_arnoldi_givens<T>(h->n, m, m, h->partB, h->ctl, s));
-        h->launches += 1;
-        return JFNK_OK;
-    }
-    int j = 0;
-    for (; j < m; ++j) {
-        jfnk_status st = fused_step<T>(h, uT, learned, arnoldi_pairs, j);
-        if (st != JFNK_OK) return st;
-        CK(cudaMemcpyAsync(&h->hdone[j], &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaEventRecord(h->ev[j], s));
-        if (j >= lag) {
-            CK(cudaEventSynchronize(h->ev[j - lag]));
-            if (h->hdone[j - lag]) break;
+    } else {
+        int j = 0;
+        for (; j < m; ++j) {
+            jfnk_status st = fused ? fused_step<T>(h, uT, learned, arnoldi_pairs, j)
+                                   : plain_step<T>(h, uT, learned, arnoldi_pairs, j);
+            if (st != JFNK_OK) return st;
+            CK(cudaMemcpyAsync(&h->hdone[j], &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaEventRecord(h->ev[j], s));
+            if (j >= lag) {
+                CK(cudaEventSynchronize(h->ev[j - lag]));
+                if (h->hdone[j - lag]) break;
+            }
         }
+        ncol = std::min(j + 1, m);
+        h->kt_step = -1;
     }
-    h->kt_step = -1;
-    // Givens update of the cycle's last column (returns at once when the cycle ended earlier)
-    CK(launch_arnoldi_givens<T>(h->n, std::min(j + 1, m), m, h->partB, h->ctl, s));
-    h->launches += 1;
+    if (fused) {   // Givens update of the last column (returns at once when the cycle ended earlier)
+        CK(launch_arnoldi_givens<T>(h->n, ncol, m, h->partB, h->ctl, s));
+        h->launches += 1;
+    }
     return JFNK_OK;
 }
 
@@ -1014,7 +1094,7 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
     *restarts = 0;
     *conv = 0;
     *switched = 0;
-    // Two-pass Arnoldi steps (fused_cycle) pay for themselves where a solve runs
+    // Two-pass Arnoldi steps (fused_step) pay for themselves where a solve runs
     // many Krylov steps per expensive preconditioner apply; the Schur-complement
     // preconditioner converges in a few steps per solve, where the lagged scheme's
     // one extra (speculative) preconditioner apply and Jacobian product per cycle
@@ -1023,70 +1103,8 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
     int iters_before = 0;
     for (int cycle = 0;; ++cycle) {
         bool graph = false;
-        if (fused) {
-            jfnk_status st = fused_cycle<T>(h, uT, learned, arnoldi_pairs, lag, &graph);
-            if (st != JFNK_OK) return st;
-        }
-        for (int j = 0; j < m && !fused; ++j) {
-            h->kt_step = j;
-            T* vj = V + (size_t)j * ld;
-            T* zj = Z + (size_t)j * ld;
-            if (pc) {
-                kt_begin(h, JFNK_KF_PRECOND);
-                CK(launch_precond<T>(G, h->opts.pc_sweeps, vj, zj, (T*)h->za, (T*)h->zb, (T*)h->da,
-                                     (T*)h->db, (const T*)h->nu, h->part, h->ctl, 1, s, &h->launches));
-                kt_end(h, JFNK_KF_PRECOND, pc_bytes(h));
-            }
-            if constexpr (sizeof(T) == sizeof(float)) {
-                if (learned) {   // z_j += N(v_j), then the FD step for the new ||z_j||
-                    kt_begin(h, JFNK_KF_UNET);
-                    CK(unet_apply(h->net, vj, zj, 1, &h->ctl->done, s));
-                    kt_end(h, JFNK_KF_UNET, 3.0 * (double)n * sizeof(float));
-                    CK(launch_pc_eps(zj, n, h->part, h->ctl, s));
-                    h->launches += unet_launches_per_apply() + 1;
-                }
-            }
-            jfnk_status st = apply_jv<T>(h, uT, zj, w, 1);
-            if (st != JFNK_OK) return st;
-            T* wa = w;                      // the vector the Arnoldi step orthogonalises
-            if (left) {                     // w <- M^{-1} J v_j
-                kt_begin(h, JFNK_KF_PRECOND);
-                CK(launch_precond<T>(G, h->opts.pc_sweeps, w, (T*)h->tB, (T*)h->za, (T*)h->zb, (T*)h->da,
-                                     (T*)h->db, (const T*)h->nu, h->part, h->ctl, 1, s, &h->launches));
-                kt_end(h, JFNK_KF_PRECOND, pc_bytes(h));
-                CK(launch_unit_eps(h->ctl, s));      // the next product acts on the unit vector v_{j+1}
-                h->launches += 1;
-                wa = (T*)h->tB;
-            }
-            if constexpr (sizeof(T) == sizeof(float)) {
-                if (arnoldi_pairs) {   // (J z_j, z_j) is an exact inverse pair
-                    CK(launch_pair_arnoldi(w, (float*)h->tA, n, h->part, h->ctl, s));
-                    CK(launch_precond<float>(G, h->opts.pc_sweeps, (const float*)h->tA, (float*)h->tB,
-                                             (float*)h->za, (float*)h->zb, (float*)h->da, (float*)h->db,
-                                             (const float*)h->nu, h->part, h->ctl, 1, s, &h->launches));
-                    CK(launch_pair_store<float>((const float*)h->tA, zj, (const float*)h->tB, h->capX, h->capT, n,
-                                                h->cap_cap, 1, h->ctl, s));
-                    h->launches += 4;
-                }
-            }
-            const double vb = (double)n * sizeof(T);
-            kt_begin(h, JFNK_KF_ARNOLDI_A);
-            CK(launch_arnoldi_a<T>(V, ld, wa, n, j + 1, h->part, h->ctl, s));
-            kt_end(h, JFNK_KF_ARNOLDI_A, (j + 2) * vb);
-            kt_begin(h, JFNK_KF_ARNOLDI_B);
-            CK(launch_arnoldi_b<T>(V, ld, wa, n, j + 1, h->part, h->partB, h->ctl, s));
-            kt_end(h, JFNK_KF_ARNOLDI_B, (j + 3) * vb);   // reads v_0..v_j, w; writes w'
-            kt_begin(h, JFNK_KF_ARNOLDI_C);
-            CK(launch_arnoldi_c<T>(V, ld, wa, n, j + 1, m, h->partB, h->ctl, s));
-            kt_end(h, JFNK_KF_ARNOLDI_C, (j + 3) * vb);
-            h->launches += 3;
-            CK(cudaMemcpyAsync(&h->hdone[j], &h->ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-            CK(cudaEventRecord(h->ev[j], s));
-            if (j >= lag) {
-                CK(cudaEventSynchronize(h->ev[j - lag]));
-                if (h->hdone[j - lag]) break;
-            }
-        }
+        jfnk_status st0 = run_cycle<T>(h, uT, fused, learned, arnoldi_pairs, lag, &graph);
+        if (st0 != JFNK_OK) return st0;
         h->kt_step = -1;
         CK(launch_update<T>(Z, ld, h->x, h->mixed ? xT : nullptr, n, h->part, h->ctl, s));
         h->launches += 1;
@@ -1096,7 +1114,7 @@ static jfnk_status gmres_solve(jfnk_handle* h, const T* uT, int* iters, int* res
         *iters = c.iters;
         if (h->kt_mask) {   // this cycle's timed launches, those past its end left out
             const int cols = c.iters - iters_before;
-            if (graph) kt_drain_graph(h, cols);
+            if (graph) kt_drain_graph(h, cols, fused);
             kt_drain_cycle(h, cols, fused);
         }
         iters_before = c.iters;

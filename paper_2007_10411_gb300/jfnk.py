@@ -293,7 +293,8 @@ class Solver:
         _check(self.lib.jfnk_set_tiles(self.h, int(tile_jv), int(tile_pc)), "jfnk_set_tiles")
 
     def set_cycle_graph(self, steps: int):
-        """Krylov steps per captured graph segment of a GMRES cycle (0: stream launches)."""
+        """Krylov steps per captured graph segment of a GMRES cycle (0: stream launches;
+        -1: the library's default for the cycle's kind)."""
         _check(self.lib.jfnk_set_cycle_graph(self.h, int(steps)), "jfnk_set_cycle_graph")
 
     def launch_count(self) -> int:
@@ -396,6 +397,11 @@ class Batch:
         h = ctypes.c_void_p()
         _check(self.lib.jfnk_batch_handle(self.b, i, ctypes.byref(h)), "jfnk_batch_handle")
         _check(self.lib.jfnk_set_surface_flux(h, None if H is None else _ptr(H)), "jfnk_set_surface_flux")
+
+    def set_cycle_graph(self, steps: int):
+        """jfnk_set_cycle_graph on every instance's handle."""
+        for i in range(self.n):
+            _check(self.lib.jfnk_set_cycle_graph(self.handle(i), int(steps)), "jfnk_set_cycle_graph")
 
     def handle(self, i: int):
         h = ctypes.c_void_p()

@@ -29,13 +29,14 @@ def jf():
     return jfnk
 
 
-def stable_case(nx, nz, prec, m=20):
+def stable_case(nx, nz, prec, m=20, precond=synth.PC_BLOCK, sweeps=2):
     c = synth.case("tiny_%dx%d" % (nx, nz))
     c["strat"]["beta"] = synth.brunt_beta(0.01)
     c["sgs"]["mode"] = synth.SGS_SMAGORINSKY
     c["opts"]["precision"] = prec
     c["opts"]["krylov_m"] = m
-    c["opts"]["pc_sweeps"] = 2
+    c["opts"]["precond"] = precond
+    c["opts"]["pc_sweeps"] = sweeps
     return c
 
 
@@ -60,6 +61,11 @@ CASES = [
     ("thermal_neutral_128x64", None),                       # float64, GMRES(30), four sweeps
     ("stable_mixed_256x128", (256, 128, synth.PREC_MIXED, 20)),
     ("stable_fp64_100x37", (100, 37, synth.PREC_FP64, 8)),   # ragged tiles, restarts
+    # three-pass cycles: acoustic Schur complement, nonlinear (left), none
+    ("schur_mixed_130x70", (130, 70, synth.PREC_MIXED, 20, synth.PC_SCHUR, 8)),
+    ("schur_fp64_64x32", (64, 32, synth.PREC_FP64, 4, synth.PC_SCHUR, 4)),
+    ("nonlinear_mixed_128x64", (128, 64, synth.PREC_MIXED, 12, synth.PC_NONLINEAR, 2)),
+    ("none_fp64_64x32", (64, 32, synth.PREC_FP64, 10, synth.PC_NONE, 2)),
 ]
 
 
@@ -73,12 +79,13 @@ def test_graph_cycle_matches_stream_launches(name, spec, segment):
     assert all(x["converged"] for x in st_ref)
     assert counts(st) == counts(st_ref)
     assert np.array_equal(got, ref)
-    if segment == 32:
+    if segment == 32 and st_ref[0]["gmres_per_newton"][0] < c["opts"]["krylov_m"] - 2:
         # whole-cycle graphs launch every step of a cycle (those past its end return at once)
         assert n > n_ref
 
 
 def test_graph_recaptured_after_tiles_flux_and_preconditioner_change():
+    # also switches between the fused and three-pass cycles on one handle
     c = stable_case(128, 64, synth.PREC_MIXED, m=16)
     c["init"] = {"kind": "rest", "H0": 200.0, "patch_halfwidth": c["grid"]["lx"] / 5, "xi": 0.1, "l": 1.5}
     U = synth.random_state(c, 3, amp=(0.3, 0.1, 0.001))
@@ -98,6 +105,11 @@ def test_graph_recaptured_after_tiles_flux_and_preconditioner_change():
         seq.append(s.step(u))
         s.set_precond(synth.PC_BLOCK)
         seq.append(s.step(u))
+        s.set_precond(synth.PC_NONLINEAR)
+        seq.append(s.step(u))
+        seq.append(s.step(u))
+        s.set_precond(synth.PC_BLOCK)
+        seq.append(s.step(u))
         torch.cuda.synchronize()
         results.append((u.cpu().numpy(), counts(seq)))
         s.close()
@@ -105,11 +117,12 @@ def test_graph_recaptured_after_tiles_flux_and_preconditioner_change():
     assert np.array_equal(results[0][0], results[1][0])
 
 
-def test_set_cycle_graph_rejects_negative_steps():
+def test_set_cycle_graph_argument_rules():
     c = stable_case(64, 32, synth.PREC_FP64)
     s = jf().Solver(c)
     with pytest.raises(jf().JfnkError):
-        s.set_cycle_graph(-1)
+        s.set_cycle_graph(-2)
+    s.set_cycle_graph(-1)            # the default rule
     s.set_cycle_graph(1000)          # taken as m
     s.close()
 
