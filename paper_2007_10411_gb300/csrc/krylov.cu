@@ -407,7 +407,7 @@ __device__ __forceinline__ void work_b(const VT (&v)[CH], VT wv, T* __restrict__
     }
 }
 
-// Pass B, split over KS lanes per element: h1 from pass A's partials (every
+// Pass B, split over KS = NV / 8 lanes per element: h1 from pass A's partials (every
 // block, grid_sums), w' = w - V h1 (stored over w), ||w'||^2 and h2 = V^T w'
 // into this pass's partials.  Each lane keeps its CH basis entries in
 // registers for both uses, so every basis vector is read from memory once;
@@ -421,7 +421,9 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int 
     const int done = ctl->done;     // no writer during this launch; read beside the partials
     // jscale >= 0: w is used as zscale[jscale] w (lagged second projection, see arnoldi_ca)
     const T sig = jscale >= 0 ? T(ctl->zscale[jscale]) : T(1);
-    constexpr int KS = 4, CH = NV / KS;
+    // eight basis entries per lane (KS = 1, 2, 4 lanes per element for NV = 8, 16, 32):
+    // each lane keeps up to nine loads in flight, and for small nv no lane idles
+    constexpr int CH = NV < 8 ? NV : 8, KS = NV / CH;
     __shared__ double h1d[NV];
     __shared__ T h1s[NV];
     __shared__ T red[NV + 1][NTHREADS / 32];
