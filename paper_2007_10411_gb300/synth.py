@@ -50,6 +50,11 @@ PC_NONLINEAR = 4      # nonlinear preconditioning (field block on the left)
 
 
 def _base_case(dim, nx, nz, lx, lz, ny=1, ly=1.0):
+    # Two Chebyshev sweeps per field block: at the eddy coefficients of these
+    # workloads each block's Gershgorin interval [2/dt, 2/dt + 2.25 K_max sum 1/h^2]
+    # has a condition number close to 1, where two sweeps already bound the
+    # error of the block inverse by ~5e-4; three or four sweeps give the same
+    # Krylov counts at a higher cost per apply.
     theta0 = 300.0
     return {
         "grid": {"dim": dim, "nx": nx, "ny": ny, "nz": nz,
@@ -59,7 +64,7 @@ def _base_case(dim, nx, nz, lx, lz, ny=1, ly=1.0):
                   "gamma_p": R_GAS / CV, "rho0": P0 / (R_GAS * theta0), "cp": CP},
         "sgs": {"mode": SGS_CONST, "K_M": 10.0, "K_H": 14.1, "Cs": 0.18, "Pr": 0.71},
         "opts": {"precision": PREC_FP64, "wavelet_p": 2, "krylov_m": 30,
-                 "flexible": 1, "precond": PC_BLOCK, "pc_sweeps": 4,
+                 "flexible": 1, "precond": PC_BLOCK, "pc_sweeps": 2,
                  "newton_rtol": 1e-8, "newton_atol_factor": 1e-13, "eta": 1e-4,
                  "max_newton": 20, "max_restarts": 20, "dt": 1.0,
                  "scale_u": 10.0, "scale_theta": 1.0, "scale_p": 0.01},
@@ -95,11 +100,6 @@ def case(name: str) -> dict:
         c["strat"]["beta"] = brunt_beta(0.01)
         c["sgs"].update(mode=SGS_SMAGORINSKY, Cs=0.18, Pr=0.71)
         c["opts"]["precision"] = PREC_MIXED
-        # Two Chebyshev sweeps per block: at these eddy viscosities the blocks'
-        # Gershgorin interval [2/dt, 2/dt + 2.25 K_max sum 1/h^2] has a condition
-        # number below 1.1, where two sweeps already bound the error of the block
-        # inverse by 5e-4 (four sweeps cost 13 % more per step for the same counts).
-        c["opts"]["pc_sweeps"] = 2
         c["init"] = {"kind": "bubble", "dtheta": 2.0, "radius": 2000.0, "zc": 2000.0,
                      "noise": 0.01}
         return c

@@ -126,7 +126,7 @@ def test_jv_parity_3d(grid, var, prec):
 @pytest.mark.parametrize("grid", GRIDS3[1:])
 @pytest.mark.parametrize("var", range(len(VARS3)))
 @pytest.mark.parametrize("prec", [synth.PREC_FP64, synth.PREC_MIXED])
-@pytest.mark.parametrize("sweeps", [1, 4])
+@pytest.mark.parametrize("sweeps", [1, 2, 4])
 def test_precond_parity_3d(grid, var, prec, sweeps):
     c = make3(*grid, prec=prec, **VARS3[var])
     c["opts"]["pc_sweeps"] = sweeps
