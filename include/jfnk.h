@@ -431,22 +431,22 @@ jfnk_status jfnk_autotune(jfnk_handle* h, const double* u, int* tiles);
 jfnk_status jfnk_set_tiles(jfnk_handle* h, int tile_jv, int tile_pc);
 
 /* Launch the Krylov steps of GMRES cycles as CUDA graphs (Section 2.5.1's
- * restarted FGMRES(m), every preconditioner but the learned one, float32
- * or float64).  steps > 0: the cycle's m steps are captured once into
- * segments of `steps` steps each (steps > m is taken as m) and each segment
+ * restarted FGMRES(m), every preconditioner, float32 or float64).
+ * steps > 0: the cycle's m steps are captured once into segments of
+ * `steps` steps each (steps > m is taken as m) and each segment
  * is one graph launch; the host polls for the end of the cycle once per
  * segment instead of once per step.  steps = 0: every kernel is a separate
  * stream launch.  steps = JFNK_CYCLE_GRAPH_AUTO (the default of jfnk_create):
- * one step per segment with the Schur complement, min(m,
- * JFNK_CYCLE_GRAPH_SEGMENT) on grids of at most
+ * one step per segment with the Schur complement, two with the learned
+ * correction, min(m, JFNK_CYCLE_GRAPH_SEGMENT) on grids of at most
  * JFNK_CYCLE_GRAPH_SEGMENT_POINTS points and m above.  Results are
  * bit-identical either way: every kernel of a step returns at entry once the
  * cycle has ended, so steps launched past the end change nothing.  The
  * segments are captured on a private stream (the first cycle with each
  * preconditioner runs as stream launches) and again whenever the grid
  * description, tiles, surface flux, sweep count, preconditioner or
- * kernel-timing settings change; timed families are timed by event nodes
- * inside the graphs.  The learned preconditioner and pair recording use
+ * kernel-timing settings or the learned network's weights change; timed
+ * families are timed by event nodes inside the graphs.  Pair recording uses
  * stream launches.  Returns JFNK_ERR_INVALID_ARG for h NULL or steps < -1. */
 jfnk_status jfnk_set_cycle_graph(jfnk_handle* h, int steps);
 

@@ -85,7 +85,8 @@ struct jfnk_handle {
     Geo gG;
     int gsweeps, gseg_key;
     unsigned int gkt_mask;
-    int gkt_every, gprecond;
+    int gkt_every, gprecond, glearned;
+    unsigned long long gnet_ver;  // network version a learned capture holds
     unsigned int gwarm_modes;     // preconditioner modes whose cycles have run once as stream launches
     const void *guT, *gZ, *gw2;
 };
@@ -911,12 +912,14 @@ static jfnk_status plain_step(jfnk_handle* h, const T* uT, bool learned, bool ar
 
 // Krylov steps per captured segment.  By default one for the Schur
 // complement (a solve takes a few steps, and a longer segment runs its
-// expensive steps past the end), otherwise JFNK_CYCLE_GRAPH_SEGMENT on grids
-// up to JFNK_CYCLE_GRAPH_SEGMENT_POINTS points and the whole cycle above,
-// where the steps are long enough that those past the end cost little.
-static int cycle_segment(const jfnk_handle* h) {
+// expensive steps past the end), two with the learned correction (eight
+// network launches per step), otherwise JFNK_CYCLE_GRAPH_SEGMENT on grids up
+// to JFNK_CYCLE_GRAPH_SEGMENT_POINTS points and the whole cycle above, where
+// the steps are long enough that those past the end cost little.
+static int cycle_segment(const jfnk_handle* h, bool learned) {
     if (h->gseg >= 0) return h->gseg;
     if (h->G.pc_schur) return 1;
+    if (learned) return std::min(h->m, 2);
     return h->npt <= (size_t)JFNK_CYCLE_GRAPH_SEGMENT_POINTS ? std::min(h->m, JFNK_CYCLE_GRAPH_SEGMENT) : h->m;
 }
 
@@ -936,7 +939,7 @@ static void graph_release(jfnk_handle* h) {
 // captured launches read nothing from the host but the Geo, the sweep count
 // and the buffer pointers, which form the key a later cycle compares.
 template <typename T>
-static jfnk_status graph_capture(jfnk_handle* h, const T* uT, bool fused) {
+static jfnk_status graph_capture(jfnk_handle* h, const T* uT, bool fused, bool learned) {
     graph_release(h);
     if (!h->gstream) CK(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
     if (h->kt_mask && !h->gkt_ready) {
@@ -947,7 +950,7 @@ static jfnk_status graph_capture(jfnk_handle* h, const T* uT, bool fused) {
             }
         h->gkt_ready = true;
     }
-    const int m = h->m, S = cycle_segment(h);
+    const int m = h->m, S = cycle_segment(h, learned);
     const int nseg = (m + S - 1) / S;
     cudaStream_t user = h->stream;
     h->stream = h->gstream;
@@ -961,7 +964,7 @@ static jfnk_status graph_capture(jfnk_handle* h, const T* uT, bool fused) {
             break;
         }
         for (int j = k * S; j < std::min(m, (k + 1) * S) && st == JFNK_OK; ++j)
-            st = fused ? fused_step<T>(h, uT, false, false, j) : plain_step<T>(h, uT, false, false, j);
+            st = fused ? fused_step<T>(h, uT, learned, false, j) : plain_step<T>(h, uT, learned, false, j);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(h->gstream, &g);
         h->gnl[k] = h->launches - l0;
@@ -991,14 +994,17 @@ static jfnk_status graph_capture(jfnk_handle* h, const T* uT, bool fused) {
     h->gkt_mask = h->kt_mask;
     h->gkt_every = h->kt_every;
     h->gprecond = h->opts.precond;
+    h->glearned = learned;
+    h->gnet_ver = learned ? unet_version(h->net) : 0;
     return JFNK_OK;
 }
 
 template <typename T>
-static bool graph_current(const jfnk_handle* h, const T* uT) {
-    return h->gnseg > 0 && h->gseg_key == cycle_segment(h) && h->gsweeps == h->opts.pc_sweeps && h->guT == uT &&
+static bool graph_current(const jfnk_handle* h, const T* uT, bool learned) {
+    return h->gnseg > 0 && h->gseg_key == cycle_segment(h, learned) && h->gsweeps == h->opts.pc_sweeps && h->guT == uT &&
            h->gZ == h->Z && h->gw2 == h->w2 && h->gkt_mask == h->kt_mask &&
            h->gkt_every == h->kt_every && h->gprecond == h->opts.precond &&
+           h->glearned == (int)learned && (!learned || h->gnet_ver == unet_version(h->net)) &&
            memcmp(&h->gG, &h->G, sizeof(Geo)) == 0;
 }
 
@@ -1012,16 +1018,20 @@ static jfnk_status run_cycle(jfnk_handle* h, const T* uT, bool fused, bool learn
                              bool* used_graph) {
     cudaStream_t s = h->stream;
     const int m = h->m;
-    // the first cycle of each preconditioner mode runs as stream launches (one-time
-    // kernel attribute set-up happens outside any capture); later ones may use graphs
-    const unsigned int mode_bit = 1u << h->opts.precond;
-    const bool graph = cycle_segment(h) > 0 && (h->gwarm_modes & mode_bit) && !learned && !arnoldi_pairs;
+    // the first cycle of each preconditioner mode (with and without the learned
+    // correction) runs as stream launches (one-time kernel attribute set-up happens
+    // outside any capture); later ones may use graphs
+    const unsigned int mode_bit = 1u << (2 * h->opts.precond + (learned ? 1 : 0));
+    const bool graph = cycle_segment(h, learned) > 0 && (h->gwarm_modes & mode_bit) && !arnoldi_pairs;
     h->gwarm_modes |= mode_bit;
     *used_graph = graph;
     int ncol = m;   // columns the closing Givens update of a fused cycle may cover
     if (graph) {
-        if (!graph_current<T>(h, uT)) {
-            jfnk_status st = graph_capture<T>(h, uT, fused);
+        if constexpr (sizeof(T) == sizeof(float)) {
+            if (learned) CK(unet_prepare(h->net, s));   // weights composed outside the capture
+        }
+        if (!graph_current<T>(h, uT, learned)) {
+            jfnk_status st = graph_capture<T>(h, uT, fused, learned);
             if (st != JFNK_OK) return st;
         }
         for (int k = 0; k < h->gnseg; ++k) {

@@ -12,6 +12,7 @@
 // kernel with flipped, transposed weights; the weight gradient is a float32
 // reduction over pixel tiles (CUDA cores) with one atomic add per weight and
 // tile.
+#include <atomic>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -939,6 +940,7 @@ struct UNet {
     bf16 *wb, *wt;                          // bfloat16 weights, flipped/transposed copies
     bf16* wc;                               // L0d composed with L0c (inference), [tap][16][48]
     bool wc_stale;                          // the composition predates the current weights
+    unsigned long long version;             // bumped whenever what an apply computes may change
     // activations (NHWC bfloat16) and gradients
     bf16 *x0, *h0a, *cat0, *p1, *h1a, *cat1, *p2, *h2a, *h2b, *h1c, *h0c;
     bf16 *dy, *dh0c, *dcat0, *dh1c, *dcat1, *dh2b, *dh2a, *dp2, *ds1, *dh1a, *dp1, *ds0, *dh0a;
@@ -965,6 +967,12 @@ bool unet_grid_ok(int dim, int nx, int ny, int nz) {
     return dim == 3 && ny % 64 == 0 && nz % 4 == 0 && (long long)nx * ny * nz < (1ll << 31);
 }
 
+// Versions are unique over the process (a new network never repeats an old one's).
+static unsigned long long next_version() {
+    static std::atomic<unsigned long long> counter{0};
+    return ++counter;
+}
+
 UNet* unet_create(int dim, int nx, int ny, int nz, const double* balance, unsigned long long seed,
                   cudaError_t* err) {
     *err = cudaSuccess;
@@ -975,6 +983,7 @@ UNet* unet_create(int dim, int nx, int ny, int nz, const double* balance, unsign
     UNet* n = new (std::nothrow) UNet;
     if (!n) { *err = cudaErrorMemoryAllocation; return nullptr; }
     memset(n, 0, sizeof(*n));
+    n->version = next_version();
     n->nx = nx;
     n->ny = ny;
     n->nz = nz;
@@ -1054,6 +1063,7 @@ cudaError_t unet_set_weights(UNet* n, const float* host, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     to_bf16<<<grid_for(n->nw), 256, 0, s>>>(n->w32, n->wb, n->nw);
     n->wc_stale = true;
+    n->version = next_version();
     if ((e = cudaMemsetAsync(n->m32, 0, n->nw * 4, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(n->v32, 0, n->nw * 4, s)) != cudaSuccess) return e;
     n->step = 0;
@@ -1159,6 +1169,7 @@ static cudaError_t backward(UNet* n, cudaStream_t s) {
 cudaError_t unet_set_engine(UNet* n, int engine) {
     if (engine != ENGINE_TCGEN05 && engine != ENGINE_MMA_SYNC) return cudaErrorInvalidValue;
     n->engine = engine;
+    n->version = next_version();
     return cudaSuccess;
 }
 
@@ -1171,12 +1182,19 @@ cudaError_t unet_check(UNet* n, cudaStream_t s) {
     return e ? cudaErrorLaunchTimeout : cudaSuccess;
 }
 
-cudaError_t unet_apply(UNet* n, const float* x, float* y, int accumulate, const int* skip, cudaStream_t s) {
+cudaError_t unet_prepare(UNet* n, cudaStream_t s) {
     if (n->wc_stale) {
         compose_l0<<<27, 256, 0, s>>>(n->w32 + n->woff[L0c], n->w32 + n->woff[L0d], n->bal.nf, n->wc);
         UCK(cudaGetLastError());
         n->wc_stale = false;
     }
+    return cudaSuccess;
+}
+
+unsigned long long unet_version(const UNet* n) { return n->version; }
+
+cudaError_t unet_apply(UNet* n, const float* x, float* y, int accumulate, const int* skip, cudaStream_t s) {
+    UCK(unet_prepare(n, s));
     return forward_fused(n, x, y, accumulate, s, skip);
 }
 
@@ -1218,6 +1236,7 @@ cudaError_t unet_train(UNet* n, const float* X, const float* T, int npairs, int 
             const float c2 = 1.0f / (1.0f - powf(0.999f, (float)n->step));
             adam_step<<<grid_for(n->nw), 256, 0, s>>>(n->w32, n->g32, n->m32, n->v32, n->wb, n->nw, lr, c1, c2);
             n->wc_stale = true;
+            n->version = next_version();
             UCK(cudaGetLastError());
             if (loss_hist) {
                 double sc[2];

@@ -49,6 +49,12 @@ cudaError_t unet_set_weights(UNet* net, const float* host, cudaStream_t s);
 // overlap x.  When skip is
 // non-NULL and *skip != 0 at kernel run time, every kernel returns at entry.
 cudaError_t unet_apply(UNet* net, const float* x, float* y, int accumulate, const int* skip, cudaStream_t s);
+// The one-time work an apply does before its launches (composing the first
+// layers' weights after they changed), so that a capture of unet_apply holds
+// only the network's fixed launch sequence.
+cudaError_t unet_prepare(UNet* net, cudaStream_t s);
+// Changes whenever weights, training steps or the engine change what an apply computes.
+unsigned long long unet_version(const UNet* net);
 int unet_launches_per_apply();
 
 // Convolution engine: 0 tcgen05.mma with TMEM accumulators (default), 1 the

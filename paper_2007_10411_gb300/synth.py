@@ -45,6 +45,7 @@ PREC_MIXED = 1
 
 PC_NONE = 0
 PC_BLOCK = 1
+PC_UNET = 2           # field block plus the learned correction
 PC_SCHUR = 3
 PC_NONLINEAR = 4      # nonlinear preconditioning (field block on the left)
 

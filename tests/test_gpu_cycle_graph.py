@@ -156,3 +156,28 @@ def test_kernel_timing_counts_only_launches_that_did_work(prec, every):
         assert k0[fam]["launches"] == k1[fam]["launches"], fam
         assert k0[fam]["bytes"] == pytest.approx(k1[fam]["bytes"], rel=1e-12), fam
         assert k1[fam]["ms"] > 0.0, fam
+
+
+def test_learned_cycles_in_graphs_match_stream_launches():
+    # The learned correction's launches are captured with the cycle; a weight
+    # change between steps changes the network's version and forces a new
+    # capture, so graph and stream launches stay bit-identical.
+    c = stable_case(256, 128, synth.PREC_MIXED, m=20, precond=synth.PC_UNET)
+    U = synth.random_state(c, 21, amp=(0.3, 0.1, 0.001))
+    results = []
+    for segment in (0, 8):
+        s = jf().Solver(c)
+        s.set_cycle_graph(segment)
+        s.unet_init(11)
+        rng = np.random.default_rng(5)
+        nw = s.unet_num_weights()
+        s.unet_set_weights((0.01 * rng.standard_normal(nw)).astype(np.float32))
+        u = torch.from_numpy(U.copy()).cuda()
+        seq = [s.step(u) for _ in range(2)]
+        s.unet_set_weights((0.02 * rng.standard_normal(nw)).astype(np.float32))
+        seq += [s.step(u) for _ in range(2)]
+        torch.cuda.synchronize()
+        results.append((u.cpu().numpy(), counts(seq), [x["pc_switches"] for x in seq]))
+        s.close()
+    assert results[0][1] == results[1][1] and results[0][2] == results[1][2]
+    assert np.array_equal(results[0][0], results[1][0])
