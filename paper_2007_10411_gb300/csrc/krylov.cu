@@ -407,12 +407,12 @@ __device__ __forceinline__ void work_b(const VT (&v)[CH], VT wv, T* __restrict__
     }
 }
 
-// Pass B, split over KS = NV / 8 lanes per element: h1 from pass A's partials (every
+// Pass B, split over KS lanes per element: h1 from pass A's partials (every
 // block, grid_sums), w' = w - V h1 (stored over w), ||w'||^2 and h2 = V^T w'
 // into this pass's partials.  Each lane keeps its CH basis entries in
 // registers for both uses, so every basis vector is read from memory once;
-// the next element's loads are issued before the current one is combined
-// (software pipeline).
+// with at most eight entries per lane the next element's loads are issued
+// before the current one is combined (software pipeline).
 template <typename T, int NV>
 __global__ void __launch_bounds__(NTHREADS, 2)
 arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int nv,
@@ -421,9 +421,15 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int 
     const int done = ctl->done;     // no writer during this launch; read beside the partials
     // jscale >= 0: w is used as zscale[jscale] w (lagged second projection, see arnoldi_ca)
     const T sig = jscale >= 0 ? T(ctl->zscale[jscale]) : T(1);
-    // eight basis entries per lane (KS = 1, 2, 4 lanes per element for NV = 8, 16, 32):
-    // each lane keeps up to nine loads in flight, and for small nv no lane idles
-    constexpr int CH = NV < 8 ? NV : 8, KS = NV / CH;
+    // one lane per element up to NV = 16, two above (four for a float64 basis at
+    // NV = 32, where two would not fit the registers): a lane keeps up to sixteen
+    // loads in flight, and the instantiation nearest above nv (8, 12, 16, 24, 32)
+    // leaves few of its entries empty
+    constexpr int KS = NV <= 16 ? 1 : ((sizeof(T) == sizeof(double) && NV > 24) ? 4 : 2), CH = NV / KS;
+    // the next element's loads are issued ahead (software pipeline) where the
+    // registers allow it; twelve or more entries per lane are deep enough without
+    constexpr bool PF = CH <= 8;
+    static_assert(CH * KS == NV && CH <= 16, "lane split");
     __shared__ double h1d[NV];
     __shared__ T h1s[NV];
     __shared__ T red[NV + 1][NTHREADS / 32];
@@ -443,24 +449,33 @@ arnoldi_b(const T* __restrict__ V, size_t ldv, T* __restrict__ w, size_t n, int 
     const size_t nvec = n / W;
     const size_t g0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) / KS;
     const size_t gstride = (size_t)gridDim.x * blockDim.x / KS;
-    VT vn[CH], wn = zerov<VT>();
     const Walk wk = make_walk(g0, gstride, nvec, !(nv & 1));
-    if (wk.cnt > 0) {
-        load_b<T, VT, CH>(V, ldv, wk.at(0), nv, q, vn);
-        wn = scalev(reinterpret_cast<const VT*>(w)[wk.at(0)], sig);
-    }
-    for (size_t cc = 0; cc < wk.cnt; ++cc) {
-        const size_t i = wk.at(cc);
-        VT v[CH];
-#pragma unroll
-        for (int c = 0; c < CH; ++c) v[c] = vn[c];
-        const VT wv = wn;
-        if (cc + 1 < wk.cnt) {
-            const size_t inext = wk.at(cc + 1);
-            load_b<T, VT, CH>(V, ldv, inext, nv, q, vn);
-            wn = scalev(reinterpret_cast<const VT*>(w)[inext], sig);
+    if constexpr (!PF) {
+        for (size_t cc = 0; cc < wk.cnt; ++cc) {
+            const size_t i = wk.at(cc);
+            VT v[CH];
+            load_b<T, VT, CH>(V, ldv, i, nv, q, v);
+            work_b<T, VT, CH, KS>(v, scalev(reinterpret_cast<const VT*>(w)[i], sig), w, i, q, h1s, acc, accn);
         }
-        work_b<T, VT, CH, KS>(v, wv, w, i, q, h1s, acc, accn);
+    } else {
+        VT vn[CH], wn = zerov<VT>();
+        if (wk.cnt > 0) {
+            load_b<T, VT, CH>(V, ldv, wk.at(0), nv, q, vn);
+            wn = scalev(reinterpret_cast<const VT*>(w)[wk.at(0)], sig);
+        }
+        for (size_t cc = 0; cc < wk.cnt; ++cc) {
+            const size_t i = wk.at(cc);
+            VT v[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) v[c] = vn[c];
+            const VT wv = wn;
+            if (cc + 1 < wk.cnt) {
+                const size_t inext = wk.at(cc + 1);
+                load_b<T, VT, CH>(V, ldv, inext, nv, q, vn);
+                wn = scalev(reinterpret_cast<const VT*>(w)[inext], sig);
+            }
+            work_b<T, VT, CH, KS>(v, wv, w, i, q, h1s, acc, accn);
+        }
     }
     for (size_t i = nvec * W + g0; i < n; i += gstride) {
         T v[CH];
@@ -1022,7 +1037,9 @@ cudaError_t launch_arnoldi_b(const T* V, size_t ldv, T* w, size_t n, int nv, con
                              double* partB, Ctl* ctl, cudaStream_t s) {
     const int nb = grid_b<T>(n), na = grid_a<T>(n);
     if (nv <= 8) return launch_pdl(arnoldi_b<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl, -1);
+    if (nv <= 12) return launch_pdl(arnoldi_b<T, 12>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl, -1);
     if (nv <= 16) return launch_pdl(arnoldi_b<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl, -1);
+    if (nv <= 24) return launch_pdl(arnoldi_b<T, 24>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl, -1);
     return launch_pdl(arnoldi_b<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, na, partB, ctl, -1);
 }
 
@@ -1072,7 +1089,9 @@ cudaError_t launch_arnoldi_b_from(const T* V, size_t ldv, T* w, size_t n, int nv
     const int nb = grid_b<T>(n);
     const int js = nv > 1 ? nv - 1 : -1;    // step j = nv - 1 >= 1 follows pass CA: w is scaled
     if (nv <= 8) return launch_pdl(arnoldi_b<T, 8>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, nblkA, partB, ctl, js);
+    if (nv <= 12) return launch_pdl(arnoldi_b<T, 12>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, nblkA, partB, ctl, js);
     if (nv <= 16) return launch_pdl(arnoldi_b<T, 16>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, nblkA, partB, ctl, js);
+    if (nv <= 24) return launch_pdl(arnoldi_b<T, 24>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, nblkA, partB, ctl, js);
     return launch_pdl(arnoldi_b<T, 32>, nb, NTHREADS, 0, s, V, ldv, w, n, nv, partA, nblkA, partB, ctl, js);
 }
 template cudaError_t launch_arnoldi_b_from<float>(const float*, size_t, float*, size_t, int, const double*, int,
