@@ -585,6 +585,7 @@ arnoldi_ca(T* __restrict__ V, size_t ldv, const T* __restrict__ wprev, const T* 
     __shared__ T red[NV + 1][NTHREADS / 32];
     // block 0 writes ctl->done during this launch: one thread reads it for the whole block
     if (threadIdx.x == 0) done = *(volatile int*)&ctl->done;
+    for (int k = j + 1 + threadIdx.x; k <= NV; k += blockDim.x) tots[k] = T(0);   // h2 past the basis: zero
     grid_sums(reinterpret_cast<const P*>(partB), nblkB, j + 1, tot, tots);   // ||w'||^2, h2_0 .. h2_{j-1}
     if (done) return;
     if (blockIdx.x == 0) {
@@ -608,54 +609,80 @@ arnoldi_ca(T* __restrict__ V, size_t ldv, const T* __restrict__ wprev, const T* 
     __syncthreads();
     const T inv = inv_s;
     const T sig = sig_s;
-    T acc[NV];
+    // KS lanes per element (one up to NV = 16, two above; four for a float64
+    // basis at NV = 32): a lane loads all its basis entries before it combines
+    // them, so that they are in flight together; the lanes' parts of V h2 meet
+    // by shuffles and lane 0 stores v_j
+    constexpr int KS = NV <= 16 ? 1 : ((sizeof(T) == sizeof(double) && NV > 24) ? 4 : 2), CH = NV / KS;
+    const int q = threadIdx.x & (KS - 1);
+    T acc[CH];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = T(0);
+    for (int c = 0; c < CH; ++c) acc[c] = T(0);
     T accn = T(0);                  // v_j . w_j (v_j is formed in registers)
     const size_t nvec = n / W;
     const size_t nblk = gridDim.x - 1, blk = blockIdx.x - 1;
-    const size_t stride = nblk * blockDim.x;
+    const size_t g0 = (blk * blockDim.x + threadIdx.x) / KS;
+    const size_t gstride = nblk * blockDim.x / KS;
     T* vout = V + (size_t)j * ldv;
-    const Walk wk = make_walk(blk * blockDim.x + threadIdx.x, stride, nvec, (j + 1) & 1);
-    for (size_t c = 0; c < wk.cnt; ++c) {
-        const size_t i = wk.at(c);
-        VT wp = reinterpret_cast<const VT*>(wprev)[i];
+    const Walk wk = make_walk(g0, gstride, nvec, (j + 1) & 1);
+    for (size_t cc = 0; cc < wk.cnt; ++cc) {
+        const size_t i = wk.at(cc);
+        VT v[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int k = q * CH + c;
+            v[c] = k < j ? reinterpret_cast<const VT*>(V + k * ldv)[i] : zerov<VT>();
+        }
+        const VT wpv = reinterpret_cast<const VT*>(wprev)[i];
         const VT wv = scalev(reinterpret_cast<const VT*>(w)[i], sig);
+        VT sum = zerov<VT>();
 #pragma unroll
-        for (int k = 0; k < NV; ++k)
-            if (k < j) {
-                const VT vk = reinterpret_cast<const VT*>(V + k * ldv)[i];
-                wp = axpyv(wp, hs[k], vk);
-                acc[k] += dotv(vk, wv);
-            }
-        const VT vn = scalev(wp, inv);
-        reinterpret_cast<VT*>(vout)[i] = vn;
-        accn += dotv(vn, wv);
+        for (int c = 0; c < CH; ++c) {
+            sum = fmav(hs[q * CH + c], v[c], sum);
+            acc[c] += dotv(v[c], wv);
+        }
+        if (KS > 1) {
+            const unsigned mask = __activemask();     // the KS lanes of an element are active together
+#pragma unroll
+            for (int o = 1; o < KS; o <<= 1) sum = addv(sum, shfl_xor_v(mask, sum, o));
+        }
+        const VT vn = scalev(subv(wpv, sum), inv);
+        if (q == 0) {
+            reinterpret_cast<VT*>(vout)[i] = vn;
+            accn += dotv(vn, wv);
+        }
     }
-    for (size_t i = nvec * W + blk * blockDim.x + threadIdx.x; i < n; i += stride) {
-        T wp = wprev[i];
+    for (size_t i = nvec * W + g0; i < n; i += gstride) {
         const T wv = sig * w[i];
+        T sum = T(0);
 #pragma unroll
-        for (int k = 0; k < NV; ++k)
+        for (int c = 0; c < CH; ++c) {
+            const int k = q * CH + c;
             if (k < j) {
                 const T vk = V[k * ldv + i];
-                wp -= hs[k] * vk;
-                acc[k] += vk * wv;
+                sum = fmav(hs[k], vk, sum);
+                acc[c] += vk * wv;
             }
-        const T vn = wp * inv;
-        vout[i] = vn;
-        accn += vn * wv;
+        }
+        if (KS > 1) {
+            const unsigned mask = __activemask();
+#pragma unroll
+            for (int o = 1; o < KS; o <<= 1) sum += __shfl_xor_sync(mask, sum, o);
+        }
+        const T vn = (wprev[i] - sum) * inv;
+        if (q == 0) {
+            vout[i] = vn;
+            accn += vn * wv;
+        }
     }
     pdl_trigger();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        if (k < j) {
-            T x = acc[k];
+    for (int c = 0; c < CH; ++c) {
+        T x = acc[c];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) red[k][warp] = x;
-        }
+        for (int o = KS; o < 32; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane < KS && lane * CH + c < j) red[lane * CH + c][warp] = x;
     }
     {
         T x = accn;
@@ -1073,8 +1100,12 @@ cudaError_t launch_arnoldi_ca(T* V, size_t ldv, const T* wprev, const T* w, size
     const int nc = grid_ca<T>(n), nb = grid_b<T>(n);
     if (j + 1 <= 8)
         return launch_pdl(arnoldi_ca<T, 8>, nc, NTHREADS, 0, s, V, ldv, wprev, w, n, j, m, partB, nb, partA, ctl);
+    if (j + 1 <= 12)
+        return launch_pdl(arnoldi_ca<T, 12>, nc, NTHREADS, 0, s, V, ldv, wprev, w, n, j, m, partB, nb, partA, ctl);
     if (j + 1 <= 16)
         return launch_pdl(arnoldi_ca<T, 16>, nc, NTHREADS, 0, s, V, ldv, wprev, w, n, j, m, partB, nb, partA, ctl);
+    if (j + 1 <= 24)
+        return launch_pdl(arnoldi_ca<T, 24>, nc, NTHREADS, 0, s, V, ldv, wprev, w, n, j, m, partB, nb, partA, ctl);
     return launch_pdl(arnoldi_ca<T, 32>, nc, NTHREADS, 0, s, V, ldv, wprev, w, n, j, m, partB, nb, partA, ctl);
 }
 template cudaError_t launch_arnoldi_ca<float>(float*, size_t, const float*, const float*, size_t, int, int,
