@@ -933,11 +933,13 @@ static void graph_release(jfnk_handle* h) {
     h->gnseg = 0;
 }
 
-// Capture the cycle's m Krylov steps as segments of gseg steps.  Every kernel
-// of a step returns at entry once the device has ended the cycle (ctl->done),
-// so a segment launched past the end leaves the state untouched, and the
-// captured launches read nothing from the host but the Geo, the sweep count
-// and the buffer pointers, which form the key a later cycle compares.
+// Capture the cycle's m Krylov steps as segments of cycle_segment() steps.
+// Every kernel of a step returns at entry once the device has ended the cycle
+// (ctl->done), so a segment launched past the end leaves the state untouched,
+// and the captured launches depend on the host only through the Geo, the
+// sweep count, the preconditioner, the buffer pointers, the timing settings
+// and (learned cycles) the network's weight version: the key a later cycle
+// compares (graph_current).
 template <typename T>
 static jfnk_status graph_capture(jfnk_handle* h, const T* uT, bool fused, bool learned) {
     graph_release(h);

@@ -73,6 +73,8 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.jfnk_step(None, P(1), None) == jfnk.JFNK_ERR_INVALID_ARG
     assert lib.jfnk_jv(None, P(1), None, P(1), 0.0, P(1), None) == jfnk.JFNK_ERR_INVALID_ARG
     assert lib.jfnk_set_cycle_graph(None, 1) == jfnk.JFNK_ERR_INVALID_ARG
+    assert lib.jfnk_kernel_timing(None, 1) == jfnk.JFNK_ERR_INVALID_ARG
+    assert lib.jfnk_kernel_timing_sampled(None, 1, 5) == jfnk.JFNK_ERR_INVALID_ARG
     assert lib.jfnk_destroy(None) == jfnk.JFNK_OK
 
 
