@@ -522,6 +522,7 @@ arnoldi_c(T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int 
     // block 0 writes ctl->done during this launch: one thread reads it for the
     // whole block, so that every thread of a block takes the same branch
     if (threadIdx.x == 0) done = *(volatile int*)&ctl->done;
+    for (int k = nv + 1 + threadIdx.x; k <= NV; k += blockDim.x) tots[k] = T(0);   // h2 past the basis: zero
     grid_sums(reinterpret_cast<const typename PartOf<T>::type*>(partB), nblkB, nv + 1, tot, tots);
     if (done) return;
     if (blockIdx.x == 0) {
@@ -536,23 +537,49 @@ arnoldi_c(T* __restrict__ V, size_t ldv, const T* __restrict__ w, size_t n, int 
     }
     __syncthreads();
     const T inv = inv_s;
+    // KS = NV / 8 lanes per element (at most eight basis entries per lane, within
+    // the registers of three CTAs per SM); a lane loads all its entries before it
+    // combines them, the lanes' parts of V h2 meet by shuffles and lane 0 stores
+    constexpr int KS = NV <= 8 ? 1 : NV / 8, CH = NV / KS;
+    const int q = threadIdx.x & (KS - 1);
     const size_t nvec = n / W;
     const size_t nblk = gridDim.x - 1, blk = blockIdx.x - 1;
-    const size_t stride = nblk * blockDim.x;
+    const size_t g0 = (blk * blockDim.x + threadIdx.x) / KS;
+    const size_t gstride = nblk * blockDim.x / KS;
     T* vout = V + (size_t)nv * ldv;
-    const Walk wk = make_walk(blk * blockDim.x + threadIdx.x, stride, nvec, nv & 1);
-    for (size_t c = 0; c < wk.cnt; ++c) {
-        const size_t i = wk.at(c);
-        VT wp = reinterpret_cast<const VT*>(w)[i];
+    const Walk wk = make_walk(g0, gstride, nvec, nv & 1);
+    for (size_t cc = 0; cc < wk.cnt; ++cc) {
+        const size_t i = wk.at(cc);
+        VT v[CH];
 #pragma unroll
-        for (int k = 0; k < NV; ++k)
-            if (k < nv) wp = axpyv(wp, hs[k], reinterpret_cast<const VT*>(V + k * ldv)[i]);
-        reinterpret_cast<VT*>(vout)[i] = scalev(wp, inv);
+        for (int c = 0; c < CH; ++c) {
+            const int k = q * CH + c;
+            v[c] = k < nv ? reinterpret_cast<const VT*>(V + k * ldv)[i] : zerov<VT>();
+        }
+        const VT wv = reinterpret_cast<const VT*>(w)[i];
+        VT sum = zerov<VT>();
+#pragma unroll
+        for (int c = 0; c < CH; ++c) sum = fmav(hs[q * CH + c], v[c], sum);
+        if (KS > 1) {
+            const unsigned mask = __activemask();     // the KS lanes of an element are active together
+#pragma unroll
+            for (int o = 1; o < KS; o <<= 1) sum = addv(sum, shfl_xor_v(mask, sum, o));
+        }
+        if (q == 0) reinterpret_cast<VT*>(vout)[i] = scalev(subv(wv, sum), inv);
     }
-    for (size_t i = nvec * W + blk * blockDim.x + threadIdx.x; i < n; i += stride) {
-        T wp = w[i];
-        for (int k = 0; k < nv; ++k) wp -= hs[k] * V[k * ldv + i];
-        vout[i] = wp * inv;
+    for (size_t i = nvec * W + g0; i < n; i += gstride) {
+        T sum = T(0);
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int k = q * CH + c;
+            if (k < nv) sum = fmav(hs[k], V[k * ldv + i], sum);
+        }
+        if (KS > 1) {
+            const unsigned mask = __activemask();
+#pragma unroll
+            for (int o = 1; o < KS; o <<= 1) sum += __shfl_xor_sync(mask, sum, o);
+        }
+        if (q == 0) vout[i] = (w[i] - sum) * inv;
     }
 }
 
