@@ -74,3 +74,12 @@ def test_default_arguments(monkeypatch):
 def test_job_throughput_sums_over_ranks(world):
     one = bench.job_throughput(524288, 10, 1, 1000.0)
     assert bench.job_throughput(524288, 10, world, 1000.0) == pytest.approx(world * one)
+
+
+def test_metric_label_names_the_precision():
+    # the headline label is fixed; another workload or a float64 step says so in its label
+    assert bench.metric_name(bench.WORKLOAD) == bench.METRICS[bench.WORKLOAD]
+    assert "mixed FP32/FP64" in bench.metric_name(bench.WORKLOAD)
+    assert "FP64 JFNK" in bench.metric_name(bench.WORKLOAD, fp64=True)
+    assert "mixed" not in bench.metric_name(bench.WORKLOAD, fp64=True)
+    assert bench.metric_name("thermal_neutral_128x64", fp64=True).endswith("(thermal_neutral_128x64, FP64 JFNK)")
